@@ -1,0 +1,286 @@
+"""Seeded synthetic inputs: Si/C structures, Maxwell-Boltzmann velocities and
+parameter-file loading.
+
+This module only generates inputs. It holds lattice geometry, random
+displacements and placements, and Gaussian velocity draws, and none of the
+potential's arithmetic (no cutoff, bond order, charge or force code). Both the
+CUDA path and the CPU checker read the arrays it returns.
+
+The structures stand in for the shapes of the paper's MD cells (Sec. 3.3: a
+stepped 4H-SiC(0001) substrate of about 12,000 atoms with a fixed bottom; the
+fitting-set shapes of Sec. 2: SiC crystals, amorphous C, graphene, clusters).
+The paper ships no structure files, so every structure here is generated from
+ideal tetrahedral geometry at a = 4.36 A.
+
+Units: A, fs, u, eV, e. Types: 0 = Si, 1 = C.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SI, C = 0, 1
+TYPE_NAMES = ("Si", "C")
+# IUPAC standard atomic weights (u)
+MASS = np.array([28.0855, 12.011])
+KB_EV = 8.617333262e-5          # Boltzmann constant, eV/K
+EV_PER_U_TO_A2_FS2 = 9.648533212e-3  # 1 eV/u expressed in A^2/fs^2
+
+_PARAM_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "params")
+
+
+@dataclass
+class Structure:
+    """One periodic or open atomic configuration.
+
+    x: (N,3) float64 positions (A); types: (N,) int32; box: (3,) float64
+    orthorhombic edge lengths (ignored along non-periodic axes);
+    pbc: (3,) bool; frozen: (N,) bool atoms held fixed by the integrator.
+    """
+    name: str
+    x: np.ndarray
+    types: np.ndarray
+    box: np.ndarray
+    pbc: np.ndarray
+    frozen: np.ndarray = None
+    meta: dict = field(default_factory=dict)
+
+    def __post_init__(self):
+        self.x = np.ascontiguousarray(self.x, dtype=np.float64)
+        self.types = np.ascontiguousarray(self.types, dtype=np.int32)
+        self.box = np.asarray(self.box, dtype=np.float64)
+        self.pbc = np.asarray(self.pbc, dtype=bool)
+        if self.frozen is None:
+            self.frozen = np.zeros(len(self.types), dtype=bool)
+        self.frozen = np.ascontiguousarray(self.frozen, dtype=bool)
+
+    @property
+    def n(self) -> int:
+        return int(self.types.shape[0])
+
+
+def load_params(name: str = "p0") -> dict:
+    """Load a parameter set (JSON) shipped with the package."""
+    path = name if os.path.isfile(name) else os.path.join(_PARAM_DIR, f"{name}.json")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+# --------------------------------------------------------------------------
+# 3C-SiC bulk
+# --------------------------------------------------------------------------
+def sic_3c(ncell: int = 4, a: float = 4.36, disp: float = 0.05, seed: int = 1,
+           strain=None) -> Structure:
+    """Zincblende SiC, ncell^3 conventional cubic cells, periodic.
+
+    Si on the fcc sites, C on the fcc sites shifted by a(1/4,1/4,1/4). Every
+    coordinate is displaced by U(-disp, +disp) from a seeded generator.
+    strain: optional (3,3) symmetric strain applied as x -> (I + eps) x
+    (the box must stay orthorhombic, so only the diagonal is accepted).
+    """
+    fcc = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
+    basis = np.concatenate([fcc, fcc + 0.25])
+    btype = np.array([SI] * 4 + [C] * 4, dtype=np.int32)
+    g = np.arange(ncell)
+    cells = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    frac = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3)
+    x = frac * a
+    types = np.tile(btype, len(cells))
+    rng = np.random.default_rng(seed)
+    x = x + rng.uniform(-disp, disp, size=x.shape)
+    box = np.full(3, ncell * a)
+    if strain is not None:
+        eps = np.asarray(strain, dtype=np.float64)
+        if np.any(np.abs(eps - np.diag(np.diag(eps))) > 0):
+            raise ValueError("only diagonal strain keeps the box orthorhombic")
+        f = 1.0 + np.diag(eps)
+        x = x * f
+        box = box * f
+    x = np.mod(x, box)
+    return Structure(f"3C-SiC {ncell}x{ncell}x{ncell}", x, types, box,
+                     np.array([True, True, True]))
+
+
+# --------------------------------------------------------------------------
+# 4H-SiC(0001) Si-face slabs
+# --------------------------------------------------------------------------
+# In-plane sites of a hexagonal close-packed plane, in units of the
+# orthorhombic cell (a_h, sqrt(3) a_h); two lattice points per cell.
+_SITE = {
+    "A": np.array([[0.0, 0.0], [0.5, 0.5]]),
+    "B": np.array([[0.5, 1.0 / 6.0], [0.0, 2.0 / 3.0]]),
+    "C": np.array([[0.0, 1.0 / 3.0], [0.5, 5.0 / 6.0]]),
+}
+_STACK_4H = "ABCB"
+
+
+def sic_4h_slab(nx: int, ny: int, n_bilayers: int, a: float = 4.36,
+                step: str | None = None, n_frozen_bilayers: int = 2,
+                vacuum: float = 15.0) -> Structure:
+    """4H-SiC(0001) Si-terminated slab, periodic in x/y, open in z.
+
+    Orthorhombic in-plane cell a_h x sqrt(3) a_h with a_h = a/sqrt(2), four
+    atoms per bilayer per cell. Bilayer m holds a C plane on stacking site
+    S_m at z = m P and a Si plane on site S_(m+1) at z = m P + P/4
+    (P = a/sqrt(3)); the Si of bilayer m bonds straight up to the C of
+    bilayer m+1 (length 3P/4). The top plane is Si (Si face).
+
+    step: None (flat), "strip" (top bilayer kept only for x < Lx/2: two step
+    edges along y), or "staircase" (strip s = floor(4x/Lx) loses its top s
+    bilayers: three one-bilayer down-steps and one three-bilayer step at the
+    periodic boundary).
+    Bottom n_frozen_bilayers bilayers are marked frozen.
+    """
+    ah = a / math.sqrt(2.0)
+    P = a / math.sqrt(3.0)
+    Lx, Ly = nx * ah, ny * ah * math.sqrt(3.0)
+    gx, gy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    cells = np.stack([gx.ravel(), gy.ravel()], -1).astype(np.float64)
+    xs, ts, layer = [], [], []
+    for m in range(n_bilayers):
+        for plane, (typ, site, dz) in enumerate(
+                ((C, _STACK_4H[m % 4], 0.0), (SI, _STACK_4H[(m + 1) % 4], P / 4.0))):
+            pts = (cells[:, None, :] + _SITE[site][None, :, :]).reshape(-1, 2)
+            xy = pts * np.array([ah, ah * math.sqrt(3.0)])
+            z = np.full((len(xy), 1), m * P + dz)
+            xs.append(np.concatenate([xy, z], 1))
+            ts.append(np.full(len(xy), typ, dtype=np.int32))
+            layer.append(np.full(len(xy), m, dtype=np.int32))
+    x = np.concatenate(xs)
+    types = np.concatenate(ts)
+    layer = np.concatenate(layer)
+    keep = np.ones(len(x), dtype=bool)
+    if step == "strip":
+        keep &= ~((layer == n_bilayers - 1) & (x[:, 0] >= 0.5 * Lx))
+    elif step == "staircase":
+        strip = np.minimum((4.0 * x[:, 0] / Lx).astype(int), 3)
+        keep &= layer < (n_bilayers - strip)
+    elif step is not None:
+        raise ValueError(f"unknown step pattern {step!r}")
+    x, types, layer = x[keep], types[keep], layer[keep]
+    x[:, 2] += 1.0
+    frozen = layer < n_frozen_bilayers
+    thick = (n_bilayers - 1) * P + P / 4.0
+    box = np.array([Lx, Ly, thick + 2.0 + vacuum])
+    s = Structure(f"4H-SiC(0001) {nx}x{ny}x{n_bilayers} step={step}", x, types,
+                  box, np.array([True, True, False]), frozen)
+    s.meta["bilayer"] = layer
+    s.meta["atoms_per_bilayer"] = 4 * nx * ny
+    return s
+
+
+def add_adatoms(s: Structure, count: int, zmin: float = 1.5, zmax: float = 3.0,
+                min_sep: float = 1.2, typ: int = C, seed: int = 3,
+                lateral_radius: float = 3.0) -> Structure:
+    """Place `count` adatoms uniformly in-plane, zmin..zmax above the highest
+    atom within `lateral_radius` (periodic in x/y), rejecting any closer than
+    min_sep to an existing atom or to an earlier adatom."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    Lx, Ly = s.box[0], s.box[1]
+    xy_tree = cKDTree(np.mod(s.x[:, :2], [Lx, Ly]), boxsize=[Lx, Ly])
+    zshift = -s.x[:, 2].min() + 10.0
+    big = 1.0e6
+    pts = np.mod(s.x, [Lx, Ly, big]) + [0, 0, zshift]
+    tree3 = cKDTree(pts, boxsize=[Lx, Ly, big])
+    new = []
+    tries = 0
+    while len(new) < count:
+        tries += 1
+        if tries > 200 * count + 1000:
+            raise RuntimeError("could not place adatoms")
+        p = rng.uniform([0, 0], [Lx, Ly])
+        idx = xy_tree.query_ball_point(p, lateral_radius)
+        if not idx:
+            continue
+        z = s.x[idx, 2].max() + rng.uniform(zmin, zmax)
+        cand = np.array([p[0], p[1], z])
+        q = np.mod(cand, [Lx, Ly, big]) + [0, 0, zshift]
+        if tree3.query_ball_point(q, min_sep):
+            continue
+        if new:
+            d = np.array(new) - cand
+            d[:, :2] -= np.round(d[:, :2] / [Lx, Ly]) * [Lx, Ly]
+            if np.min(np.einsum("ij,ij->i", d, d)) < min_sep ** 2:
+                continue
+        new.append(cand)
+    x = np.concatenate([s.x, np.array(new).reshape(-1, 3)])
+    types = np.concatenate([s.types, np.full(count, typ, dtype=np.int32)])
+    frozen = np.concatenate([s.frozen, np.zeros(count, dtype=bool)])
+    box = s.box.copy()
+    box[2] = max(box[2], x[:, 2].max() + 10.0)
+    out = Structure(s.name + f" +{count} adatoms", x, types, box, s.pbc.copy(), frozen)
+    out.meta = dict(s.meta)
+    if "bilayer" in out.meta:
+        out.meta["bilayer"] = np.concatenate([s.meta["bilayer"], np.full(count, -1)])
+    return out
+
+
+# --------------------------------------------------------------------------
+# Workloads with the shapes of the benchmark configurations
+# --------------------------------------------------------------------------
+def bulk_3c_512(seed: int = 1) -> Structure:
+    """512-atom 3C-SiC, 4x4x4 cubic cells, a = 4.36 A, +-0.05 A displacements."""
+    return sic_3c(4, 4.36, 0.05, seed)
+
+
+def stepped_slab_20k() -> Structure:
+    """4H-SiC(0001) slab 24x14 cells x 15 bilayers with half the top bilayer
+    removed (two step edges): 19,488 atoms, bottom two bilayers frozen."""
+    return sic_4h_slab(24, 14, 15, step="strip")
+
+
+def stepped_slab_1m(seed: int = 3) -> Structure:
+    """4H-SiC(0001) slab 96x48 cells x 56 bilayers, staircase of three
+    one-bilayer steps, plus C adatoms numbering 5% of a bilayer's sites,
+    1.5-3 A above the surface: 1,005,466 atoms."""
+    s = sic_4h_slab(96, 48, 56, step="staircase")
+    n_ad = int(round(0.05 * s.meta["atoms_per_bilayer"]))
+    return add_adatoms(s, n_ad, seed=seed)
+
+
+def stepped_slab_small(nx: int = 12, ny: int = 6, n_bilayers: int = 8,
+                       seed: int = 3) -> Structure:
+    """A small stand-in with the same shape as the 1M-atom slab (staircase +
+    5% C adatoms), used where a full-size evaluation is too costly."""
+    s = sic_4h_slab(nx, ny, n_bilayers, step="staircase")
+    n_ad = max(1, int(round(0.05 * s.meta["atoms_per_bilayer"])))
+    return add_adatoms(s, n_ad, seed=seed)
+
+
+# --------------------------------------------------------------------------
+# Velocities
+# --------------------------------------------------------------------------
+def maxwell_boltzmann(types: np.ndarray, T: float, seed: int,
+                      frozen: np.ndarray | None = None) -> np.ndarray:
+    """Maxwell-Boltzmann velocities (A/fs) at exactly temperature T.
+
+    Each mobile component ~ N(0, kT/m). Frozen atoms get v = 0. The centre-of-
+    mass velocity is removed only when no atom is frozen. The draw is then
+    rescaled so that 2 KE / (dof k_B) = T with dof = 3 N_mobile (- 3 if the
+    centre-of-mass motion was removed).
+    """
+    types = np.asarray(types)
+    n = len(types)
+    frozen = np.zeros(n, bool) if frozen is None else np.asarray(frozen, bool)
+    m = MASS[types]
+    rng = np.random.default_rng(seed)
+    sd = np.sqrt(KB_EV * T / m * EV_PER_U_TO_A2_FS2)
+    v = rng.standard_normal((n, 3)) * sd[:, None]
+    v[frozen] = 0.0
+    mob = ~frozen
+    dof = 3 * int(mob.sum())
+    if not frozen.any() and n > 1:
+        vcm = (m[:, None] * v).sum(0) / m.sum()
+        v -= vcm
+        dof -= 3
+    if T > 0 and dof > 0:
+        ke = 0.5 * np.sum(m[:, None] * v * v) / EV_PER_U_TO_A2_FS2
+        t_now = 2.0 * ke / (dof * KB_EV)
+        v *= math.sqrt(T / t_now)
+    return v
