@@ -1,0 +1,203 @@
+/*
+ * ctbop.h — C ABI of libctbop: one MD step of the charge-transfer
+ * bond-order Si/C potential of Takamoto et al. (arXiv:1802.07871) on one GPU.
+ *
+ * What a step computes (paper references are sections and equations of the
+ * paper; "reading" marks choices the paper leaves open, documented with the
+ * library):
+ *   - environment sums zeta_1, zeta_2 of every directed bond (Sec. 2, Eq. 2)
+ *     and the vectorised bond order b_ij (Eq. 7, L = 2, p = 2);
+ *   - Tersoff-type pair energies with the covalent-ionic factor
+ *     1 - kappa (q_i - q_j)^2 on the attractive term (reading of f_q, Sec. 2);
+ *   - self energy E0 + chi q + J q^2 (Sec. 2 adds the constant E0) and a
+ *     shielded, tapered charge interaction over all periodic images;
+ *   - charges minimising the total energy at every step (Sec. 2), solved by
+ *     preconditioned conjugate gradients on the device;
+ *   - forces -dE/dx at the minimising charges, virial, per-atom energies;
+ *   - NVE velocity Verlet with frozen atoms (Sec. 3.3 fixes the substrate
+ *     bottom).
+ *
+ * Conventions
+ *   Units: Angstrom, fs, u, eV, e. Atom types: 0 = Si, 1 = C.
+ *   Every function returns CTBOP_OK (0) or a negative CTBOP_ERR_* code;
+ *   ctbop_last_error() gives a message for the last failure of that system.
+ *   A system handle is used from one host thread at a time (not reentrant).
+ *   Array arguments are plain pointers. `mem` says where a pointer lives:
+ *   CTBOP_HOST (pageable or pinned host memory) or CTBOP_DEVICE (device
+ *   memory of the system's GPU). Inputs are copied in; the caller keeps
+ *   ownership of every buffer it passes. The library owns its device memory.
+ *   Device-pointer transfers and compute/step calls are ordered on the
+ *   system's stream; host-pointer transfers and ctbop_status synchronise it.
+ *   Atoms are laid out replica by replica: atom_offsets[r]..atom_offsets[r+1]-1
+ *   belong to replica r; atoms of different replicas never interact.
+ */
+#ifndef CTBOP_H
+#define CTBOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define CTBOP_OK                    0
+#define CTBOP_ERR_INVALID_ARG      -1   /* null pointer, size mismatch, bad type or box */
+#define CTBOP_ERR_OOM              -2   /* device allocation failed */
+#define CTBOP_ERR_NEIGH_OVERFLOW   -3   /* neighbour capacity exceeded and could not grow */
+#define CTBOP_ERR_CG_NOT_CONVERGED -4   /* charge solve hit max_iter; results still written */
+#define CTBOP_ERR_NONFINITE        -5   /* non-finite energy, force or position */
+#define CTBOP_ERR_CUDA             -6   /* a CUDA runtime call failed */
+#define CTBOP_ERR_STATE            -7   /* call out of order (e.g. compute before positions) */
+
+/* ---- memory location of a pointer argument ----------------------------- */
+#define CTBOP_HOST   0
+#define CTBOP_DEVICE 1
+
+/* ---- precision policy --------------------------------------------------- */
+/* FP64: every quantity in double precision.
+ * MIXED: bond-order, cutoff, three-body, charge-kernel arithmetic and the
+ * CG matrix-vector products in float; positions as float offsets from the
+ * owning cell's origin (exact FP64 master copy kept); per-atom energies,
+ * virial, CG vectors, dot products and residual norms in double. */
+#define CTBOP_PREC_FP64  0
+#define CTBOP_PREC_MIXED 1
+
+/* ---- compute flags ------------------------------------------------------ */
+#define CTBOP_FIXED_CHARGES 1u   /* use the charges last set; skip the solve */
+
+/* ---- ctbop_get selectors (dst layouts) ---------------------------------- */
+#define CTBOP_GET_ENERGY    0   /* double[R]   total potential energy per replica (eV) */
+#define CTBOP_GET_FORCES    1   /* double[N*3] forces (eV/A) */
+#define CTBOP_GET_CHARGES   2   /* double[N]   charges (e) */
+#define CTBOP_GET_POSITIONS 3   /* double[N*3] positions (A); wrapped into the box along periodic axes at list rebuilds */
+#define CTBOP_GET_VELOCITIES 4  /* double[N*3] velocities (A/fs) */
+#define CTBOP_GET_VIRIAL    5   /* double[R*9] virial W = -sum_u u (x) dE/du, row-major 3x3 (eV) */
+#define CTBOP_GET_E_ATOM    6   /* double[N]   per-atom energies (eV) */
+#define CTBOP_GET_MU        7   /* double[R]   electronegativity (Lagrange multiplier of sum q = Q), eV/e */
+#define CTBOP_GET_KINETIC   8   /* double[R]   kinetic energy of the last step (eV) */
+
+/* ---- parameters --------------------------------------------------------- */
+/* Index conventions: pair tables [ti*2+tj] (symmetric for the pair block),
+ * ordered pair [ti*2+tj] for the bond-order block, ordered triplet
+ * [(ti*2+tj)*2+tk] (i centre, j bond partner, k third atom), then l = 0,1. */
+typedef struct ctbop_params {
+    /* pair: E_ij = 1/2 fc(r)[A e^{-lambda1 r} - c_ij b_ij B e^{-lambda2 r}],
+     * fc from R to S; c_ij = 1 - kappa (q_i - q_j)^2 */
+    double A[4], B[4], lambda1[4], lambda2[4], R[4], S[4], kappa[4];
+    /* bond order (Eq. 7): b = G[(g1+z1^n1)^-p + (g2+z2^n2)^-p]^(1/(2 sigma p)) */
+    double sigma[4], p[4], g[4][2], n[4][2];
+    /* environment sums (Eq. 2): zeta_l = sum_k fc(r_ik) ang_l(cos) e^{alpha_l (r_ij - r_ik)},
+     * ang_l(c) = gamma_l [1 + c_l^2/d_l^2 - c_l^2/(d_l^2 + (h_l - c)^2)] */
+    double gamma[8][2], c[8][2], d[8][2], h[8][2], alpha[8][2];
+    /* per type: self energy E0 + chi q + J q^2, charge shielding gamma_c, mass (u) */
+    double E0[2], chi[2], J[2], gamma_c[2], mass[2];
+    /* charge kernel k_e T(r/r_coul) / (r^3 + (gamma_ci gamma_cj)^(-3/2))^(1/3) */
+    double r_coul, k_e;
+} ctbop_params;
+
+typedef struct ctbop_options {
+    int32_t precision;    /* CTBOP_PREC_FP64 or CTBOP_PREC_MIXED */
+    int32_t cg_max_iter;  /* charge-solve iteration cap (default 200) */
+    double  cg_tol;       /* stop when the rms over a replica's atoms of H q + chi - mu is below
+                           cg_tol (eV/e); 0 = policy default (FP64 1e-10, MIXED 1e-6) */
+    double  skin;         /* neighbour-list skin (A, default 0.3) */
+    int32_t cap_cov;      /* covalent entries per atom; 0 = sized from the first configuration */
+    int32_t cap_all;      /* all entries (charge cutoff) per atom; 0 = sized automatically */
+    int32_t device;       /* CUDA device ordinal */
+    int32_t reserved;
+} ctbop_options;
+
+typedef struct ctbop_stats {
+    int64_t steps;            /* MD steps taken */
+    int64_t rebuilds;         /* neighbour-list rebuilds */
+    int32_t cg_iters_last;    /* CG iterations of the last charge solve */
+    int32_t max_cov;          /* largest covalent entry count at the last rebuild */
+    int64_t cg_iters_total;   /* summed over all solves */
+    int64_t solves;           /* number of charge solves */
+    double  cg_residual_last; /* rms of H q + chi - mu after the last solve, replica 0 (eV/e) */
+    int32_t max_all;          /* largest total entry count at the last rebuild */
+    uint32_t error_bits;      /* device-side error bits seen (see ctbop_last_error) */
+    double  mean_cov;         /* mean covalent entries (incl. skin) at the last rebuild */
+    double  mean_all;         /* mean total entries at the last rebuild */
+} ctbop_stats;
+
+typedef struct ctbop_system ctbop_system;
+
+/* Fill *o with defaults (MIXED precision, skin 0.3 A, 200 iterations). */
+int ctbop_default_options(ctbop_options* o);
+
+/* Create a system on o->device. p and o are copied. *out receives the handle.
+ * Fails with INVALID_ARG on null pointers, non-positive masses or cutoffs,
+ * R >= S, or a charge cutoff below the largest covalent cutoff. */
+int ctbop_create(const ctbop_params* p, const ctbop_options* o, ctbop_system** out);
+
+/* Free the system and all of its device memory. Null is accepted. */
+int ctbop_destroy(ctbop_system* s);
+
+/* Message for the last error on s (empty string if none; never null). */
+const char* ctbop_last_error(const ctbop_system* s);
+
+/* Order all later work on `cuda_stream` (a cudaStream_t; null = legacy stream). */
+int ctbop_set_stream(ctbop_system* s, void* cuda_stream);
+
+/* Replica layout: n_replicas >= 1, atom_offsets host int64[n_replicas+1],
+ * atom_offsets[0] = 0, non-decreasing; N = atom_offsets[n_replicas].
+ * Resets all per-atom state. */
+int ctbop_set_layout(ctbop_system* s, int32_t n_replicas, const int64_t* atom_offsets);
+
+/* Boxes: h host double[R*9], row-major 3x3 cell matrix per replica whose
+ * rows are the cell vectors; only orthorhombic (diagonal) cells are accepted.
+ * pbc host uint8[R*3], 1 = periodic axis. Along open axes the diagonal entry
+ * is the extent used for binning; atoms outside [0, L) are still handled. */
+int ctbop_set_box(ctbop_system* s, const double* h, const uint8_t* pbc);
+
+/* Per-atom inputs, N entries (x and v: N*3, row-major). types: 0 or 1. */
+int ctbop_set_types(ctbop_system* s, const int32_t* types, int mem);
+int ctbop_set_positions(ctbop_system* s, const double* x, int mem);
+int ctbop_set_velocities(ctbop_system* s, const double* v, int mem);
+/* Charges: warm start for the solve, or the fixed charges for CTBOP_FIXED_CHARGES. */
+int ctbop_set_charges(ctbop_system* s, const double* q, int mem);
+/* frozen: uint8[N], 1 = atom never moves (its force is still computed). */
+int ctbop_set_frozen(ctbop_system* s, const uint8_t* frozen, int mem);
+/* Total charge per replica, host double[R] (default 0: neutral). */
+int ctbop_set_total_charge(ctbop_system* s, const double* Q);
+
+/* One evaluation: neighbour lists (rebuilt when needed), bond orders,
+ * charges (unless CTBOP_FIXED_CHARGES), energy, forces, virial, per-atom
+ * energies. Stream-ordered; returns before the GPU finishes. Errors found on
+ * the device are reported by the next synchronising call. */
+int ctbop_compute(ctbop_system* s, uint32_t flags);
+
+/* n_steps velocity-Verlet steps of dt_fs each, charges re-minimised every
+ * step. Runs as a CUDA graph replay per step; synchronises at the end to
+ * check device status (neighbour overflow is repaired by growing the lists
+ * and redoing the affected steps). */
+int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs);
+
+/* Copy a result out (see CTBOP_GET_*). mem = CTBOP_HOST synchronises. */
+int ctbop_get(ctbop_system* s, int what, void* dst, int mem);
+
+/* Synchronise and report counters and device error bits. */
+int ctbop_status(ctbop_system* s, ctbop_stats* st);
+
+/* Phases of one step, for ctbop_profile_steps. */
+#define CTBOP_NPHASE 10
+/* 0 kick + drift, 1 neighbour lists (flag-guarded, no-op without a rebuild),
+ * 2 bond orders (Eq. 2, 7), 3 charge-system assembly, 4 CG start, 5 CG matrix
+ * pass, 6 CG update, 7 charges from the CG solution, 8 covalent force slots,
+ * 9 charge forces + slot gather + half kick. */
+
+/* Run n_steps velocity-Verlet steps (same arithmetic as ctbop_step) with
+ * every kernel launched directly and bracketed by CUDA events on the
+ * system's stream, synchronising after each phase. Adds the GPU time of each
+ * phase (ms) to ms_out[CTBOP_NPHASE] and the number of kernel launches to
+ * launches_out[CTBOP_NPHASE] (host arrays, caller-owned, not cleared).
+ * Slower than ctbop_step: for per-kernel timing only. */
+int ctbop_profile_steps(ctbop_system* s, int64_t n_steps, double dt_fs, double* ms_out, int64_t* launches_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTBOP_H */

@@ -1,0 +1,938 @@
+// api.cu — the C ABI of libctbop (include/ctbop.h): system state, device
+// memory, parameter packing, the evaluation sequence, CUDA-graph capture
+// (the charge CG loop is a conditional WHILE node) and MD stepping.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctbop.h"
+#include "kernels.h"
+
+using namespace ct;
+
+namespace {
+
+const double kAcc = 9.648533212e-3;   // 1 eV/(A u) in A/fs^2
+
+struct DevBuf {
+  std::vector<void*> ptrs;
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+}  // namespace
+
+struct ctbop_system {
+  ctbop_params p;
+  ctbop_options o;
+  cudaStream_t stream = nullptr;       // stream all work is ordered on
+  cudaStream_t own_stream = nullptr;   // used when the caller gives none
+  cudaStream_t body_stream = nullptr;
+  std::string err;
+  DevState S;
+  PotParams<float> Pf;
+  PotParams<double> Pd;
+  TypeParams T;
+  bool mixed = true;
+  double rlist = 0.0;
+  // host-side layout
+  int R = 0;
+  std::vector<int64_t> off;
+  std::vector<double> box;      // R*3
+  std::vector<uint8_t> pbc;     // R*3
+  std::vector<double> Q;        // R
+  bool have_layout = false, have_box = false, have_types = false, have_pos = false;
+  bool have_forces = false, need_rebuild = true, reps_dirty = true, caps_known = false;
+  // allocations
+  DevBuf atom_buf, list_buf, cell_buf, rep_buf;
+  int alloc_N = -1, alloc_R = -1, alloc_cells = -1, alloc_cov = -1, alloc_all = -1;
+  // graphs
+  cudaGraphExec_t g_eval = nullptr, g_step = nullptr;
+  double g_step_dt = -1.0;
+  bool use_graph = true;
+  // pinned host scratch
+  int* h_int = nullptr;
+  // counters
+  int64_t steps = 0, solves = 0;
+};
+
+static int fail(ctbop_system* s, int code, const std::string& msg) {
+  if (s) s->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(s, e_ == cudaErrorMemoryAllocation ? CTBOP_ERR_OOM : CTBOP_ERR_CUDA,    \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+template <class T>
+static cudaError_t dalloc(DevBuf& b, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  b.ptrs.push_back(q);
+  *p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------- parameters
+template <class Rr>
+static void pack_params(const ctbop_params& p, double skin, PotParams<Rr>& P) {
+  for (int k = 0; k < 4; ++k) {
+    P.A[k] = (Rr)p.A[k];
+    P.B[k] = (Rr)p.B[k];
+    P.lam1[k] = (Rr)p.lambda1[k];
+    P.lam2[k] = (Rr)p.lambda2[k];
+    P.Rin[k] = (Rr)p.R[k];
+    P.Sout[k] = (Rr)p.S[k];
+    P.kappa[k] = (Rr)p.kappa[k];
+    P.pi_SR[k] = (Rr)(M_PI / (p.S[k] - p.R[k]));
+    P.rcov_list2[k] = (Rr)((p.S[k] + skin) * (p.S[k] + skin));
+    double sg = p.sigma[k], pp = p.p[k];
+    P.sigma[k] = (Rr)sg;
+    P.p[k] = (Rr)pp;
+    P.g1[k] = (Rr)p.g[k][0];
+    P.g2[k] = (Rr)p.g[k][1];
+    P.n1[k] = (Rr)p.n[k][0];
+    P.n2[k] = (Rr)p.n[k][1];
+    // G normalises b to 1 at zeta = 0 (Sec. 2, after Eq. 5 and Eq. 7)
+    P.G[k] = (Rr)std::pow(std::pow(p.g[k][0], -pp) + std::pow(p.g[k][1], -pp), -1.0 / (2.0 * sg * pp));
+    P.inv2s[k] = (Rr)(1.0 / (2.0 * sg));
+    P.inv2sp[k] = (Rr)(1.0 / (2.0 * sg * pp));
+    int a = k / 2, b = k % 2;
+    P.gshield3[k] = (Rr)std::pow(p.gamma_c[a] * p.gamma_c[b], -1.5);
+  }
+  for (int t = 0; t < 8; ++t)
+    for (int l = 0; l < 2; ++l) {
+      P.gam[t][l] = (Rr)p.gamma[t][l];
+      P.c2[t][l] = (Rr)(p.c[t][l] * p.c[t][l]);
+      P.d2[t][l] = (Rr)(p.d[t][l] * p.d[t][l]);
+      P.h[t][l] = (Rr)p.h[t][l];
+      P.alpha[t][l] = (Rr)p.alpha[t][l];
+      P.c2d2[t][l] = (Rr)(p.c[t][l] * p.c[t][l] / (p.d[t][l] * p.d[t][l]));
+    }
+  P.rcoul = (Rr)p.r_coul;
+  P.inv_rcoul = (Rr)(1.0 / p.r_coul);
+  P.ke = (Rr)p.k_e;
+  P.rall_list2 = (Rr)((p.r_coul + skin) * (p.r_coul + skin));
+}
+
+static bool params_valid(const ctbop_params* p, std::string& why) {
+  for (int k = 0; k < 4; ++k) {
+    if (!(p->R[k] > 0 && p->S[k] > p->R[k])) { why = "need 0 < R < S for every pair"; return false; }
+    if (!(p->sigma[k] > 0 && p->p[k] > 0 && p->g[k][0] > 0 && p->g[k][1] > 0 && p->n[k][0] > 0 && p->n[k][1] > 0)) {
+      why = "sigma, p, g_l, n_l must be positive (Sec. 2)";
+      return false;
+    }
+  }
+  int a = 0;
+  for (int t = 0; t < 2; ++t) {
+    if (!(p->mass[t] > 0)) { why = "masses must be positive"; return false; }
+    if (!(p->gamma_c[t] > 0)) { why = "charge shielding gamma_c must be positive"; return false; }
+    if (!(p->J[t] > 0)) { why = "J must be positive"; return false; }
+    ++a;
+  }
+  double smax = 0;
+  for (int k = 0; k < 4; ++k) smax = std::max(smax, p->S[k]);
+  if (!(p->r_coul >= smax)) { why = "charge cutoff must be at least the largest covalent cutoff"; return false; }
+  return true;
+}
+
+// ------------------------------------------------------------- helpers
+static void destroy_graphs(ctbop_system* s) {
+  if (s->g_eval) cudaGraphExecDestroy(s->g_eval);
+  if (s->g_step) cudaGraphExecDestroy(s->g_step);
+  s->g_eval = s->g_step = nullptr;
+  s->g_step_dt = -1.0;
+}
+
+static int setup_reps(ctbop_system* s) {
+  std::vector<RepInfo> info(s->R);
+  int cells = 0;
+  for (int r = 0; r < s->R; ++r) {
+    RepInfo& ri = info[r];
+    memset(&ri, 0, sizeof(ri));
+    for (int d = 0; d < 3; ++d) {
+      double L = s->box[3 * r + d];
+      ri.L[d] = L;
+      ri.pbc[d] = s->pbc[3 * r + d] ? 1 : 0;
+      int n = (int)std::floor(L / (0.5 * s->rlist));
+      if (n < 1) n = 1;
+      if (n > 4096) n = 4096;
+      ri.n[d] = n;
+      ri.hc[d] = L / n;
+      ri.hcf[d] = (float)ri.hc[d];
+      int m = (int)std::ceil(s->rlist / ri.hc[d] - 1e-12);
+      if (m < 1) m = 1;
+      if (!ri.pbc[d] && m > n - 1) m = std::max(1, n - 1);
+      if (m > 8) return fail(s, CTBOP_ERR_INVALID_ARG, "box edge too small for the cutoff (more than 8 cells of stencil)");
+      ri.m[d] = m;
+    }
+    long long nc = (long long)ri.n[0] * ri.n[1] * ri.n[2];
+    if (cells + nc > 4 * 1024 * 1024) return fail(s, CTBOP_ERR_INVALID_ARG, "too many cells (more than 4M)");
+    ri.cell_off = cells;
+    cells += (int)nc;
+    ri.atom_off = (int)s->off[r];
+    ri.natoms = (int)(s->off[r + 1] - s->off[r]);
+  }
+  if (s->alloc_cells < cells) {
+    s->cell_buf.release();
+    DevState& S = s->S;
+    CK(dalloc(s->cell_buf, &S.cell_count, cells));
+    CK(dalloc(s->cell_buf, &S.cell_fill, cells));
+    CK(dalloc(s->cell_buf, &S.cell_start, cells));
+    s->alloc_cells = cells;
+    destroy_graphs(s);
+  }
+  s->S.ncells = cells;
+  CK(cudaMemcpy(s->S.reps, info.data(), sizeof(RepInfo) * s->R, cudaMemcpyHostToDevice));
+  // per-replica CG constants
+  std::vector<double> cg((size_t)s->R * CG_STRIDE, 0.0);
+  for (int r = 0; r < s->R; ++r) {
+    cg[(size_t)r * CG_STRIDE + CG_Q] = s->Q[r];
+    cg[(size_t)r * CG_STRIDE + CG_NAT] = (double)(s->off[r + 1] - s->off[r]);
+  }
+  CK(cudaMemcpy(s->S.cg, cg.data(), sizeof(double) * cg.size(), cudaMemcpyHostToDevice));
+  s->reps_dirty = false;
+  return CTBOP_OK;
+}
+
+static int alloc_atoms(ctbop_system* s) {
+  DevState& S = s->S;
+  int N = (int)s->off[s->R];
+  if (s->alloc_N == N && s->alloc_R == s->R) return CTBOP_OK;
+  destroy_graphs(s);
+  s->atom_buf.release();
+  s->rep_buf.release();
+  s->list_buf.release();
+  s->alloc_cov = s->alloc_all = -1;
+  S.N = N;
+  S.R = s->R;
+  size_t rs = s->mixed ? 4 : 8;
+  CK(dalloc(s->atom_buf, &S.x, 3 * (size_t)N));
+  CK(dalloc(s->atom_buf, &S.v, 3 * (size_t)N));
+  CK(dalloc(s->atom_buf, &S.F, 3 * (size_t)N));
+  CK(dalloc(s->atom_buf, &S.xref, 3 * (size_t)N));
+  CK(dalloc(s->atom_buf, &S.q, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.e_atom, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.type, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.rep, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.frozen, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.cell4, (size_t)N));
+  unsigned char* u = nullptr;
+  CK(dalloc(s->atom_buf, &u, (size_t)N * 4 * rs));
+  S.u = u;
+  CK(dalloc(s->atom_buf, &S.cell_atoms, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.Dg, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.dinv, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.cx, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.cr, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.cp, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.cs, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.cz, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.cw, (size_t)N));
+  unsigned char* zr = nullptr;
+  CK(dalloc(s->atom_buf, &zr, (size_t)N * 2 * rs));
+  S.czr = zr;
+  CK(dalloc(s->atom_buf, &S.ncov, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.nall, (size_t)N));
+  CK(cudaMemset(S.v, 0, sizeof(double) * 3 * (size_t)N));
+  CK(cudaMemset(S.F, 0, sizeof(double) * 3 * (size_t)N));
+  CK(cudaMemset(S.q, 0, sizeof(double) * (size_t)N));
+  CK(cudaMemset(S.frozen, 0, (size_t)N));
+  CK(cudaMemset(S.cx, 0, sizeof(double2) * (size_t)N));
+  CK(cudaMemset(S.cp, 0, sizeof(double2) * (size_t)N));
+  CK(cudaMemset(S.cs, 0, sizeof(double2) * (size_t)N));
+  // replica ids
+  std::vector<int> rep(N);
+  for (int r = 0; r < s->R; ++r)
+    for (int64_t i = s->off[r]; i < s->off[r + 1]; ++i) rep[i] = r;
+  CK(cudaMemcpy(S.rep, rep.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
+  // per-replica and control
+  CK(dalloc(s->rep_buf, &S.reps, (size_t)s->R));
+  CK(dalloc(s->rep_buf, &S.rep_acc, (size_t)s->R * RA_STRIDE));
+  CK(dalloc(s->rep_buf, &S.cg, (size_t)s->R * CG_STRIDE));
+  CK(dalloc(s->rep_buf, &S.cg_conv, (size_t)s->R));
+  CK(dalloc(s->rep_buf, &S.cg_iters, (size_t)s->R));
+  CK(dalloc(s->rep_buf, &S.scan_tmp, 1040));
+  CK(dalloc(s->rep_buf, &S.flag_rebuild, 1));
+  CK(dalloc(s->rep_buf, &S.rebuild_count, 1));
+  CK(dalloc(s->rep_buf, &S.maxcnt, 2));
+  CK(dalloc(s->rep_buf, &S.err, 1));
+  CK(dalloc(s->rep_buf, &S.cg_it, 1));
+  CK(dalloc(s->rep_buf, &S.cg_blocks, 2));
+  CK(dalloc(s->rep_buf, &S.cg_active, 1));
+  CK(dalloc(s->rep_buf, &S.cg_total, 1));
+  CK(cudaMemset(S.rep_acc, 0, sizeof(double) * s->R * RA_STRIDE));
+  CK(cudaMemset(S.rebuild_count, 0, sizeof(long long)));
+  CK(cudaMemset(S.err, 0, sizeof(unsigned)));
+  CK(cudaMemset(S.cg_total, 0, sizeof(long long)));
+  CK(cudaMemset(S.cg_blocks, 0, 2 * sizeof(int)));
+  CK(cudaMemset(S.maxcnt, 0, 2 * sizeof(int)));
+  CK(cudaMemset(S.cg_it, 0, sizeof(int)));
+  s->alloc_N = N;
+  s->alloc_R = s->R;
+  s->reps_dirty = true;
+  s->caps_known = false;
+  s->have_forces = false;
+  return CTBOP_OK;
+}
+
+static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
+  DevState& S = s->S;
+  if (s->alloc_cov == cap_cov && s->alloc_all == cap_all) return CTBOP_OK;
+  destroy_graphs(s);
+  s->list_buf.release();
+  int N = S.N;
+  size_t rs = s->mixed ? 4 : 8;
+  S.cap_cov = cap_cov;
+  S.cap_all = cap_all;
+  CK(dalloc(s->list_buf, &S.nbr, (size_t)N * cap_all));
+  CK(dalloc(s->list_buf, &S.code, (size_t)N * cap_all));
+  CK(dalloc(s->list_buf, &S.rev, (size_t)N * cap_cov));
+  unsigned char *bo = nullptr, *gs = nullptr, *M = nullptr;
+  CK(dalloc(s->list_buf, &bo, (size_t)N * cap_cov * 4 * rs));
+  CK(dalloc(s->list_buf, &gs, (size_t)N * cap_cov * 4 * rs));
+  CK(dalloc(s->list_buf, &M, (size_t)N * cap_all * rs));
+  S.bo = bo;
+  S.gslot = gs;
+  S.M = M;
+  if (cap_cov > 512) return fail(s, CTBOP_ERR_NEIGH_OVERFLOW, "covalent entries per atom beyond 512");
+  CK(s->mixed ? setup_pot<float>(cap_cov) : setup_pot<double>(cap_cov));
+  s->alloc_cov = cap_cov;
+  s->alloc_all = cap_all;
+  return CTBOP_OK;
+}
+
+// ------------------------------------------------------------- evaluation
+static double cg_tol(const ctbop_system* s) {
+  if (s->o.cg_tol > 0) return s->o.cg_tol;
+  return s->mixed ? 1e-6 : 1e-10;
+}
+
+template <class Rr>
+static void enqueue_front(ctbop_system* s, const PotParams<Rr>& P, cudaStream_t st, bool md, double dt) {
+  DevState& S = s->S;
+  if (md) launch_kick_drift<Rr>(S, s->T, dt, 0.25 * s->o.skin * s->o.skin, st);
+  launch_zero_acc(S, st);
+  launch_rebuild<Rr>(S, P, st);
+}
+
+template <class Rr>
+static void enqueue_middle(ctbop_system* s, const PotParams<Rr>& P, cudaStream_t st) {
+  DevState& S = s->S;
+  launch_bond<Rr>(S, P, st);
+  launch_assemble<Rr>(S, P, s->T, st);
+  launch_cg_begin<Rr>(S, s->T, st, cg_tol(s));
+}
+
+template <class Rr>
+static void enqueue_back(ctbop_system* s, const PotParams<Rr>& P, cudaStream_t st, bool md, double dt,
+                         bool solve) {
+  DevState& S = s->S;
+  if (solve) launch_cg_end<Rr>(S, st);
+  launch_forces<Rr>(S, P, s->T, md ? 1 : 0, 0.5 * dt, st);
+}
+
+template <class Rr>
+static int capture_graph(ctbop_system* s, const PotParams<Rr>& P, bool md, double dt, cudaGraphExec_t* out) {
+  cudaStream_t cs = s->stream;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  enqueue_front<Rr>(s, P, cs, md, dt);
+  enqueue_middle<Rr>(s, P, cs);
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cg_graph;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg_graph, &deps, nullptr, &ndeps);
+  cudaGraphConditionalHandle handle;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, cg_graph, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, cg_graph, deps, nullptr, ndeps, &cp);
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(s->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      SolveCfg cfg{cg_tol(s), s->o.cg_max_iter, 1, handle};
+      launch_cg_iter<Rr>(s->S, cfg, s->body_stream);
+      e = cudaStreamEndCapture(s->body_stream, &body);
+    }
+  }
+  enqueue_back<Rr>(s, P, cs, md, dt, true);
+  cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(s, CTBOP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  if (e2 != cudaSuccess) return fail(s, CTBOP_ERR_CUDA, std::string("graph capture end: ") + cudaGetErrorString(e2));
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(s, CTBOP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return CTBOP_OK;
+}
+
+// Host-driven variant of the same sequence (no graph): the CG loop polls the
+// device's active flag every few iterations.
+template <class Rr>
+static int run_direct(ctbop_system* s, const PotParams<Rr>& P, bool md, double dt, bool solve) {
+  cudaStream_t st = s->stream;
+  enqueue_front<Rr>(s, P, st, md, dt);
+  if (solve) {
+    enqueue_middle<Rr>(s, P, st);
+    SolveCfg cfg{cg_tol(s), s->o.cg_max_iter, 0, 0};
+    for (int it = 0; it < s->o.cg_max_iter + 4; it += 4) {
+      for (int k = 0; k < 4; ++k) launch_cg_iter<Rr>(s->S, cfg, st);
+      CK(cudaMemcpyAsync(s->h_int, s->S.cg_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (*s->h_int == 0) break;
+    }
+  } else {
+    launch_bond<Rr>(s->S, P, st);
+  }
+  enqueue_back<Rr>(s, P, st, md, dt, solve);
+  CK(cudaGetLastError());
+  return CTBOP_OK;
+}
+
+static int read_err(ctbop_system* s, unsigned& bits) {
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemcpy(&bits, s->S.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  return CTBOP_OK;
+}
+
+// Build the lists for the current positions. The first build of a layout
+// measures the entry counts and sizes the lists from them; an overflow grows
+// them and builds again.
+static int ensure_lists(ctbop_system* s) {
+  DevState& S = s->S;
+  int one = 1;
+  if (!s->caps_known) {
+    int cc = s->o.cap_cov > 0 ? s->o.cap_cov : 32;
+    int ca = s->o.cap_all > 0 ? s->o.cap_all : 64;
+    int rc = alloc_lists(s, cc, std::max(ca, cc));
+    if (rc) return rc;
+  }
+  for (int attempt = 0;; ++attempt) {
+    if (attempt > 4) return fail(s, CTBOP_ERR_NEIGH_OVERFLOW, "could not size the neighbour lists");
+    CK(cudaMemcpyAsync(S.flag_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemsetAsync(S.err, 0, sizeof(unsigned), s->stream));
+    if (s->mixed) launch_rebuild<float>(S, s->Pf, s->stream);
+    else launch_rebuild<double>(S, s->Pd, s->stream);
+    CK(cudaGetLastError());
+    unsigned bits = 0;
+    int rc = read_err(s, bits);
+    if (rc) return rc;
+    int mc[2];
+    CK(cudaMemcpy(mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost));
+    if (bits & CT_ERR_NONFINITE) return fail(s, CTBOP_ERR_NONFINITE, "non-finite position");
+    bool over = (bits & (CT_ERR_NBR_OVERFLOW | CT_ERR_COV_OVERFLOW)) != 0;
+    if (!over && (bits & CT_ERR_REV_MISSING)) return fail(s, CTBOP_ERR_CUDA, "internal: asymmetric covalent list");
+    if (!over && s->caps_known) break;
+    // size from the measured maxima with headroom for motion
+    int cc = std::max(mc[0] + mc[0] / 4 + 4, 8);
+    int ca = std::max(mc[1] + mc[1] / 8 + 16, cc);
+    cc = (cc + 3) & ~3;
+    ca = (ca + 7) & ~7;
+    if (s->o.cap_cov > 0) cc = std::max(cc, s->o.cap_cov);
+    if (s->o.cap_all > 0) ca = std::max(ca, s->o.cap_all);
+    if (over) {
+      cc = std::max(cc, S.cap_cov);
+      ca = std::max(ca, S.cap_all);
+    }
+    bool same = (cc == S.cap_cov && ca == S.cap_all);
+    s->caps_known = true;
+    if (same && !over) break;
+    rc = alloc_lists(s, cc, ca);   // fresh buffers: build again
+    if (rc) return rc;
+  }
+  s->need_rebuild = false;
+  CK(cudaMemsetAsync(S.err, 0, sizeof(unsigned), s->stream));
+  return CTBOP_OK;
+}
+
+static int prepare(ctbop_system* s) {
+  if (!s->have_layout || !s->have_box || !s->have_types || !s->have_pos)
+    return fail(s, CTBOP_ERR_STATE, "layout, box, types and positions must be set first");
+  int rc = alloc_atoms(s);
+  if (rc) return rc;
+  if (s->reps_dirty) {
+    rc = setup_reps(s);
+    if (rc) return rc;
+  }
+  if (s->need_rebuild || !s->caps_known) {
+    rc = ensure_lists(s);
+    if (rc) return rc;
+  }
+  return CTBOP_OK;
+}
+
+template <class Rr>
+static int eval_t(ctbop_system* s, const PotParams<Rr>& P, uint32_t flags) {
+  bool solve = !(flags & CTBOP_FIXED_CHARGES);
+  if (s->use_graph && solve) {
+    if (!s->g_eval) {
+      int rc = capture_graph<Rr>(s, P, false, 0.0, &s->g_eval);
+      if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(s->g_eval, s->stream));
+  } else {
+    int rc = run_direct<Rr>(s, P, false, 0.0, solve);
+    if (rc) return rc;
+  }
+  if (solve) s->solves++;
+  s->have_forces = true;
+  return CTBOP_OK;
+}
+
+template <class Rr>
+static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double dt, double* ms, int64_t* cnt) {
+  cudaStream_t st = s->stream;
+  DevState& S = s->S;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto timed = [&](int ph, int launches, auto&& fn) -> int {
+    CK(cudaEventRecord(e0, st));
+    fn();
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    ms[ph] += t;
+    cnt[ph] += launches;
+    return CTBOP_OK;
+  };
+  int rc = CTBOP_OK;
+  SolveCfg cfg{cg_tol(s), s->o.cg_max_iter, 0, 0};
+  for (int64_t k = 0; k < n && !rc; ++k) {
+    CK(cudaMemsetAsync(S.err, 0, sizeof(unsigned), st));
+    rc = timed(0, 1, [&] { launch_kick_drift<Rr>(S, s->T, dt, 0.25 * s->o.skin * s->o.skin, st); });
+    if (!rc) rc = timed(1, 11, [&] { launch_zero_acc(S, st); launch_rebuild<Rr>(S, P, st); });
+    if (!rc) rc = timed(2, 1, [&] { launch_bond<Rr>(S, P, st); });
+    if (!rc) rc = timed(3, 1, [&] { launch_assemble<Rr>(S, P, s->T, st); });
+    if (!rc) rc = timed(4, 2, [&] { launch_cg_begin<Rr>(S, s->T, st, cg_tol(s)); });
+    for (int it = 0; it < s->o.cg_max_iter && !rc; ++it) {
+      CK(cudaMemcpyAsync(s->h_int, S.cg_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (*s->h_int == 0) break;
+      rc = timed(5, 1, [&] { launch_cg_mv<Rr>(S, st); });
+      if (!rc) rc = timed(6, 1, [&] { launch_cg_up<Rr>(S, cfg, st); });
+    }
+    if (!rc) rc = timed(7, 1, [&] { launch_cg_end<Rr>(S, st); });
+    if (!rc) rc = timed(8, 1, [&] { launch_cov_force<Rr>(S, P, s->T, st); });
+    if (!rc) rc = timed(9, 1, [&] { launch_coul_gather<Rr>(S, P, s->T, 1, 0.5 * dt, st); });
+    if (!rc) {
+      unsigned bits = 0;
+      rc = read_err(s, bits);
+      if (!rc && (bits & (CT_ERR_NBR_OVERFLOW | CT_ERR_COV_OVERFLOW)))
+        rc = fail(s, CTBOP_ERR_NEIGH_OVERFLOW, "neighbour lists overflowed during profiling; run ctbop_step first");
+      if (!rc && (bits & CT_ERR_NONFINITE)) rc = fail(s, CTBOP_ERR_NONFINITE, "non-finite energy, force or position");
+    }
+    s->steps++;
+    s->solves++;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+// ------------------------------------------------------------- C ABI
+extern "C" {
+
+int ctbop_default_options(ctbop_options* o) {
+  if (!o) return CTBOP_ERR_INVALID_ARG;
+  memset(o, 0, sizeof(*o));
+  o->precision = CTBOP_PREC_MIXED;
+  o->cg_max_iter = 200;
+  o->cg_tol = 0.0;
+  o->skin = 0.3;
+  o->device = 0;
+  return CTBOP_OK;
+}
+
+int ctbop_create(const ctbop_params* p, const ctbop_options* o, ctbop_system** out) {
+  if (!p || !o || !out) return CTBOP_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::string why;
+  if (!params_valid(p, why)) return CTBOP_ERR_INVALID_ARG;
+  if (o->precision != CTBOP_PREC_FP64 && o->precision != CTBOP_PREC_MIXED) return CTBOP_ERR_INVALID_ARG;
+  if (!(o->skin >= 0) || o->cg_max_iter < 1) return CTBOP_ERR_INVALID_ARG;
+  if (cudaSetDevice(o->device) != cudaSuccess) return CTBOP_ERR_CUDA;
+  ctbop_system* s = new ctbop_system();
+  s->p = *p;
+  s->o = *o;
+  s->mixed = o->precision == CTBOP_PREC_MIXED;
+  pack_params<float>(*p, o->skin, s->Pf);
+  pack_params<double>(*p, o->skin, s->Pd);
+  for (int t = 0; t < 2; ++t) {
+    s->T.E0[t] = p->E0[t];
+    s->T.chi[t] = p->chi[t];
+    s->T.J[t] = p->J[t];
+    s->T.mass[t] = p->mass[t] / kAcc;          // KE = 1/2 m v^2 in eV with v in A/fs
+    s->T.inv_mass_acc[t] = kAcc / p->mass[t];
+  }
+  double smax = 0;
+  for (int k = 0; k < 4; ++k) smax = std::max(smax, p->S[k]);
+  s->rlist = std::max(p->r_coul, smax) + o->skin;
+  const char* ng = getenv("CTBOP_NO_GRAPH");
+  s->use_graph = !(ng && ng[0] == '1');
+  int dev = 0;
+  cudaDeviceProp prop;
+  cudaGetDevice(&dev);
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) s->S.nsm = prop.multiProcessorCount;
+  if (cudaStreamCreate(&s->own_stream) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost(&s->h_int, 64) != cudaSuccess) {
+    delete s;
+    return CTBOP_ERR_CUDA;
+  }
+  s->stream = s->own_stream;
+  *out = s;
+  return CTBOP_OK;
+}
+
+int ctbop_destroy(ctbop_system* s) {
+  if (!s) return CTBOP_OK;
+  cudaSetDevice(s->o.device);
+  cudaStreamSynchronize(s->stream);
+  destroy_graphs(s);
+  s->atom_buf.release();
+  s->list_buf.release();
+  s->cell_buf.release();
+  s->rep_buf.release();
+  if (s->body_stream) cudaStreamDestroy(s->body_stream);
+  if (s->own_stream) cudaStreamDestroy(s->own_stream);
+  if (s->h_int) cudaFreeHost(s->h_int);
+  delete s;
+  return CTBOP_OK;
+}
+
+const char* ctbop_last_error(const ctbop_system* s) { return s ? s->err.c_str() : "null system"; }
+
+int ctbop_set_stream(ctbop_system* s, void* stream) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  // a graph cannot be captured on the legacy default stream: null selects
+  // the library's own stream, which synchronises with the legacy stream
+  s->stream = stream ? (cudaStream_t)stream : s->own_stream;
+  return CTBOP_OK;
+}
+
+int ctbop_set_layout(ctbop_system* s, int32_t n_replicas, const int64_t* atom_offsets) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (n_replicas < 1 || !atom_offsets) return fail(s, CTBOP_ERR_INVALID_ARG, "need n_replicas >= 1 and offsets");
+  if (atom_offsets[0] != 0) return fail(s, CTBOP_ERR_INVALID_ARG, "atom_offsets[0] must be 0");
+  for (int r = 0; r < n_replicas; ++r)
+    if (atom_offsets[r + 1] < atom_offsets[r]) return fail(s, CTBOP_ERR_INVALID_ARG, "atom_offsets must not decrease");
+  if (atom_offsets[n_replicas] > (int64_t)INT32_MAX / 64) return fail(s, CTBOP_ERR_INVALID_ARG, "too many atoms");
+  cudaSetDevice(s->o.device);
+  s->R = n_replicas;
+  s->off.assign(atom_offsets, atom_offsets + n_replicas + 1);
+  s->Q.assign(n_replicas, 0.0);
+  s->box.assign(3 * n_replicas, 0.0);
+  s->pbc.assign(3 * n_replicas, 0);
+  s->have_layout = true;
+  s->have_box = s->have_types = s->have_pos = false;
+  s->need_rebuild = true;
+  s->reps_dirty = true;
+  s->alloc_N = -1;
+  return alloc_atoms(s);
+}
+
+int ctbop_set_box(ctbop_system* s, const double* h, const uint8_t* pbc) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
+  if (!h || !pbc) return fail(s, CTBOP_ERR_INVALID_ARG, "null box or pbc");
+  for (int r = 0; r < s->R; ++r) {
+    const double* m = h + 9 * r;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        if (a != b && m[3 * a + b] != 0.0)
+          return fail(s, CTBOP_ERR_INVALID_ARG, "only orthorhombic (diagonal) cells are supported");
+    for (int d = 0; d < 3; ++d) {
+      double L = m[4 * d];
+      if (!(L > 0) || !std::isfinite(L)) return fail(s, CTBOP_ERR_INVALID_ARG, "box edges must be positive");
+      s->box[3 * r + d] = L;
+      s->pbc[3 * r + d] = pbc[3 * r + d] ? 1 : 0;
+    }
+  }
+  destroy_graphs(s);
+  s->have_box = true;
+  s->reps_dirty = true;
+  s->need_rebuild = true;
+  return CTBOP_OK;
+}
+
+static int copy_in(ctbop_system* s, void* dst, const void* src, size_t bytes, int mem) {
+  if (!src && bytes) return fail(s, CTBOP_ERR_INVALID_ARG, "null input pointer");
+  if (mem != CTBOP_HOST && mem != CTBOP_DEVICE) return fail(s, CTBOP_ERR_INVALID_ARG, "mem must be CTBOP_HOST or CTBOP_DEVICE");
+  cudaSetDevice(s->o.device);
+  if (mem == CTBOP_HOST) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  } else {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  return CTBOP_OK;
+}
+
+int ctbop_set_types(ctbop_system* s, const int32_t* types, int mem) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
+  size_t N = s->S.N;
+  if (mem == CTBOP_HOST && types)
+    for (size_t i = 0; i < N; ++i)
+      if (types[i] != 0 && types[i] != 1) return fail(s, CTBOP_ERR_INVALID_ARG, "types must be 0 (Si) or 1 (C)");
+  int rc = copy_in(s, s->S.type, types, sizeof(int) * N, mem);
+  if (rc) return rc;
+  s->have_types = true;
+  s->need_rebuild = true;
+  return CTBOP_OK;
+}
+
+int ctbop_set_positions(ctbop_system* s, const double* x, int mem) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
+  int rc = copy_in(s, s->S.x, x, sizeof(double) * 3 * s->S.N, mem);
+  if (rc) return rc;
+  s->have_pos = true;
+  s->need_rebuild = true;
+  s->have_forces = false;
+  return CTBOP_OK;
+}
+
+int ctbop_set_velocities(ctbop_system* s, const double* v, int mem) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
+  return copy_in(s, s->S.v, v, sizeof(double) * 3 * s->S.N, mem);
+}
+
+int ctbop_set_charges(ctbop_system* s, const double* q, int mem) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
+  return copy_in(s, s->S.q, q, sizeof(double) * s->S.N, mem);
+}
+
+int ctbop_set_frozen(ctbop_system* s, const uint8_t* frozen, int mem) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
+  return copy_in(s, s->S.frozen, frozen, s->S.N, mem);
+}
+
+int ctbop_set_total_charge(ctbop_system* s, const double* Q) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
+  if (!Q) return fail(s, CTBOP_ERR_INVALID_ARG, "null Q");
+  for (int r = 0; r < s->R; ++r) {
+    if (!std::isfinite(Q[r])) return fail(s, CTBOP_ERR_INVALID_ARG, "Q must be finite");
+    s->Q[r] = Q[r];
+  }
+  s->reps_dirty = true;
+  return CTBOP_OK;
+}
+
+int ctbop_compute(ctbop_system* s, uint32_t flags) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  cudaSetDevice(s->o.device);
+  int rc = prepare(s);
+  if (rc) return rc;
+  rc = s->mixed ? eval_t<float>(s, s->Pf, flags) : eval_t<double>(s, s->Pd, flags);
+  if (rc) return rc;
+  CK(cudaGetLastError());
+  return CTBOP_OK;
+}
+
+int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (n_steps < 0 || !(dt_fs > 0) || !std::isfinite(dt_fs)) return fail(s, CTBOP_ERR_INVALID_ARG, "need n_steps >= 0, dt > 0");
+  cudaSetDevice(s->o.device);
+  int rc = prepare(s);
+  if (rc) return rc;
+  if (!s->have_forces) {
+    rc = ctbop_compute(s, 0);
+    if (rc) return rc;
+  }
+  DevState& S = s->S;
+  const int64_t chunk = 100;
+  // snapshot buffers for redoing a chunk after a list overflow
+  double *sx = nullptr, *sv = nullptr, *sF = nullptr, *sq = nullptr;
+  double2* scx = nullptr;
+  size_t N = S.N;
+  CK(cudaMallocAsync(&sx, sizeof(double) * 3 * N + 8, s->stream));
+  CK(cudaMallocAsync(&sv, sizeof(double) * 3 * N + 8, s->stream));
+  CK(cudaMallocAsync(&sF, sizeof(double) * 3 * N + 8, s->stream));
+  CK(cudaMallocAsync(&sq, sizeof(double) * N + 8, s->stream));
+  CK(cudaMallocAsync(&scx, sizeof(double2) * N + 16, s->stream));
+  int result = CTBOP_OK;
+  int64_t done = 0;
+  int redo = 0;
+  while (done < n_steps) {
+    int64_t n = std::min(chunk, n_steps - done);
+    cudaMemcpyAsync(sx, S.x, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s->stream);
+    cudaMemcpyAsync(sv, S.v, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s->stream);
+    cudaMemcpyAsync(sF, S.F, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s->stream);
+    cudaMemcpyAsync(sq, S.q, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->stream);
+    cudaMemcpyAsync(scx, S.cx, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s->stream);
+    cudaMemsetAsync(S.err, 0, sizeof(unsigned), s->stream);
+    if (s->use_graph) {
+      if (!s->g_step || s->g_step_dt != dt_fs) {
+        if (s->g_step) cudaGraphExecDestroy(s->g_step);
+        s->g_step = nullptr;
+        result = s->mixed ? capture_graph<float>(s, s->Pf, true, dt_fs, &s->g_step)
+                          : capture_graph<double>(s, s->Pd, true, dt_fs, &s->g_step);
+        if (result) break;
+        s->g_step_dt = dt_fs;
+      }
+      for (int64_t k = 0; k < n; ++k) {
+        cudaError_t e = cudaGraphLaunch(s->g_step, s->stream);
+        if (e != cudaSuccess) { result = fail(s, CTBOP_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e)); break; }
+      }
+      if (result) break;
+    } else {
+      for (int64_t k = 0; k < n && !result; ++k)
+        result = s->mixed ? run_direct<float>(s, s->Pf, true, dt_fs, true)
+                          : run_direct<double>(s, s->Pd, true, dt_fs, true);
+      if (result) break;
+    }
+    unsigned bits = 0;
+    result = read_err(s, bits);
+    if (result) break;
+    if (bits & (CT_ERR_NBR_OVERFLOW | CT_ERR_COV_OVERFLOW)) {
+      if (++redo > 3) { result = fail(s, CTBOP_ERR_NEIGH_OVERFLOW, "neighbour lists kept overflowing"); break; }
+      // restore the chunk's starting state, grow the lists, redo the chunk
+      cudaMemcpyAsync(S.x, sx, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s->stream);
+      cudaMemcpyAsync(S.v, sv, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s->stream);
+      cudaMemcpyAsync(S.F, sF, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s->stream);
+      cudaMemcpyAsync(S.q, sq, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->stream);
+      cudaMemcpyAsync(S.cx, scx, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s->stream);
+      int mc[2];
+      cudaMemcpy(mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost);
+      int cc = std::max(S.cap_cov, mc[0] + mc[0] / 4 + 4);
+      int ca = std::max(S.cap_all, mc[1] + mc[1] / 8 + 16);
+      result = alloc_lists(s, (cc + 3) & ~3, (ca + 7) & ~7);
+      if (result) break;
+      s->need_rebuild = true;
+      result = ensure_lists(s);
+      if (result) break;
+      // recompute forces at the restored positions with the new lists
+      result = ctbop_compute(s, 0);
+      if (result) break;
+      continue;
+    }
+    if (bits & CT_ERR_NONFINITE) { result = fail(s, CTBOP_ERR_NONFINITE, "non-finite energy, force or position"); done += n; break; }
+    if (bits & CT_ERR_REV_MISSING) { result = fail(s, CTBOP_ERR_CUDA, "internal: asymmetric covalent list"); break; }
+    done += n;
+    s->steps += n;
+    s->solves += n;
+    if (bits & CT_ERR_CG_MAXITER) { result = fail(s, CTBOP_ERR_CG_NOT_CONVERGED, "charge CG reached max_iter"); break; }
+  }
+  cudaFreeAsync(sx, s->stream);
+  cudaFreeAsync(sv, s->stream);
+  cudaFreeAsync(sF, s->stream);
+  cudaFreeAsync(sq, s->stream);
+  cudaFreeAsync(scx, s->stream);
+  cudaStreamSynchronize(s->stream);
+  return result;
+}
+
+int ctbop_get(ctbop_system* s, int what, void* dst, int mem) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!dst) return fail(s, CTBOP_ERR_INVALID_ARG, "null destination");
+  if (mem != CTBOP_HOST && mem != CTBOP_DEVICE) return fail(s, CTBOP_ERR_INVALID_ARG, "mem must be CTBOP_HOST or CTBOP_DEVICE");
+  if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "nothing computed");
+  cudaSetDevice(s->o.device);
+  DevState& S = s->S;
+  cudaMemcpyKind kind = mem == CTBOP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  size_t N = S.N, R = s->R;
+  const void* src = nullptr;
+  size_t width = 0, pitch = 0, rows = 1;
+  switch (what) {
+    case CTBOP_GET_ENERGY: src = S.rep_acc + RA_E; width = 8; pitch = RA_STRIDE * 8; rows = R; break;
+    case CTBOP_GET_VIRIAL: src = S.rep_acc + RA_W; width = 72; pitch = RA_STRIDE * 8; rows = R; break;
+    case CTBOP_GET_KINETIC: src = S.rep_acc + RA_KE; width = 8; pitch = RA_STRIDE * 8; rows = R; break;
+    case CTBOP_GET_MU: src = S.cg + CG_MU; width = 8; pitch = CG_STRIDE * 8; rows = R; break;
+    case CTBOP_GET_FORCES: src = S.F; width = pitch = 24 * N; break;
+    case CTBOP_GET_POSITIONS: src = S.x; width = pitch = 24 * N; break;
+    case CTBOP_GET_VELOCITIES: src = S.v; width = pitch = 24 * N; break;
+    case CTBOP_GET_CHARGES: src = S.q; width = pitch = 8 * N; break;
+    case CTBOP_GET_E_ATOM: src = S.e_atom; width = pitch = 8 * N; break;
+    default: return fail(s, CTBOP_ERR_INVALID_ARG, "unknown selector");
+  }
+  if (width == 0) return CTBOP_OK;
+  CK(cudaMemcpy2DAsync(dst, width, src, pitch, width, rows, kind, s->stream));
+  if (mem == CTBOP_HOST) CK(cudaStreamSynchronize(s->stream));
+  return CTBOP_OK;
+}
+
+int ctbop_profile_steps(ctbop_system* s, int64_t n_steps, double dt_fs, double* ms_out, int64_t* launches_out) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!ms_out || !launches_out || n_steps < 0 || !(dt_fs > 0)) return fail(s, CTBOP_ERR_INVALID_ARG, "bad profile arguments");
+  cudaSetDevice(s->o.device);
+  int rc = prepare(s);
+  if (rc) return rc;
+  if (!s->have_forces) {
+    rc = ctbop_compute(s, 0);
+    if (rc) return rc;
+  }
+  return s->mixed ? profile_t<float>(s, s->Pf, n_steps, dt_fs, ms_out, launches_out)
+                  : profile_t<double>(s, s->Pd, n_steps, dt_fs, ms_out, launches_out);
+}
+
+int ctbop_status(ctbop_system* s, ctbop_stats* st) {
+  if (!s || !st) return CTBOP_ERR_INVALID_ARG;
+  cudaSetDevice(s->o.device);
+  memset(st, 0, sizeof(*st));
+  st->steps = s->steps;
+  st->solves = s->solves;
+  if (s->alloc_N < 0) return CTBOP_OK;
+  DevState& S = s->S;
+  CK(cudaStreamSynchronize(s->stream));
+  unsigned bits = 0;
+  long long rb = 0, tot = 0;
+  int it = 0, mc[2] = {0, 0};
+  CK(cudaMemcpy(&bits, S.err, sizeof(bits), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&rb, S.rebuild_count, sizeof(rb), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&tot, S.cg_total, sizeof(tot), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&it, S.cg_it, sizeof(it), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost));
+  double res = 0;
+  CK(cudaMemcpy(&res, S.cg + CG_RES, sizeof(double), cudaMemcpyDeviceToHost));
+  st->error_bits = bits;
+  st->rebuilds = rb;
+  st->cg_iters_total = tot;
+  st->cg_iters_last = it;
+  st->cg_residual_last = res;
+  st->max_cov = mc[0];
+  st->max_all = mc[1];
+  if (S.N > 0 && S.ncov) {
+    std::vector<int> a(S.N), b(S.N);
+    CK(cudaMemcpy(a.data(), S.ncov, sizeof(int) * S.N, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(b.data(), S.nall, sizeof(int) * S.N, cudaMemcpyDeviceToHost));
+    double sa = 0, sb = 0;
+    for (int i = 0; i < S.N; ++i) { sa += a[i]; sb += b[i]; }
+    st->mean_cov = sa / S.N;
+    st->mean_all = sb / S.N;
+  }
+  if (bits & CT_ERR_NONFINITE) return fail(s, CTBOP_ERR_NONFINITE, "non-finite energy, force or position");
+  if (bits & CT_ERR_CG_MAXITER) return fail(s, CTBOP_ERR_CG_NOT_CONVERGED, "charge CG reached max_iter");
+  return CTBOP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,374 @@
+// cg.cu — charge minimisation (Sec. 2: charges minimise E_tot at every
+// step, by conjugate gradients).
+//
+// E is quadratic in q, so the constrained minimum (sum_r q = Q_r per
+// replica) solves H q + chi = mu 1. Two Jacobi-preconditioned CG solves share
+// every pass over the matrix: H s = -chi and H t = 1, after which
+// q = s + mu t with mu = (Q - sum s) / sum t. Vectors are stored (s, t)
+// interleaved as double2. The iteration is the one-reduction (Chronopoulos-
+// Gear) form of PCG: per iteration one matrix pass that also forms the two
+// dot products (r.z, w.z), and one element-wise update that forms the sums
+// for the convergence test. Dot products, residual sums and the vectors are
+// FP64; the matrix entries and the gathered z_j are in the working precision.
+//
+// Convergence (per replica): rms over the replica's atoms of r_s + mu r_t
+// (= mu 1 - H q - chi, the stationarity residual) below tol. The last block
+// of each update launch decides, marks converged replicas, and ends the loop
+// through the CUDA-graph condition (or a device flag the host polls).
+#include "internal.cuh"
+#include "kernels.h"
+
+namespace ct {
+
+__device__ inline double ldcg(const double* p) { return __ldcg(p); }
+
+// Grid-wide "am I the last block" after this block's atomics.
+__device__ inline bool last_block(int* counter) {
+  __shared__ bool am_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    int t = atomicAdd(counter, 1);
+    am_last = (t == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+// Convergence test for every unconverged replica from the sums in upd.
+__device__ inline int check_replicas(int R, double* cg, int* conv, int* iters, const double* upd_base,
+                                     int upd_off, int it_done, double tol) {
+  int all = 1;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    if (conv[r]) continue;
+    double* c = cg + (size_t)r * CG_STRIDE;
+    const double* u5 = upd_base + (size_t)r * CG_STRIDE + upd_off;
+    double rss = ldcg(u5 + 0), rtt = ldcg(u5 + 1), rst = ldcg(u5 + 2), xs = ldcg(u5 + 3), xt = ldcg(u5 + 4);
+    double mu = (c[CG_Q] - xs) / xt;
+    double nat = c[CG_NAT];
+    double res2 = (rss + 2.0 * mu * rst + mu * mu * rtt) / (nat > 0 ? nat : 1.0);
+    double rms = sqrt(fmax(res2, 0.0));
+    c[CG_MU] = mu;
+    c[CG_RES] = rms;
+    if (rms <= tol || nat == 0) {
+      conv[r] = 1;
+      iters[r] = it_done;
+    } else {
+      all = 0;
+    }
+  }
+  return __syncthreads_and(all);
+}
+
+// --------------------------------------------------------------- prepare
+__global__ void k_cg_prep(int R, double* __restrict__ cg, int* __restrict__ conv, int* __restrict__ iters,
+                          int* __restrict__ it, int* __restrict__ blocks, int* __restrict__ active) {
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double* c = cg + (size_t)r * CG_STRIDE;
+    for (int k = 0; k < CG_MU; ++k) c[k] = 0.0;
+    conv[r] = 0;
+    iters[r] = 0;
+  }
+  if (threadIdx.x == 0) {
+    *it = 0;
+    blocks[0] = 0;
+    blocks[1] = 0;
+    *active = 1;
+  }
+}
+
+// r = b - H x0, z = D^-1 r, with b = (-chi, 1); sums for the initial test.
+template <class R>
+__global__ void k_cg_init(int N, int cap_all, int chunk, const int* __restrict__ nbr,
+                          const int* __restrict__ nall, const R* __restrict__ M, const double* __restrict__ Dg,
+                          const double* __restrict__ dinv, const int* __restrict__ type, const int* __restrict__ rep,
+                          TypeParams T, const double2* __restrict__ x, double2* __restrict__ r,
+                          double2* __restrict__ z, typename Vec2<R>::T* __restrict__ zr,
+                          double* __restrict__ cg, int Rn, int* __restrict__ conv, int* __restrict__ iters,
+                          int* __restrict__ blocks, int* __restrict__ active, double tol) {
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
+  RepAcc<5> acc;
+  acc.init();
+  for (int i = a0 + warp; i < a1; i += nw) {
+    int na = min(nall[i], cap_all);
+    R hs = R(0), ht = R(0);
+    for (int e = lane; e < na; e += 32) {
+      size_t idx = (size_t)i * cap_all + e;
+      double2 xj = x[nbr[idx]];
+      R m = M[idx];
+      hs += m * (R)xj.x;
+      ht += m * (R)xj.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      hs += __shfl_xor_sync(CT_FULL, hs, o);
+      ht += __shfl_xor_sync(CT_FULL, ht, o);
+    }
+    if (lane == 0) {
+      double2 xi = x[i];
+      double D = Dg[i];
+      double2 ri;
+      ri.x = -T.chi[type[i]] - (D * xi.x + (double)hs);
+      ri.y = 1.0 - (D * xi.y + (double)ht);
+      double di = dinv[i];
+      double2 zi;
+      zi.x = ri.x * di;
+      zi.y = ri.y * di;
+      r[i] = ri;
+      z[i] = zi;
+      typename Vec2<R>::T zz;
+      zz.x = (R)zi.x;
+      zz.y = (R)zi.y;
+      zr[i] = zz;
+      acc.to(rep[i], cg + CG_UPD + 2 * 5, CG_STRIDE);  // update buffer 2
+      acc.v[0] += ri.x * ri.x;
+      acc.v[1] += ri.y * ri.y;
+      acc.v[2] += ri.x * ri.y;
+      acc.v[3] += xi.x;
+      acc.v[4] += xi.y;
+    }
+  }
+  block_flush<5>(acc, cg + CG_UPD + 2 * 5, CG_STRIDE);
+  if (last_block(blocks)) {
+    int all = check_replicas(Rn, cg, conv, iters, cg, CG_UPD + 2 * 5, 0, tol);
+    if (threadIdx.x == 0) {
+      blocks[0] = 0;
+      if (all) *active = 0;
+    }
+  }
+}
+
+// w = H z and the dots (r.z, w.z) for both solves.
+template <class R>
+__global__ void k_cg_mv(int N, int cap_all, int chunk, const int* __restrict__ nbr, const int* __restrict__ nall,
+                        const R* __restrict__ M, const double* __restrict__ Dg, const int* __restrict__ rep,
+                        const int* __restrict__ conv, const int* __restrict__ itp,
+                        const typename Vec2<R>::T* __restrict__ zr, const double2* __restrict__ z,
+                        const double2* __restrict__ r, double2* __restrict__ w, double* __restrict__ cg,
+                        const int* __restrict__ active) {
+  if (*active == 0) return;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
+  int it = *itp;
+  int buf = CG_DOTS + (it & 1) * 4;
+  RepAcc<4> acc;
+  acc.init();
+  for (int i = a0 + warp; i < a1; i += nw) {
+    int ri_id = rep[i];
+    if (conv[ri_id]) continue;
+    int na = min(nall[i], cap_all);
+    R hs = R(0), ht = R(0);
+    for (int e = lane; e < na; e += 32) {
+      size_t idx = (size_t)i * cap_all + e;
+      typename Vec2<R>::T zj = zr[nbr[idx]];
+      R m = M[idx];
+      hs += m * zj.x;
+      ht += m * zj.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      hs += __shfl_xor_sync(CT_FULL, hs, o);
+      ht += __shfl_xor_sync(CT_FULL, ht, o);
+    }
+    if (lane == 0) {
+      double2 zi = z[i], rri = r[i];
+      double D = Dg[i];
+      double2 wi;
+      wi.x = D * zi.x + (double)hs;
+      wi.y = D * zi.y + (double)ht;
+      w[i] = wi;
+      acc.to(ri_id, cg + buf, CG_STRIDE);
+      acc.v[0] += rri.x * zi.x;
+      acc.v[1] += wi.x * zi.x;
+      acc.v[2] += rri.y * zi.y;
+      acc.v[3] += wi.y * zi.y;
+    }
+  }
+  block_flush<4>(acc, cg + buf, CG_STRIDE);
+}
+
+// Element-wise update and the sums for the convergence test.
+template <class R>
+__global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const double* __restrict__ dinv,
+                        int* __restrict__ conv, int* __restrict__ iters, int* __restrict__ itp,
+                        const double2* __restrict__ w, double2* __restrict__ x, double2* __restrict__ r,
+                        double2* __restrict__ p, double2* __restrict__ s, double2* __restrict__ z,
+                        typename Vec2<R>::T* __restrict__ zr, double* __restrict__ cg, int Rn,
+                        const RepInfo* __restrict__ reps, int* __restrict__ blocks, int* __restrict__ active,
+                        long long* __restrict__ total, unsigned* __restrict__ err, double tol, int max_iter,
+                        int use_cond, cudaGraphConditionalHandle cond) {
+  if (*active == 0) {
+    // nothing left to do (converged at the start): end the loop
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
+  int it = *itp;
+  int dbuf = CG_DOTS + (it & 1) * 4;
+  int ubuf = CG_UPD + (it % 3) * 5;
+  int sprev = CG_SCAL + ((it + 1) & 1) * 4;
+  int scur = CG_SCAL + (it & 1) * 4;
+  // zero the buffers the next iteration accumulates into
+  if (blockIdx.x == 0) {
+    int dn = CG_DOTS + ((it + 1) & 1) * 4, un = CG_UPD + ((it + 1) % 3) * 5;
+    for (int q = threadIdx.x; q < Rn * 9; q += blockDim.x) {
+      int rr = q / 9, k = q % 9;
+      double* c = cg + (size_t)rr * CG_STRIDE;
+      if (k < 4) c[dn + k] = 0.0;
+      else c[un + k - 4] = 0.0;
+    }
+  }
+  RepAcc<5> acc;
+  acc.init();
+  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
+  int lane = threadIdx.x & 31;
+  // thread-per-atom; warp-level merge before the replica accumulator
+  for (int base = a0; base < a1; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int rid = -1;
+    double v5[5] = {0, 0, 0, 0, 0};
+    if (i < a1) {
+      rid = rep[i];
+      if (!conv[rid]) {
+        const double* c = cg + (size_t)rid * CG_STRIDE;
+        double gs = ldcg(c + dbuf + 0), ds = ldcg(c + dbuf + 1);
+        double gt = ldcg(c + dbuf + 2), dt = ldcg(c + dbuf + 3);
+        double as, at, bs, bt;
+        if (it == 0) {
+          bs = 0.0; bt = 0.0;
+          as = gs / ds; at = gt / dt;
+        } else {
+          double gps = c[sprev + 0], aps = c[sprev + 1], gpt = c[sprev + 2], apt = c[sprev + 3];
+          bs = gs / gps; bt = gt / gpt;
+          as = gs / (ds - bs * gs / aps);
+          at = gt / (dt - bt * gt / apt);
+        }
+        if (i == reps[rid].atom_off) {
+          double* cw = cg + (size_t)rid * CG_STRIDE;
+          cw[scur + 0] = gs; cw[scur + 1] = as; cw[scur + 2] = gt; cw[scur + 3] = at;
+        }
+        double2 zi = z[i], wi = w[i], pi = p[i], si = s[i], xi = x[i], ri = r[i];
+        pi.x = zi.x + bs * pi.x; pi.y = zi.y + bt * pi.y;
+        si.x = wi.x + bs * si.x; si.y = wi.y + bt * si.y;
+        xi.x += as * pi.x; xi.y += at * pi.y;
+        ri.x -= as * si.x; ri.y -= at * si.y;
+        double di = dinv[i];
+        zi.x = ri.x * di; zi.y = ri.y * di;
+        p[i] = pi; s[i] = si; x[i] = xi; r[i] = ri; z[i] = zi;
+        typename Vec2<R>::T zz;
+        zz.x = (R)zi.x; zz.y = (R)zi.y;
+        zr[i] = zz;
+        v5[0] = ri.x * ri.x; v5[1] = ri.y * ri.y; v5[2] = ri.x * ri.y; v5[3] = xi.x; v5[4] = xi.y;
+      } else {
+        rid = -1;
+      }
+    }
+    // merge lanes of the same replica
+    int r0 = __shfl_sync(CT_FULL, rid, 0);
+    bool same = __all_sync(CT_FULL, rid == r0);
+    if (same) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v5[k] = warp_sum(v5[k]);
+      if (lane == 0 && r0 >= 0) {
+        acc.to(r0, cg + ubuf, CG_STRIDE);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc.v[k] += v5[k];
+      }
+    } else if (rid >= 0) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) atomicAdd(cg + (size_t)rid * CG_STRIDE + ubuf + k, v5[k]);
+    }
+  }
+  block_flush<5>(acc, cg + ubuf, CG_STRIDE);
+  if (last_block(blocks + 1)) {
+    int all = check_replicas(Rn, cg, conv, iters, cg, ubuf, it + 1, tol);
+    if (threadIdx.x == 0) {
+      blocks[1] = 0;
+      *itp = it + 1;
+      bool stop = all || (it + 1 >= max_iter);
+      if (stop) {
+        if (!all) atomicOr(err, CT_ERR_CG_MAXITER);
+        *active = 0;
+        *total += it + 1;
+      }
+      if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
+    }
+  }
+}
+
+// q = s + mu t per replica.
+__global__ void k_cg_final(int N, const int* __restrict__ rep, const double2* __restrict__ x,
+                           const double* __restrict__ cg, double* __restrict__ q) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double mu = cg[(size_t)rep[i] * CG_STRIDE + CG_MU];
+  double2 xi = x[i];
+  q[i] = xi.x + mu * xi.y;
+}
+
+// --------------------------------------------------------------- launchers
+static inline int chunk_grid(int N, int per_block_min, int gmax, int& chunk) {
+  int grid = (N + per_block_min - 1) / per_block_min;
+  if (grid > gmax) grid = gmax;
+  if (grid < 1) grid = 1;
+  chunk = (N + grid - 1) / grid;
+  return (N + chunk - 1) / chunk;
+}
+
+template <class R>
+void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, double tol) {
+  k_cg_prep<<<1, 256, 0, st>>>(S.R, S.cg, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
+  if (S.N == 0) return;
+  int chunk;
+  int grid = chunk_grid(S.N, 8, S.nsm * 8, chunk);
+  k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.cap_all, chunk, S.nbr, S.nall, (const R*)S.M, S.Dg, S.dinv,
+                                     S.type, S.rep, T, S.cx, S.cr, S.cz, (typename Vec2<R>::T*)S.czr,
+                                     S.cg, S.R, S.cg_conv, S.cg_iters, S.cg_blocks, S.cg_active, tol);
+}
+
+template <class R>
+void launch_cg_mv(const DevState& S, cudaStream_t st) {
+  if (S.N == 0) return;
+  int chunk;
+  int grid = chunk_grid(S.N, 8, S.nsm * 8, chunk);
+  k_cg_mv<R><<<grid, 256, 0, st>>>(S.N, S.cap_all, chunk, S.nbr, S.nall, (const R*)S.M, S.Dg, S.rep,
+                                   S.cg_conv, S.cg_it, (const typename Vec2<R>::T*)S.czr, S.cz, S.cr,
+                                   S.cw, S.cg, S.cg_active);
+}
+
+template <class R>
+void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
+  if (S.N == 0) return;
+  int chunk2;
+  int grid2 = chunk_grid(S.N, 256, S.nsm * 4, chunk2);
+  k_cg_up<R><<<grid2, 256, 0, st>>>(S.N, chunk2, S.rep, S.dinv, S.cg_conv, S.cg_iters, S.cg_it, S.cw, S.cx,
+                                    S.cr, S.cp, S.cs, S.cz, (typename Vec2<R>::T*)S.czr, S.cg, S.R, S.reps,
+                                    S.cg_blocks, S.cg_active, S.cg_total, S.err, cfg.tol, cfg.max_iter,
+                                    cfg.use_cond, cfg.cond);
+}
+
+template <class R>
+void launch_cg_iter(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
+  launch_cg_mv<R>(S, st);
+  launch_cg_up<R>(S, cfg, st);
+}
+
+template <class R>
+void launch_cg_end(const DevState& S, cudaStream_t st) {
+  if (S.N == 0) return;
+  k_cg_final<<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.rep, S.cx, S.cg, S.q);
+}
+
+template void launch_cg_begin<float>(const DevState&, const TypeParams&, cudaStream_t, double);
+template void launch_cg_begin<double>(const DevState&, const TypeParams&, cudaStream_t, double);
+template void launch_cg_mv<float>(const DevState&, cudaStream_t);
+template void launch_cg_mv<double>(const DevState&, cudaStream_t);
+template void launch_cg_up<float>(const DevState&, const SolveCfg&, cudaStream_t);
+template void launch_cg_up<double>(const DevState&, const SolveCfg&, cudaStream_t);
+template void launch_cg_iter<float>(const DevState&, const SolveCfg&, cudaStream_t);
+template void launch_cg_iter<double>(const DevState&, const SolveCfg&, cudaStream_t);
+template void launch_cg_end<float>(const DevState&, cudaStream_t);
+template void launch_cg_end<double>(const DevState&, cudaStream_t);
+
+}  // namespace ct

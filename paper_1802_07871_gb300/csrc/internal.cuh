@@ -1,0 +1,216 @@
+// internal.cuh — device-side types and helpers shared by the libctbop kernels.
+//
+// Layout (all device memory, N atoms, R replicas):
+//   x, v, F          double[N*3]   master positions / velocities / forces
+//   q                double[N]     charges
+//   type, rep        int32[N]      atom type (0 Si, 1 C), replica id
+//   cell4            int4[N]       cell coordinates (x,y,z) and global cell id, fixed between rebuilds
+//   u                Real4[N]      position relative to the owning cell's origin (w = type)
+//   nbr, code        int32[N*cap]  one list per atom: entries [0, ncov) are the covalent
+//                                  list (r < S + skin), [ncov, nall) the rest inside Rc + skin
+//   code             packed cell offset (dx,dy,dz) such that r_ij = u_j - u_i + d*h
+//   rev              int32[N*capc] entry of j's list that points back to i (covalent part)
+//   bo               Real4[N*capc] b_ij, db/dzeta_1, db/dzeta_2 per directed bond
+//   gslot            Real4[N*capc] dE_i/du_e: gradient of the terms centred on i w.r.t. bond e
+//   M                Real[N*cap]   charge-Hessian off-diagonal entries K_ij - 2 w_ij
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#define CT_WARP 32
+#define CT_FULL 0xffffffffu
+
+// device error bits
+#define CT_ERR_NBR_OVERFLOW 1u
+#define CT_ERR_COV_OVERFLOW 2u
+#define CT_ERR_REV_MISSING 4u
+#define CT_ERR_NONFINITE 8u
+#define CT_ERR_CG_MAXITER 16u
+#define CT_ERR_CODE_RANGE 32u
+
+namespace ct {
+
+template <class R> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+template <> struct Vec4<double> { using T = double4_32a; };
+template <class R> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2; };
+
+// Potential parameters in the working precision, passed by value to kernels.
+template <class R> struct PotParams {
+  // pair block [ti*2+tj]
+  R A[4], B[4], lam1[4], lam2[4], Rin[4], Sout[4], kappa[4], pi_SR[4];
+  R rcov_list2[4];                 // (S + skin)^2, covalent list radius squared
+  // bond order block [ti*2+tj]
+  R sigma[4], p[4], g1[4], g2[4], n1[4], n2[4], G[4], inv2s[4], inv2sp[4];
+  // triplet block [(ti*2+tj)*2+tk][l]
+  R gam[8][2], c2[8][2], d2[8][2], h[8][2], alpha[8][2], c2d2[8][2];
+  // charge kernel
+  R gshield3[4];                   // (gamma_i gamma_j)^(-3/2)
+  R rcoul, inv_rcoul, ke;
+  R rall_list2;                    // (Rc + skin)^2
+};
+
+// Per-type quantities that always stay double.
+struct TypeParams {
+  double E0[2], chi[2], J[2], inv_mass_acc[2], mass[2];
+};
+
+// One replica's box and cell grid.
+struct RepInfo {
+  double L[3];        // box lengths (binning extent along open axes)
+  double hc[3];       // cell edge
+  float hcf[3];
+  int pbc[3];
+  int n[3];           // cells per axis
+  int m[3];           // stencil half width per axis
+  int cell_off;       // first global cell id
+  int atom_off;       // first atom
+  int natoms;
+};
+
+__host__ __device__ inline int pack_code(int dx, int dy, int dz) {
+  return (dx + 512) | ((dy + 512) << 10) | ((dz + 512) << 20);
+}
+__host__ __device__ inline void unpack_code(int c, int& dx, int& dy, int& dz) {
+  dx = (c & 1023) - 512;
+  dy = ((c >> 10) & 1023) - 512;
+  dz = ((c >> 20) & 1023) - 512;
+}
+
+template <class R> __device__ inline R ct_exp(R x);
+template <> __device__ inline float ct_exp<float>(float x) { return expf(x); }
+template <> __device__ inline double ct_exp<double>(double x) { return exp(x); }
+template <class R> __device__ inline R ct_pow(R x, R y);
+template <> __device__ inline float ct_pow<float>(float x, float y) { return powf(x, y); }
+template <> __device__ inline double ct_pow<double>(double x, double y) { return pow(x, y); }
+template <class R> __device__ inline R ct_sqrt(R x);
+template <> __device__ inline float ct_sqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ inline double ct_sqrt<double>(double x) { return sqrt(x); }
+template <class R> __device__ inline R ct_cbrt(R x);
+template <> __device__ inline float ct_cbrt<float>(float x) { return cbrtf(x); }
+template <> __device__ inline double ct_cbrt<double>(double x) { return cbrt(x); }
+template <class R> __device__ inline R ct_cospi(R x);
+template <> __device__ inline float ct_cospi<float>(float x) { return cospif(x); }
+template <> __device__ inline double ct_cospi<double>(double x) { return cospi(x); }
+template <class R> __device__ inline R ct_sinpi(R x);
+template <> __device__ inline float ct_sinpi<float>(float x) { return sinpif(x); }
+template <> __device__ inline double ct_sinpi<double>(double x) { return sinpi(x); }
+
+// Tersoff cutoff and its derivative.
+template <class R>
+__device__ inline void cutoff_fn(R r, R Rin, R Sout, R pi_SR, R& f, R& df) {
+  if (r < Rin) { f = R(1); df = R(0); return; }
+  if (r >= Sout) { f = R(0); df = R(0); return; }
+  R t = (r - Rin) / (Sout - Rin);
+  f = R(0.5) * (R(1) + ct_cospi<R>(t));
+  df = R(-0.5) * pi_SR * ct_sinpi<R>(t);
+}
+
+// Shielded, tapered charge kernel K(r) and dK/dr.
+template <class R>
+__device__ inline void coul_fn(R r, R gs3, R inv_rc, R ke, R& K, R& dK) {
+  R x = r * inv_rc;
+  if (x >= R(1)) { K = R(0); dK = R(0); return; }
+  R x2 = x * x, x3 = x2 * x, x4 = x2 * x2;
+  R T = R(1) + x4 * (R(-35) + x * (R(84) + x * (R(-70) + R(20) * x)));
+  R xm = x - R(1);
+  R dT = R(140) * x3 * xm * xm * xm;
+  R r3 = r * r * r;
+  R D = ct_cbrt<R>(r3 + gs3);
+  R iD = R(1) / D;
+  K = ke * T * iD;
+  R iD3 = iD * iD * iD;
+  dK = ke * (dT * inv_rc * iD - T * r * r * iD3 * iD);
+}
+
+// ---------------------------------------------------------------- reductions
+// Accumulate NV doubles per replica. Each warp keeps a running partial for
+// the replica it is on and flushes with atomics when the replica changes; the
+// block merges its warps' final partials so a block that stays inside one
+// replica issues NV atomics in total.
+template <int NV>
+struct RepAcc {
+  int rep;
+  double v[NV];
+  __device__ inline void init() {
+    rep = -1;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  }
+  __device__ inline void flush(double* out, int stride) {
+    if (rep >= 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k)
+        if (v[k] != 0.0) atomicAdd(out + (size_t)rep * stride + k, v[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  }
+  // lane 0 only: switch to replica r, flushing the old partial
+  __device__ inline void to(int r, double* out, int stride) {
+    if (r != rep) { flush(out, stride); rep = r; }
+  }
+};
+
+template <int NV>
+__device__ inline void block_flush(RepAcc<NV>& acc, double* out, int stride) {
+  // acc is valid on lane 0 of every warp
+  __shared__ int s_rep[32];
+  __shared__ double s_v[32][NV];
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int nw = blockDim.x >> 5;
+  if (lane == 0) {
+    s_rep[warp] = acc.rep;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s_v[warp][k] = acc.v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int cur = -1;
+    double sum[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sum[k] = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      int r = s_rep[w];
+      if (r < 0) continue;
+      if (r != cur) {
+        if (cur >= 0)
+          for (int k = 0; k < NV; ++k)
+            if (sum[k] != 0.0) atomicAdd(out + (size_t)cur * stride + k, sum[k]);
+        cur = r;
+        for (int k = 0; k < NV; ++k) sum[k] = 0.0;
+      }
+      for (int k = 0; k < NV; ++k) sum[k] += s_v[w][k];
+    }
+    if (cur >= 0)
+      for (int k = 0; k < NV; ++k)
+        if (sum[k] != 0.0) atomicAdd(out + (size_t)cur * stride + k, sum[k]);
+  }
+  __syncthreads();
+}
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(CT_FULL, v, o);
+  return v;
+}
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(CT_FULL, v, o);
+  return v;
+}
+__device__ inline double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(CT_FULL, v, o));
+  return v;
+}
+
+// atomic max for non-negative doubles (bit patterns order like the values)
+__device__ inline void atomic_max_nonneg(double* addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+}  // namespace ct

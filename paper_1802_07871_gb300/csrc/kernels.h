@@ -1,0 +1,96 @@
+// kernels.h — device state and kernel launchers of libctbop (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "internal.cuh"
+
+namespace ct {
+
+// Per-replica double accumulators, one row of RA_STRIDE per replica.
+enum RepSlots {
+  RA_E = 0,        // potential energy
+  RA_W = 1,        // virial, 9 components
+  RA_KE = 10,      // kinetic energy
+  RA_STRIDE = 12
+};
+
+// CG scalars per replica (double), see cg.cu.
+enum CgSlots {
+  CG_DOTS = 0,     // [2 buffers][4]: (r.z, w.z) for the s and t solves
+  CG_UPD = 8,      // [3 buffers][5]: sum r_s^2, r_t^2, r_s r_t, x_s, x_t
+  CG_SCAL = 23,    // [2 buffers][4]: gamma_s, alpha_s, gamma_t, alpha_t of the last iteration
+  CG_MU = 31,      // final mu
+  CG_RES = 32,     // final rms residual
+  CG_Q = 33,       // requested total charge
+  CG_NAT = 34,     // atoms in the replica
+  CG_STRIDE = 36
+};
+
+struct DevState {
+  int N = 0, R = 0, ncells = 0;
+  int cap_cov = 0, cap_all = 0;
+  // per atom
+  double *x = nullptr, *v = nullptr, *F = nullptr, *xref = nullptr, *q = nullptr, *e_atom = nullptr;
+  int *type = nullptr, *rep = nullptr;
+  uint8_t* frozen = nullptr;
+  int4* cell4 = nullptr;
+  void* u = nullptr;            // Real4[N]
+  // per replica
+  RepInfo* reps = nullptr;
+  double* rep_acc = nullptr;    // [R][RA_STRIDE]
+  double* cg = nullptr;         // [R][CG_STRIDE]
+  int* cg_conv = nullptr;       // [R] converged flag
+  int* cg_iters = nullptr;      // [R] iterations used
+  // cells
+  int *cell_count = nullptr, *cell_fill = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
+  int* scan_tmp = nullptr;      // >= 1025 ints
+  // lists
+  int *nbr = nullptr, *code = nullptr, *ncov = nullptr, *nall = nullptr, *rev = nullptr;
+  void* bo = nullptr;           // Real4[N*cap_cov]
+  void* gslot = nullptr;        // Real4[N*cap_cov]
+  void* M = nullptr;            // Real[N*cap_all]
+  double *Dg = nullptr, *dinv = nullptr;
+  // CG vectors, (s, t) interleaved
+  double2 *cx = nullptr, *cr = nullptr, *cp = nullptr, *cs = nullptr, *cz = nullptr, *cw = nullptr;
+  void* czr = nullptr;          // Real2[N]: z in the matvec precision
+  // control
+  int* flag_rebuild = nullptr;
+  long long* rebuild_count = nullptr;
+  int* maxcnt = nullptr;        // [2] max ncov, max nall at the last rebuild
+  unsigned* err = nullptr;
+  int* cg_it = nullptr;         // iteration counter of the running solve
+  int* cg_blocks = nullptr;     // last-block counters
+  int* cg_active = nullptr;     // 1 while the solve runs (host-loop mirror of the graph condition)
+  long long* cg_total = nullptr;
+  // sizes for launches
+  int nsm = 152;
+};
+
+struct SolveCfg {
+  double tol;
+  int max_iter;
+  int use_cond;
+  cudaGraphConditionalHandle cond;
+};
+
+template <class R> void launch_rebuild(const DevState& S, const PotParams<R>& P, cudaStream_t st);
+template <class R> void launch_bond(const DevState& S, const PotParams<R>& P, cudaStream_t st);
+template <class R> void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams& T,
+                                        cudaStream_t st);
+template <class R> void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, double tol);
+template <class R> void launch_cg_iter(const DevState& S, const SolveCfg& cfg, cudaStream_t st);
+template <class R> void launch_cg_end(const DevState& S, cudaStream_t st);
+template <class R> void launch_cg_mv(const DevState& S, cudaStream_t st);
+template <class R> void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st);
+template <class R> void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams& T,
+                                         cudaStream_t st);
+template <class R> void launch_coul_gather(const DevState& S, const PotParams<R>& P, const TypeParams& T,
+                                           int kick, double half_dt, cudaStream_t st);
+template <class R> void launch_forces(const DevState& S, const PotParams<R>& P, const TypeParams& T,
+                                      int kick, double half_dt, cudaStream_t st);
+template <class R> void launch_kick_drift(const DevState& S, const TypeParams& T, double dt, double half_skin2,
+                                          cudaStream_t st);
+void launch_zero_acc(const DevState& S, cudaStream_t st);
+template <class R> cudaError_t setup_pot(int cap_cov);
+
+}  // namespace ct

@@ -1,0 +1,66 @@
+// md.cu — velocity-Verlet kick + drift, cell-local coordinates and the
+// neighbour-skin test (the MD of Sec. 3.3: frozen substrate atoms never
+// move; their forces are still computed).
+#include "internal.cuh"
+#include "kernels.h"
+
+namespace ct {
+
+// v += dt/2 F/m; x += dt v (mobile atoms); refresh the cell-local
+// coordinates; request a list rebuild when an atom moved more than half the
+// skin since the last rebuild.
+template <class R>
+__global__ void k_kick_drift(int N, double dt, double half_skin2, const int* __restrict__ type,
+                             const uint8_t* __restrict__ frozen, const int* __restrict__ rep,
+                             const RepInfo* __restrict__ reps, const int4* __restrict__ cell4,
+                             const double* __restrict__ F, double* __restrict__ v, double* __restrict__ x,
+                             const double* __restrict__ xref, typename Vec4<R>::T* __restrict__ u,
+                             TypeParams T, int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int ti = type[i];
+  double xi[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
+  if (!frozen[i]) {
+    double s = 0.5 * dt * T.inv_mass_acc[ti];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double vv = v[3 * i + d] + s * F[3 * i + d];
+      v[3 * i + d] = vv;
+      xi[d] += dt * vv;
+      x[3 * i + d] = xi[d];
+    }
+  }
+  const RepInfo& ri = reps[rep[i]];
+  int4 c = cell4[i];
+  typename Vec4<R>::T uu;
+  uu.x = (R)(xi[0] - c.x * ri.hc[0]);
+  uu.y = (R)(xi[1] - c.y * ri.hc[1]);
+  uu.z = (R)(xi[2] - c.z * ri.hc[2]);
+  uu.w = (R)ti;
+  u[i] = uu;
+  double dx = xi[0] - xref[3 * i], dy = xi[1] - xref[3 * i + 1], dz = xi[2] - xref[3 * i + 2];
+  if (dx * dx + dy * dy + dz * dz > half_skin2) *flag = 1;
+}
+
+__global__ void k_zero_acc(int n, double* __restrict__ a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = 0.0;
+}
+
+template <class R>
+void launch_kick_drift(const DevState& S, const TypeParams& T, double dt, double half_skin2, cudaStream_t st) {
+  if (S.N == 0) return;
+  k_kick_drift<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, dt, half_skin2, S.type, S.frozen, S.rep, S.reps,
+                                                     S.cell4, S.F, S.v, S.x, S.xref,
+                                                     (typename Vec4<R>::T*)S.u, T, S.flag_rebuild);
+}
+
+void launch_zero_acc(const DevState& S, cudaStream_t st) {
+  int n = S.R * RA_STRIDE;
+  k_zero_acc<<<(n + 255) / 256, 256, 0, st>>>(n, S.rep_acc);
+}
+
+template void launch_kick_drift<float>(const DevState&, const TypeParams&, double, double, cudaStream_t);
+template void launch_kick_drift<double>(const DevState&, const TypeParams&, double, double, cudaStream_t);
+
+}  // namespace ct

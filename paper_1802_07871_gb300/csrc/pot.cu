@@ -1,0 +1,514 @@
+// pot.cu — bond pass, charge-system assembly and forces.
+//
+// bond pass (k_bond): eight lanes per atom i; i's covalent entries are staged
+//   in shared memory; each lane owns bonds e and sums over the third atoms k
+//   the environment terms zeta_l,ie = sum_k fc(r_ik) ang_l(cos) e^{alpha_l (r_ie - r_ik)}
+//   (Sec. 2, Eq. 2), then b_ie and db/dzeta_l from the L = 2 form (Eq. 7).
+// assembly (k_assemble): one warp per atom; the off-diagonal charge Hessian
+//   entries M_e = K(r_e) - 2 w_e (w_e = 1/2 kappa fc B e^{-lambda2 r} (b_ij + b_ji)
+//   on covalent entries), diagonal 2 J + 2 sum w and the Jacobi inverse.
+// covalent forces (k_cov_force): eight lanes per atom; for every entry e the
+//   gradient dE_i/du_e of all terms centred on i (pair part, and the
+//   environment-sum chain rule both with e as bond and e as third atom);
+//   written to a per-bond slot, no atomics.
+// charge forces + gather (k_coul_gather): one warp per atom over all entries;
+//   F_i = sum_j q_i q_j K'(r) u_ij/r + sum_e slot(i,e) - sum_e slot(j_e, rev_e);
+//   per-atom energy, virial, optional velocity-Verlet half kick; FP64
+//   per-replica sums.
+#include "internal.cuh"
+#include "kernels.h"
+
+namespace ct {
+
+#define GRP 8           // lanes per atom in the covalent kernels
+#define APB 16          // atoms per block in the covalent kernels
+
+template <class R>
+__device__ inline void bond_order7(R z1, R z2, int pb, const PotParams<R>& P, R& b, R& db1, R& db2) {
+  R n1 = P.n1[pb], n2 = P.n2[pb], p = P.p[pb];
+  R zn1 = z1 > R(0) ? ct_pow<R>(z1, n1) : R(0);
+  R zn2 = z2 > R(0) ? ct_pow<R>(z2, n2) : R(0);
+  R Z1 = P.g1[pb] + zn1, Z2 = P.g2[pb] + zn2;
+  R t1 = ct_pow<R>(Z1, -p), t2 = ct_pow<R>(Z2, -p);
+  R Ssum = t1 + t2;
+  b = P.G[pb] * ct_pow<R>(Ssum, P.inv2sp[pb]);
+  R pre = -b * P.inv2s[pb] / Ssum;
+  db1 = z1 > R(0) ? pre * (t1 / Z1) * n1 * (zn1 / z1) : R(0);
+  db2 = z2 > R(0) ? pre * (t2 / Z2) * n2 * (zn2 / z2) : R(0);
+}
+
+template <class R>
+__device__ inline void rel_vec(const typename Vec4<R>::T& ui, const typename Vec4<R>::T& uj, int cd,
+                               R hx, R hy, R hz, R& rx, R& ry, R& rz) {
+  int dx, dy, dz;
+  unpack_code(cd, dx, dy, dz);
+  rx = (uj.x - ui.x) + (R)dx * hx;
+  ry = (uj.y - ui.y) + (R)dy * hy;
+  rz = (uj.z - ui.z) + (R)dz * hz;
+}
+
+// ---------------------------------------------------------------- bond pass
+template <class R>
+__global__ void __launch_bounds__(APB * GRP)
+k_bond(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restrict__ u,
+       const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
+       const int* __restrict__ code, const int* __restrict__ ncov, PotParams<R> P,
+       typename Vec4<R>::T* __restrict__ bo) {
+  using R4 = typename Vec4<R>::T;
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  int g = threadIdx.x / GRP, l = threadIdx.x % GRP;
+  R4* s_u = reinterpret_cast<R4*>(smem_raw) + (size_t)g * cap_cov;               // (ux,uy,uz,r)
+  R* s_fc = reinterpret_cast<R*>(reinterpret_cast<R4*>(smem_raw) + (size_t)APB * cap_cov) + (size_t)g * cap_cov;
+  int* s_t = reinterpret_cast<int*>(reinterpret_cast<R*>(reinterpret_cast<R4*>(smem_raw) + (size_t)APB * cap_cov)
+                                    + (size_t)APB * cap_cov) + (size_t)g * cap_cov;
+  int i = blockIdx.x * APB + g;
+  bool live = i < N;
+  int nc = 0, ti = 0;
+  R4 ui;
+  if (live) {
+    ui = u[i];
+    ti = (int)ui.w;
+    nc = min(ncov[i], cap_cov);
+    const RepInfo& ri = reps[rep[i]];
+    R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
+    if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
+    for (int e = l; e < nc; e += GRP) {
+      int j = nbr[(size_t)i * cap_all + e];
+      R4 uj = u[j];
+      R rx, ry, rz;
+      rel_vec<R>(ui, uj, code[(size_t)i * cap_all + e], hx, hy, hz, rx, ry, rz);
+      R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
+      int tj = (int)uj.w;
+      int pb = ti * 2 + tj;
+      R fc, dfc;
+      cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
+      R4 w;
+      w.x = rx; w.y = ry; w.z = rz; w.w = r;
+      s_u[e] = w;
+      s_fc[e] = fc;
+      s_t[e] = tj;
+    }
+  }
+  __syncwarp();
+  if (!live) return;
+  for (int e = l; e < nc; e += GRP) {
+    R4 ue = s_u[e];
+    int tj = s_t[e];
+    int pb = ti * 2 + tj;
+    R4 out;
+    out.w = R(0);
+    if (ue.w >= P.Sout[pb]) {
+      out.x = R(1); out.y = R(0); out.z = R(0);
+      bo[(size_t)i * cap_cov + e] = out;
+      continue;
+    }
+    R re = ue.w, ire = R(1) / re;
+    R z1 = R(0), z2 = R(0);
+    int tbase = pb * 2;
+    for (int k = 0; k < nc; ++k) {
+      if (k == e) continue;
+      R fck = s_fc[k];
+      if (fck == R(0)) continue;
+      R4 uk = s_u[k];
+      int tri = tbase + s_t[k];
+      R ct = (ue.x * uk.x + ue.y * uk.y + ue.z * uk.z) * ire / uk.w;
+      R dr = re - uk.w;
+      {
+        R hm = P.h[tri][0] - ct;
+        R ang = P.gam[tri][0] * (R(1) + P.c2d2[tri][0] - P.c2[tri][0] / (P.d2[tri][0] + hm * hm));
+        z1 += fck * ang * ct_exp<R>(P.alpha[tri][0] * dr);
+      }
+      {
+        R hm = P.h[tri][1] - ct;
+        R ang = P.gam[tri][1] * (R(1) + P.c2d2[tri][1] - P.c2[tri][1] / (P.d2[tri][1] + hm * hm));
+        z2 += fck * ang * ct_exp<R>(P.alpha[tri][1] * dr);
+      }
+    }
+    R b, db1, db2;
+    bond_order7<R>(z1, z2, pb, P, b, db1, db2);
+    out.x = b; out.y = db1; out.z = db2;
+    bo[(size_t)i * cap_cov + e] = out;
+  }
+}
+
+// ---------------------------------------------------------------- assembly
+template <class R>
+__global__ void k_assemble(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restrict__ u,
+                           const int* __restrict__ rep, const RepInfo* __restrict__ reps,
+                           const int* __restrict__ nbr, const int* __restrict__ code,
+                           const int* __restrict__ ncov, const int* __restrict__ nall,
+                           const int* __restrict__ rev, const typename Vec4<R>::T* __restrict__ bo,
+                           PotParams<R> P, TypeParams T, R* __restrict__ M, double* __restrict__ Dg,
+                           double* __restrict__ dinv) {
+  using R4 = typename Vec4<R>::T;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int i = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (i >= N) return;
+  R4 ui = u[i];
+  int ti = (int)ui.w;
+  const RepInfo& ri = reps[rep[i]];
+  R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
+  if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
+  int nc = min(ncov[i], cap_cov), na = min(nall[i], cap_all);
+  R wsum = R(0), selfm = R(0);
+  for (int e = lane; e < na; e += 32) {
+    size_t idx = (size_t)i * cap_all + e;
+    int j = nbr[idx];
+    R4 uj = u[j];
+    R rx, ry, rz;
+    rel_vec<R>(ui, uj, code[idx], hx, hy, hz, rx, ry, rz);
+    R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
+    int tj = (int)uj.w;
+    int pb = ti * 2 + tj;
+    R K, dK;
+    coul_fn<R>(r, P.gshield3[pb], P.inv_rcoul, P.ke, K, dK);
+    R m = K;
+    if (e < nc && r < P.Sout[pb]) {
+      R fc, dfc;
+      cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
+      R fA = P.B[pb] * ct_exp<R>(-P.lam2[pb] * r);
+      R bij = bo[(size_t)i * cap_cov + e].x;
+      R bji = bo[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]].x;
+      R w = R(0.5) * P.kappa[pb] * fc * fA * (bij + bji);
+      m -= R(2) * w;
+      wsum += w;
+    }
+    if (j == i) selfm += m;
+    M[idx] = m;
+  }
+  double ws = warp_sum((double)wsum);
+  double sm = warp_sum((double)selfm);
+  if (lane == 0) {
+    double D = 2.0 * T.J[ti] + 2.0 * ws;
+    Dg[i] = D;
+    dinv[i] = 1.0 / (D + sm);
+  }
+}
+
+// ---------------------------------------------------------------- covalent forces
+template <class R>
+__global__ void __launch_bounds__(APB * GRP)
+k_cov_force(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restrict__ u,
+            const int* __restrict__ rep, const RepInfo* __restrict__ reps,
+            const int* __restrict__ nbr, const int* __restrict__ code, const int* __restrict__ ncov,
+            const typename Vec4<R>::T* __restrict__ bo, const double* __restrict__ q, PotParams<R> P,
+            TypeParams T, typename Vec4<R>::T* __restrict__ gslot, double* __restrict__ e_atom) {
+  using R4 = typename Vec4<R>::T;
+  using R2 = typename Vec2<R>::T;
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  int g = threadIdx.x / GRP, l = threadIdx.x % GRP;
+  // layout: R4 u[APB][cap] | R2 D[APB][cap] | R fc | R dfc | R pair dE/dr | int type
+  R4* s_u = reinterpret_cast<R4*>(smem_raw);
+  R2* s_D = reinterpret_cast<R2*>(s_u + (size_t)APB * cap_cov);
+  R* s_fc = reinterpret_cast<R*>(s_D + (size_t)APB * cap_cov);
+  R* s_dfc = s_fc + (size_t)APB * cap_cov;
+  R* s_pd = s_dfc + (size_t)APB * cap_cov;
+  int* s_t = reinterpret_cast<int*>(s_pd + (size_t)APB * cap_cov);
+  s_u += (size_t)g * cap_cov; s_D += (size_t)g * cap_cov; s_fc += (size_t)g * cap_cov;
+  s_dfc += (size_t)g * cap_cov; s_pd += (size_t)g * cap_cov; s_t += (size_t)g * cap_cov;
+
+  int i = blockIdx.x * APB + g;
+  bool live = i < N;
+  int nc = 0, ti = 0;
+  double eacc = 0.0, qi = 0.0;
+  if (live) {
+    R4 ui = u[i];
+    ti = (int)ui.w;
+    nc = min(ncov[i], cap_cov);
+    const RepInfo& ri = reps[rep[i]];
+    R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
+    if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
+    qi = q[i];
+    for (int e = l; e < nc; e += GRP) {
+      size_t idx = (size_t)i * cap_all + e;
+      int j = nbr[idx];
+      R4 uj = u[j];
+      R rx, ry, rz;
+      rel_vec<R>(ui, uj, code[idx], hx, hy, hz, rx, ry, rz);
+      R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
+      int tj = (int)uj.w;
+      int pb = ti * 2 + tj;
+      R fc, dfc;
+      cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
+      R2 D;
+      D.x = R(0); D.y = R(0);
+      R pd = R(0);
+      if (fc > R(0)) {
+        R4 bb = bo[(size_t)i * cap_cov + e];
+        R dq = (R)(qi - q[j]);
+        R cq = R(1) - P.kappa[pb] * dq * dq;
+        R fR = P.A[pb] * ct_exp<R>(-P.lam1[pb] * r);
+        R fA = P.B[pb] * ct_exp<R>(-P.lam2[pb] * r);
+        R att = cq * bb.x * fA;
+        eacc += (double)(R(0.5) * fc * (fR - att));
+        pd = R(0.5) * (dfc * (fR - att) + fc * (-P.lam1[pb] * fR + P.lam2[pb] * att));
+        R pre = R(-0.5) * cq * fc * fA;
+        D.x = pre * bb.y;
+        D.y = pre * bb.z;
+      }
+      R4 w;
+      w.x = rx; w.y = ry; w.z = rz; w.w = r;
+      s_u[e] = w;
+      s_D[e] = D;
+      s_fc[e] = fc;
+      s_dfc[e] = dfc;
+      s_pd[e] = pd;
+      s_t[e] = tj;
+    }
+  }
+  __syncwarp();
+  if (live) {
+    for (int e = l; e < nc; e += GRP) {
+      R4 ux = s_u[e];
+      R rx = ux.w;
+      R fcx = s_fc[e];
+      R4 out;
+      out.x = R(0); out.y = R(0); out.z = R(0); out.w = R(0);
+      if (fcx > R(0)) {
+        R irx = R(1) / rx;
+        R hx_ = ux.x * irx, hy_ = ux.y * irx, hz_ = ux.z * irx;
+        R2 Dx = s_D[e];
+        R dfcx = s_dfc[e];
+        int tx = s_t[e];
+        R c_ux = s_pd[e];
+        R gx = R(0), gy = R(0), gz = R(0);
+        for (int k = 0; k < nc; ++k) {
+          if (k == e) continue;
+          R fck = s_fc[k];
+          if (fck == R(0)) continue;
+          R4 uk = s_u[k];
+          R rk = uk.w, irk = R(1) / rk;
+          R kx = uk.x * irk, ky = uk.y * irk, kz = uk.z * irk;
+          R ct = hx_ * kx + hy_ * ky + hz_ * kz;
+          int tk = s_t[k];
+          R2 Dk = s_D[k];
+          R c_perp = R(0);
+          // e as the bond, k as the third atom: triplet (ti, tx, tk)
+          {
+            int tri = (ti * 2 + tx) * 2 + tk;
+            R dr = rx - rk;
+#pragma unroll
+            for (int ll = 0; ll < 2; ++ll) {
+              R Dl = ll == 0 ? Dx.x : Dx.y;
+              R hm = P.h[tri][ll] - ct;
+              R den = P.d2[tri][ll] + hm * hm;
+              R ang = P.gam[tri][ll] * (R(1) + P.c2d2[tri][ll] - P.c2[tri][ll] / den);
+              R dang = R(-2) * P.gam[tri][ll] * P.c2[tri][ll] * hm / (den * den);
+              R ex = ct_exp<R>(P.alpha[tri][ll] * dr);
+              c_ux += Dl * P.alpha[tri][ll] * fck * ang * ex;
+              c_perp += Dl * fck * dang * ex;
+            }
+          }
+          // k as the bond, e as the third atom: triplet (ti, tk, tx)
+          {
+            int tri = (ti * 2 + tk) * 2 + tx;
+            R dr = rk - rx;
+#pragma unroll
+            for (int ll = 0; ll < 2; ++ll) {
+              R Dl = ll == 0 ? Dk.x : Dk.y;
+              R hm = P.h[tri][ll] - ct;
+              R den = P.d2[tri][ll] + hm * hm;
+              R ang = P.gam[tri][ll] * (R(1) + P.c2d2[tri][ll] - P.c2[tri][ll] / den);
+              R dang = R(-2) * P.gam[tri][ll] * P.c2[tri][ll] * hm / (den * den);
+              R ex = ct_exp<R>(P.alpha[tri][ll] * dr);
+              c_ux += Dl * (dfcx * ang * ex - P.alpha[tri][ll] * fcx * ang * ex);
+              c_perp += Dl * fcx * dang * ex;
+            }
+          }
+          // c_perp multiplies d cos / d u_e = (u_k/r_k - cos u_e/r_e) / r_e
+          R cp = c_perp * irx;
+          gx += cp * (kx - ct * hx_);
+          gy += cp * (ky - ct * hy_);
+          gz += cp * (kz - ct * hz_);
+        }
+        out.x = gx + c_ux * hx_;
+        out.y = gy + c_ux * hy_;
+        out.z = gz + c_ux * hz_;
+      }
+      gslot[(size_t)i * cap_cov + e] = out;
+    }
+  }
+  // per-atom energy: covalent part + self energy (all lanes take part)
+#pragma unroll
+  for (int o = GRP / 2; o > 0; o >>= 1) eacc += __shfl_xor_sync(CT_FULL, eacc, o, GRP);
+  if (live && l == 0) e_atom[i] = eacc + T.E0[ti] + T.chi[ti] * qi + T.J[ti] * qi * qi;
+}
+
+// ---------------------------------------------------------------- charge forces + gather
+template <class R>
+__global__ void k_coul_gather(int N, int cap_cov, int cap_all, int chunk,
+                              const typename Vec4<R>::T* __restrict__ u, const int* __restrict__ rep,
+                              const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
+                              const int* __restrict__ code, const int* __restrict__ ncov,
+                              const int* __restrict__ nall, const int* __restrict__ rev,
+                              const typename Vec4<R>::T* __restrict__ gslot, const double* __restrict__ q,
+                              PotParams<R> P, TypeParams T, int kick, double half_dt,
+                              const uint8_t* __restrict__ frozen, double* __restrict__ F,
+                              double* __restrict__ v, double* __restrict__ e_atom,
+                              double* __restrict__ rep_acc, unsigned* __restrict__ err) {
+  using R4 = typename Vec4<R>::T;
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
+  RepAcc<RA_STRIDE> acc;
+  acc.init();
+  for (int i = a0 + warp; i < a1; i += nw) {
+    R4 ui = u[i];
+    int ti = (int)ui.w;
+    int ri_id = rep[i];
+    const RepInfo& ri = reps[ri_id];
+    R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
+    if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
+    int nc = min(ncov[i], cap_cov), na = min(nall[i], cap_all);
+    R qi = (R)q[i];
+    R fx = R(0), fy = R(0), fz = R(0), ec = R(0);
+    R w[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) w[k] = R(0);
+    for (int e = lane; e < na; e += 32) {
+      size_t idx = (size_t)i * cap_all + e;
+      int j = nbr[idx];
+      R4 uj = u[j];
+      R rx, ry, rz;
+      rel_vec<R>(ui, uj, code[idx], hx, hy, hz, rx, ry, rz);
+      R r2 = rx * rx + ry * ry + rz * rz;
+      R r = ct_sqrt<R>(r2);
+      int tj = (int)uj.w;
+      R K, dK;
+      coul_fn<R>(r, P.gshield3[ti * 2 + tj], P.inv_rcoul, P.ke, K, dK);
+      R qq = qi * (R)q[j];
+      R c = qq * dK / r;          // force on i along (rx,ry,rz)
+      fx += c * rx; fy += c * ry; fz += c * rz;
+      ec += R(0.5) * qq * K;
+      R hc = R(-0.5) * c;         // virial of this directed pair: -1/2 qq K'/r r (x) r
+      w[0] += hc * rx * rx; w[1] += hc * rx * ry; w[2] += hc * rx * rz;
+      w[3] += hc * ry * rx; w[4] += hc * ry * ry; w[5] += hc * ry * rz;
+      w[6] += hc * rz * rx; w[7] += hc * rz * ry; w[8] += hc * rz * rz;
+      if (e < nc) {
+        R4 go = gslot[(size_t)i * cap_cov + e];
+        R4 gr = gslot[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]];
+        fx += go.x - gr.x; fy += go.y - gr.y; fz += go.z - gr.z;
+        w[0] -= rx * go.x; w[1] -= rx * go.y; w[2] -= rx * go.z;
+        w[3] -= ry * go.x; w[4] -= ry * go.y; w[5] -= ry * go.z;
+        w[6] -= rz * go.x; w[7] -= rz * go.y; w[8] -= rz * go.z;
+      }
+    }
+    // warp reductions in the working precision
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      fx += __shfl_xor_sync(CT_FULL, fx, o);
+      fy += __shfl_xor_sync(CT_FULL, fy, o);
+      fz += __shfl_xor_sync(CT_FULL, fz, o);
+      ec += __shfl_xor_sync(CT_FULL, ec, o);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) w[k] += __shfl_xor_sync(CT_FULL, w[k], o);
+    }
+    if (lane == 0) {
+      double Fx = fx, Fy = fy, Fz = fz;
+      F[3 * i] = Fx; F[3 * i + 1] = Fy; F[3 * i + 2] = Fz;
+      double ea = e_atom[i] + (double)ec;
+      e_atom[i] = ea;
+      if (!isfinite(ea) || !isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) atomicOr(err, CT_ERR_NONFINITE);
+      acc.to(ri_id, rep_acc, RA_STRIDE);
+      acc.v[RA_E] += ea;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc.v[RA_W + k] += (double)w[k];
+      if (kick) {
+        if (!frozen[i]) {
+          double s = half_dt * T.inv_mass_acc[ti];
+          v[3 * i] += s * Fx; v[3 * i + 1] += s * Fy; v[3 * i + 2] += s * Fz;
+        }
+        double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
+        acc.v[RA_KE] += 0.5 * T.mass[ti] * (vx * vx + vy * vy + vz * vz);
+      }
+    }
+  }
+  block_flush<RA_STRIDE>(acc, rep_acc, RA_STRIDE);
+}
+
+// ---------------------------------------------------------------- launchers
+template <class R> static size_t bond_smem(int cap) {
+  return (size_t)APB * cap * (sizeof(typename Vec4<R>::T) + sizeof(R) + sizeof(int));
+}
+template <class R> static size_t force_smem(int cap) {
+  return (size_t)APB * cap * (sizeof(typename Vec4<R>::T) + sizeof(typename Vec2<R>::T) + 3 * sizeof(R) + sizeof(int));
+}
+
+template <class R>
+void launch_bond(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
+  if (S.N == 0) return;
+  size_t sm = bond_smem<R>(S.cap_cov);
+  k_bond<R><<<(S.N + APB - 1) / APB, APB * GRP, sm, st>>>(
+      S.N, S.cap_cov, S.cap_all, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+      S.ncov, P, (typename Vec4<R>::T*)S.bo);
+}
+
+template <class R>
+void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st) {
+  if (S.N == 0) return;
+  int wpb = 8;
+  k_assemble<R><<<(S.N + wpb - 1) / wpb, wpb * 32, 0, st>>>(
+      S.N, S.cap_cov, S.cap_all, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, (R*)S.M, S.Dg, S.dinv);
+}
+
+template <class R>
+void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st) {
+  if (S.N == 0) return;
+  size_t sm = force_smem<R>(S.cap_cov);
+  k_cov_force<R><<<(S.N + APB - 1) / APB, APB * GRP, sm, st>>>(
+      S.N, S.cap_cov, S.cap_all, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code, S.ncov,
+      (const typename Vec4<R>::T*)S.bo, S.q, P, T, (typename Vec4<R>::T*)S.gslot, S.e_atom);
+}
+
+template <class R>
+void launch_coul_gather(const DevState& S, const PotParams<R>& P, const TypeParams& T, int kick, double half_dt,
+                        cudaStream_t st) {
+  if (S.N == 0) return;
+  int wpb = 8;
+  int grid = (S.N + wpb - 1) / wpb;
+  int gmax = S.nsm * 8;
+  if (grid > gmax) grid = gmax;
+  int chunk = (S.N + grid - 1) / grid;
+  grid = (S.N + chunk - 1) / chunk;
+  k_coul_gather<R><<<grid, wpb * 32, 0, st>>>(
+      S.N, S.cap_cov, S.cap_all, chunk, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.gslot, S.q, P, T, kick, half_dt, S.frozen, S.F,
+      S.v, S.e_atom, S.rep_acc, S.err);
+}
+
+template <class R>
+void launch_forces(const DevState& S, const PotParams<R>& P, const TypeParams& T, int kick, double half_dt,
+                   cudaStream_t st) {
+  launch_cov_force<R>(S, P, T, st);
+  launch_coul_gather<R>(S, P, T, kick, half_dt, st);
+}
+
+// Allow the dynamic shared memory the covalent kernels need for cap_cov
+// entries per atom (call before launching or capturing them).
+template <class R>
+cudaError_t setup_pot(int cap_cov) {
+  cudaError_t e = cudaFuncSetAttribute(k_bond<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bond_smem<R>(cap_cov));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_cov_force<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)force_smem<R>(cap_cov));
+}
+template cudaError_t setup_pot<float>(int);
+template cudaError_t setup_pot<double>(int);
+
+template void launch_bond<float>(const DevState&, const PotParams<float>&, cudaStream_t);
+template void launch_bond<double>(const DevState&, const PotParams<double>&, cudaStream_t);
+template void launch_assemble<float>(const DevState&, const PotParams<float>&, const TypeParams&, cudaStream_t);
+template void launch_assemble<double>(const DevState&, const PotParams<double>&, const TypeParams&, cudaStream_t);
+template void launch_cov_force<float>(const DevState&, const PotParams<float>&, const TypeParams&, cudaStream_t);
+template void launch_cov_force<double>(const DevState&, const PotParams<double>&, const TypeParams&, cudaStream_t);
+template void launch_coul_gather<float>(const DevState&, const PotParams<float>&, const TypeParams&, int, double,
+                                        cudaStream_t);
+template void launch_coul_gather<double>(const DevState&, const PotParams<double>&, const TypeParams&, int, double,
+                                         cudaStream_t);
+template void launch_forces<float>(const DevState&, const PotParams<float>&, const TypeParams&, int, double,
+                                   cudaStream_t);
+template void launch_forces<double>(const DevState&, const PotParams<double>&, const TypeParams&, int, double,
+                                    cudaStream_t);
+
+}  // namespace ct

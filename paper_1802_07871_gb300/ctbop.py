@@ -1,0 +1,312 @@
+"""Thin ctypes binding of libctbop (include/ctbop.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. Host arrays are numpy arrays; device arrays are torch CUDA tensors
+(their data_ptr() is passed with CTBOP_DEVICE). There is no CPU fallback: if
+the library is not built this module raises on first use.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .structures import TYPE_NAMES
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libctbop.so")
+
+OK = 0
+ERR = {
+    -1: "INVALID_ARG", -2: "OOM", -3: "NEIGH_OVERFLOW", -4: "CG_NOT_CONVERGED",
+    -5: "NONFINITE", -6: "CUDA", -7: "STATE",
+}
+HOST, DEVICE = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+FIXED_CHARGES = 1
+GET = {"energy": 0, "forces": 1, "charges": 2, "positions": 3, "velocities": 4,
+       "virial": 5, "e_atom": 6, "mu": 7, "kinetic": 8}
+
+# every symbol include/ctbop.h declares
+EXPORTS = (
+    "ctbop_default_options", "ctbop_create", "ctbop_destroy", "ctbop_last_error",
+    "ctbop_set_stream", "ctbop_set_layout", "ctbop_set_box", "ctbop_set_types",
+    "ctbop_set_positions", "ctbop_set_velocities", "ctbop_set_charges", "ctbop_set_frozen",
+    "ctbop_set_total_charge", "ctbop_compute", "ctbop_step", "ctbop_get", "ctbop_status",
+    "ctbop_profile_steps",
+)
+NPHASE = 10
+PHASES = ("kick_drift", "lists", "bond", "assemble", "cg_start", "cg_matvec", "cg_update",
+          "cg_charges", "cov_force", "coul_gather_kick")
+
+D4 = C.c_double * 4
+D2x4 = (C.c_double * 2) * 4
+D2x8 = (C.c_double * 2) * 8
+D2 = C.c_double * 2
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("A", D4), ("B", D4), ("lambda1", D4), ("lambda2", D4), ("R", D4), ("S", D4), ("kappa", D4),
+        ("sigma", D4), ("p", D4), ("g", D2x4), ("n", D2x4),
+        ("gamma", D2x8), ("c", D2x8), ("d", D2x8), ("h", D2x8), ("alpha", D2x8),
+        ("E0", D2), ("chi", D2), ("J", D2), ("gamma_c", D2), ("mass", D2),
+        ("r_coul", C.c_double), ("k_e", C.c_double),
+    ]
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32), ("cg_max_iter", C.c_int32), ("cg_tol", C.c_double),
+        ("skin", C.c_double), ("cap_cov", C.c_int32), ("cap_all", C.c_int32),
+        ("device", C.c_int32), ("reserved", C.c_int32),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("steps", C.c_int64), ("rebuilds", C.c_int64), ("cg_iters_last", C.c_int32),
+        ("max_cov", C.c_int32), ("cg_iters_total", C.c_int64), ("solves", C.c_int64),
+        ("cg_residual_last", C.c_double), ("max_all", C.c_int32), ("error_bits", C.c_uint32),
+        ("mean_cov", C.c_double), ("mean_all", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libctbop.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is not built; run paper_1802_07871_gb300.build.build()")
+    L = C.CDLL(_LIB_PATH)
+    vp = C.c_void_p
+    sig = {
+        "ctbop_default_options": ([C.POINTER(Options)], C.c_int),
+        "ctbop_create": ([C.POINTER(Params), C.POINTER(Options), C.POINTER(vp)], C.c_int),
+        "ctbop_destroy": ([vp], C.c_int),
+        "ctbop_last_error": ([vp], C.c_char_p),
+        "ctbop_set_stream": ([vp, vp], C.c_int),
+        "ctbop_set_layout": ([vp, C.c_int32, vp], C.c_int),
+        "ctbop_set_box": ([vp, vp, vp], C.c_int),
+        "ctbop_set_types": ([vp, vp, C.c_int], C.c_int),
+        "ctbop_set_positions": ([vp, vp, C.c_int], C.c_int),
+        "ctbop_set_velocities": ([vp, vp, C.c_int], C.c_int),
+        "ctbop_set_charges": ([vp, vp, C.c_int], C.c_int),
+        "ctbop_set_frozen": ([vp, vp, C.c_int], C.c_int),
+        "ctbop_set_total_charge": ([vp, vp], C.c_int),
+        "ctbop_compute": ([vp, C.c_uint32], C.c_int),
+        "ctbop_step": ([vp, C.c_int64, C.c_double], C.c_int),
+        "ctbop_get": ([vp, C.c_int, vp, C.c_int], C.c_int),
+        "ctbop_status": ([vp, C.POINTER(Stats)], C.c_int),
+        "ctbop_profile_steps": ([vp, C.c_int64, C.c_double, vp, vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def params_struct(d: dict) -> Params:
+    """Marshal a parameter dictionary (the JSON layout of params/*.json) into
+    the C struct. A set with L = 1 gets an inert second component
+    (g_2 = 1e30, n_2 = 1, gamma_2 = 0), which leaves Eq. 7 equal to the L = 1
+    form to far below double rounding."""
+    P = Params()
+    T = TYPE_NAMES
+    for a in range(2):
+        for b in range(2):
+            k = a * 2 + b
+            pr = d["pair"][T[min(a, b)] + T[max(a, b)]]
+            P.A[k], P.B[k] = pr["A"], pr["B"]
+            P.lambda1[k], P.lambda2[k] = pr["lambda1"], pr["lambda2"]
+            P.R[k], P.S[k], P.kappa[k] = pr["R"], pr["S"], pr["kappa"]
+            bo = d["bond"][T[a] + T[b]]
+            P.sigma[k], P.p[k] = bo["sigma"], bo["p"]
+            g, n = list(bo["g"]), list(bo["n"])
+            if len(g) == 1:
+                g, n = g + [1e30], n + [1.0]
+            P.g[k][0], P.g[k][1] = g
+            P.n[k][0], P.n[k][1] = n
+            for c in range(2):
+                t = (a * 2 + b) * 2 + c
+                tp = d["triplet"][T[a] + T[b] + T[c]]
+                for key, dst in (("gamma", P.gamma), ("c", P.c), ("d", P.d), ("h", P.h), ("alpha", P.alpha)):
+                    vals = list(tp[key])
+                    if len(vals) == 1:
+                        vals = vals + ([0.0] if key == "gamma" else [1.0 if key in ("c", "d") else 0.0])
+                    dst[t][0], dst[t][1] = vals
+    se, co = d["self"], d["coulomb"]
+    for t in range(2):
+        P.E0[t], P.chi[t], P.J[t] = se["E0"][t], se["chi"][t], se["J"][t]
+        P.gamma_c[t], P.mass[t] = co["gamma"][t], d["mass"][t]
+    P.r_coul, P.k_e = co["r_coul"], co["k_e"]
+    return P
+
+
+def _ptr(a):
+    """(pointer, mem) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data_as(C.c_void_p), HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return C.c_void_p(a.data_ptr()), (DEVICE if a.is_cuda else HOST)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class CtbopError(RuntimeError):
+    pass
+
+
+class System:
+    """One simulation (one or more replicas) on one GPU."""
+
+    def __init__(self, params: dict, precision: str = "mixed", skin: float = 0.3,
+                 cg_tol: float = 0.0, cg_max_iter: int = 200, device: int = 0,
+                 cap_cov: int = 0, cap_all: int = 0):
+        L = lib()
+        self._L = L
+        o = Options()
+        L.ctbop_default_options(C.byref(o))
+        o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
+        o.skin, o.cg_tol, o.cg_max_iter, o.device = skin, cg_tol, cg_max_iter, device
+        o.cap_cov, o.cap_all = cap_cov, cap_all
+        self._p = params_struct(params)
+        h = C.c_void_p()
+        rc = L.ctbop_create(C.byref(self._p), C.byref(o), C.byref(h))
+        if rc != OK:
+            raise CtbopError(f"ctbop_create failed: {ERR.get(rc, rc)}")
+        self._h = h
+        self.n = 0
+        self.R = 0
+        self.precision = precision
+
+    def _check(self, rc, what):
+        if rc != OK:
+            msg = self._L.ctbop_last_error(self._h).decode()
+            raise CtbopError(f"{what}: {ERR.get(rc, rc)}: {msg}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ctbop_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- setup
+    def set_stream(self, stream_handle: int):
+        self._check(self._L.ctbop_set_stream(self._h, C.c_void_p(stream_handle)), "set_stream")
+
+    def set_layout(self, offsets):
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        self._check(self._L.ctbop_set_layout(self._h, len(off) - 1, off.ctypes.data_as(C.c_void_p)), "set_layout")
+        self.n = int(off[-1])
+        self.R = len(off) - 1
+
+    def set_box(self, lengths, pbc):
+        lengths = np.asarray(lengths, dtype=np.float64).reshape(-1, 3)
+        h = np.zeros((len(lengths), 3, 3))
+        for r in range(len(lengths)):
+            h[r] = np.diag(lengths[r])
+        h = np.ascontiguousarray(h)
+        p = np.ascontiguousarray(np.asarray(pbc).reshape(-1, 3), dtype=np.uint8)
+        self._check(self._L.ctbop_set_box(self._h, h.ctypes.data_as(C.c_void_p), p.ctypes.data_as(C.c_void_p)),
+                    "set_box")
+
+    def _set(self, fn, a, dtype, what):
+        if isinstance(a, np.ndarray):
+            a = np.ascontiguousarray(a, dtype=dtype)
+        ptr, mem = _ptr(a)
+        self._keep = a
+        self._check(fn(self._h, ptr, mem), what)
+
+    def set_types(self, t):
+        self._set(self._L.ctbop_set_types, t, np.int32, "set_types")
+
+    def set_positions(self, x):
+        self._set(self._L.ctbop_set_positions, x, np.float64, "set_positions")
+
+    def set_velocities(self, v):
+        self._set(self._L.ctbop_set_velocities, v, np.float64, "set_velocities")
+
+    def set_charges(self, q):
+        self._set(self._L.ctbop_set_charges, q, np.float64, "set_charges")
+
+    def set_frozen(self, f):
+        self._set(self._L.ctbop_set_frozen, f, np.uint8, "set_frozen")
+
+    def set_total_charge(self, Q):
+        Q = np.ascontiguousarray(np.atleast_1d(Q), dtype=np.float64)
+        self._check(self._L.ctbop_set_total_charge(self._h, Q.ctypes.data_as(C.c_void_p)), "set_total_charge")
+
+    def load(self, structure, velocities=None, charges=None):
+        """Set layout, box, types, positions and frozen mask of one structure."""
+        s = structure
+        self.set_layout([0, s.n])
+        self.set_box(s.box, s.pbc)
+        self.set_types(s.types)
+        self.set_positions(s.x)
+        self.set_frozen(s.frozen.astype(np.uint8))
+        if velocities is not None:
+            self.set_velocities(velocities)
+        if charges is not None:
+            self.set_charges(charges)
+
+    def load_replicas(self, structures):
+        off = np.concatenate([[0], np.cumsum([s.n for s in structures])])
+        self.set_layout(off)
+        self.set_box(np.array([s.box for s in structures]), np.array([s.pbc for s in structures]))
+        self.set_types(np.concatenate([s.types for s in structures]))
+        self.set_positions(np.concatenate([s.x for s in structures]))
+        self.set_frozen(np.concatenate([s.frozen for s in structures]).astype(np.uint8))
+
+    # ---- run
+    def compute(self, fixed_charges: bool = False):
+        self._check(self._L.ctbop_compute(self._h, FIXED_CHARGES if fixed_charges else 0), "compute")
+
+    def step(self, n: int, dt: float):
+        self._check(self._L.ctbop_step(self._h, int(n), float(dt)), "step")
+
+    def profile_steps(self, n: int, dt: float) -> dict:
+        """Per-phase GPU time (ms, summed) and launch counts over n steps."""
+        ms = np.zeros(NPHASE)
+        cnt = np.zeros(NPHASE, dtype=np.int64)
+        self._check(self._L.ctbop_profile_steps(self._h, int(n), float(dt), ms.ctypes.data_as(C.c_void_p),
+                                                cnt.ctypes.data_as(C.c_void_p)), "profile_steps")
+        return {name: (float(ms[k]), int(cnt[k])) for k, name in enumerate(PHASES)}
+
+    def status(self) -> dict:
+        st = Stats()
+        rc = self._L.ctbop_status(self._h, C.byref(st))
+        d = st.as_dict()
+        d["rc"] = ERR.get(rc, rc) if rc else "OK"
+        return d
+
+    def get(self, what: str, out=None):
+        """Copy a result out. Without `out` returns a numpy array (synchronises);
+        `out` may be a numpy array or a torch tensor (device copy is
+        stream-ordered)."""
+        sel = GET[what]
+        shape = {"energy": (self.R,), "mu": (self.R,), "kinetic": (self.R,), "virial": (self.R, 3, 3),
+                 "forces": (self.n, 3), "positions": (self.n, 3), "velocities": (self.n, 3),
+                 "charges": (self.n,), "e_atom": (self.n,)}[what]
+        if out is None:
+            out = np.empty(shape, dtype=np.float64)
+        ptr, mem = _ptr(out)
+        self._check(self._L.ctbop_get(self._h, sel, ptr, mem), f"get {what}")
+        return out

@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs, FP64 and mixed precision, at sizes the oracle solves
+exactly plus full-size sampled checks."""
+import numpy as np
+import pytest
+
+from oracle import ctbop_oracle as O
+from paper_1802_07871_gb300 import structures as st
+from tests.gpu_helpers import TOL, compare, gpu_eval, oracle_eval, sampled_local_check
+
+pytestmark = pytest.mark.gpu
+P0 = st.load_params("p0")
+PT = st.load_params("pt")
+PRECS = ["fp64", "mixed"]
+
+
+def _cluster(n, seed, spread=3.5, min_sep=1.45):
+    rng = np.random.default_rng(seed)
+    xs = []
+    while len(xs) < n:
+        c = rng.uniform(-spread, spread, 3)
+        if all(np.linalg.norm(c - y) >= min_sep for y in xs):
+            xs.append(c)
+    x = np.array(xs) + 15.0
+    t = rng.integers(0, 2, n).astype(np.int32)
+    return st.Structure(f"cluster{n}", x, t, np.full(3, 30.0), np.array([False] * 3))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_bulk_512(prec):
+    """3C-SiC 4x4x4 cells, 512 atoms, +-0.05 A displacements, periodic."""
+    s = st.bulk_3c_512()
+    g = gpu_eval(s, P0, prec)
+    o = oracle_eval(s, P0)
+    compare(g, o, s.n, prec)
+    assert g["status"]["rc"] == "OK"
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_stepped_slab_with_adatoms(prec):
+    """Open-z 4H-SiC(0001) staircase slab with C adatoms and a frozen bottom."""
+    s = st.stepped_slab_small(8, 4, 6)
+    g = gpu_eval(s, P0, prec)
+    o = oracle_eval(s, P0)
+    compare(g, o, s.n, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("ncell", [1, 2])
+def test_small_periodic_boxes_images(prec, ncell):
+    """Edges of 4.36 and 8.72 A, below the 8 A charge cutoff: many periodic
+    images and self-images inside the cutoff; strained and displaced."""
+    s = st.sic_3c(ncell, 4.36, 0.1, seed=30 + ncell, strain=np.diag([0.03, -0.02, 0.01]))
+    t = s.types.copy()
+    t[1] = 1 - t[1]
+    s = st.Structure("small", s.x, t, s.box, s.pbc)
+    g = gpu_eval(s, P0, prec)
+    o = oracle_eval(s, P0)
+    compare(g, o, s.n, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_open_cluster(prec):
+    s = _cluster(41, 3)
+    g = gpu_eval(s, P0, prec)
+    o = oracle_eval(s, P0)
+    compare(g, o, s.n, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batched_replicas_uneven(prec):
+    """Replicas of different kinds and sizes in one launch (one empty, one
+    single atom); each replica compared with its own oracle solve."""
+    reps = [st.sic_3c(2, 4.36, 0.08, seed=5, strain=np.diag([0.04, 0.0, -0.03])),
+            _cluster(23, 9),
+            st.Structure("empty", np.zeros((0, 3)), np.zeros(0, np.int32), np.full(3, 20.0), np.array([True] * 3)),
+            st.Structure("atom", np.array([[5.0, 5.0, 5.0]]), np.array([1], np.int32), np.full(3, 12.0),
+                         np.array([False] * 3)),
+            st.sic_4h_slab(3, 2, 4, step="strip")]
+    g = gpu_eval(reps, P0, prec)
+    off = np.concatenate([[0], np.cumsum([s.n for s in reps])])
+    for r, s in enumerate(reps):
+        o = oracle_eval(s, P0) if s.n else {"F": np.zeros((0, 3)), "E": 0.0, "q": np.zeros(0),
+                                              "virial": np.zeros((3, 3)), "e_atom": np.zeros(0), "mu": None}
+        compare(g, o, s.n, prec, sl=slice(off[r], off[r + 1]), r=r)
+    # the lone C atom: no neighbours, q = Q = 0, E = E0(C)
+    assert abs(g["energy"][3] - P0["self"]["E0"][1]) < 1e-12
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_charged_system(prec):
+    s = st.sic_4h_slab(3, 2, 4, step="strip")
+    g = gpu_eval(s, P0, prec, Q=[1.5])
+    o = oracle_eval(s, P0, Q=1.5)
+    compare(g, o, s.n, prec)
+    assert abs(g["charges"].sum() - 1.5) < 1e-9
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fixed_charges(prec):
+    s = st.sic_3c(2, 4.36, 0.1, seed=77)
+    q = np.random.default_rng(4).normal(0, 0.3, s.n)
+    g = gpu_eval(s, P0, prec, charges=q, fixed=True)
+    o = oracle_eval(s, P0, q=q)
+    compare(g, o, s.n, prec, check_mu=False)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tersoff_reduction_parameters(prec):
+    """The L = 1, kappa = 0 set through the L = 2 kernels (inert second
+    component) against the oracle's general-L bond order."""
+    s = st.stepped_slab_small(6, 3, 5)
+    g = gpu_eval(s, PT, prec)
+    o = oracle_eval(s, PT)
+    compare(g, o, s.n, prec)
+
+
+def test_dimer_closed_form_gpu():
+    x = np.array([[10.0, 10.0, 10.0], [11.9, 10.0, 10.0]])
+    s = st.Structure("dimer", x, np.array([0, 1], np.int32), np.full(3, 30.0), np.array([False] * 3))
+    g = gpu_eval(s, P0, "fp64")
+    o = oracle_eval(s, P0)
+    compare(g, o, 2, "fp64")
+    assert abs(g["charges"][0] + g["charges"][1]) < 1e-14
+
+
+def test_device_pointer_path_matches_host():
+    torch = pytest.importorskip("torch")
+    from paper_1802_07871_gb300 import ctbop
+    s = st.sic_3c(2, 4.36, 0.1, seed=3)
+    gh = gpu_eval(s, P0, "mixed")
+    sysm = ctbop.System(P0, precision="mixed")
+    sysm.set_stream(torch.cuda.current_stream().cuda_stream)
+    sysm.set_layout([0, s.n])
+    sysm.set_box(s.box, s.pbc)
+    sysm.set_types(torch.tensor(s.types, device="cuda"))
+    sysm.set_positions(torch.tensor(s.x, device="cuda"))
+    sysm.set_frozen(torch.zeros(s.n, dtype=torch.uint8, device="cuda"))
+    sysm.compute()
+    F = torch.empty((s.n, 3), dtype=torch.float64, device="cuda")
+    sysm.get("forces", F)
+    torch.cuda.synchronize()
+    assert np.array_equal(F.cpu().numpy(), gh["forces"])
+    sysm.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_md_matches_oracle_trajectory(prec):
+    """20 NVE steps of 0.5 fs from the 512-atom state with 300 K velocities:
+    GPU positions follow the oracle's velocity-Verlet trajectory."""
+    from paper_1802_07871_gb300 import ctbop
+    s = st.bulk_3c_512()
+    v = st.maxwell_boltzmann(s.types, 300.0, seed=101)
+    sysm = ctbop.System(P0, precision=prec)
+    sysm.load(s, velocities=v)
+    sysm.step(20, 0.5)
+    xg = sysm.get("positions")
+    vg = sysm.get("velocities")
+    sysm.close()
+    xo, vo, qo, _ = O.velocity_verlet(s.x, v, s.types, s.box, s.pbc, P0, 0.5, 20)
+    d = xg - xo
+    d -= np.round(d / s.box) * s.box
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    assert np.max(np.abs(d)) < tol
+    assert np.max(np.abs(vg - vo)) < tol
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_md_energy_conservation(prec):
+    from paper_1802_07871_gb300 import ctbop
+    s = st.bulk_3c_512()
+    v = st.maxwell_boltzmann(s.types, 300.0, seed=101)
+    sysm = ctbop.System(P0, precision=prec)
+    sysm.load(s, velocities=v)
+    sysm.compute()
+    e0 = sysm.get("energy")[0] + O.kinetic_energy(v, s.types, P0)
+    et = []
+    for _ in range(10):
+        sysm.step(10, 0.5)
+        et.append(sysm.get("energy")[0] + sysm.get("kinetic")[0])
+    st_ = sysm.status()
+    sysm.close()
+    drift = np.max(np.abs(np.array(et) - e0)) / s.n
+    assert drift < 2e-5, drift
+    assert st_["steps"] == 100 and st_["rc"] == "OK"
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_slab_20k_sampled(prec):
+    """The 19,488-atom stepped slab at full size: sampled atoms re-evaluated
+    by the oracle on local cuts with the GPU charges held fixed; charge
+    stationarity dE/dq_i = mu at the sampled atoms; neutrality."""
+    s = st.stepped_slab_20k()
+    g = gpu_eval(s, P0, prec)
+    rng = np.random.default_rng(20)
+    top = np.argsort(s.x[:, 2])[-200:]
+    samples = np.concatenate([rng.choice(s.n, 24, replace=False), rng.choice(top, 8, replace=False)])
+    sampled_local_check(s, P0, g, prec, samples)
+    assert abs(g["charges"].sum()) < 1e-8
+    # Newton's third law holds for the whole system (all forces are internal)
+    assert np.max(np.abs(g["forces"].sum(0))) < (1e-6 if prec == "fp64" else 5e-2)
+
+
+def test_full_size_slab_1m_sampled():
+    """The ~1.005M-atom stepped slab with C adatoms, mixed precision, in the
+    launch configuration the benchmark times: sampled local oracle checks."""
+    s = st.stepped_slab_1m()
+    g = gpu_eval(s, P0, "mixed")
+    rng = np.random.default_rng(1)
+    ad = np.nonzero(s.types == 1)[0][-900:]
+    samples = np.concatenate([rng.choice(s.n, 24, replace=False), rng.choice(ad, 8, replace=False)])
+    sampled_local_check(s, P0, g, "mixed", samples)
+    assert abs(g["charges"].sum()) < 1e-6
