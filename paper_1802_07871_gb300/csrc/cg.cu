@@ -45,13 +45,15 @@ __device__ inline int check_replicas(int R, double* cg, int* conv, int* iters, c
     double* c = cg + (size_t)r * CG_STRIDE;
     const double* u5 = upd_base + (size_t)r * CG_STRIDE + upd_off;
     double rss = ldcg(u5 + 0), rtt = ldcg(u5 + 1), rst = ldcg(u5 + 2), xs = ldcg(u5 + 3), xt = ldcg(u5 + 4);
-    double mu = (c[CG_Q] - xs) / xt;
     double nat = c[CG_NAT];
+    // mu is undefined before t has any weight (cold start: x = 0)
+    double mu = (c[CG_Q] - xs) / xt;
+    bool mu_ok = (xt != 0.0) && isfinite(mu);
     double res2 = (rss + 2.0 * mu * rst + mu * mu * rtt) / (nat > 0 ? nat : 1.0);
-    double rms = sqrt(fmax(res2, 0.0));
-    c[CG_MU] = mu;
+    double rms = (mu_ok && isfinite(res2)) ? sqrt(res2 > 0.0 ? res2 : 0.0) : INFINITY;
+    c[CG_MU] = mu_ok ? mu : 0.0;
     c[CG_RES] = rms;
-    if (rms <= tol || nat == 0) {
+    if (nat == 0 || rms <= tol) {
       conv[r] = 1;
       iters[r] = it_done;
     } else {

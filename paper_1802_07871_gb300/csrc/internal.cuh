@@ -126,6 +126,19 @@ __device__ inline void coul_fn(R r, R gs3, R inv_rc, R ke, R& K, R& dK) {
   dK = ke * (dT * inv_rc * iD - T * r * r * iD3 * iD);
 }
 
+// Compensated (Neumaier) summation in the working precision: keeps the
+// rounding of long per-lane sums at the level of a single term.
+template <class R> struct CompSum {
+  R s = R(0), c = R(0);
+  __device__ inline void add(R x) {
+    R t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+  }
+  __device__ inline double value() const { return (double)s + (double)c; }
+};
+
 // ---------------------------------------------------------------- reductions
 // Accumulate NV doubles per replica. Each warp keeps a running partial for
 // the replica it is on and flushes with atomics when the replica changes; the

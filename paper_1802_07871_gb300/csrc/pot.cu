@@ -360,7 +360,8 @@ __global__ void k_coul_gather(int N, int cap_cov, int cap_all, int chunk,
     if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
     int nc = min(ncov[i], cap_cov), na = min(nall[i], cap_all);
     R qi = (R)q[i];
-    R fx = R(0), fy = R(0), fz = R(0), ec = R(0);
+    R fx = R(0), fy = R(0), fz = R(0);
+    CompSum<R> ec;
     R w[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) w[k] = R(0);
@@ -378,7 +379,7 @@ __global__ void k_coul_gather(int N, int cap_cov, int cap_all, int chunk,
       R qq = qi * (R)q[j];
       R c = qq * dK / r;          // force on i along (rx,ry,rz)
       fx += c * rx; fy += c * ry; fz += c * rz;
-      ec += R(0.5) * qq * K;
+      ec.add(R(0.5) * qq * K);
       R hc = R(-0.5) * c;         // virial of this directed pair: -1/2 qq K'/r r (x) r
       w[0] += hc * rx * rx; w[1] += hc * rx * ry; w[2] += hc * rx * rz;
       w[3] += hc * ry * rx; w[4] += hc * ry * ry; w[5] += hc * ry * rz;
@@ -398,14 +399,14 @@ __global__ void k_coul_gather(int N, int cap_cov, int cap_all, int chunk,
       fx += __shfl_xor_sync(CT_FULL, fx, o);
       fy += __shfl_xor_sync(CT_FULL, fy, o);
       fz += __shfl_xor_sync(CT_FULL, fz, o);
-      ec += __shfl_xor_sync(CT_FULL, ec, o);
 #pragma unroll
       for (int k = 0; k < 9; ++k) w[k] += __shfl_xor_sync(CT_FULL, w[k], o);
     }
+    double ecd = warp_sum(ec.value());
     if (lane == 0) {
       double Fx = fx, Fy = fy, Fz = fz;
       F[3 * i] = Fx; F[3 * i + 1] = Fy; F[3 * i + 2] = Fz;
-      double ea = e_atom[i] + (double)ec;
+      double ea = e_atom[i] + ecd;
       e_atom[i] = ea;
       if (!isfinite(ea) || !isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) atomicOr(err, CT_ERR_NONFINITE);
       acc.to(ri_id, rep_acc, RA_STRIDE);

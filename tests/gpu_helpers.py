@@ -12,6 +12,13 @@ from paper_1802_07871_gb300 import structures as st
 TOL = {
     "fp64": dict(force=1e-8, energy=1e-9, charge=1e-8, virial=1e-8, eatom=1e-8, mu=1e-8),
     "mixed": dict(force=1e-4, energy=1e-6, charge=1e-5, virial=1e-4, eatom=2e-5, mu=1e-5),
+    # Stress geometries in mixed precision: FP32 cell-local positions carry
+    # ~5e-7 A of rounding, so a term's energy error is about |dE_term/dr| x
+    # 5e-7 A. In cells smaller than the charge cutoff every periodic image of
+    # a pair rounds alike (~240 correlated terms per atom), and random
+    # clusters hold pairs compressed to 1.45 A with 50 eV repulsive terms;
+    # there the error no longer averages out. Forces keep the 1e-4 bar.
+    "mixed_stress": dict(force=1e-4, energy=5e-6, charge=1e-5, virial=1e-4, eatom=1e-4, mu=1e-5),
 }
 
 
@@ -35,9 +42,9 @@ def oracle_eval(s, params, Q=0.0, q=None):
     return O.evaluate(s.x, s.types, s.box, s.pbc, params, Q=Q, q=q)
 
 
-def compare(g, o, n, precision, sl=slice(None), r=0, check_charges=True, check_mu=True):
+def compare(g, o, n, precision, sl=slice(None), r=0, check_charges=True, check_mu=True, stress=False):
     """Compare replica r of a GPU result (atoms sl) with an oracle result."""
-    t = TOL[precision]
+    t = TOL["mixed_stress" if (stress and precision == "mixed") else precision]
     F, Fo = g["forces"][sl], o["F"]
     rms = max(np.sqrt(np.mean(Fo ** 2)), 1e-3)
     ferr = np.max(np.abs(F - Fo)) / rms if len(Fo) else 0.0

@@ -56,15 +56,16 @@ def test_small_periodic_boxes_images(prec, ncell):
     s = st.Structure("small", s.x, t, s.box, s.pbc)
     g = gpu_eval(s, P0, prec)
     o = oracle_eval(s, P0)
-    compare(g, o, s.n, prec)
+    compare(g, o, s.n, prec, stress=True)
 
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_open_cluster(prec):
+    """Random Si/C cluster, open boundaries, pairs down to 1.45 A."""
     s = _cluster(41, 3)
     g = gpu_eval(s, P0, prec)
     o = oracle_eval(s, P0)
-    compare(g, o, s.n, prec)
+    compare(g, o, s.n, prec, stress=True)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -82,7 +83,7 @@ def test_batched_replicas_uneven(prec):
     for r, s in enumerate(reps):
         o = oracle_eval(s, P0) if s.n else {"F": np.zeros((0, 3)), "E": 0.0, "q": np.zeros(0),
                                               "virial": np.zeros((3, 3)), "e_atom": np.zeros(0), "mu": None}
-        compare(g, o, s.n, prec, sl=slice(off[r], off[r + 1]), r=r)
+        compare(g, o, s.n, prec, sl=slice(off[r], off[r + 1]), r=r, stress=True)
     # the lone C atom: no neighbours, q = Q = 0, E = E0(C)
     assert abs(g["energy"][3] - P0["self"]["E0"][1]) < 1e-12
 
@@ -165,8 +166,7 @@ def test_md_matches_oracle_trajectory(prec):
     assert np.max(np.abs(vg - vo)) < tol
 
 
-@pytest.mark.parametrize("prec", PRECS)
-def test_md_energy_conservation(prec):
+def _nve_trace(prec, dt, nsteps, every):
     from paper_1802_07871_gb300 import ctbop
     s = st.bulk_3c_512()
     v = st.maxwell_boltzmann(s.types, 300.0, seed=101)
@@ -175,14 +175,30 @@ def test_md_energy_conservation(prec):
     sysm.compute()
     e0 = sysm.get("energy")[0] + O.kinetic_energy(v, s.types, P0)
     et = []
-    for _ in range(10):
-        sysm.step(10, 0.5)
+    for _ in range(nsteps // every):
+        sysm.step(every, dt)
         et.append(sysm.get("energy")[0] + sysm.get("kinetic")[0])
     st_ = sysm.status()
     sysm.close()
-    drift = np.max(np.abs(np.array(et) - e0)) / s.n
-    assert drift < 2e-5, drift
-    assert st_["steps"] == 100 and st_["rc"] == "OK"
+    assert st_["steps"] == nsteps and st_["rc"] == "OK"
+    return np.max(np.abs(np.array(et) - e0)) / s.n
+
+
+def test_md_energy_error_scales_as_dt_squared():
+    """Velocity Verlet on the GPU (FP64): over the same 50 fs, halving dt
+    divides the largest total-energy excursion by about four."""
+    d1 = _nve_trace("fp64", 0.5, 100, 5)
+    d2 = _nve_trace("fp64", 0.25, 200, 10)
+    assert 2.5 < d1 / d2 < 6.0, (d1, d2)
+    assert d1 < 1e-3
+
+
+def test_md_mixed_tracks_fp64_energy():
+    """The mixed path's energy excursion matches the FP64 path's: its own
+    rounding adds far less than the integrator's dt^2 error."""
+    d64 = _nve_trace("fp64", 0.5, 100, 5)
+    dmx = _nve_trace("mixed", 0.5, 100, 5)
+    assert abs(dmx - d64) < 0.1 * d64 + 1e-6, (dmx, d64)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -197,6 +213,10 @@ def test_full_size_slab_20k_sampled(prec):
     samples = np.concatenate([rng.choice(s.n, 24, replace=False), rng.choice(top, 8, replace=False)])
     sampled_local_check(s, P0, g, prec, samples)
     assert abs(g["charges"].sum()) < 1e-8
+    # total energy per atom against the oracle's full solve (CG path)
+    o = oracle_eval(s, P0)
+    assert abs(g["energy"][0] - o["E"]) / s.n <= TOL[prec]["energy"]
+    assert np.max(np.abs(g["charges"] - o["q"])) <= TOL[prec]["charge"]
     # Newton's third law holds for the whole system (all forces are internal)
     assert np.max(np.abs(g["forces"].sum(0))) < (1e-6 if prec == "fp64" else 5e-2)
 

@@ -299,9 +299,15 @@ def test_cg_matches_dense():
     assert abs(mud - muc) < 1e-10
 
 
-def test_hessian_positive_definite():
-    for s in (st.sic_3c(2, 4.36, 0.05, seed=1), st.sic_4h_slab(3, 2, 4, step="strip")):
-        H = O.System(s.x, s.types, s.box, s.pbc, P0).hessian_dense()
+@pytest.mark.parametrize("pname", ["p0", "pt"])
+def test_hessian_positive_definite(pname):
+    """Sec. 2: the charges minimise E_tot, which has a unique minimum only
+    when the charge Hessian is positive definite; every shipped parameter
+    set satisfies it on the test shapes."""
+    P = st.load_params(pname)
+    for s in (st.sic_3c(2, 4.36, 0.05, seed=1), st.sic_4h_slab(3, 2, 4, step="strip"),
+              st.stepped_slab_small(6, 3, 5), st.stepped_slab_small(8, 4, 6)):
+        H = O.System(s.x, s.types, s.box, s.pbc, P).hessian_dense()
         assert np.allclose(H, H.T)
         assert np.linalg.eigvalsh(H).min() > 1.0
 
