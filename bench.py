@@ -39,7 +39,7 @@ def args_():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="1m", choices=["1m", "20k", "512"])
+    ap.add_argument("--workload", default="1m", choices=["1m", "250k", "20k", "512"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=3)
@@ -52,6 +52,9 @@ def workload(name):
     if name == "1m":
         s = st.stepped_slab_1m()
         desc = "stepped 4H-SiC(0001) slab 96x48 cells x 56 bilayers, 3 steps, + 5% C adatoms"
+    elif name == "250k":
+        s = st.stepped_slab_250k()
+        desc = "stepped 4H-SiC(0001) slab 48x24 cells x 56 bilayers, 3 steps, + 5% C adatoms"
     elif name == "20k":
         s = st.stepped_slab_20k()
         desc = "stepped 4H-SiC(0001) slab 24x14 cells x 15 bilayers, 2 step edges"

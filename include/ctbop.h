@@ -100,7 +100,7 @@ typedef struct ctbop_options {
     int32_t precision;    /* CTBOP_PREC_FP64 or CTBOP_PREC_MIXED */
     int32_t cg_max_iter;  /* charge-solve iteration cap (default 200) */
     double  cg_tol;       /* stop when the rms over a replica's atoms of H q + chi - mu is below
-                           cg_tol (eV/e); 0 = policy default (FP64 1e-10, MIXED 1e-6) */
+                           cg_tol (eV/e); 0 = policy default (FP64 1e-10, MIXED 1e-5) */
     double  skin;         /* neighbour-list skin (A, default 0.3) */
     int32_t cap_cov;      /* covalent entries per atom; 0 = sized from the first configuration */
     int32_t cap_all;      /* all entries (charge cutoff) per atom; 0 = sized automatically */

@@ -7,9 +7,13 @@
 // q = s + mu t with mu = (Q - sum s) / sum t. Vectors are stored (s, t)
 // interleaved as double2. The iteration is the one-reduction (Chronopoulos-
 // Gear) form of PCG: per iteration one matrix pass that also forms the two
-// dot products (r.z, w.z), and one element-wise update that forms the sums
-// for the convergence test. Dot products, residual sums and the vectors are
-// FP64; the matrix entries and the gathered z_j are in the working precision.
+// dot products (r.z, w.z) and, in its last block, the step lengths; and one
+// element-wise update that forms the sums for the convergence test. Dot
+// products, residual sums and the vectors are FP64; the matrix entries and
+// the gathered z_j are in the working precision.
+//
+// Starting guess: the previous solutions extrapolated in time (quadratic
+// from three, linear from two, the last one alone otherwise).
 //
 // Convergence (per replica): rms over the replica's atoms of r_s + mu r_t
 // (= mu 1 - H q - chi, the stationarity residual) below tol. The last block
@@ -36,14 +40,14 @@ __device__ inline bool last_block(int* counter) {
   return am_last;
 }
 
-// Convergence test for every unconverged replica from the sums in upd.
-__device__ inline int check_replicas(int R, double* cg, int* conv, int* iters, const double* upd_base,
-                                     int upd_off, int it_done, double tol) {
+// Convergence test for every unconverged replica from the sums at upd_off.
+__device__ inline int check_replicas(int R, double* cg, int* conv, int* iters, int upd_off, int it_done,
+                                     double tol, int res_slot) {
   int all = 1;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     if (conv[r]) continue;
     double* c = cg + (size_t)r * CG_STRIDE;
-    const double* u5 = upd_base + (size_t)r * CG_STRIDE + upd_off;
+    const double* u5 = c + upd_off;
     double rss = ldcg(u5 + 0), rtt = ldcg(u5 + 1), rst = ldcg(u5 + 2), xs = ldcg(u5 + 3), xt = ldcg(u5 + 4);
     double nat = c[CG_NAT];
     // mu is undefined before t has any weight (cold start: x = 0)
@@ -53,6 +57,7 @@ __device__ inline int check_replicas(int R, double* cg, int* conv, int* iters, c
     double rms = (mu_ok && isfinite(res2)) ? sqrt(res2 > 0.0 ? res2 : 0.0) : INFINITY;
     c[CG_MU] = mu_ok ? mu : 0.0;
     c[CG_RES] = rms;
+    if (res_slot >= 0) c[res_slot] = rms;
     if (nat == 0 || rms <= tol) {
       conv[r] = 1;
       iters[r] = it_done;
@@ -76,21 +81,46 @@ __global__ void k_cg_prep(int R, double* __restrict__ cg, int* __restrict__ conv
     *it = 0;
     blocks[0] = 0;
     blocks[1] = 0;
+    blocks[2] = 0;
     *active = 1;
   }
 }
 
-// r = b - H x0, z = D^-1 r, with b = (-chi, 1); sums for the initial test.
+// Starting guess extrapolated from the stored solutions; shifts the
+// history (h2 <- h1, h1 <- the last solution).
+__global__ void k_cg_extrap(int N, double2* __restrict__ x, double2* __restrict__ h1, double2* __restrict__ h2,
+                            const int* __restrict__ hist) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int nh = *hist;
+  double2 xo = x[i], a = h1[i], b = h2[i], x0;
+  if (nh >= 3) {
+    x0.x = 3.0 * xo.x - 3.0 * a.x + b.x;
+    x0.y = 3.0 * xo.y - 3.0 * a.y + b.y;
+  } else if (nh == 2) {
+    x0.x = 2.0 * xo.x - a.x;
+    x0.y = 2.0 * xo.y - a.y;
+  } else {
+    x0 = xo;
+  }
+  h2[i] = a;
+  h1[i] = xo;
+  x[i] = x0;
+}
+
+// r = b - H x0, z = D^-1 r with b = (-chi, 1); sums for the initial test
+// (kept in update buffer 2).
 template <class R>
 __global__ void k_cg_init(int N, int cap_all, int chunk, const int* __restrict__ nbr,
                           const int* __restrict__ nall, const R* __restrict__ M, const double* __restrict__ Dg,
                           const double* __restrict__ dinv, const int* __restrict__ type, const int* __restrict__ rep,
                           TypeParams T, const double2* __restrict__ x, double2* __restrict__ r,
-                          double2* __restrict__ z, typename Vec2<R>::T* __restrict__ zr,
-                          double* __restrict__ cg, int Rn, int* __restrict__ conv, int* __restrict__ iters,
-                          int* __restrict__ blocks, int* __restrict__ active, double tol) {
+                          double2* __restrict__ z, typename Vec2<R>::T* __restrict__ zr, double* __restrict__ cg,
+                          int Rn, int* __restrict__ conv, int* __restrict__ iters, int* __restrict__ blocks,
+                          int* __restrict__ active, double tol) {
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
+  const int ub = CG_UPD + 2 * 5;
   RepAcc<5> acc;
   acc.init();
   for (int i = a0 + warp; i < a1; i += nw) {
@@ -124,7 +154,7 @@ __global__ void k_cg_init(int N, int cap_all, int chunk, const int* __restrict__
       zz.x = (R)zi.x;
       zz.y = (R)zi.y;
       zr[i] = zz;
-      acc.to(rep[i], cg + CG_UPD + 2 * 5, CG_STRIDE);  // update buffer 2
+      acc.to(rep[i], cg + ub, CG_STRIDE);
       acc.v[0] += ri.x * ri.x;
       acc.v[1] += ri.y * ri.y;
       acc.v[2] += ri.x * ri.y;
@@ -132,9 +162,9 @@ __global__ void k_cg_init(int N, int cap_all, int chunk, const int* __restrict__
       acc.v[4] += xi.y;
     }
   }
-  block_flush<5>(acc, cg + CG_UPD + 2 * 5, CG_STRIDE);
+  block_flush<5>(acc, cg + ub, CG_STRIDE);
   if (last_block(blocks)) {
-    int all = check_replicas(Rn, cg, conv, iters, cg, CG_UPD + 2 * 5, 0, tol);
+    int all = check_replicas(Rn, cg, conv, iters, ub, 0, tol, CG_RES0);
     if (threadIdx.x == 0) {
       blocks[0] = 0;
       if (all) *active = 0;
@@ -142,14 +172,15 @@ __global__ void k_cg_init(int N, int cap_all, int chunk, const int* __restrict__
   }
 }
 
-// w = H z and the dots (r.z, w.z) for both solves.
+// w = H z and the dots (r.z, w.z) for both solves; the last block turns the
+// dots into the step lengths alpha, beta of this iteration.
 template <class R>
 __global__ void k_cg_mv(int N, int cap_all, int chunk, const int* __restrict__ nbr, const int* __restrict__ nall,
                         const R* __restrict__ M, const double* __restrict__ Dg, const int* __restrict__ rep,
                         const int* __restrict__ conv, const int* __restrict__ itp,
                         const typename Vec2<R>::T* __restrict__ zr, const double2* __restrict__ z,
-                        const double2* __restrict__ r, double2* __restrict__ w, double* __restrict__ cg,
-                        const int* __restrict__ active) {
+                        const double2* __restrict__ r, double2* __restrict__ w, double* __restrict__ cg, int Rn,
+                        int* __restrict__ blocks, const int* __restrict__ active) {
   if (*active == 0) return;
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
@@ -161,13 +192,24 @@ __global__ void k_cg_mv(int N, int cap_all, int chunk, const int* __restrict__ n
     int ri_id = rep[i];
     if (conv[ri_id]) continue;
     int na = min(nall[i], cap_all);
+    const int* nrow = nbr + (size_t)i * cap_all;
+    const R* mrow = M + (size_t)i * cap_all;
     R hs = R(0), ht = R(0);
-    for (int e = lane; e < na; e += 32) {
-      size_t idx = (size_t)i * cap_all + e;
-      typename Vec2<R>::T zj = zr[nbr[idx]];
-      R m = M[idx];
-      hs += m * zj.x;
-      ht += m * zj.y;
+    int e = lane;
+    // two entries in flight per lane
+    for (; e + 32 < na; e += 64) {
+      int j0 = __ldg(nrow + e), j1 = __ldg(nrow + e + 32);
+      R m0 = __ldg(mrow + e), m1 = __ldg(mrow + e + 32);
+      typename Vec2<R>::T z0 = zr[j0], z1 = zr[j1];
+      hs += m0 * z0.x + m1 * z1.x;
+      ht += m0 * z0.y + m1 * z1.y;
+    }
+    if (e < na) {
+      int j0 = __ldg(nrow + e);
+      R m0 = __ldg(mrow + e);
+      typename Vec2<R>::T z0 = zr[j0];
+      hs += m0 * z0.x;
+      ht += m0 * z0.y;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -189,6 +231,32 @@ __global__ void k_cg_mv(int N, int cap_all, int chunk, const int* __restrict__ n
     }
   }
   block_flush<4>(acc, cg + buf, CG_STRIDE);
+  if (last_block(blocks + 2)) {
+    int sprev = CG_SCAL + ((it + 1) & 1) * 4;
+    int scur = CG_SCAL + (it & 1) * 4;
+    for (int rr = threadIdx.x; rr < Rn; rr += blockDim.x) {
+      if (conv[rr]) continue;
+      double* c = cg + (size_t)rr * CG_STRIDE;
+      double g[2] = {ldcg(c + buf + 0), ldcg(c + buf + 2)};
+      double d[2] = {ldcg(c + buf + 1), ldcg(c + buf + 3)};
+      for (int k = 0; k < 2; ++k) {
+        double a = 0.0, b = 0.0;
+        if (it == 0) {
+          a = d[k] != 0.0 ? g[k] / d[k] : 0.0;
+        } else {
+          double gp = c[sprev + 2 * k], ap = c[sprev + 2 * k + 1];
+          b = gp != 0.0 ? g[k] / gp : 0.0;
+          double den = d[k] - (ap != 0.0 ? b * g[k] / ap : 0.0);
+          a = den != 0.0 ? g[k] / den : 0.0;
+        }
+        c[CG_AB + 2 * k] = a;
+        c[CG_AB + 2 * k + 1] = b;
+        c[scur + 2 * k] = g[k];
+        c[scur + 2 * k + 1] = a;
+      }
+    }
+    if (threadIdx.x == 0) blocks[2] = 0;
+  }
 }
 
 // Element-wise update and the sums for the convergence test.
@@ -198,19 +266,15 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const dou
                         const double2* __restrict__ w, double2* __restrict__ x, double2* __restrict__ r,
                         double2* __restrict__ p, double2* __restrict__ s, double2* __restrict__ z,
                         typename Vec2<R>::T* __restrict__ zr, double* __restrict__ cg, int Rn,
-                        const RepInfo* __restrict__ reps, int* __restrict__ blocks, int* __restrict__ active,
-                        long long* __restrict__ total, unsigned* __restrict__ err, double tol, int max_iter,
-                        int use_cond, cudaGraphConditionalHandle cond) {
+                        int* __restrict__ blocks, int* __restrict__ active, unsigned* __restrict__ err,
+                        double tol, int max_iter, int use_cond, cudaGraphConditionalHandle cond) {
   if (*active == 0) {
     // nothing left to do (converged at the start): end the loop
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
     return;
   }
   int it = *itp;
-  int dbuf = CG_DOTS + (it & 1) * 4;
   int ubuf = CG_UPD + (it % 3) * 5;
-  int sprev = CG_SCAL + ((it + 1) & 1) * 4;
-  int scur = CG_SCAL + (it & 1) * 4;
   // zero the buffers the next iteration accumulates into
   if (blockIdx.x == 0) {
     int dn = CG_DOTS + ((it + 1) & 1) * 4, un = CG_UPD + ((it + 1) % 3) * 5;
@@ -225,7 +289,8 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const dou
   acc.init();
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
   int lane = threadIdx.x & 31;
-  // thread-per-atom; warp-level merge before the replica accumulator
+  int crid = -1;
+  double as = 0, bs = 0, at = 0, bt = 0;
   for (int base = a0; base < a1; base += blockDim.x) {
     int i = base + threadIdx.x;
     int rid = -1;
@@ -233,22 +298,11 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const dou
     if (i < a1) {
       rid = rep[i];
       if (!conv[rid]) {
-        const double* c = cg + (size_t)rid * CG_STRIDE;
-        double gs = ldcg(c + dbuf + 0), ds = ldcg(c + dbuf + 1);
-        double gt = ldcg(c + dbuf + 2), dt = ldcg(c + dbuf + 3);
-        double as, at, bs, bt;
-        if (it == 0) {
-          bs = 0.0; bt = 0.0;
-          as = gs / ds; at = gt / dt;
-        } else {
-          double gps = c[sprev + 0], aps = c[sprev + 1], gpt = c[sprev + 2], apt = c[sprev + 3];
-          bs = gs / gps; bt = gt / gpt;
-          as = gs / (ds - bs * gs / aps);
-          at = gt / (dt - bt * gt / apt);
-        }
-        if (i == reps[rid].atom_off) {
-          double* cw = cg + (size_t)rid * CG_STRIDE;
-          cw[scur + 0] = gs; cw[scur + 1] = as; cw[scur + 2] = gt; cw[scur + 3] = at;
+        if (rid != crid) {
+          const double* c = cg + (size_t)rid * CG_STRIDE;
+          as = ldcg(c + CG_AB + 0); bs = ldcg(c + CG_AB + 1);
+          at = ldcg(c + CG_AB + 2); bt = ldcg(c + CG_AB + 3);
+          crid = rid;
         }
         double2 zi = z[i], wi = w[i], pi = p[i], si = s[i], xi = x[i], ri = r[i];
         pi.x = zi.x + bs * pi.x; pi.y = zi.y + bt * pi.y;
@@ -284,7 +338,7 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const dou
   }
   block_flush<5>(acc, cg + ubuf, CG_STRIDE);
   if (last_block(blocks + 1)) {
-    int all = check_replicas(Rn, cg, conv, iters, cg, ubuf, it + 1, tol);
+    int all = check_replicas(Rn, cg, conv, iters, ubuf, it + 1, tol, -1);
     if (threadIdx.x == 0) {
       blocks[1] = 0;
       *itp = it + 1;
@@ -292,17 +346,22 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const dou
       if (stop) {
         if (!all) atomicOr(err, CT_ERR_CG_MAXITER);
         *active = 0;
-        *total += it + 1;
       }
       if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
     }
   }
 }
 
-// q = s + mu t per replica.
+// q = s + mu t per replica; count the solve's iterations and its history.
 __global__ void k_cg_final(int N, const int* __restrict__ rep, const double2* __restrict__ x,
-                           const double* __restrict__ cg, double* __restrict__ q) {
+                           const double* __restrict__ cg, double* __restrict__ q, const int* __restrict__ itp,
+                           long long* __restrict__ total, int* __restrict__ hist) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    *total += *itp;
+    int h = *hist;
+    *hist = h < 3 ? h + 1 : 3;
+  }
   if (i >= N) return;
   double mu = cg[(size_t)rep[i] * CG_STRIDE + CG_MU];
   double2 xi = x[i];
@@ -322,11 +381,12 @@ template <class R>
 void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, double tol) {
   k_cg_prep<<<1, 256, 0, st>>>(S.R, S.cg, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
   if (S.N == 0) return;
+  k_cg_extrap<<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.cx, S.cxh1, S.cxh2, S.cg_hist);
   int chunk;
   int grid = chunk_grid(S.N, 8, S.nsm * 8, chunk);
-  k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.cap_all, chunk, S.nbr, S.nall, (const R*)S.M, S.Dg, S.dinv,
-                                     S.type, S.rep, T, S.cx, S.cr, S.cz, (typename Vec2<R>::T*)S.czr,
-                                     S.cg, S.R, S.cg_conv, S.cg_iters, S.cg_blocks, S.cg_active, tol);
+  k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.cap_all, chunk, S.nbr, S.nall, (const R*)S.M, S.Dg, S.dinv, S.type,
+                                     S.rep, T, S.cx, S.cr, S.cz, (typename Vec2<R>::T*)S.czr, S.cg, S.R,
+                                     S.cg_conv, S.cg_iters, S.cg_blocks, S.cg_active, tol);
 }
 
 template <class R>
@@ -334,9 +394,9 @@ void launch_cg_mv(const DevState& S, cudaStream_t st) {
   if (S.N == 0) return;
   int chunk;
   int grid = chunk_grid(S.N, 8, S.nsm * 8, chunk);
-  k_cg_mv<R><<<grid, 256, 0, st>>>(S.N, S.cap_all, chunk, S.nbr, S.nall, (const R*)S.M, S.Dg, S.rep,
-                                   S.cg_conv, S.cg_it, (const typename Vec2<R>::T*)S.czr, S.cz, S.cr,
-                                   S.cw, S.cg, S.cg_active);
+  k_cg_mv<R><<<grid, 256, 0, st>>>(S.N, S.cap_all, chunk, S.nbr, S.nall, (const R*)S.M, S.Dg, S.rep, S.cg_conv,
+                                   S.cg_it, (const typename Vec2<R>::T*)S.czr, S.cz, S.cr, S.cw, S.cg, S.R,
+                                   S.cg_blocks, S.cg_active);
 }
 
 template <class R>
@@ -344,10 +404,9 @@ void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
   if (S.N == 0) return;
   int chunk2;
   int grid2 = chunk_grid(S.N, 256, S.nsm * 4, chunk2);
-  k_cg_up<R><<<grid2, 256, 0, st>>>(S.N, chunk2, S.rep, S.dinv, S.cg_conv, S.cg_iters, S.cg_it, S.cw, S.cx,
-                                    S.cr, S.cp, S.cs, S.cz, (typename Vec2<R>::T*)S.czr, S.cg, S.R, S.reps,
-                                    S.cg_blocks, S.cg_active, S.cg_total, S.err, cfg.tol, cfg.max_iter,
-                                    cfg.use_cond, cfg.cond);
+  k_cg_up<R><<<grid2, 256, 0, st>>>(S.N, chunk2, S.rep, S.dinv, S.cg_conv, S.cg_iters, S.cg_it, S.cw, S.cx, S.cr,
+                                    S.cp, S.cs, S.cz, (typename Vec2<R>::T*)S.czr, S.cg, S.R, S.cg_blocks,
+                                    S.cg_active, S.err, cfg.tol, cfg.max_iter, cfg.use_cond, cfg.cond);
 }
 
 template <class R>
@@ -358,8 +417,8 @@ void launch_cg_iter(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
 
 template <class R>
 void launch_cg_end(const DevState& S, cudaStream_t st) {
-  if (S.N == 0) return;
-  k_cg_final<<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.rep, S.cx, S.cg, S.q);
+  int n = S.N > 0 ? S.N : 1;
+  k_cg_final<<<(n + 255) / 256, 256, 0, st>>>(S.N, S.rep, S.cx, S.cg, S.q, S.cg_it, S.cg_total, S.cg_hist);
 }
 
 template void launch_cg_begin<float>(const DevState&, const TypeParams&, cudaStream_t, double);

@@ -18,12 +18,14 @@ enum RepSlots {
 enum CgSlots {
   CG_DOTS = 0,     // [2 buffers][4]: (r.z, w.z) for the s and t solves
   CG_UPD = 8,      // [3 buffers][5]: sum r_s^2, r_t^2, r_s r_t, x_s, x_t
-  CG_SCAL = 23,    // [2 buffers][4]: gamma_s, alpha_s, gamma_t, alpha_t of the last iteration
-  CG_MU = 31,      // final mu
-  CG_RES = 32,     // final rms residual
-  CG_Q = 33,       // requested total charge
-  CG_NAT = 34,     // atoms in the replica
-  CG_STRIDE = 36
+  CG_SCAL = 23,    // [2 buffers][4]: gamma_s, alpha_s, gamma_t, alpha_t of an iteration
+  CG_AB = 31,      // alpha_s, beta_s, alpha_t, beta_t of the running iteration
+  CG_MU = 35,      // final mu
+  CG_RES = 36,     // final rms residual
+  CG_Q = 37,       // requested total charge
+  CG_NAT = 38,     // atoms in the replica
+  CG_RES0 = 39,    // rms residual of the starting guess
+  CG_STRIDE = 40
 };
 
 struct DevState {
@@ -53,13 +55,15 @@ struct DevState {
   // CG vectors, (s, t) interleaved
   double2 *cx = nullptr, *cr = nullptr, *cp = nullptr, *cs = nullptr, *cz = nullptr, *cw = nullptr;
   void* czr = nullptr;          // Real2[N]: z in the matvec precision
+  double2 *cxh1 = nullptr, *cxh2 = nullptr;  // (s, t) of the previous two solves
+  int* cg_hist = nullptr;       // solutions held in cx, cxh1, cxh2 (0..3)
   // control
   int* flag_rebuild = nullptr;
   long long* rebuild_count = nullptr;
   int* maxcnt = nullptr;        // [2] max ncov, max nall at the last rebuild
   unsigned* err = nullptr;
   int* cg_it = nullptr;         // iteration counter of the running solve
-  int* cg_blocks = nullptr;     // last-block counters
+  int* cg_blocks = nullptr;     // last-block counters [3]
   int* cg_active = nullptr;     // 1 while the solve runs (host-loop mirror of the graph condition)
   long long* cg_total = nullptr;
   // sizes for launches

@@ -244,6 +244,14 @@ def stepped_slab_1m(seed: int = 3) -> Structure:
     return add_adatoms(s, n_ad, seed=seed)
 
 
+def stepped_slab_250k(seed: int = 3) -> Structure:
+    """A quarter-area version of the 1M-atom slab (48x24 cells x 56 bilayers,
+    same staircase and adatom density): about 251k atoms."""
+    s = sic_4h_slab(48, 24, 56, step="staircase")
+    n_ad = int(round(0.05 * s.meta["atoms_per_bilayer"]))
+    return add_adatoms(s, n_ad, seed=seed)
+
+
 def stepped_slab_small(nx: int = 12, ny: int = 6, n_bilayers: int = 8,
                        seed: int = 3) -> Structure:
     """A small stand-in with the same shape as the 1M-atom slab (staircase +
