@@ -99,8 +99,9 @@ typedef struct ctbop_params {
 typedef struct ctbop_options {
     int32_t precision;    /* CTBOP_PREC_FP64 or CTBOP_PREC_MIXED */
     int32_t cg_max_iter;  /* charge-solve iteration cap (default 200) */
-    double  cg_tol;       /* stop when the rms over a replica's atoms of H q + chi - mu is below
-                           cg_tol (eV/e); 0 = policy default (FP64 1e-10, MIXED 1e-5) */
+    double  cg_tol;       /* stop when max|r_s| + |mu| max|r_t|, a bound on max_i |H q + chi - mu|_i
+                           over a replica, is below cg_tol (eV/e); 0 = policy default
+                           (FP64 1e-9, MIXED 1e-5) */
     double  skin;         /* neighbour-list skin (A, default 0.3) */
     int32_t cap_cov;      /* covalent entries per atom; 0 = sized from the first configuration */
     int32_t cap_all;      /* all entries (charge cutoff) per atom; 0 = sized automatically */
@@ -115,7 +116,7 @@ typedef struct ctbop_stats {
     int32_t max_cov;          /* largest covalent entry count at the last rebuild */
     int64_t cg_iters_total;   /* summed over all solves */
     int64_t solves;           /* number of charge solves */
-    double  cg_residual_last; /* rms of H q + chi - mu after the last solve, replica 0 (eV/e) */
+    double  cg_residual_last; /* max-norm bound of H q + chi - mu after the last solve, replica 0 (eV/e) */
     int32_t max_all;          /* largest total entry count at the last rebuild */
     uint32_t error_bits;      /* device-side error bits seen (see ctbop_last_error) */
     double  mean_cov;         /* mean covalent entries (incl. skin) at the last rebuild */

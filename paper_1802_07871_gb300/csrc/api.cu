@@ -245,9 +245,14 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->atom_buf, &S.cw, (size_t)N));
   CK(dalloc(s->atom_buf, &S.cxh1, (size_t)N));
   CK(dalloc(s->atom_buf, &S.cxh2, (size_t)N));
-  unsigned char* zr = nullptr;
+  unsigned char *zr = nullptr, *xr = nullptr, *qr = nullptr;
   CK(dalloc(s->atom_buf, &zr, (size_t)N * 2 * rs));
+  CK(dalloc(s->atom_buf, &xr, (size_t)N * 2 * rs));
+  CK(dalloc(s->atom_buf, &qr, (size_t)N * rs));
   S.czr = zr;
+  S.cxr = xr;
+  S.qr = qr;
+  CK(cudaMemset(S.qr, 0, (size_t)N * rs));
   CK(dalloc(s->atom_buf, &S.ncov, (size_t)N));
   CK(dalloc(s->atom_buf, &S.nall, (size_t)N));
   CK(cudaMemset(S.v, 0, sizeof(double) * 3 * (size_t)N));
@@ -268,6 +273,7 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->rep_buf, &S.reps, (size_t)s->R));
   CK(dalloc(s->rep_buf, &S.rep_acc, (size_t)s->R * RA_STRIDE));
   CK(dalloc(s->rep_buf, &S.cg, (size_t)s->R * CG_STRIDE));
+  CK(dalloc(s->rep_buf, &S.cg_rmax, (size_t)s->R * 6));
   CK(dalloc(s->rep_buf, &S.cg_conv, (size_t)s->R));
   CK(dalloc(s->rep_buf, &S.cg_iters, (size_t)s->R));
   CK(dalloc(s->rep_buf, &S.scan_tmp, 1040));
@@ -298,6 +304,10 @@ static int alloc_atoms(ctbop_system* s) {
 
 static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   DevState& S = s->S;
+  // rows are read four entries at a time with 16/32-byte loads: keep every
+  // row start aligned (capacities multiples of 8 and 4)
+  cap_all = (std::max(cap_all, cap_cov) + 7) & ~7;
+  cap_cov = (cap_cov + 3) & ~3;
   if (s->alloc_cov == cap_cov && s->alloc_all == cap_all) return CTBOP_OK;
   destroy_graphs(s);
   s->list_buf.release();
@@ -325,7 +335,7 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
 // ------------------------------------------------------------- evaluation
 static double cg_tol(const ctbop_system* s) {
   if (s->o.cg_tol > 0) return s->o.cg_tol;
-  return s->mixed ? 1e-5 : 1e-10;
+  return s->mixed ? 1e-5 : 1e-9;
 }
 
 template <class Rr>
@@ -463,6 +473,8 @@ static int ensure_lists(ctbop_system* s) {
       cc = std::max(cc, S.cap_cov);
       ca = std::max(ca, S.cap_all);
     }
+    cc = (cc + 3) & ~3;
+    ca = (std::max(ca, cc) + 7) & ~7;
     bool same = (cc == S.cap_cov && ca == S.cap_all);
     s->caps_known = true;
     if (same && !over) break;
@@ -738,7 +750,12 @@ int ctbop_set_velocities(ctbop_system* s, const double* v, int mem) {
 int ctbop_set_charges(ctbop_system* s, const double* q, int mem) {
   if (!s) return CTBOP_ERR_INVALID_ARG;
   if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
-  return copy_in(s, s->S.q, q, sizeof(double) * s->S.N, mem);
+  int rc = copy_in(s, s->S.q, q, sizeof(double) * s->S.N, mem);
+  if (rc) return rc;
+  if (s->mixed) launch_copy_q<float>(s->S, s->stream);
+  else launch_copy_q<double>(s->S, s->stream);
+  CK(cudaGetLastError());
+  return CTBOP_OK;
 }
 
 int ctbop_set_frozen(ctbop_system* s, const uint8_t* frozen, int mem) {
@@ -924,7 +941,7 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   CK(cudaMemcpy(&it, S.cg_it, sizeof(it), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost));
   double res = 0;
-  CK(cudaMemcpy(&res, S.cg + CG_RES, sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&res, S.cg + CG_RESMAX, sizeof(double), cudaMemcpyDeviceToHost));
   st->error_bits = bits;
   st->rebuilds = rb;
   st->cg_iters_total = tot;

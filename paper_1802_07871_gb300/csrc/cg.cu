@@ -12,13 +12,21 @@
 // products, residual sums and the vectors are FP64; the matrix entries and
 // the gathered z_j are in the working precision.
 //
+// FP64 on this GPU issues at a small fraction of the FP32 rate and a warp
+// instruction costs the same with one lane active as with 32, so the matrix
+// passes (one warp per atom) do their FP64 epilogues lane-parallel: a warp
+// walks 32 atoms, lane k keeps atom k's FP32 row sums, then every lane
+// finishes its own atom in FP64 at once.
+//
 // Starting guess: the previous solutions extrapolated in time (quadratic
 // from three, linear from two, the last one alone otherwise).
 //
-// Convergence (per replica): rms over the replica's atoms of r_s + mu r_t
-// (= mu 1 - H q - chi, the stationarity residual) below tol. The last block
-// of each update launch decides, marks converged replicas, and ends the loop
-// through the CUDA-graph condition (or a device flag the host polls).
+// Convergence (per replica): max|r_s| + |mu| max|r_t| below tol, a bound on
+// the max-norm of the stationarity residual mu 1 - H q - chi (an rms test
+// lets a few weakly coupled atoms, such as adatoms, keep large errors). The
+// last block of each update launch decides, marks converged replicas, and
+// ends the loop through the CUDA-graph condition (or a device flag the host
+// polls).
 #include "internal.cuh"
 #include "kernels.h"
 
@@ -40,25 +48,30 @@ __device__ inline bool last_block(int* counter) {
   return am_last;
 }
 
-// Convergence test for every unconverged replica from the sums at upd_off.
-__device__ inline int check_replicas(int R, double* cg, int* conv, int* iters, int upd_off, int it_done,
-                                     double tol, int res_slot) {
+// Convergence test for every unconverged replica from the sums at upd_off
+// and the residual maxima of buffer mbuf.
+__device__ inline int check_replicas(int R, double* cg, const float* rmax, int* conv, int* iters, int upd_off,
+                                     int mbuf, int it_done, double tol, int first) {
   int all = 1;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     if (conv[r]) continue;
     double* c = cg + (size_t)r * CG_STRIDE;
     const double* u5 = c + upd_off;
     double rss = ldcg(u5 + 0), rtt = ldcg(u5 + 1), rst = ldcg(u5 + 2), xs = ldcg(u5 + 3), xt = ldcg(u5 + 4);
+    float ms = __ldcg(rmax + (size_t)r * 6 + mbuf * 2), mt = __ldcg(rmax + (size_t)r * 6 + mbuf * 2 + 1);
     double nat = c[CG_NAT];
     // mu is undefined before t has any weight (cold start: x = 0)
     double mu = (c[CG_Q] - xs) / xt;
     bool mu_ok = (xt != 0.0) && isfinite(mu);
     double res2 = (rss + 2.0 * mu * rst + mu * mu * rtt) / (nat > 0 ? nat : 1.0);
     double rms = (mu_ok && isfinite(res2)) ? sqrt(res2 > 0.0 ? res2 : 0.0) : INFINITY;
+    double bound = mu_ok ? (double)ms + fabs(mu) * (double)mt : INFINITY;
+    if (!isfinite(bound)) bound = INFINITY;
     c[CG_MU] = mu_ok ? mu : 0.0;
     c[CG_RES] = rms;
-    if (res_slot >= 0) c[res_slot] = rms;
-    if (nat == 0 || rms <= tol) {
+    c[CG_RESMAX] = bound;
+    if (first) c[CG_RES0] = bound;
+    if (nat == 0 || bound <= tol) {
       conv[r] = 1;
       iters[r] = it_done;
     } else {
@@ -68,12 +81,44 @@ __device__ inline int check_replicas(int R, double* cg, int* conv, int* iters, i
   return __syncthreads_and(all);
 }
 
+// Per-lane running maxima of |r_s|, |r_t| for one replica, merged per warp
+// and flushed with atomics (float bit patterns order like non-negative values).
+struct LaneMax {
+  int rep = -1;
+  float s = 0.f, t = 0.f;
+  __device__ inline void flush(float* base) {
+    if (rep >= 0) {
+      atomic_max_nonneg(base + (size_t)rep * 6, s);
+      atomic_max_nonneg(base + (size_t)rep * 6 + 1, t);
+    }
+    s = t = 0.f;
+  }
+  __device__ inline void add(int r, float as, float at, float* base) {
+    if (r != rep) { flush(base); rep = r; }
+    s = fmaxf(s, as);
+    t = fmaxf(t, at);
+  }
+  __device__ inline void finish(float* base) {
+    int r0 = __shfl_sync(CT_FULL, rep, 0);
+    if (__all_sync(CT_FULL, rep == r0)) {
+      for (int o = 16; o > 0; o >>= 1) {
+        s = fmaxf(s, __shfl_xor_sync(CT_FULL, s, o));
+        t = fmaxf(t, __shfl_xor_sync(CT_FULL, t, o));
+      }
+      if ((threadIdx.x & 31) != 0) rep = -1;
+    }
+    flush(base);
+  }
+};
+
 // --------------------------------------------------------------- prepare
-__global__ void k_cg_prep(int R, double* __restrict__ cg, int* __restrict__ conv, int* __restrict__ iters,
-                          int* __restrict__ it, int* __restrict__ blocks, int* __restrict__ active) {
+__global__ void k_cg_prep(int R, double* __restrict__ cg, float* __restrict__ rmax, int* __restrict__ conv,
+                          int* __restrict__ iters, int* __restrict__ it, int* __restrict__ blocks,
+                          int* __restrict__ active) {
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     double* c = cg + (size_t)r * CG_STRIDE;
     for (int k = 0; k < CG_MU; ++k) c[k] = 0.0;
+    for (int k = 0; k < 6; ++k) rmax[(size_t)r * 6 + k] = 0.f;
     conv[r] = 0;
     iters[r] = 0;
   }
@@ -86,10 +131,11 @@ __global__ void k_cg_prep(int R, double* __restrict__ cg, int* __restrict__ conv
   }
 }
 
-// Starting guess extrapolated from the stored solutions; shifts the
-// history (h2 <- h1, h1 <- the last solution).
+// Starting guess extrapolated from the stored solutions and its copy in the
+// matvec precision; shifts the history (h2 <- h1, h1 <- the last solution).
+template <class R>
 __global__ void k_cg_extrap(int N, double2* __restrict__ x, double2* __restrict__ h1, double2* __restrict__ h2,
-                            const int* __restrict__ hist) {
+                            typename Vec2<R>::T* __restrict__ xr, const int* __restrict__ hist) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   int nh = *hist;
@@ -106,39 +152,80 @@ __global__ void k_cg_extrap(int N, double2* __restrict__ x, double2* __restrict_
   h2[i] = a;
   h1[i] = xo;
   x[i] = x0;
+  typename Vec2<R>::T v;
+  v.x = (R)x0.x;
+  v.y = (R)x0.y;
+  xr[i] = v;
 }
 
-// r = b - H x0, z = D^-1 r with b = (-chi, 1); sums for the initial test
-// (kept in update buffer 2).
+// Row sums sum_e M_e v_j(e) of atoms b0 .. b0+nb-1 (one warp, lanes over
+// entries, four consecutive entries per lane per step through 16-byte (FP32)
+// or 32-byte (FP64) loads, so four gathers are in flight per lane); lane k
+// returns atom b0+k's sums. Atoms of converged replicas are left at zero.
+// Rows are padded to a multiple of 8 entries; padding is masked.
 template <class R>
-__global__ void k_cg_init(int N, int cap_all, int chunk, const int* __restrict__ nbr,
-                          const int* __restrict__ nall, const R* __restrict__ M, const double* __restrict__ Dg,
-                          const double* __restrict__ dinv, const int* __restrict__ type, const int* __restrict__ rep,
-                          TypeParams T, const double2* __restrict__ x, double2* __restrict__ r,
-                          double2* __restrict__ z, typename Vec2<R>::T* __restrict__ zr, double* __restrict__ cg,
-                          int Rn, int* __restrict__ conv, int* __restrict__ iters, int* __restrict__ blocks,
-                          int* __restrict__ active, double tol) {
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
-  const int ub = CG_UPD + 2 * 5;
-  RepAcc<5> acc;
-  acc.init();
-  for (int i = a0 + warp; i < a1; i += nw) {
+__device__ inline void batch_rowsums(int b0, int nb, int cap_all, const int* __restrict__ nbr,
+                                     const int* __restrict__ nall, const R* __restrict__ M,
+                                     const typename Vec2<R>::T* __restrict__ v, const int* __restrict__ rep,
+                                     const int* __restrict__ conv, R& ms, R& mt) {
+  using V2 = typename Vec2<R>::T;
+  using V4 = typename Vec4<R>::T;
+  int lane = threadIdx.x & 31;
+  ms = R(0);
+  mt = R(0);
+  for (int k = 0; k < nb; ++k) {
+    int i = b0 + k;
+    if (conv && conv[rep[i]]) continue;
     int na = min(nall[i], cap_all);
+    const int4* nr = reinterpret_cast<const int4*>(nbr + (size_t)i * cap_all);
+    const V4* mr = reinterpret_cast<const V4*>(M + (size_t)i * cap_all);
+    int n4 = (na + 3) >> 2;
     R hs = R(0), ht = R(0);
-    for (int e = lane; e < na; e += 32) {
-      size_t idx = (size_t)i * cap_all + e;
-      double2 xj = x[nbr[idx]];
-      R m = M[idx];
-      hs += m * (R)xj.x;
-      ht += m * (R)xj.y;
+    for (int q = lane; q < n4; q += 32) {
+      int4 jj = nr[q];
+      V4 mm = mr[q];
+      int e = 4 * q;
+      bool ok1 = e + 1 < na, ok2 = e + 2 < na, ok3 = e + 3 < na;
+      V2 z0 = v[jj.x];
+      V2 z1 = v[ok1 ? jj.y : jj.x];
+      V2 z2 = v[ok2 ? jj.z : jj.x];
+      V2 z3 = v[ok3 ? jj.w : jj.x];
+      R m1 = ok1 ? mm.y : R(0), m2 = ok2 ? mm.z : R(0), m3 = ok3 ? mm.w : R(0);
+      hs += mm.x * z0.x + m1 * z1.x + m2 * z2.x + m3 * z3.x;
+      ht += mm.x * z0.y + m1 * z1.y + m2 * z2.y + m3 * z3.y;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       hs += __shfl_xor_sync(CT_FULL, hs, o);
       ht += __shfl_xor_sync(CT_FULL, ht, o);
     }
-    if (lane == 0) {
+    if (lane == k) {
+      ms = hs;
+      mt = ht;
+    }
+  }
+}
+
+// r = b - H x0, z = D^-1 r with b = (-chi, 1); sums and maxima for the
+// initial test (kept in update buffer 2).
+template <class R>
+__global__ void k_cg_init(int N, int cap_all, int bpw, const int* __restrict__ nbr,
+                          const int* __restrict__ nall, const R* __restrict__ M, const double* __restrict__ Dg,
+                          const double* __restrict__ dinv, const int* __restrict__ type, const int* __restrict__ rep,
+                          TypeParams T, const double2* __restrict__ x, const typename Vec2<R>::T* __restrict__ xr,
+                          double2* __restrict__ r, double2* __restrict__ z, typename Vec2<R>::T* __restrict__ zr,
+                          double* __restrict__ cg, float* __restrict__ rmax, int Rn, int* __restrict__ conv,
+                          int* __restrict__ iters, int* __restrict__ blocks, int* __restrict__ active, double tol) {
+  int lane = threadIdx.x & 31;
+  const int ub = CG_UPD + 2 * 5;
+  RepAcc<5> acc;
+  acc.init();
+  LaneMax lm;
+  BATCH_LOOP_BEGIN(N, bpw)
+    R hs, ht;
+    batch_rowsums<R>(b0, nb, cap_all, nbr, nall, M, xr, rep, nullptr, hs, ht);
+    if (lane < nb) {
+      int i = b0 + lane;
       double2 xi = x[i];
       double D = Dg[i];
       double2 ri;
@@ -154,17 +241,20 @@ __global__ void k_cg_init(int N, int cap_all, int chunk, const int* __restrict__
       zz.x = (R)zi.x;
       zz.y = (R)zi.y;
       zr[i] = zz;
-      acc.to(rep[i], cg + ub, CG_STRIDE);
+      int rid = rep[i];
+      acc.to(rid, cg + ub, CG_STRIDE);
       acc.v[0] += ri.x * ri.x;
       acc.v[1] += ri.y * ri.y;
       acc.v[2] += ri.x * ri.y;
       acc.v[3] += xi.x;
       acc.v[4] += xi.y;
+      lm.add(rid, fabsf((float)ri.x), fabsf((float)ri.y), rmax + 2 * 2);
     }
-  }
-  block_flush<5>(acc, cg + ub, CG_STRIDE);
+  BATCH_LOOP_END
+  lane_flush<5>(acc, cg + ub, CG_STRIDE);
+  lm.finish(rmax + 2 * 2);
   if (last_block(blocks)) {
-    int all = check_replicas(Rn, cg, conv, iters, ub, 0, tol, CG_RES0);
+    int all = check_replicas(Rn, cg, rmax, conv, iters, ub, 2, 0, tol, 1);
     if (threadIdx.x == 0) {
       blocks[0] = 0;
       if (all) *active = 0;
@@ -175,62 +265,40 @@ __global__ void k_cg_init(int N, int cap_all, int chunk, const int* __restrict__
 // w = H z and the dots (r.z, w.z) for both solves; the last block turns the
 // dots into the step lengths alpha, beta of this iteration.
 template <class R>
-__global__ void k_cg_mv(int N, int cap_all, int chunk, const int* __restrict__ nbr, const int* __restrict__ nall,
+__global__ void k_cg_mv(int N, int cap_all, int bpw, const int* __restrict__ nbr, const int* __restrict__ nall,
                         const R* __restrict__ M, const double* __restrict__ Dg, const int* __restrict__ rep,
                         const int* __restrict__ conv, const int* __restrict__ itp,
                         const typename Vec2<R>::T* __restrict__ zr, const double2* __restrict__ z,
                         const double2* __restrict__ r, double2* __restrict__ w, double* __restrict__ cg, int Rn,
                         int* __restrict__ blocks, const int* __restrict__ active) {
   if (*active == 0) return;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
+  int lane = threadIdx.x & 31;
   int it = *itp;
   int buf = CG_DOTS + (it & 1) * 4;
   RepAcc<4> acc;
   acc.init();
-  for (int i = a0 + warp; i < a1; i += nw) {
-    int ri_id = rep[i];
-    if (conv[ri_id]) continue;
-    int na = min(nall[i], cap_all);
-    const int* nrow = nbr + (size_t)i * cap_all;
-    const R* mrow = M + (size_t)i * cap_all;
-    R hs = R(0), ht = R(0);
-    int e = lane;
-    // two entries in flight per lane
-    for (; e + 32 < na; e += 64) {
-      int j0 = __ldg(nrow + e), j1 = __ldg(nrow + e + 32);
-      R m0 = __ldg(mrow + e), m1 = __ldg(mrow + e + 32);
-      typename Vec2<R>::T z0 = zr[j0], z1 = zr[j1];
-      hs += m0 * z0.x + m1 * z1.x;
-      ht += m0 * z0.y + m1 * z1.y;
+  BATCH_LOOP_BEGIN(N, bpw)
+    R hs, ht;
+    batch_rowsums<R>(b0, nb, cap_all, nbr, nall, M, zr, rep, conv, hs, ht);
+    if (lane < nb) {
+      int i = b0 + lane;
+      int rid = rep[i];
+      if (!conv[rid]) {
+        double2 zi = z[i], rri = r[i];
+        double D = Dg[i];
+        double2 wi;
+        wi.x = D * zi.x + (double)hs;
+        wi.y = D * zi.y + (double)ht;
+        w[i] = wi;
+        acc.to(rid, cg + buf, CG_STRIDE);
+        acc.v[0] += rri.x * zi.x;
+        acc.v[1] += wi.x * zi.x;
+        acc.v[2] += rri.y * zi.y;
+        acc.v[3] += wi.y * zi.y;
+      }
     }
-    if (e < na) {
-      int j0 = __ldg(nrow + e);
-      R m0 = __ldg(mrow + e);
-      typename Vec2<R>::T z0 = zr[j0];
-      hs += m0 * z0.x;
-      ht += m0 * z0.y;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      hs += __shfl_xor_sync(CT_FULL, hs, o);
-      ht += __shfl_xor_sync(CT_FULL, ht, o);
-    }
-    if (lane == 0) {
-      double2 zi = z[i], rri = r[i];
-      double D = Dg[i];
-      double2 wi;
-      wi.x = D * zi.x + (double)hs;
-      wi.y = D * zi.y + (double)ht;
-      w[i] = wi;
-      acc.to(ri_id, cg + buf, CG_STRIDE);
-      acc.v[0] += rri.x * zi.x;
-      acc.v[1] += wi.x * zi.x;
-      acc.v[2] += rri.y * zi.y;
-      acc.v[3] += wi.y * zi.y;
-    }
-  }
-  block_flush<4>(acc, cg + buf, CG_STRIDE);
+  BATCH_LOOP_END
+  lane_flush<4>(acc, cg + buf, CG_STRIDE);
   if (last_block(blocks + 2)) {
     int sprev = CG_SCAL + ((it + 1) & 1) * 4;
     int scur = CG_SCAL + (it & 1) * 4;
@@ -259,14 +327,14 @@ __global__ void k_cg_mv(int N, int cap_all, int chunk, const int* __restrict__ n
   }
 }
 
-// Element-wise update and the sums for the convergence test.
+// Element-wise update, the sums and maxima for the convergence test.
 template <class R>
 __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const double* __restrict__ dinv,
                         int* __restrict__ conv, int* __restrict__ iters, int* __restrict__ itp,
                         const double2* __restrict__ w, double2* __restrict__ x, double2* __restrict__ r,
                         double2* __restrict__ p, double2* __restrict__ s, double2* __restrict__ z,
-                        typename Vec2<R>::T* __restrict__ zr, double* __restrict__ cg, int Rn,
-                        int* __restrict__ blocks, int* __restrict__ active, unsigned* __restrict__ err,
+                        typename Vec2<R>::T* __restrict__ zr, double* __restrict__ cg, float* __restrict__ rmax,
+                        int Rn, int* __restrict__ blocks, int* __restrict__ active, unsigned* __restrict__ err,
                         double tol, int max_iter, int use_cond, cudaGraphConditionalHandle cond) {
   if (*active == 0) {
     // nothing left to do (converged at the start): end the loop
@@ -274,71 +342,54 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const dou
     return;
   }
   int it = *itp;
-  int ubuf = CG_UPD + (it % 3) * 5;
+  int mb = it % 3;
+  int ubuf = CG_UPD + mb * 5;
   // zero the buffers the next iteration accumulates into
   if (blockIdx.x == 0) {
-    int dn = CG_DOTS + ((it + 1) & 1) * 4, un = CG_UPD + ((it + 1) % 3) * 5;
-    for (int q = threadIdx.x; q < Rn * 9; q += blockDim.x) {
-      int rr = q / 9, k = q % 9;
+    int dn = CG_DOTS + ((it + 1) & 1) * 4, un = CG_UPD + ((it + 1) % 3) * 5, mn = (it + 1) % 3;
+    for (int q = threadIdx.x; q < Rn * 11; q += blockDim.x) {
+      int rr = q / 11, k = q % 11;
       double* c = cg + (size_t)rr * CG_STRIDE;
       if (k < 4) c[dn + k] = 0.0;
-      else c[un + k - 4] = 0.0;
+      else if (k < 9) c[un + k - 4] = 0.0;
+      else rmax[(size_t)rr * 6 + mn * 2 + (k - 9)] = 0.f;
     }
   }
   RepAcc<5> acc;
   acc.init();
+  LaneMax lm;
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
-  int lane = threadIdx.x & 31;
   int crid = -1;
   double as = 0, bs = 0, at = 0, bt = 0;
-  for (int base = a0; base < a1; base += blockDim.x) {
-    int i = base + threadIdx.x;
-    int rid = -1;
-    double v5[5] = {0, 0, 0, 0, 0};
-    if (i < a1) {
-      rid = rep[i];
-      if (!conv[rid]) {
-        if (rid != crid) {
-          const double* c = cg + (size_t)rid * CG_STRIDE;
-          as = ldcg(c + CG_AB + 0); bs = ldcg(c + CG_AB + 1);
-          at = ldcg(c + CG_AB + 2); bt = ldcg(c + CG_AB + 3);
-          crid = rid;
-        }
-        double2 zi = z[i], wi = w[i], pi = p[i], si = s[i], xi = x[i], ri = r[i];
-        pi.x = zi.x + bs * pi.x; pi.y = zi.y + bt * pi.y;
-        si.x = wi.x + bs * si.x; si.y = wi.y + bt * si.y;
-        xi.x += as * pi.x; xi.y += at * pi.y;
-        ri.x -= as * si.x; ri.y -= at * si.y;
-        double di = dinv[i];
-        zi.x = ri.x * di; zi.y = ri.y * di;
-        p[i] = pi; s[i] = si; x[i] = xi; r[i] = ri; z[i] = zi;
-        typename Vec2<R>::T zz;
-        zz.x = (R)zi.x; zz.y = (R)zi.y;
-        zr[i] = zz;
-        v5[0] = ri.x * ri.x; v5[1] = ri.y * ri.y; v5[2] = ri.x * ri.y; v5[3] = xi.x; v5[4] = xi.y;
-      } else {
-        rid = -1;
-      }
+  for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
+    int rid = rep[i];
+    if (conv[rid]) continue;
+    if (rid != crid) {
+      const double* c = cg + (size_t)rid * CG_STRIDE;
+      as = ldcg(c + CG_AB + 0); bs = ldcg(c + CG_AB + 1);
+      at = ldcg(c + CG_AB + 2); bt = ldcg(c + CG_AB + 3);
+      crid = rid;
     }
-    // merge lanes of the same replica
-    int r0 = __shfl_sync(CT_FULL, rid, 0);
-    bool same = __all_sync(CT_FULL, rid == r0);
-    if (same) {
-#pragma unroll
-      for (int k = 0; k < 5; ++k) v5[k] = warp_sum(v5[k]);
-      if (lane == 0 && r0 >= 0) {
-        acc.to(r0, cg + ubuf, CG_STRIDE);
-#pragma unroll
-        for (int k = 0; k < 5; ++k) acc.v[k] += v5[k];
-      }
-    } else if (rid >= 0) {
-#pragma unroll
-      for (int k = 0; k < 5; ++k) atomicAdd(cg + (size_t)rid * CG_STRIDE + ubuf + k, v5[k]);
-    }
+    double2 zi = z[i], wi = w[i], pi = p[i], si = s[i], xi = x[i], ri = r[i];
+    pi.x = zi.x + bs * pi.x; pi.y = zi.y + bt * pi.y;
+    si.x = wi.x + bs * si.x; si.y = wi.y + bt * si.y;
+    xi.x += as * pi.x; xi.y += at * pi.y;
+    ri.x -= as * si.x; ri.y -= at * si.y;
+    double di = dinv[i];
+    zi.x = ri.x * di; zi.y = ri.y * di;
+    p[i] = pi; s[i] = si; x[i] = xi; r[i] = ri; z[i] = zi;
+    typename Vec2<R>::T zz;
+    zz.x = (R)zi.x; zz.y = (R)zi.y;
+    zr[i] = zz;
+    acc.to(rid, cg + ubuf, CG_STRIDE);
+    acc.v[0] += ri.x * ri.x; acc.v[1] += ri.y * ri.y; acc.v[2] += ri.x * ri.y;
+    acc.v[3] += xi.x; acc.v[4] += xi.y;
+    lm.add(rid, fabsf((float)ri.x), fabsf((float)ri.y), rmax + mb * 2);
   }
-  block_flush<5>(acc, cg + ubuf, CG_STRIDE);
+  lane_flush<5>(acc, cg + ubuf, CG_STRIDE);
+  lm.finish(rmax + mb * 2);
   if (last_block(blocks + 1)) {
-    int all = check_replicas(Rn, cg, conv, iters, ubuf, it + 1, tol, -1);
+    int all = check_replicas(Rn, cg, rmax, conv, iters, ubuf, mb, it + 1, tol, 0);
     if (threadIdx.x == 0) {
       blocks[1] = 0;
       *itp = it + 1;
@@ -352,10 +403,12 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const dou
   }
 }
 
-// q = s + mu t per replica; count the solve's iterations and its history.
+// q = s + mu t per replica (and its copy in the working precision); count
+// the solve's iterations and its history.
+template <class R>
 __global__ void k_cg_final(int N, const int* __restrict__ rep, const double2* __restrict__ x,
-                           const double* __restrict__ cg, double* __restrict__ q, const int* __restrict__ itp,
-                           long long* __restrict__ total, int* __restrict__ hist) {
+                           const double* __restrict__ cg, double* __restrict__ q, R* __restrict__ qr,
+                           const int* __restrict__ itp, long long* __restrict__ total, int* __restrict__ hist) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     *total += *itp;
@@ -365,7 +418,16 @@ __global__ void k_cg_final(int N, const int* __restrict__ rep, const double2* __
   if (i >= N) return;
   double mu = cg[(size_t)rep[i] * CG_STRIDE + CG_MU];
   double2 xi = x[i];
-  q[i] = xi.x + mu * xi.y;
+  double qi = xi.x + mu * xi.y;
+  q[i] = qi;
+  qr[i] = (R)qi;
+}
+
+// Working-precision copy of charges set from outside the solve.
+template <class R>
+__global__ void k_copy_q(int N, const double* __restrict__ q, R* __restrict__ qr) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) qr[i] = (R)q[i];
 }
 
 // --------------------------------------------------------------- launchers
@@ -379,22 +441,24 @@ static inline int chunk_grid(int N, int per_block_min, int gmax, int& chunk) {
 
 template <class R>
 void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, double tol) {
-  k_cg_prep<<<1, 256, 0, st>>>(S.R, S.cg, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
+  k_cg_prep<<<1, 256, 0, st>>>(S.R, S.cg, S.cg_rmax, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
   if (S.N == 0) return;
-  k_cg_extrap<<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.cx, S.cxh1, S.cxh2, S.cg_hist);
-  int chunk;
-  int grid = chunk_grid(S.N, 8, S.nsm * 8, chunk);
-  k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.cap_all, chunk, S.nbr, S.nall, (const R*)S.M, S.Dg, S.dinv, S.type,
-                                     S.rep, T, S.cx, S.cr, S.cz, (typename Vec2<R>::T*)S.czr, S.cg, S.R,
-                                     S.cg_conv, S.cg_iters, S.cg_blocks, S.cg_active, tol);
+  k_cg_extrap<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.cx, S.cxh1, S.cxh2, (typename Vec2<R>::T*)S.cxr,
+                                                    S.cg_hist);
+  int bpw, threads;
+  int grid = batch_dims(S.N, S.nsm, (const void*)k_cg_init<R>, bpw, threads);
+  k_cg_init<R><<<grid, threads, 0, st>>>(S.N, S.cap_all, bpw, S.nbr, S.nall, (const R*)S.M, S.Dg, S.dinv, S.type,
+                                     S.rep, T, S.cx, (const typename Vec2<R>::T*)S.cxr, S.cr, S.cz,
+                                     (typename Vec2<R>::T*)S.czr, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
+                                     S.cg_blocks, S.cg_active, tol);
 }
 
 template <class R>
 void launch_cg_mv(const DevState& S, cudaStream_t st) {
   if (S.N == 0) return;
-  int chunk;
-  int grid = chunk_grid(S.N, 8, S.nsm * 8, chunk);
-  k_cg_mv<R><<<grid, 256, 0, st>>>(S.N, S.cap_all, chunk, S.nbr, S.nall, (const R*)S.M, S.Dg, S.rep, S.cg_conv,
+  int bpw, threads;
+  int grid = batch_dims(S.N, S.nsm, (const void*)k_cg_mv<R>, bpw, threads);
+  k_cg_mv<R><<<grid, threads, 0, st>>>(S.N, S.cap_all, bpw, S.nbr, S.nall, (const R*)S.M, S.Dg, S.rep, S.cg_conv,
                                    S.cg_it, (const typename Vec2<R>::T*)S.czr, S.cz, S.cr, S.cw, S.cg, S.R,
                                    S.cg_blocks, S.cg_active);
 }
@@ -405,8 +469,8 @@ void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
   int chunk2;
   int grid2 = chunk_grid(S.N, 256, S.nsm * 4, chunk2);
   k_cg_up<R><<<grid2, 256, 0, st>>>(S.N, chunk2, S.rep, S.dinv, S.cg_conv, S.cg_iters, S.cg_it, S.cw, S.cx, S.cr,
-                                    S.cp, S.cs, S.cz, (typename Vec2<R>::T*)S.czr, S.cg, S.R, S.cg_blocks,
-                                    S.cg_active, S.err, cfg.tol, cfg.max_iter, cfg.use_cond, cfg.cond);
+                                    S.cp, S.cs, S.cz, (typename Vec2<R>::T*)S.czr, S.cg, S.cg_rmax, S.R,
+                                    S.cg_blocks, S.cg_active, S.err, cfg.tol, cfg.max_iter, cfg.use_cond, cfg.cond);
 }
 
 template <class R>
@@ -418,7 +482,14 @@ void launch_cg_iter(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
 template <class R>
 void launch_cg_end(const DevState& S, cudaStream_t st) {
   int n = S.N > 0 ? S.N : 1;
-  k_cg_final<<<(n + 255) / 256, 256, 0, st>>>(S.N, S.rep, S.cx, S.cg, S.q, S.cg_it, S.cg_total, S.cg_hist);
+  k_cg_final<R><<<(n + 255) / 256, 256, 0, st>>>(S.N, S.rep, S.cx, S.cg, S.q, (R*)S.qr, S.cg_it, S.cg_total,
+                                                 S.cg_hist);
+}
+
+template <class R>
+void launch_copy_q(const DevState& S, cudaStream_t st) {
+  if (S.N == 0) return;
+  k_copy_q<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.q, (R*)S.qr);
 }
 
 template void launch_cg_begin<float>(const DevState&, const TypeParams&, cudaStream_t, double);
@@ -431,5 +502,7 @@ template void launch_cg_iter<float>(const DevState&, const SolveCfg&, cudaStream
 template void launch_cg_iter<double>(const DevState&, const SolveCfg&, cudaStream_t);
 template void launch_cg_end<float>(const DevState&, cudaStream_t);
 template void launch_cg_end<double>(const DevState&, cudaStream_t);
+template void launch_copy_q<float>(const DevState&, cudaStream_t);
+template void launch_copy_q<double>(const DevState&, cudaStream_t);
 
 }  // namespace ct

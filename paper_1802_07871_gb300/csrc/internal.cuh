@@ -139,6 +139,22 @@ template <class R> struct CompSum {
   __device__ inline double value() const { return (double)s + (double)c; }
 };
 
+// Warps take atoms in batches of 32; warp gw (global) handles the batch range
+// [gw * bpw, (gw + 1) * bpw). Inside the loop b0 is the first atom of the
+// batch and nb its size.
+#define BATCH_LOOP_BEGIN(N_, bpw_)                                          \
+  {                                                                         \
+    int gw_ = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);         \
+    int nbatch_ = ((N_) + 31) >> 5;                                         \
+    int bb1_ = min(nbatch_, (gw_ + 1) * (bpw_));                           \
+    for (int bb_ = gw_ * (bpw_); bb_ < bb1_; ++bb_) {                      \
+      int b0 = bb_ * 32;                                                    \
+      int nb = min(32, (N_) - b0);
+
+#define BATCH_LOOP_END \
+    }                  \
+  }
+
 // ---------------------------------------------------------------- reductions
 // Accumulate NV doubles per replica. Each warp keeps a running partial for
 // the replica it is on and flushes with atomics when the replica changes; the
@@ -205,6 +221,12 @@ __device__ inline void block_flush(RepAcc<NV>& acc, double* out, int stride) {
   __syncthreads();
 }
 
+// End-of-kernel flush of per-lane replica partials: lanes of a warp that
+// share a replica are summed with shuffles, the warps of a block merged in
+// shared memory, then one atomic per value and replica.
+template <int NV>
+__device__ inline void lane_flush(RepAcc<NV>& a, double* out, int stride);
+
 __device__ inline double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(CT_FULL, v, o);
@@ -219,6 +241,31 @@ __device__ inline double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(CT_FULL, v, o));
   return v;
+}
+
+template <int NV>
+__device__ inline void lane_flush(RepAcc<NV>& a, double* out, int stride) {
+  int lane = threadIdx.x & 31;
+  int r0 = __shfl_sync(CT_FULL, a.rep, 0);
+  bool same = __all_sync(CT_FULL, a.rep == r0);
+  RepAcc<NV> w;
+  w.init();
+  if (same) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = warp_sum(a.v[k]);
+      if (lane == 0) w.v[k] = t;
+    }
+    if (lane == 0) w.rep = r0;
+  } else {
+    a.flush(out, stride);
+  }
+  block_flush<NV>(w, out, stride);
+}
+
+// atomic max for non-negative floats (bit patterns order like the values)
+__device__ inline void atomic_max_nonneg(float* addr, float v) {
+  atomicMax(reinterpret_cast<unsigned*>(addr), __float_as_uint(v));
 }
 
 // atomic max for non-negative doubles (bit patterns order like the values)

@@ -9,8 +9,8 @@ namespace ct {
 // Per-replica double accumulators, one row of RA_STRIDE per replica.
 enum RepSlots {
   RA_E = 0,        // potential energy
-  RA_W = 1,        // virial, 9 components
-  RA_KE = 10,      // kinetic energy
+  RA_KE = 1,       // kinetic energy
+  RA_W = 2,        // virial, 9 components
   RA_STRIDE = 12
 };
 
@@ -24,8 +24,9 @@ enum CgSlots {
   CG_RES = 36,     // final rms residual
   CG_Q = 37,       // requested total charge
   CG_NAT = 38,     // atoms in the replica
-  CG_RES0 = 39,    // rms residual of the starting guess
-  CG_STRIDE = 40
+  CG_RES0 = 39,    // max-norm bound of the starting guess's residual
+  CG_RESMAX = 40,  // final max-norm bound max|r_s| + |mu| max|r_t|
+  CG_STRIDE = 42
 };
 
 struct DevState {
@@ -55,6 +56,9 @@ struct DevState {
   // CG vectors, (s, t) interleaved
   double2 *cx = nullptr, *cr = nullptr, *cp = nullptr, *cs = nullptr, *cz = nullptr, *cw = nullptr;
   void* czr = nullptr;          // Real2[N]: z in the matvec precision
+  void* cxr = nullptr;          // Real2[N]: starting guess in the matvec precision
+  float* cg_rmax = nullptr;     // [R][3 buffers][2]: max |r_s|, max |r_t|
+  void* qr = nullptr;           // Real[N]: charges in the working precision
   double2 *cxh1 = nullptr, *cxh2 = nullptr;  // (s, t) of the previous two solves
   int* cg_hist = nullptr;       // solutions held in cx, cxh1, cxh2 (0..3)
   // control
@@ -96,5 +100,8 @@ template <class R> void launch_kick_drift(const DevState& S, const TypeParams& T
                                           cudaStream_t st);
 void launch_zero_acc(const DevState& S, cudaStream_t st);
 template <class R> cudaError_t setup_pot(int cap_cov);
+template <class R> void launch_copy_q(const DevState& S, cudaStream_t st);
+// launch shape for kernels whose warps take atoms in batches of 32
+int batch_dims(int N, int nsm, const void* kernel, int& bpw, int& threads);
 
 }  // namespace ct

@@ -132,8 +132,10 @@ k_bond(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restrict__ 
 }
 
 // ---------------------------------------------------------------- assembly
+// One warp per atom for the entries; a warp walks 32 atoms and lane k keeps
+// atom k's sums so the FP64 diagonal and its inverse are formed lane-parallel.
 template <class R>
-__global__ void k_assemble(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restrict__ u,
+__global__ void k_assemble(int N, int cap_cov, int cap_all, int bpw, const typename Vec4<R>::T* __restrict__ u,
                            const int* __restrict__ rep, const RepInfo* __restrict__ reps,
                            const int* __restrict__ nbr, const int* __restrict__ code,
                            const int* __restrict__ ncov, const int* __restrict__ nall,
@@ -141,48 +143,68 @@ __global__ void k_assemble(int N, int cap_cov, int cap_all, const typename Vec4<
                            PotParams<R> P, TypeParams T, R* __restrict__ M, double* __restrict__ Dg,
                            double* __restrict__ dinv) {
   using R4 = typename Vec4<R>::T;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int i = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (i >= N) return;
-  R4 ui = u[i];
-  int ti = (int)ui.w;
-  const RepInfo& ri = reps[rep[i]];
-  R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
-  if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
-  int nc = min(ncov[i], cap_cov), na = min(nall[i], cap_all);
-  R wsum = R(0), selfm = R(0);
-  for (int e = lane; e < na; e += 32) {
-    size_t idx = (size_t)i * cap_all + e;
-    int j = nbr[idx];
-    R4 uj = u[j];
-    R rx, ry, rz;
-    rel_vec<R>(ui, uj, code[idx], hx, hy, hz, rx, ry, rz);
-    R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
-    int tj = (int)uj.w;
-    int pb = ti * 2 + tj;
-    R K, dK;
-    coul_fn<R>(r, P.gshield3[pb], P.inv_rcoul, P.ke, K, dK);
-    R m = K;
-    if (e < nc && r < P.Sout[pb]) {
-      R fc, dfc;
-      cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
-      R fA = P.B[pb] * ct_exp<R>(-P.lam2[pb] * r);
-      R bij = bo[(size_t)i * cap_cov + e].x;
-      R bji = bo[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]].x;
-      R w = R(0.5) * P.kappa[pb] * fc * fA * (bij + bji);
-      m -= R(2) * w;
-      wsum += w;
+  int lane = threadIdx.x & 31;
+  BATCH_LOOP_BEGIN(N, bpw)
+    R my_w = R(0), my_self = R(0);
+    for (int k = 0; k < nb; ++k) {
+      int i = b0 + k;
+      R4 ui = u[i];
+      int ti = (int)ui.w;
+      const RepInfo& ri = reps[rep[i]];
+      R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
+      if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
+      int nc = min(ncov[i], cap_cov), na = min(nall[i], cap_all);
+      R wsum = R(0), selfm = R(0);
+      const int4* nr4 = reinterpret_cast<const int4*>(nbr + (size_t)i * cap_all);
+      const int4* cd4 = reinterpret_cast<const int4*>(code + (size_t)i * cap_all);
+      int n4 = (na + 3) >> 2;
+      for (int q = lane; q < n4; q += 32) {
+        int4 jj = nr4[q], cc = cd4[q];
+        int jv[4] = {jj.x, jj.y, jj.z, jj.w}, cv[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+        int e = 4 * q + c4;
+        if (e >= na) break;
+        size_t idx = (size_t)i * cap_all + e;
+        int j = jv[c4];
+        R4 uj = u[j];
+        R rx, ry, rz;
+        rel_vec<R>(ui, uj, cv[c4], hx, hy, hz, rx, ry, rz);
+        R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
+        int tj = (int)uj.w;
+        int pb = ti * 2 + tj;
+        R K, dK;
+        coul_fn<R>(r, P.gshield3[pb], P.inv_rcoul, P.ke, K, dK);
+        R m = K;
+        if (e < nc && r < P.Sout[pb]) {
+          R fc, dfc;
+          cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
+          R fA = P.B[pb] * ct_exp<R>(-P.lam2[pb] * r);
+          R bij = bo[(size_t)i * cap_cov + e].x;
+          R bji = bo[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]].x;
+          R w = R(0.5) * P.kappa[pb] * fc * fA * (bij + bji);
+          m -= R(2) * w;
+          wsum += w;
+        }
+        if (j == i) selfm += m;
+        M[idx] = m;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        wsum += __shfl_xor_sync(CT_FULL, wsum, o);
+        selfm += __shfl_xor_sync(CT_FULL, selfm, o);
+      }
+      if (lane == k) { my_w = wsum; my_self = selfm; }
     }
-    if (j == i) selfm += m;
-    M[idx] = m;
-  }
-  double ws = warp_sum((double)wsum);
-  double sm = warp_sum((double)selfm);
-  if (lane == 0) {
-    double D = 2.0 * T.J[ti] + 2.0 * ws;
-    Dg[i] = D;
-    dinv[i] = 1.0 / (D + sm);
-  }
+    if (lane < nb) {
+      int i = b0 + lane;
+      int ti = (int)u[i].w;
+      double D = 2.0 * T.J[ti] + 2.0 * (double)my_w;
+      Dg[i] = D;
+      dinv[i] = 1.0 / (D + (double)my_self);
+    }
+  BATCH_LOOP_END
 }
 
 // ---------------------------------------------------------------- covalent forces
@@ -191,8 +213,9 @@ __global__ void __launch_bounds__(APB * GRP)
 k_cov_force(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restrict__ u,
             const int* __restrict__ rep, const RepInfo* __restrict__ reps,
             const int* __restrict__ nbr, const int* __restrict__ code, const int* __restrict__ ncov,
-            const typename Vec4<R>::T* __restrict__ bo, const double* __restrict__ q, PotParams<R> P,
-            TypeParams T, typename Vec4<R>::T* __restrict__ gslot, double* __restrict__ e_atom) {
+            const typename Vec4<R>::T* __restrict__ bo, const double* __restrict__ q,
+            const R* __restrict__ qr, PotParams<R> P, TypeParams T, typename Vec4<R>::T* __restrict__ gslot,
+            double* __restrict__ e_atom) {
   using R4 = typename Vec4<R>::T;
   using R2 = typename Vec2<R>::T;
   extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -210,7 +233,7 @@ k_cov_force(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restri
   int i = blockIdx.x * APB + g;
   bool live = i < N;
   int nc = 0, ti = 0;
-  double eacc = 0.0, qi = 0.0;
+  CompSum<R> eacc;
   if (live) {
     R4 ui = u[i];
     ti = (int)ui.w;
@@ -218,7 +241,7 @@ k_cov_force(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restri
     const RepInfo& ri = reps[rep[i]];
     R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
     if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
-    qi = q[i];
+    R qi = qr[i];
     for (int e = l; e < nc; e += GRP) {
       size_t idx = (size_t)i * cap_all + e;
       int j = nbr[idx];
@@ -235,12 +258,12 @@ k_cov_force(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restri
       R pd = R(0);
       if (fc > R(0)) {
         R4 bb = bo[(size_t)i * cap_cov + e];
-        R dq = (R)(qi - q[j]);
+        R dq = qi - qr[j];
         R cq = R(1) - P.kappa[pb] * dq * dq;
         R fR = P.A[pb] * ct_exp<R>(-P.lam1[pb] * r);
         R fA = P.B[pb] * ct_exp<R>(-P.lam2[pb] * r);
         R att = cq * bb.x * fA;
-        eacc += (double)(R(0.5) * fc * (fR - att));
+        eacc.add(R(0.5) * fc * (fR - att));
         pd = R(0.5) * (dfc * (fR - att) + fc * (-P.lam1[pb] * fR + P.lam2[pb] * att));
         R pre = R(-0.5) * cq * fc * fA;
         D.x = pre * bb.y;
@@ -329,104 +352,158 @@ k_cov_force(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restri
     }
   }
   // per-atom energy: covalent part + self energy (all lanes take part)
+  R es = eacc.s, ec = eacc.c;
 #pragma unroll
-  for (int o = GRP / 2; o > 0; o >>= 1) eacc += __shfl_xor_sync(CT_FULL, eacc, o, GRP);
-  if (live && l == 0) e_atom[i] = eacc + T.E0[ti] + T.chi[ti] * qi + T.J[ti] * qi * qi;
+  for (int o = GRP / 2; o > 0; o >>= 1) {
+    es += __shfl_xor_sync(CT_FULL, es, o, GRP);
+    ec += __shfl_xor_sync(CT_FULL, ec, o, GRP);
+  }
+  if (live && l == 0) {
+    double qd = q[i];
+    e_atom[i] = ((double)es + (double)ec) + T.E0[ti] + T.chi[ti] * qd + T.J[ti] * qd * qd;
+  }
 }
 
 // ---------------------------------------------------------------- charge forces + gather
+// One warp per atom for the entries; a warp walks 32 atoms and lane k keeps
+// atom k's force and energy sums, so the FP64 epilogue (force store, energy,
+// half kick, kinetic energy, replica sums) runs lane-parallel. The virial
+// is summed per lane in FP32 within a batch and in FP64 across batches.
 template <class R>
-__global__ void k_coul_gather(int N, int cap_cov, int cap_all, int chunk,
+__global__ void k_coul_gather(int N, int cap_cov, int cap_all, int bpw,
                               const typename Vec4<R>::T* __restrict__ u, const int* __restrict__ rep,
                               const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
                               const int* __restrict__ code, const int* __restrict__ ncov,
                               const int* __restrict__ nall, const int* __restrict__ rev,
-                              const typename Vec4<R>::T* __restrict__ gslot, const double* __restrict__ q,
+                              const typename Vec4<R>::T* __restrict__ gslot, const R* __restrict__ qr,
                               PotParams<R> P, TypeParams T, int kick, double half_dt,
                               const uint8_t* __restrict__ frozen, double* __restrict__ F,
                               double* __restrict__ v, double* __restrict__ e_atom,
                               double* __restrict__ rep_acc, unsigned* __restrict__ err) {
   using R4 = typename Vec4<R>::T;
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
-  RepAcc<RA_STRIDE> acc;
-  acc.init();
-  for (int i = a0 + warp; i < a1; i += nw) {
-    R4 ui = u[i];
-    int ti = (int)ui.w;
-    int ri_id = rep[i];
-    const RepInfo& ri = reps[ri_id];
-    R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
-    if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
-    int nc = min(ncov[i], cap_cov), na = min(nall[i], cap_all);
-    R qi = (R)q[i];
-    R fx = R(0), fy = R(0), fz = R(0);
-    CompSum<R> ec;
-    R w[9];
+  int lane = threadIdx.x & 31;
+  RepAcc<2> accE;   // (E, KE) of the lane's own atoms
+  RepAcc<9> accW;   // virial of the entries the lane processed
+  accE.init();
+  accW.init();
+  BATCH_LOOP_BEGIN(N, bpw)
+    R mf[5] = {R(0), R(0), R(0), R(0), R(0)};
+    R wb[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) w[k] = R(0);
-    for (int e = lane; e < na; e += 32) {
-      size_t idx = (size_t)i * cap_all + e;
-      int j = nbr[idx];
-      R4 uj = u[j];
-      R rx, ry, rz;
-      rel_vec<R>(ui, uj, code[idx], hx, hy, hz, rx, ry, rz);
-      R r2 = rx * rx + ry * ry + rz * rz;
-      R r = ct_sqrt<R>(r2);
-      int tj = (int)uj.w;
-      R K, dK;
-      coul_fn<R>(r, P.gshield3[ti * 2 + tj], P.inv_rcoul, P.ke, K, dK);
-      R qq = qi * (R)q[j];
-      R c = qq * dK / r;          // force on i along (rx,ry,rz)
-      fx += c * rx; fy += c * ry; fz += c * rz;
-      ec.add(R(0.5) * qq * K);
-      R hc = R(-0.5) * c;         // virial of this directed pair: -1/2 qq K'/r r (x) r
-      w[0] += hc * rx * rx; w[1] += hc * rx * ry; w[2] += hc * rx * rz;
-      w[3] += hc * ry * rx; w[4] += hc * ry * ry; w[5] += hc * ry * rz;
-      w[6] += hc * rz * rx; w[7] += hc * rz * ry; w[8] += hc * rz * rz;
-      if (e < nc) {
-        R4 go = gslot[(size_t)i * cap_cov + e];
-        R4 gr = gslot[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]];
-        fx += go.x - gr.x; fy += go.y - gr.y; fz += go.z - gr.z;
-        w[0] -= rx * go.x; w[1] -= rx * go.y; w[2] -= rx * go.z;
-        w[3] -= ry * go.x; w[4] -= ry * go.y; w[5] -= ry * go.z;
-        w[6] -= rz * go.x; w[7] -= rz * go.y; w[8] -= rz * go.z;
+    for (int k = 0; k < 9; ++k) wb[k] = R(0);
+    int wrep = rep[b0];
+    for (int k = 0; k < nb; ++k) {
+      int i = b0 + k;
+      R4 ui = u[i];
+      int ti = (int)ui.w;
+      int ri_id = rep[i];
+      if (ri_id != wrep) {   // warp-uniform: keep virial partials per replica
+        accW.to(wrep, rep_acc + RA_W, RA_STRIDE);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) { accW.v[q] += (double)wb[q]; wb[q] = R(0); }
+        wrep = ri_id;
+      }
+      const RepInfo& ri = reps[ri_id];
+      R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
+      if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
+      int nc = min(ncov[i], cap_cov), na = min(nall[i], cap_all);
+      R qi = qr[i];
+      R fx = R(0), fy = R(0), fz = R(0);
+      CompSum<R> ec;
+      const int4* nr4 = reinterpret_cast<const int4*>(nbr + (size_t)i * cap_all);
+      const int4* cd4 = reinterpret_cast<const int4*>(code + (size_t)i * cap_all);
+      int n4 = (na + 3) >> 2;
+      for (int q = lane; q < n4; q += 32) {
+        int4 jj = nr4[q], cc = cd4[q];
+        int jv[4] = {jj.x, jj.y, jj.z, jj.w}, cv[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+        int e = 4 * q + c4;
+        if (e >= na) break;
+        int j = jv[c4];
+        R4 uj = u[j];
+        R rx, ry, rz;
+        rel_vec<R>(ui, uj, cv[c4], hx, hy, hz, rx, ry, rz);
+        R r2 = rx * rx + ry * ry + rz * rz;
+        R r = ct_sqrt<R>(r2);
+        int tj = (int)uj.w;
+        R K, dK;
+        coul_fn<R>(r, P.gshield3[ti * 2 + tj], P.inv_rcoul, P.ke, K, dK);
+        R qq = qi * qr[j];
+        R c = qq * dK / r;          // force on i along (rx,ry,rz)
+        fx += c * rx; fy += c * ry; fz += c * rz;
+        ec.add(R(0.5) * qq * K);
+        R hc = R(-0.5) * c;         // virial of this directed pair: -1/2 qq K'/r r (x) r
+        wb[0] += hc * rx * rx; wb[1] += hc * rx * ry; wb[2] += hc * rx * rz;
+        wb[3] += hc * ry * rx; wb[4] += hc * ry * ry; wb[5] += hc * ry * rz;
+        wb[6] += hc * rz * rx; wb[7] += hc * rz * ry; wb[8] += hc * rz * rz;
+        if (e < nc) {
+          R4 go = gslot[(size_t)i * cap_cov + e];
+          R4 gr = gslot[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]];
+          fx += go.x - gr.x; fy += go.y - gr.y; fz += go.z - gr.z;
+          wb[0] -= rx * go.x; wb[1] -= rx * go.y; wb[2] -= rx * go.z;
+          wb[3] -= ry * go.x; wb[4] -= ry * go.y; wb[5] -= ry * go.z;
+          wb[6] -= rz * go.x; wb[7] -= rz * go.y; wb[8] -= rz * go.z;
+        }
+        }
+      }
+      R red[5] = {fx, fy, fz, ec.s, ec.c};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) red[q] += __shfl_xor_sync(CT_FULL, red[q], o);
+      }
+      if (lane == k) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) mf[q] = red[q];
       }
     }
-    // warp reductions in the working precision
+    accW.to(wrep, rep_acc + RA_W, RA_STRIDE);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      fx += __shfl_xor_sync(CT_FULL, fx, o);
-      fy += __shfl_xor_sync(CT_FULL, fy, o);
-      fz += __shfl_xor_sync(CT_FULL, fz, o);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) w[k] += __shfl_xor_sync(CT_FULL, w[k], o);
-    }
-    double ecd = warp_sum(ec.value());
-    if (lane == 0) {
-      double Fx = fx, Fy = fy, Fz = fz;
+    for (int q = 0; q < 9; ++q) accW.v[q] += (double)wb[q];
+    if (lane < nb) {
+      int i = b0 + lane;
+      int ti = (int)u[i].w;
+      double Fx = mf[0], Fy = mf[1], Fz = mf[2];
       F[3 * i] = Fx; F[3 * i + 1] = Fy; F[3 * i + 2] = Fz;
-      double ea = e_atom[i] + ecd;
+      double ea = e_atom[i] + ((double)mf[3] + (double)mf[4]);
       e_atom[i] = ea;
       if (!isfinite(ea) || !isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) atomicOr(err, CT_ERR_NONFINITE);
-      acc.to(ri_id, rep_acc, RA_STRIDE);
-      acc.v[RA_E] += ea;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) acc.v[RA_W + k] += (double)w[k];
+      accE.to(rep[i], rep_acc, RA_STRIDE);
+      accE.v[0] += ea;
       if (kick) {
         if (!frozen[i]) {
-          double s = half_dt * T.inv_mass_acc[ti];
-          v[3 * i] += s * Fx; v[3 * i + 1] += s * Fy; v[3 * i + 2] += s * Fz;
+          double sc = half_dt * T.inv_mass_acc[ti];
+          v[3 * i] += sc * Fx; v[3 * i + 1] += sc * Fy; v[3 * i + 2] += sc * Fz;
         }
         double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
-        acc.v[RA_KE] += 0.5 * T.mass[ti] * (vx * vx + vy * vy + vz * vz);
+        accE.v[1] += 0.5 * T.mass[ti] * (vx * vx + vy * vy + vz * vz);
       }
     }
-  }
-  block_flush<RA_STRIDE>(acc, rep_acc, RA_STRIDE);
+  BATCH_LOOP_END
+  lane_flush<2>(accE, rep_acc, RA_STRIDE);
+  lane_flush<9>(accW, rep_acc + RA_W, RA_STRIDE);
 }
 
 // ---------------------------------------------------------------- launchers
+// Launch shape of the batch kernels: 8-warp blocks for large systems (2-warp
+// blocks when there are too few batches to fill the GPU), as many blocks as
+// are resident at once (queried from the occupancy calculator), and an
+// equal range of 32-atom batches per warp.
+int batch_dims(int N, int nsm, const void* kernel, int& bpw, int& threads) {
+  int nbatch = (N + 31) / 32;
+  int wpb = (nbatch >= 8 * 2 * nsm) ? 8 : 2;
+  threads = wpb * 32;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess || occ < 1) occ = 1;
+  long long slots = (long long)nsm * occ;
+  long long warps = slots * wpb;
+  bpw = (int)((nbatch + warps - 1) / warps);
+  if (bpw < 1) bpw = 1;
+  long long grid = ((long long)nbatch + (long long)bpw * wpb - 1) / ((long long)bpw * wpb);
+  return (int)(grid < 1 ? 1 : grid);
+}
+
 template <class R> static size_t bond_smem(int cap) {
   return (size_t)APB * cap * (sizeof(typename Vec4<R>::T) + sizeof(R) + sizeof(int));
 }
@@ -446,9 +523,10 @@ void launch_bond(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
 template <class R>
 void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st) {
   if (S.N == 0) return;
-  int wpb = 8;
-  k_assemble<R><<<(S.N + wpb - 1) / wpb, wpb * 32, 0, st>>>(
-      S.N, S.cap_cov, S.cap_all, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+  int bpw, threads;
+  int grid = batch_dims(S.N, S.nsm, (const void*)k_assemble<R>, bpw, threads);
+  k_assemble<R><<<grid, threads, 0, st>>>(
+      S.N, S.cap_cov, S.cap_all, bpw, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
       S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, (R*)S.M, S.Dg, S.dinv);
 }
 
@@ -458,23 +536,19 @@ void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams
   size_t sm = force_smem<R>(S.cap_cov);
   k_cov_force<R><<<(S.N + APB - 1) / APB, APB * GRP, sm, st>>>(
       S.N, S.cap_cov, S.cap_all, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code, S.ncov,
-      (const typename Vec4<R>::T*)S.bo, S.q, P, T, (typename Vec4<R>::T*)S.gslot, S.e_atom);
+      (const typename Vec4<R>::T*)S.bo, S.q, (const R*)S.qr, P, T, (typename Vec4<R>::T*)S.gslot, S.e_atom);
 }
 
 template <class R>
 void launch_coul_gather(const DevState& S, const PotParams<R>& P, const TypeParams& T, int kick, double half_dt,
                         cudaStream_t st) {
   if (S.N == 0) return;
-  int wpb = 8;
-  int grid = (S.N + wpb - 1) / wpb;
-  int gmax = S.nsm * 8;
-  if (grid > gmax) grid = gmax;
-  int chunk = (S.N + grid - 1) / grid;
-  grid = (S.N + chunk - 1) / chunk;
-  k_coul_gather<R><<<grid, wpb * 32, 0, st>>>(
-      S.N, S.cap_cov, S.cap_all, chunk, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
-      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.gslot, S.q, P, T, kick, half_dt, S.frozen, S.F,
-      S.v, S.e_atom, S.rep_acc, S.err);
+  int bpw, threads;
+  int grid = batch_dims(S.N, S.nsm, (const void*)k_coul_gather<R>, bpw, threads);
+  k_coul_gather<R><<<grid, threads, 0, st>>>(
+      S.N, S.cap_cov, S.cap_all, bpw, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.gslot, (const R*)S.qr, P, T, kick, half_dt,
+      S.frozen, S.F, S.v, S.e_atom, S.rep_acc, S.err);
 }
 
 template <class R>
