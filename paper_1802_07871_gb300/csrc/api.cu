@@ -304,8 +304,7 @@ static int alloc_atoms(ctbop_system* s) {
 
 static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   DevState& S = s->S;
-  // rows are read four entries at a time with 16/32-byte loads: keep every
-  // row start aligned (capacities multiples of 8 and 4)
+  // capacities rounded to multiples of 8 (all entries) and 4 (covalent)
   cap_all = (std::max(cap_all, cap_cov) + 7) & ~7;
   cap_cov = (cap_cov + 3) & ~3;
   if (s->alloc_cov == cap_cov && s->alloc_all == cap_all) return CTBOP_OK;
@@ -315,13 +314,16 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   size_t rs = s->mixed ? 4 : 8;
   S.cap_cov = cap_cov;
   S.cap_all = cap_all;
-  CK(dalloc(s->list_buf, &S.nbr, (size_t)N * cap_all));
-  CK(dalloc(s->list_buf, &S.code, (size_t)N * cap_all));
+  S.ld = ((N + 31) / 32) * 32;
+  if (S.ld == 0) S.ld = 32;
+  size_t ncol = (size_t)S.ld * cap_all;
+  CK(dalloc(s->list_buf, &S.nbr, ncol));
+  CK(dalloc(s->list_buf, &S.code, ncol));
   CK(dalloc(s->list_buf, &S.rev, (size_t)N * cap_cov));
   unsigned char *bo = nullptr, *gs = nullptr, *M = nullptr;
   CK(dalloc(s->list_buf, &bo, (size_t)N * cap_cov * 4 * rs));
   CK(dalloc(s->list_buf, &gs, (size_t)N * cap_cov * 4 * rs));
-  CK(dalloc(s->list_buf, &M, (size_t)N * cap_all * rs));
+  CK(dalloc(s->list_buf, &M, ncol * rs));
   S.bo = bo;
   S.gslot = gs;
   S.M = M;

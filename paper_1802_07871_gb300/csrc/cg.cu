@@ -12,11 +12,11 @@
 // products, residual sums and the vectors are FP64; the matrix entries and
 // the gathered z_j are in the working precision.
 //
-// FP64 on this GPU issues at a small fraction of the FP32 rate and a warp
-// instruction costs the same with one lane active as with 32, so the matrix
-// passes (one warp per atom) do their FP64 epilogues lane-parallel: a warp
-// walks 32 atoms, lane k keeps atom k's FP32 row sums, then every lane
-// finishes its own atom in FP64 at once.
+// The matrix passes run one thread per atom over its column of the list
+// (entry e of atom i at e * ld + i), so every warp load of entry e of 32
+// consecutive atoms is one 128-byte line, four entries are in flight per
+// thread, and the FP64 epilogue (which on this GPU issues at a small fraction
+// of the FP32 rate) is lane-parallel rather than once per atom.
 //
 // Starting guess: the previous solutions extrapolated in time (quadratic
 // from three, linear from two, the last one alone otherwise).
@@ -158,99 +158,78 @@ __global__ void k_cg_extrap(int N, double2* __restrict__ x, double2* __restrict_
   xr[i] = v;
 }
 
-// Row sums sum_e M_e v_j(e) of atoms b0 .. b0+nb-1 (one warp, lanes over
-// entries, four consecutive entries per lane per step through 16-byte (FP32)
-// or 32-byte (FP64) loads, so four gathers are in flight per lane); lane k
-// returns atom b0+k's sums. Atoms of converged replicas are left at zero.
-// Rows are padded to a multiple of 8 entries; padding is masked.
+// Row sums sum_e M_e v_j(e) of atom i over its column of the list.
 template <class R>
-__device__ inline void batch_rowsums(int b0, int nb, int cap_all, const int* __restrict__ nbr,
-                                     const int* __restrict__ nall, const R* __restrict__ M,
-                                     const typename Vec2<R>::T* __restrict__ v, const int* __restrict__ rep,
-                                     const int* __restrict__ conv, R& ms, R& mt) {
+__device__ inline void row_sum(int i, int na, int ld, const int* __restrict__ nbr, const R* __restrict__ M,
+                               const typename Vec2<R>::T* __restrict__ v, R& hs, R& ht) {
   using V2 = typename Vec2<R>::T;
-  using V4 = typename Vec4<R>::T;
-  int lane = threadIdx.x & 31;
-  ms = R(0);
-  mt = R(0);
-  for (int k = 0; k < nb; ++k) {
-    int i = b0 + k;
-    if (conv && conv[rep[i]]) continue;
-    int na = min(nall[i], cap_all);
-    const int4* nr = reinterpret_cast<const int4*>(nbr + (size_t)i * cap_all);
-    const V4* mr = reinterpret_cast<const V4*>(M + (size_t)i * cap_all);
-    int n4 = (na + 3) >> 2;
-    R hs = R(0), ht = R(0);
-    for (int q = lane; q < n4; q += 32) {
-      int4 jj = nr[q];
-      V4 mm = mr[q];
-      int e = 4 * q;
-      bool ok1 = e + 1 < na, ok2 = e + 2 < na, ok3 = e + 3 < na;
-      V2 z0 = v[jj.x];
-      V2 z1 = v[ok1 ? jj.y : jj.x];
-      V2 z2 = v[ok2 ? jj.z : jj.x];
-      V2 z3 = v[ok3 ? jj.w : jj.x];
-      R m1 = ok1 ? mm.y : R(0), m2 = ok2 ? mm.z : R(0), m3 = ok3 ? mm.w : R(0);
-      hs += mm.x * z0.x + m1 * z1.x + m2 * z2.x + m3 * z3.x;
-      ht += mm.x * z0.y + m1 * z1.y + m2 * z2.y + m3 * z3.y;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      hs += __shfl_xor_sync(CT_FULL, hs, o);
-      ht += __shfl_xor_sync(CT_FULL, ht, o);
-    }
-    if (lane == k) {
-      ms = hs;
-      mt = ht;
-    }
+  const int* pn = nbr + i;
+  const R* pm = M + i;
+  hs = R(0);
+  ht = R(0);
+  int e = 0;
+  for (; e + 4 <= na; e += 4) {
+    size_t o = (size_t)e * ld;
+    int j0 = __ldg(pn + o), j1 = __ldg(pn + o + ld), j2 = __ldg(pn + o + 2 * (size_t)ld),
+        j3 = __ldg(pn + o + 3 * (size_t)ld);
+    R m0 = __ldg(pm + o), m1 = __ldg(pm + o + ld), m2 = __ldg(pm + o + 2 * (size_t)ld),
+      m3 = __ldg(pm + o + 3 * (size_t)ld);
+    V2 z0 = v[j0], z1 = v[j1], z2 = v[j2], z3 = v[j3];
+    hs += m0 * z0.x + m1 * z1.x + m2 * z2.x + m3 * z3.x;
+    ht += m0 * z0.y + m1 * z1.y + m2 * z2.y + m3 * z3.y;
+  }
+  for (; e < na; ++e) {
+    size_t o = (size_t)e * ld;
+    int j0 = __ldg(pn + o);
+    R m0 = __ldg(pm + o);
+    V2 z0 = v[j0];
+    hs += m0 * z0.x;
+    ht += m0 * z0.y;
   }
 }
 
 // r = b - H x0, z = D^-1 r with b = (-chi, 1); sums and maxima for the
 // initial test (kept in update buffer 2).
 template <class R>
-__global__ void k_cg_init(int N, int cap_all, int bpw, const int* __restrict__ nbr,
+__global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
                           const int* __restrict__ nall, const R* __restrict__ M, const double* __restrict__ Dg,
                           const double* __restrict__ dinv, const int* __restrict__ type, const int* __restrict__ rep,
                           TypeParams T, const double2* __restrict__ x, const typename Vec2<R>::T* __restrict__ xr,
                           double2* __restrict__ r, double2* __restrict__ z, typename Vec2<R>::T* __restrict__ zr,
                           double* __restrict__ cg, float* __restrict__ rmax, int Rn, int* __restrict__ conv,
                           int* __restrict__ iters, int* __restrict__ blocks, int* __restrict__ active, double tol) {
-  int lane = threadIdx.x & 31;
   const int ub = CG_UPD + 2 * 5;
   RepAcc<5> acc;
   acc.init();
   LaneMax lm;
-  BATCH_LOOP_BEGIN(N, bpw)
+  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
+  for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
     R hs, ht;
-    batch_rowsums<R>(b0, nb, cap_all, nbr, nall, M, xr, rep, nullptr, hs, ht);
-    if (lane < nb) {
-      int i = b0 + lane;
-      double2 xi = x[i];
-      double D = Dg[i];
-      double2 ri;
-      ri.x = -T.chi[type[i]] - (D * xi.x + (double)hs);
-      ri.y = 1.0 - (D * xi.y + (double)ht);
-      double di = dinv[i];
-      double2 zi;
-      zi.x = ri.x * di;
-      zi.y = ri.y * di;
-      r[i] = ri;
-      z[i] = zi;
-      typename Vec2<R>::T zz;
-      zz.x = (R)zi.x;
-      zz.y = (R)zi.y;
-      zr[i] = zz;
-      int rid = rep[i];
-      acc.to(rid, cg + ub, CG_STRIDE);
-      acc.v[0] += ri.x * ri.x;
-      acc.v[1] += ri.y * ri.y;
-      acc.v[2] += ri.x * ri.y;
-      acc.v[3] += xi.x;
-      acc.v[4] += xi.y;
-      lm.add(rid, fabsf((float)ri.x), fabsf((float)ri.y), rmax + 2 * 2);
-    }
-  BATCH_LOOP_END
+    row_sum<R>(i, nall[i], ld, nbr, M, xr, hs, ht);
+    double2 xi = x[i];
+    double D = Dg[i];
+    double2 ri;
+    ri.x = -T.chi[type[i]] - (D * xi.x + (double)hs);
+    ri.y = 1.0 - (D * xi.y + (double)ht);
+    double di = dinv[i];
+    double2 zi;
+    zi.x = ri.x * di;
+    zi.y = ri.y * di;
+    r[i] = ri;
+    z[i] = zi;
+    typename Vec2<R>::T zz;
+    zz.x = (R)zi.x;
+    zz.y = (R)zi.y;
+    zr[i] = zz;
+    int rid = rep[i];
+    acc.to(rid, cg + ub, CG_STRIDE);
+    acc.v[0] += ri.x * ri.x;
+    acc.v[1] += ri.y * ri.y;
+    acc.v[2] += ri.x * ri.y;
+    acc.v[3] += xi.x;
+    acc.v[4] += xi.y;
+    lm.add(rid, fabsf((float)ri.x), fabsf((float)ri.y), rmax + 2 * 2);
+  }
   lane_flush<5>(acc, cg + ub, CG_STRIDE);
   lm.finish(rmax + 2 * 2);
   if (last_block(blocks)) {
@@ -265,39 +244,35 @@ __global__ void k_cg_init(int N, int cap_all, int bpw, const int* __restrict__ n
 // w = H z and the dots (r.z, w.z) for both solves; the last block turns the
 // dots into the step lengths alpha, beta of this iteration.
 template <class R>
-__global__ void k_cg_mv(int N, int cap_all, int bpw, const int* __restrict__ nbr, const int* __restrict__ nall,
+__global__ void k_cg_mv(int N, int ld, int chunk, const int* __restrict__ nbr, const int* __restrict__ nall,
                         const R* __restrict__ M, const double* __restrict__ Dg, const int* __restrict__ rep,
                         const int* __restrict__ conv, const int* __restrict__ itp,
                         const typename Vec2<R>::T* __restrict__ zr, const double2* __restrict__ z,
                         const double2* __restrict__ r, double2* __restrict__ w, double* __restrict__ cg, int Rn,
                         int* __restrict__ blocks, const int* __restrict__ active) {
   if (*active == 0) return;
-  int lane = threadIdx.x & 31;
   int it = *itp;
   int buf = CG_DOTS + (it & 1) * 4;
   RepAcc<4> acc;
   acc.init();
-  BATCH_LOOP_BEGIN(N, bpw)
+  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
+  for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
+    int rid = rep[i];
+    if (conv[rid]) continue;
     R hs, ht;
-    batch_rowsums<R>(b0, nb, cap_all, nbr, nall, M, zr, rep, conv, hs, ht);
-    if (lane < nb) {
-      int i = b0 + lane;
-      int rid = rep[i];
-      if (!conv[rid]) {
-        double2 zi = z[i], rri = r[i];
-        double D = Dg[i];
-        double2 wi;
-        wi.x = D * zi.x + (double)hs;
-        wi.y = D * zi.y + (double)ht;
-        w[i] = wi;
-        acc.to(rid, cg + buf, CG_STRIDE);
-        acc.v[0] += rri.x * zi.x;
-        acc.v[1] += wi.x * zi.x;
-        acc.v[2] += rri.y * zi.y;
-        acc.v[3] += wi.y * zi.y;
-      }
-    }
-  BATCH_LOOP_END
+    row_sum<R>(i, nall[i], ld, nbr, M, zr, hs, ht);
+    double2 zi = z[i], rri = r[i];
+    double D = Dg[i];
+    double2 wi;
+    wi.x = D * zi.x + (double)hs;
+    wi.y = D * zi.y + (double)ht;
+    w[i] = wi;
+    acc.to(rid, cg + buf, CG_STRIDE);
+    acc.v[0] += rri.x * zi.x;
+    acc.v[1] += wi.x * zi.x;
+    acc.v[2] += rri.y * zi.y;
+    acc.v[3] += wi.y * zi.y;
+  }
   lane_flush<4>(acc, cg + buf, CG_STRIDE);
   if (last_block(blocks + 2)) {
     int sprev = CG_SCAL + ((it + 1) & 1) * 4;
@@ -445,9 +420,9 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
   if (S.N == 0) return;
   k_cg_extrap<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.cx, S.cxh1, S.cxh2, (typename Vec2<R>::T*)S.cxr,
                                                     S.cg_hist);
-  int bpw, threads;
-  int grid = batch_dims(S.N, S.nsm, (const void*)k_cg_init<R>, bpw, threads);
-  k_cg_init<R><<<grid, threads, 0, st>>>(S.N, S.cap_all, bpw, S.nbr, S.nall, (const R*)S.M, S.Dg, S.dinv, S.type,
+  int chunk;
+  int grid = atom_dims(S.N, S.nsm, (const void*)k_cg_init<R>, 256, chunk);
+  k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.ld, chunk, S.nbr, S.nall, (const R*)S.M, S.Dg, S.dinv, S.type,
                                      S.rep, T, S.cx, (const typename Vec2<R>::T*)S.cxr, S.cr, S.cz,
                                      (typename Vec2<R>::T*)S.czr, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
                                      S.cg_blocks, S.cg_active, tol);
@@ -456,9 +431,9 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
 template <class R>
 void launch_cg_mv(const DevState& S, cudaStream_t st) {
   if (S.N == 0) return;
-  int bpw, threads;
-  int grid = batch_dims(S.N, S.nsm, (const void*)k_cg_mv<R>, bpw, threads);
-  k_cg_mv<R><<<grid, threads, 0, st>>>(S.N, S.cap_all, bpw, S.nbr, S.nall, (const R*)S.M, S.Dg, S.rep, S.cg_conv,
+  int chunk;
+  int grid = atom_dims(S.N, S.nsm, (const void*)k_cg_mv<R>, 256, chunk);
+  k_cg_mv<R><<<grid, 256, 0, st>>>(S.N, S.ld, chunk, S.nbr, S.nall, (const R*)S.M, S.Dg, S.rep, S.cg_conv,
                                    S.cg_it, (const typename Vec2<R>::T*)S.czr, S.cz, S.cr, S.cw, S.cg, S.R,
                                    S.cg_blocks, S.cg_active);
 }

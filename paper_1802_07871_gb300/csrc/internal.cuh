@@ -6,13 +6,16 @@
 //   type, rep        int32[N]      atom type (0 Si, 1 C), replica id
 //   cell4            int4[N]       cell coordinates (x,y,z) and global cell id, fixed between rebuilds
 //   u                Real4[N]      position relative to the owning cell's origin (w = type)
-//   nbr, code        int32[N*cap]  one list per atom: entries [0, ncov) are the covalent
-//                                  list (r < S + skin), [ncov, nall) the rest inside Rc + skin
+//   nbr, code        int32[cap*ld] one list per atom, column-major: entry e of atom i at
+//                                  e*ld + i (ld = N rounded up to 32), so a warp reading entry e
+//                                  of 32 consecutive atoms touches 128 contiguous bytes. Entries
+//                                  [0, ncov) are the covalent list (r < S + skin), [ncov, nall)
+//                                  the rest inside Rc + skin
 //   code             packed cell offset (dx,dy,dz) such that r_ij = u_j - u_i + d*h
 //   rev              int32[N*capc] entry of j's list that points back to i (covalent part)
 //   bo               Real4[N*capc] b_ij, db/dzeta_1, db/dzeta_2 per directed bond
 //   gslot            Real4[N*capc] dE_i/du_e: gradient of the terms centred on i w.r.t. bond e
-//   M                Real[N*cap]   charge-Hessian off-diagonal entries K_ij - 2 w_ij
+//   M                Real[cap*ld]  charge-Hessian off-diagonal entries K_ij - 2 w_ij (list layout)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -138,22 +141,6 @@ template <class R> struct CompSum {
   }
   __device__ inline double value() const { return (double)s + (double)c; }
 };
-
-// Warps take atoms in batches of 32; warp gw (global) handles the batch range
-// [gw * bpw, (gw + 1) * bpw). Inside the loop b0 is the first atom of the
-// batch and nb its size.
-#define BATCH_LOOP_BEGIN(N_, bpw_)                                          \
-  {                                                                         \
-    int gw_ = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);         \
-    int nbatch_ = ((N_) + 31) >> 5;                                         \
-    int bb1_ = min(nbatch_, (gw_ + 1) * (bpw_));                           \
-    for (int bb_ = gw_ * (bpw_); bb_ < bb1_; ++bb_) {                      \
-      int b0 = bb_ * 32;                                                    \
-      int nb = min(32, (N_) - b0);
-
-#define BATCH_LOOP_END \
-    }                  \
-  }
 
 // ---------------------------------------------------------------- reductions
 // Accumulate NV doubles per replica. Each warp keeps a running partial for

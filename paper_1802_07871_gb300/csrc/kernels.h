@@ -32,6 +32,7 @@ enum CgSlots {
 struct DevState {
   int N = 0, R = 0, ncells = 0;
   int cap_cov = 0, cap_all = 0;
+  int ld = 0;                   // column stride of the lists: N rounded up to 32
   // per atom
   double *x = nullptr, *v = nullptr, *F = nullptr, *xref = nullptr, *q = nullptr, *e_atom = nullptr;
   int *type = nullptr, *rep = nullptr;
@@ -101,7 +102,8 @@ template <class R> void launch_kick_drift(const DevState& S, const TypeParams& T
 void launch_zero_acc(const DevState& S, cudaStream_t st);
 template <class R> cudaError_t setup_pot(int cap_cov);
 template <class R> void launch_copy_q(const DevState& S, cudaStream_t st);
-// launch shape for kernels whose warps take atoms in batches of 32
-int batch_dims(int N, int nsm, const void* kernel, int& bpw, int& threads);
+// launch shape for kernels with one thread per atom: resident blocks only,
+// each block a contiguous chunk of atoms (a multiple of its size)
+int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk);
 
 }  // namespace ct

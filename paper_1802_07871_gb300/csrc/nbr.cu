@@ -8,6 +8,8 @@
 // stores the atom index j and the stencil offset d in cells, which is exactly
 // the cell-lattice vector from i's cell to j's image cell, so
 // r_ij = u_j - u_i + d * h with u the offset from the owning cell's origin.
+// Lists are stored column-major (entry e of atom i at e * ld + i) for the
+// thread-per-atom consumers.
 #include "internal.cuh"
 #include "kernels.h"
 
@@ -147,7 +149,7 @@ __global__ void k_build(int N, const typename Vec4<R>::T* __restrict__ u,
                         const int4* __restrict__ cell4, const int* __restrict__ rep,
                         const RepInfo* __restrict__ reps, const int* __restrict__ cell_start,
                         const int* __restrict__ cell_count, const int* __restrict__ cell_atoms,
-                        PotParams<R> P, int cap_cov, int cap_all, int* __restrict__ nbr,
+                        PotParams<R> P, int cap_cov, int cap_all, int ld, int* __restrict__ nbr,
                         int* __restrict__ code, int* __restrict__ ncov, int* __restrict__ nall,
                         int* __restrict__ maxcnt, unsigned* __restrict__ err,
                         const int* __restrict__ flag) {
@@ -160,8 +162,8 @@ __global__ void k_build(int N, const typename Vec4<R>::T* __restrict__ u,
   int ti = (int)ui.w;
   int4 ci = cell4[i];
   R hx = (R)ri.hc[0], hy = (R)ri.hc[1], hz = (R)ri.hc[2];
-  int* row_nbr = nbr + (size_t)i * cap_all;
-  int* row_code = code + (size_t)i * cap_all;
+  int* col_nbr = nbr + i;
+  int* col_code = code + i;
   // `count` is the number of stored entries (never above the capacities, so
   // every stored entry is a valid atom even after an overflow); `need`
   // counts what the lists would need, for regrowing them.
@@ -217,8 +219,8 @@ __global__ void k_build(int N, const typename Vec4<R>::T* __restrict__ u,
           if (take) {
             int pos = count + __popc(bal & ((1u << lane) - 1u));
             if (pos < cap_pass) {
-              row_nbr[pos] = j;
-              row_code[pos] = cd;
+              col_nbr[(size_t)pos * ld] = j;
+              col_code[(size_t)pos * ld] = cd;
             }
           }
           int nt = __popc(bal);
@@ -242,23 +244,23 @@ __global__ void k_build(int N, const typename Vec4<R>::T* __restrict__ u,
 
 // Reverse covalent entry: for entry e of i pointing at (j, d), the entry of
 // j pointing at (i, -d).
-__global__ void k_rev(int N, int cap_cov, int cap_all, const int* __restrict__ nbr,
+__global__ void k_rev(int N, int cap_cov, int ld, const int* __restrict__ nbr,
                       const int* __restrict__ code, const int* __restrict__ ncov,
                       int* __restrict__ rev, unsigned* __restrict__ err,
                       const int* __restrict__ flag) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)N * cap_cov || *flag == 0) return;
-  int i = (int)(t / cap_cov), e = (int)(t % cap_cov);
+  int i = (int)(t % N), e = (int)(t / N);   // consecutive threads: consecutive atoms
   int nc = min(ncov[i], cap_cov);
   if (e >= nc) return;
-  int j = nbr[(size_t)i * cap_all + e];
+  int j = nbr[(size_t)e * ld + i];
   int dx, dy, dz;
-  unpack_code(code[(size_t)i * cap_all + e], dx, dy, dz);
+  unpack_code(code[(size_t)e * ld + i], dx, dy, dz);
   int want = pack_code(-dx, -dy, -dz);
   int ncj = min(ncov[j], cap_cov);
   int found = -1;
   for (int k = 0; k < ncj; ++k) {
-    if (nbr[(size_t)j * cap_all + k] == i && code[(size_t)j * cap_all + k] == want) { found = k; break; }
+    if (nbr[(size_t)k * ld + j] == i && code[(size_t)k * ld + j] == want) { found = k; break; }
   }
   if (found < 0) { atomicOr(err, CT_ERR_REV_MISSING); found = 0; }
   rev[(size_t)i * cap_cov + e] = found;
@@ -297,10 +299,10 @@ void launch_rebuild(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   int wpb = 8;
   k_build<R><<<(N + wpb - 1) / wpb, wpb * 32, 0, st>>>(
       N, (const typename Vec4<R>::T*)S.u, S.cell4, S.rep, S.reps, S.cell_start, S.cell_count,
-      S.cell_atoms, P, S.cap_cov, S.cap_all, S.nbr, S.code, S.ncov, S.nall, S.maxcnt, S.err, f);
+      S.cell_atoms, P, S.cap_cov, S.cap_all, S.ld, S.nbr, S.code, S.ncov, S.nall, S.maxcnt, S.err, f);
   size_t tot = (size_t)N * S.cap_cov;
-  k_rev<<<(unsigned)((tot + tb - 1) / tb), tb, 0, st>>>(N, S.cap_cov, S.cap_all, S.nbr, S.code,
-                                                        S.ncov, S.rev, S.err, f);
+  k_rev<<<(unsigned)((tot + tb - 1) / tb), tb, 0, st>>>(N, S.cap_cov, S.ld, S.nbr, S.code, S.ncov, S.rev,
+                                                        S.err, f);
   k_finish_rebuild<<<1, 1, 0, st>>>(S.flag_rebuild, S.rebuild_count);
 }
 

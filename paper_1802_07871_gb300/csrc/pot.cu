@@ -4,14 +4,15 @@
 //   in shared memory; each lane owns bonds e and sums over the third atoms k
 //   the environment terms zeta_l,ie = sum_k fc(r_ik) ang_l(cos) e^{alpha_l (r_ie - r_ik)}
 //   (Sec. 2, Eq. 2), then b_ie and db/dzeta_l from the L = 2 form (Eq. 7).
-// assembly (k_assemble): one warp per atom; the off-diagonal charge Hessian
-//   entries M_e = K(r_e) - 2 w_e (w_e = 1/2 kappa fc B e^{-lambda2 r} (b_ij + b_ji)
-//   on covalent entries), diagonal 2 J + 2 sum w and the Jacobi inverse.
+// assembly (k_assemble): one thread per atom over its column of the list;
+//   the off-diagonal charge Hessian entries M_e = K(r_e) - 2 w_e
+//   (w_e = 1/2 kappa fc B e^{-lambda2 r} (b_ij + b_ji) on covalent entries),
+//   diagonal 2 J + 2 sum w and the Jacobi inverse.
 // covalent forces (k_cov_force): eight lanes per atom; for every entry e the
 //   gradient dE_i/du_e of all terms centred on i (pair part, and the
 //   environment-sum chain rule both with e as bond and e as third atom);
 //   written to a per-bond slot, no atomics.
-// charge forces + gather (k_coul_gather): one warp per atom over all entries;
+// charge forces + gather (k_coul_gather): one thread per atom over all entries;
 //   F_i = sum_j q_i q_j K'(r) u_ij/r + sum_e slot(i,e) - sum_e slot(j_e, rev_e);
 //   per-atom energy, virial, optional velocity-Verlet half kick; FP64
 //   per-replica sums.
@@ -50,7 +51,7 @@ __device__ inline void rel_vec(const typename Vec4<R>::T& ui, const typename Vec
 // ---------------------------------------------------------------- bond pass
 template <class R>
 __global__ void __launch_bounds__(APB * GRP)
-k_bond(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restrict__ u,
+k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
        const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
        const int* __restrict__ code, const int* __restrict__ ncov, PotParams<R> P,
        typename Vec4<R>::T* __restrict__ bo) {
@@ -73,10 +74,10 @@ k_bond(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restrict__ 
     R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
     if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
     for (int e = l; e < nc; e += GRP) {
-      int j = nbr[(size_t)i * cap_all + e];
+      int j = nbr[(size_t)e * ld + i];
       R4 uj = u[j];
       R rx, ry, rz;
-      rel_vec<R>(ui, uj, code[(size_t)i * cap_all + e], hx, hy, hz, rx, ry, rz);
+      rel_vec<R>(ui, uj, code[(size_t)e * ld + i], hx, hy, hz, rx, ry, rz);
       R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
       int tj = (int)uj.w;
       int pb = ti * 2 + tj;
@@ -132,10 +133,8 @@ k_bond(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restrict__ 
 }
 
 // ---------------------------------------------------------------- assembly
-// One warp per atom for the entries; a warp walks 32 atoms and lane k keeps
-// atom k's sums so the FP64 diagonal and its inverse are formed lane-parallel.
 template <class R>
-__global__ void k_assemble(int N, int cap_cov, int cap_all, int bpw, const typename Vec4<R>::T* __restrict__ u,
+__global__ void k_assemble(int N, int cap_cov, int ld, int chunk, const typename Vec4<R>::T* __restrict__ u,
                            const int* __restrict__ rep, const RepInfo* __restrict__ reps,
                            const int* __restrict__ nbr, const int* __restrict__ code,
                            const int* __restrict__ ncov, const int* __restrict__ nall,
@@ -143,74 +142,54 @@ __global__ void k_assemble(int N, int cap_cov, int cap_all, int bpw, const typen
                            PotParams<R> P, TypeParams T, R* __restrict__ M, double* __restrict__ Dg,
                            double* __restrict__ dinv) {
   using R4 = typename Vec4<R>::T;
-  int lane = threadIdx.x & 31;
-  BATCH_LOOP_BEGIN(N, bpw)
-    R my_w = R(0), my_self = R(0);
-    for (int k = 0; k < nb; ++k) {
-      int i = b0 + k;
-      R4 ui = u[i];
-      int ti = (int)ui.w;
-      const RepInfo& ri = reps[rep[i]];
-      R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
-      if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
-      int nc = min(ncov[i], cap_cov), na = min(nall[i], cap_all);
-      R wsum = R(0), selfm = R(0);
-      const int4* nr4 = reinterpret_cast<const int4*>(nbr + (size_t)i * cap_all);
-      const int4* cd4 = reinterpret_cast<const int4*>(code + (size_t)i * cap_all);
-      int n4 = (na + 3) >> 2;
-      for (int q = lane; q < n4; q += 32) {
-        int4 jj = nr4[q], cc = cd4[q];
-        int jv[4] = {jj.x, jj.y, jj.z, jj.w}, cv[4] = {cc.x, cc.y, cc.z, cc.w};
-#pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-        int e = 4 * q + c4;
-        if (e >= na) break;
-        size_t idx = (size_t)i * cap_all + e;
-        int j = jv[c4];
-        R4 uj = u[j];
-        R rx, ry, rz;
-        rel_vec<R>(ui, uj, cv[c4], hx, hy, hz, rx, ry, rz);
-        R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
-        int tj = (int)uj.w;
-        int pb = ti * 2 + tj;
-        R K, dK;
-        coul_fn<R>(r, P.gshield3[pb], P.inv_rcoul, P.ke, K, dK);
-        R m = K;
-        if (e < nc && r < P.Sout[pb]) {
-          R fc, dfc;
-          cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
-          R fA = P.B[pb] * ct_exp<R>(-P.lam2[pb] * r);
-          R bij = bo[(size_t)i * cap_cov + e].x;
-          R bji = bo[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]].x;
-          R w = R(0.5) * P.kappa[pb] * fc * fA * (bij + bji);
-          m -= R(2) * w;
-          wsum += w;
-        }
-        if (j == i) selfm += m;
-        M[idx] = m;
-        }
+  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
+  for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
+    R4 ui = u[i];
+    int ti = (int)ui.w;
+    const RepInfo& ri = reps[rep[i]];
+    R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
+    if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
+    int nc = ncov[i], na = nall[i];
+    R wsum = R(0), selfm = R(0);
+    const int* pn = nbr + i;
+    const int* pc = code + i;
+    R* pm = M + i;
+#pragma unroll 4
+    for (int e = 0; e < na; ++e) {
+      size_t off = (size_t)e * ld;
+      int j = pn[off];
+      R4 uj = u[j];
+      R rx, ry, rz;
+      rel_vec<R>(ui, uj, pc[off], hx, hy, hz, rx, ry, rz);
+      R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
+      int tj = (int)uj.w;
+      int pb = ti * 2 + tj;
+      R K, dK;
+      coul_fn<R>(r, P.gshield3[pb], P.inv_rcoul, P.ke, K, dK);
+      R m = K;
+      if (e < nc && r < P.Sout[pb]) {
+        R fc, dfc;
+        cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
+        R fA = P.B[pb] * ct_exp<R>(-P.lam2[pb] * r);
+        R bij = bo[(size_t)i * cap_cov + e].x;
+        R bji = bo[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]].x;
+        R w = R(0.5) * P.kappa[pb] * fc * fA * (bij + bji);
+        m -= R(2) * w;
+        wsum += w;
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        wsum += __shfl_xor_sync(CT_FULL, wsum, o);
-        selfm += __shfl_xor_sync(CT_FULL, selfm, o);
-      }
-      if (lane == k) { my_w = wsum; my_self = selfm; }
+      if (j == i) selfm += m;
+      pm[off] = m;
     }
-    if (lane < nb) {
-      int i = b0 + lane;
-      int ti = (int)u[i].w;
-      double D = 2.0 * T.J[ti] + 2.0 * (double)my_w;
-      Dg[i] = D;
-      dinv[i] = 1.0 / (D + (double)my_self);
-    }
-  BATCH_LOOP_END
+    double D = 2.0 * T.J[ti] + 2.0 * (double)wsum;
+    Dg[i] = D;
+    dinv[i] = 1.0 / (D + (double)selfm);
+  }
 }
 
 // ---------------------------------------------------------------- covalent forces
 template <class R>
 __global__ void __launch_bounds__(APB * GRP)
-k_cov_force(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restrict__ u,
+k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
             const int* __restrict__ rep, const RepInfo* __restrict__ reps,
             const int* __restrict__ nbr, const int* __restrict__ code, const int* __restrict__ ncov,
             const typename Vec4<R>::T* __restrict__ bo, const double* __restrict__ q,
@@ -243,7 +222,7 @@ k_cov_force(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restri
     if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
     R qi = qr[i];
     for (int e = l; e < nc; e += GRP) {
-      size_t idx = (size_t)i * cap_all + e;
+      size_t idx = (size_t)e * ld + i;
       int j = nbr[idx];
       R4 uj = u[j];
       R rx, ry, rz;
@@ -365,12 +344,11 @@ k_cov_force(int N, int cap_cov, int cap_all, const typename Vec4<R>::T* __restri
 }
 
 // ---------------------------------------------------------------- charge forces + gather
-// One warp per atom for the entries; a warp walks 32 atoms and lane k keeps
-// atom k's force and energy sums, so the FP64 epilogue (force store, energy,
-// half kick, kinetic energy, replica sums) runs lane-parallel. The virial
-// is summed per lane in FP32 within a batch and in FP64 across batches.
+// One thread per atom over its column of the list: force, per-atom energy
+// and virial in the working precision (compensated energy sum), then the
+// FP64 store, half kick, kinetic energy and per-replica sums.
 template <class R>
-__global__ void k_coul_gather(int N, int cap_cov, int cap_all, int bpw,
+__global__ void k_coul_gather(int N, int cap_cov, int ld, int chunk,
                               const typename Vec4<R>::T* __restrict__ u, const int* __restrict__ rep,
                               const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
                               const int* __restrict__ code, const int* __restrict__ ncov,
@@ -381,127 +359,111 @@ __global__ void k_coul_gather(int N, int cap_cov, int cap_all, int bpw,
                               double* __restrict__ v, double* __restrict__ e_atom,
                               double* __restrict__ rep_acc, unsigned* __restrict__ err) {
   using R4 = typename Vec4<R>::T;
-  int lane = threadIdx.x & 31;
-  RepAcc<2> accE;   // (E, KE) of the lane's own atoms
-  RepAcc<9> accW;   // virial of the entries the lane processed
+  RepAcc<2> accE;   // (E, KE)
+  RepAcc<9> accW;   // virial
   accE.init();
   accW.init();
-  BATCH_LOOP_BEGIN(N, bpw)
-    R mf[5] = {R(0), R(0), R(0), R(0), R(0)};
-    R wb[9];
+  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
+  for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
+    R4 ui = u[i];
+    int ti = (int)ui.w;
+    int ri_id = rep[i];
+    const RepInfo& ri = reps[ri_id];
+    R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
+    if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
+    int nc = ncov[i], na = nall[i];
+    R qi = qr[i];
+    R fx = R(0), fy = R(0), fz = R(0);
+    CompSum<R> ec;
+    R w[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) wb[k] = R(0);
-    int wrep = rep[b0];
-    for (int k = 0; k < nb; ++k) {
-      int i = b0 + k;
-      R4 ui = u[i];
-      int ti = (int)ui.w;
-      int ri_id = rep[i];
-      if (ri_id != wrep) {   // warp-uniform: keep virial partials per replica
-        accW.to(wrep, rep_acc + RA_W, RA_STRIDE);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) { accW.v[q] += (double)wb[q]; wb[q] = R(0); }
-        wrep = ri_id;
-      }
-      const RepInfo& ri = reps[ri_id];
-      R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
-      if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
-      int nc = min(ncov[i], cap_cov), na = min(nall[i], cap_all);
-      R qi = qr[i];
-      R fx = R(0), fy = R(0), fz = R(0);
-      CompSum<R> ec;
-      const int4* nr4 = reinterpret_cast<const int4*>(nbr + (size_t)i * cap_all);
-      const int4* cd4 = reinterpret_cast<const int4*>(code + (size_t)i * cap_all);
-      int n4 = (na + 3) >> 2;
-      for (int q = lane; q < n4; q += 32) {
-        int4 jj = nr4[q], cc = cd4[q];
-        int jv[4] = {jj.x, jj.y, jj.z, jj.w}, cv[4] = {cc.x, cc.y, cc.z, cc.w};
-#pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-        int e = 4 * q + c4;
-        if (e >= na) break;
-        int j = jv[c4];
-        R4 uj = u[j];
-        R rx, ry, rz;
-        rel_vec<R>(ui, uj, cv[c4], hx, hy, hz, rx, ry, rz);
-        R r2 = rx * rx + ry * ry + rz * rz;
-        R r = ct_sqrt<R>(r2);
-        int tj = (int)uj.w;
-        R K, dK;
-        coul_fn<R>(r, P.gshield3[ti * 2 + tj], P.inv_rcoul, P.ke, K, dK);
-        R qq = qi * qr[j];
-        R c = qq * dK / r;          // force on i along (rx,ry,rz)
-        fx += c * rx; fy += c * ry; fz += c * rz;
-        ec.add(R(0.5) * qq * K);
-        R hc = R(-0.5) * c;         // virial of this directed pair: -1/2 qq K'/r r (x) r
-        wb[0] += hc * rx * rx; wb[1] += hc * rx * ry; wb[2] += hc * rx * rz;
-        wb[3] += hc * ry * rx; wb[4] += hc * ry * ry; wb[5] += hc * ry * rz;
-        wb[6] += hc * rz * rx; wb[7] += hc * rz * ry; wb[8] += hc * rz * rz;
-        if (e < nc) {
-          R4 go = gslot[(size_t)i * cap_cov + e];
-          R4 gr = gslot[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]];
-          fx += go.x - gr.x; fy += go.y - gr.y; fz += go.z - gr.z;
-          wb[0] -= rx * go.x; wb[1] -= rx * go.y; wb[2] -= rx * go.z;
-          wb[3] -= ry * go.x; wb[4] -= ry * go.y; wb[5] -= ry * go.z;
-          wb[6] -= rz * go.x; wb[7] -= rz * go.y; wb[8] -= rz * go.z;
-        }
-        }
-      }
-      R red[5] = {fx, fy, fz, ec.s, ec.c};
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) red[q] += __shfl_xor_sync(CT_FULL, red[q], o);
-      }
-      if (lane == k) {
-#pragma unroll
-        for (int q = 0; q < 5; ++q) mf[q] = red[q];
-      }
+    for (int k = 0; k < 9; ++k) w[k] = R(0);
+    const int* pn = nbr + i;
+    const int* pc = code + i;
+    // covalent entries: charge term plus the slot gather
+    for (int e = 0; e < nc; ++e) {
+      size_t off = (size_t)e * ld;
+      int j = pn[off];
+      R4 uj = u[j];
+      R rx, ry, rz;
+      rel_vec<R>(ui, uj, pc[off], hx, hy, hz, rx, ry, rz);
+      R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
+      int tj = (int)uj.w;
+      R K, dK;
+      coul_fn<R>(r, P.gshield3[ti * 2 + tj], P.inv_rcoul, P.ke, K, dK);
+      R qq = qi * qr[j];
+      R c = qq * dK / r;
+      R4 go = gslot[(size_t)i * cap_cov + e];
+      R4 gr = gslot[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]];
+      R gx = c * rx + go.x - gr.x, gy = c * ry + go.y - gr.y, gz = c * rz + go.z - gr.z;
+      fx += gx; fy += gy; fz += gz;
+      ec.add(R(0.5) * qq * K);
+      // virial: -1/2 qq K'/r r (x) r for the charge pair, -r (x) slot for the bond
+      R hc = R(-0.5) * c;
+      R tx = hc * rx - go.x, ty = hc * ry - go.y, tz = hc * rz - go.z;
+      w[0] += rx * tx; w[1] += rx * ty; w[2] += rx * tz;
+      w[3] += ry * tx; w[4] += ry * ty; w[5] += ry * tz;
+      w[6] += rz * tx; w[7] += rz * ty; w[8] += rz * tz;
     }
-    accW.to(wrep, rep_acc + RA_W, RA_STRIDE);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) accW.v[q] += (double)wb[q];
-    if (lane < nb) {
-      int i = b0 + lane;
-      int ti = (int)u[i].w;
-      double Fx = mf[0], Fy = mf[1], Fz = mf[2];
-      F[3 * i] = Fx; F[3 * i + 1] = Fy; F[3 * i + 2] = Fz;
-      double ea = e_atom[i] + ((double)mf[3] + (double)mf[4]);
-      e_atom[i] = ea;
-      if (!isfinite(ea) || !isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) atomicOr(err, CT_ERR_NONFINITE);
-      accE.to(rep[i], rep_acc, RA_STRIDE);
-      accE.v[0] += ea;
-      if (kick) {
-        if (!frozen[i]) {
-          double sc = half_dt * T.inv_mass_acc[ti];
-          v[3 * i] += sc * Fx; v[3 * i + 1] += sc * Fy; v[3 * i + 2] += sc * Fz;
-        }
-        double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
-        accE.v[1] += 0.5 * T.mass[ti] * (vx * vx + vy * vy + vz * vz);
-      }
+    // remaining entries: charge term only
+#pragma unroll 4
+    for (int e = nc; e < na; ++e) {
+      size_t off = (size_t)e * ld;
+      int j = pn[off];
+      R4 uj = u[j];
+      R rx, ry, rz;
+      rel_vec<R>(ui, uj, pc[off], hx, hy, hz, rx, ry, rz);
+      R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
+      int tj = (int)uj.w;
+      R K, dK;
+      coul_fn<R>(r, P.gshield3[ti * 2 + tj], P.inv_rcoul, P.ke, K, dK);
+      R qq = qi * qr[j];
+      R c = qq * dK / r;
+      fx += c * rx; fy += c * ry; fz += c * rz;
+      ec.add(R(0.5) * qq * K);
+      R hc = R(-0.5) * c;
+      R hx_ = hc * rx, hy_ = hc * ry, hz_ = hc * rz;
+      w[0] += rx * hx_; w[1] += rx * hy_; w[2] += rx * hz_;
+      w[3] += ry * hx_; w[4] += ry * hy_; w[5] += ry * hz_;
+      w[6] += rz * hx_; w[7] += rz * hy_; w[8] += rz * hz_;
     }
-  BATCH_LOOP_END
+    double Fx = fx, Fy = fy, Fz = fz;
+    F[3 * i] = Fx; F[3 * i + 1] = Fy; F[3 * i + 2] = Fz;
+    double ea = e_atom[i] + ec.value();
+    e_atom[i] = ea;
+    if (!isfinite(ea) || !isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) atomicOr(err, CT_ERR_NONFINITE);
+    accE.to(ri_id, rep_acc, RA_STRIDE);
+    accW.to(ri_id, rep_acc + RA_W, RA_STRIDE);
+    accE.v[0] += ea;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) accW.v[k] += (double)w[k];
+    if (kick) {
+      if (!frozen[i]) {
+        double sc = half_dt * T.inv_mass_acc[ti];
+        v[3 * i] += sc * Fx; v[3 * i + 1] += sc * Fy; v[3 * i + 2] += sc * Fz;
+      }
+      double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
+      accE.v[1] += 0.5 * T.mass[ti] * (vx * vx + vy * vy + vz * vz);
+    }
+  }
   lane_flush<2>(accE, rep_acc, RA_STRIDE);
   lane_flush<9>(accW, rep_acc + RA_W, RA_STRIDE);
 }
 
 // ---------------------------------------------------------------- launchers
-// Launch shape of the batch kernels: 8-warp blocks for large systems (2-warp
-// blocks when there are too few batches to fill the GPU), as many blocks as
-// are resident at once (queried from the occupancy calculator), and an
-// equal range of 32-atom batches per warp.
-int batch_dims(int N, int nsm, const void* kernel, int& bpw, int& threads) {
-  int nbatch = (N + 31) / 32;
-  int wpb = (nbatch >= 8 * 2 * nsm) ? 8 : 2;
-  threads = wpb * 32;
+// One thread per atom: as many 256-thread blocks as are resident at once
+// (occupancy calculator), each a contiguous chunk of atoms.
+int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk) {
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess || occ < 1) occ = 1;
   long long slots = (long long)nsm * occ;
-  long long warps = slots * wpb;
-  bpw = (int)((nbatch + warps - 1) / warps);
-  if (bpw < 1) bpw = 1;
-  long long grid = ((long long)nbatch + (long long)bpw * wpb - 1) / ((long long)bpw * wpb);
-  return (int)(grid < 1 ? 1 : grid);
+  long long need = ((long long)N + threads - 1) / threads;
+  long long grid = need < slots ? need : slots;
+  if (grid < 1) grid = 1;
+  long long ch = ((long long)N + grid - 1) / grid;
+  ch = ((ch + threads - 1) / threads) * threads;
+  chunk = (int)ch;
+  return (int)(((long long)N + ch - 1) / ch);
 }
 
 template <class R> static size_t bond_smem(int cap) {
@@ -516,17 +478,17 @@ void launch_bond(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   if (S.N == 0) return;
   size_t sm = bond_smem<R>(S.cap_cov);
   k_bond<R><<<(S.N + APB - 1) / APB, APB * GRP, sm, st>>>(
-      S.N, S.cap_cov, S.cap_all, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
       S.ncov, P, (typename Vec4<R>::T*)S.bo);
 }
 
 template <class R>
 void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st) {
   if (S.N == 0) return;
-  int bpw, threads;
-  int grid = batch_dims(S.N, S.nsm, (const void*)k_assemble<R>, bpw, threads);
-  k_assemble<R><<<grid, threads, 0, st>>>(
-      S.N, S.cap_cov, S.cap_all, bpw, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+  int chunk;
+  int grid = atom_dims(S.N, S.nsm, (const void*)k_assemble<R>, 256, chunk);
+  k_assemble<R><<<grid, 256, 0, st>>>(
+      S.N, S.cap_cov, S.ld, chunk, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
       S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, (R*)S.M, S.Dg, S.dinv);
 }
 
@@ -535,7 +497,7 @@ void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams
   if (S.N == 0) return;
   size_t sm = force_smem<R>(S.cap_cov);
   k_cov_force<R><<<(S.N + APB - 1) / APB, APB * GRP, sm, st>>>(
-      S.N, S.cap_cov, S.cap_all, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code, S.ncov,
+      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code, S.ncov,
       (const typename Vec4<R>::T*)S.bo, S.q, (const R*)S.qr, P, T, (typename Vec4<R>::T*)S.gslot, S.e_atom);
 }
 
@@ -543,10 +505,10 @@ template <class R>
 void launch_coul_gather(const DevState& S, const PotParams<R>& P, const TypeParams& T, int kick, double half_dt,
                         cudaStream_t st) {
   if (S.N == 0) return;
-  int bpw, threads;
-  int grid = batch_dims(S.N, S.nsm, (const void*)k_coul_gather<R>, bpw, threads);
-  k_coul_gather<R><<<grid, threads, 0, st>>>(
-      S.N, S.cap_cov, S.cap_all, bpw, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+  int chunk;
+  int grid = atom_dims(S.N, S.nsm, (const void*)k_coul_gather<R>, 256, chunk);
+  k_coul_gather<R><<<grid, 256, 0, st>>>(
+      S.N, S.cap_cov, S.ld, chunk, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
       S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.gslot, (const R*)S.qr, P, T, kick, half_dt,
       S.frozen, S.F, S.v, S.e_atom, S.rep_acc, S.err);
 }
