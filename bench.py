@@ -121,10 +121,10 @@ def peaks():
 
 
 def cg_matvec_bytes(n_atoms, entries, rs):
-    """Algorithmic bytes of one CG matrix pass: per list entry the index and
-    the stored coefficient; per atom its z (as gathered, once), z, r, D, the
-    entry count, the replica id, and the written w."""
-    return entries * (4 + rs) + n_atoms * (2 * rs + 16 + 16 + 8 + 4 + 4 + 16)
+    """Algorithmic bytes of one CG matrix pass: per list entry the neighbour
+    index and the stored coefficient; per atom the gathered y (once), its own
+    y, d, v, r and D, the written w, the entry count and the replica id."""
+    return entries * (4 + rs) + n_atoms * (7 * rs + 8)
 
 
 def run_ours(a):

@@ -235,35 +235,27 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->atom_buf, &u, (size_t)N * 4 * rs));
   S.u = u;
   CK(dalloc(s->atom_buf, &S.cell_atoms, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.Dg, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.dinv, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.cx, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.cr, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.cp, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.cs, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.cz, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.cw, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.cxh1, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.cxh2, (size_t)N));
-  unsigned char *zr = nullptr, *xr = nullptr, *qr = nullptr;
-  CK(dalloc(s->atom_buf, &zr, (size_t)N * 2 * rs));
-  CK(dalloc(s->atom_buf, &xr, (size_t)N * 2 * rs));
-  CK(dalloc(s->atom_buf, &qr, (size_t)N * rs));
-  S.czr = zr;
-  S.cxr = xr;
-  S.qr = qr;
-  CK(cudaMemset(S.qr, 0, (size_t)N * rs));
+  {
+    void** rv[] = {&S.Dg, &S.dinv, &S.cr, &S.cp, &S.cs, &S.cy, &S.cw, &S.cd, &S.cv, &S.qr};
+    for (void** pp : rv) {
+      unsigned char* b = nullptr;
+      CK(dalloc(s->atom_buf, &b, (size_t)N * rs));
+      *pp = b;
+    }
+  }
+  CK(dalloc(s->atom_buf, &S.cqh1, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.cqh2, (size_t)N));
   CK(dalloc(s->atom_buf, &S.ncov, (size_t)N));
   CK(dalloc(s->atom_buf, &S.nall, (size_t)N));
   CK(cudaMemset(S.v, 0, sizeof(double) * 3 * (size_t)N));
   CK(cudaMemset(S.F, 0, sizeof(double) * 3 * (size_t)N));
   CK(cudaMemset(S.q, 0, sizeof(double) * (size_t)N));
   CK(cudaMemset(S.frozen, 0, (size_t)N));
-  CK(cudaMemset(S.cx, 0, sizeof(double2) * (size_t)N));
-  CK(cudaMemset(S.cxh1, 0, sizeof(double2) * (size_t)N));
-  CK(cudaMemset(S.cxh2, 0, sizeof(double2) * (size_t)N));
-  CK(cudaMemset(S.cp, 0, sizeof(double2) * (size_t)N));
-  CK(cudaMemset(S.cs, 0, sizeof(double2) * (size_t)N));
+  CK(cudaMemset(S.cqh1, 0, sizeof(double) * (size_t)N));
+  CK(cudaMemset(S.cqh2, 0, sizeof(double) * (size_t)N));
+  CK(cudaMemset(S.cp, 0, (size_t)N * rs));
+  CK(cudaMemset(S.cs, 0, (size_t)N * rs));
+  CK(cudaMemset(S.qr, 0, (size_t)N * rs));
   // replica ids
   std::vector<int> rep(N);
   for (int r = 0; r < s->R; ++r)
@@ -803,13 +795,11 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
   const int64_t chunk = 100;
   // snapshot buffers for redoing a chunk after a list overflow
   double *sx = nullptr, *sv = nullptr, *sF = nullptr, *sq = nullptr;
-  double2* scx = nullptr;
   size_t N = S.N;
   CK(cudaMallocAsync(&sx, sizeof(double) * 3 * N + 8, s->stream));
   CK(cudaMallocAsync(&sv, sizeof(double) * 3 * N + 8, s->stream));
   CK(cudaMallocAsync(&sF, sizeof(double) * 3 * N + 8, s->stream));
   CK(cudaMallocAsync(&sq, sizeof(double) * N + 8, s->stream));
-  CK(cudaMallocAsync(&scx, sizeof(double2) * N + 16, s->stream));
   int result = CTBOP_OK;
   int64_t done = 0;
   int redo = 0;
@@ -819,7 +809,6 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
     cudaMemcpyAsync(sv, S.v, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s->stream);
     cudaMemcpyAsync(sF, S.F, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s->stream);
     cudaMemcpyAsync(sq, S.q, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->stream);
-    cudaMemcpyAsync(scx, S.cx, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s->stream);
     cudaMemsetAsync(S.err, 0, sizeof(unsigned), s->stream);
     if (s->use_graph) {
       if (!s->g_step || s->g_step_dt != dt_fs) {
@@ -851,7 +840,9 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
       cudaMemcpyAsync(S.v, sv, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s->stream);
       cudaMemcpyAsync(S.F, sF, sizeof(double) * 3 * N, cudaMemcpyDeviceToDevice, s->stream);
       cudaMemcpyAsync(S.q, sq, sizeof(double) * N, cudaMemcpyDeviceToDevice, s->stream);
-      cudaMemcpyAsync(S.cx, scx, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s->stream);
+      // the restored q is the next starting guess; its time history is gone
+      *s->h_int = 1;
+      cudaMemcpyAsync(S.cg_hist, s->h_int, sizeof(int), cudaMemcpyHostToDevice, s->stream);
       int mc[2];
       cudaMemcpy(mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost);
       int cc = std::max(S.cap_cov, mc[0] + mc[0] / 4 + 4);
@@ -877,7 +868,6 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
   cudaFreeAsync(sv, s->stream);
   cudaFreeAsync(sF, s->stream);
   cudaFreeAsync(sq, s->stream);
-  cudaFreeAsync(scx, s->stream);
   cudaStreamSynchronize(s->stream);
   return result;
 }

@@ -16,17 +16,21 @@ enum RepSlots {
 
 // CG scalars per replica (double), see cg.cu.
 enum CgSlots {
-  CG_DOTS = 0,     // [2 buffers][4]: (r.z, w.z) for the s and t solves
-  CG_UPD = 8,      // [3 buffers][5]: sum r_s^2, r_t^2, r_s r_t, x_s, x_t
-  CG_SCAL = 23,    // [2 buffers][4]: gamma_s, alpha_s, gamma_t, alpha_t of an iteration
-  CG_AB = 31,      // alpha_s, beta_s, alpha_t, beta_t of the running iteration
-  CG_MU = 35,      // final mu
-  CG_RES = 36,     // final rms residual
-  CG_Q = 37,       // requested total charge
-  CG_NAT = 38,     // atoms in the replica
-  CG_RES0 = 39,    // max-norm bound of the starting guess's residual
-  CG_RESMAX = 40,  // final max-norm bound max|r_s| + |mu| max|r_t|
-  CG_STRIDE = 42
+  CG_DOTS = 0,     // [2 buffers][2]: r.z, w.z
+  CG_UPD = 4,      // [3 buffers][3]: sum y, sum r, sum r^2
+  CG_SCAL = 13,    // [2 buffers][2]: gamma, alpha of an iteration
+  CG_AB = 17,      // alpha, beta of the running iteration
+  CG_C = 19,       // c = sum y / sum d of the running iteration
+  CG_SD = 20,      // sum d (d = D^-1 1)
+  CG_SQ0 = 21,     // sum of the extrapolated starting guess
+  CG_DQ = 22,      // uniform shift putting the starting guess on sum q = Q
+  CG_MU = 23,      // mu = -mean(r), the electronegativity
+  CG_RES = 24,     // rms of r - mean(r)
+  CG_RESMAX = 25,  // max |r - mean(r)|
+  CG_Q = 26,       // requested total charge
+  CG_NAT = 27,     // atoms in the replica
+  CG_RES0 = 28,    // max |r - mean(r)| of the starting guess
+  CG_STRIDE = 30
 };
 
 struct DevState {
@@ -53,15 +57,14 @@ struct DevState {
   void* bo = nullptr;           // Real4[N*cap_cov]
   void* gslot = nullptr;        // Real4[N*cap_cov]
   void* M = nullptr;            // Real[N*cap_all]
-  double *Dg = nullptr, *dinv = nullptr;
-  // CG vectors, (s, t) interleaved
-  double2 *cx = nullptr, *cr = nullptr, *cp = nullptr, *cs = nullptr, *cz = nullptr, *cw = nullptr;
-  void* czr = nullptr;          // Real2[N]: z in the matvec precision
-  void* cxr = nullptr;          // Real2[N]: starting guess in the matvec precision
-  float* cg_rmax = nullptr;     // [R][3 buffers][2]: max |r_s|, max |r_t|
+  void *Dg = nullptr, *dinv = nullptr;   // Real[N]: Hessian diagonal without self-images, Jacobi inverse
+  // CG: the iterate is q itself (FP64); the rest in the working precision
+  double *cqh1 = nullptr, *cqh2 = nullptr;  // q of the previous two solves
+  void *cr = nullptr, *cp = nullptr, *cs = nullptr, *cy = nullptr, *cw = nullptr, *cd = nullptr,
+       *cv = nullptr;           // Real[N]: r, p, s = H p, y = D^-1 r, w = H z, d = D^-1 1, v = H d
+  unsigned* cg_rmax = nullptr;  // [R][3 buffers][2]: max r, max -r (order-preserving map)
   void* qr = nullptr;           // Real[N]: charges in the working precision
-  double2 *cxh1 = nullptr, *cxh2 = nullptr;  // (s, t) of the previous two solves
-  int* cg_hist = nullptr;       // solutions held in cx, cxh1, cxh2 (0..3)
+  int* cg_hist = nullptr;       // solutions held in q, cqh1, cqh2 (0..3)
   // control
   int* flag_rebuild = nullptr;
   long long* rebuild_count = nullptr;

@@ -139,8 +139,8 @@ __global__ void k_assemble(int N, int cap_cov, int ld, int chunk, const typename
                            const int* __restrict__ nbr, const int* __restrict__ code,
                            const int* __restrict__ ncov, const int* __restrict__ nall,
                            const int* __restrict__ rev, const typename Vec4<R>::T* __restrict__ bo,
-                           PotParams<R> P, TypeParams T, R* __restrict__ M, double* __restrict__ Dg,
-                           double* __restrict__ dinv) {
+                           PotParams<R> P, TypeParams T, R* __restrict__ M, R* __restrict__ Dg,
+                           R* __restrict__ dinv) {
   using R4 = typename Vec4<R>::T;
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
   for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
@@ -180,9 +180,9 @@ __global__ void k_assemble(int N, int cap_cov, int ld, int chunk, const typename
       if (j == i) selfm += m;
       pm[off] = m;
     }
-    double D = 2.0 * T.J[ti] + 2.0 * (double)wsum;
+    R D = (R)(2.0 * T.J[ti]) + R(2) * wsum;
     Dg[i] = D;
-    dinv[i] = 1.0 / (D + (double)selfm);
+    dinv[i] = R(1) / (D + selfm);
   }
 }
 
@@ -489,7 +489,7 @@ void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams&
   int grid = atom_dims(S.N, S.nsm, (const void*)k_assemble<R>, 256, chunk);
   k_assemble<R><<<grid, 256, 0, st>>>(
       S.N, S.cap_cov, S.ld, chunk, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
-      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, (R*)S.M, S.Dg, S.dinv);
+      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, (R*)S.M, (R*)S.Dg, (R*)S.dinv);
 }
 
 template <class R>
