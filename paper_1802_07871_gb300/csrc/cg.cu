@@ -14,9 +14,16 @@
 // that give the next c and the convergence test). H d is formed once per
 // solve, in the starting pass.
 //
+// Re-centring: r carries a large constant part (-mu 1) that the projection
+// removes only in exact arithmetic; once the residual is small, rounding of
+// that part pollutes r.z and the iteration diverges. The projection and every
+// CG scalar are unchanged by adding a constant to r, so each update subtracts
+// the previous mean of r and accumulates the shift (mu = -(mean r + shift)).
+//
 // Precision: the iterate q and every reduction (dots, sums) are FP64; the
 // other vectors, the matrix entries and the gathered y_j are in the working
-// precision (FP32 in the mixed policy).
+// precision (FP32 in the mixed policy). Directions in FP32 do not sum to
+// exactly zero, so after the solve q is shifted uniformly onto sum q = Q.
 //
 // The matrix passes run one thread per atom over its column of the list
 // (entry e of atom i at e * ld + i): a warp load of entry e of 32 consecutive
@@ -96,16 +103,17 @@ struct LaneMax {
 };
 
 // Convergence test for every unconverged replica from the sums (sum y,
-// sum r, sum r^2) at upd_off and the maxima of buffer mbuf; sets c for the
-// next matrix pass.
+// sum r, sum r^2, sum q) at upd_off and the maxima of buffer mbuf; records
+// the mean of r for the next re-centring, c for the next matrix pass and the
+// shift that restores sum q = Q.
 __device__ inline int check_replicas(int R, double* cg, const unsigned* rmax, int* conv, int* iters, int upd_off,
                                      int mbuf, int it_done, double tol, int first) {
   int all = 1;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     if (conv[r]) continue;
     double* c = cg + (size_t)r * CG_STRIDE;
-    const double* u3 = c + upd_off;
-    double sy = ldcg(u3 + 0), sr = ldcg(u3 + 1), srr = ldcg(u3 + 2);
+    const double* u4 = c + upd_off;
+    double sy = ldcg(u4 + 0), sr = ldcg(u4 + 1), srr = ldcg(u4 + 2), sq = ldcg(u4 + 3);
     double hi = funmap(__ldcg(rmax + (size_t)r * 6 + mbuf * 2));
     double lo = funmap(__ldcg(rmax + (size_t)r * 6 + mbuf * 2 + 1));
     double nat = c[CG_NAT];
@@ -114,9 +122,11 @@ __device__ inline int check_replicas(int R, double* cg, const unsigned* rmax, in
     double var = nat > 0 ? srr / nat - m * m : 0.0;
     double rms = sqrt(var > 0.0 ? var : 0.0);
     if (!isfinite(bound)) bound = INFINITY;
-    c[CG_MU] = -m;
+    c[CG_M] = m;
+    c[CG_MU] = -(m + c[CG_SHIFT]);
     c[CG_RES] = rms;
     c[CG_RESMAX] = bound;
+    c[CG_DQ] = nat > 0 ? (c[CG_Q] - sq) / nat : 0.0;
     if (first) c[CG_RES0] = bound;
     double sd = c[CG_SD];
     c[CG_C] = sd != 0.0 ? sy / sd : 0.0;
@@ -230,8 +240,8 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
                           R* __restrict__ r, R* __restrict__ y, R* __restrict__ v, double* __restrict__ cg,
                           unsigned* __restrict__ rmax, int Rn, int* __restrict__ conv, int* __restrict__ iters,
                           int* __restrict__ blocks, int* __restrict__ active, double tol) {
-  const int ub = CG_UPD + 2 * 3;
-  RepAcc<3> acc;
+  const int ub = CG_UPD + 2 * 4;
+  RepAcc<4> acc;
   RepAcc<1> accd;
   acc.init();
   accd.init();
@@ -262,10 +272,11 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
     acc.v[0] += (double)yi;
     acc.v[1] += ri;
     acc.v[2] += ri * ri;
+    acc.v[3] += qi;
     accd.v[0] += (double)di;
     lm.add(rid, (float)rr, rmax + 2 * 2);
   }
-  lane_flush<3>(acc, cg + ub, CG_STRIDE);
+  lane_flush<4>(acc, cg + ub, CG_STRIDE);
   lane_flush<1>(accd, cg + CG_SD, CG_STRIDE);
   lm.finish(rmax + 2 * 2);
   if (last_block(blocks)) {
@@ -357,24 +368,24 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
   }
   int it = *itp;
   int mb = it % 3;
-  int ubuf = CG_UPD + mb * 3;
+  int ubuf = CG_UPD + mb * 4;
   // zero the buffers the next iteration accumulates into
   if (blockIdx.x == 0) {
-    int dn = CG_DOTS + ((it + 1) & 1) * 2, un = CG_UPD + ((it + 1) % 3) * 3, mn = (it + 1) % 3;
-    for (int k = threadIdx.x; k < Rn * 7; k += blockDim.x) {
-      int rr = k / 7, kk = k % 7;
+    int dn = CG_DOTS + ((it + 1) & 1) * 2, un = CG_UPD + ((it + 1) % 3) * 4, mn = (it + 1) % 3;
+    for (int k = threadIdx.x; k < Rn * 8; k += blockDim.x) {
+      int rr = k / 8, kk = k % 8;
       double* c = cg + (size_t)rr * CG_STRIDE;
       if (kk < 2) c[dn + kk] = 0.0;
-      else if (kk < 5) c[un + kk - 2] = 0.0;
-      else rmax[(size_t)rr * 6 + mn * 2 + (kk - 5)] = 0u;
+      else if (kk < 6) c[un + kk - 2] = 0.0;
+      else rmax[(size_t)rr * 6 + mn * 2 + (kk - 6)] = 0u;
     }
   }
-  RepAcc<3> acc;
+  RepAcc<4> acc;
   acc.init();
   LaneMax lm;
   int crid = -1;
   double alpha = 0.0;
-  R a = R(0), b = R(0), c = R(0);
+  R a = R(0), b = R(0), c = R(0), mprev = R(0);
   R py = R(0);                      // working-precision partial of sum y for the current replica
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
   for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
@@ -389,13 +400,14 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
       a = (R)alpha;
       b = (R)ldcg(cc + CG_AB + 1);
       c = (R)ldcg(cc + CG_C);
+      mprev = (R)ldcg(cc + CG_M);
       crid = rid;
     }
     R zi = y[i] - c * d[i];
     R pi = zi + b * p[i];
     R si = w[i] + b * s[i];
     double qi = q[i] + alpha * (double)pi;
-    R ri = r[i] - a * si;
+    R ri = (r[i] - a * si) - mprev;
     R yi = dinv[i] * ri;
     p[i] = pi;
     s[i] = si;
@@ -405,12 +417,21 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
     py += yi;
     acc.v[1] += (double)ri;
     acc.v[2] += (double)(ri * ri);
+    acc.v[3] += qi;
     lm.add(rid, (float)ri, rmax + mb * 2);
   }
   if (crid >= 0) acc.v[0] += (double)py;
-  lane_flush<3>(acc, cg + ubuf, CG_STRIDE);
+  lane_flush<4>(acc, cg + ubuf, CG_STRIDE);
   lm.finish(rmax + mb * 2);
   if (last_block(blocks + 1)) {
+    // the mean this launch subtracted joins the accumulated shift (the value
+    // every thread used is still in CG_M)
+    for (int rr = threadIdx.x; rr < Rn; rr += blockDim.x)
+      if (!conv[rr]) {
+        double* cc = cg + (size_t)rr * CG_STRIDE;
+        cc[CG_SHIFT] += (double)(R)cc[CG_M];
+      }
+    __syncthreads();
     int all = check_replicas(Rn, cg, rmax, conv, iters, ubuf, mb, it + 1, tol, 0);
     if (threadIdx.x == 0) {
       blocks[1] = 0;
@@ -425,10 +446,12 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
   }
 }
 
-// Working-precision copy of the solved charges for the force passes; count
-// the solve's iterations and extend its history.
+// Restore sum q = Q exactly (uniform shift), write the working-precision
+// copy for the force passes, count the solve's iterations and extend its
+// history.
 template <class R>
-__global__ void k_cg_final(int N, const double* __restrict__ q, R* __restrict__ qr, const int* __restrict__ itp,
+__global__ void k_cg_final(int N, const int* __restrict__ rep, const double* __restrict__ cg,
+                           double* __restrict__ q, R* __restrict__ qr, const int* __restrict__ itp,
                            long long* __restrict__ total, int* __restrict__ hist) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
@@ -436,7 +459,11 @@ __global__ void k_cg_final(int N, const double* __restrict__ q, R* __restrict__ 
     int h = *hist;
     *hist = h < 3 ? h + 1 : 3;
   }
-  if (i < N) qr[i] = (R)q[i];
+  if (i < N) {
+    double qi = q[i] + cg[(size_t)rep[i] * CG_STRIDE + CG_DQ];
+    q[i] = qi;
+    qr[i] = (R)qi;
+  }
 }
 
 // Working-precision copy of charges set from outside the solve.
@@ -491,7 +518,8 @@ void launch_cg_iter(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
 template <class R>
 void launch_cg_end(const DevState& S, cudaStream_t st) {
   int n = S.N > 0 ? S.N : 1;
-  k_cg_final<R><<<(n + 255) / 256, 256, 0, st>>>(S.N, S.q, (R*)S.qr, S.cg_it, S.cg_total, S.cg_hist);
+  k_cg_final<R><<<(n + 255) / 256, 256, 0, st>>>(S.N, S.rep, S.cg, S.q, (R*)S.qr, S.cg_it, S.cg_total,
+                                                 S.cg_hist);
 }
 
 template <class R>

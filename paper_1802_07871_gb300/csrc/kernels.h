@@ -17,20 +17,22 @@ enum RepSlots {
 // CG scalars per replica (double), see cg.cu.
 enum CgSlots {
   CG_DOTS = 0,     // [2 buffers][2]: r.z, w.z
-  CG_UPD = 4,      // [3 buffers][3]: sum y, sum r, sum r^2
-  CG_SCAL = 13,    // [2 buffers][2]: gamma, alpha of an iteration
-  CG_AB = 17,      // alpha, beta of the running iteration
-  CG_C = 19,       // c = sum y / sum d of the running iteration
-  CG_SD = 20,      // sum d (d = D^-1 1)
-  CG_SQ0 = 21,     // sum of the extrapolated starting guess
-  CG_DQ = 22,      // uniform shift putting the starting guess on sum q = Q
-  CG_MU = 23,      // mu = -mean(r), the electronegativity
-  CG_RES = 24,     // rms of r - mean(r)
-  CG_RESMAX = 25,  // max |r - mean(r)|
-  CG_Q = 26,       // requested total charge
-  CG_NAT = 27,     // atoms in the replica
-  CG_RES0 = 28,    // max |r - mean(r)| of the starting guess
-  CG_STRIDE = 30
+  CG_UPD = 4,      // [3 buffers][4]: sum y, sum r, sum r^2, sum q
+  CG_SCAL = 16,    // [2 buffers][2]: gamma, alpha of an iteration
+  CG_AB = 20,      // alpha, beta of the running iteration
+  CG_C = 22,       // c = sum y / sum d of the running iteration
+  CG_SD = 23,      // sum d (d = D^-1 1)
+  CG_SQ0 = 24,     // sum of the extrapolated starting guess
+  CG_DQ = 25,      // uniform shift putting q on sum q = Q
+  CG_M = 26,       // mean of the stored (re-centred) r
+  CG_SHIFT = 27,   // total subtracted from r by the re-centring
+  CG_MU = 28,      // mu = -mean(r), the electronegativity
+  CG_RES = 29,     // rms of r - mean(r)
+  CG_RESMAX = 30,  // max |r - mean(r)|
+  CG_Q = 31,       // requested total charge
+  CG_NAT = 32,     // atoms in the replica
+  CG_RES0 = 33,    // max |r - mean(r)| of the starting guess
+  CG_STRIDE = 34
 };
 
 struct DevState {
