@@ -62,39 +62,41 @@ __device__ inline bool last_block(int* counter) {
   return am_last;
 }
 
-// Order-preserving map of floats to unsigned ints (max of the map = map of the max).
-__device__ inline unsigned fmap(float f) {
-  unsigned b = __float_as_uint(f);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+// Order-preserving map of doubles to unsigned 64-bit ints (max of the map =
+// map of the max), for atomicMax on signed values.
+__device__ inline unsigned long long dmap(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
 }
-__device__ inline float funmap(unsigned u) {
-  unsigned b = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
-  return __uint_as_float(b);
+__device__ inline double dunmap(unsigned long long u) {
+  unsigned long long b = (u & 0x8000000000000000ull) ? (u & 0x7fffffffffffffffull) : ~u;
+  return __longlong_as_double((long long)b);
 }
 
-// Per-lane running max of r and of -r for one replica; merged per warp and
-// flushed with atomicMax on the order-preserving map.
+// Per-lane running max of r and of -r for one replica (working precision);
+// merged per warp and flushed with atomicMax on the order-preserving map.
+template <class R>
 struct LaneMax {
   int rep = -1;
-  float hi = -INFINITY, lo = -INFINITY;   // max r, max -r
-  __device__ inline void flush(unsigned* base) {
+  R hi = -R(INFINITY), lo = -R(INFINITY);   // max r, max -r
+  __device__ inline void flush(unsigned long long* base) {
     if (rep >= 0) {
-      atomicMax(base + (size_t)rep * 6, fmap(hi));
-      atomicMax(base + (size_t)rep * 6 + 1, fmap(lo));
+      atomicMax(base + (size_t)rep * 6, dmap((double)hi));
+      atomicMax(base + (size_t)rep * 6 + 1, dmap((double)lo));
     }
-    hi = lo = -INFINITY;
+    hi = lo = -R(INFINITY);
   }
-  __device__ inline void add(int r, float v, unsigned* base) {
+  __device__ inline void add(int r, R v, unsigned long long* base) {
     if (r != rep) { flush(base); rep = r; }
-    hi = fmaxf(hi, v);
-    lo = fmaxf(lo, -v);
+    hi = fmax(hi, v);
+    lo = fmax(lo, -v);
   }
-  __device__ inline void finish(unsigned* base) {
+  __device__ inline void finish(unsigned long long* base) {
     int r0 = __shfl_sync(CT_FULL, rep, 0);
     if (__all_sync(CT_FULL, rep == r0)) {
       for (int o = 16; o > 0; o >>= 1) {
-        hi = fmaxf(hi, __shfl_xor_sync(CT_FULL, hi, o));
-        lo = fmaxf(lo, __shfl_xor_sync(CT_FULL, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(CT_FULL, hi, o));
+        lo = fmax(lo, __shfl_xor_sync(CT_FULL, lo, o));
       }
       if ((threadIdx.x & 31) != 0) rep = -1;
     }
@@ -106,7 +108,8 @@ struct LaneMax {
 // sum r, sum r^2, sum q) at upd_off and the maxima of buffer mbuf; records
 // the mean of r for the next re-centring, c for the next matrix pass and the
 // shift that restores sum q = Q.
-__device__ inline int check_replicas(int R, double* cg, const unsigned* rmax, int* conv, int* iters, int upd_off,
+__device__ inline int check_replicas(int R, double* cg, const unsigned long long* rmax, int* conv, int* iters,
+                                     int upd_off,
                                      int mbuf, int it_done, double tol, int first) {
   int all = 1;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
@@ -114,8 +117,8 @@ __device__ inline int check_replicas(int R, double* cg, const unsigned* rmax, in
     double* c = cg + (size_t)r * CG_STRIDE;
     const double* u4 = c + upd_off;
     double sy = ldcg(u4 + 0), sr = ldcg(u4 + 1), srr = ldcg(u4 + 2), sq = ldcg(u4 + 3);
-    double hi = funmap(__ldcg(rmax + (size_t)r * 6 + mbuf * 2));
-    double lo = funmap(__ldcg(rmax + (size_t)r * 6 + mbuf * 2 + 1));
+    double hi = dunmap(__ldcg(rmax + (size_t)r * 6 + mbuf * 2));
+    double lo = dunmap(__ldcg(rmax + (size_t)r * 6 + mbuf * 2 + 1));
     double nat = c[CG_NAT];
     double m = nat > 0 ? sr / nat : 0.0;
     double bound = fmax(hi - m, lo + m);       // max_i |r_i - m|
@@ -141,13 +144,13 @@ __device__ inline int check_replicas(int R, double* cg, const unsigned* rmax, in
 }
 
 // --------------------------------------------------------------- prepare
-__global__ void k_cg_prep(int R, double* __restrict__ cg, unsigned* __restrict__ rmax, int* __restrict__ conv,
+__global__ void k_cg_prep(int R, double* __restrict__ cg, unsigned long long* __restrict__ rmax, int* __restrict__ conv,
                           int* __restrict__ iters, int* __restrict__ it, int* __restrict__ blocks,
                           int* __restrict__ active) {
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     double* c = cg + (size_t)r * CG_STRIDE;
     for (int k = 0; k < CG_MU; ++k) c[k] = 0.0;
-    for (int k = 0; k < 6; ++k) rmax[(size_t)r * 6 + k] = 0u;
+    for (int k = 0; k < 6; ++k) rmax[(size_t)r * 6 + k] = 0ull;
     conv[r] = 0;
     iters[r] = 0;
   }
@@ -200,15 +203,32 @@ __global__ void k_cg_extrap(int N, double* __restrict__ q, double* __restrict__ 
 }
 
 // Row sums sum_e M_e v_j(e) of atom i over its column of the list, for one
-// or two gathered vectors (NV = 1, 2), plus sum_e M_e (NV = 3).
+// or two gathered vectors (NV = 1, 2), plus sum_e M_e (NV = 3). In FP32 the
+// products are summed with compensation: a plain FP32 sum of ~230 terms
+// whose partial sums are much larger than the result limits the reachable
+// residual of the charge solve (about 1e-4 eV/e); compensated, the limit is
+// the rounding of the stored entries.
+template <class R>
+struct RowAcc {
+  R s = R(0), c = R(0);
+  __device__ inline void add(R x) {
+    if (sizeof(R) == 4) {
+      R t = s + x;
+      c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+      s = t;
+    } else {
+      s += x;
+    }
+  }
+  __device__ inline R value() const { return s + c; }
+};
+
 template <class R, int NV>
 __device__ inline void row_sum(int i, int na, int ld, const int* __restrict__ nbr, const R* __restrict__ M,
                                const R* __restrict__ v0, const R* __restrict__ v1, R& h0, R& h1, R& hm) {
   const int* pn = nbr + i;
   const R* pm = M + i;
-  h0 = R(0);
-  h1 = R(0);
-  hm = R(0);
+  RowAcc<R> a0, a1, am;
   int e = 0;
   for (; e + 4 <= na; e += 4) {
     size_t o = (size_t)e * ld;
@@ -216,18 +236,25 @@ __device__ inline void row_sum(int i, int na, int ld, const int* __restrict__ nb
         j3 = __ldg(pn + o + 3 * (size_t)ld);
     R m0 = __ldg(pm + o), m1 = __ldg(pm + o + ld), m2 = __ldg(pm + o + 2 * (size_t)ld),
       m3 = __ldg(pm + o + 3 * (size_t)ld);
-    h0 += m0 * v0[j0] + m1 * v0[j1] + m2 * v0[j2] + m3 * v0[j3];
-    if (NV >= 2) h1 += m0 * v1[j0] + m1 * v1[j1] + m2 * v1[j2] + m3 * v1[j3];
-    if (NV >= 3) hm += (m0 + m1) + (m2 + m3);
+    R x0 = v0[j0], x1 = v0[j1], x2 = v0[j2], x3 = v0[j3];
+    a0.add(m0 * x0); a0.add(m1 * x1); a0.add(m2 * x2); a0.add(m3 * x3);
+    if (NV >= 2) {
+      R y0 = v1[j0], y1 = v1[j1], y2 = v1[j2], y3 = v1[j3];
+      a1.add(m0 * y0); a1.add(m1 * y1); a1.add(m2 * y2); a1.add(m3 * y3);
+    }
+    if (NV >= 3) { am.add(m0); am.add(m1); am.add(m2); am.add(m3); }
   }
   for (; e < na; ++e) {
     size_t o = (size_t)e * ld;
     int j0 = __ldg(pn + o);
     R m0 = __ldg(pm + o);
-    h0 += m0 * v0[j0];
-    if (NV >= 2) h1 += m0 * v1[j0];
-    if (NV >= 3) hm += m0;
+    a0.add(m0 * v0[j0]);
+    if (NV >= 2) a1.add(m0 * v1[j0]);
+    if (NV >= 3) am.add(m0);
   }
+  h0 = a0.value();
+  h1 = a1.value();
+  hm = am.value();
 }
 
 // r = -(H q0 + chi), y = D^-1 r, v = H d; sums (sum y, sum r, sum r^2,
@@ -238,14 +265,14 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
                           const int* __restrict__ type, const int* __restrict__ rep, TypeParams T,
                           double* __restrict__ q, const R* __restrict__ qr, const R* __restrict__ d,
                           R* __restrict__ r, R* __restrict__ y, R* __restrict__ v, double* __restrict__ cg,
-                          unsigned* __restrict__ rmax, int Rn, int* __restrict__ conv, int* __restrict__ iters,
+                          unsigned long long* __restrict__ rmax, int Rn, int* __restrict__ conv, int* __restrict__ iters,
                           int* __restrict__ blocks, int* __restrict__ active, double tol) {
   const int ub = CG_UPD + 2 * 4;
   RepAcc<4> acc;
   RepAcc<1> accd;
   acc.init();
   accd.init();
-  LaneMax lm;
+  LaneMax<R> lm;
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
   int crid = -1;
   double dq = 0.0;
@@ -274,7 +301,7 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
     acc.v[2] += ri * ri;
     acc.v[3] += qi;
     accd.v[0] += (double)di;
-    lm.add(rid, (float)rr, rmax + 2 * 2);
+    lm.add(rid, rr, rmax + 2 * 2);
   }
   lane_flush<4>(acc, cg + ub, CG_STRIDE);
   lane_flush<1>(accd, cg + CG_SD, CG_STRIDE);
@@ -358,7 +385,7 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
                         int* __restrict__ conv, int* __restrict__ iters, int* __restrict__ itp,
                         const R* __restrict__ w, const R* __restrict__ d, double* __restrict__ q,
                         R* __restrict__ qr, R* __restrict__ r, R* __restrict__ p, R* __restrict__ s,
-                        R* __restrict__ y, double* __restrict__ cg, unsigned* __restrict__ rmax, int Rn,
+                        R* __restrict__ y, double* __restrict__ cg, unsigned long long* __restrict__ rmax, int Rn,
                         int* __restrict__ blocks, int* __restrict__ active, unsigned* __restrict__ err,
                         double tol, int max_iter, int use_cond, cudaGraphConditionalHandle cond) {
   if (*active == 0) {
@@ -377,12 +404,12 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
       double* c = cg + (size_t)rr * CG_STRIDE;
       if (kk < 2) c[dn + kk] = 0.0;
       else if (kk < 6) c[un + kk - 2] = 0.0;
-      else rmax[(size_t)rr * 6 + mn * 2 + (kk - 6)] = 0u;
+      else rmax[(size_t)rr * 6 + mn * 2 + (kk - 6)] = 0ull;
     }
   }
   RepAcc<4> acc;
   acc.init();
-  LaneMax lm;
+  LaneMax<R> lm;
   int crid = -1;
   double alpha = 0.0;
   R a = R(0), b = R(0), c = R(0), mprev = R(0);
@@ -418,7 +445,7 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
     acc.v[1] += (double)ri;
     acc.v[2] += (double)(ri * ri);
     acc.v[3] += qi;
-    lm.add(rid, (float)ri, rmax + mb * 2);
+    lm.add(rid, ri, rmax + mb * 2);
   }
   if (crid >= 0) acc.v[0] += (double)py;
   lane_flush<4>(acc, cg + ubuf, CG_STRIDE);
