@@ -116,7 +116,7 @@ typedef struct ctbop_stats {
     int32_t max_cov;          /* largest covalent entry count at the last rebuild */
     int64_t cg_iters_total;   /* summed over all solves */
     int64_t solves;           /* number of charge solves */
-    double  cg_residual_last; /* max-norm bound of H q + chi - mu after the last solve, replica 0 (eV/e) */
+    double  cg_residual_last; /* max_i |H q + chi - mu|_i after the last solve, replica 0 (eV/e) */
     int32_t max_all;          /* largest total entry count at the last rebuild */
     uint32_t error_bits;      /* device-side error bits seen (see ctbop_last_error) */
     double  mean_cov;         /* mean covalent entries (incl. skin) at the last rebuild */
