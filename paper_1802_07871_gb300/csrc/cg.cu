@@ -20,10 +20,12 @@
 // CG scalar are unchanged by adding a constant to r, so each update subtracts
 // the previous mean of r and accumulates the shift (mu = -(mean r + shift)).
 //
-// Precision: the iterate q and every reduction (dots, sums) are FP64; the
-// other vectors, the matrix entries and the gathered y_j are in the working
-// precision (FP32 in the mixed policy). Directions in FP32 do not sum to
-// exactly zero, so after the solve q is shifted uniformly onto sum q = Q.
+// Precision: the iterate q, the recursion vectors r, p, s = H p and every
+// reduction (dots, sums) are FP64 (in FP32 the s = H p recursion loses
+// conjugacy and the iteration stalls); y = D^-1 r, w = H z, d, v, the matrix
+// entries and the gathered y_j are in the working precision (FP32 in the
+// mixed policy). Rounding of y and d keeps sum z from being exactly zero, so
+// after the solve q is shifted uniformly onto sum q = Q.
 //
 // The matrix passes run one thread per atom over its column of the list
 // (entry e of atom i at e * ld + i): a warp load of entry e of 32 consecutive
@@ -264,7 +266,7 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
                           const R* __restrict__ M, const R* __restrict__ Dg, const R* __restrict__ dinv,
                           const int* __restrict__ type, const int* __restrict__ rep, TypeParams T,
                           double* __restrict__ q, const R* __restrict__ qr, const R* __restrict__ d,
-                          R* __restrict__ r, R* __restrict__ y, R* __restrict__ v, double* __restrict__ cg,
+                          double* __restrict__ r, R* __restrict__ y, R* __restrict__ v, double* __restrict__ cg,
                           unsigned long long* __restrict__ rmax, int Rn, int* __restrict__ conv, int* __restrict__ iters,
                           int* __restrict__ blocks, int* __restrict__ active, double tol) {
   const int ub = CG_UPD + 2 * 4;
@@ -272,7 +274,7 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
   RepAcc<1> accd;
   acc.init();
   accd.init();
-  LaneMax<R> lm;
+  LaneMax<double> lm;
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
   int crid = -1;
   double dq = 0.0;
@@ -289,9 +291,8 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
     double qi = q[i] + dq;
     q[i] = qi;
     double ri = -T.chi[type[i]] - ((double)Di * qi + (double)hq + dq * (double)hm);
-    R rr = (R)ri;
-    R yi = dinv[i] * rr;
-    r[i] = rr;
+    R yi = dinv[i] * (R)ri;
+    r[i] = ri;
     y[i] = yi;
     v[i] = Di * di + hd;
     acc.to(rid, cg + ub, CG_STRIDE);
@@ -301,7 +302,7 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
     acc.v[2] += ri * ri;
     acc.v[3] += qi;
     accd.v[0] += (double)di;
-    lm.add(rid, rr, rmax + 2 * 2);
+    lm.add(rid, ri, rmax + 2 * 2);
   }
   lane_flush<4>(acc, cg + ub, CG_STRIDE);
   lane_flush<1>(accd, cg + CG_SD, CG_STRIDE);
@@ -321,7 +322,7 @@ template <class R>
 __global__ void k_cg_mv(int N, int ld, int chunk, const int* __restrict__ nbr, const int* __restrict__ nall,
                         const R* __restrict__ M, const R* __restrict__ Dg, const int* __restrict__ rep,
                         const int* __restrict__ conv, const int* __restrict__ itp, const R* __restrict__ y,
-                        const R* __restrict__ d, const R* __restrict__ v, const R* __restrict__ r,
+                        const R* __restrict__ d, const R* __restrict__ v, const double* __restrict__ r,
                         R* __restrict__ w, double* __restrict__ cg, int Rn, int* __restrict__ blocks,
                         const int* __restrict__ active) {
   if (*active == 0) return;
@@ -331,14 +332,16 @@ __global__ void k_cg_mv(int N, int ld, int chunk, const int* __restrict__ nbr, c
   acc.init();
   int crid = -1;
   R c = R(0);
-  R pg = R(0), pd = R(0);   // working-precision partials for the current replica
+  double pg = 0.0;          // r.z partial (FP64) for the current replica
+  R pd = R(0);              // w.z partial (working precision)
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
   for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
     int rid = rep[i];
     if (conv[rid]) continue;
     if (rid != crid) {
-      if (crid >= 0) { acc.v[0] += (double)pg; acc.v[1] += (double)pd; }
-      pg = pd = R(0);
+      if (crid >= 0) { acc.v[0] += pg; acc.v[1] += (double)pd; }
+      pg = 0.0;
+      pd = R(0);
       acc.to(rid, cg + buf, CG_STRIDE);
       c = (R)ldcg(cg + (size_t)rid * CG_STRIDE + CG_C);
       crid = rid;
@@ -349,10 +352,10 @@ __global__ void k_cg_mv(int N, int ld, int chunk, const int* __restrict__ nbr, c
     R zi = yi - c * d[i];
     R wi = Dg[i] * yi + hy - c * v[i];
     w[i] = wi;
-    pg += r[i] * zi;
+    pg += r[i] * (double)zi;
     pd += wi * zi;
   }
-  if (crid >= 0) { acc.v[0] += (double)pg; acc.v[1] += (double)pd; }
+  if (crid >= 0) { acc.v[0] += pg; acc.v[1] += (double)pd; }
   lane_flush<2>(acc, cg + buf, CG_STRIDE);
   if (last_block(blocks + 2)) {
     int sprev = CG_SCAL + ((it + 1) & 1) * 2;
@@ -384,7 +387,7 @@ template <class R>
 __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* __restrict__ dinv,
                         int* __restrict__ conv, int* __restrict__ iters, int* __restrict__ itp,
                         const R* __restrict__ w, const R* __restrict__ d, double* __restrict__ q,
-                        R* __restrict__ qr, R* __restrict__ r, R* __restrict__ p, R* __restrict__ s,
+                        double* __restrict__ r, double* __restrict__ p, double* __restrict__ s,
                         R* __restrict__ y, double* __restrict__ cg, unsigned long long* __restrict__ rmax, int Rn,
                         int* __restrict__ blocks, int* __restrict__ active, unsigned* __restrict__ err,
                         double tol, int max_iter, int use_cond, cudaGraphConditionalHandle cond) {
@@ -409,10 +412,10 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
   }
   RepAcc<4> acc;
   acc.init();
-  LaneMax<R> lm;
+  LaneMax<double> lm;
   int crid = -1;
-  double alpha = 0.0;
-  R a = R(0), b = R(0), c = R(0), mprev = R(0);
+  double a = 0.0, b = 0.0, mprev = 0.0;
+  R c = R(0);
   R py = R(0);                      // working-precision partial of sum y for the current replica
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
   for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
@@ -423,27 +426,26 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
       py = R(0);
       acc.to(rid, cg + ubuf, CG_STRIDE);
       const double* cc = cg + (size_t)rid * CG_STRIDE;
-      alpha = ldcg(cc + CG_AB);
-      a = (R)alpha;
-      b = (R)ldcg(cc + CG_AB + 1);
+      a = ldcg(cc + CG_AB);
+      b = ldcg(cc + CG_AB + 1);
       c = (R)ldcg(cc + CG_C);
-      mprev = (R)ldcg(cc + CG_M);
+      mprev = ldcg(cc + CG_M);
       crid = rid;
     }
-    R zi = y[i] - c * d[i];
-    R pi = zi + b * p[i];
-    R si = w[i] + b * s[i];
-    double qi = q[i] + alpha * (double)pi;
-    R ri = (r[i] - a * si) - mprev;
-    R yi = dinv[i] * ri;
+    double zi = (double)(y[i] - c * d[i]);   // the same z as the matrix pass formed
+    double pi = zi + b * p[i];
+    double si = (double)w[i] + b * s[i];
+    double qi = q[i] + a * pi;
+    double ri = (r[i] - a * si) - mprev;
+    R yi = dinv[i] * (R)ri;
     p[i] = pi;
     s[i] = si;
     q[i] = qi;
     r[i] = ri;
     y[i] = yi;
     py += yi;
-    acc.v[1] += (double)ri;
-    acc.v[2] += (double)(ri * ri);
+    acc.v[1] += ri;
+    acc.v[2] += ri * ri;
     acc.v[3] += qi;
     lm.add(rid, ri, rmax + mb * 2);
   }
@@ -456,7 +458,7 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
     for (int rr = threadIdx.x; rr < Rn; rr += blockDim.x)
       if (!conv[rr]) {
         double* cc = cg + (size_t)rr * CG_STRIDE;
-        cc[CG_SHIFT] += (double)(R)cc[CG_M];
+        cc[CG_SHIFT] += cc[CG_M];
       }
     __syncthreads();
     int all = check_replicas(Rn, cg, rmax, conv, iters, ubuf, mb, it + 1, tol, 0);
@@ -511,7 +513,7 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
   int grid = atom_dims(S.N, S.nsm, (const void*)k_cg_init<R>, 256, chunk);
   k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.ld, chunk, S.nbr, S.nall, (const R*)S.M, (const R*)S.Dg,
                                      (const R*)S.dinv, S.type, S.rep, T, S.q, (const R*)S.qr, (const R*)S.cd,
-                                     (R*)S.cr, (R*)S.cy, (R*)S.cv, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
+                                     S.cr, (R*)S.cy, (R*)S.cv, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
                                      S.cg_blocks, S.cg_active, tol);
 }
 
@@ -522,7 +524,7 @@ void launch_cg_mv(const DevState& S, cudaStream_t st) {
   int grid = atom_dims(S.N, S.nsm, (const void*)k_cg_mv<R>, 256, chunk);
   k_cg_mv<R><<<grid, 256, 0, st>>>(S.N, S.ld, chunk, S.nbr, S.nall, (const R*)S.M, (const R*)S.Dg, S.rep,
                                    S.cg_conv, S.cg_it, (const R*)S.cy, (const R*)S.cd, (const R*)S.cv,
-                                   (const R*)S.cr, (R*)S.cw, S.cg, S.R, S.cg_blocks, S.cg_active);
+                                   S.cr, (R*)S.cw, S.cg, S.R, S.cg_blocks, S.cg_active);
 }
 
 template <class R>
@@ -531,8 +533,7 @@ void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
   int chunk;
   int grid = atom_dims(S.N, S.nsm, (const void*)k_cg_up<R>, 256, chunk);
   k_cg_up<R><<<grid, 256, 0, st>>>(S.N, chunk, S.rep, (const R*)S.dinv, S.cg_conv, S.cg_iters, S.cg_it,
-                                   (const R*)S.cw, (const R*)S.cd, S.q, (R*)S.qr, (R*)S.cr, (R*)S.cp, (R*)S.cs,
-                                   (R*)S.cy, S.cg, S.cg_rmax, S.R, S.cg_blocks, S.cg_active, S.err, cfg.tol,
+                                   (const R*)S.cw, (const R*)S.cd, S.q, S.cr, S.cp, S.cs, (R*)S.cy, S.cg, S.cg_rmax, S.R, S.cg_blocks, S.cg_active, S.err, cfg.tol,
                                    cfg.max_iter, cfg.use_cond, cfg.cond);
 }
 
