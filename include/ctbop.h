@@ -101,7 +101,7 @@ typedef struct ctbop_options {
     int32_t cg_max_iter;  /* charge-solve iteration cap (default 200) */
     double  cg_tol;       /* stop when max_i |H q + chi - mu|_i over a replica (the max-norm of
                            the stationarity residual) is below cg_tol (eV/e); 0 = policy default
-                           (FP64 1e-11, MIXED 3e-6) */
+                           (FP64 1e-11, MIXED 1e-5) */
     double  skin;         /* neighbour-list skin (A, default 0.3) */
     int32_t cap_cov;      /* covalent entries per atom; 0 = sized from the first configuration */
     int32_t cap_all;      /* all entries (charge cutoff) per atom; 0 = sized automatically */

@@ -332,7 +332,7 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
 // ------------------------------------------------------------- evaluation
 static double cg_tol(const ctbop_system* s) {
   if (s->o.cg_tol > 0) return s->o.cg_tol;
-  return s->mixed ? 3e-6 : 1e-11;
+  return s->mixed ? 1e-5 : 1e-11;
 }
 
 template <class Rr>

@@ -14,11 +14,12 @@ TOL = {
     "mixed": dict(force=1e-4, energy=1e-6, charge=1e-5, virial=1e-4, eatom=2e-5, mu=1e-5),
     # Stress geometries in mixed precision: FP32 cell-local positions carry
     # ~5e-7 A of rounding, so a term's energy error is about |dE_term/dr| x
-    # 5e-7 A. In cells smaller than the charge cutoff every periodic image of
-    # a pair rounds alike (~240 correlated terms per atom), and random
+    # 5e-7 A, and each stored FP32 charge-matrix entry is rounded by ~6e-8
+    # relative. In cells smaller than the charge cutoff every periodic image
+    # of a pair rounds alike (~240 correlated terms per atom), and random
     # clusters hold pairs compressed to 1.45 A with 50 eV repulsive terms;
-    # there the error no longer averages out. Forces keep the 1e-4 bar.
-    "mixed_stress": dict(force=1e-4, energy=5e-6, charge=1e-5, virial=1e-4, eatom=1e-4, mu=1e-5),
+    # there the errors no longer average out. Forces keep the 1e-4 bar.
+    "mixed_stress": dict(force=1e-4, energy=5e-6, charge=3e-5, virial=1e-4, eatom=1e-4, mu=3e-5),
 }
 
 
