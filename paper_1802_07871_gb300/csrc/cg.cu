@@ -318,6 +318,10 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
 
 // w = H z = H y - c v with z = y - c d, and the dots (r.z, w.z); the last
 // block turns them into the step lengths alpha, beta of this iteration.
+// r.z is formed from r - mean(r): rounding leaves sum z slightly off zero,
+// and before the first re-centring r carries its whole mean (-mu), whose
+// product with that sum would swamp r.z once the residual is small (warm
+// starts near the tolerance then diverge).
 template <class R>
 __global__ void k_cg_mv(int N, int ld, int chunk, const int* __restrict__ nbr, const int* __restrict__ nall,
                         const R* __restrict__ M, const R* __restrict__ Dg, const int* __restrict__ rep,
@@ -332,6 +336,7 @@ __global__ void k_cg_mv(int N, int ld, int chunk, const int* __restrict__ nbr, c
   acc.init();
   int crid = -1;
   R c = R(0);
+  double m = 0.0;           // mean of the stored r (r.z is formed from r - m)
   double pg = 0.0;          // r.z partial (FP64) for the current replica
   R pd = R(0);              // w.z partial (working precision)
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
@@ -344,6 +349,7 @@ __global__ void k_cg_mv(int N, int ld, int chunk, const int* __restrict__ nbr, c
       pd = R(0);
       acc.to(rid, cg + buf, CG_STRIDE);
       c = (R)ldcg(cg + (size_t)rid * CG_STRIDE + CG_C);
+      m = ldcg(cg + (size_t)rid * CG_STRIDE + CG_M);
       crid = rid;
     }
     R hy, unused, unused2;
@@ -352,7 +358,7 @@ __global__ void k_cg_mv(int N, int ld, int chunk, const int* __restrict__ nbr, c
     R zi = yi - c * d[i];
     R wi = Dg[i] * yi + hy - c * v[i];
     w[i] = wi;
-    pg += r[i] * (double)zi;
+    pg += (r[i] - m) * (double)zi;
     pd += wi * zi;
   }
   if (crid >= 0) { acc.v[0] += pg; acc.v[1] += (double)pd; }
