@@ -236,16 +236,13 @@ static int alloc_atoms(ctbop_system* s) {
   S.u = u;
   CK(dalloc(s->atom_buf, &S.cell_atoms, (size_t)N));
   {
-    void** rv[] = {&S.Dg, &S.dinv, &S.cy, &S.cw, &S.cd, &S.cv, &S.qr};
+    void** rv[] = {&S.Dg, &S.dinv, &S.cy, &S.cw, &S.cd, &S.cv, &S.qr, &S.cr, &S.cp, &S.cs};
     for (void** pp : rv) {
       unsigned char* b = nullptr;
       CK(dalloc(s->atom_buf, &b, (size_t)N * rs));
       *pp = b;
     }
   }
-  CK(dalloc(s->atom_buf, &S.cr, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.cp, (size_t)N));
-  CK(dalloc(s->atom_buf, &S.cs, (size_t)N));
   CK(dalloc(s->atom_buf, &S.cqh1, (size_t)N));
   CK(dalloc(s->atom_buf, &S.cqh2, (size_t)N));
   CK(dalloc(s->atom_buf, &S.ncov, (size_t)N));
@@ -256,8 +253,8 @@ static int alloc_atoms(ctbop_system* s) {
   CK(cudaMemset(S.frozen, 0, (size_t)N));
   CK(cudaMemset(S.cqh1, 0, sizeof(double) * (size_t)N));
   CK(cudaMemset(S.cqh2, 0, sizeof(double) * (size_t)N));
-  CK(cudaMemset(S.cp, 0, sizeof(double) * (size_t)N));
-  CK(cudaMemset(S.cs, 0, sizeof(double) * (size_t)N));
+  CK(cudaMemset(S.cp, 0, (size_t)N * rs));
+  CK(cudaMemset(S.cs, 0, (size_t)N * rs));
   CK(cudaMemset(S.qr, 0, (size_t)N * rs));
   // replica ids
   std::vector<int> rep(N);

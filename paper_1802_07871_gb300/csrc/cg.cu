@@ -75,8 +75,9 @@ __device__ inline double dunmap(unsigned long long u) {
   return __longlong_as_double((long long)b);
 }
 
-// Per-lane running max of r and of -r for one replica (working precision);
-// merged per warp and flushed with atomicMax on the order-preserving map.
+// Per-thread running max of r and of -r for one replica. finish() merges
+// them over the warp and the block (one atomicMax per block and replica, on
+// the order-preserving map); every thread of the block must call it.
 template <class R>
 struct LaneMax {
   int rep = -1;
@@ -94,17 +95,76 @@ struct LaneMax {
     lo = fmax(lo, -v);
   }
   __device__ inline void finish(unsigned long long* base) {
+    __shared__ int s_rep[32];
+    __shared__ R s_hi[32], s_lo[32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int r0 = __shfl_sync(CT_FULL, rep, 0);
-    if (__all_sync(CT_FULL, rep == r0)) {
+    bool same = __all_sync(CT_FULL, rep == r0);
+    if (same) {
       for (int o = 16; o > 0; o >>= 1) {
         hi = fmax(hi, __shfl_xor_sync(CT_FULL, hi, o));
         lo = fmax(lo, __shfl_xor_sync(CT_FULL, lo, o));
       }
-      if ((threadIdx.x & 31) != 0) rep = -1;
+    } else {
+      flush(base);   // a replica boundary inside the warp: per-lane atomics
     }
-    flush(base);
+    if (lane == 0) {
+      s_rep[warp] = same ? r0 : -1;
+      s_hi[warp] = hi;
+      s_lo[warp] = lo;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int nw = blockDim.x >> 5;
+      rep = -1;
+      hi = lo = -R(INFINITY);
+      for (int w = 0; w < nw; ++w) {
+        if (s_rep[w] < 0) continue;
+        if (s_rep[w] != rep) { flush(base); rep = s_rep[w]; }
+        hi = fmax(hi, s_hi[w]);
+        lo = fmax(lo, s_lo[w]);
+      }
+      flush(base);
+    }
+    __syncthreads();
   }
 };
+
+// Sums of one value set per thread (rid < 0: none) into out[rid * stride +
+// k]: a warp sum in the working precision when the warp holds one replica
+// (the common case), per-lane atomics otherwise, then one FP64 atomic per
+// block and replica. Every thread of the block must call it.
+template <class R, int NV>
+__device__ inline void flush_values(int rid, const R (&v)[NV], double* out, int stride) {
+  int lane = threadIdx.x & 31;
+  int r0 = __shfl_sync(CT_FULL, rid, 0);
+  bool same = __all_sync(CT_FULL, rid == r0);
+  RepAcc<NV> w;
+  w.init();
+  if (same) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      R t = warp_sum(v[k]);
+      if (lane == 0) w.v[k] = (double)t;
+    }
+    if (lane == 0) w.rep = r0;
+  } else if (rid >= 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) atomicAdd(out + (size_t)rid * stride + k, (double)v[k]);
+  }
+  block_flush<NV>(w, out, stride);
+}
+
+// Blocks for an element-wise pass over 256-atom tiles: at most what fits on
+// the device at once, so each thread takes several atoms and the reductions
+// are paid once per thread, not once per atom.
+static int stride_grid(int N, int nsm, const void* kernel) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+  long long tiles = ((long long)N + 255) / 256, slots = (long long)nsm * occ;
+  long long g = tiles < slots ? tiles : slots;
+  return (int)(g < 1 ? 1 : g);
+}
 
 // Convergence test for every unconverged replica from the sums (sum y,
 // sum r, sum r^2, sum q) at upd_off and the maxima of buffer mbuf; records
@@ -259,14 +319,73 @@ __device__ inline void row_sum(int i, int na, int ld, const int* __restrict__ nb
   hm = am.value();
 }
 
+// Row sum sum_e M_e x_j(e) of atom i for the matrix pass, software-pipelined:
+// the list indices and entries of the next CT_MV_BATCH entries are loaded
+// before the current batch's x_j are gathered, so the streamed list (the
+// bound of this pass) always has loads in flight. Each batch is summed as a
+// small tree and only the running sum is compensated: the error that limits
+// the solve comes from adding small terms to a large running sum, not from
+// the few terms of a batch.
+#ifndef CT_MV_BATCH
+#define CT_MV_BATCH 16
+#endif
+#ifndef CT_MV_MINB
+#define CT_MV_MINB 1
+#endif
+template <class R>
+__device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict__ nbr, const R* __restrict__ M,
+                                   const R* __restrict__ x) {
+  constexpr int B = CT_MV_BATCH;
+  const int* pn = nbr + i;
+  const R* pm = M + i;
+  int jn[B];
+  R mn[B];
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    bool ok = k < na;
+    jn[k] = ok ? __ldg(pn + (size_t)k * ld) : i;
+    mn[k] = ok ? __ldg(pm + (size_t)k * ld) : R(0);
+  }
+  RowAcc<R> acc;
+  for (int e = 0; e < na; e += B) {
+    int jc[B];
+    R mc[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      jc[k] = jn[k];
+      mc[k] = mn[k];
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      int en = e + B + k;
+      bool ok = en < na;
+      jn[k] = ok ? __ldg(pn + (size_t)en * ld) : i;
+      mn[k] = ok ? __ldg(pm + (size_t)en * ld) : R(0);
+    }
+    R t[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) t[k] = mc[k] * __ldg(x + jc[k]);
+#pragma unroll
+    for (int w = 1; w < B; w <<= 1)
+#pragma unroll
+      for (int k = 0; k + w < B; k += 2 * w) t[k] += t[k + w];
+    acc.add(t[0]);
+  }
+  return acc.value();
+}
+
 // r = -(H q0 + chi), y = D^-1 r, v = H d; sums (sum y, sum r, sum r^2,
-// sum d) and the maxima of r, -r for the initial test (update buffer 2).
+// sum q, sum d) and the maxima of r, -r for the initial test (update buffer
+// 2). r is stored shifted by the previous solve's mean (-mu of that solve),
+// which keeps the stored values small: in FP32 the whole mean of r (several
+// eV/e) would otherwise cost about 1e-7 of it in every element. The shift
+// starts the accumulated one, so mu = -(mean of stored r + shift) holds.
 template <class R>
 __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr, const int* __restrict__ nall,
                           const R* __restrict__ M, const R* __restrict__ Dg, const R* __restrict__ dinv,
                           const int* __restrict__ type, const int* __restrict__ rep, TypeParams T,
                           double* __restrict__ q, const R* __restrict__ qr, const R* __restrict__ d,
-                          double* __restrict__ r, R* __restrict__ y, R* __restrict__ v, double* __restrict__ cg,
+                          R* __restrict__ r, R* __restrict__ y, R* __restrict__ v, double* __restrict__ cg,
                           unsigned long long* __restrict__ rmax, int Rn, int* __restrict__ conv, int* __restrict__ iters,
                           int* __restrict__ blocks, int* __restrict__ active, double tol) {
   const int ub = CG_UPD + 2 * 4;
@@ -274,14 +393,17 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
   RepAcc<1> accd;
   acc.init();
   accd.init();
-  LaneMax<double> lm;
+  LaneMax<R> lm;
   int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
   int crid = -1;
-  double dq = 0.0;
+  double dq = 0.0, s0 = 0.0;
   for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
     int rid = rep[i];
     if (rid != crid) {
-      dq = ldcg(cg + (size_t)rid * CG_STRIDE + CG_DQ);
+      const double* cc = cg + (size_t)rid * CG_STRIDE;
+      dq = ldcg(cc + CG_DQ);
+      double mp = ldcg(cc + CG_MU);
+      s0 = isfinite(mp) ? -mp : 0.0;
       crid = rid;
     }
     R hq, hd, hm;
@@ -290,16 +412,16 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
     // the guess shifted by dq: H (q0 + dq 1) = D (q0 + dq) + sum M q0_j + dq sum M
     double qi = q[i] + dq;
     q[i] = qi;
-    double ri = -T.chi[type[i]] - ((double)Di * qi + (double)hq + dq * (double)hm);
-    R yi = dinv[i] * (R)ri;
+    R ri = (R)(-T.chi[type[i]] - ((double)Di * qi + (double)hq + dq * (double)hm) - s0);
+    R yi = dinv[i] * ri;
     r[i] = ri;
     y[i] = yi;
     v[i] = Di * di + hd;
     acc.to(rid, cg + ub, CG_STRIDE);
     accd.to(rid, cg + CG_SD, CG_STRIDE);
     acc.v[0] += (double)yi;
-    acc.v[1] += ri;
-    acc.v[2] += ri * ri;
+    acc.v[1] += (double)ri;
+    acc.v[2] += (double)ri * (double)ri;
     acc.v[3] += qi;
     accd.v[0] += (double)di;
     lm.add(rid, ri, rmax + 2 * 2);
@@ -308,6 +430,12 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
   lane_flush<1>(accd, cg + CG_SD, CG_STRIDE);
   lm.finish(rmax + 2 * 2);
   if (last_block(blocks)) {
+    for (int rr = threadIdx.x; rr < Rn; rr += blockDim.x) {
+      double* cc = cg + (size_t)rr * CG_STRIDE;
+      double mp = cc[CG_MU];
+      cc[CG_SHIFT] = isfinite(mp) ? -mp : 0.0;   // the shift every thread applied
+    }
+    __syncthreads();
     int all = check_replicas(Rn, cg, rmax, conv, iters, ub, 2, 0, tol, 1);
     if (threadIdx.x == 0) {
       blocks[0] = 0;
@@ -323,46 +451,33 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
 // product with that sum would swamp r.z once the residual is small (warm
 // starts near the tolerance then diverge).
 template <class R>
-__global__ void k_cg_mv(int N, int ld, int chunk, const int* __restrict__ nbr, const int* __restrict__ nall,
-                        const R* __restrict__ M, const R* __restrict__ Dg, const int* __restrict__ rep,
-                        const int* __restrict__ conv, const int* __restrict__ itp, const R* __restrict__ y,
-                        const R* __restrict__ d, const R* __restrict__ v, const double* __restrict__ r,
-                        R* __restrict__ w, double* __restrict__ cg, int Rn, int* __restrict__ blocks,
-                        const int* __restrict__ active) {
+__global__ void __launch_bounds__(256, CT_MV_MINB)
+    k_cg_mv(int N, int ld, const int* __restrict__ nbr, const int* __restrict__ nall, const R* __restrict__ M,
+            const R* __restrict__ Dg, const int* __restrict__ rep, const int* __restrict__ conv,
+            const int* __restrict__ itp, const R* __restrict__ y, const R* __restrict__ d, const R* __restrict__ v,
+            const R* __restrict__ r, R* __restrict__ w, double* __restrict__ cg, int Rn,
+            int* __restrict__ blocks, const int* __restrict__ active) {
   if (*active == 0) return;
   int it = *itp;
   int buf = CG_DOTS + (it & 1) * 2;
-  RepAcc<2> acc;
-  acc.init();
-  int crid = -1;
-  R c = R(0);
-  double m = 0.0;           // mean of the stored r (r.z is formed from r - m)
-  double pg = 0.0;          // r.z partial (FP64) for the current replica
-  R pd = R(0);              // w.z partial (working precision)
-  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
-  for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
-    int rid = rep[i];
-    if (conv[rid]) continue;
-    if (rid != crid) {
-      if (crid >= 0) { acc.v[0] += pg; acc.v[1] += (double)pd; }
-      pg = 0.0;
-      pd = R(0);
-      acc.to(rid, cg + buf, CG_STRIDE);
-      c = (R)ldcg(cg + (size_t)rid * CG_STRIDE + CG_C);
-      m = ldcg(cg + (size_t)rid * CG_STRIDE + CG_M);
-      crid = rid;
-    }
-    R hy, unused, unused2;
-    row_sum<R, 1>(i, nall[i], ld, nbr, M, y, nullptr, hy, unused, unused2);
+  R dots[2] = {R(0), R(0)};
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int rid = i < N ? rep[i] : -1;
+  if (rid >= 0 && !conv[rid]) {
+    const double* cc = cg + (size_t)rid * CG_STRIDE;
+    R c = (R)ldcg(cc + CG_C);
+    R m = (R)ldcg(cc + CG_M);   // mean of the stored r
+    R hy = row_sum_stream<R>(i, nall[i], ld, nbr, M, y);
     R yi = y[i];
     R zi = yi - c * d[i];
     R wi = Dg[i] * yi + hy - c * v[i];
     w[i] = wi;
-    pg += (r[i] - m) * (double)zi;
-    pd += wi * zi;
+    dots[0] = (r[i] - m) * zi;   // r.z
+    dots[1] = wi * zi;           // w.z
+  } else {
+    rid = -1;
   }
-  if (crid >= 0) { acc.v[0] += pg; acc.v[1] += (double)pd; }
-  lane_flush<2>(acc, cg + buf, CG_STRIDE);
+  flush_values<R, 2>(rid, dots, cg + buf, CG_STRIDE);
   if (last_block(blocks + 2)) {
     int sprev = CG_SCAL + ((it + 1) & 1) * 2;
     int scur = CG_SCAL + (it & 1) * 2;
@@ -389,14 +504,16 @@ __global__ void k_cg_mv(int N, int ld, int chunk, const int* __restrict__ nbr, c
 }
 
 // Element-wise update; the sums and maxima for the next c and the test.
+// Threads take 256-atom tiles strided over the grid; per-thread partial sums
+// in the working precision (a few atoms each), FP64 across warps and blocks.
 template <class R>
-__global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* __restrict__ dinv,
-                        int* __restrict__ conv, int* __restrict__ iters, int* __restrict__ itp,
-                        const R* __restrict__ w, const R* __restrict__ d, double* __restrict__ q,
-                        double* __restrict__ r, double* __restrict__ p, double* __restrict__ s,
-                        R* __restrict__ y, double* __restrict__ cg, unsigned long long* __restrict__ rmax, int Rn,
-                        int* __restrict__ blocks, int* __restrict__ active, unsigned* __restrict__ err,
-                        double tol, int max_iter, int use_cond, cudaGraphConditionalHandle cond) {
+__global__ void __launch_bounds__(256)
+    k_cg_up(int N, const int* __restrict__ rep, const R* __restrict__ dinv, int* __restrict__ conv,
+            int* __restrict__ iters, int* __restrict__ itp, const R* __restrict__ w, const R* __restrict__ d,
+            double* __restrict__ q, R* __restrict__ r, R* __restrict__ p, R* __restrict__ s,
+            R* __restrict__ y, double* __restrict__ cg, unsigned long long* __restrict__ rmax, int Rn,
+            int* __restrict__ blocks, int* __restrict__ active, unsigned* __restrict__ err, double tol,
+            int max_iter, int use_cond, cudaGraphConditionalHandle cond) {
   if (*active == 0) {
     // nothing left to do (converged at the start): end the loop
     if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
@@ -416,47 +533,52 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
       else rmax[(size_t)rr * 6 + mn * 2 + (kk - 6)] = 0ull;
     }
   }
-  RepAcc<4> acc;
-  acc.init();
-  LaneMax<double> lm;
+  LaneMax<R> lm;
   int crid = -1;
-  double a = 0.0, b = 0.0, mprev = 0.0;
-  R c = R(0);
-  R py = R(0);                      // working-precision partial of sum y for the current replica
-  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
-  for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
+  R a = R(0), b = R(0), c = R(0), mprev = R(0);
+  double da = 0.0;
+  R part[3] = {R(0), R(0), R(0)};   // sum y, sum r, sum r^2
+  double pq[1] = {0.0};             // sum q
+  for (int t = blockIdx.x; (long long)t * 256 < N; t += gridDim.x) {
+    int i = t * 256 + (int)threadIdx.x;
+    if (i >= N) break;
     int rid = rep[i];
     if (conv[rid]) continue;
     if (rid != crid) {
-      if (crid >= 0) acc.v[0] += (double)py;
-      py = R(0);
-      acc.to(rid, cg + ubuf, CG_STRIDE);
+      if (crid >= 0) {   // a replica boundary in this thread's atoms
+        double* o = cg + (size_t)crid * CG_STRIDE + ubuf;
+        for (int k = 0; k < 3; ++k) atomicAdd(o + k, (double)part[k]);
+        atomicAdd(o + 3, pq[0]);
+        part[0] = part[1] = part[2] = R(0);
+        pq[0] = 0.0;
+      }
       const double* cc = cg + (size_t)rid * CG_STRIDE;
-      a = ldcg(cc + CG_AB);
-      b = ldcg(cc + CG_AB + 1);
+      a = (R)ldcg(cc + CG_AB);
+      b = (R)ldcg(cc + CG_AB + 1);
       c = (R)ldcg(cc + CG_C);
-      mprev = ldcg(cc + CG_M);
+      mprev = (R)ldcg(cc + CG_M);
+      da = (double)a;   // q and r take the same step length
       crid = rid;
     }
-    double zi = (double)(y[i] - c * d[i]);   // the same z as the matrix pass formed
-    double pi = zi + b * p[i];
-    double si = (double)w[i] + b * s[i];
-    double qi = q[i] + a * pi;
-    double ri = (r[i] - a * si) - mprev;
-    R yi = dinv[i] * (R)ri;
+    R zi = y[i] - c * d[i];   // the same z as the matrix pass formed
+    R pi = zi + b * p[i];
+    R si = w[i] + b * s[i];
+    double qi = q[i] + da * (double)pi;
+    R ri = (r[i] - a * si) - mprev;
+    R yi = dinv[i] * ri;
     p[i] = pi;
     s[i] = si;
     q[i] = qi;
     r[i] = ri;
     y[i] = yi;
-    py += yi;
-    acc.v[1] += ri;
-    acc.v[2] += ri * ri;
-    acc.v[3] += qi;
+    part[0] += yi;
+    part[1] += ri;
+    part[2] += ri * ri;
+    pq[0] += qi;
     lm.add(rid, ri, rmax + mb * 2);
   }
-  if (crid >= 0) acc.v[0] += (double)py;
-  lane_flush<4>(acc, cg + ubuf, CG_STRIDE);
+  flush_values<R, 3>(crid, part, cg + ubuf, CG_STRIDE);
+  flush_values<double, 1>(crid, pq, cg + ubuf + 3, CG_STRIDE);
   lm.finish(rmax + mb * 2);
   if (last_block(blocks + 1)) {
     // the mean this launch subtracted joins the accumulated shift (the value
@@ -464,7 +586,7 @@ __global__ void k_cg_up(int N, int chunk, const int* __restrict__ rep, const R* 
     for (int rr = threadIdx.x; rr < Rn; rr += blockDim.x)
       if (!conv[rr]) {
         double* cc = cg + (size_t)rr * CG_STRIDE;
-        cc[CG_SHIFT] += cc[CG_M];
+        cc[CG_SHIFT] += (double)(R)cc[CG_M];
       }
     __syncthreads();
     int all = check_replicas(Rn, cg, rmax, conv, iters, ubuf, mb, it + 1, tol, 0);
@@ -519,28 +641,26 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
   int grid = atom_dims(S.N, S.nsm, (const void*)k_cg_init<R>, 256, chunk);
   k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.ld, chunk, S.nbr, S.nall, (const R*)S.M, (const R*)S.Dg,
                                      (const R*)S.dinv, S.type, S.rep, T, S.q, (const R*)S.qr, (const R*)S.cd,
-                                     S.cr, (R*)S.cy, (R*)S.cv, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
+                                     (R*)S.cr, (R*)S.cy, (R*)S.cv, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
                                      S.cg_blocks, S.cg_active, tol);
 }
 
 template <class R>
 void launch_cg_mv(const DevState& S, cudaStream_t st) {
   if (S.N == 0) return;
-  int chunk;
-  int grid = atom_dims(S.N, S.nsm, (const void*)k_cg_mv<R>, 256, chunk);
-  k_cg_mv<R><<<grid, 256, 0, st>>>(S.N, S.ld, chunk, S.nbr, S.nall, (const R*)S.M, (const R*)S.Dg, S.rep,
-                                   S.cg_conv, S.cg_it, (const R*)S.cy, (const R*)S.cd, (const R*)S.cv,
-                                   S.cr, (R*)S.cw, S.cg, S.R, S.cg_blocks, S.cg_active);
+  k_cg_mv<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nbr, S.nall, (const R*)S.M, (const R*)S.Dg, S.rep,
+                                                S.cg_conv, S.cg_it, (const R*)S.cy, (const R*)S.cd, (const R*)S.cv,
+                                                (const R*)S.cr, (R*)S.cw, S.cg, S.R, S.cg_blocks, S.cg_active);
 }
 
 template <class R>
 void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
   if (S.N == 0) return;
-  int chunk;
-  int grid = atom_dims(S.N, S.nsm, (const void*)k_cg_up<R>, 256, chunk);
-  k_cg_up<R><<<grid, 256, 0, st>>>(S.N, chunk, S.rep, (const R*)S.dinv, S.cg_conv, S.cg_iters, S.cg_it,
-                                   (const R*)S.cw, (const R*)S.cd, S.q, S.cr, S.cp, S.cs, (R*)S.cy, S.cg, S.cg_rmax, S.R, S.cg_blocks, S.cg_active, S.err, cfg.tol,
-                                   cfg.max_iter, cfg.use_cond, cfg.cond);
+  int grid = stride_grid(S.N, S.nsm, (const void*)k_cg_up<R>);
+  k_cg_up<R><<<grid, 256, 0, st>>>(S.N, S.rep, (const R*)S.dinv, S.cg_conv, S.cg_iters, S.cg_it, (const R*)S.cw,
+                                   (const R*)S.cd, S.q, (R*)S.cr, (R*)S.cp, (R*)S.cs, (R*)S.cy, S.cg, S.cg_rmax,
+                                   S.R, S.cg_blocks, S.cg_active, S.err, cfg.tol, cfg.max_iter, cfg.use_cond,
+                                   cfg.cond);
 }
 
 template <class R>

@@ -62,7 +62,7 @@ struct DevState {
   void *Dg = nullptr, *dinv = nullptr;   // Real[N]: Hessian diagonal without self-images, Jacobi inverse
   // CG: the iterate is q itself (FP64); the rest in the working precision
   double *cqh1 = nullptr, *cqh2 = nullptr;  // q of the previous two solves
-  double *cr = nullptr, *cp = nullptr, *cs = nullptr;  // r, p, s = H p (FP64)
+  void *cr = nullptr, *cp = nullptr, *cs = nullptr;  // Real[N]: r (shifted), p, s = H p
   void *cy = nullptr, *cw = nullptr, *cd = nullptr, *cv = nullptr;  // Real[N]: y = D^-1 r, w = H z, d = D^-1 1, v = H d
   unsigned long long* cg_rmax = nullptr;  // [R][3 buffers][2]: max r, max -r (order-preserving map)
   void* qr = nullptr;           // Real[N]: charges in the working precision
