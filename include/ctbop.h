@@ -121,6 +121,7 @@ typedef struct ctbop_stats {
     uint32_t error_bits;      /* device-side error bits seen (see ctbop_last_error) */
     double  mean_cov;         /* mean covalent entries (incl. skin) at the last rebuild */
     double  mean_all;         /* mean total entries at the last rebuild */
+    double  cg_residual_start; /* max_i |H q0 + chi - mu|_i of the last solve's starting guess, replica 0 (eV/e) */
 } ctbop_stats;
 
 typedef struct ctbop_system ctbop_system;

@@ -236,7 +236,7 @@ static int alloc_atoms(ctbop_system* s) {
   S.u = u;
   CK(dalloc(s->atom_buf, &S.cell_atoms, (size_t)N));
   {
-    void** rv[] = {&S.Dg, &S.dinv, &S.cy, &S.cw, &S.cd, &S.cv, &S.qr, &S.cr, &S.cp, &S.cs};
+    void** rv[] = {&S.Dg, &S.dinv, &S.cy, &S.cw, &S.cd, &S.cv, &S.qr, &S.cr, &S.cp, &S.cs, &S.cdq};
     for (void** pp : rv) {
       unsigned char* b = nullptr;
       CK(dalloc(s->atom_buf, &b, (size_t)N * rs));
@@ -548,7 +548,7 @@ static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double 
       rc = timed(5, 1, [&] { launch_cg_mv<Rr>(S, st); });
       if (!rc) rc = timed(6, 1, [&] { launch_cg_up<Rr>(S, cfg, st); });
     }
-    if (!rc) rc = timed(7, 1, [&] { launch_cg_end<Rr>(S, st); });
+    if (!rc) rc = timed(7, 2, [&] { launch_cg_end<Rr>(S, st); });
     if (!rc) rc = timed(8, 1, [&] { launch_cov_force<Rr>(S, P, s->T, st); });
     if (!rc) rc = timed(9, 1, [&] { launch_coul_gather<Rr>(S, P, s->T, 1, 0.5 * dt, st); });
     if (!rc) {
@@ -932,8 +932,10 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   CK(cudaMemcpy(&tot, S.cg_total, sizeof(tot), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&it, S.cg_it, sizeof(it), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost));
-  double res = 0;
+  double res = 0, res0 = 0;
   CK(cudaMemcpy(&res, S.cg + CG_RESMAX, sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&res0, S.cg + CG_RES0, sizeof(double), cudaMemcpyDeviceToHost));
+  st->cg_residual_start = res0;
   st->error_bits = bits;
   st->rebuilds = rb;
   st->cg_iters_total = tot;

@@ -167,9 +167,8 @@ static int stride_grid(int N, int nsm, const void* kernel) {
 }
 
 // Convergence test for every unconverged replica from the sums (sum y,
-// sum r, sum r^2, sum q) at upd_off and the maxima of buffer mbuf; records
-// the mean of r for the next re-centring, c for the next matrix pass and the
-// shift that restores sum q = Q.
+// sum r, sum r^2) at upd_off and the maxima of buffer mbuf; records the mean
+// of r for the next re-centring and c for the next matrix pass.
 __device__ inline int check_replicas(int R, double* cg, const unsigned long long* rmax, int* conv, int* iters,
                                      int upd_off,
                                      int mbuf, int it_done, double tol, int first) {
@@ -178,7 +177,7 @@ __device__ inline int check_replicas(int R, double* cg, const unsigned long long
     if (conv[r]) continue;
     double* c = cg + (size_t)r * CG_STRIDE;
     const double* u4 = c + upd_off;
-    double sy = ldcg(u4 + 0), sr = ldcg(u4 + 1), srr = ldcg(u4 + 2), sq = ldcg(u4 + 3);
+    double sy = ldcg(u4 + 0), sr = ldcg(u4 + 1), srr = ldcg(u4 + 2);
     double hi = dunmap(__ldcg(rmax + (size_t)r * 6 + mbuf * 2));
     double lo = dunmap(__ldcg(rmax + (size_t)r * 6 + mbuf * 2 + 1));
     double nat = c[CG_NAT];
@@ -191,7 +190,6 @@ __device__ inline int check_replicas(int R, double* cg, const unsigned long long
     c[CG_MU] = -(m + c[CG_SHIFT]);
     c[CG_RES] = rms;
     c[CG_RESMAX] = bound;
-    c[CG_DQ] = nat > 0 ? (c[CG_Q] - sq) / nat : 0.0;
     if (first) c[CG_RES0] = bound;
     double sd = c[CG_SD];
     c[CG_C] = sd != 0.0 ? sy / sd : 0.0;
@@ -212,6 +210,7 @@ __global__ void k_cg_prep(int R, double* __restrict__ cg, unsigned long long* __
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     double* c = cg + (size_t)r * CG_STRIDE;
     for (int k = 0; k < CG_MU; ++k) c[k] = 0.0;
+    c[CG_SQF] = 0.0;
     for (int k = 0; k < 6; ++k) rmax[(size_t)r * 6 + k] = 0ull;
     conv[r] = 0;
     iters[r] = 0;
@@ -335,7 +334,7 @@ __device__ inline void row_sum(int i, int na, int ld, const int* __restrict__ nb
 template <class R>
 __device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict__ nbr, const R* __restrict__ M,
                                    const R* __restrict__ x) {
-  constexpr int B = CT_MV_BATCH;
+  constexpr int B = sizeof(R) == 4 ? CT_MV_BATCH : CT_MV_BATCH / 2;   // FP64: half the entries in flight
   const int* pn = nbr + i;
   const R* pm = M + i;
   int jn[B];
@@ -374,8 +373,8 @@ __device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict_
   return acc.value();
 }
 
-// r = -(H q0 + chi), y = D^-1 r, v = H d; sums (sum y, sum r, sum r^2,
-// sum q, sum d) and the maxima of r, -r for the initial test (update buffer
+// r = -(H q0 + chi), y = D^-1 r, v = H d, dq = 0; sums (sum y, sum r,
+// sum r^2, sum d) and the maxima of r, -r for the initial test (update buffer
 // 2). r is stored shifted by the previous solve's mean (-mu of that solve),
 // which keeps the stored values small: in FP32 the whole mean of r (several
 // eV/e) would otherwise cost about 1e-7 of it in every element. The shift
@@ -385,11 +384,12 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
                           const R* __restrict__ M, const R* __restrict__ Dg, const R* __restrict__ dinv,
                           const int* __restrict__ type, const int* __restrict__ rep, TypeParams T,
                           double* __restrict__ q, const R* __restrict__ qr, const R* __restrict__ d,
-                          R* __restrict__ r, R* __restrict__ y, R* __restrict__ v, double* __restrict__ cg,
+                          R* __restrict__ r, R* __restrict__ y, R* __restrict__ v, R* __restrict__ dqv,
+                          double* __restrict__ cg,
                           unsigned long long* __restrict__ rmax, int Rn, int* __restrict__ conv, int* __restrict__ iters,
                           int* __restrict__ blocks, int* __restrict__ active, double tol) {
   const int ub = CG_UPD + 2 * 4;
-  RepAcc<4> acc;
+  RepAcc<3> acc;
   RepAcc<1> accd;
   acc.init();
   accd.init();
@@ -417,16 +417,16 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
     r[i] = ri;
     y[i] = yi;
     v[i] = Di * di + hd;
+    dqv[i] = R(0);
     acc.to(rid, cg + ub, CG_STRIDE);
     accd.to(rid, cg + CG_SD, CG_STRIDE);
     acc.v[0] += (double)yi;
     acc.v[1] += (double)ri;
     acc.v[2] += (double)ri * (double)ri;
-    acc.v[3] += qi;
     accd.v[0] += (double)di;
     lm.add(rid, ri, rmax + 2 * 2);
   }
-  lane_flush<4>(acc, cg + ub, CG_STRIDE);
+  lane_flush<3>(acc, cg + ub, CG_STRIDE);
   lane_flush<1>(accd, cg + CG_SD, CG_STRIDE);
   lm.finish(rmax + 2 * 2);
   if (last_block(blocks)) {
@@ -506,11 +506,14 @@ __global__ void __launch_bounds__(256, CT_MV_MINB)
 // Element-wise update; the sums and maxima for the next c and the test.
 // Threads take 256-atom tiles strided over the grid; per-thread partial sums
 // in the working precision (a few atoms each), FP64 across warps and blocks.
+// The iterate's change dq = q - q0 is accumulated in the working precision
+// (it is small next to q) and added to the FP64 q once, after the loop, so
+// the loop issues no FP64 arithmetic per atom.
 template <class R>
 __global__ void __launch_bounds__(256)
     k_cg_up(int N, const int* __restrict__ rep, const R* __restrict__ dinv, int* __restrict__ conv,
             int* __restrict__ iters, int* __restrict__ itp, const R* __restrict__ w, const R* __restrict__ d,
-            double* __restrict__ q, R* __restrict__ r, R* __restrict__ p, R* __restrict__ s,
+            R* __restrict__ dqv, R* __restrict__ r, R* __restrict__ p, R* __restrict__ s,
             R* __restrict__ y, double* __restrict__ cg, unsigned long long* __restrict__ rmax, int Rn,
             int* __restrict__ blocks, int* __restrict__ active, unsigned* __restrict__ err, double tol,
             int max_iter, int use_cond, cudaGraphConditionalHandle cond) {
@@ -536,9 +539,7 @@ __global__ void __launch_bounds__(256)
   LaneMax<R> lm;
   int crid = -1;
   R a = R(0), b = R(0), c = R(0), mprev = R(0);
-  double da = 0.0;
   R part[3] = {R(0), R(0), R(0)};   // sum y, sum r, sum r^2
-  double pq[1] = {0.0};             // sum q
   for (int t = blockIdx.x; (long long)t * 256 < N; t += gridDim.x) {
     int i = t * 256 + (int)threadIdx.x;
     if (i >= N) break;
@@ -548,37 +549,31 @@ __global__ void __launch_bounds__(256)
       if (crid >= 0) {   // a replica boundary in this thread's atoms
         double* o = cg + (size_t)crid * CG_STRIDE + ubuf;
         for (int k = 0; k < 3; ++k) atomicAdd(o + k, (double)part[k]);
-        atomicAdd(o + 3, pq[0]);
         part[0] = part[1] = part[2] = R(0);
-        pq[0] = 0.0;
       }
       const double* cc = cg + (size_t)rid * CG_STRIDE;
       a = (R)ldcg(cc + CG_AB);
       b = (R)ldcg(cc + CG_AB + 1);
       c = (R)ldcg(cc + CG_C);
       mprev = (R)ldcg(cc + CG_M);
-      da = (double)a;   // q and r take the same step length
       crid = rid;
     }
     R zi = y[i] - c * d[i];   // the same z as the matrix pass formed
     R pi = zi + b * p[i];
     R si = w[i] + b * s[i];
-    double qi = q[i] + da * (double)pi;
     R ri = (r[i] - a * si) - mprev;
     R yi = dinv[i] * ri;
     p[i] = pi;
     s[i] = si;
-    q[i] = qi;
+    dqv[i] += a * pi;
     r[i] = ri;
     y[i] = yi;
     part[0] += yi;
     part[1] += ri;
     part[2] += ri * ri;
-    pq[0] += qi;
     lm.add(rid, ri, rmax + mb * 2);
   }
   flush_values<R, 3>(crid, part, cg + ubuf, CG_STRIDE);
-  flush_values<double, 1>(crid, pq, cg + ubuf + 3, CG_STRIDE);
   lm.finish(rmax + mb * 2);
   if (last_block(blocks + 1)) {
     // the mean this launch subtracted joins the accumulated shift (the value
@@ -603,13 +598,30 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Restore sum q = Q exactly (uniform shift), write the working-precision
-// copy for the force passes, count the solve's iterations and extend its
-// history.
+// sum_i (q_i + dq_i) per replica: the iterate's total before the final
+// shift.
+template <class R>
+__global__ void __launch_bounds__(256) k_cg_qsum(int N, const int* __restrict__ rep, const double* __restrict__ q,
+                                                 const R* __restrict__ dqv, double* __restrict__ cg) {
+  RepAcc<1> acc;
+  acc.init();
+  for (int t = blockIdx.x; (long long)t * 256 < N; t += gridDim.x) {
+    int i = t * 256 + (int)threadIdx.x;
+    if (i >= N) break;
+    acc.to(rep[i], cg + CG_SQF, CG_STRIDE);
+    acc.v[0] += q[i] + (double)dqv[i];
+  }
+  lane_flush<1>(acc, cg + CG_SQF, CG_STRIDE);
+}
+
+// q <- q + dq, shifted uniformly onto sum q = Q exactly (rounding of y and d
+// keeps sum z, and so the iterate's total, from being exact); the
+// working-precision copy for the force passes; the solve's iteration count
+// and its history.
 template <class R>
 __global__ void k_cg_final(int N, const int* __restrict__ rep, const double* __restrict__ cg,
-                           double* __restrict__ q, R* __restrict__ qr, const int* __restrict__ itp,
-                           long long* __restrict__ total, int* __restrict__ hist) {
+                           double* __restrict__ q, const R* __restrict__ dqv, R* __restrict__ qr,
+                           const int* __restrict__ itp, long long* __restrict__ total, int* __restrict__ hist) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     *total += *itp;
@@ -617,7 +629,10 @@ __global__ void k_cg_final(int N, const int* __restrict__ rep, const double* __r
     *hist = h < 3 ? h + 1 : 3;
   }
   if (i < N) {
-    double qi = q[i] + cg[(size_t)rep[i] * CG_STRIDE + CG_DQ];
+    const double* c = cg + (size_t)rep[i] * CG_STRIDE;
+    double nat = c[CG_NAT];
+    double shift = nat > 0 ? (c[CG_Q] - c[CG_SQF]) / nat : 0.0;
+    double qi = q[i] + (double)dqv[i] + shift;
     q[i] = qi;
     qr[i] = (R)qi;
   }
@@ -641,7 +656,7 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
   int grid = atom_dims(S.N, S.nsm, (const void*)k_cg_init<R>, 256, chunk);
   k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.ld, chunk, S.nbr, S.nall, (const R*)S.M, (const R*)S.Dg,
                                      (const R*)S.dinv, S.type, S.rep, T, S.q, (const R*)S.qr, (const R*)S.cd,
-                                     (R*)S.cr, (R*)S.cy, (R*)S.cv, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
+                                     (R*)S.cr, (R*)S.cy, (R*)S.cv, (R*)S.cdq, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
                                      S.cg_blocks, S.cg_active, tol);
 }
 
@@ -658,7 +673,7 @@ void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
   if (S.N == 0) return;
   int grid = stride_grid(S.N, S.nsm, (const void*)k_cg_up<R>);
   k_cg_up<R><<<grid, 256, 0, st>>>(S.N, S.rep, (const R*)S.dinv, S.cg_conv, S.cg_iters, S.cg_it, (const R*)S.cw,
-                                   (const R*)S.cd, S.q, (R*)S.cr, (R*)S.cp, (R*)S.cs, (R*)S.cy, S.cg, S.cg_rmax,
+                                   (const R*)S.cd, (R*)S.cdq, (R*)S.cr, (R*)S.cp, (R*)S.cs, (R*)S.cy, S.cg, S.cg_rmax,
                                    S.R, S.cg_blocks, S.cg_active, S.err, cfg.tol, cfg.max_iter, cfg.use_cond,
                                    cfg.cond);
 }
@@ -671,9 +686,13 @@ void launch_cg_iter(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
 
 template <class R>
 void launch_cg_end(const DevState& S, cudaStream_t st) {
+  if (S.N > 0) {
+    int grid = stride_grid(S.N, S.nsm, (const void*)k_cg_qsum<R>);
+    k_cg_qsum<R><<<grid, 256, 0, st>>>(S.N, S.rep, S.q, (const R*)S.cdq, S.cg);
+  }
   int n = S.N > 0 ? S.N : 1;
-  k_cg_final<R><<<(n + 255) / 256, 256, 0, st>>>(S.N, S.rep, S.cg, S.q, (R*)S.qr, S.cg_it, S.cg_total,
-                                                 S.cg_hist);
+  k_cg_final<R><<<(n + 255) / 256, 256, 0, st>>>(S.N, S.rep, S.cg, S.q, (const R*)S.cdq, (R*)S.qr, S.cg_it,
+                                                 S.cg_total, S.cg_hist);
 }
 
 template <class R>

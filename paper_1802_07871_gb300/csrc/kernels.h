@@ -17,13 +17,13 @@ enum RepSlots {
 // CG scalars per replica (double), see cg.cu.
 enum CgSlots {
   CG_DOTS = 0,     // [2 buffers][2]: r.z, w.z
-  CG_UPD = 4,      // [3 buffers][4]: sum y, sum r, sum r^2, sum q
+  CG_UPD = 4,      // [3 buffers][4]: sum y, sum r, sum r^2, (unused)
   CG_SCAL = 16,    // [2 buffers][2]: gamma, alpha of an iteration
   CG_AB = 20,      // alpha, beta of the running iteration
   CG_C = 22,       // c = sum y / sum d of the running iteration
   CG_SD = 23,      // sum d (d = D^-1 1)
   CG_SQ0 = 24,     // sum of the extrapolated starting guess
-  CG_DQ = 25,      // uniform shift putting q on sum q = Q
+  CG_DQ = 25,      // uniform shift putting the starting guess on sum q = Q
   CG_M = 26,       // mean of the stored (re-centred) r
   CG_SHIFT = 27,   // total subtracted from r by the re-centring
   CG_MU = 28,      // mu = -mean(r), the electronegativity
@@ -32,7 +32,8 @@ enum CgSlots {
   CG_Q = 31,       // requested total charge
   CG_NAT = 32,     // atoms in the replica
   CG_RES0 = 33,    // max |r - mean(r)| of the starting guess
-  CG_STRIDE = 34
+  CG_SQF = 34,     // sum of q + dq after the iteration (the final neutrality shift)
+  CG_STRIDE = 36
 };
 
 struct DevState {
@@ -63,6 +64,7 @@ struct DevState {
   // CG: the iterate is q itself (FP64); the rest in the working precision
   double *cqh1 = nullptr, *cqh2 = nullptr;  // q of the previous two solves
   void *cr = nullptr, *cp = nullptr, *cs = nullptr;  // Real[N]: r (shifted), p, s = H p
+  void* cdq = nullptr;          // Real[N]: q - q0, the iteration's change (added to q at the end)
   void *cy = nullptr, *cw = nullptr, *cd = nullptr, *cv = nullptr;  // Real[N]: y = D^-1 r, w = H z, d = D^-1 1, v = H d
   unsigned long long* cg_rmax = nullptr;  // [R][3 buffers][2]: max r, max -r (order-preserving map)
   void* qr = nullptr;           // Real[N]: charges in the working precision

@@ -68,7 +68,7 @@ class Stats(C.Structure):
         ("steps", C.c_int64), ("rebuilds", C.c_int64), ("cg_iters_last", C.c_int32),
         ("max_cov", C.c_int32), ("cg_iters_total", C.c_int64), ("solves", C.c_int64),
         ("cg_residual_last", C.c_double), ("max_all", C.c_int32), ("error_bits", C.c_uint32),
-        ("mean_cov", C.c_double), ("mean_all", C.c_double),
+        ("mean_cov", C.c_double), ("mean_all", C.c_double), ("cg_residual_start", C.c_double),
     ]
 
     def as_dict(self):
