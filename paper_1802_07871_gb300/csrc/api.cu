@@ -193,11 +193,20 @@ static int setup_reps(ctbop_system* s) {
     CK(dalloc(s->cell_buf, &S.cell_count, cells));
     CK(dalloc(s->cell_buf, &S.cell_fill, cells));
     CK(dalloc(s->cell_buf, &S.cell_start, cells));
+    CK(dalloc(s->cell_buf, &S.cell_rep, cells));
     s->alloc_cells = cells;
     destroy_graphs(s);
   }
   s->S.ncells = cells;
   CK(cudaMemcpy(s->S.reps, info.data(), sizeof(RepInfo) * s->R, cudaMemcpyHostToDevice));
+  {
+    std::vector<int> crep(cells);
+    for (int r = 0; r < s->R; ++r) {
+      int end = r + 1 < s->R ? info[r + 1].cell_off : cells;
+      for (int c = info[r].cell_off; c < end; ++c) crep[c] = r;
+    }
+    CK(cudaMemcpy(s->S.cell_rep, crep.data(), sizeof(int) * cells, cudaMemcpyHostToDevice));
+  }
   // per-replica CG constants
   std::vector<double> cg((size_t)s->R * CG_STRIDE, 0.0);
   for (int r = 0; r < s->R; ++r) {
@@ -271,7 +280,7 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->rep_buf, &S.scan_tmp, 1040));
   CK(dalloc(s->rep_buf, &S.flag_rebuild, 1));
   CK(dalloc(s->rep_buf, &S.rebuild_count, 1));
-  CK(dalloc(s->rep_buf, &S.maxcnt, 2));
+  CK(dalloc(s->rep_buf, &S.maxcnt, 3));
   CK(dalloc(s->rep_buf, &S.err, 1));
   CK(dalloc(s->rep_buf, &S.cg_it, 1));
   CK(dalloc(s->rep_buf, &S.cg_blocks, 3));
@@ -284,7 +293,7 @@ static int alloc_atoms(ctbop_system* s) {
   CK(cudaMemset(S.cg_total, 0, sizeof(long long)));
   CK(cudaMemset(S.cg_blocks, 0, 3 * sizeof(int)));
   CK(cudaMemset(S.cg_hist, 0, sizeof(int)));
-  CK(cudaMemset(S.maxcnt, 0, 2 * sizeof(int)));
+  CK(cudaMemset(S.maxcnt, 0, 3 * sizeof(int)));
   CK(cudaMemset(S.cg_it, 0, sizeof(int)));
   s->alloc_N = N;
   s->alloc_R = s->R;
@@ -311,6 +320,7 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   size_t ncol = (size_t)S.ld * cap_all;
   CK(dalloc(s->list_buf, &S.nbr, ncol));
   CK(dalloc(s->list_buf, &S.code, ncol));
+  CK(dalloc(s->list_buf, &S.lst, (size_t)std::max(N, 1) * cap_all));
   CK(dalloc(s->list_buf, &S.rev, (size_t)N * cap_cov));
   unsigned char *bo = nullptr, *gs = nullptr, *M = nullptr;
   CK(dalloc(s->list_buf, &bo, (size_t)N * cap_cov * 4 * rs));
@@ -450,15 +460,17 @@ static int ensure_lists(ctbop_system* s) {
     unsigned bits = 0;
     int rc = read_err(s, bits);
     if (rc) return rc;
-    int mc[2];
+    int mc[3];
     CK(cudaMemcpy(mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost));
     if (bits & CT_ERR_NONFINITE) return fail(s, CTBOP_ERR_NONFINITE, "non-finite position");
     bool over = (bits & (CT_ERR_NBR_OVERFLOW | CT_ERR_COV_OVERFLOW)) != 0;
     if (!over && (bits & CT_ERR_REV_MISSING)) return fail(s, CTBOP_ERR_CUDA, "internal: asymmetric covalent list");
     if (!over && s->caps_known) break;
-    // size from the measured maxima with headroom for motion
+    // size from the measured maxima with headroom for motion (a list holds
+    // cap_cov covalent slots, then the rest)
     int cc = std::max(mc[0] + mc[0] / 4 + 4, 8);
-    int ca = std::max(mc[1] + mc[1] / 8 + 16, cc);
+    cc = (cc + 3) & ~3;
+    int ca = cc + mc[1] + mc[1] / 8 + 16;
     cc = (cc + 3) & ~3;
     ca = (ca + 7) & ~7;
     if (s->o.cap_cov > 0) cc = std::max(cc, s->o.cap_cov);
@@ -843,11 +855,11 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
       // the restored q is the next starting guess; its time history is gone
       *s->h_int = 1;
       cudaMemcpyAsync(S.cg_hist, s->h_int, sizeof(int), cudaMemcpyHostToDevice, s->stream);
-      int mc[2];
+      int mc[3];
       cudaMemcpy(mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost);
-      int cc = std::max(S.cap_cov, mc[0] + mc[0] / 4 + 4);
-      int ca = std::max(S.cap_all, mc[1] + mc[1] / 8 + 16);
-      result = alloc_lists(s, (cc + 3) & ~3, (ca + 7) & ~7);
+      int cc = (std::max(S.cap_cov, mc[0] + mc[0] / 4 + 4) + 3) & ~3;
+      int ca = std::max(S.cap_all, cc + mc[1] + mc[1] / 8 + 16);
+      result = alloc_lists(s, cc, (ca + 7) & ~7);
       if (result) break;
       s->need_rebuild = true;
       result = ensure_lists(s);
@@ -926,7 +938,7 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   CK(cudaStreamSynchronize(s->stream));
   unsigned bits = 0;
   long long rb = 0, tot = 0;
-  int it = 0, mc[2] = {0, 0};
+  int it = 0, mc[3] = {0, 0, 0};
   CK(cudaMemcpy(&bits, S.err, sizeof(bits), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&rb, S.rebuild_count, sizeof(rb), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&tot, S.cg_total, sizeof(tot), cudaMemcpyDeviceToHost));
@@ -942,7 +954,7 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   st->cg_iters_last = it;
   st->cg_residual_last = res;
   st->max_cov = mc[0];
-  st->max_all = mc[1];
+  st->max_all = mc[2];
   if (S.N > 0 && S.ncov) {
     std::vector<int> a(S.N), b(S.N);
     CK(cudaMemcpy(a.data(), S.ncov, sizeof(int) * S.N, cudaMemcpyDeviceToHost));

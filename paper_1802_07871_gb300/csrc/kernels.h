@@ -54,9 +54,11 @@ struct DevState {
   int* cg_iters = nullptr;      // [R] iterations used
   // cells
   int *cell_count = nullptr, *cell_fill = nullptr, *cell_start = nullptr, *cell_atoms = nullptr;
+  int* cell_rep = nullptr;      // [ncells] replica of each cell
   int* scan_tmp = nullptr;      // >= 1025 ints
   // lists
   int *nbr = nullptr, *code = nullptr, *ncov = nullptr, *nall = nullptr, *rev = nullptr;
+  int2* lst = nullptr;          // [N][cap_all] row-major build scratch (j, code)
   void* bo = nullptr;           // Real4[N*cap_cov]
   void* gslot = nullptr;        // Real4[N*cap_cov]
   void* M = nullptr;            // Real[N*cap_all]
@@ -72,7 +74,7 @@ struct DevState {
   // control
   int* flag_rebuild = nullptr;
   long long* rebuild_count = nullptr;
-  int* maxcnt = nullptr;        // [2] max ncov, max nall at the last rebuild
+  int* maxcnt = nullptr;        // [3] at the last rebuild: max ncov, max count of the rest, max nall
   unsigned* err = nullptr;
   int* cg_it = nullptr;         // iteration counter of the running solve
   int* cg_blocks = nullptr;     // last-block counters [3]

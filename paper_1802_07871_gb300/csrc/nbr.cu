@@ -135,135 +135,259 @@ __global__ void k_sort_cells(int C, const int* __restrict__ cell_start,
 }
 
 // ---------------------------------------------------------------- lists
-#define MAXR 17  // stencil cells along x per row (half width <= 8)
-
 __device__ inline int wrap_cell(int c, int n) {
   c %= n;
   return c < 0 ? c + n : c;
 }
 
-// One warp per atom. Two sweeps over the stencil: covalent entries first,
-// then the remaining entries inside the charge cutoff.
+// Lists are built one warp per cell: the atoms of a cell share one stencil,
+// so each candidate j of the stencil is loaded once and tested against every
+// atom i of the cell (up to 32 at a time, staged in shared memory). The
+// stencil's cells are taken in batches of BC; a warp scan of their counts
+// flattens the batch into one candidate sequence that the lanes walk 32 at a
+// time (a lane finds its cell by binary search over the prefix sums).
+//
+// The atoms of a cell have scattered indices, so the pass writes each atom's
+// entries contiguously (row-major scratch `lst`, one int2 (j, code) per
+// entry: a ballot's entries land on one or two lines) and k_list_transpose
+// turns the rows into the column-major lists through shared-memory tiles.
+// Column-major stores straight from here would each touch a different line,
+// completed only much later by other warps: with lists far larger than L2
+// the partial lines are evicted and written back piecemeal.
+//
+// One pass writes both parts of a row: covalent entries from slot 0, the
+// others from slot cap_cov. The gap left between them is then closed by
+// moving the last of the other entries into it (their order is free), so
+// entries 0 .. ncov-1 are covalent and ncov .. nall-1 the rest. maxcnt
+// receives the largest covalent count, the largest count of the rest (the
+// list needs cap_cov + that) and the largest total.
+#define BC 128   // stencil cells per batch
+#define BW 4     // warps per block
 template <class R>
-__global__ void k_build(int N, const typename Vec4<R>::T* __restrict__ u,
-                        const int4* __restrict__ cell4, const int* __restrict__ rep,
-                        const RepInfo* __restrict__ reps, const int* __restrict__ cell_start,
-                        const int* __restrict__ cell_count, const int* __restrict__ cell_atoms,
-                        PotParams<R> P, int cap_cov, int cap_all, int ld, int* __restrict__ nbr,
-                        int* __restrict__ code, int* __restrict__ ncov, int* __restrict__ nall,
-                        int* __restrict__ maxcnt, unsigned* __restrict__ err,
-                        const int* __restrict__ flag) {
-  __shared__ int s_start[8][MAXR], s_cnt[8][MAXR], s_dx[8][MAXR];
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int i = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (i >= N || *flag == 0) return;
-  const RepInfo& ri = reps[rep[i]];
-  typename Vec4<R>::T ui = u[i];
-  int ti = (int)ui.w;
-  int4 ci = cell4[i];
-  R hx = (R)ri.hc[0], hy = (R)ri.hc[1], hz = (R)ri.hc[2];
-  int* col_nbr = nbr + i;
-  int* col_code = code + i;
-  // `count` is the number of stored entries (never above the capacities, so
-  // every stored entry is a valid atom even after an overflow); `need`
-  // counts what the lists would need, for regrowing them.
-  int count = 0, count_cov = 0, need_cov = 0, need_all = 0;
-  for (int pass = 0; pass < 2; ++pass) {
-    int cap_pass = pass == 0 ? cap_cov : cap_all;
-    for (int dz = -ri.m[2]; dz <= ri.m[2]; ++dz) {
-      int cz = ci.z + dz;
-      if (ri.pbc[2]) cz = wrap_cell(cz, ri.n[2]);
-      else if (cz < 0 || cz >= ri.n[2]) continue;
-      for (int dy = -ri.m[1]; dy <= ri.m[1]; ++dy) {
-        int cy = ci.y + dy;
-        if (ri.pbc[1]) cy = wrap_cell(cy, ri.n[1]);
-        else if (cy < 0 || cy >= ri.n[1]) continue;
-        // the x cells of this row
-        int nx = 2 * ri.m[0] + 1;
-        __syncwarp();
-        if (lane < nx) {
-          int dx = lane - ri.m[0];
-          int cx = ci.x + dx;
-          bool ok = true;
-          if (ri.pbc[0]) cx = wrap_cell(cx, ri.n[0]);
-          else ok = (cx >= 0 && cx < ri.n[0]);
-          int g = ok ? ri.cell_off + (cz * ri.n[1] + cy) * ri.n[0] + cx : 0;
-          s_start[warp][lane] = ok ? cell_start[g] : 0;
-          s_cnt[warp][lane] = ok ? cell_count[g] : 0;
-          s_dx[warp][lane] = dx;
-        }
-        __syncwarp();
-        int tot = 0;
-        for (int k = 0; k < nx; ++k) tot += s_cnt[warp][k];
-        for (int t0 = 0; t0 < tot; t0 += 32) {
-          int t = t0 + lane;
-          bool take = false;
-          int j = 0, cd = 0;
-          if (t < tot) {
-            int k = 0, off = t;
-            while (off >= s_cnt[warp][k]) { off -= s_cnt[warp][k]; ++k; }
-            j = cell_atoms[s_start[warp][k] + off];
-            int dx = s_dx[warp][k];
-            typename Vec4<R>::T uj = u[j];
-            R rx = (uj.x - ui.x) + (R)dx * hx;
-            R ry = (uj.y - ui.y) + (R)dy * hy;
-            R rz = (uj.z - ui.z) + (R)dz * hz;
-            R r2 = rx * rx + ry * ry + rz * rz;
-            int tj = (int)uj.w;
-            bool self0 = (j == i) && dx == 0 && dy == 0 && dz == 0;
-            bool cov = r2 < P.rcov_list2[ti * 2 + tj];
-            take = !self0 && (pass == 0 ? cov : (!cov && r2 < P.rall_list2));
+__global__ void __launch_bounds__(BW * 32)
+    k_build(int C, const typename Vec4<R>::T* __restrict__ u, const int* __restrict__ cell_rep,
+            const RepInfo* __restrict__ reps, const int* __restrict__ cell_start,
+            const int* __restrict__ cell_count, const int* __restrict__ cell_atoms, PotParams<R> P,
+            int cap_cov, int cap_all, int2* __restrict__ lst,
+            int* __restrict__ ncov, int* __restrict__ nall, int* __restrict__ maxcnt,
+            unsigned* __restrict__ err, const int* __restrict__ flag) {
+  typedef typename Vec4<R>::T R4;
+  __shared__ int s_st[BW][BC], s_pre[BW][BC + 1], s_cd[BW][BC];
+  __shared__ R4 s_u[BW][32];
+  __shared__ int s_i[BW][32];
+  __shared__ int s_need[BW][3];
+  if (*flag == 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int need_cov = 0, need_rest = 0, need_tot = 0;   // this lane's maxima over the atoms it owned
+  for (int g = blockIdx.x * BW + warp; g < C; g += gridDim.x * BW) {
+    int nci = cell_count[g];
+    if (nci == 0) continue;
+    const int ci0 = cell_start[g];
+    const RepInfo& ri = reps[cell_rep[g]];
+    const int loc = g - ri.cell_off;
+    const int cx = loc % ri.n[0], cy = (loc / ri.n[0]) % ri.n[1], cz = loc / (ri.n[0] * ri.n[1]);
+    const R hx = (R)ri.hc[0], hy = (R)ri.hc[1], hz = (R)ri.hc[2];
+    const int sx = 2 * ri.m[0] + 1, sy = 2 * ri.m[1] + 1;
+    const int ns = sx * sy * (2 * ri.m[2] + 1);
+    for (int ib = 0; ib < nci; ib += 32) {
+      const int ni = min(32, nci - ib);
+      int my_i = -1, cnt_c = 0, cnt_r = 0;
+      if (lane < ni) {
+        my_i = cell_atoms[ci0 + ib + lane];
+        s_u[warp][lane] = u[my_i];
+        s_i[warp][lane] = my_i;
+      }
+      __syncwarp();
+      for (int sb = 0; sb < ns; sb += BC) {
+        const int nb = min(BC, ns - sb);
+        // this batch's cells: start, count (0 outside an open box) and offset code
+        int cnt[BC / 32];
+#pragma unroll
+        for (int k = 0; k < BC / 32; ++k) {
+          int c = k * 32 + lane, st = 0, n = 0, cd = 0;
+          if (c < nb) {
+            int sidx = sb + c;
+            int dx = sidx % sx - ri.m[0], dy = (sidx / sx) % sy - ri.m[1], dz = sidx / (sx * sy) - ri.m[2];
+            int ax = cx + dx, ay = cy + dy, az = cz + dz;
+            bool ok = true;
+            if (ri.pbc[0]) ax = wrap_cell(ax, ri.n[0]); else ok = ok && ax >= 0 && ax < ri.n[0];
+            if (ri.pbc[1]) ay = wrap_cell(ay, ri.n[1]); else ok = ok && ay >= 0 && ay < ri.n[1];
+            if (ri.pbc[2]) az = wrap_cell(az, ri.n[2]); else ok = ok && az >= 0 && az < ri.n[2];
+            if (ok) {
+              int gc = ri.cell_off + (az * ri.n[1] + ay) * ri.n[0] + ax;
+              st = cell_start[gc];
+              n = cell_count[gc];
+            }
             cd = pack_code(dx, dy, dz);
+            s_st[warp][c] = st;
+            s_cd[warp][c] = cd;
           }
-          unsigned bal = __ballot_sync(CT_FULL, take);
-          if (take) {
-            int pos = count + __popc(bal & ((1u << lane) - 1u));
-            if (pos < cap_pass) {
-              col_nbr[(size_t)pos * ld] = j;
-              col_code[(size_t)pos * ld] = cd;
+          cnt[k] = n;
+        }
+        // exclusive prefix sums of the counts, in batch order (cell k * 32 + lane)
+        int T = 0;
+#pragma unroll
+        for (int k = 0; k < BC / 32; ++k) {
+          int v = cnt[k], sc = v;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(CT_FULL, sc, o);
+            if (lane >= o) sc += t;
+          }
+          if (k * 32 + lane < nb) s_pre[warp][k * 32 + lane] = T + sc - v;
+          T += __shfl_sync(CT_FULL, sc, 31);
+        }
+        if (lane == 0) s_pre[warp][nb] = T;
+        __syncwarp();
+        for (int t0 = 0; t0 < T; t0 += 32) {
+          const int t = t0 + lane;
+          const bool valid = t < T;
+          int j = -1, cd = 0;
+          R4 uj;
+          uj.x = uj.y = uj.z = uj.w = R(0);
+          R ox = R(0), oy = R(0), oz = R(0);
+          if (valid) {
+            int lo = 0, hi = nb;   // largest k with s_pre[k] <= t
+            while (hi - lo > 1) {
+              int mid = (lo + hi) >> 1;
+              if (s_pre[warp][mid] <= t) lo = mid; else hi = mid;
+            }
+            j = cell_atoms[s_st[warp][lo] + (t - s_pre[warp][lo])];
+            cd = s_cd[warp][lo];
+            uj = u[j];
+            int dx, dy, dz;
+            unpack_code(cd, dx, dy, dz);
+            ox = (R)dx * hx;
+            oy = (R)dy * hy;
+            oz = (R)dz * hz;
+          }
+          const int tj = (int)uj.w;
+          const bool zero_off = cd == pack_code(0, 0, 0);
+          for (int ii = 0; ii < ni; ++ii) {
+            const R4 ui = s_u[warp][ii];
+            const int i = s_i[warp][ii];
+            R rx = (uj.x - ui.x) + ox, ry = (uj.y - ui.y) + oy, rz = (uj.z - ui.z) + oz;
+            R r2 = rx * rx + ry * ry + rz * rz;
+            bool self0 = zero_off && j == i;
+            bool in = valid && !self0;
+            bool cov = in && r2 < P.rcov_list2[(int)ui.w * 2 + tj];
+            bool rest = in && !cov && r2 < P.rall_list2;
+            unsigned bc = __ballot_sync(CT_FULL, cov), br = __ballot_sync(CT_FULL, rest);
+            int bcc = __shfl_sync(CT_FULL, cnt_c, ii), bcr = __shfl_sync(CT_FULL, cnt_r, ii);
+            if (cov) {
+              int pos = bcc + __popc(bc & lt);
+              if (pos < cap_cov) lst[(size_t)i * cap_all + pos] = make_int2(j, cd);
+            } else if (rest) {
+              int pos = cap_cov + bcr + __popc(br & lt);
+              if (pos < cap_all) lst[(size_t)i * cap_all + pos] = make_int2(j, cd);
+            }
+            if (lane == ii) {
+              cnt_c += __popc(bc);
+              cnt_r += __popc(br);
             }
           }
-          int nt = __popc(bal);
-          if (pass == 0) need_cov += nt;
-          need_all += nt;
-          count = min(count + nt, cap_pass);
         }
+        __syncwarp();
+      }
+      // close the gap between the covalent part and the rest
+      if (lane < ni) {
+        int nc = min(cnt_c, cap_cov);
+        int nr = min(cnt_r, cap_all - cap_cov);
+        int mv = min(cap_cov - nc, nr);
+        int2* row = lst + (size_t)my_i * cap_all;
+        for (int k = 0; k < mv; ++k) row[nc + k] = row[cap_cov + nr - 1 - k];
+        ncov[my_i] = nc;
+        nall[my_i] = nc + nr;
+        need_cov = max(need_cov, cnt_c);
+        need_rest = max(need_rest, cnt_r);
+        need_tot = max(need_tot, cnt_c + cnt_r);
+        if (cnt_c > cap_cov) atomicOr(err, CT_ERR_COV_OVERFLOW);
+        if (cap_cov + cnt_r > cap_all) atomicOr(err, CT_ERR_NBR_OVERFLOW);
+      }
+      __syncwarp();
+    }
+  }
+  // one atomicMax per block for each count
+  need_cov = __reduce_max_sync(CT_FULL, (unsigned)need_cov);
+  need_rest = __reduce_max_sync(CT_FULL, (unsigned)need_rest);
+  need_tot = __reduce_max_sync(CT_FULL, (unsigned)need_tot);
+  if (lane == 0) {
+    s_need[warp][0] = need_cov;
+    s_need[warp][1] = need_rest;
+    s_need[warp][2] = need_tot;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0, b = 0, c = 0;
+    for (int w = 0; w < BW; ++w) {
+      a = max(a, s_need[w][0]);
+      b = max(b, s_need[w][1]);
+      c = max(c, s_need[w][2]);
+    }
+    atomicMax(maxcnt + 0, a);
+    atomicMax(maxcnt + 1, b);
+    atomicMax(maxcnt + 2, c);
+  }
+}
+
+// Row-major scratch -> column-major lists (entry e of atom i at e * ld + i),
+// 32 atoms x 32 entries per tile through shared memory; tiles past every
+// row's end are skipped. Grid-strided over the tiles.
+__global__ void __launch_bounds__(256)
+    k_list_transpose(int N, int cap_all, int ld, const int2* __restrict__ lst, const int* __restrict__ nall,
+                     int* __restrict__ nbr, int* __restrict__ code, const int* __restrict__ flag) {
+  __shared__ int2 tile[32][33];
+  if (*flag == 0) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int ta = (N + 31) / 32, te = (cap_all + 31) / 32;
+  for (long long t = blockIdx.x; t < (long long)ta * te; t += gridDim.x) {
+    const int a0 = (int)(t % ta) * 32, e0 = (int)(t / ta) * 32;
+    int na = a0 + tx < N ? nall[a0 + tx] : 0;
+    int nmax = __reduce_max_sync(CT_FULL, (unsigned)na);
+    if (e0 >= nmax) continue;   // uniform over the block: every warp reads the same 32 counts
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int a = a0 + ty + 8 * r, e = e0 + tx;
+      if (a < N && e < nall[a]) tile[ty + 8 * r][tx] = lst[(size_t)a * cap_all + e];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int e = e0 + ty + 8 * r, a = a0 + tx;
+      if (e < na) {
+        int2 v = tile[tx][ty + 8 * r];
+        nbr[(size_t)e * ld + a] = v.x;
+        code[(size_t)e * ld + a] = v.y;
       }
     }
-    if (pass == 0) count_cov = count;
-  }
-  if (lane == 0) {
-    ncov[i] = count_cov;
-    nall[i] = count;
-    atomicMax(maxcnt + 0, need_cov);
-    atomicMax(maxcnt + 1, need_all);
-    if (need_cov > cap_cov) atomicOr(err, CT_ERR_COV_OVERFLOW);
-    if (need_all > cap_all) atomicOr(err, CT_ERR_NBR_OVERFLOW);
+    __syncthreads();
   }
 }
 
 // Reverse covalent entry: for entry e of i pointing at (j, d), the entry of
-// j pointing at (i, -d).
+// j pointing at (i, -d). One thread per atom, grid-strided.
 __global__ void k_rev(int N, int cap_cov, int ld, const int* __restrict__ nbr,
                       const int* __restrict__ code, const int* __restrict__ ncov,
                       int* __restrict__ rev, unsigned* __restrict__ err,
                       const int* __restrict__ flag) {
-  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)N * cap_cov || *flag == 0) return;
-  int i = (int)(t % N), e = (int)(t / N);   // consecutive threads: consecutive atoms
-  int nc = min(ncov[i], cap_cov);
-  if (e >= nc) return;
-  int j = nbr[(size_t)e * ld + i];
-  int dx, dy, dz;
-  unpack_code(code[(size_t)e * ld + i], dx, dy, dz);
-  int want = pack_code(-dx, -dy, -dz);
-  int ncj = min(ncov[j], cap_cov);
-  int found = -1;
-  for (int k = 0; k < ncj; ++k) {
-    if (nbr[(size_t)k * ld + j] == i && code[(size_t)k * ld + j] == want) { found = k; break; }
+  if (*flag == 0) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    int nc = min(ncov[i], cap_cov);
+    for (int e = 0; e < nc; ++e) {
+      int j = nbr[(size_t)e * ld + i];
+      int dx, dy, dz;
+      unpack_code(code[(size_t)e * ld + i], dx, dy, dz);
+      int want = pack_code(-dx, -dy, -dz);
+      int ncj = min(ncov[j], cap_cov);
+      int found = -1;
+      for (int k = 0; k < ncj; ++k) {
+        if (nbr[(size_t)k * ld + j] == i && code[(size_t)k * ld + j] == want) { found = k; break; }
+      }
+      if (found < 0) { atomicOr(err, CT_ERR_REV_MISSING); found = 0; }
+      rev[(size_t)i * cap_cov + e] = found;
+    }
   }
-  if (found < 0) { atomicOr(err, CT_ERR_REV_MISSING); found = 0; }
-  rev[(size_t)i * cap_cov + e] = found;
 }
 
 __global__ void k_zero_cells(int C, int* __restrict__ cell_count, int* __restrict__ cell_fill,
@@ -271,7 +395,7 @@ __global__ void k_zero_cells(int C, int* __restrict__ cell_count, int* __restric
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (*flag == 0) return;
   if (c < C) { cell_count[c] = 0; cell_fill[c] = 0; }
-  if (c < 2) maxcnt[c] = 0;
+  if (c < 3) maxcnt[c] = 0;
 }
 
 // Clear the rebuild request and count the rebuild (one thread).
@@ -287,7 +411,7 @@ void launch_rebuild(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   int tb = 256;
   int C = S.ncells;
   const int* f = S.flag_rebuild;
-  k_zero_cells<<<(max(C, 2) + tb - 1) / tb, tb, 0, st>>>(C, S.cell_count, S.cell_fill, S.maxcnt, f);
+  k_zero_cells<<<(max(C, 3) + tb - 1) / tb, tb, 0, st>>>(C, S.cell_count, S.cell_fill, S.maxcnt, f);
   k_bin<R><<<(N + tb - 1) / tb, tb, 0, st>>>(N, S.x, S.xref, S.type, S.rep, S.reps, S.cell4,
                                               (typename Vec4<R>::T*)S.u, S.cell_count, S.err, f);
   int nb = (C + SCAN_T * SCAN_E - 1) / (SCAN_T * SCAN_E);
@@ -296,13 +420,13 @@ void launch_rebuild(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   k_scan_add<<<(C + tb - 1) / tb, tb, 0, st>>>(C, S.cell_start, S.scan_tmp, f);
   k_scatter<<<(N + tb - 1) / tb, tb, 0, st>>>(N, S.cell4, S.cell_start, S.cell_fill, S.cell_atoms, f);
   k_sort_cells<<<(C + tb - 1) / tb, tb, 0, st>>>(C, S.cell_start, S.cell_count, S.cell_atoms, f);
-  int wpb = 8;
-  k_build<R><<<(N + wpb - 1) / wpb, wpb * 32, 0, st>>>(
-      N, (const typename Vec4<R>::T*)S.u, S.cell4, S.rep, S.reps, S.cell_start, S.cell_count,
-      S.cell_atoms, P, S.cap_cov, S.cap_all, S.ld, S.nbr, S.code, S.ncov, S.nall, S.maxcnt, S.err, f);
-  size_t tot = (size_t)N * S.cap_cov;
-  k_rev<<<(unsigned)((tot + tb - 1) / tb), tb, 0, st>>>(N, S.cap_cov, S.ld, S.nbr, S.code, S.ncov, S.rev,
-                                                        S.err, f);
+  // grid-strided: when no rebuild is due these launches return at once
+  int gb = S.nsm * 8;
+  k_build<R><<<gb, BW * 32, 0, st>>>(C, (const typename Vec4<R>::T*)S.u, S.cell_rep, S.reps, S.cell_start,
+                                     S.cell_count, S.cell_atoms, P, S.cap_cov, S.cap_all, S.lst, S.ncov, S.nall,
+                                     S.maxcnt, S.err, f);
+  k_list_transpose<<<S.nsm * 8, 256, 0, st>>>(N, S.cap_all, S.ld, S.lst, S.nall, S.nbr, S.code, f);
+  k_rev<<<S.nsm * 4, tb, 0, st>>>(N, S.cap_cov, S.ld, S.nbr, S.code, S.ncov, S.rev, S.err, f);
   k_finish_rebuild<<<1, 1, 0, st>>>(S.flag_rebuild, S.rebuild_count);
 }
 

@@ -1,0 +1,95 @@
+"""GPU neighbour lists against brute-force pair enumeration.
+
+The lists are index work: the number of directed entries (i, j, image) with
+r < S_ij + skin (covalent part) and r < Rc + skin (whole list) must equal the
+oracle's enumeration over every periodic image, self-images included. The
+FP64 path compares exactly. The mixed path tests distances in FP32, where a
+pair within ~1e-6 A of a cutoff can fall either way, so it allows a couple
+of entries per ten thousand atoms."""
+import numpy as np
+import pytest
+
+from oracle import ctbop_oracle as O
+from paper_1802_07871_gb300 import ctbop
+from paper_1802_07871_gb300 import structures as st
+
+pytestmark = pytest.mark.gpu
+P0 = st.load_params("p0")
+SKIN = 0.3
+TYPES = ["Si", "C"]
+
+
+def _s_matrix(params):
+    S = np.zeros((2, 2))
+    for a in range(2):
+        for b in range(2):
+            S[a, b] = params["pair"][TYPES[min(a, b)] + TYPES[max(a, b)]]["S"]
+    return S
+
+
+def _oracle_counts(s):
+    rall = P0["coulomb"]["r_coul"] + SKIN
+    i, j, n, u = O.pairs(s.x, s.box, s.pbc, rall)
+    r = np.sqrt(np.einsum("ij,ij->i", u, u))
+    S = _s_matrix(P0)
+    cov = r < S[s.types[i], s.types[j]] + SKIN
+    per_all = np.bincount(i, minlength=s.n)
+    per_cov = np.bincount(i[cov], minlength=s.n)
+    return int(cov.sum()), len(i), int(per_cov.max(initial=0)), int(per_all.max(initial=0))
+
+
+def _gpu_counts(structs, prec):
+    sysm = ctbop.System(P0, precision=prec, skin=SKIN)
+    sysm.load_replicas(structs)
+    sysm.compute()
+    d = sysm.status()
+    n = sum(s.n for s in structs)
+    sysm.close()
+    return int(round(d["mean_cov"] * n)), int(round(d["mean_all"] * n)), d["max_cov"], d["max_all"]
+
+
+def _cluster(n, seed, spread=3.5, min_sep=1.45):
+    rng = np.random.default_rng(seed)
+    xs = []
+    while len(xs) < n:
+        c = rng.uniform(-spread, spread, 3)
+        if all(np.linalg.norm(c - y) >= min_sep for y in xs):
+            xs.append(c)
+    x = np.array(xs) + 15.0
+    t = rng.integers(0, 2, n).astype(np.int32)
+    return st.Structure(f"cluster{n}", x, t, np.full(3, 30.0), np.array([False] * 3))
+
+
+CASES = {
+    "bulk512": lambda: [st.bulk_3c_512()],
+    "small_box_1cell": lambda: [st.sic_3c(1, 4.36, 0.1, seed=31)],
+    "small_box_2cell": lambda: [st.sic_3c(2, 4.36, 0.1, seed=32, strain=np.diag([0.03, -0.02, 0.01]))],
+    "cluster": lambda: [_cluster(41, 3)],
+    "stepped_slab": lambda: [st.stepped_slab_small(8, 4, 6)],
+    "replicas": lambda: [st.sic_3c(2, 4.36, 0.05, seed=40), _cluster(17, 41), st.stepped_slab_small(6, 3, 4)],
+}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_list_counts_match_bruteforce(case, prec):
+    structs = CASES[case]()
+    ncov, nall, mcov, mall = 0, 0, 0, 0
+    for s in structs:
+        c, a, mc, ma = _oracle_counts(s)
+        ncov, nall, mcov, mall = ncov + c, nall + a, max(mcov, mc), max(mall, ma)
+    g = _gpu_counts(structs, prec)
+    if prec == "fp64":
+        assert g == (ncov, nall, mcov, mall), (g, (ncov, nall, mcov, mall))
+    else:
+        n = sum(s.n for s in structs)
+        slack = 2 + n // 5000
+        assert abs(g[0] - ncov) <= slack and abs(g[1] - nall) <= slack, (g, (ncov, nall))
+        assert abs(g[2] - mcov) <= 1 and abs(g[3] - mall) <= 1, (g, (mcov, mall))
+
+
+def test_list_counts_slab_20k_fp64():
+    """The 19,488-atom stepped slab: every cell row of a large open-z grid."""
+    s = st.stepped_slab_20k()
+    c, a, mc, ma = _oracle_counts(s)
+    assert _gpu_counts([s], "fp64") == (c, a, mc, ma)
