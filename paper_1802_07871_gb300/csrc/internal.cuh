@@ -95,6 +95,12 @@ template <> __device__ inline double ct_sqrt<double>(double x) { return sqrt(x);
 template <class R> __device__ inline R ct_cbrt(R x);
 template <> __device__ inline float ct_cbrt<float>(float x) { return cbrtf(x); }
 template <> __device__ inline double ct_cbrt<double>(double x) { return cbrt(x); }
+template <class R> __device__ inline R ct_rsqrt(R x);
+template <> __device__ inline float ct_rsqrt<float>(float x) { return rsqrtf(x); }
+template <> __device__ inline double ct_rsqrt<double>(double x) { return 1.0 / sqrt(x); }
+template <class R> __device__ inline R ct_rcbrt(R x);
+template <> __device__ inline float ct_rcbrt<float>(float x) { return rcbrtf(x); }
+template <> __device__ inline double ct_rcbrt<double>(double x) { return 1.0 / cbrt(x); }
 template <class R> __device__ inline R ct_cospi(R x);
 template <> __device__ inline float ct_cospi<float>(float x) { return cospif(x); }
 template <> __device__ inline double ct_cospi<double>(double x) { return cospi(x); }
@@ -127,6 +133,34 @@ __device__ inline void coul_fn(R r, R gs3, R inv_rc, R ke, R& K, R& dK) {
   K = ke * T * iD;
   R iD3 = iD * iD * iD;
   dK = ke * (dT * inv_rc * iD - T * r * r * iD3 * iD);
+}
+
+// The same K(r) from r^2 for the streamed passes: 1/r and 1/(r^3 +
+// gamma^-3)^(1/3) come from the reciprocal root functions (FP32 path) instead
+// of a root and a division each. Returns r, 1/r, K and K'(r)/r.
+template <class R>
+__device__ inline void coul_fn_r2(R r2, R gs3, R inv_rc, R ke, R& r, R& ir, R& K, R& dK_r) {
+  ir = ct_rsqrt<R>(r2);
+  r = r2 * ir;
+  R x = r * inv_rc;
+  if (x >= R(1)) { K = R(0); dK_r = R(0); return; }
+  R x2 = x * x, x3 = x2 * x, x4 = x2 * x2;
+  R T = R(1) + x4 * (R(-35) + x * (R(84) + x * (R(-70) + R(20) * x)));
+  R xm = x - R(1);
+  R dT = R(140) * x3 * xm * xm * xm;
+  R iD = ct_rcbrt<R>(r2 * r + gs3);
+  K = ke * T * iD;
+  R iD3 = iD * iD * iD;
+  dK_r = ke * (dT * inv_rc * iD * ir - T * r * iD3 * iD);
+}
+template <class R>
+__device__ inline R coul_K_r2(R r2, R gs3, R inv_rc, R ke) {
+  R r = r2 * ct_rsqrt<R>(r2);
+  R x = r * inv_rc;
+  if (x >= R(1)) return R(0);
+  R x4 = (x * x) * (x * x);
+  R T = R(1) + x4 * (R(-35) + x * (R(84) + x * (R(-70) + R(20) * x)));
+  return ke * T * ct_rcbrt<R>(r2 * r + gs3);
 }
 
 // Compensated (Neumaier) summation in the working precision: keeps the

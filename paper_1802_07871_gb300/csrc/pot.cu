@@ -133,57 +133,93 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
 }
 
 // ---------------------------------------------------------------- assembly
+// Entries past the covalent part are streamed: the list indices and offset
+// codes of the next PB entries are loaded before the current ones are used,
+// so the list (the bound of these passes) always has loads in flight.
+#define PB 8
 template <class R>
-__global__ void k_assemble(int N, int cap_cov, int ld, int chunk, const typename Vec4<R>::T* __restrict__ u,
-                           const int* __restrict__ rep, const RepInfo* __restrict__ reps,
-                           const int* __restrict__ nbr, const int* __restrict__ code,
-                           const int* __restrict__ ncov, const int* __restrict__ nall,
-                           const int* __restrict__ rev, const typename Vec4<R>::T* __restrict__ bo,
-                           PotParams<R> P, TypeParams T, R* __restrict__ M, R* __restrict__ Dg,
-                           R* __restrict__ dinv) {
+__global__ void __launch_bounds__(256)
+    k_assemble(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
+               const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
+               const int* __restrict__ code, const int* __restrict__ ncov, const int* __restrict__ nall,
+               const int* __restrict__ rev, const typename Vec4<R>::T* __restrict__ bo, PotParams<R> P,
+               TypeParams T, R* __restrict__ M, R* __restrict__ Dg, R* __restrict__ dinv) {
   using R4 = typename Vec4<R>::T;
-  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
-  for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
-    R4 ui = u[i];
-    int ti = (int)ui.w;
-    const RepInfo& ri = reps[rep[i]];
-    R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
-    if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
-    int nc = ncov[i], na = nall[i];
-    R wsum = R(0), selfm = R(0);
-    const int* pn = nbr + i;
-    const int* pc = code + i;
-    R* pm = M + i;
-#pragma unroll 4
-    for (int e = 0; e < na; ++e) {
-      size_t off = (size_t)e * ld;
-      int j = pn[off];
-      R4 uj = u[j];
-      R rx, ry, rz;
-      rel_vec<R>(ui, uj, pc[off], hx, hy, hz, rx, ry, rz);
-      R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
-      int tj = (int)uj.w;
-      int pb = ti * 2 + tj;
-      R K, dK;
-      coul_fn<R>(r, P.gshield3[pb], P.inv_rcoul, P.ke, K, dK);
-      R m = K;
-      if (e < nc && r < P.Sout[pb]) {
-        R fc, dfc;
-        cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
-        R fA = P.B[pb] * ct_exp<R>(-P.lam2[pb] * r);
-        R bij = bo[(size_t)i * cap_cov + e].x;
-        R bji = bo[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]].x;
-        R w = R(0.5) * P.kappa[pb] * fc * fA * (bij + bji);
-        m -= R(2) * w;
-        wsum += w;
-      }
-      if (j == i) selfm += m;
-      pm[off] = m;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  R4 ui = u[i];
+  int ti = (int)ui.w;
+  const RepInfo& ri = reps[rep[i]];
+  R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
+  if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
+  int nc = ncov[i], na = nall[i];
+  R wsum = R(0), selfm = R(0);
+  const int* pn = nbr + i;
+  const int* pc = code + i;
+  R* pm = M + i;
+  // covalent entries: K minus twice the bond-order coupling w
+  for (int e = 0; e < nc; ++e) {
+    size_t off = (size_t)e * ld;
+    int j = pn[off];
+    R4 uj = u[j];
+    R rx, ry, rz;
+    rel_vec<R>(ui, uj, pc[off], hx, hy, hz, rx, ry, rz);
+    R r2 = rx * rx + ry * ry + rz * rz;
+    int tj = (int)uj.w;
+    int pb = ti * 2 + tj;
+    R m = coul_K_r2<R>(r2, P.gshield3[pb], P.inv_rcoul, P.ke);
+    R r = ct_sqrt<R>(r2);
+    if (r < P.Sout[pb]) {
+      R fc, dfc;
+      cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
+      R fA = P.B[pb] * ct_exp<R>(-P.lam2[pb] * r);
+      R bij = bo[(size_t)i * cap_cov + e].x;
+      R bji = bo[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]].x;
+      R w = R(0.5) * P.kappa[pb] * fc * fA * (bij + bji);
+      m -= R(2) * w;
+      wsum += w;
     }
-    R D = (R)(2.0 * T.J[ti]) + R(2) * wsum;
-    Dg[i] = D;
-    dinv[i] = R(1) / (D + selfm);
+    if (j == i) selfm += m;
+    pm[off] = m;
   }
+  // the rest: K only, streamed
+  const R gs_i0 = P.gshield3[ti * 2], gs_i1 = P.gshield3[ti * 2 + 1];
+  int jn[PB], cn[PB];
+#pragma unroll
+  for (int k = 0; k < PB; ++k) {
+    bool ok = nc + k < na;
+    jn[k] = ok ? __ldg(pn + (size_t)(nc + k) * ld) : i;
+    cn[k] = ok ? __ldg(pc + (size_t)(nc + k) * ld) : pack_code(0, 0, 0);
+  }
+  for (int e = nc; e < na; e += PB) {
+    int jc[PB], cc[PB];
+#pragma unroll
+    for (int k = 0; k < PB; ++k) {
+      jc[k] = jn[k];
+      cc[k] = cn[k];
+      int en = e + PB + k;
+      bool ok = en < na;
+      jn[k] = ok ? __ldg(pn + (size_t)en * ld) : i;
+      cn[k] = ok ? __ldg(pc + (size_t)en * ld) : pack_code(0, 0, 0);
+    }
+    R4 uj[PB];
+#pragma unroll
+    for (int k = 0; k < PB; ++k) uj[k] = u[jc[k]];
+#pragma unroll
+    for (int k = 0; k < PB; ++k) {
+      if (e + k < na) {
+        R rx, ry, rz;
+        rel_vec<R>(ui, uj[k], cc[k], hx, hy, hz, rx, ry, rz);
+        R r2 = rx * rx + ry * ry + rz * rz;
+        R m = coul_K_r2<R>(r2, uj[k].w != R(0) ? gs_i1 : gs_i0, P.inv_rcoul, P.ke);
+        if (jc[k] == i) selfm += m;
+        pm[(size_t)(e + k) * ld] = m;
+      }
+    }
+  }
+  R D = (R)(2.0 * T.J[ti]) + R(2) * wsum;
+  Dg[i] = D;
+  dinv[i] = R(1) / (D + selfm);
 }
 
 // ---------------------------------------------------------------- covalent forces
@@ -346,25 +382,26 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
 // ---------------------------------------------------------------- charge forces + gather
 // One thread per atom over its column of the list: force, per-atom energy
 // and virial in the working precision (compensated energy sum), then the
-// FP64 store, half kick, kinetic energy and per-replica sums.
+// FP64 store, half kick, kinetic energy and per-replica sums. Threads take
+// 256-atom tiles strided over the grid, so the FP64 per-replica reductions
+// are paid once per thread, not once per atom.
 template <class R>
-__global__ void k_coul_gather(int N, int cap_cov, int ld, int chunk,
-                              const typename Vec4<R>::T* __restrict__ u, const int* __restrict__ rep,
-                              const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
-                              const int* __restrict__ code, const int* __restrict__ ncov,
-                              const int* __restrict__ nall, const int* __restrict__ rev,
-                              const typename Vec4<R>::T* __restrict__ gslot, const R* __restrict__ qr,
-                              PotParams<R> P, TypeParams T, int kick, double half_dt,
-                              const uint8_t* __restrict__ frozen, double* __restrict__ F,
-                              double* __restrict__ v, double* __restrict__ e_atom,
-                              double* __restrict__ rep_acc, unsigned* __restrict__ err) {
+__global__ void __launch_bounds__(256)
+    k_coul_gather(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
+                  const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
+                  const int* __restrict__ code, const int* __restrict__ ncov, const int* __restrict__ nall,
+                  const int* __restrict__ rev, const typename Vec4<R>::T* __restrict__ gslot,
+                  const R* __restrict__ qr, PotParams<R> P, TypeParams T, int kick, double half_dt,
+                  const uint8_t* __restrict__ frozen, double* __restrict__ F, double* __restrict__ v,
+                  double* __restrict__ e_atom, double* __restrict__ rep_acc, unsigned* __restrict__ err) {
   using R4 = typename Vec4<R>::T;
   RepAcc<2> accE;   // (E, KE)
   RepAcc<9> accW;   // virial
   accE.init();
   accW.init();
-  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
-  for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
+  for (int t = blockIdx.x; (long long)t * 256 < N; t += gridDim.x) {
+    int i = t * 256 + (int)threadIdx.x;
+    if (i >= N) break;
     R4 ui = u[i];
     int ti = (int)ui.w;
     int ri_id = rep[i];
@@ -380,6 +417,7 @@ __global__ void k_coul_gather(int N, int cap_cov, int ld, int chunk,
     for (int k = 0; k < 9; ++k) w[k] = R(0);
     const int* pn = nbr + i;
     const int* pc = code + i;
+    const R gs_i0 = P.gshield3[ti * 2], gs_i1 = P.gshield3[ti * 2 + 1];
     // covalent entries: charge term plus the slot gather
     for (int e = 0; e < nc; ++e) {
       size_t off = (size_t)e * ld;
@@ -387,12 +425,11 @@ __global__ void k_coul_gather(int N, int cap_cov, int ld, int chunk,
       R4 uj = u[j];
       R rx, ry, rz;
       rel_vec<R>(ui, uj, pc[off], hx, hy, hz, rx, ry, rz);
-      R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
-      int tj = (int)uj.w;
-      R K, dK;
-      coul_fn<R>(r, P.gshield3[ti * 2 + tj], P.inv_rcoul, P.ke, K, dK);
+      R r2 = rx * rx + ry * ry + rz * rz;
+      R r, ir, K, c;
+      coul_fn_r2<R>(r2, uj.w != R(0) ? gs_i1 : gs_i0, P.inv_rcoul, P.ke, r, ir, K, c);
       R qq = qi * qr[j];
-      R c = qq * dK / r;
+      c *= qq;
       R4 go = gslot[(size_t)i * cap_cov + e];
       R4 gr = gslot[(size_t)j * cap_cov + rev[(size_t)i * cap_cov + e]];
       R gx = c * rx + go.x - gr.x, gy = c * ry + go.y - gr.y, gz = c * rz + go.z - gr.z;
@@ -405,27 +442,51 @@ __global__ void k_coul_gather(int N, int cap_cov, int ld, int chunk,
       w[3] += ry * tx; w[4] += ry * ty; w[5] += ry * tz;
       w[6] += rz * tx; w[7] += rz * ty; w[8] += rz * tz;
     }
-    // remaining entries: charge term only
-#pragma unroll 4
-    for (int e = nc; e < na; ++e) {
-      size_t off = (size_t)e * ld;
-      int j = pn[off];
-      R4 uj = u[j];
-      R rx, ry, rz;
-      rel_vec<R>(ui, uj, pc[off], hx, hy, hz, rx, ry, rz);
-      R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
-      int tj = (int)uj.w;
-      R K, dK;
-      coul_fn<R>(r, P.gshield3[ti * 2 + tj], P.inv_rcoul, P.ke, K, dK);
-      R qq = qi * qr[j];
-      R c = qq * dK / r;
-      fx += c * rx; fy += c * ry; fz += c * rz;
-      ec.add(R(0.5) * qq * K);
-      R hc = R(-0.5) * c;
-      R hx_ = hc * rx, hy_ = hc * ry, hz_ = hc * rz;
-      w[0] += rx * hx_; w[1] += rx * hy_; w[2] += rx * hz_;
-      w[3] += ry * hx_; w[4] += ry * hy_; w[5] += ry * hz_;
-      w[6] += rz * hx_; w[7] += rz * hy_; w[8] += rz * hz_;
+    // remaining entries: charge term only, streamed
+    int jn[PB], cn[PB];
+#pragma unroll
+    for (int k = 0; k < PB; ++k) {
+      bool ok = nc + k < na;
+      jn[k] = ok ? __ldg(pn + (size_t)(nc + k) * ld) : i;
+      cn[k] = ok ? __ldg(pc + (size_t)(nc + k) * ld) : pack_code(0, 0, 0);
+    }
+    for (int e = nc; e < na; e += PB) {
+      int jc[PB], cc[PB];
+#pragma unroll
+      for (int k = 0; k < PB; ++k) {
+        jc[k] = jn[k];
+        cc[k] = cn[k];
+        int en = e + PB + k;
+        bool ok = en < na;
+        jn[k] = ok ? __ldg(pn + (size_t)en * ld) : i;
+        cn[k] = ok ? __ldg(pc + (size_t)en * ld) : pack_code(0, 0, 0);
+      }
+      R4 uj[PB];
+      R qj[PB];
+#pragma unroll
+      for (int k = 0; k < PB; ++k) {
+        uj[k] = u[jc[k]];
+        qj[k] = qr[jc[k]];
+      }
+#pragma unroll
+      for (int k = 0; k < PB; ++k) {
+        if (e + k < na) {
+          R rx, ry, rz;
+          rel_vec<R>(ui, uj[k], cc[k], hx, hy, hz, rx, ry, rz);
+          R r2 = rx * rx + ry * ry + rz * rz;
+          R r, ir, K, c;
+          coul_fn_r2<R>(r2, uj[k].w != R(0) ? gs_i1 : gs_i0, P.inv_rcoul, P.ke, r, ir, K, c);
+          R qq = qi * qj[k];
+          c *= qq;
+          fx += c * rx; fy += c * ry; fz += c * rz;
+          ec.add(R(0.5) * qq * K);
+          R hc = R(-0.5) * c;
+          R hx_ = hc * rx, hy_ = hc * ry, hz_ = hc * rz;
+          w[0] += rx * hx_; w[1] += rx * hy_; w[2] += rx * hz_;
+          w[3] += ry * hx_; w[4] += ry * hy_; w[5] += ry * hz_;
+          w[6] += rz * hx_; w[7] += rz * hy_; w[8] += rz * hz_;
+        }
+      }
     }
     double Fx = fx, Fy = fy, Fz = fz;
     F[3 * i] = Fx; F[3 * i + 1] = Fy; F[3 * i + 2] = Fz;
@@ -485,10 +546,8 @@ void launch_bond(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
 template <class R>
 void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st) {
   if (S.N == 0) return;
-  int chunk;
-  int grid = atom_dims(S.N, S.nsm, (const void*)k_assemble<R>, 256, chunk);
-  k_assemble<R><<<grid, 256, 0, st>>>(
-      S.N, S.cap_cov, S.ld, chunk, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+  k_assemble<R><<<(S.N + 255) / 256, 256, 0, st>>>(
+      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
       S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, (R*)S.M, (R*)S.Dg, (R*)S.dinv);
 }
 
@@ -505,10 +564,13 @@ template <class R>
 void launch_coul_gather(const DevState& S, const PotParams<R>& P, const TypeParams& T, int kick, double half_dt,
                         cudaStream_t st) {
   if (S.N == 0) return;
-  int chunk;
-  int grid = atom_dims(S.N, S.nsm, (const void*)k_coul_gather<R>, 256, chunk);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coul_gather<R>, 256, 0) != cudaSuccess || occ < 1)
+    occ = 1;
+  long long tiles = ((long long)S.N + 255) / 256, slots = (long long)S.nsm * occ;
+  int grid = (int)(tiles < slots ? tiles : slots);
   k_coul_gather<R><<<grid, 256, 0, st>>>(
-      S.N, S.cap_cov, S.ld, chunk, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
       S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.gslot, (const R*)S.qr, P, T, kick, half_dt,
       S.frozen, S.F, S.v, S.e_atom, S.rep_acc, S.err);
 }
