@@ -13,9 +13,15 @@ max-over-ranks time. `--impl reference` times the FP64 CPU oracle on a
 bounded sample of the same workload (there is no other reference
 implementation: the paper ships no code).
 """
+import os
+
+# The CPU baseline (the oracle) runs single-threaded, so that its reported
+# core count is what it used: pin the BLAS/OpenMP pools before numpy loads.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import argparse
 import json
-import os
 import statistics
 import subprocess
 import sys
@@ -120,11 +126,36 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# DRAM traffic of one k_cg_mv launch from one `ncu --set full` capture on
+# the 251,366-atom stepped slab (dram__bytes_read.sum + dram__bytes_write.sum)
+# and the list entries of that launch. Traffic grows with the entries
+# (it is 0.98 x the algorithmic bytes there), so a full launch is scaled by
+# its entry count. Reset to None when the kernel changes.
+MV_TRAFFIC_CAPTURE = {"bytes": 461.072896e6 + 3.870208e6, "entries": 251366 * 226.5986569384881}
+
+
 def cg_matvec_bytes(n_atoms, entries, rs):
     """Algorithmic bytes of one CG matrix pass: per list entry the neighbour
     index and the stored coefficient; per atom the gathered y (once), its own
     y, d, v, r and D, the written w, the entry count and the replica id."""
     return entries * (4 + rs) + n_atoms * (7 * rs + 8)
+
+
+def max_over_ranks(x, device, world):
+    """Max of a per-rank float over all ranks (identity at world 1)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(n_atoms, steps, world, ms):
+    """Whole-job atom-steps/s: every rank steps its own n_atoms-atom replica,
+    timed by the slowest rank's ms."""
+    return n_atoms * steps * world / (ms / 1e3)
 
 
 def run_ours(a):
@@ -168,19 +199,16 @@ def run_ours(a):
     e1.record(stream)
     barrier()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dev, world)
     st1 = sysm.status()
     n = s.n
-    value = n * a.steps * world / (ms / 1e3)
+    value = aggregate_value(n, a.steps, world, ms)
     cg_per_step = (st1["cg_iters_total"] - st0["cg_iters_total"]) / a.steps
     rebuilds = st1["rebuilds"] - st0["rebuilds"]
-    # our kernel launches in the timed region: 20 per step outside the CG
-    # loop, 2 per CG iteration (at least one iteration per solve)
-    launches = int(20 * a.steps + 2 * max(st1["cg_iters_total"] - st0["cg_iters_total"], a.steps))
+    # our kernel launches in the timed region: 22 per step outside the CG
+    # loop (12 of them the list check/rebuild, which return at once when no
+    # rebuild is due), 2 per CG iteration
+    launches = int(22 * a.steps + 2 * (st1["cg_iters_total"] - st0["cg_iters_total"]))
 
     # per-kernel timing (CUDA events on the library's stream)
     ph = sysm.profile_steps(a.profile_steps, DT)
@@ -191,6 +219,8 @@ def run_ours(a):
     peak, peak_kind = peaks()
     mv_s = mv_ms / max(mv_n, 1) / 1e3
     achieved = bytes_mv / mv_s / 1e9 if mv_n else None
+    traffic = (MV_TRAFFIC_CAPTURE["bytes"] * entries / MV_TRAFFIC_CAPTURE["entries"]
+               if MV_TRAFFIC_CAPTURE else None)
     total_ph = sum(t for t, _ in ph.values())
     phases = {k: {"ms_per_step": round(t / a.profile_steps, 4), "launches": c, "share": round(t / total_ph, 4)}
               for k, (t, c) in ph.items()}
@@ -211,12 +241,8 @@ def run_ours(a):
         sysm.get("positions", pin_x)
         sysm.get("velocities", pin_v)
     barrier()
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": n * a.e2e_steps * world / t_e2e, "unit": UNIT,
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dev, world)
+    e2e = {"value": aggregate_value(n, a.e2e_steps, world, t_e2e * 1e3), "unit": UNIT,
            "h2d_bytes_per_step": 24 * n, "d2h_bytes_per_step": 48 * n + 8}
     sysm.close()
     del sysm
@@ -257,7 +283,7 @@ def run_ours(a):
                    "mean_entries_per_atom": st2["mean_all"], "mean_covalent_entries": st2["mean_cov"]},
         "roofline": {"kernel": "k_cg_mv (charge CG matrix pass)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": None, "peak_kind": peak_kind,
+                     "traffic": traffic, "peak_kind": peak_kind,
                      "bytes_per_launch": bytes_mv, "ms_per_launch": mv_s * 1e3},
         "phases": phases,
         "e2e": e2e,

@@ -99,6 +99,12 @@ static void pack_params(const ctbop_params& p, double skin, PotParams<Rr>& P) {
     P.Sout[k] = (Rr)p.S[k];
     P.kappa[k] = (Rr)p.kappa[k];
     P.pi_SR[k] = (Rr)(M_PI / (p.S[k] - p.R[k]));
+    P.A64[k] = p.A[k];
+    P.B64[k] = p.B[k];
+    P.lam1_64[k] = p.lambda1[k];
+    P.lam2_64[k] = p.lambda2[k];
+    P.Rin64[k] = p.R[k];
+    P.Sout64[k] = p.S[k];
     P.rcov_list2[k] = (Rr)((p.S[k] + skin) * (p.S[k] + skin));
     double sg = p.sigma[k], pp = p.p[k];
     P.sigma[k] = (Rr)sg;
@@ -549,7 +555,7 @@ static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double 
   for (int64_t k = 0; k < n && !rc; ++k) {
     CK(cudaMemsetAsync(S.err, 0, sizeof(unsigned), st));
     rc = timed(0, 1, [&] { launch_kick_drift<Rr>(S, s->T, dt, 0.25 * s->o.skin * s->o.skin, st); });
-    if (!rc) rc = timed(1, 11, [&] { launch_zero_acc(S, st); launch_rebuild<Rr>(S, P, st); });
+    if (!rc) rc = timed(1, 12, [&] { launch_zero_acc(S, st); launch_rebuild<Rr>(S, P, st); });
     if (!rc) rc = timed(2, 1, [&] { launch_bond<Rr>(S, P, st); });
     if (!rc) rc = timed(3, 1, [&] { launch_assemble<Rr>(S, P, s->T, st); });
     if (!rc) rc = timed(4, 3, [&] { launch_cg_begin<Rr>(S, s->T, st, cg_tol(s)); });

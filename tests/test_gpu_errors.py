@@ -1,0 +1,97 @@
+"""Error paths of the C ABI, all raised on the host side or through the
+library's device error word. Nothing here faults the GPU: bad values are
+rejected by argument checks, and non-finite positions are caught by the
+binning kernel, which records them and substitutes zero."""
+import numpy as np
+import pytest
+
+from paper_1802_07871_gb300 import ctbop
+from paper_1802_07871_gb300 import structures as st
+
+pytestmark = pytest.mark.gpu
+P0 = st.load_params("p0")
+
+
+def _system(s, **kw):
+    sysm = ctbop.System(P0, **kw)
+    sysm.load(s)
+    return sysm
+
+
+def test_cg_iteration_limit_is_reported():
+    """Too few CG iterations: status says CG_NOT_CONVERGED, the solve stopped
+    at the limit, and the results are still written (finite)."""
+    s = st.bulk_3c_512()
+    sysm = _system(s, precision="fp64", cg_max_iter=3)
+    sysm.compute()
+    d = sysm.status()
+    assert d["rc"] == "CG_NOT_CONVERGED"
+    assert d["cg_iters_last"] == 3
+    q = sysm.get("charges")
+    assert np.all(np.isfinite(q)) and abs(q.sum()) < 1e-10
+    with pytest.raises(ctbop.CtbopError, match="CG_NOT_CONVERGED"):
+        sysm.step(1, 0.5)
+    sysm.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tiny_capacities_regrow(prec):
+    """Capacities far below the need: the first build measures the counts and
+    the lists regrow; results equal a default run (entry order inside a
+    list may differ, so only rounding changes)."""
+    s = st.stepped_slab_small(8, 4, 6)
+    a = _system(s, precision=prec)
+    a.compute()
+    Fa, qa = a.get("forces"), a.get("charges")
+    b = _system(s, precision=prec, cap_cov=4, cap_all=8)
+    b.compute()
+    Fb, qb = b.get("forces"), b.get("charges")
+    tol = 1e-10 if prec == "fp64" else 2e-4
+    rms = np.sqrt(np.mean(Fa ** 2))
+    assert np.max(np.abs(Fa - Fb)) / rms < tol
+    assert np.max(np.abs(qa - qb)) < (1e-10 if prec == "fp64" else 1e-5)
+    assert b.status()["rc"] == "OK"
+    a.close()
+    b.close()
+
+
+def test_nonfinite_position_is_reported():
+    s = st.bulk_3c_512()
+    x = s.x.copy()
+    x[7, 1] = np.nan
+    sysm = ctbop.System(P0, precision="mixed")
+    sysm.load(st.Structure("bad", x, s.types, s.box, s.pbc))
+    with pytest.raises(ctbop.CtbopError, match="NONFINITE"):
+        sysm.compute()
+    sysm.close()
+
+
+def test_invalid_arguments_are_rejected():
+    s = st.bulk_3c_512()
+    sysm = ctbop.System(P0, precision="mixed")
+    with pytest.raises(ctbop.CtbopError, match="STATE"):
+        sysm.set_types(s.types)                    # before set_layout
+    with pytest.raises(ctbop.CtbopError, match="INVALID_ARG"):
+        sysm.set_layout([0, 10, 5])                # offsets decrease
+    sysm.set_layout([0, s.n])
+    with pytest.raises(ctbop.CtbopError, match="INVALID_ARG"):
+        sysm.set_box([[-1.0, 5.0, 5.0]], [[True, True, True]])
+    bad = s.types.copy()
+    bad[3] = 2
+    with pytest.raises(ctbop.CtbopError, match="INVALID_ARG"):
+        sysm.set_types(bad)
+    sysm.load(s)
+    with pytest.raises(ctbop.CtbopError, match="INVALID_ARG"):
+        sysm.step(1, 0.0)
+    with pytest.raises(ctbop.CtbopError, match="INVALID_ARG"):
+        sysm.step(1, float("nan"))
+    sysm.compute()
+    assert sysm.status()["rc"] == "OK"
+    sysm.close()
+
+
+def test_create_rejects_bad_options():
+    with pytest.raises(ctbop.CtbopError):
+        ctbop.System(P0, cg_max_iter=0)
+    with pytest.raises(ctbop.CtbopError):
+        ctbop.System(P0, skin=-0.1)
