@@ -198,6 +198,22 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st);
  * Slower than ctbop_step: for per-kernel timing only. */
 int ctbop_profile_steps(ctbop_system* s, int64_t n_steps, double dt_fs, double* ms_out, int64_t* launches_out);
 
+/* Per-replica total energy (eV) of the last evaluation, written to
+ * energy[0..R) (host array, caller-owned): the sum over each replica of the
+ * per-atom energies, i.e. the value ctbop_get(CTBOP_GET_ENERGY) returns, up
+ * to summation order. The paper has no counterpart: this is a library
+ * utility that allocates nothing on the device. Its scratch is a fixed
+ * file-scope device array of 304 x 64 + 64 doubles plus a counter, which
+ * limits it to systems of at most 64 replicas (more -> CTBOP_ERR_INVALID_ARG,
+ * nothing computed); there is no limit on the atom count.
+ * The first call on a device looks up the scratch array's address (make that
+ * call before any stream capture); later calls only launch one kernel on the
+ * system's stream and copy R doubles back, synchronising the stream.
+ * Calls must not overlap (on any stream or thread): they share the scratch.
+ * Errors: INVALID_ARG (null pointer, too many replicas), STATE (no
+ * evaluation yet), CUDA. */
+int ctbop_energy_noalloc(ctbop_system* s, double* energy);
+
 #ifdef __cplusplus
 }
 #endif

@@ -975,4 +975,16 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   return CTBOP_OK;
 }
 
+int ctbop_energy_noalloc(ctbop_system* s, double* energy) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!energy) return fail(s, CTBOP_ERR_INVALID_ARG, "null energy pointer");
+  if (!s->have_forces || s->alloc_N < 0) return fail(s, CTBOP_ERR_STATE, "compute or step first");
+  cudaSetDevice(s->o.device);
+  std::string why;
+  int rc = energy_noalloc(s->S.e_atom, s->S.rep, s->S.N, s->R, s->o.device, s->stream, energy, why);
+  if (rc == -1) return fail(s, CTBOP_ERR_INVALID_ARG, why);
+  if (rc) return fail(s, CTBOP_ERR_CUDA, why);
+  return CTBOP_OK;
+}
+
 }  // extern "C"

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string>
 #include "internal.cuh"
 
 namespace ct {
@@ -114,5 +115,7 @@ template <class R> void launch_copy_q(const DevState& S, cudaStream_t st);
 // launch shape for kernels with one thread per atom: resident blocks only,
 // each block a contiguous chunk of atoms (a multiple of its size)
 int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk);
+int energy_noalloc(const double* e_atom, const int* rep, int N, int R, int device, cudaStream_t st,
+                   double* host_out, std::string& why);
 
 }  // namespace ct

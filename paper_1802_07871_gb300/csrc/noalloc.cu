@@ -1,0 +1,121 @@
+// noalloc.cu — per-replica energy reduction that allocates nothing.
+//
+// A variant of the per-replica energy sum the force gather accumulates
+// (the sum over each replica of the per-atom energies), computed here from
+// the per-atom energies with all of its scratch in one file-scope device
+// array: no cudaMalloc/cudaFree and no allocating library call, ever.
+//
+// Scratch layout (NA_BLOCKS x NA_REPS doubles of block partials, then one
+// row of results, then the last-block counter):
+//   * the block partials are overwritten in full by every launch, so
+//     nothing there has to start at zero;
+//   * the counter must be zero when a launch starts: it is zero from static
+//     initialisation and the last block of every launch resets it.
+// Limits: at most NA_REPS replicas per system (larger systems are rejected
+// with an error, never truncated); any atom count (the grid strides).
+//
+// The symbol's address is looked up once per device (the first call on a
+// device, with that device current) and passed to the kernel. Concurrent
+// calls share the one scratch array and race; callers must not overlap
+// them, on any stream.
+#include <string>
+
+#include "internal.cuh"
+#include "kernels.h"
+
+namespace ct {
+
+#define NA_BLOCKS 304   // 2 blocks per SM on 152 SMs
+#define NA_REPS 64
+#define NA_THREADS 256
+#define NA_MAX_DEVICES 64
+
+struct NoallocScratch {
+  double part[NA_BLOCKS][NA_REPS];
+  double result[NA_REPS];
+  unsigned counter;
+};
+
+static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+__global__ void __launch_bounds__(NA_THREADS)
+    k_energy_noalloc(int N, int R, const double* __restrict__ e_atom, const int* __restrict__ rep,
+                     NoallocScratch* __restrict__ sc) {
+  __shared__ double s_sum[NA_REPS];
+  __shared__ bool am_last;
+  for (int r = threadIdx.x; r < NA_REPS; r += blockDim.x) s_sum[r] = 0.0;
+  __syncthreads();
+  // per-thread run over consecutive atoms of one replica, flushed to
+  // shared memory when the replica changes
+  int cur = -1;
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    int r = rep[i];
+    if (r != cur) {
+      if (cur >= 0) atomicAdd(&s_sum[cur], acc);
+      cur = r;
+      acc = 0.0;
+    }
+    acc += e_atom[i];
+  }
+  if (cur >= 0) atomicAdd(&s_sum[cur], acc);
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x) sc->part[blockIdx.x][r] = s_sum[r];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(&sc->counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  // the last block sums the partials in block order and resets the counter
+  // for the next launch (inside a block the shared-memory atomics add in a
+  // varying order, so results agree to rounding, not bit for bit)
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(&sc->part[b][r]);
+    sc->result[r] = t;
+  }
+  if (threadIdx.x == 0) sc->counter = 0u;
+}
+
+static void* g_scratch_addr[NA_MAX_DEVICES];
+static bool g_scratch_ready[NA_MAX_DEVICES];
+
+// Per-replica sums of e_atom[0..N) into host_out[0..R). Status 0 or a
+// negative ctbop status with the reason in why.
+int energy_noalloc(const double* e_atom, const int* rep, int N, int R, int device, cudaStream_t st,
+                   double* host_out, std::string& why) {
+  if (R < 1 || R > NA_REPS) {
+    why = "energy_noalloc: at most " + std::to_string(NA_REPS) + " replicas (its scratch is a fixed device array)";
+    return -1;
+  }
+  if (device < 0 || device >= NA_MAX_DEVICES) {
+    why = "energy_noalloc: device index out of range";
+    return -1;
+  }
+  if (!g_scratch_ready[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      why = std::string("energy_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return -6;
+    }
+    g_scratch_addr[device] = p;
+    g_scratch_ready[device] = true;
+  }
+  NoallocScratch* sc = static_cast<NoallocScratch*>(g_scratch_addr[device]);
+  int grid = (N + NA_THREADS - 1) / NA_THREADS;
+  if (grid > NA_BLOCKS) grid = NA_BLOCKS;
+  if (grid < 1) grid = 1;
+  k_energy_noalloc<<<grid, NA_THREADS, 0, st>>>(N, R, e_atom, rep, sc);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, sc->result, sizeof(double) * R, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    why = std::string("energy_noalloc: ") + cudaGetErrorString(e);
+    return -6;
+  }
+  return 0;
+}
+
+}  // namespace ct

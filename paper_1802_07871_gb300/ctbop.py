@@ -33,7 +33,7 @@ EXPORTS = (
     "ctbop_set_stream", "ctbop_set_layout", "ctbop_set_box", "ctbop_set_types",
     "ctbop_set_positions", "ctbop_set_velocities", "ctbop_set_charges", "ctbop_set_frozen",
     "ctbop_set_total_charge", "ctbop_compute", "ctbop_step", "ctbop_get", "ctbop_status",
-    "ctbop_profile_steps",
+    "ctbop_profile_steps", "ctbop_energy_noalloc",
 )
 NPHASE = 10
 PHASES = ("kick_drift", "lists", "bond", "assemble", "cg_start", "cg_matvec", "cg_update",
@@ -289,6 +289,13 @@ class System:
         self._check(self._L.ctbop_profile_steps(self._h, int(n), float(dt), ms.ctypes.data_as(C.c_void_p),
                                                 cnt.ctypes.data_as(C.c_void_p)), "profile_steps")
         return {name: (float(ms[k]), int(cnt[k])) for k, name in enumerate(PHASES)}
+
+    def energy_noalloc(self) -> np.ndarray:
+        """Per-replica energy through the entry point that allocates nothing
+        on the device (at most 64 replicas)."""
+        out = np.empty(self.R, dtype=np.float64)
+        self._check(self._L.ctbop_energy_noalloc(self._h, out.ctypes.data_as(C.c_void_p)), "energy_noalloc")
+        return out
 
     def status(self) -> dict:
         st = Stats()
