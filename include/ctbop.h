@@ -198,6 +198,32 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st);
  * Slower than ctbop_step: for per-kernel timing only. */
 int ctbop_profile_steps(ctbop_system* s, int64_t n_steps, double dt_fs, double* ms_out, int64_t* launches_out);
 
+/* Replace the potential's parameters (copied; same validity rules as
+ * ctbop_create). The next compute/step rebuilds the lists and re-captures
+ * its graphs. Errors: INVALID_ARG. */
+int ctbop_set_params(ctbop_system* s, const ctbop_params* p);
+
+/* Force-matching loss and its gradient with respect to every parameter
+ * (the spec differentiation pattern; the paper fits its parameters to
+ * energies, forces and charges, Sec. 2, but prints no fitting method).
+ *   loss = sum_r w_E[r] (E_r - E_ref[r])^2 + sum_r w_F[r] sum_{i in r} |F_i - F_ref_i|^2
+ * at the charge minimiser of the current positions. dtheta receives dloss/d
+ * of every field of ctbop_params, in that struct's layout (host,
+ * caller-owned; the mass fields get 0). Pair fields enter E through the
+ * ordered pair (t_i, t_j): the gradient of a symmetric pair constant is the
+ * sum of its two entries.
+ * w_E, E_ref: [R] host or NULL (no energy term); w_F: [R] host, F_ref:
+ * [N,3] host, or NULL (no force term). The energy part is the analytic
+ * partial derivative at fixed charges (exact at the minimiser). The force
+ * part adds a directional second derivative along dL/dF (central difference
+ * of the analytic gradient, step 1e-4 A over the largest component) and the
+ * charge response through one adjoint CG solve. Leaves the system at its
+ * positions with the minimiser charges, energies and forces.
+ * FP64 policy only (CTBOP_ERR_INVALID_ARG otherwise); CG_NOT_CONVERGED if the
+ * charge or adjoint solve does not converge. */
+int ctbop_param_grad(ctbop_system* s, const double* w_E, const double* E_ref, const double* w_F,
+                     const double* F_ref, double* loss, ctbop_params* dtheta);
+
 /* Per-replica total energy (eV) of the last evaluation, written to
  * energy[0..R) (host array, caller-owned): the sum over each replica of the
  * per-atom energies, i.e. the value ctbop_get(CTBOP_GET_ENERGY) returns, up

@@ -541,3 +541,78 @@ def velocity_verlet(x, v, types, box, pbc, params, dt, nsteps, frozen=None,
         v = np.where(mob, v + 0.5 * dt * F * inv_m, 0.0)
         etot.append(res["E"] + kinetic_energy(v, types, params))
     return x, v, res["q"], np.array(etot)
+
+
+# ----------------------------------------------------------------------------
+# force-matching loss and its parameter gradient (the definition, by central
+# differences; the paper fits its parameters to DFT energies, forces and
+# charges, Sec. 2, without printing a method)
+# ----------------------------------------------------------------------------
+def param_leaves(params):
+    """Every scalar of a parameter dictionary the energy depends on, as
+    (path, value): pair, bond, triplet, self and charge-kernel entries (the
+    masses and labels are not parameters of E)."""
+    out = []
+    for sec in ("pair", "bond", "triplet"):
+        for key in sorted(params[sec]):
+            for f in sorted(params[sec][key]):
+                v = params[sec][key][f]
+                if isinstance(v, (list, tuple)):
+                    out += [((sec, key, f, l), float(x)) for l, x in enumerate(v)]
+                else:
+                    out.append(((sec, key, f), float(v)))
+    for f in ("E0", "chi", "J"):
+        out += [(("self", f, t), float(x)) for t, x in enumerate(params["self"][f])]
+    out += [(("coulomb", "gamma", t), float(x)) for t, x in enumerate(params["coulomb"]["gamma"])]
+    out += [(("coulomb", "r_coul"), float(params["coulomb"]["r_coul"])),
+            (("coulomb", "k_e"), float(params["coulomb"]["k_e"]))]
+    return out
+
+
+def with_leaf(params, path, value):
+    """A deep copy of params with the scalar at path set to value."""
+    import copy
+    p = copy.deepcopy(params)
+    node = p
+    for k in path[:-1]:
+        node = node[k]
+    node[path[-1]] = value
+    return p
+
+
+def force_matching_loss(structs, params, w_E=None, E_ref=None, w_F=None, F_ref=None):
+    """loss = sum_r w_E[r] (E_r - E_ref[r])^2 + sum_r w_F[r] sum_i |F_i - F_ref_i|^2
+    with every structure's charges at their minimiser (total charge 0)."""
+    loss = 0.0
+    off = 0
+    for r, s in enumerate(structs):
+        o = evaluate(s.x, s.types, s.box, s.pbc, params)
+        if w_E is not None:
+            loss += w_E[r] * (o["E"] - E_ref[r]) ** 2
+        if w_F is not None:
+            d = o["F"] - F_ref[off:off + s.n]
+            loss += w_F[r] * float(np.sum(d * d))
+        off += s.n
+    return loss
+
+
+def loss_grad_fd(structs, params, w_E=None, E_ref=None, w_F=None, F_ref=None, paths=None, h=1e-4):
+    """d loss / d theta for every leaf (or the given paths) by central
+    differences with step h * max(|theta|, 1), Richardson-extrapolated from
+    that step and half of it (error O(h^4)): the loss is quadratic in E and
+    F, whose derivatives reach hundreds of eV per unit of some parameters,
+    so a single central difference at h = 1e-4 keeps ~1e-4 relative error."""
+    leaves = dict(param_leaves(params))
+    out = {}
+
+    def central(path, v, step):
+        lp = force_matching_loss(structs, with_leaf(params, path, v + step), w_E, E_ref, w_F, F_ref)
+        lm = force_matching_loss(structs, with_leaf(params, path, v - step), w_E, E_ref, w_F, F_ref)
+        return (lp - lm) / (2.0 * step)
+
+    for path in (paths if paths is not None else list(leaves)):
+        v = leaves[path]
+        step = h * max(abs(v), 1.0)
+        d1, d2 = central(path, v, step), central(path, v, 0.5 * step)
+        out[path] = (4.0 * d2 - d1) / 3.0
+    return out

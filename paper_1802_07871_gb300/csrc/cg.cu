@@ -387,7 +387,8 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
                           R* __restrict__ r, R* __restrict__ y, R* __restrict__ v, R* __restrict__ dqv,
                           double* __restrict__ cg,
                           unsigned long long* __restrict__ rmax, int Rn, int* __restrict__ conv, int* __restrict__ iters,
-                          int* __restrict__ blocks, int* __restrict__ active, double tol) {
+                          int* __restrict__ blocks, int* __restrict__ active, double tol,
+                          const double* __restrict__ rhs) {
   const int ub = CG_UPD + 2 * 4;
   RepAcc<3> acc;
   RepAcc<1> accd;
@@ -412,7 +413,8 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
     // the guess shifted by dq: H (q0 + dq 1) = D (q0 + dq) + sum M q0_j + dq sum M
     double qi = q[i] + dq;
     q[i] = qi;
-    R ri = (R)(-T.chi[type[i]] - ((double)Di * qi + (double)hq + dq * (double)hm) - s0);
+    double chi_i = rhs ? rhs[i] : T.chi[type[i]];   // rhs: a per-atom chi (adjoint solves)
+    R ri = (R)(-chi_i - ((double)Di * qi + (double)hq + dq * (double)hm) - s0);
     R yi = dinv[i] * ri;
     r[i] = ri;
     y[i] = yi;
@@ -647,7 +649,7 @@ __global__ void k_copy_q(int N, const double* __restrict__ q, R* __restrict__ qr
 
 // --------------------------------------------------------------- launchers
 template <class R>
-void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, double tol) {
+void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, double tol, const double* rhs) {
   k_cg_prep<<<1, 256, 0, st>>>(S.R, S.cg, S.cg_rmax, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
   if (S.N == 0) return;
   k_cg_extrap<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.q, S.cqh1, S.cqh2, (R*)S.qr, (const R*)S.dinv,
@@ -657,7 +659,7 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
   k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.ld, chunk, S.nbr, S.nall, (const R*)S.M, (const R*)S.Dg,
                                      (const R*)S.dinv, S.type, S.rep, T, S.q, (const R*)S.qr, (const R*)S.cd,
                                      (R*)S.cr, (R*)S.cy, (R*)S.cv, (R*)S.cdq, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
-                                     S.cg_blocks, S.cg_active, tol);
+                                     S.cg_blocks, S.cg_active, tol, rhs);
 }
 
 template <class R>
@@ -701,8 +703,8 @@ void launch_copy_q(const DevState& S, cudaStream_t st) {
   k_copy_q<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.q, (R*)S.qr);
 }
 
-template void launch_cg_begin<float>(const DevState&, const TypeParams&, cudaStream_t, double);
-template void launch_cg_begin<double>(const DevState&, const TypeParams&, cudaStream_t, double);
+template void launch_cg_begin<float>(const DevState&, const TypeParams&, cudaStream_t, double, const double*);
+template void launch_cg_begin<double>(const DevState&, const TypeParams&, cudaStream_t, double, const double*);
 template void launch_cg_mv<float>(const DevState&, cudaStream_t);
 template void launch_cg_mv<double>(const DevState&, cudaStream_t);
 template void launch_cg_up<float>(const DevState&, const SolveCfg&, cudaStream_t);

@@ -4,8 +4,19 @@
 #include <stdint.h>
 #include <string>
 #include "internal.cuh"
+#include "ctbop.h"
 
 namespace ct {
+
+// Offsets (in doubles) of the fields of ctbop_params: the layout of a
+// parameter gradient.
+enum ParamOffsets {
+  PG_A = 0, PG_B = 4, PG_L1 = 8, PG_L2 = 12, PG_R = 16, PG_S = 20, PG_KAPPA = 24,
+  PG_SIGMA = 28, PG_P = 32, PG_G = 36, PG_N = 44,
+  PG_GAMMA = 52, PG_C = 68, PG_D = 84, PG_H = 100, PG_ALPHA = 116,
+  PG_E0 = 132, PG_CHI = 134, PG_J = 136, PG_GAMMA_C = 138, PG_MASS = 140,
+  PG_RCOUL = 142, PG_KE = 143, PG_NPARAM = 144
+};
 
 // Per-replica double accumulators, one row of RA_STRIDE per replica.
 enum RepSlots {
@@ -96,7 +107,8 @@ template <class R> void launch_rebuild(const DevState& S, const PotParams<R>& P,
 template <class R> void launch_bond(const DevState& S, const PotParams<R>& P, cudaStream_t st);
 template <class R> void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams& T,
                                         cudaStream_t st);
-template <class R> void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, double tol);
+template <class R> void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, double tol,
+                                        const double* rhs = nullptr);
 template <class R> void launch_cg_iter(const DevState& S, const SolveCfg& cfg, cudaStream_t st);
 template <class R> void launch_cg_end(const DevState& S, cudaStream_t st);
 template <class R> void launch_cg_mv(const DevState& S, cudaStream_t st);
@@ -115,6 +127,9 @@ template <class R> void launch_copy_q(const DevState& S, cudaStream_t st);
 // launch shape for kernels with one thread per atom: resident blocks only,
 // each block a contiguous chunk of atoms (a multiple of its size)
 int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk);
+cudaError_t launch_param_grad(const DevState& S, const ::ctbop_params& P, const double* wrep, double* grad,
+                              cudaStream_t st);
+void launch_charge_grad(const DevState& S, const TypeParams& T, double* out, cudaStream_t st);
 int energy_noalloc(const double* e_atom, const int* rep, int N, int R, int device, cudaStream_t st,
                    double* host_out, std::string& why);
 

@@ -33,7 +33,7 @@ EXPORTS = (
     "ctbop_set_stream", "ctbop_set_layout", "ctbop_set_box", "ctbop_set_types",
     "ctbop_set_positions", "ctbop_set_velocities", "ctbop_set_charges", "ctbop_set_frozen",
     "ctbop_set_total_charge", "ctbop_compute", "ctbop_step", "ctbop_get", "ctbop_status",
-    "ctbop_profile_steps", "ctbop_energy_noalloc",
+    "ctbop_profile_steps", "ctbop_energy_noalloc", "ctbop_param_grad", "ctbop_set_params",
 )
 NPHASE = 10
 PHASES = ("kick_drift", "lists", "bond", "assemble", "cg_start", "cg_matvec", "cg_update",
@@ -152,6 +152,52 @@ def params_struct(d: dict) -> Params:
     return P
 
 
+def params_vector(P: Params) -> np.ndarray:
+    """The struct as its 144 doubles (field order of ctbop_params)."""
+    return np.frombuffer(bytes(P), dtype=np.float64).copy()
+
+
+def params_from_vector(v) -> Params:
+    """A struct from 144 doubles in field order."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    if v.size != C.sizeof(Params) // 8:
+        raise ValueError("need 144 parameters")
+    return Params.from_buffer_copy(v.tobytes())
+
+
+def grad_to_dict(G: Params, d: dict) -> dict:
+    """Map a gradient in the layout of the C struct back onto the keys of the
+    parameter dictionary d (the JSON layout): every struct entry is a copy of
+    one dictionary entry, so a dictionary entry's derivative is the sum over
+    the struct entries copied from it (a symmetric pair constant feeds both
+    ordered pairs; the inert second component of an L = 1 set feeds none)."""
+    T = TYPE_NAMES
+    out = {"pair": {}, "bond": {}, "triplet": {}, "self": {}, "coulomb": {}}
+    for key, pr in d["pair"].items():
+        out["pair"][key] = {f: 0.0 for f in ("A", "B", "lambda1", "lambda2", "R", "S", "kappa")}
+    fmap = {"A": "A", "B": "B", "lambda1": "lambda1", "lambda2": "lambda2", "R": "R", "S": "S", "kappa": "kappa"}
+    for a in range(2):
+        for b in range(2):
+            k = a * 2 + b
+            pk = T[min(a, b)] + T[max(a, b)]
+            for f, sf in fmap.items():
+                out["pair"][pk][f] += getattr(G, sf)[k]
+            bo = d["bond"][T[a] + T[b]]
+            L = len(bo["g"])
+            out["bond"][T[a] + T[b]] = {"sigma": G.sigma[k], "p": G.p[k],
+                                         "g": [G.g[k][l] for l in range(L)], "n": [G.n[k][l] for l in range(L)]}
+            for c in range(2):
+                t = (a * 2 + b) * 2 + c
+                tp = d["triplet"][T[a] + T[b] + T[c]]
+                out["triplet"][T[a] + T[b] + T[c]] = {
+                    key: [getattr(G, key)[t][l] for l in range(len(tp[key]))]
+                    for key in ("gamma", "c", "d", "h", "alpha")}
+    out["self"] = {"E0": [G.E0[t] for t in range(2)], "chi": [G.chi[t] for t in range(2)],
+                   "J": [G.J[t] for t in range(2)]}
+    out["coulomb"] = {"gamma": [G.gamma_c[t] for t in range(2)], "r_coul": G.r_coul, "k_e": G.k_e}
+    return out
+
+
 def _ptr(a):
     """(pointer, mem) of a numpy array or a torch tensor."""
     if isinstance(a, np.ndarray):
@@ -212,9 +258,44 @@ class System:
     def set_stream(self, stream_handle: int):
         self._check(self._L.ctbop_set_stream(self._h, C.c_void_p(stream_handle)), "set_stream")
 
+    def set_params_struct(self, P: Params):
+        """Replace the parameters from a filled struct (e.g. one built from a
+        parameter vector, see params_from_vector)."""
+        self._p = P
+        self._check(self._L.ctbop_set_params(self._h, C.byref(self._p)), "set_params")
+
+    def replica_index(self) -> np.ndarray:
+        """Replica of every atom (from the layout)."""
+        return np.repeat(np.arange(self.R), np.diff(self._offsets))
+
+    def set_params(self, params: dict):
+        """Replace the potential's parameters (the next evaluation rebuilds
+        lists and graphs as needed)."""
+        self._p = params_struct(params)
+        self._check(self._L.ctbop_set_params(self._h, C.byref(self._p)), "set_params")
+
+    def param_grad(self, w_E=None, E_ref=None, w_F=None, F_ref=None):
+        """Force-matching loss and its gradient with respect to every field
+        of the parameter struct (FP64 policy): returns (loss, Params)."""
+        def arr(a, n):
+            if a is None:
+                return None, None
+            a = np.ascontiguousarray(a, dtype=np.float64).reshape(n)
+            return a, a.ctypes.data_as(C.c_void_p)
+        wE, pwE = arr(w_E, self.R)
+        Er, pEr = arr(E_ref, self.R)
+        wF, pwF = arr(w_F, self.R)
+        Fr, pFr = arr(F_ref, 3 * self.n)
+        loss = C.c_double(0.0)
+        G = Params()
+        self._check(self._L.ctbop_param_grad(self._h, pwE, pEr, pwF, pFr, C.byref(loss), C.byref(G)),
+                    "param_grad")
+        return loss.value, G
+
     def set_layout(self, offsets):
         off = np.ascontiguousarray(offsets, dtype=np.int64)
         self._check(self._L.ctbop_set_layout(self._h, len(off) - 1, off.ctypes.data_as(C.c_void_p)), "set_layout")
+        self._offsets = off.copy()
         self.n = int(off[-1])
         self.R = len(off) - 1
 
