@@ -280,7 +280,9 @@ def run_ours(a):
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2: the neighbour list and "
                    "charge-matrix entries streamed every step exceed 3 GB",
                    "cg_iters_per_step": cg_per_step, "rebuilds_in_timed_region": rebuilds,
-                   "mean_entries_per_atom": st2["mean_all"], "mean_covalent_entries": st2["mean_cov"]},
+                   "mean_entries_per_atom": st2["mean_all"], "mean_covalent_entries": st2["mean_cov"],
+                   "cg_matvec_depth_tuned": st2["cg_mv_batch"],
+                   "cg_matvec_ms_by_depth_4_8_16": [round(x, 4) for x in st2["cg_mv_ms"]]},
         "roofline": {"kernel": "k_cg_mv (charge CG matrix pass)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "peak_kind": peak_kind,

@@ -122,6 +122,9 @@ typedef struct ctbop_stats {
     double  mean_cov;         /* mean covalent entries (incl. skin) at the last rebuild */
     double  mean_all;         /* mean total entries at the last rebuild */
     double  cg_residual_start; /* max_i |H q0 + chi - mu|_i of the last solve's starting guess, replica 0 (eV/e) */
+    int32_t cg_mv_batch;      /* list entries in flight per thread in the CG matrix pass (autotuned) */
+    int32_t reserved0;
+    double  cg_mv_ms[3];      /* ms per matrix pass of the depths 4, 8, 16 at the last tuning (0: not timed) */
 } ctbop_stats;
 
 typedef struct ctbop_system ctbop_system;

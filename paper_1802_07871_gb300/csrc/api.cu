@@ -57,6 +57,9 @@ struct ctbop_system {
   int alloc_N = -1, alloc_R = -1, alloc_cells = -1, alloc_cov = -1, alloc_all = -1;
   // graphs
   cudaGraphExec_t g_eval = nullptr, g_step = nullptr;
+  // matrix-pass autotuning: the lists it was tuned on, and the timings
+  int tuned_N = -1, tuned_cap = -1;
+  float mv_ms[3] = {0.f, 0.f, 0.f};
   double g_step_dt = -1.0;
   bool use_graph = true;
   // pinned host scratch
@@ -333,6 +336,7 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   CK(dalloc(s->list_buf, &bo, (size_t)N * cap_cov * 4 * rs));
   CK(dalloc(s->list_buf, &gs, (size_t)N * cap_cov * 4 * rs));
   CK(dalloc(s->list_buf, &M, ncol * rs));
+  CK(cudaMemset(M, 0, ncol * rs));   // defined values for the first tuning run
   S.bo = bo;
   S.gslot = gs;
   S.M = M;
@@ -496,6 +500,22 @@ static int ensure_lists(ctbop_system* s) {
   }
   s->need_rebuild = false;
   CK(cudaMemsetAsync(S.err, 0, sizeof(unsigned), s->stream));
+  // choose the matrix pass's depth for these lists (CTBOP_MV_BATCH = 4, 8
+  // or 16 forces one)
+  if (S.N > 0 && (s->tuned_N != S.N || s->tuned_cap != S.cap_all)) {
+    int before = S.mv_batch;
+    const char* fb = getenv("CTBOP_MV_BATCH");
+    int forced = fb ? atoi(fb) : 0;
+    if (forced == 4 || forced == 8 || forced == 16) {
+      S.mv_batch = forced;
+    } else {
+      cudaError_t e = s->mixed ? tune_cg_mv<float>(S, s->stream, s->mv_ms) : tune_cg_mv<double>(S, s->stream, s->mv_ms);
+      if (e != cudaSuccess) return fail(s, CTBOP_ERR_CUDA, std::string("matrix-pass tuning: ") + cudaGetErrorString(e));
+    }
+    s->tuned_N = S.N;
+    s->tuned_cap = S.cap_all;
+    if (S.mv_batch != before) destroy_graphs(s);
+  }
   return CTBOP_OK;
 }
 
@@ -985,6 +1005,8 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   CK(cudaMemcpy(&res, S.cg + CG_RESMAX, sizeof(double), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&res0, S.cg + CG_RES0, sizeof(double), cudaMemcpyDeviceToHost));
   st->cg_residual_start = res0;
+  st->cg_mv_batch = S.mv_batch;
+  for (int k = 0; k < 3; ++k) st->cg_mv_ms[k] = s->mv_ms[k];
   st->error_bits = bits;
   st->rebuilds = rb;
   st->cg_iters_total = tot;

@@ -319,22 +319,16 @@ __device__ inline void row_sum(int i, int na, int ld, const int* __restrict__ nb
 }
 
 // Row sum sum_e M_e x_j(e) of atom i for the matrix pass, software-pipelined:
-// the list indices and entries of the next CT_MV_BATCH entries are loaded
-// before the current batch's x_j are gathered, so the streamed list (the
-// bound of this pass) always has loads in flight. Each batch is summed as a
-// small tree and only the running sum is compensated: the error that limits
-// the solve comes from adding small terms to a large running sum, not from
-// the few terms of a batch.
-#ifndef CT_MV_BATCH
-#define CT_MV_BATCH 16
-#endif
-#ifndef CT_MV_MINB
-#define CT_MV_MINB 1
-#endif
-template <class R>
+// the list indices and entries of the next B entries are loaded before the
+// current batch's x_j are gathered, so the streamed list (the bound of this
+// pass) always has loads in flight. Each batch is summed as a small tree and
+// only the running sum is compensated: the error that limits the solve
+// comes from adding small terms to a large running sum, not from the few
+// terms of a batch. B (entries in flight per thread) is chosen at run time
+// by tune_cg_mv among the instantiated depths.
+template <class R, int B>
 __device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict__ nbr, const R* __restrict__ M,
                                    const R* __restrict__ x) {
-  constexpr int B = sizeof(R) == 4 ? CT_MV_BATCH : CT_MV_BATCH / 2;   // FP64: half the entries in flight
   const int* pn = nbr + i;
   const R* pm = M + i;
   int jn[B];
@@ -452,8 +446,8 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
 // and before the first re-centring r carries its whole mean (-mu), whose
 // product with that sum would swamp r.z once the residual is small (warm
 // starts near the tolerance then diverge).
-template <class R>
-__global__ void __launch_bounds__(256, CT_MV_MINB)
+template <class R, int B>
+__global__ void __launch_bounds__(256)
     k_cg_mv(int N, int ld, const int* __restrict__ nbr, const int* __restrict__ nall, const R* __restrict__ M,
             const R* __restrict__ Dg, const int* __restrict__ rep, const int* __restrict__ conv,
             const int* __restrict__ itp, const R* __restrict__ y, const R* __restrict__ d, const R* __restrict__ v,
@@ -469,7 +463,7 @@ __global__ void __launch_bounds__(256, CT_MV_MINB)
     const double* cc = cg + (size_t)rid * CG_STRIDE;
     R c = (R)ldcg(cc + CG_C);
     R m = (R)ldcg(cc + CG_M);   // mean of the stored r
-    R hy = row_sum_stream<R>(i, nall[i], ld, nbr, M, y);
+    R hy = row_sum_stream<R, B>(i, nall[i], ld, nbr, M, y);
     R yi = y[i];
     R zi = yi - c * d[i];
     R wi = Dg[i] * yi + hy - c * v[i];
@@ -662,12 +656,58 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
                                      S.cg_blocks, S.cg_active, tol, rhs);
 }
 
+template <class R, int B>
+static void launch_cg_mv_b(const DevState& S, cudaStream_t st) {
+  k_cg_mv<R, B><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nbr, S.nall, (const R*)S.M, (const R*)S.Dg, S.rep,
+                                                   S.cg_conv, S.cg_it, (const R*)S.cy, (const R*)S.cd,
+                                                   (const R*)S.cv, (const R*)S.cr, (R*)S.cw, S.cg, S.R,
+                                                   S.cg_blocks, S.cg_active);
+}
+
 template <class R>
 void launch_cg_mv(const DevState& S, cudaStream_t st) {
   if (S.N == 0) return;
-  k_cg_mv<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nbr, S.nall, (const R*)S.M, (const R*)S.Dg, S.rep,
-                                                S.cg_conv, S.cg_it, (const R*)S.cy, (const R*)S.cd, (const R*)S.cv,
-                                                (const R*)S.cr, (R*)S.cw, S.cg, S.R, S.cg_blocks, S.cg_active);
+  if (S.mv_batch == 4) launch_cg_mv_b<R, 4>(S, st);
+  else if (S.mv_batch == 8) launch_cg_mv_b<R, 8>(S, st);
+  else launch_cg_mv_b<R, 16>(S, st);
+}
+
+// Autotuner of the matrix pass: times each instantiated depth (entries in
+// flight per thread: 4, 8, 16) on the current lists, one warm-up and three
+// timed launches each with CUDA events on the system's stream, and keeps the
+// fastest in S.mv_batch. It runs the pass on whatever the CG vectors hold
+// (the timing does not depend on their values) after resetting the solver's
+// per-solve state, which every solve resets again anyway. Returns the
+// milliseconds per launch of each depth in ms_out[3].
+template <class R>
+cudaError_t tune_cg_mv(DevState& S, cudaStream_t st, float* ms_out) {
+  if (S.N == 0) return cudaSuccess;
+  const int depth[3] = {4, 8, 16};
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  float best = 1e30f;
+  int pick = 16;
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    S.mv_batch = depth[k];
+    k_cg_prep<<<1, 256, 0, st>>>(S.R, S.cg, S.cg_rmax, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
+    launch_cg_mv<R>(S, st);
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 3; ++rep) launch_cg_mv<R>(S, st);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 3.0f;
+    if (ms_out) ms_out[k] = ms;
+    if (ms < best) { best = ms; pick = depth[k]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  S.mv_batch = pick;
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 template <class R>
@@ -706,6 +746,8 @@ void launch_copy_q(const DevState& S, cudaStream_t st) {
 template void launch_cg_begin<float>(const DevState&, const TypeParams&, cudaStream_t, double, const double*);
 template void launch_cg_begin<double>(const DevState&, const TypeParams&, cudaStream_t, double, const double*);
 template void launch_cg_mv<float>(const DevState&, cudaStream_t);
+template cudaError_t tune_cg_mv<float>(DevState&, cudaStream_t, float*);
+template cudaError_t tune_cg_mv<double>(DevState&, cudaStream_t, float*);
 template void launch_cg_mv<double>(const DevState&, cudaStream_t);
 template void launch_cg_up<float>(const DevState&, const SolveCfg&, cudaStream_t);
 template void launch_cg_up<double>(const DevState&, const SolveCfg&, cudaStream_t);

@@ -94,6 +94,7 @@ struct DevState {
   long long* cg_total = nullptr;
   // sizes for launches
   int nsm = 152;
+  int mv_batch = 16;            // list entries in flight per thread in the CG matrix pass (tuned)
 };
 
 struct SolveCfg {
@@ -112,6 +113,7 @@ template <class R> void launch_cg_begin(const DevState& S, const TypeParams& T, 
 template <class R> void launch_cg_iter(const DevState& S, const SolveCfg& cfg, cudaStream_t st);
 template <class R> void launch_cg_end(const DevState& S, cudaStream_t st);
 template <class R> void launch_cg_mv(const DevState& S, cudaStream_t st);
+template <class R> cudaError_t tune_cg_mv(DevState& S, cudaStream_t st, float* ms_out);
 template <class R> void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st);
 template <class R> void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams& T,
                                          cudaStream_t st);
