@@ -222,6 +222,167 @@ def add_adatoms(s: Structure, count: int, zmin: float = 1.5, zmax: float = 3.0,
 
 
 # --------------------------------------------------------------------------
+# Fitting-set / annealing-ensemble shapes (Sec. 2: SiC crystals with
+# defects, amorphous carbon, graphene on SiC)
+# --------------------------------------------------------------------------
+def _slab_dims(n_target: int, n_bilayers: int):
+    """In-plane cells (nx, ny) of a 4H slab closest to n_target atoms."""
+    per_cell = 4 * n_bilayers
+    cells = max(1, round(n_target / per_cell))
+    ny = max(1, int(round(math.sqrt(cells / math.sqrt(3.0)))))
+    nx = max(1, int(round(cells / ny)))
+    return nx, ny
+
+
+def slab_with_vacancies(n_target: int, vac_frac: float, seed: int, n_bilayers: int = 4) -> Structure:
+    """4H-SiC(0001) slab of about n_target atoms (periodic in x/y, bottom
+    bilayer frozen) with a fraction vac_frac of its Si atoms removed at
+    random."""
+    rng = np.random.default_rng(seed)
+    nx, ny = _slab_dims(n_target / max(1e-9, 1.0 - 0.5 * vac_frac), n_bilayers)
+    s = sic_4h_slab(nx, ny, n_bilayers, n_frozen_bilayers=1)
+    si = np.nonzero(s.types == SI)[0]
+    drop = rng.choice(si, int(round(vac_frac * len(si))), replace=False)
+    keep = np.ones(s.n, dtype=bool)
+    keep[drop] = False
+    out = Structure(f"4H-SiC slab {nx}x{ny}x{n_bilayers}, {vac_frac:.0%} Si vacancies", s.x[keep],
+                    s.types[keep], s.box, s.pbc, s.frozen[keep])
+    return out
+
+
+def amorphous_carbon_cluster(n: int, density_gcc: float, seed: int, min_sep: float = 1.2) -> Structure:
+    """n C atoms placed by random sequential addition in a sphere holding
+    them at density_gcc (g/cm^3), no two closer than min_sep; open box."""
+    rng = np.random.default_rng(seed)
+    n_rho = density_gcc * 0.602214076 / MASS[C]          # atoms per A^3
+    R = (3.0 * n / (4.0 * math.pi * n_rho)) ** (1.0 / 3.0)
+    cell = min_sep
+    grid: dict = {}
+    pts = []
+    tries = 0
+    while len(pts) < n:
+        tries += 1
+        if tries > 2000 * n:
+            raise RuntimeError("could not pack the cluster")
+        p = rng.uniform(-R, R, 3)
+        if p @ p > R * R:
+            continue
+        k = tuple(np.floor(p / cell).astype(int))
+        ok = True
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    for q in grid.get((k[0] + dx, k[1] + dy, k[2] + dz), ()):
+                        d = p - q
+                        if d @ d < min_sep * min_sep:
+                            ok = False
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if not ok:
+                break
+        if not ok:
+            continue
+        grid.setdefault(k, []).append(p)
+        pts.append(p)
+    edge = 2.0 * R + 30.0
+    x = np.array(pts) + edge / 2.0
+    return Structure(f"amorphous C cluster n={n} rho={density_gcc:.2f}", x, np.full(n, C, dtype=np.int32),
+                     np.full(3, edge), np.array([False] * 3))
+
+
+def graphene_flake(n: int, seed: int, vac_frac: float = 0.03, n_stone_wales: int = 2) -> np.ndarray:
+    """Positions (z = 0) of a roughly circular graphene flake (C-C 1.42 A)
+    of about n atoms, with a fraction vac_frac of its atoms removed and
+    n_stone_wales Stone-Wales defects (a C-C bond rotated by 90 degrees about
+    its midpoint, turning four hexagons into two pentagons and two
+    heptagons)."""
+    rng = np.random.default_rng(seed)
+    b = 1.42
+    a = b * math.sqrt(3.0)
+    R = math.sqrt(n / (math.pi * 4.0 / (math.sqrt(3.0) * a * a)))
+    m = int(R / a) + 3
+    pts = []
+    for i in range(-2 * m, 2 * m + 1):
+        for j in range(-2 * m, 2 * m + 1):
+            o = np.array([i * a + j * a / 2.0, j * a * math.sqrt(3.0) / 2.0])
+            pts.append(o)
+            pts.append(o + np.array([a / 2.0, a / (2.0 * math.sqrt(3.0))]))
+    xy = np.array(pts)
+    xy = xy[np.einsum("ij,ij->i", xy, xy) <= R * R]
+    # Stone-Wales: rotate interior bonds by 90 degrees
+    from scipy.spatial import cKDTree
+    for _ in range(n_stone_wales):
+        tree = cKDTree(xy)
+        inner = np.nonzero(np.einsum("ij,ij->i", xy, xy) < (0.6 * R) ** 2)[0]
+        if len(inner) == 0:
+            break
+        i = rng.choice(inner)
+        nb = [j for j in tree.query_ball_point(xy[i], 1.05 * b) if j != i]
+        if not nb:
+            continue
+        j = rng.choice(nb)
+        mid = 0.5 * (xy[i] + xy[j])
+        old = xy[[i, j]].copy()
+        for k in (i, j):
+            d = xy[k] - mid
+            xy[k] = mid + np.array([-d[1], d[0]])
+        # keep the rotation only if the moved pair stays clear of every other atom
+        others = np.ones(len(xy), dtype=bool)
+        others[[i, j]] = False
+        dmin = min(np.min(np.linalg.norm(xy[others] - xy[k], axis=1)) for k in (i, j))
+        if dmin < 1.2:
+            xy[[i, j]] = old
+    keep = rng.random(len(xy)) >= vac_frac
+    return xy[keep]
+
+
+def graphene_on_sic(n_target: int, seed: int) -> Structure:
+    """A defected graphene flake (about 20% of the atoms) 2.5-3.0 A above a
+    3-bilayer 4H-SiC(0001) slab whose periodic cell is at least the flake's
+    diameter + 6 A wide, so the flake never meets its periodic images."""
+    rng = np.random.default_rng(seed)
+    flake = graphene_flake(max(20, int(0.2 * n_target)), seed + 1)
+    diam = 2.0 * np.sqrt(np.einsum("ij,ij->i", flake, flake).max()) + 6.0
+    ah = 4.36 / math.sqrt(2.0)
+    nx, ny = int(math.ceil(diam / ah)), int(math.ceil(diam / (ah * math.sqrt(3.0))))
+    slab = sic_4h_slab(nx, ny, 3, n_frozen_bilayers=1)
+    h = rng.uniform(2.5, 3.0)
+    c = slab.box[:2] / 2.0
+    z = slab.x[:, 2].max() + h
+    fx = np.concatenate([flake + c, np.full((len(flake), 1), z)], 1)
+    x = np.concatenate([slab.x, fx])
+    types = np.concatenate([slab.types, np.full(len(fx), C, dtype=np.int32)])
+    frozen = np.concatenate([slab.frozen, np.zeros(len(fx), dtype=bool)])
+    box = slab.box.copy()
+    box[2] = x[:, 2].max() + 15.0
+    return Structure(f"graphene flake ({len(fx)}) on SiC slab ({slab.n})", x, types, box, slab.pbc.copy(), frozen)
+
+
+def annealing_ensemble(n_replicas: int = 256, seed: int = 4, n_min: int = 200, n_max: int = 3000):
+    """Independent replicas of uneven size (uniform n_min..n_max atoms) in
+    three kinds taken in turn: SiC slabs with 0-30% Si vacancies, amorphous C
+    clusters at 1.8-2.3 g/cm^3, defected graphene flakes on SiC. Returns the
+    structures and a temperature (K) for each, uniform in 1500-3000."""
+    rng = np.random.default_rng(seed)
+    out, temps = [], []
+    for r in range(n_replicas):
+        n = int(rng.integers(n_min, n_max + 1))
+        k = r % 3
+        if k == 0:
+            s = slab_with_vacancies(n, float(rng.uniform(0.0, 0.3)), seed * 1000 + r)
+        elif k == 1:
+            s = amorphous_carbon_cluster(n, float(rng.uniform(1.8, 2.3)), seed * 1000 + r)
+        else:
+            s = graphene_on_sic(n, seed * 1000 + r)
+        out.append(s)
+        temps.append(float(rng.uniform(1500.0, 3000.0)))
+    return out, temps
+
+
+# --------------------------------------------------------------------------
 # Workloads with the shapes of the benchmark configurations
 # --------------------------------------------------------------------------
 def bulk_3c_512(seed: int = 1) -> Structure:

@@ -231,3 +231,18 @@ def test_full_size_slab_1m_sampled():
     samples = np.concatenate([rng.choice(s.n, 24, replace=False), rng.choice(ad, 8, replace=False)])
     sampled_local_check(s, P0, g, "mixed", samples)
     assert abs(g["charges"].sum()) < 1e-6
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_annealing_ensemble_replicas(prec):
+    """A reduced annealing ensemble in one batch: SiC slabs with Si
+    vacancies, amorphous C clusters at 1.8-2.3 g/cc and defected graphene
+    flakes on SiC, uneven sizes; every replica against its own oracle
+    evaluation."""
+    structs, _ = st.annealing_ensemble(n_replicas=9, seed=7, n_min=150, n_max=500)
+    g = gpu_eval(structs, P0, prec)
+    off = 0
+    for r, s in enumerate(structs):
+        o = oracle_eval(s, P0)
+        compare(g, o, s.n, prec, sl=slice(off, off + s.n), r=r, stress=True)
+        off += s.n
