@@ -132,7 +132,7 @@ def peaks():
 # and the list entries of that launch. Traffic grows with the entries
 # (it is 0.98 x the algorithmic bytes there), so a full launch is scaled by
 # its entry count. Reset to None when the kernel changes.
-MV_TRAFFIC_CAPTURE = {"bytes": 461.072896e6 + 3.870208e6, "entries": 251366 * 226.5986569384881}
+MV_TRAFFIC_CAPTURE = {"bytes": 461.367040e6 + 3.391232e6, "entries": 251366 * 226.5986569384881}
 
 
 def cg_matvec_bytes(n_atoms, entries, rs):

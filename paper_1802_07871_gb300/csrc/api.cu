@@ -335,8 +335,9 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   unsigned char *bo = nullptr, *gs = nullptr, *M = nullptr;
   CK(dalloc(s->list_buf, &bo, (size_t)N * cap_cov * 4 * rs));
   CK(dalloc(s->list_buf, &gs, (size_t)N * cap_cov * 4 * rs));
-  CK(dalloc(s->list_buf, &M, ncol * rs));
-  CK(cudaMemset(M, 0, ncol * rs));   // defined values for the first tuning run
+  // 8 bytes per entry: (j, FP32 coefficient) pairs, or FP64 coefficients
+  CK(dalloc(s->list_buf, &M, ncol * 8));
+  CK(cudaMemset(M, 0, ncol * 8));    // defined values for the first tuning run
   S.bo = bo;
   S.gslot = gs;
   S.M = M;

@@ -285,18 +285,19 @@ struct RowAcc {
 };
 
 template <class R, int NV>
-__device__ inline void row_sum(int i, int na, int ld, const int* __restrict__ nbr, const R* __restrict__ M,
+__device__ inline void row_sum(int i, int na, int ld, const int* __restrict__ nbr, const void* __restrict__ M,
                                const R* __restrict__ v0, const R* __restrict__ v1, R& h0, R& h1, R& hm) {
-  const int* pn = nbr + i;
-  const R* pm = M + i;
+  const MatView<R> mat(nbr, M);
   RowAcc<R> a0, a1, am;
   int e = 0;
   for (; e + 4 <= na; e += 4) {
-    size_t o = (size_t)e * ld;
-    int j0 = __ldg(pn + o), j1 = __ldg(pn + o + ld), j2 = __ldg(pn + o + 2 * (size_t)ld),
-        j3 = __ldg(pn + o + 3 * (size_t)ld);
-    R m0 = __ldg(pm + o), m1 = __ldg(pm + o + ld), m2 = __ldg(pm + o + 2 * (size_t)ld),
-      m3 = __ldg(pm + o + 3 * (size_t)ld);
+    size_t o = (size_t)e * ld + i;
+    int j0, j1, j2, j3;
+    R m0, m1, m2, m3;
+    mat.get(o, j0, m0);
+    mat.get(o + ld, j1, m1);
+    mat.get(o + 2 * (size_t)ld, j2, m2);
+    mat.get(o + 3 * (size_t)ld, j3, m3);
     R x0 = v0[j0], x1 = v0[j1], x2 = v0[j2], x3 = v0[j3];
     a0.add(m0 * x0); a0.add(m1 * x1); a0.add(m2 * x2); a0.add(m3 * x3);
     if (NV >= 2) {
@@ -306,9 +307,9 @@ __device__ inline void row_sum(int i, int na, int ld, const int* __restrict__ nb
     if (NV >= 3) { am.add(m0); am.add(m1); am.add(m2); am.add(m3); }
   }
   for (; e < na; ++e) {
-    size_t o = (size_t)e * ld;
-    int j0 = __ldg(pn + o);
-    R m0 = __ldg(pm + o);
+    int j0;
+    R m0;
+    mat.get((size_t)e * ld + i, j0, m0);
     a0.add(m0 * v0[j0]);
     if (NV >= 2) a1.add(m0 * v1[j0]);
     if (NV >= 3) am.add(m0);
@@ -327,17 +328,16 @@ __device__ inline void row_sum(int i, int na, int ld, const int* __restrict__ nb
 // terms of a batch. B (entries in flight per thread) is chosen at run time
 // by tune_cg_mv among the instantiated depths.
 template <class R, int B>
-__device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict__ nbr, const R* __restrict__ M,
+__device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict__ nbr, const void* __restrict__ M,
                                    const R* __restrict__ x) {
-  const int* pn = nbr + i;
-  const R* pm = M + i;
+  const MatView<R> mat(nbr, M);
   int jn[B];
   R mn[B];
 #pragma unroll
   for (int k = 0; k < B; ++k) {
-    bool ok = k < na;
-    jn[k] = ok ? __ldg(pn + (size_t)k * ld) : i;
-    mn[k] = ok ? __ldg(pm + (size_t)k * ld) : R(0);
+    jn[k] = i;
+    mn[k] = R(0);
+    if (k < na) mat.get((size_t)k * ld + i, jn[k], mn[k]);
   }
   RowAcc<R> acc;
   for (int e = 0; e < na; e += B) {
@@ -351,9 +351,9 @@ __device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict_
 #pragma unroll
     for (int k = 0; k < B; ++k) {
       int en = e + B + k;
-      bool ok = en < na;
-      jn[k] = ok ? __ldg(pn + (size_t)en * ld) : i;
-      mn[k] = ok ? __ldg(pm + (size_t)en * ld) : R(0);
+      jn[k] = i;
+      mn[k] = R(0);
+      if (en < na) mat.get((size_t)en * ld + i, jn[k], mn[k]);
     }
     R t[B];
 #pragma unroll
@@ -375,7 +375,7 @@ __device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict_
 // starts the accumulated one, so mu = -(mean of stored r + shift) holds.
 template <class R>
 __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr, const int* __restrict__ nall,
-                          const R* __restrict__ M, const R* __restrict__ Dg, const R* __restrict__ dinv,
+                          const void* __restrict__ M, const R* __restrict__ Dg, const R* __restrict__ dinv,
                           const int* __restrict__ type, const int* __restrict__ rep, TypeParams T,
                           double* __restrict__ q, const R* __restrict__ qr, const R* __restrict__ d,
                           R* __restrict__ r, R* __restrict__ y, R* __restrict__ v, R* __restrict__ dqv,
@@ -448,7 +448,7 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
 // starts near the tolerance then diverge).
 template <class R, int B>
 __global__ void __launch_bounds__(256)
-    k_cg_mv(int N, int ld, const int* __restrict__ nbr, const int* __restrict__ nall, const R* __restrict__ M,
+    k_cg_mv(int N, int ld, const int* __restrict__ nbr, const int* __restrict__ nall, const void* __restrict__ M,
             const R* __restrict__ Dg, const int* __restrict__ rep, const int* __restrict__ conv,
             const int* __restrict__ itp, const R* __restrict__ y, const R* __restrict__ d, const R* __restrict__ v,
             const R* __restrict__ r, R* __restrict__ w, double* __restrict__ cg, int Rn,
@@ -650,7 +650,7 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
                                                     (R*)S.cd, S.rep, S.cg, S.R, S.cg_hist, S.cg_blocks);
   int chunk;
   int grid = atom_dims(S.N, S.nsm, (const void*)k_cg_init<R>, 256, chunk);
-  k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.ld, chunk, S.nbr, S.nall, (const R*)S.M, (const R*)S.Dg,
+  k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.ld, chunk, S.nbr, S.nall, S.M, (const R*)S.Dg,
                                      (const R*)S.dinv, S.type, S.rep, T, S.q, (const R*)S.qr, (const R*)S.cd,
                                      (R*)S.cr, (R*)S.cy, (R*)S.cv, (R*)S.cdq, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
                                      S.cg_blocks, S.cg_active, tol, rhs);
@@ -658,7 +658,7 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
 
 template <class R, int B>
 static void launch_cg_mv_b(const DevState& S, cudaStream_t st) {
-  k_cg_mv<R, B><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nbr, S.nall, (const R*)S.M, (const R*)S.Dg, S.rep,
+  k_cg_mv<R, B><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nbr, S.nall, S.M, (const R*)S.Dg, S.rep,
                                                    S.cg_conv, S.cg_it, (const R*)S.cy, (const R*)S.cd,
                                                    (const R*)S.cv, (const R*)S.cr, (R*)S.cw, S.cg, S.R,
                                                    S.cg_blocks, S.cg_active);

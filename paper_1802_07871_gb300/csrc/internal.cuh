@@ -15,7 +15,8 @@
 //   rev              int32[N*capc] entry of j's list that points back to i (covalent part)
 //   bo               Real4[N*capc] b_ij, db/dzeta_1, db/dzeta_2 per directed bond
 //   gslot            Real4[N*capc] dE_i/du_e: gradient of the terms centred on i w.r.t. bond e
-//   M                Real[cap*ld]  charge-Hessian off-diagonal entries K_ij - 2 w_ij (list layout)
+//   M                [cap*ld]      charge-Hessian off-diagonal entries K_ij - 2 w_ij (list layout):
+//                                  FP32 (j, coefficient) int2 pairs, or FP64 coefficients
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -164,6 +165,34 @@ __device__ inline R coul_K_r2(R r2, R gs3, R inv_rc, R ke) {
   R T = R(1) + x4 * (R(-35) + x * (R(84) + x * (R(-70) + R(20) * x)));
   return ke * T * ct_rcbrt<R>(r2 * r + gs3);
 }
+
+// The stored charge matrix, one entry per list entry (e * ld + i). The FP32
+// path keeps (j, coefficient bits) pairs, so a matrix pass streams one
+// 8-byte load per entry instead of two 4-byte streams; the FP64 path keeps
+// the FP64 coefficients beside the index list.
+template <class R> struct MatView;
+template <> struct MatView<float> {
+  const int2* ml;
+  __device__ MatView(const int* /*nbr*/, const void* m) : ml(static_cast<const int2*>(m)) {}
+  __device__ inline void get(size_t idx, int& j, float& v) const {
+    int2 t = __ldg(ml + idx);
+    j = t.x;
+    v = __int_as_float(t.y);
+  }
+};
+template <> struct MatView<double> {
+  const int* nbr;
+  const double* M;
+  __device__ MatView(const int* n, const void* m) : nbr(n), M(static_cast<const double*>(m)) {}
+  __device__ inline void get(size_t idx, int& j, double& v) const {
+    j = __ldg(nbr + idx);
+    v = __ldg(M + idx);
+  }
+};
+__device__ inline void mat_store(void* M, size_t idx, int j, float v) {
+  static_cast<int2*>(M)[idx] = make_int2(j, __float_as_int(v));
+}
+__device__ inline void mat_store(void* M, size_t idx, int /*j*/, double v) { static_cast<double*>(M)[idx] = v; }
 
 // Compensated (Neumaier) summation in the working precision: keeps the
 // rounding of long per-lane sums at the level of a single term.

@@ -73,7 +73,7 @@ struct DevState {
   int2* lst = nullptr;          // [N][cap_all] row-major build scratch (j, code)
   void* bo = nullptr;           // Real4[N*cap_cov]
   void* gslot = nullptr;        // Real4[N*cap_cov]
-  void* M = nullptr;            // Real[N*cap_all]
+  void* M = nullptr;            // [cap_all*ld] charge matrix: FP32 (j, coefficient) int2 pairs, or FP64 coefficients
   void *Dg = nullptr, *dinv = nullptr;   // Real[N]: Hessian diagonal without self-images, Jacobi inverse
   // CG: the iterate is q itself (FP64); the rest in the working precision
   double *cqh1 = nullptr, *cqh2 = nullptr;  // q of the previous two solves

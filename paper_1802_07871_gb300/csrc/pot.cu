@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256)
                const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
                const int* __restrict__ code, const int* __restrict__ ncov, const int* __restrict__ nall,
                const int* __restrict__ rev, const typename Vec4<R>::T* __restrict__ bo, PotParams<R> P,
-               TypeParams T, R* __restrict__ M, R* __restrict__ Dg, R* __restrict__ dinv) {
+               TypeParams T, void* __restrict__ M, R* __restrict__ Dg, R* __restrict__ dinv) {
   using R4 = typename Vec4<R>::T;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -163,7 +163,6 @@ __global__ void __launch_bounds__(256)
   R wsum = R(0), selfm = R(0);
   const int* pn = nbr + i;
   const int* pc = code + i;
-  R* pm = M + i;
   // covalent entries: K minus twice the bond-order coupling w
   for (int e = 0; e < nc; ++e) {
     size_t off = (size_t)e * ld;
@@ -187,7 +186,7 @@ __global__ void __launch_bounds__(256)
       wsum += w;
     }
     if (j == i) selfm += m;
-    pm[off] = m;
+    mat_store(M, off + i, j, m);
   }
   // the rest: K only, streamed
   const R gs_i0 = P.gshield3[ti * 2], gs_i1 = P.gshield3[ti * 2 + 1];
@@ -220,7 +219,7 @@ __global__ void __launch_bounds__(256)
         R r2 = rx * rx + ry * ry + rz * rz;
         R m = coul_K_r2<R>(r2, uj[k].w != R(0) ? gs_i1 : gs_i0, P.inv_rcoul, P.ke);
         if (jc[k] == i) selfm += m;
-        pm[(size_t)(e + k) * ld] = m;
+        mat_store(M, (size_t)(e + k) * ld + i, jc[k], m);
       }
     }
   }
@@ -584,7 +583,7 @@ void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams&
   if (S.N == 0) return;
   k_assemble<R><<<(S.N + 255) / 256, 256, 0, st>>>(
       S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
-      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, (R*)S.M, (R*)S.Dg, (R*)S.dinv);
+      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, S.M, (R*)S.Dg, (R*)S.dinv);
 }
 
 template <class R>
