@@ -109,6 +109,7 @@ static void pack_params(const ctbop_params& p, double skin, PotParams<Rr>& P) {
     P.lam2_64[k] = p.lambda2[k];
     P.Rin64[k] = p.R[k];
     P.Sout64[k] = p.S[k];
+    P.kappa64[k] = p.kappa[k];
     P.rcov_list2[k] = (Rr)((p.S[k] + skin) * (p.S[k] + skin));
     double sg = p.sigma[k], pp = p.p[k];
     P.sigma[k] = (Rr)sg;
@@ -291,6 +292,8 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->rep_buf, &S.flag_rebuild, 1));
   CK(dalloc(s->rep_buf, &S.rebuild_count, 1));
   CK(dalloc(s->rep_buf, &S.maxcnt, 3));
+  CK(dalloc(s->rep_buf, &S.stiff_n, 1));
+  CK(cudaMemset(S.stiff_n, 0, sizeof(int)));
   CK(dalloc(s->rep_buf, &S.err, 1));
   CK(dalloc(s->rep_buf, &S.cg_it, 1));
   CK(dalloc(s->rep_buf, &S.cg_blocks, 3));
@@ -332,6 +335,12 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   CK(dalloc(s->list_buf, &S.code, ncol));
   CK(dalloc(s->list_buf, &S.lst, (size_t)std::max(N, 1) * cap_all));
   CK(dalloc(s->list_buf, &S.rev, (size_t)N * cap_cov));
+  CK(dalloc(s->list_buf, &S.stiff_q, (size_t)std::max(N, 1) * cap_cov));
+  {
+    float2* pe = nullptr;
+    CK(dalloc(s->list_buf, &pe, (size_t)std::max(N, 1) * cap_cov));
+    S.stiff_pe = pe;
+  }
   unsigned char *bo = nullptr, *gs = nullptr, *M = nullptr;
   CK(dalloc(s->list_buf, &bo, (size_t)N * cap_cov * 4 * rs));
   CK(dalloc(s->list_buf, &gs, (size_t)N * cap_cov * 4 * rs));
@@ -589,7 +598,7 @@ static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double 
       if (!rc) rc = timed(6, 1, [&] { launch_cg_up<Rr>(S, cfg, st); });
     }
     if (!rc) rc = timed(7, 2, [&] { launch_cg_end<Rr>(S, st); });
-    if (!rc) rc = timed(8, 1, [&] { launch_cov_force<Rr>(S, P, s->T, st); });
+    if (!rc) rc = timed(8, sizeof(Rr) == 4 ? 2 : 1, [&] { launch_cov_force<Rr>(S, P, s->T, st); });
     if (!rc) rc = timed(9, 1, [&] { launch_coul_gather<Rr>(S, P, s->T, 1, 0.5 * dt, st); });
     if (!rc) {
       unsigned bits = 0;

@@ -56,7 +56,7 @@ template <class R> struct PotParams {
   R rcoul, inv_rcoul, ke;
   R rall_list2;                    // (Rc + skin)^2
   // the pair block in FP64, for the stiff-bond pair terms of the FP32 path
-  double A64[4], B64[4], lam1_64[4], lam2_64[4], Rin64[4], Sout64[4];
+  double A64[4], B64[4], lam1_64[4], lam2_64[4], Rin64[4], Sout64[4], kappa64[4];
 };
 
 // Per-type quantities that always stay double.

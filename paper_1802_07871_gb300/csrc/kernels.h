@@ -71,6 +71,11 @@ struct DevState {
   // lists
   int *nbr = nullptr, *code = nullptr, *ncov = nullptr, *nall = nullptr, *rev = nullptr;
   int2* lst = nullptr;          // [N][cap_all] row-major build scratch (j, code)
+  // stiff covalent bonds (FP32 path): a queue of bond ids i * cap_cov + e and,
+  // per bond, the FP64-evaluated pair term (dE/dr, energy) as float2
+  int* stiff_n = nullptr;
+  int* stiff_q = nullptr;       // [N * cap_cov]
+  void* stiff_pe = nullptr;     // float2 [N * cap_cov]
   void* bo = nullptr;           // Real4[N*cap_cov]
   void* gslot = nullptr;        // Real4[N*cap_cov]
   void* M = nullptr;            // [cap_all*ld] charge matrix: FP32 (j, coefficient) int2 pairs, or FP64 coefficients

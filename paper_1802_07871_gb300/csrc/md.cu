@@ -42,9 +42,10 @@ __global__ void k_kick_drift(int N, double dt, double half_skin2, const int* __r
   if (dx * dx + dy * dy + dz * dz > half_skin2) *flag = 1;
 }
 
-__global__ void k_zero_acc(int n, double* __restrict__ a) {
+__global__ void k_zero_acc(int n, double* __restrict__ a, int* __restrict__ stiff_n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = 0.0;
+  if (i == 0) *stiff_n = 0;   // the stiff-bond queue of this evaluation
 }
 
 template <class R>
@@ -57,7 +58,7 @@ void launch_kick_drift(const DevState& S, const TypeParams& T, double dt, double
 
 void launch_zero_acc(const DevState& S, cudaStream_t st) {
   int n = S.R * RA_STRIDE;
-  k_zero_acc<<<(n + 255) / 256, 256, 0, st>>>(n, S.rep_acc);
+  k_zero_acc<<<(n + 255) / 256, 256, 0, st>>>(n, S.rep_acc, S.stiff_n);
 }
 
 template void launch_kick_drift<float>(const DevState&, const TypeParams&, double, double, cudaStream_t);

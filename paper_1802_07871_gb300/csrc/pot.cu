@@ -23,9 +23,9 @@ namespace ct {
 
 #define GRP 8           // lanes per atom in the covalent kernels
 // Bonds whose repulsive radial derivative lambda1 * A e^(-lambda1 r) exceeds
-// this (eV/A) get their pair term in FP64 on the FP32 path. Equilibrium
-// Si-C bonds of the synthetic set stay near 11 eV/A; compressed adatom
-// bonds reach 35-65 eV/A.
+// this (eV/A) get their pair term in FP64 on the FP32 path (queued by the
+// bond pass, evaluated by k_stiff). Equilibrium Si-C bonds of the synthetic
+// set stay near 11 eV/A; compressed adatom bonds reach 35-65 eV/A.
 #define STIFF_PAIR 20.0f
 #define APB 16          // atoms per block in the covalent kernels
 
@@ -59,9 +59,11 @@ __global__ void __launch_bounds__(APB * GRP)
 k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
        const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
        const int* __restrict__ code, const int* __restrict__ ncov, PotParams<R> P,
-       typename Vec4<R>::T* __restrict__ bo) {
+       typename Vec4<R>::T* __restrict__ bo, int* __restrict__ stiff_n, int* __restrict__ stiff_q) {
   using R4 = typename Vec4<R>::T;
   extern __shared__ __align__(32) unsigned char smem_raw[];
+  __shared__ int s_nstiff, s_base;
+  if (threadIdx.x == 0) s_nstiff = 0;
   int g = threadIdx.x / GRP, l = threadIdx.x % GRP;
   R4* s_u = reinterpret_cast<R4*>(smem_raw) + (size_t)g * cap_cov;               // (ux,uy,uz,r)
   R* s_fc = reinterpret_cast<R*>(reinterpret_cast<R4*>(smem_raw) + (size_t)APB * cap_cov) + (size_t)g * cap_cov;
@@ -95,14 +97,21 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
       s_t[e] = tj;
     }
   }
-  __syncwarp();
-  if (!live) return;
-  for (int e = l; e < nc; e += GRP) {
+  __syncthreads();
+  int my_stiff = 0;
+  for (int e = l; live && e < nc; e += GRP) {
     R4 ue = s_u[e];
     int tj = s_t[e];
     int pb = ti * 2 + tj;
     R4 out;
+    // .w marks a stiff bond (FP32 path): its pair term is evaluated in FP64
+    // by k_stiff, from the queue built below
     out.w = R(0);
+    if (sizeof(R) == 4 && ue.w < P.Sout[pb] &&
+        P.lam1[pb] * P.A[pb] * ct_exp<R>(-P.lam1[pb] * ue.w) > R(STIFF_PAIR)) {
+      out.w = R(1);
+      ++my_stiff;
+    }
     if (ue.w >= P.Sout[pb]) {
       out.x = R(1); out.y = R(0); out.z = R(0);
       bo[(size_t)i * cap_cov + e] = out;
@@ -136,6 +145,60 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
     bond_order7<R>(z1, z2, pb, P, b, db1, db2);
     out.x = b; out.y = db1; out.z = db2;
     bo[(size_t)i * cap_cov + e] = out;
+  }
+  if (sizeof(R) != 4) return;   // (uniform over the block)
+  // append this block's stiff bonds to the queue: one global atomic per block
+  int off = my_stiff ? atomicAdd(&s_nstiff, my_stiff) : 0;
+  __syncthreads();
+  if (threadIdx.x == 0) s_base = s_nstiff ? atomicAdd(stiff_n, s_nstiff) : 0;
+  __syncthreads();
+  if (my_stiff) {
+    int pos = s_base + off;
+    for (int e = l; e < nc; e += GRP)
+      if (bo[(size_t)i * cap_cov + e].w != R(0)) stiff_q[pos++] = i * cap_cov + e;
+  }
+}
+
+// The pair term of every queued stiff bond in FP64 (fully occupied lanes,
+// unlike a per-bond branch inside the force pass): the bond vector from the
+// master positions (r_ij = x_j - x_i + the periodic shift of the stencil
+// cell), c_ij from the FP64 charges, b_ij from the bond pass. Stores dE/dr
+// and the energy 1/2 fc (A e^{-l1 r} - c b B e^{-l2 r}) as float2.
+__global__ void __launch_bounds__(256)
+    k_stiff(int cap_cov, int ld, const int* __restrict__ nq, const int* __restrict__ q_ids,
+            const int* __restrict__ nbr, const int* __restrict__ code, const int* __restrict__ rep,
+            const RepInfo* __restrict__ reps, const double* __restrict__ x, const int4* __restrict__ cell4,
+            const int* __restrict__ type, const float4* __restrict__ bo, const double* __restrict__ q,
+            PotParams<float> P, float2* __restrict__ pe) {
+  int n = *nq;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    int id = q_ids[t];
+    int i = id / cap_cov, e = id - i * cap_cov;
+    size_t idx = (size_t)e * ld + i;
+    int j = nbr[idx];
+    int dcx, dcy, dcz;
+    unpack_code(code[idx], dcx, dcy, dcz);
+    const RepInfo& ri = reps[rep[i]];
+    int4 ci4 = cell4[i], cj4 = cell4[j];
+    double ax = x[3 * j] - x[3 * i] + (double)(ci4.x + dcx - cj4.x) * ri.hc[0];
+    double ay = x[3 * j + 1] - x[3 * i + 1] + (double)(ci4.y + dcy - cj4.y) * ri.hc[1];
+    double az = x[3 * j + 2] - x[3 * i + 2] + (double)(ci4.z + dcz - cj4.z) * ri.hc[2];
+    double r = sqrt(ax * ax + ay * ay + az * az);
+    int pb = type[i] * 2 + type[j];
+    double fc = 1.0, dfc = 0.0;
+    if (r >= P.Sout64[pb]) {
+      fc = 0.0;
+    } else if (r >= P.Rin64[pb]) {
+      double w = P.Sout64[pb] - P.Rin64[pb], tt = (r - P.Rin64[pb]) / w;
+      fc = 0.5 * (1.0 + cospi(tt));
+      dfc = -0.5 * (M_PI / w) * sinpi(tt);
+    }
+    double dq = q[i] - q[j];
+    double cq = 1.0 - P.kappa64[pb] * dq * dq;
+    double fR = P.A64[pb] * exp(-P.lam1_64[pb] * r);
+    double att = cq * (double)bo[id].x * P.B64[pb] * exp(-P.lam2_64[pb] * r);
+    double pd = 0.5 * (dfc * (fR - att) + fc * (-P.lam1_64[pb] * fR + P.lam2_64[pb] * att));
+    pe[id] = make_float2((float)pd, (float)(0.5 * fc * (fR - att)));
   }
 }
 
@@ -236,7 +299,7 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
             const int* __restrict__ nbr, const int* __restrict__ code, const int* __restrict__ ncov,
             const typename Vec4<R>::T* __restrict__ bo, const double* __restrict__ q,
             const R* __restrict__ qr, PotParams<R> P, TypeParams T, typename Vec4<R>::T* __restrict__ gslot,
-            double* __restrict__ e_atom, const double* __restrict__ x, const int4* __restrict__ cell4) {
+            double* __restrict__ e_atom, const void* __restrict__ stiff_pe) {
   using R4 = typename Vec4<R>::T;
   using R2 = typename Vec2<R>::T;
   extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -284,33 +347,11 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
         R fR = P.A[pb] * ct_exp<R>(-P.lam1[pb] * r);
         R fA = P.B[pb] * ct_exp<R>(-P.lam2[pb] * r);
         R att = cq * bb.x * fA;
-        if (sizeof(R) == 4 && P.lam1[pb] * fR > R(STIFF_PAIR)) {
-          // A stiff (compressed) bond: its repulsive and attractive radial
-          // derivatives reach tens of eV/A and cancel to a few, and FP32
-          // rounding of the two terms and of the bond length would stand out
-          // against the net force. The pair term is evaluated in FP64 from
-          // the master positions (r_ij = x_j - x_i + the periodic shift of
-          // the stencil cell). Such bonds are rare, so the FP64 pipe is
-          // touched only by the lanes that hold one.
-          int dcx, dcy, dcz;
-          unpack_code(code[idx], dcx, dcy, dcz);
-          int4 ci4 = cell4[i], cj4 = cell4[j];
-          double ax = x[3 * j] - x[3 * i] + (double)(ci4.x + dcx - cj4.x) * ri.hc[0];
-          double ay = x[3 * j + 1] - x[3 * i + 1] + (double)(ci4.y + dcy - cj4.y) * ri.hc[1];
-          double az = x[3 * j + 2] - x[3 * i + 2] + (double)(ci4.z + dcz - cj4.z) * ri.hc[2];
-          double r64 = sqrt(ax * ax + ay * ay + az * az);
-          double fc64 = 1.0, dfc64 = 0.0;
-          if (r64 >= P.Sout64[pb]) {
-            fc64 = 0.0;
-          } else if (r64 >= P.Rin64[pb]) {
-            double w = P.Sout64[pb] - P.Rin64[pb], t = (r64 - P.Rin64[pb]) / w;
-            fc64 = 0.5 * (1.0 + cospi(t));
-            dfc64 = -0.5 * (M_PI / w) * sinpi(t);
-          }
-          double fR64 = P.A64[pb] * exp(-P.lam1_64[pb] * r64);
-          double att64 = (double)cq * (double)bb.x * P.B64[pb] * exp(-P.lam2_64[pb] * r64);
-          eacc.add((R)(0.5 * fc64 * (fR64 - att64)));
-          pd = (R)(0.5 * (dfc64 * (fR64 - att64) + fc64 * (-P.lam1_64[pb] * fR64 + P.lam2_64[pb] * att64)));
+        if (sizeof(R) == 4 && bb.w != R(0)) {
+          // stiff bond: pair term evaluated in FP64 by k_stiff
+          float2 v = static_cast<const float2*>(stiff_pe)[(size_t)i * cap_cov + e];
+          eacc.add((R)v.y);
+          pd = (R)v.x;
         } else {
           eacc.add(R(0.5) * fc * (fR - att));
           pd = R(0.5) * (dfc * (fR - att) + fc * (-P.lam1[pb] * fR + P.lam2[pb] * att));
@@ -575,7 +616,7 @@ void launch_bond(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   size_t sm = bond_smem<R>(S.cap_cov);
   k_bond<R><<<(S.N + APB - 1) / APB, APB * GRP, sm, st>>>(
       S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
-      S.ncov, P, (typename Vec4<R>::T*)S.bo);
+      S.ncov, P, (typename Vec4<R>::T*)S.bo, S.stiff_n, S.stiff_q);
 }
 
 template <class R>
@@ -589,11 +630,16 @@ void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams&
 template <class R>
 void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st) {
   if (S.N == 0) return;
+  if constexpr (sizeof(R) == 4) {
+    // the stiff bonds queued by the bond pass, in FP64 (grid-strided over the queue)
+    k_stiff<<<S.nsm * 4, 256, 0, st>>>(S.cap_cov, S.ld, S.stiff_n, S.stiff_q, S.nbr, S.code, S.rep, S.reps, S.x,
+                                       S.cell4, S.type, (const float4*)S.bo, S.q, P, (float2*)S.stiff_pe);
+  }
   size_t sm = force_smem<R>(S.cap_cov);
   k_cov_force<R><<<(S.N + APB - 1) / APB, APB * GRP, sm, st>>>(
       S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code, S.ncov,
       (const typename Vec4<R>::T*)S.bo, S.q, (const R*)S.qr, P, T, (typename Vec4<R>::T*)S.gslot, S.e_atom,
-      S.x, S.cell4);
+      S.stiff_pe);
 }
 
 template <class R>
