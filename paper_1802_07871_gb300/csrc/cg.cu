@@ -284,41 +284,6 @@ struct RowAcc {
   __device__ inline R value() const { return s + c; }
 };
 
-template <class R, int NV>
-__device__ inline void row_sum(int i, int na, int ld, const int* __restrict__ nbr, const void* __restrict__ M,
-                               const R* __restrict__ v0, const R* __restrict__ v1, R& h0, R& h1, R& hm) {
-  const MatView<R> mat(nbr, M);
-  RowAcc<R> a0, a1, am;
-  int e = 0;
-  for (; e + 4 <= na; e += 4) {
-    size_t o = (size_t)e * ld + i;
-    int j0, j1, j2, j3;
-    R m0, m1, m2, m3;
-    mat.get(o, j0, m0);
-    mat.get(o + ld, j1, m1);
-    mat.get(o + 2 * (size_t)ld, j2, m2);
-    mat.get(o + 3 * (size_t)ld, j3, m3);
-    R x0 = v0[j0], x1 = v0[j1], x2 = v0[j2], x3 = v0[j3];
-    a0.add(m0 * x0); a0.add(m1 * x1); a0.add(m2 * x2); a0.add(m3 * x3);
-    if (NV >= 2) {
-      R y0 = v1[j0], y1 = v1[j1], y2 = v1[j2], y3 = v1[j3];
-      a1.add(m0 * y0); a1.add(m1 * y1); a1.add(m2 * y2); a1.add(m3 * y3);
-    }
-    if (NV >= 3) { am.add(m0); am.add(m1); am.add(m2); am.add(m3); }
-  }
-  for (; e < na; ++e) {
-    int j0;
-    R m0;
-    mat.get((size_t)e * ld + i, j0, m0);
-    a0.add(m0 * v0[j0]);
-    if (NV >= 2) a1.add(m0 * v1[j0]);
-    if (NV >= 3) am.add(m0);
-  }
-  h0 = a0.value();
-  h1 = a1.value();
-  hm = am.value();
-}
-
 // Row sum sum_e M_e x_j(e) of atom i for the matrix pass, software-pipelined:
 // the list indices and entries of the next B entries are loaded before the
 // current batch's x_j are gathered, so the streamed list (the bound of this
@@ -367,6 +332,58 @@ __device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict_
   return acc.value();
 }
 
+// The start of a solve needs three row sums at once: sum M q0_j, sum M d_j
+// and sum M (for the uniform shift of the guess), streamed like the matrix
+// pass (the next B entries loaded ahead), compensated running sums.
+template <class R, int B>
+__device__ inline void row_sum_stream3(int i, int na, int ld, const int* __restrict__ nbr, const void* __restrict__ M,
+                                       const R* __restrict__ x0, const R* __restrict__ x1, R& h0, R& h1, R& hm) {
+  const MatView<R> mat(nbr, M);
+  int jn[B];
+  R mn[B];
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    jn[k] = i;
+    mn[k] = R(0);
+    if (k < na) mat.get((size_t)k * ld + i, jn[k], mn[k]);
+  }
+  RowAcc<R> a0, a1, am;
+  for (int e = 0; e < na; e += B) {
+    int jc[B];
+    R mc[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      jc[k] = jn[k];
+      mc[k] = mn[k];
+      int en = e + B + k;
+      jn[k] = i;
+      mn[k] = R(0);
+      if (en < na) mat.get((size_t)en * ld + i, jn[k], mn[k]);
+    }
+    R t0[B], t1[B], tm[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      t0[k] = mc[k] * __ldg(x0 + jc[k]);
+      t1[k] = mc[k] * __ldg(x1 + jc[k]);
+      tm[k] = mc[k];
+    }
+#pragma unroll
+    for (int w = 1; w < B; w <<= 1)
+#pragma unroll
+      for (int k = 0; k + w < B; k += 2 * w) {
+        t0[k] += t0[k + w];
+        t1[k] += t1[k + w];
+        tm[k] += tm[k + w];
+      }
+    a0.add(t0[0]);
+    a1.add(t1[0]);
+    am.add(tm[0]);
+  }
+  h0 = a0.value();
+  h1 = a1.value();
+  hm = am.value();
+}
+
 // r = -(H q0 + chi), y = D^-1 r, v = H d, dq = 0; sums (sum y, sum r,
 // sum r^2, sum d) and the maxima of r, -r for the initial test (update buffer
 // 2). r is stored shifted by the previous solve's mean (-mu of that solve),
@@ -374,7 +391,8 @@ __device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict_
 // eV/e) would otherwise cost about 1e-7 of it in every element. The shift
 // starts the accumulated one, so mu = -(mean of stored r + shift) holds.
 template <class R>
-__global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr, const int* __restrict__ nall,
+__global__ void __launch_bounds__(256)
+    k_cg_init(int N, int ld, const int* __restrict__ nbr, const int* __restrict__ nall,
                           const void* __restrict__ M, const R* __restrict__ Dg, const R* __restrict__ dinv,
                           const int* __restrict__ type, const int* __restrict__ rep, TypeParams T,
                           double* __restrict__ q, const R* __restrict__ qr, const R* __restrict__ d,
@@ -384,25 +402,18 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
                           int* __restrict__ blocks, int* __restrict__ active, double tol,
                           const double* __restrict__ rhs) {
   const int ub = CG_UPD + 2 * 4;
-  RepAcc<3> acc;
-  RepAcc<1> accd;
-  acc.init();
-  accd.init();
   LaneMax<R> lm;
-  int a0 = blockIdx.x * chunk, a1 = min(N, a0 + chunk);
-  int crid = -1;
-  double dq = 0.0, s0 = 0.0;
-  for (int i = a0 + (int)threadIdx.x; i < a1; i += blockDim.x) {
-    int rid = rep[i];
-    if (rid != crid) {
-      const double* cc = cg + (size_t)rid * CG_STRIDE;
-      dq = ldcg(cc + CG_DQ);
-      double mp = ldcg(cc + CG_MU);
-      s0 = isfinite(mp) ? -mp : 0.0;
-      crid = rid;
-    }
+  R part[3] = {R(0), R(0), R(0)};   // sum y, sum r, sum r^2
+  R pd[1] = {R(0)};                 // sum d
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int rid = i < N ? rep[i] : -1;
+  if (rid >= 0) {
+    const double* cc = cg + (size_t)rid * CG_STRIDE;
+    double dq = ldcg(cc + CG_DQ);
+    double mp = ldcg(cc + CG_MU);
+    double s0 = isfinite(mp) ? -mp : 0.0;
     R hq, hd, hm;
-    row_sum<R, 3>(i, nall[i], ld, nbr, M, qr, d, hq, hd, hm);
+    row_sum_stream3<R, 8>(i, nall[i], ld, nbr, M, qr, d, hq, hd, hm);
     R Di = Dg[i], di = d[i];
     // the guess shifted by dq: H (q0 + dq 1) = D (q0 + dq) + sum M q0_j + dq sum M
     double qi = q[i] + dq;
@@ -414,16 +425,14 @@ __global__ void k_cg_init(int N, int ld, int chunk, const int* __restrict__ nbr,
     y[i] = yi;
     v[i] = Di * di + hd;
     dqv[i] = R(0);
-    acc.to(rid, cg + ub, CG_STRIDE);
-    accd.to(rid, cg + CG_SD, CG_STRIDE);
-    acc.v[0] += (double)yi;
-    acc.v[1] += (double)ri;
-    acc.v[2] += (double)ri * (double)ri;
-    accd.v[0] += (double)di;
+    part[0] = yi;
+    part[1] = ri;
+    part[2] = ri * ri;
+    pd[0] = di;
     lm.add(rid, ri, rmax + 2 * 2);
   }
-  lane_flush<3>(acc, cg + ub, CG_STRIDE);
-  lane_flush<1>(accd, cg + CG_SD, CG_STRIDE);
+  flush_values<R, 3>(rid, part, cg + ub, CG_STRIDE);
+  flush_values<R, 1>(rid, pd, cg + CG_SD, CG_STRIDE);
   lm.finish(rmax + 2 * 2);
   if (last_block(blocks)) {
     for (int rr = threadIdx.x; rr < Rn; rr += blockDim.x) {
@@ -648,9 +657,7 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
   if (S.N == 0) return;
   k_cg_extrap<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.q, S.cqh1, S.cqh2, (R*)S.qr, (const R*)S.dinv,
                                                     (R*)S.cd, S.rep, S.cg, S.R, S.cg_hist, S.cg_blocks);
-  int chunk;
-  int grid = atom_dims(S.N, S.nsm, (const void*)k_cg_init<R>, 256, chunk);
-  k_cg_init<R><<<grid, 256, 0, st>>>(S.N, S.ld, chunk, S.nbr, S.nall, S.M, (const R*)S.Dg,
+  k_cg_init<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nbr, S.nall, S.M, (const R*)S.Dg,
                                      (const R*)S.dinv, S.type, S.rep, T, S.q, (const R*)S.qr, (const R*)S.cd,
                                      (R*)S.cr, (R*)S.cy, (R*)S.cv, (R*)S.cdq, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
                                      S.cg_blocks, S.cg_active, tol, rhs);
