@@ -331,8 +331,7 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   S.ld = ((N + 31) / 32) * 32;
   if (S.ld == 0) S.ld = 32;
   size_t ncol = (size_t)S.ld * cap_all;
-  CK(dalloc(s->list_buf, &S.nbr, ncol));
-  CK(dalloc(s->list_buf, &S.code, ncol));
+  CK(dalloc(s->list_buf, &S.nl, ncol));
   CK(dalloc(s->list_buf, &S.lst, (size_t)std::max(N, 1) * cap_all));
   CK(dalloc(s->list_buf, &S.rev, (size_t)N * cap_cov));
   CK(dalloc(s->list_buf, &S.stiff_q, (size_t)std::max(N, 1) * cap_cov));

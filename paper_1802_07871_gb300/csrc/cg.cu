@@ -293,9 +293,9 @@ struct RowAcc {
 // terms of a batch. B (entries in flight per thread) is chosen at run time
 // by tune_cg_mv among the instantiated depths.
 template <class R, int B>
-__device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict__ nbr, const void* __restrict__ M,
+__device__ inline R row_sum_stream(int i, int na, int ld, const int2* __restrict__ nl, const void* __restrict__ M,
                                    const R* __restrict__ x) {
-  const MatView<R> mat(nbr, M);
+  const MatView<R> mat(nl, M);
   int jn[B];
   R mn[B];
 #pragma unroll
@@ -336,9 +336,9 @@ __device__ inline R row_sum_stream(int i, int na, int ld, const int* __restrict_
 // and sum M (for the uniform shift of the guess), streamed like the matrix
 // pass (the next B entries loaded ahead), compensated running sums.
 template <class R, int B>
-__device__ inline void row_sum_stream3(int i, int na, int ld, const int* __restrict__ nbr, const void* __restrict__ M,
+__device__ inline void row_sum_stream3(int i, int na, int ld, const int2* __restrict__ nl, const void* __restrict__ M,
                                        const R* __restrict__ x0, const R* __restrict__ x1, R& h0, R& h1, R& hm) {
-  const MatView<R> mat(nbr, M);
+  const MatView<R> mat(nl, M);
   int jn[B];
   R mn[B];
 #pragma unroll
@@ -392,7 +392,7 @@ __device__ inline void row_sum_stream3(int i, int na, int ld, const int* __restr
 // starts the accumulated one, so mu = -(mean of stored r + shift) holds.
 template <class R>
 __global__ void __launch_bounds__(256)
-    k_cg_init(int N, int ld, const int* __restrict__ nbr, const int* __restrict__ nall,
+    k_cg_init(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nall,
                           const void* __restrict__ M, const R* __restrict__ Dg, const R* __restrict__ dinv,
                           const int* __restrict__ type, const int* __restrict__ rep, TypeParams T,
                           double* __restrict__ q, const R* __restrict__ qr, const R* __restrict__ d,
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(256)
     double mp = ldcg(cc + CG_MU);
     double s0 = isfinite(mp) ? -mp : 0.0;
     R hq, hd, hm;
-    row_sum_stream3<R, 8>(i, nall[i], ld, nbr, M, qr, d, hq, hd, hm);
+    row_sum_stream3<R, 8>(i, nall[i], ld, nl, M, qr, d, hq, hd, hm);
     R Di = Dg[i], di = d[i];
     // the guess shifted by dq: H (q0 + dq 1) = D (q0 + dq) + sum M q0_j + dq sum M
     double qi = q[i] + dq;
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(256)
 // starts near the tolerance then diverge).
 template <class R, int B>
 __global__ void __launch_bounds__(256)
-    k_cg_mv(int N, int ld, const int* __restrict__ nbr, const int* __restrict__ nall, const void* __restrict__ M,
+    k_cg_mv(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nall, const void* __restrict__ M,
             const R* __restrict__ Dg, const int* __restrict__ rep, const int* __restrict__ conv,
             const int* __restrict__ itp, const R* __restrict__ y, const R* __restrict__ d, const R* __restrict__ v,
             const R* __restrict__ r, R* __restrict__ w, double* __restrict__ cg, int Rn,
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(256)
     const double* cc = cg + (size_t)rid * CG_STRIDE;
     R c = (R)ldcg(cc + CG_C);
     R m = (R)ldcg(cc + CG_M);   // mean of the stored r
-    R hy = row_sum_stream<R, B>(i, nall[i], ld, nbr, M, y);
+    R hy = row_sum_stream<R, B>(i, nall[i], ld, nl, M, y);
     R yi = y[i];
     R zi = yi - c * d[i];
     R wi = Dg[i] * yi + hy - c * v[i];
@@ -657,7 +657,7 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
   if (S.N == 0) return;
   k_cg_extrap<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.q, S.cqh1, S.cqh2, (R*)S.qr, (const R*)S.dinv,
                                                     (R*)S.cd, S.rep, S.cg, S.R, S.cg_hist, S.cg_blocks);
-  k_cg_init<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nbr, S.nall, S.M, (const R*)S.Dg,
+  k_cg_init<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nl, S.nall, S.M, (const R*)S.Dg,
                                      (const R*)S.dinv, S.type, S.rep, T, S.q, (const R*)S.qr, (const R*)S.cd,
                                      (R*)S.cr, (R*)S.cy, (R*)S.cv, (R*)S.cdq, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
                                      S.cg_blocks, S.cg_active, tol, rhs);
@@ -665,7 +665,7 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
 
 template <class R, int B>
 static void launch_cg_mv_b(const DevState& S, cudaStream_t st) {
-  k_cg_mv<R, B><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nbr, S.nall, S.M, (const R*)S.Dg, S.rep,
+  k_cg_mv<R, B><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nl, S.nall, S.M, (const R*)S.Dg, S.rep,
                                                    S.cg_conv, S.cg_it, (const R*)S.cy, (const R*)S.cd,
                                                    (const R*)S.cv, (const R*)S.cr, (R*)S.cw, S.cg, S.R,
                                                    S.cg_blocks, S.cg_active);

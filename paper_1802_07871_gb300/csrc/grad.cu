@@ -49,7 +49,7 @@ __device__ inline double fc_only(double r, double Rin, double S) {
 // memory, then one atomicAdd per parameter and block.
 __global__ void __launch_bounds__(PG_APB * PG_GRP)
     k_pgrad_cov(int N, int cap_cov, int ld, const double4_32a* __restrict__ u, const int* __restrict__ rep,
-                const RepInfo* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ code,
+                const RepInfo* __restrict__ reps, const int2* __restrict__ nl, 
                 const int* __restrict__ ncov, const double* __restrict__ q, const double* __restrict__ wrep,
                 ctbop_params P, double* __restrict__ grad) {
   extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -74,10 +74,10 @@ __global__ void __launch_bounds__(PG_APB * PG_GRP)
     qi = q[i];
     for (int e = l; e < nc; e += PG_GRP) {
       size_t idx = (size_t)e * ld + i;
-      int j = nbr[idx];
+      int j = nl[idx].x;
       double4_32a uj = u[j];
       int dx, dy, dz;
-      unpack_code(code[idx], dx, dy, dz);
+      unpack_code(nl[idx].y, dx, dy, dz);
       double rx = (uj.x - ui.x) + dx * ri.hc[0], ry = (uj.y - ui.y) + dy * ri.hc[1],
              rz = (uj.z - ui.z) + dz * ri.hc[2];
       double4_32a w;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(PG_APB * PG_GRP)
 // 1/2 of the energy). Block sums in shared memory.
 __global__ void __launch_bounds__(256)
     k_pgrad_coul(int N, int ld, const double4_32a* __restrict__ u, const int* __restrict__ rep,
-                 const RepInfo* __restrict__ reps, const int* __restrict__ nbr, const int* __restrict__ code,
+                 const RepInfo* __restrict__ reps, const int2* __restrict__ nl, 
                  const int* __restrict__ nall, const double* __restrict__ q, const double* __restrict__ wrep,
                  ctbop_params P, double* __restrict__ grad) {
   __shared__ double s_g[PG_NPARAM];
@@ -221,10 +221,10 @@ __global__ void __launch_bounds__(256)
       int na = nall[i];
       for (int e = 0; e < na; ++e) {
         size_t idx = (size_t)e * ld + i;
-        int j = nbr[idx];
+        int j = nl[idx].x;
         double4_32a uj = u[j];
         int dx, dy, dz;
-        unpack_code(code[idx], dx, dy, dz);
+        unpack_code(nl[idx].y, dx, dy, dz);
         double rx = (uj.x - ui.x) + dx * ri.hc[0], ry = (uj.y - ui.y) + dy * ri.hc[1],
                rz = (uj.z - ui.z) + dz * ri.hc[2];
         double r = sqrt(rx * rx + ry * ry + rz * rz);
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(256)
 
 // dE/dq_i = (H q)_i + chi_i at the assembled matrix (diagonal without
 // self-images plus every stored entry, self-images included), FP64.
-__global__ void k_charge_grad(int N, int ld, const int* __restrict__ nbr, const int* __restrict__ nall,
+__global__ void k_charge_grad(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nall,
                               const double* __restrict__ M, const double* __restrict__ Dg,
                               const int* __restrict__ type, TypeParams T, const double* __restrict__ q,
                               double* __restrict__ out) {
@@ -268,7 +268,7 @@ __global__ void k_charge_grad(int N, int ld, const int* __restrict__ nbr, const 
   int na = nall[i];
   for (int e = 0; e < na; ++e) {
     size_t idx = (size_t)e * ld + i;
-    s += M[idx] * q[nbr[idx]];
+    s += M[idx] * q[nl[idx].x];
   }
   out[i] = s;
 }
@@ -282,15 +282,15 @@ cudaError_t launch_param_grad(const DevState& S, const ctbop_params& P, const do
   e = cudaFuncSetAttribute(k_pgrad_cov, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_pgrad_cov<<<(S.N + PG_APB - 1) / PG_APB, PG_APB * PG_GRP, sm, st>>>(
-      S.N, S.cap_cov, S.ld, (const double4_32a*)S.u, S.rep, S.reps, S.nbr, S.code, S.ncov, S.q, wrep, P, grad);
-  k_pgrad_coul<<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, (const double4_32a*)S.u, S.rep, S.reps, S.nbr,
-                                                   S.code, S.nall, S.q, wrep, P, grad);
+      S.N, S.cap_cov, S.ld, (const double4_32a*)S.u, S.rep, S.reps, S.nl, S.ncov, S.q, wrep, P, grad);
+  k_pgrad_coul<<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, (const double4_32a*)S.u, S.rep, S.reps, S.nl,
+                                                   S.nall, S.q, wrep, P, grad);
   return cudaGetLastError();
 }
 
 void launch_charge_grad(const DevState& S, const TypeParams& T, double* out, cudaStream_t st) {
   if (S.N == 0) return;
-  k_charge_grad<<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nbr, S.nall, (const double*)S.M,
+  k_charge_grad<<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nl, S.nall, (const double*)S.M,
                                                     (const double*)S.Dg, S.type, T, S.q, out);
 }
 

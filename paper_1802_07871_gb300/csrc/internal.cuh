@@ -6,9 +6,9 @@
 //   type, rep        int32[N]      atom type (0 Si, 1 C), replica id
 //   cell4            int4[N]       cell coordinates (x,y,z) and global cell id, fixed between rebuilds
 //   u                Real4[N]      position relative to the owning cell's origin (w = type)
-//   nbr, code        int32[cap*ld] one list per atom, column-major: entry e of atom i at
-//                                  e*ld + i (ld = N rounded up to 32), so a warp reading entry e
-//                                  of 32 consecutive atoms touches 128 contiguous bytes. Entries
+//   nl               int2[cap*ld]  one list per atom of (j, code) pairs, column-major: entry e of
+//                                  atom i at e*ld + i (ld = N rounded up to 32), so a warp reading
+//                                  entry e of 32 consecutive atoms touches 256 contiguous bytes. Entries
 //                                  [0, ncov) are the covalent list (r < S + skin), [ncov, nall)
 //                                  the rest inside Rc + skin
 //   code             packed cell offset (dx,dy,dz) such that r_ij = u_j - u_i + d*h
@@ -173,7 +173,7 @@ __device__ inline R coul_K_r2(R r2, R gs3, R inv_rc, R ke) {
 template <class R> struct MatView;
 template <> struct MatView<float> {
   const int2* ml;
-  __device__ MatView(const int* /*nbr*/, const void* m) : ml(static_cast<const int2*>(m)) {}
+  __device__ MatView(const int2* /*nl*/, const void* m) : ml(static_cast<const int2*>(m)) {}
   __device__ inline void get(size_t idx, int& j, float& v) const {
     int2 t = __ldg(ml + idx);
     j = t.x;
@@ -181,11 +181,11 @@ template <> struct MatView<float> {
   }
 };
 template <> struct MatView<double> {
-  const int* nbr;
+  const int2* nl;
   const double* M;
-  __device__ MatView(const int* n, const void* m) : nbr(n), M(static_cast<const double*>(m)) {}
+  __device__ MatView(const int2* n, const void* m) : nl(n), M(static_cast<const double*>(m)) {}
   __device__ inline void get(size_t idx, int& j, double& v) const {
-    j = __ldg(nbr + idx);
+    j = __ldg(&nl[idx].x);
     v = __ldg(M + idx);
   }
 };

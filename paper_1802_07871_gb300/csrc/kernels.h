@@ -69,7 +69,8 @@ struct DevState {
   int* cell_rep = nullptr;      // [ncells] replica of each cell
   int* scan_tmp = nullptr;      // >= 1025 ints
   // lists
-  int *nbr = nullptr, *code = nullptr, *ncov = nullptr, *nall = nullptr, *rev = nullptr;
+  int2* nl = nullptr;           // [cap_all*ld] (j, code) list entries, column-major
+  int *ncov = nullptr, *nall = nullptr, *rev = nullptr;
   int2* lst = nullptr;          // [N][cap_all] row-major build scratch (j, code)
   // stiff covalent bonds (FP32 path): a queue of bond ids i * cap_cov + e and,
   // per bond, the FP64-evaluated pair term (dE/dr, energy) as float2

@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(BW * 32)
 // row's end are skipped. Grid-strided over the tiles.
 __global__ void __launch_bounds__(256)
     k_list_transpose(int N, int cap_all, int ld, const int2* __restrict__ lst, const int* __restrict__ nall,
-                     int* __restrict__ nbr, int* __restrict__ code, const int* __restrict__ flag) {
+                     int2* __restrict__ nl, const int* __restrict__ flag) {
   __shared__ int2 tile[32][33];
   if (*flag == 0) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -357,8 +357,7 @@ __global__ void __launch_bounds__(256)
       int e = e0 + ty + 8 * r, a = a0 + tx;
       if (e < na) {
         int2 v = tile[tx][ty + 8 * r];
-        nbr[(size_t)e * ld + a] = v.x;
-        code[(size_t)e * ld + a] = v.y;
+        nl[(size_t)e * ld + a] = v;
       }
     }
     __syncthreads();
@@ -367,22 +366,21 @@ __global__ void __launch_bounds__(256)
 
 // Reverse covalent entry: for entry e of i pointing at (j, d), the entry of
 // j pointing at (i, -d). One thread per atom, grid-strided.
-__global__ void k_rev(int N, int cap_cov, int ld, const int* __restrict__ nbr,
-                      const int* __restrict__ code, const int* __restrict__ ncov,
+__global__ void k_rev(int N, int cap_cov, int ld, const int2* __restrict__ nl, const int* __restrict__ ncov,
                       int* __restrict__ rev, unsigned* __restrict__ err,
                       const int* __restrict__ flag) {
   if (*flag == 0) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     int nc = min(ncov[i], cap_cov);
     for (int e = 0; e < nc; ++e) {
-      int j = nbr[(size_t)e * ld + i];
+      int j = nl[(size_t)e * ld + i].x;
       int dx, dy, dz;
-      unpack_code(code[(size_t)e * ld + i], dx, dy, dz);
+      unpack_code(nl[(size_t)e * ld + i].y, dx, dy, dz);
       int want = pack_code(-dx, -dy, -dz);
       int ncj = min(ncov[j], cap_cov);
       int found = -1;
       for (int k = 0; k < ncj; ++k) {
-        if (nbr[(size_t)k * ld + j] == i && code[(size_t)k * ld + j] == want) { found = k; break; }
+        if (nl[(size_t)k * ld + j].x == i && nl[(size_t)k * ld + j].y == want) { found = k; break; }
       }
       if (found < 0) { atomicOr(err, CT_ERR_REV_MISSING); found = 0; }
       rev[(size_t)i * cap_cov + e] = found;
@@ -425,8 +423,8 @@ void launch_rebuild(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   k_build<R><<<gb, BW * 32, 0, st>>>(C, (const typename Vec4<R>::T*)S.u, S.cell_rep, S.reps, S.cell_start,
                                      S.cell_count, S.cell_atoms, P, S.cap_cov, S.cap_all, S.lst, S.ncov, S.nall,
                                      S.maxcnt, S.err, f);
-  k_list_transpose<<<S.nsm * 8, 256, 0, st>>>(N, S.cap_all, S.ld, S.lst, S.nall, S.nbr, S.code, f);
-  k_rev<<<S.nsm * 4, tb, 0, st>>>(N, S.cap_cov, S.ld, S.nbr, S.code, S.ncov, S.rev, S.err, f);
+  k_list_transpose<<<S.nsm * 8, 256, 0, st>>>(N, S.cap_all, S.ld, S.lst, S.nall, S.nl, f);
+  k_rev<<<S.nsm * 4, tb, 0, st>>>(N, S.cap_cov, S.ld, S.nl, S.ncov, S.rev, S.err, f);
   k_finish_rebuild<<<1, 1, 0, st>>>(S.flag_rebuild, S.rebuild_count);
 }
 

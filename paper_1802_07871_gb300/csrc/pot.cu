@@ -57,8 +57,8 @@ __device__ inline void rel_vec(const typename Vec4<R>::T& ui, const typename Vec
 template <class R>
 __global__ void __launch_bounds__(APB * GRP)
 k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
-       const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
-       const int* __restrict__ code, const int* __restrict__ ncov, PotParams<R> P,
+       const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
+        const int* __restrict__ ncov, PotParams<R> P,
        typename Vec4<R>::T* __restrict__ bo, int* __restrict__ stiff_n, int* __restrict__ stiff_q) {
   using R4 = typename Vec4<R>::T;
   extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -81,10 +81,10 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
     R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
     if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
     for (int e = l; e < nc; e += GRP) {
-      int j = nbr[(size_t)e * ld + i];
+      int j = nl[(size_t)e * ld + i].x;
       R4 uj = u[j];
       R rx, ry, rz;
-      rel_vec<R>(ui, uj, code[(size_t)e * ld + i], hx, hy, hz, rx, ry, rz);
+      rel_vec<R>(ui, uj, nl[(size_t)e * ld + i].y, hx, hy, hz, rx, ry, rz);
       R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
       int tj = (int)uj.w;
       int pb = ti * 2 + tj;
@@ -166,7 +166,7 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
 // and the energy 1/2 fc (A e^{-l1 r} - c b B e^{-l2 r}) as float2.
 __global__ void __launch_bounds__(256)
     k_stiff(int cap_cov, int ld, const int* __restrict__ nq, const int* __restrict__ q_ids,
-            const int* __restrict__ nbr, const int* __restrict__ code, const int* __restrict__ rep,
+            const int2* __restrict__ nl,  const int* __restrict__ rep,
             const RepInfo* __restrict__ reps, const double* __restrict__ x, const int4* __restrict__ cell4,
             const int* __restrict__ type, const float4* __restrict__ bo, const double* __restrict__ q,
             PotParams<float> P, float2* __restrict__ pe) {
@@ -175,9 +175,9 @@ __global__ void __launch_bounds__(256)
     int id = q_ids[t];
     int i = id / cap_cov, e = id - i * cap_cov;
     size_t idx = (size_t)e * ld + i;
-    int j = nbr[idx];
+    int j = nl[idx].x;
     int dcx, dcy, dcz;
-    unpack_code(code[idx], dcx, dcy, dcz);
+    unpack_code(nl[idx].y, dcx, dcy, dcz);
     const RepInfo& ri = reps[rep[i]];
     int4 ci4 = cell4[i], cj4 = cell4[j];
     double ax = x[3 * j] - x[3 * i] + (double)(ci4.x + dcx - cj4.x) * ri.hc[0];
@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(256)
 template <class R>
 __global__ void __launch_bounds__(256)
     k_assemble(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
-               const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
-               const int* __restrict__ code, const int* __restrict__ ncov, const int* __restrict__ nall,
+               const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
+                const int* __restrict__ ncov, const int* __restrict__ nall,
                const int* __restrict__ rev, const typename Vec4<R>::T* __restrict__ bo, PotParams<R> P,
                TypeParams T, void* __restrict__ M, R* __restrict__ Dg, R* __restrict__ dinv) {
   using R4 = typename Vec4<R>::T;
@@ -224,15 +224,15 @@ __global__ void __launch_bounds__(256)
   if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
   int nc = ncov[i], na = nall[i];
   R wsum = R(0), selfm = R(0);
-  const int* pn = nbr + i;
-  const int* pc = code + i;
+  const int2* pl = nl + i;
   // covalent entries: K minus twice the bond-order coupling w
   for (int e = 0; e < nc; ++e) {
     size_t off = (size_t)e * ld;
-    int j = pn[off];
+    int2 jcd = __ldg(pl + off);
+      int j = jcd.x;
     R4 uj = u[j];
     R rx, ry, rz;
-    rel_vec<R>(ui, uj, pc[off], hx, hy, hz, rx, ry, rz);
+    rel_vec<R>(ui, uj, jcd.y, hx, hy, hz, rx, ry, rz);
     R r2 = rx * rx + ry * ry + rz * rz;
     int tj = (int)uj.w;
     int pb = ti * 2 + tj;
@@ -257,8 +257,9 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int k = 0; k < PB; ++k) {
     bool ok = nc + k < na;
-    jn[k] = ok ? __ldg(pn + (size_t)(nc + k) * ld) : i;
-    cn[k] = ok ? __ldg(pc + (size_t)(nc + k) * ld) : pack_code(0, 0, 0);
+    int2 t = ok ? __ldg(pl + (size_t)(nc + k) * ld) : make_int2(i, pack_code(0, 0, 0));
+    jn[k] = t.x;
+    cn[k] = t.y;
   }
   for (int e = nc; e < na; e += PB) {
     int jc[PB], cc[PB];
@@ -268,8 +269,9 @@ __global__ void __launch_bounds__(256)
       cc[k] = cn[k];
       int en = e + PB + k;
       bool ok = en < na;
-      jn[k] = ok ? __ldg(pn + (size_t)en * ld) : i;
-      cn[k] = ok ? __ldg(pc + (size_t)en * ld) : pack_code(0, 0, 0);
+      int2 t = ok ? __ldg(pl + (size_t)en * ld) : make_int2(i, pack_code(0, 0, 0));
+      jn[k] = t.x;
+      cn[k] = t.y;
     }
     R4 uj[PB];
 #pragma unroll
@@ -296,7 +298,7 @@ template <class R>
 __global__ void __launch_bounds__(APB * GRP)
 k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
             const int* __restrict__ rep, const RepInfo* __restrict__ reps,
-            const int* __restrict__ nbr, const int* __restrict__ code, const int* __restrict__ ncov,
+            const int2* __restrict__ nl,  const int* __restrict__ ncov,
             const typename Vec4<R>::T* __restrict__ bo, const double* __restrict__ q,
             const R* __restrict__ qr, PotParams<R> P, TypeParams T, typename Vec4<R>::T* __restrict__ gslot,
             double* __restrict__ e_atom, const void* __restrict__ stiff_pe) {
@@ -328,10 +330,10 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
     R qi = qr[i];
     for (int e = l; e < nc; e += GRP) {
       size_t idx = (size_t)e * ld + i;
-      int j = nbr[idx];
+      int j = nl[idx].x;
       R4 uj = u[j];
       R rx, ry, rz;
-      rel_vec<R>(ui, uj, code[idx], hx, hy, hz, rx, ry, rz);
+      rel_vec<R>(ui, uj, nl[idx].y, hx, hy, hz, rx, ry, rz);
       R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
       int tj = (int)uj.w;
       int pb = ti * 2 + tj;
@@ -464,8 +466,8 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
 template <class R>
 __global__ void __launch_bounds__(256)
     k_coul_gather(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
-                  const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int* __restrict__ nbr,
-                  const int* __restrict__ code, const int* __restrict__ ncov, const int* __restrict__ nall,
+                  const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
+                   const int* __restrict__ ncov, const int* __restrict__ nall,
                   const int* __restrict__ rev, const typename Vec4<R>::T* __restrict__ gslot,
                   const R* __restrict__ qr, PotParams<R> P, TypeParams T, int kick, double half_dt,
                   const uint8_t* __restrict__ frozen, double* __restrict__ F, double* __restrict__ v,
@@ -491,16 +493,16 @@ __global__ void __launch_bounds__(256)
     R w[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) w[k] = R(0);
-    const int* pn = nbr + i;
-    const int* pc = code + i;
+    const int2* pl = nl + i;
     const R gs_i0 = P.gshield3[ti * 2], gs_i1 = P.gshield3[ti * 2 + 1];
     // covalent entries: charge term plus the slot gather
     for (int e = 0; e < nc; ++e) {
       size_t off = (size_t)e * ld;
-      int j = pn[off];
+      int2 jcd = __ldg(pl + off);
+      int j = jcd.x;
       R4 uj = u[j];
       R rx, ry, rz;
-      rel_vec<R>(ui, uj, pc[off], hx, hy, hz, rx, ry, rz);
+      rel_vec<R>(ui, uj, jcd.y, hx, hy, hz, rx, ry, rz);
       R r2 = rx * rx + ry * ry + rz * rz;
       R r, ir, K, c;
       coul_fn_r2<R>(r2, uj.w != R(0) ? gs_i1 : gs_i0, P.inv_rcoul, P.ke, r, ir, K, c);
@@ -523,8 +525,9 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int k = 0; k < PB; ++k) {
       bool ok = nc + k < na;
-      jn[k] = ok ? __ldg(pn + (size_t)(nc + k) * ld) : i;
-      cn[k] = ok ? __ldg(pc + (size_t)(nc + k) * ld) : pack_code(0, 0, 0);
+      int2 t = ok ? __ldg(pl + (size_t)(nc + k) * ld) : make_int2(i, pack_code(0, 0, 0));
+      jn[k] = t.x;
+      cn[k] = t.y;
     }
     for (int e = nc; e < na; e += PB) {
       int jc[PB], cc[PB];
@@ -534,8 +537,9 @@ __global__ void __launch_bounds__(256)
         cc[k] = cn[k];
         int en = e + PB + k;
         bool ok = en < na;
-        jn[k] = ok ? __ldg(pn + (size_t)en * ld) : i;
-        cn[k] = ok ? __ldg(pc + (size_t)en * ld) : pack_code(0, 0, 0);
+        int2 t = ok ? __ldg(pl + (size_t)en * ld) : make_int2(i, pack_code(0, 0, 0));
+        jn[k] = t.x;
+        cn[k] = t.y;
       }
       R4 uj[PB];
       R qj[PB];
@@ -615,7 +619,7 @@ void launch_bond(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   if (S.N == 0) return;
   size_t sm = bond_smem<R>(S.cap_cov);
   k_bond<R><<<(S.N + APB - 1) / APB, APB * GRP, sm, st>>>(
-      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
       S.ncov, P, (typename Vec4<R>::T*)S.bo, S.stiff_n, S.stiff_q);
 }
 
@@ -623,7 +627,7 @@ template <class R>
 void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st) {
   if (S.N == 0) return;
   k_assemble<R><<<(S.N + 255) / 256, 256, 0, st>>>(
-      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
       S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, S.M, (R*)S.Dg, (R*)S.dinv);
 }
 
@@ -632,12 +636,12 @@ void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams
   if (S.N == 0) return;
   if constexpr (sizeof(R) == 4) {
     // the stiff bonds queued by the bond pass, in FP64 (grid-strided over the queue)
-    k_stiff<<<S.nsm * 4, 256, 0, st>>>(S.cap_cov, S.ld, S.stiff_n, S.stiff_q, S.nbr, S.code, S.rep, S.reps, S.x,
+    k_stiff<<<S.nsm * 4, 256, 0, st>>>(S.cap_cov, S.ld, S.stiff_n, S.stiff_q, S.nl, S.rep, S.reps, S.x,
                                        S.cell4, S.type, (const float4*)S.bo, S.q, P, (float2*)S.stiff_pe);
   }
   size_t sm = force_smem<R>(S.cap_cov);
   k_cov_force<R><<<(S.N + APB - 1) / APB, APB * GRP, sm, st>>>(
-      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code, S.ncov,
+      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl, S.ncov,
       (const typename Vec4<R>::T*)S.bo, S.q, (const R*)S.qr, P, T, (typename Vec4<R>::T*)S.gslot, S.e_atom,
       S.stiff_pe);
 }
@@ -652,7 +656,7 @@ void launch_coul_gather(const DevState& S, const PotParams<R>& P, const TypePara
   long long tiles = ((long long)S.N + 255) / 256, slots = (long long)S.nsm * occ;
   int grid = (int)(tiles < slots ? tiles : slots);
   k_coul_gather<R><<<grid, 256, 0, st>>>(
-      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nbr, S.code,
+      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
       S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.gslot, (const R*)S.qr, P, T, kick, half_dt,
       S.frozen, S.F, S.v, S.e_atom, S.rep_acc, S.err);
 }
