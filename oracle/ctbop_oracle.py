@@ -543,6 +543,57 @@ def velocity_verlet(x, v, types, box, pbc, params, dt, nsteps, frozen=None,
     return x, v, res["q"], np.array(etot)
 
 
+def thermostat_dof(types, frozen=None):
+    """Degrees of freedom a thermostat controls: 3 per mobile atom, less the 3
+    of the centre-of-mass motion when no atom is frozen (then the total
+    momentum is conserved)."""
+    n = len(types)
+    fr = np.zeros(n, bool) if frozen is None else np.asarray(frozen, bool)
+    g = 3 * int((~fr).sum())
+    return g - 3 if not fr.any() else g
+
+
+def nose_hoover(x, v, types, box, pbc, params, dt, nsteps, T0, tau, frozen=None, Q=0.0, xi=0.0, eta=0.0):
+    """NVT velocity Verlet with one Nose-Hoover thermostat (reading of the
+    paper's "NVT ensemble", Sec. 3.3, which names no thermostat).
+    Equations of motion: dx/dt = v, dv/dt = F/m - xi v, dxi/dt = (2K - g kB T0)/Qm,
+    deta/dt = xi, with thermostat mass Qm = g kB T0 tau^2; the extended energy
+    E + K + Qm xi^2 / 2 + g kB T0 eta is conserved. One step is the symmetric
+    splitting: xi and eta half-steps, velocity scaling by exp(-xi dt/2), the
+    velocity-Verlet kick/drift/force/kick, velocity scaling, eta and xi
+    half-steps. Frozen atoms keep v = 0 and count in neither K nor g.
+    Returns (x, v, q, xi, eta, extended energies after each step)."""
+    P = tables(params)
+    x = np.array(x, float)
+    v = np.array(v, float)
+    types = np.asarray(types)
+    frozen = np.zeros(len(x), bool) if frozen is None else np.asarray(frozen, bool)
+    inv_m = (ACC / P.mass[types])[:, None]
+    mob = (~frozen)[:, None]
+    g = thermostat_dof(types, frozen)
+    gkT = g * KB * T0
+    Qm = gkT * tau * tau
+    res = evaluate(x, types, box, pbc, params, Q)
+    F = res["F"]
+    ext = []
+    for _ in range(nsteps):
+        K = kinetic_energy(v, types, params)
+        xi = xi + 0.5 * dt * (2.0 * K - gkT) / Qm
+        eta = eta + 0.5 * dt * xi
+        v = np.where(mob, v * np.exp(-0.5 * dt * xi), 0.0)
+        v = np.where(mob, v + 0.5 * dt * F * inv_m, 0.0)
+        x = np.where(mob, x + dt * v, x)
+        res = evaluate(x, types, box, pbc, params, Q)
+        F = res["F"]
+        v = np.where(mob, v + 0.5 * dt * F * inv_m, 0.0)
+        v = np.where(mob, v * np.exp(-0.5 * dt * xi), 0.0)
+        eta = eta + 0.5 * dt * xi
+        K = kinetic_energy(v, types, params)
+        xi = xi + 0.5 * dt * (2.0 * K - gkT) / Qm
+        ext.append(res["E"] + K + 0.5 * Qm * xi * xi + gkT * eta)
+    return x, v, res["q"], xi, eta, np.array(ext)
+
+
 # ----------------------------------------------------------------------------
 # force-matching loss and its parameter gradient (the definition, by central
 # differences; the paper fits its parameters to DFT energies, forces and
