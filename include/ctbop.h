@@ -75,7 +75,9 @@ extern "C" {
 #define CTBOP_GET_VIRIAL    5   /* double[R*9] virial W = -sum_u u (x) dE/du, row-major 3x3 (eV) */
 #define CTBOP_GET_E_ATOM    6   /* double[N]   per-atom energies (eV) */
 #define CTBOP_GET_MU        7   /* double[R]   electronegativity (Lagrange multiplier of sum q = Q), eV/e */
-#define CTBOP_GET_KINETIC   8   /* double[R]   kinetic energy of the last step (eV) */
+#define CTBOP_GET_KINETIC   8   /* double[R]   kinetic energy of the current velocities (eV) */
+#define CTBOP_GET_THERMOSTAT 9  /* double[R*4] Nose-Hoover state per replica: xi (1/fs), eta (fs), thermostat
+                                   mass Qm (eV fs^2), g kB T0 (eV); zeros when the replica has none */
 
 /* ---- parameters --------------------------------------------------------- */
 /* Index conventions: pair tables [ti*2+tj] (symmetric for the pair block),
@@ -200,6 +202,16 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st);
  * launches_out[CTBOP_NPHASE] (host arrays, caller-owned, not cleared).
  * Slower than ctbop_step: for per-kernel timing only. */
 int ctbop_profile_steps(ctbop_system* s, int64_t n_steps, double dt_fs, double* ms_out, int64_t* launches_out);
+
+/* NVT (the paper's MD runs NVT, Sec. 3.3, naming no thermostat; read as one
+ * Nose-Hoover thermostat per replica). T0[r] > 0 (K) and tau[r] > 0 (fs)
+ * attach a thermostat to replica r with mass Qm = g kB T0 tau^2, g = 3 per
+ * mobile atom (less 3 when the replica has no frozen atom); T0[r] <= 0 leaves
+ * it NVE. Both arrays are [R], host; T0 == NULL turns every thermostat off.
+ * The thermostat variables xi, eta start at 0. The extended energy
+ * E + K + Qm xi^2 / 2 + g kB T0 eta is conserved by ctbop_step. Set after
+ * set_layout and set_frozen. Errors: INVALID_ARG, STATE. */
+int ctbop_set_thermostat(ctbop_system* s, const double* T0, const double* tau);
 
 /* Replace the potential's parameters (copied; same validity rules as
  * ctbop_create). The next compute/step rebuilds the lists and re-captures

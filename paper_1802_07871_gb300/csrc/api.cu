@@ -20,6 +20,7 @@ using namespace ct;
 namespace {
 
 const double kAcc = 9.648533212e-3;   // 1 eV/(A u) in A/fs^2
+const double kKB = 8.617333262e-5;    // Boltzmann constant, eV/K
 
 struct DevBuf {
   std::vector<void*> ptrs;
@@ -57,6 +58,7 @@ struct ctbop_system {
   int alloc_N = -1, alloc_R = -1, alloc_cells = -1, alloc_cov = -1, alloc_all = -1;
   // graphs
   cudaGraphExec_t g_eval = nullptr, g_step = nullptr;
+  bool nvt = false;             // some replica has a Nose-Hoover thermostat
   // matrix-pass autotuning: the lists it was tuned on, and the timings
   int tuned_N = -1, tuned_cap = -1;
   float mv_ms[3] = {0.f, 0.f, 0.f};
@@ -285,6 +287,9 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->rep_buf, &S.reps, (size_t)s->R));
   CK(dalloc(s->rep_buf, &S.rep_acc, (size_t)s->R * RA_STRIDE));
   CK(dalloc(s->rep_buf, &S.cg, (size_t)s->R * CG_STRIDE));
+  CK(dalloc(s->rep_buf, &S.nh, (size_t)s->R * NH_STRIDE));
+  CK(cudaMemset(S.nh, 0, sizeof(double) * s->R * NH_STRIDE));
+  s->nvt = false;
   CK(dalloc(s->rep_buf, &S.cg_rmax, (size_t)s->R * 6));
   CK(dalloc(s->rep_buf, &S.cg_conv, (size_t)s->R));
   CK(dalloc(s->rep_buf, &S.cg_iters, (size_t)s->R));
@@ -384,6 +389,7 @@ static void enqueue_back(ctbop_system* s, const PotParams<Rr>& P, cudaStream_t s
   DevState& S = s->S;
   if (solve) launch_cg_end<Rr>(S, st);
   launch_forces<Rr>(S, P, s->T, md ? 1 : 0, 0.5 * dt, st);
+  if (md && s->nvt) launch_nh_end(S, dt, st);
 }
 
 template <class Rr>
@@ -598,7 +604,10 @@ static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double 
     }
     if (!rc) rc = timed(7, 2, [&] { launch_cg_end<Rr>(S, st); });
     if (!rc) rc = timed(8, sizeof(Rr) == 4 ? 2 : 1, [&] { launch_cov_force<Rr>(S, P, s->T, st); });
-    if (!rc) rc = timed(9, 1, [&] { launch_coul_gather<Rr>(S, P, s->T, 1, 0.5 * dt, st); });
+    if (!rc) rc = timed(9, s->nvt ? 2 : 1, [&] {
+      launch_coul_gather<Rr>(S, P, s->T, 1, 0.5 * dt, st);
+      if (s->nvt) launch_nh_end(S, dt, st);
+    });
     if (!rc) {
       unsigned bits = 0;
       rc = read_err(s, bits);
@@ -666,6 +675,42 @@ int ctbop_create(const ctbop_params* p, const ctbop_options* o, ctbop_system** o
   }
   s->stream = s->own_stream;
   *out = s;
+  return CTBOP_OK;
+}
+
+int ctbop_set_thermostat(ctbop_system* s, const double* T0, const double* tau) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
+  if (T0 && !tau) return fail(s, CTBOP_ERR_INVALID_ARG, "tau needed with T0");
+  cudaSetDevice(s->o.device);
+  DevState& S = s->S;
+  const int R = s->R;
+  std::vector<uint8_t> fr(S.N);
+  if (S.N) CK(cudaMemcpy(fr.data(), S.frozen, S.N, cudaMemcpyDeviceToHost));
+  std::vector<double> h((size_t)R * NH_STRIDE, 0.0);
+  bool any = false;
+  for (int r = 0; r < R; ++r) {
+    if (!T0 || !(T0[r] > 0)) continue;
+    if (!(tau[r] > 0) || !std::isfinite(tau[r]) || !std::isfinite(T0[r]))
+      return fail(s, CTBOP_ERR_INVALID_ARG, "thermostat needs T0 > 0 and tau > 0");
+    int64_t mobile = 0;
+    bool any_frozen = false;
+    for (int64_t i = s->off[r]; i < s->off[r + 1]; ++i) {
+      if (fr[i]) any_frozen = true; else ++mobile;
+    }
+    double g = 3.0 * mobile - (any_frozen ? 0.0 : 3.0);
+    if (g <= 0) continue;   // nothing to thermostat
+    double gkT = g * kKB * T0[r], Qm = gkT * tau[r] * tau[r];
+    double* row = h.data() + (size_t)r * NH_STRIDE;
+    row[NH_ON] = 1.0;
+    row[NH_GKT] = gkT;
+    row[NH_QM] = Qm;
+    row[NH_QINV] = 1.0 / Qm;
+    any = true;
+  }
+  CK(cudaMemcpy(S.nh, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
+  if (any != s->nvt) destroy_graphs(s);   // the step graph holds the end-of-step update or not
+  s->nvt = any;
   return CTBOP_OK;
 }
 
@@ -971,6 +1016,7 @@ int ctbop_get(ctbop_system* s, int what, void* dst, int mem) {
     case CTBOP_GET_VELOCITIES: src = S.v; width = pitch = 24 * N; break;
     case CTBOP_GET_CHARGES: src = S.q; width = pitch = 8 * N; break;
     case CTBOP_GET_E_ATOM: src = S.e_atom; width = pitch = 8 * N; break;
+    case CTBOP_GET_THERMOSTAT: src = S.nh + NH_XI; width = 32; pitch = NH_STRIDE * 8; rows = R; break;
     default: return fail(s, CTBOP_ERR_INVALID_ARG, "unknown selector");
   }
   if (width == 0) return CTBOP_OK;

@@ -26,6 +26,18 @@ enum RepSlots {
   RA_STRIDE = 12
 };
 
+// Nose-Hoover thermostat per replica (double), see md.cu.
+enum NhSlots {
+  NH_XI = 0,       // xi (1/fs)
+  NH_ETA = 1,      // eta (fs)
+  NH_QM = 2,       // Qm (eV fs^2)
+  NH_GKT = 3,      // g kB T0 (eV)
+  NH_ON = 4,       // 1 when the replica has a thermostat
+  NH_QINV = 5,     // 1 / Qm
+  NH_XIH = 6,      // xi after this step's first half-update
+  NH_STRIDE = 8
+};
+
 // CG scalars per replica (double), see cg.cu.
 enum CgSlots {
   CG_DOTS = 0,     // [2 buffers][2]: r.z, w.z
@@ -62,6 +74,7 @@ struct DevState {
   RepInfo* reps = nullptr;
   double* rep_acc = nullptr;    // [R][RA_STRIDE]
   double* cg = nullptr;         // [R][CG_STRIDE]
+  double* nh = nullptr;         // [R][NH_STRIDE] thermostats
   int* cg_conv = nullptr;       // [R] converged flag
   int* cg_iters = nullptr;      // [R] iterations used
   // cells
@@ -130,6 +143,7 @@ template <class R> void launch_forces(const DevState& S, const PotParams<R>& P, 
 template <class R> void launch_kick_drift(const DevState& S, const TypeParams& T, double dt, double half_skin2,
                                           cudaStream_t st);
 void launch_zero_acc(const DevState& S, cudaStream_t st);
+void launch_nh_end(const DevState& S, double dt, cudaStream_t st);
 template <class R> cudaError_t setup_pot(int cap_cov);
 template <class R> void launch_copy_q(const DevState& S, cudaStream_t st);
 // launch shape for kernels with one thread per atom: resident blocks only,

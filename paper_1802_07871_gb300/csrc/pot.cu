@@ -471,7 +471,8 @@ __global__ void __launch_bounds__(256)
                   const int* __restrict__ rev, const typename Vec4<R>::T* __restrict__ gslot,
                   const R* __restrict__ qr, PotParams<R> P, TypeParams T, int kick, double half_dt,
                   const uint8_t* __restrict__ frozen, double* __restrict__ F, double* __restrict__ v,
-                  double* __restrict__ e_atom, double* __restrict__ rep_acc, unsigned* __restrict__ err) {
+                  double* __restrict__ e_atom, double* __restrict__ rep_acc, unsigned* __restrict__ err,
+                  const double* __restrict__ nh) {
   using R4 = typename Vec4<R>::T;
   RepAcc<2> accE;   // (E, KE)
   RepAcc<9> accW;   // virial
@@ -578,11 +579,17 @@ __global__ void __launch_bounds__(256)
     accE.v[0] += ea;
 #pragma unroll
     for (int k = 0; k < 9; ++k) accW.v[k] += (double)w[k];
-    if (kick) {
-      if (!frozen[i]) {
-        double sc = half_dt * T.inv_mass_acc[ti];
-        v[3 * i] += sc * Fx; v[3 * i + 1] += sc * Fy; v[3 * i + 2] += sc * Fz;
+    if (kick && !frozen[i]) {
+      double sc = half_dt * T.inv_mass_acc[ti];
+      double vx = v[3 * i] + sc * Fx, vy = v[3 * i + 1] + sc * Fy, vz = v[3 * i + 2] + sc * Fz;
+      const double* h = nh + (size_t)ri_id * NH_STRIDE;
+      if (h[NH_ON] != 0.0) {   // NVT: the second velocity scaling, exp(-xi' dt/2)
+        double s = exp(-half_dt * h[NH_XIH]);
+        vx *= s; vy *= s; vz *= s;
       }
+      v[3 * i] = vx; v[3 * i + 1] = vy; v[3 * i + 2] = vz;
+    }
+    {   // kinetic energy of the current velocities
       double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
       accE.v[1] += 0.5 * T.mass[ti] * (vx * vx + vy * vy + vz * vz);
     }
@@ -658,7 +665,7 @@ void launch_coul_gather(const DevState& S, const PotParams<R>& P, const TypePara
   k_coul_gather<R><<<grid, 256, 0, st>>>(
       S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
       S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.gslot, (const R*)S.qr, P, T, kick, half_dt,
-      S.frozen, S.F, S.v, S.e_atom, S.rep_acc, S.err);
+      S.frozen, S.F, S.v, S.e_atom, S.rep_acc, S.err, S.nh);
 }
 
 template <class R>

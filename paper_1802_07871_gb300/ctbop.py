@@ -25,7 +25,7 @@ HOST, DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 FIXED_CHARGES = 1
 GET = {"energy": 0, "forces": 1, "charges": 2, "positions": 3, "velocities": 4,
-       "virial": 5, "e_atom": 6, "mu": 7, "kinetic": 8}
+       "virial": 5, "e_atom": 6, "mu": 7, "kinetic": 8, "thermostat": 9}
 
 # every symbol include/ctbop.h declares
 EXPORTS = (
@@ -33,7 +33,7 @@ EXPORTS = (
     "ctbop_set_stream", "ctbop_set_layout", "ctbop_set_box", "ctbop_set_types",
     "ctbop_set_positions", "ctbop_set_velocities", "ctbop_set_charges", "ctbop_set_frozen",
     "ctbop_set_total_charge", "ctbop_compute", "ctbop_step", "ctbop_get", "ctbop_status",
-    "ctbop_profile_steps", "ctbop_energy_noalloc", "ctbop_param_grad", "ctbop_set_params",
+    "ctbop_profile_steps", "ctbop_energy_noalloc", "ctbop_param_grad", "ctbop_set_params", "ctbop_set_thermostat",
 )
 NPHASE = 10
 PHASES = ("kick_drift", "lists", "bond", "assemble", "cg_start", "cg_matvec", "cg_update",
@@ -271,6 +271,17 @@ class System:
         """Replica of every atom (from the layout)."""
         return np.repeat(np.arange(self.R), np.diff(self._offsets))
 
+    def set_thermostat(self, T0, tau):
+        """Nose-Hoover thermostat per replica (T0 in K, tau in fs; T0 <= 0:
+        NVE for that replica; T0=None: all NVE)."""
+        if T0 is None:
+            self._check(self._L.ctbop_set_thermostat(self._h, None, None), "set_thermostat")
+            return
+        t0 = np.ascontiguousarray(np.broadcast_to(np.asarray(T0, float), (self.R,)))
+        ta = np.ascontiguousarray(np.broadcast_to(np.asarray(tau, float), (self.R,)))
+        self._check(self._L.ctbop_set_thermostat(self._h, t0.ctypes.data_as(C.c_void_p),
+                                                 ta.ctypes.data_as(C.c_void_p)), "set_thermostat")
+
     def set_params(self, params: dict):
         """Replace the potential's parameters (the next evaluation rebuilds
         lists and graphs as needed)."""
@@ -395,7 +406,7 @@ class System:
         sel = GET[what]
         shape = {"energy": (self.R,), "mu": (self.R,), "kinetic": (self.R,), "virial": (self.R, 3, 3),
                  "forces": (self.n, 3), "positions": (self.n, 3), "velocities": (self.n, 3),
-                 "charges": (self.n,), "e_atom": (self.n,)}[what]
+                 "charges": (self.n,), "e_atom": (self.n,), "thermostat": (self.R, 4)}[what]
         if out is None:
             out = np.empty(shape, dtype=np.float64)
         ptr, mem = _ptr(out)

@@ -1,0 +1,97 @@
+"""Nose-Hoover NVT on the GPU against the oracle's integrator (same
+splitting), its conserved extended energy, and replicas that mix NVT and
+NVE in one batch."""
+import numpy as np
+import pytest
+
+from oracle import ctbop_oracle as O
+from paper_1802_07871_gb300 import ctbop
+from paper_1802_07871_gb300 import structures as st
+
+pytestmark = pytest.mark.gpu
+P0 = st.load_params("p0")
+
+
+def _wrap(d, box, pbc):
+    return d - np.where(pbc, np.round(d / box) * box, 0.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["bulk", "slab"])
+def test_nvt_matches_oracle_trajectory(prec, case):
+    if case == "bulk":
+        s = st.sic_3c(2, 4.36, 0.05, seed=91)
+        v = st.maxwell_boltzmann(s.types, 600.0, seed=92)
+    else:
+        s = st.stepped_slab_small(6, 3, 4)
+        v = st.maxwell_boltzmann(s.types, 600.0, seed=93, frozen=s.frozen)
+    T0, tau, n = 1800.0, 8.0, 20
+    sysm = ctbop.System(P0, precision=prec)
+    sysm.load(s, velocities=v)
+    sysm.set_thermostat(T0, tau)
+    sysm.step(n, 0.5)
+    xg, vg, th = sysm.get("positions"), sysm.get("velocities"), sysm.get("thermostat")[0]
+    sysm.close()
+    xo, vo, qo, xi, eta, ext = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P0, 0.5, n, T0, tau, s.frozen)
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    assert np.max(np.abs(_wrap(xg - xo, s.box, s.pbc))) < tol
+    assert np.max(np.abs(vg - vo)) < tol
+    assert th[0] == pytest.approx(xi, rel=1e-6 if prec == "fp64" else 1e-3, abs=1e-12)
+    assert th[1] == pytest.approx(eta, rel=1e-6 if prec == "fp64" else 1e-3, abs=1e-10)
+    g = O.thermostat_dof(s.types, s.frozen)
+    assert th[3] == pytest.approx(g * O.KB * T0, rel=1e-12)
+
+
+def _gpu_extended(s, v, dt, n, every):
+    sysm = ctbop.System(P0, precision="fp64")
+    sysm.load(s, velocities=v)
+    sysm.set_thermostat(1200.0, 10.0)
+    sysm.compute()
+    e0 = sysm.get("energy")[0] + sysm.get("kinetic")[0]
+    ext = [e0]
+    for _ in range(n // every):
+        sysm.step(every, dt)
+        xi, eta, Qm, gkT = sysm.get("thermostat")[0]
+        ext.append(sysm.get("energy")[0] + sysm.get("kinetic")[0] + 0.5 * Qm * xi * xi + gkT * eta)
+    sysm.close()
+    return np.array(ext)
+
+
+def test_nvt_extended_energy_follows_oracle_and_drifts_as_dt_squared():
+    """The extended energy E + K + Qm xi^2/2 + g kB T0 eta is conserved up to
+    the splitting's O(dt^2) error. The synthetic set's ideal lattice relaxes
+    violently (releasing potential energy into the bath), so that error is
+    visible at dt = 0.5 fs: the GPU's series equals the oracle's, and halving
+    dt divides the drift by about four."""
+    s = st.sic_3c(2, 4.36, 0.05, seed=94)
+    v = st.maxwell_boltzmann(s.types, 300.0, seed=95)
+    g1 = _gpu_extended(s, v, 0.5, 200, 10)
+    g2 = _gpu_extended(s, v, 0.25, 400, 20)
+    *_, ext = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P0, 0.5, 200, 1200.0, 10.0)
+    np.testing.assert_allclose(g1[1:], ext[9::10], rtol=0, atol=1e-6 * s.n)
+    d1, d2 = np.max(np.abs(g1 - g1[0])), np.max(np.abs(g2 - g2[0]))
+    assert 3.0 < d1 / d2 < 6.0, (d1, d2)
+
+
+def test_nvt_and_nve_replicas_in_one_batch():
+    """Replica 0 with a thermostat, replica 1 without: replica 1's trajectory
+    is the one it has on its own under NVE."""
+    a = st.sic_3c(1, 4.36, 0.05, seed=96)
+    b = st.sic_3c(2, 4.36, 0.05, seed=97)
+    va = st.maxwell_boltzmann(a.types, 500.0, seed=98)
+    vb = st.maxwell_boltzmann(b.types, 500.0, seed=99)
+    sysm = ctbop.System(P0, precision="fp64")
+    sysm.load_replicas([a, b])
+    sysm.set_velocities(np.concatenate([va, vb]))
+    sysm.set_thermostat([2000.0, 0.0], [5.0, 1.0])
+    sysm.step(15, 0.5)
+    xb = sysm.get("positions")[a.n:]
+    th = sysm.get("thermostat")
+    sysm.close()
+    ref = ctbop.System(P0, precision="fp64")
+    ref.load(b, velocities=vb)
+    ref.step(15, 0.5)
+    xr = ref.get("positions")
+    ref.close()
+    assert np.max(np.abs(_wrap(xb - xr, b.box, b.pbc))) < 1e-10
+    assert th[1, 0] == 0.0 and th[0, 0] != 0.0
