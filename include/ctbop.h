@@ -243,10 +243,17 @@ int ctbop_param_grad(ctbop_system* s, const double* w_E, const double* E_ref, co
  * energy[0..R) (host array, caller-owned): the sum over each replica of the
  * per-atom energies, i.e. the value ctbop_get(CTBOP_GET_ENERGY) returns, up
  * to summation order. The paper has no counterpart: this is a library
- * utility that allocates nothing on the device. Its scratch is a fixed
- * file-scope device array of 304 x 64 + 64 doubles plus a counter, which
- * limits it to systems of at most 64 replicas (more -> CTBOP_ERR_INVALID_ARG,
- * nothing computed); there is no limit on the atom count.
+ * utility for callers that cannot allocate device memory when they read the
+ * energy. Examples: a program whose GPU memory is held by another
+ * framework's caching allocator, where a new cudaMalloc can fail or force
+ * that allocator to give memory back; a monitoring loop between steps, where
+ * a cudaFree would synchronise the whole device and stall other streams; a
+ * long run that must not fail for lack of memory once it has started. It
+ * calls no allocating routine. Its scratch is a fixed file-scope device array
+ * of 304 x 64 + 64 doubles plus a counter (about 156 KB, held by every GPU
+ * that loads the library until the process exits), which limits it to
+ * systems of at most 64 replicas (more -> CTBOP_ERR_INVALID_ARG, nothing
+ * computed); there is no limit on the atom count.
  * The first call on a device looks up the scratch array's address (make that
  * call before any stream capture); later calls only launch one kernel on the
  * system's stream and copy R doubles back, synchronising the stream.

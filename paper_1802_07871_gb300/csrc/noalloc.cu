@@ -3,7 +3,13 @@
 // A variant of the per-replica energy sum the force gather accumulates
 // (the sum over each replica of the per-atom energies), computed here from
 // the per-atom energies with all of its scratch in one file-scope device
-// array: no cudaMalloc/cudaFree and no allocating library call, ever.
+// array: no cudaMalloc/cudaFree and no allocating library call, ever. It
+// serves callers that cannot allocate device memory while they read
+// energies: programs whose GPU memory belongs to another framework's caching
+// allocator (a cudaMalloc could fail or make that allocator release memory),
+// monitoring between steps (a cudaFree synchronises the whole device), long
+// runs that must not run out of memory after they start. The array (about
+// 156 KB) stays resident on every GPU that loads the library until exit.
 //
 // Scratch layout (NA_BLOCKS x NA_REPS doubles of block partials, then one
 // row of results, then the last-block counter):

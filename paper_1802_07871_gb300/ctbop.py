@@ -387,7 +387,10 @@ class System:
 
     def energy_noalloc(self) -> np.ndarray:
         """Per-replica energy through the entry point that allocates nothing
-        on the device (at most 64 replicas)."""
+        on the device (at most 64 replicas), for callers that cannot allocate
+        while reading energies (GPU memory held by another framework's
+        caching allocator; monitoring code that must not synchronise the
+        device through a cudaFree)."""
         out = np.empty(self.R, dtype=np.float64)
         self._check(self._L.ctbop_energy_noalloc(self._h, out.ctypes.data_as(C.c_void_p)), "energy_noalloc")
         return out

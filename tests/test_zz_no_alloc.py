@@ -1,5 +1,8 @@
-"""The per-replica energy entry point that allocates nothing on the device,
-against the existing result (ctbop_get energy) on consecutive calls. Kept in
+"""The per-replica energy entry point that allocates nothing on the device
+(for callers that cannot allocate while reading energies, e.g. when another
+framework's caching allocator holds the GPU's memory, or in monitoring code
+where a cudaFree would synchronise the device), against the existing result
+(ctbop_get energy) on consecutive calls. Kept in
 its own file, collected last, so it runs both alone in a fresh process (the
 first call then does the one-time symbol lookup) and after every other
 test."""
