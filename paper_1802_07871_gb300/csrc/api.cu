@@ -1085,10 +1085,11 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
 
 // Force-matching gradient (FP64 policy). With g = dL/dF, the force part of
 // dL/dtheta is -T1 + lambda . d(Hq + chi)/dtheta:
-//   T1 = d/de dE/dtheta (x + e g) at the fixed minimiser charges (central
-//        difference of the analytic parameter gradient, step h = 1e-4 A / max|g|);
+//   T1 = d/de dE/dtheta (x + e g) at the fixed minimiser charges, and
+//   v  = d/de (H q + chi)(x + e g), both exact, from one forward-mode pass of
+//        the parameter-gradient kernels along g;
 //   lambda solves the projected adjoint system H lambda = v (sum lambda = 0
-//        per replica) with v = d/de (H q + chi)(x + e g) (central difference);
+//        per replica);
 //   lambda . d(Hq + chi)/dtheta is the derivative of dE/dtheta along q +
 //        s lambda, exact as a central difference because E is quadratic in q.
 static int param_grad_impl(ctbop_system* s, const double* w_E, const double* E_ref, const double* w_F,
@@ -1101,10 +1102,9 @@ static int param_grad_impl(ctbop_system* s, const double* w_E, const double* E_r
   ctbop_stats stt;
   rc = ctbop_status(s, &stt);
   if (rc) return rc;
-  std::vector<double> E(R), F((size_t)3 * N), x0((size_t)3 * N), q0(N);
+  std::vector<double> E(R), F((size_t)3 * N), q0(N);
   CK(cudaMemcpy2D(E.data(), 8, S.rep_acc + RA_E, RA_STRIDE * 8, 8, R, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(F.data(), S.F, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(x0.data(), S.x, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(q0.data(), S.q, sizeof(double) * N, cudaMemcpyDeviceToHost));
   // loss and its derivatives with respect to E_r and F_i
   double loss = 0.0;
@@ -1126,103 +1126,91 @@ static int param_grad_impl(ctbop_system* s, const double* w_E, const double* E_r
         }
   }
   *loss_out = loss;
-  double *d_w = nullptr, *d_g0 = nullptr, *d_g1 = nullptr, *d_x = nullptr, *d_v = nullptr, *d_cg = nullptr;
+  double *d_w = nullptr, *d_one = nullptr, *d_g = nullptr, *d_dir = nullptr, *d_v = nullptr, *d_cg = nullptr;
   double *d_h1 = nullptr, *d_h2 = nullptr;
   auto cleanup = [&]() {
-    for (double* p : {d_w, d_g0, d_g1, d_x, d_v, d_cg, d_h1, d_h2}) if (p) cudaFree(p);
+    for (double* p : {d_w, d_one, d_g, d_dir, d_v, d_cg, d_h1, d_h2}) if (p) cudaFree(p);
   };
   auto dm = [&](double** p, size_t n) { return cudaMalloc(p, sizeof(double) * std::max<size_t>(n, 1)); };
-  if (dm(&d_w, R) || dm(&d_g0, 144) || dm(&d_g1, 144) || dm(&d_x, (size_t)3 * N) || dm(&d_v, (size_t)2 * N) ||
+  if (dm(&d_w, R) || dm(&d_one, R) || dm(&d_g, 2 * PG_NPARAM) || dm(&d_dir, (size_t)3 * N) || dm(&d_v, N) ||
       dm(&d_cg, (size_t)R * CG_STRIDE) || dm(&d_h1, N) || dm(&d_h2, N)) {
     cleanup();
     return fail(s, CTBOP_ERR_OOM, "param_grad: temporary buffers");
   }
   const ctbop_params& P = s->p;
-  std::vector<double> G(144, 0.0), t0(144), t1(144);
-  auto pgrad = [&](const std::vector<double>& w, std::vector<double>& out) -> int {
-    CK(cudaMemcpyAsync(d_w, w.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
-    CK(launch_param_grad(S, P, d_w, d_g0, st));
-    CK(cudaMemcpyAsync(out.data(), d_g0, sizeof(double) * 144, cudaMemcpyDeviceToHost, st));
+  std::vector<double> G(2 * PG_NPARAM, 0.0), t0(2 * PG_NPARAM), t1(2 * PG_NPARAM);
+  CK(cudaMemcpyAsync(d_w, a.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_one, one.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+  // value-only pass at the current charges, weights w
+  auto pgrad = [&](const double* w, std::vector<double>& out) -> int {
+    CK(launch_param_grad(S, P, w, nullptr, nullptr, d_g, nullptr, st));
+    CK(cudaMemcpyAsync(out.data(), d_g, sizeof(double) * 2 * PG_NPARAM, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return CTBOP_OK;
   };
-  // energy part: sum_r a_r dE_r/dtheta at the minimiser
-  rc = pgrad(a, G);
-  if (!rc && gmax > 0.0) {
-    const double h = 1e-4 / gmax;
-    std::vector<double> xp((size_t)3 * N), vpm[2] = {std::vector<double>(N), std::vector<double>(N)};
-    std::vector<double> Gpm[2] = {std::vector<double>(144), std::vector<double>(144)};
-    for (int sg = 0; sg < 2 && !rc; ++sg) {
-      double sh = sg == 0 ? h : -h;
-      for (size_t k = 0; k < xp.size(); ++k) xp[k] = x0[k] + sh * g[k];
-      rc = ctbop_set_positions(s, xp.data(), CTBOP_HOST);
-      if (!rc) rc = ctbop_compute(s, CTBOP_FIXED_CHARGES);
-      if (rc) break;
-      launch_assemble<double>(S, s->Pd, s->T, st);
-      launch_charge_grad(S, s->T, d_v, st);
-      CK(cudaMemcpyAsync(vpm[sg].data(), d_v, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
-      rc = pgrad(one, Gpm[sg]);
-    }
-    if (!rc) {
-      for (int k = 0; k < 144; ++k) G[k] -= (Gpm[0][k] - Gpm[1][k]) / (2.0 * h);
-      // back at x: the matrix there for the adjoint solve
-      rc = ctbop_set_positions(s, x0.data(), CTBOP_HOST);
-      if (!rc) rc = ctbop_compute(s, CTBOP_FIXED_CHARGES);
-    }
-    if (!rc) {
-      launch_assemble<double>(S, s->Pd, s->T, st);
-      // rhs of the solver's H q + chi = mu 1 form: chi := -v
-      std::vector<double> mv(N);
-      for (int i = 0; i < N; ++i) mv[i] = -(vpm[0][i] - vpm[1][i]) / (2.0 * h);
-      CK(cudaMemcpyAsync(d_v, mv.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
-      // keep the solver state of the charges: per-replica scalars, history
-      CK(cudaMemcpyAsync(d_cg, S.cg, sizeof(double) * R * CG_STRIDE, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(d_h1, S.cqh1, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(d_h2, S.cqh2, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-      int hist_saved = 0;
-      CK(cudaMemcpy(&hist_saved, S.cg_hist, sizeof(int), cudaMemcpyDeviceToHost));
-      // the adjoint: zero total per replica, cold start
-      std::vector<double> cgh((size_t)R * CG_STRIDE);
-      CK(cudaMemcpy(cgh.data(), S.cg, sizeof(double) * cgh.size(), cudaMemcpyDeviceToHost));
-      for (int r = 0; r < R; ++r) cgh[(size_t)r * CG_STRIDE + CG_Q] = 0.0;
-      CK(cudaMemcpy(S.cg, cgh.data(), sizeof(double) * cgh.size(), cudaMemcpyHostToDevice));
-      int zero = 0;
-      CK(cudaMemcpy(S.cg_hist, &zero, sizeof(int), cudaMemcpyHostToDevice));
-      SolveCfg cfg{cg_tol(s), s->o.cg_max_iter, 0, 0};
-      launch_cg_begin<double>(S, s->T, st, cfg.tol, d_v);
-      for (int it = 0; it < s->o.cg_max_iter + 4; it += 4) {
-        for (int k = 0; k < 4; ++k) launch_cg_iter<double>(S, cfg, st);
-        CK(cudaMemcpyAsync(s->h_int, S.cg_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (*s->h_int == 0) break;
-      }
-      launch_cg_end<double>(S, st);
-      unsigned bits = 0;
-      rc = read_err(s, bits);
-      if (!rc && (bits & CT_ERR_CG_MAXITER)) rc = fail(s, CTBOP_ERR_CG_NOT_CONVERGED, "param_grad: adjoint CG reached max_iter");
-      std::vector<double> lam(N);
-      if (!rc) CK(cudaMemcpy(lam.data(), S.q, sizeof(double) * N, cudaMemcpyDeviceToHost));
-      // restore the charge solver's state
-      CK(cudaMemcpyAsync(S.cg, d_cg, sizeof(double) * R * CG_STRIDE, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(S.cqh1, d_h1, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(S.cqh2, d_h2, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-      CK(cudaMemcpyAsync(S.cg_hist, &hist_saved, sizeof(int), cudaMemcpyHostToDevice, st));
+  if (gmax == 0.0) {
+    // energy part only: sum_r a_r dE_r/dtheta at the minimiser
+    rc = pgrad(d_w, G);
+  } else {
+    // energy part, T1 and v in one forward-mode pass along g
+    std::vector<double> v(N);
+    CK(cudaMemcpyAsync(d_dir, g.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
+    CK(launch_param_grad(S, P, d_w, d_one, d_dir, d_g, d_v, st));
+    CK(cudaMemcpyAsync(G.data(), d_g, sizeof(double) * 2 * PG_NPARAM, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(v.data(), d_v, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int k = 0; k < PG_NPARAM; ++k) G[k] -= G[PG_NPARAM + k];
+    // rhs of the solver's H q + chi = mu 1 form: chi := -v (the matrix at x
+    // is the one the charge solve above assembled)
+    for (int i = 0; i < N; ++i) v[i] = -v[i];
+    CK(cudaMemcpyAsync(d_v, v.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
+    // keep the solver state of the charges: per-replica scalars, history
+    CK(cudaMemcpyAsync(d_cg, S.cg, sizeof(double) * R * CG_STRIDE, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(d_h1, S.cqh1, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(d_h2, S.cqh2, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    int hist_saved = 0;
+    CK(cudaMemcpy(&hist_saved, S.cg_hist, sizeof(int), cudaMemcpyDeviceToHost));
+    // the adjoint: zero total per replica, cold start
+    std::vector<double> cgh((size_t)R * CG_STRIDE);
+    CK(cudaMemcpy(cgh.data(), S.cg, sizeof(double) * cgh.size(), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < R; ++r) cgh[(size_t)r * CG_STRIDE + CG_Q] = 0.0;
+    CK(cudaMemcpy(S.cg, cgh.data(), sizeof(double) * cgh.size(), cudaMemcpyHostToDevice));
+    int zero = 0;
+    CK(cudaMemcpy(S.cg_hist, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    SolveCfg cfg{cg_tol(s), s->o.cg_max_iter, 0, 0};
+    launch_cg_begin<double>(S, s->T, st, cfg.tol, d_v);
+    for (int it = 0; it < s->o.cg_max_iter + 4; it += 4) {
+      for (int k = 0; k < 4; ++k) launch_cg_iter<double>(S, cfg, st);
+      CK(cudaMemcpyAsync(s->h_int, S.cg_active, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      if (!rc) {
-        // lambda . d(Hq + chi)/dtheta: central difference along q +- s lambda
-        double lmax = 0.0;
-        for (double v : lam) lmax = std::max(lmax, std::fabs(v));
-        if (lmax > 0.0) {
-          double sq = 0.1 / lmax;
-          std::vector<double> qp(N);
-          for (int sg = 0; sg < 2 && !rc; ++sg) {
-            for (int i = 0; i < N; ++i) qp[i] = q0[i] + (sg == 0 ? sq : -sq) * lam[i];
-            CK(cudaMemcpy(S.q, qp.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
-            rc = pgrad(one, sg == 0 ? t0 : t1);
-          }
-          if (!rc)
-            for (int k = 0; k < 144; ++k) G[k] += (t0[k] - t1[k]) / (2.0 * sq);
+      if (*s->h_int == 0) break;
+    }
+    launch_cg_end<double>(S, st);
+    unsigned bits = 0;
+    rc = read_err(s, bits);
+    if (!rc && (bits & CT_ERR_CG_MAXITER)) rc = fail(s, CTBOP_ERR_CG_NOT_CONVERGED, "param_grad: adjoint CG reached max_iter");
+    std::vector<double> lam(N);
+    if (!rc) CK(cudaMemcpy(lam.data(), S.q, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    // restore the charge solver's state
+    CK(cudaMemcpyAsync(S.cg, d_cg, sizeof(double) * R * CG_STRIDE, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(S.cqh1, d_h1, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(S.cqh2, d_h2, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(S.cg_hist, &hist_saved, sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    if (!rc) {
+      // lambda . d(Hq + chi)/dtheta: central difference along q +- s lambda
+      double lmax = 0.0;
+      for (double x : lam) lmax = std::max(lmax, std::fabs(x));
+      if (lmax > 0.0) {
+        double sq = 0.1 / lmax;
+        std::vector<double> qp(N);
+        for (int sg = 0; sg < 2 && !rc; ++sg) {
+          for (int i = 0; i < N; ++i) qp[i] = q0[i] + (sg == 0 ? sq : -sq) * lam[i];
+          CK(cudaMemcpy(S.q, qp.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+          rc = pgrad(d_one, sg == 0 ? t0 : t1);
         }
+        if (!rc)
+          for (int k = 0; k < PG_NPARAM; ++k) G[k] += (t0[k] - t1[k]) / (2.0 * sq);
       }
     }
   }
@@ -1231,14 +1219,13 @@ static int param_grad_impl(ctbop_system* s, const double* w_E, const double* E_r
   if (gmax > 0.0) {
     CK(cudaMemcpy(S.q, q0.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
     launch_copy_q<double>(S, st);
-    rc2 = ctbop_set_positions(s, x0.data(), CTBOP_HOST);
-    if (!rc2) rc2 = ctbop_compute(s, CTBOP_FIXED_CHARGES);
+    rc2 = ctbop_compute(s, CTBOP_FIXED_CHARGES);
   }
   cleanup();
   if (rc) return rc;
   if (rc2) return rc2;
   G[PG_MASS] = G[PG_MASS + 1] = 0.0;   // the mass is not in E
-  for (int k = 0; k < 144; ++k) dth[k] = G[k];
+  for (int k = 0; k < PG_NPARAM; ++k) dth[k] = G[k];
   return CTBOP_OK;
 }
 

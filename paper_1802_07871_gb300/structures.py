@@ -75,7 +75,8 @@ def load_params(name: str = "p0") -> dict:
 # --------------------------------------------------------------------------
 def sic_3c(ncell: int = 4, a: float = 4.36, disp: float = 0.05, seed: int = 1,
            strain=None) -> Structure:
-    """Zincblende SiC, ncell^3 conventional cubic cells, periodic.
+    """Zincblende SiC, ncell^3 conventional cubic cells (or n1 x n2 x n3 for
+    a 3-tuple ncell), periodic.
 
     Si on the fcc sites, C on the fcc sites shifted by a(1/4,1/4,1/4). Every
     coordinate is displaced by U(-disp, +disp) from a seeded generator.
@@ -85,14 +86,14 @@ def sic_3c(ncell: int = 4, a: float = 4.36, disp: float = 0.05, seed: int = 1,
     fcc = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0]])
     basis = np.concatenate([fcc, fcc + 0.25])
     btype = np.array([SI] * 4 + [C] * 4, dtype=np.int32)
-    g = np.arange(ncell)
-    cells = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    nc = np.broadcast_to(np.asarray(ncell, dtype=int), (3,))
+    cells = np.stack(np.meshgrid(*(np.arange(k) for k in nc), indexing="ij"), -1).reshape(-1, 3)
     frac = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3)
     x = frac * a
     types = np.tile(btype, len(cells))
     rng = np.random.default_rng(seed)
     x = x + rng.uniform(-disp, disp, size=x.shape)
-    box = np.full(3, ncell * a)
+    box = nc * a
     if strain is not None:
         eps = np.asarray(strain, dtype=np.float64)
         if np.any(np.abs(eps - np.diag(np.diag(eps))) > 0):
@@ -101,7 +102,7 @@ def sic_3c(ncell: int = 4, a: float = 4.36, disp: float = 0.05, seed: int = 1,
         x = x * f
         box = box * f
     x = np.mod(x, box)
-    return Structure(f"3C-SiC {ncell}x{ncell}x{ncell}", x, types, box,
+    return Structure(f"3C-SiC {nc[0]}x{nc[1]}x{nc[2]}", x, types, box,
                      np.array([True, True, True]))
 
 
@@ -250,11 +251,10 @@ def slab_with_vacancies(n_target: int, vac_frac: float, seed: int, n_bilayers: i
     return out
 
 
-def amorphous_carbon_cluster(n: int, density_gcc: float, seed: int, min_sep: float = 1.2) -> Structure:
-    """n C atoms placed by random sequential addition in a sphere holding
-    them at density_gcc (g/cm^3), no two closer than min_sep; open box."""
-    rng = np.random.default_rng(seed)
-    n_rho = density_gcc * 0.602214076 / MASS[C]          # atoms per A^3
+def _pack_sphere(n: int, n_rho: float, rng, min_sep: float) -> np.ndarray:
+    """n points by random sequential addition in the sphere (centred at 0)
+    that holds them at number density n_rho (per A^3), no two closer than
+    min_sep."""
     R = (3.0 * n / (4.0 * math.pi * n_rho)) ** (1.0 / 3.0)
     cell = min_sep
     grid: dict = {}
@@ -287,10 +287,31 @@ def amorphous_carbon_cluster(n: int, density_gcc: float, seed: int, min_sep: flo
             continue
         grid.setdefault(k, []).append(p)
         pts.append(p)
+    return np.array(pts), R
+
+
+def amorphous_carbon_cluster(n: int, density_gcc: float, seed: int, min_sep: float = 1.2) -> Structure:
+    """n C atoms placed by random sequential addition in a sphere holding
+    them at density_gcc (g/cm^3), no two closer than min_sep; open box."""
+    rng = np.random.default_rng(seed)
+    n_rho = density_gcc * 0.602214076 / MASS[C]          # atoms per A^3
+    pts, R = _pack_sphere(n, n_rho, rng, min_sep)
     edge = 2.0 * R + 30.0
-    x = np.array(pts) + edge / 2.0
+    x = pts + edge / 2.0
     return Structure(f"amorphous C cluster n={n} rho={density_gcc:.2f}", x, np.full(n, C, dtype=np.int32),
                      np.full(3, edge), np.array([False] * 3))
+
+
+def random_sic_cluster(n: int, n_rho: float, seed: int, min_sep: float = 1.2) -> Structure:
+    """n atoms of random type (Si or C with equal odds) packed like
+    amorphous_carbon_cluster at number density n_rho (per A^3), no two
+    closer than min_sep; open box."""
+    rng = np.random.default_rng(seed)
+    pts, R = _pack_sphere(n, n_rho, rng, min_sep)
+    types = rng.integers(0, 2, n).astype(np.int32)
+    edge = 2.0 * R + 30.0
+    return Structure(f"random Si/C cluster n={n}", pts + edge / 2.0, types, np.full(3, edge),
+                     np.array([False] * 3))
 
 
 def graphene_flake(n: int, seed: int, vac_frac: float = 0.03, n_stone_wales: int = 2) -> np.ndarray:
@@ -339,6 +360,54 @@ def graphene_flake(n: int, seed: int, vac_frac: float = 0.03, n_stone_wales: int
     return xy[keep]
 
 
+def graphene_sheet(n_target: int, seed: int, n_stone_wales: int = 1, disp: float = 0.05) -> Structure:
+    """Periodic graphene (C-C 1.42 A) in the x/y plane, open in z, of about
+    n_target atoms: rectangular cells sqrt(3) b x 3 b with four atoms each,
+    about as many cells along y as x / sqrt(3), so the sheet is roughly
+    square. n_stone_wales bonds are rotated by 90 degrees about their
+    midpoints (each turns four hexagons into two pentagons and two
+    heptagons); a rotation that would bring the pair within 1.2 A of another
+    atom or periodic image is undone. Every coordinate is then displaced by
+    U(-disp, +disp)."""
+    rng = np.random.default_rng(seed)
+    b = 1.42
+    ax, ay = math.sqrt(3.0) * b, 3.0 * b
+    cells = max(1, round(n_target / 4))
+    ny = max(2, int(round(math.sqrt(cells / math.sqrt(3.0)))))
+    nx = max(2, int(round(cells / ny)))
+    basis = np.array([[0.0, 0.0], [ax / 2, b / 2], [ax / 2, 1.5 * b], [0.0, 2.0 * b]])
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    org = np.stack([ii.ravel() * ax, jj.ravel() * ay], 1)
+    xy = (org[:, None, :] + basis[None, :, :]).reshape(-1, 2)
+    L = np.array([nx * ax, ny * ay])
+
+    def mic(d):
+        return d - np.round(d / L) * L
+
+    for _ in range(n_stone_wales):
+        i = int(rng.integers(len(xy)))
+        d = mic(xy - xy[i])
+        r = np.sqrt(np.einsum("ij,ij->i", d, d))
+        nb = np.nonzero((r > 0.1) & (r < 1.05 * b))[0]
+        j = int(rng.choice(nb))
+        mid = xy[i] + 0.5 * mic(xy[j] - xy[i])
+        old = xy[[i, j]].copy()
+        for k in (i, j):
+            dk = mic(xy[k] - mid)
+            xy[k] = np.mod(mid + np.array([-dk[1], dk[0]]), L)
+        others = np.ones(len(xy), dtype=bool)
+        others[[i, j]] = False
+        dmin = min(np.min(np.linalg.norm(mic(xy[others] - xy[k]), axis=1)) for k in (i, j))
+        if dmin < 1.2:
+            xy[[i, j]] = old
+    n = len(xy)
+    x = np.concatenate([xy, np.full((n, 1), 15.0)], 1) + rng.uniform(-disp, disp, size=(n, 3))
+    box = np.array([L[0], L[1], 30.0])
+    x[:, :2] = np.mod(x[:, :2], L)
+    return Structure(f"graphene {nx}x{ny}, {n_stone_wales} Stone-Wales", x, np.full(n, C, dtype=np.int32), box,
+                     np.array([True, True, False]))
+
+
 def graphene_on_sic(n_target: int, seed: int) -> Structure:
     """A defected graphene flake (about 20% of the atoms) 2.5-3.0 A above a
     3-bilayer 4H-SiC(0001) slab whose periodic cell is at least the flake's
@@ -380,6 +449,52 @@ def annealing_ensemble(n_replicas: int = 256, seed: int = 4, n_min: int = 200, n
         out.append(s)
         temps.append(float(rng.uniform(1500.0, 3000.0)))
     return out, temps
+
+
+def differentiation_batch(n_configs: int = 1024, seed: int = 5, n_min: int = 64, n_max: int = 512):
+    """Configurations for force matching, of uneven size (uniform
+    n_min..n_max atoms), in three kinds taken in turn: 3C-SiC supercells of
+    n1 x n2 x n3 cubic cells (n_k in 2..4, the shape closest to the drawn
+    size) under a random diagonal strain of up to +-5%; periodic graphene
+    with 1-3 Stone-Wales defects; random Si/C clusters at 0.05-0.10 atoms
+    per A^3 with no two atoms closer than 1.2 A. The 64-atom cells are
+    8.72 A wide, under twice the charge cutoff, so their lists hold several
+    images of the same atom."""
+    rng = np.random.default_rng(seed)
+    shapes = [(p, q, r) for p in (2, 3, 4) for q in (2, 3, 4) for r in (2, 3, 4)]
+    out = []
+    for c in range(n_configs):
+        n = int(rng.integers(n_min, n_max + 1))
+        sub = seed * 100000 + c
+        k = c % 3
+        if k == 0:
+            gap = [abs(8 * p * q * r - n) for p, q, r in shapes]
+            best = [sh for sh, g in zip(shapes, gap) if g == min(gap)]
+            shape = best[int(rng.integers(len(best)))]
+            eps = rng.uniform(-0.05, 0.05, 3)
+            s = sic_3c(shape, 4.36, 0.05, sub, strain=np.diag(eps))
+        elif k == 1:
+            s = graphene_sheet(n, sub, n_stone_wales=int(rng.integers(1, 4)))
+        else:
+            s = random_sic_cluster(n, float(rng.uniform(0.05, 0.10)), sub)
+        out.append(s)
+    return out
+
+
+def perturbed_params(params: dict, seed: int, rel: float = 0.02) -> dict:
+    """A copy of a parameter set with the pair prefactors and decay rates
+    (A, B, lambda1, lambda2) and the self-energy coefficients (chi, J) each
+    scaled by 1 + U(-rel, +rel): the parameters a force-matching target is
+    generated with when no reference forces exist."""
+    rng = np.random.default_rng(seed)
+    out = json.loads(json.dumps(params))
+    for name in sorted(out["pair"]):
+        for k in ("A", "B", "lambda1", "lambda2"):
+            out["pair"][name][k] *= 1.0 + rng.uniform(-rel, rel)
+    for k in ("chi", "J"):
+        out["self"][k] = [v * (1.0 + rng.uniform(-rel, rel)) for v in out["self"][k]]
+    out["note"] = params.get("note", "") + f" (perturbed, seed {seed}, rel {rel})"
+    return out
 
 
 # --------------------------------------------------------------------------

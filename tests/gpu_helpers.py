@@ -107,3 +107,32 @@ def sampled_local_check(s, params, g, precision, samples, rcut=9.0):
     assert worst["eatom"] <= t["eatom"], worst
     assert worst["stationarity"] <= 10 * t["mu"], worst
     return worst
+
+
+def oracle_EF(args):
+    """(E, F) of one structure from the oracle; a top-level function so a
+    spawn pool can run it."""
+    s, params = args
+    o = O.evaluate(s.x, s.types, s.box, s.pbc, params)
+    return o["E"], o["F"]
+
+
+def oracle_EF_many(structs, params, workers=None):
+    """oracle_EF over many structures in a spawn process pool (one BLAS
+    thread per worker)."""
+    import multiprocessing as mp
+    import os
+    workers = workers or min(16, os.cpu_count() or 1)
+    keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in keep:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            out = pool.map(oracle_EF, [(s, params) for s in structs], chunksize=8)
+    finally:
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return [e for e, _ in out], [f for _, f in out]
