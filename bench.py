@@ -197,16 +197,17 @@ def run_ensemble(dev, stream, steps=20, warmup=3):
             "precision": "mixed"}
 
 
-def run_param_grad(dev, stream, calls=3, warmup=1):
+def run_param_grad(dev, stream, precision="mixed", calls=3, warmup=1):
     """Secondary measurement: the force-matching gradient on the 1024-config
     differentiation batch (64-512 atoms each: strained 3C-SiC, periodic
     graphene with Stone-Wales defects, random Si/C clusters). Targets E_ref,
     F_ref are the library's own FP64 energies and forces under a perturbed
     parameter set, made before the timed region (workload input, not a
     parity value). One call = loss + dL/dtheta for all 144 parameters over
-    the whole batch: evaluation with the charge solve, the two displaced
-    evaluations, the adjoint solve and the parameter-gradient passes. Timed
-    on the host clock, since the call synchronises with its stream."""
+    the whole batch: evaluation with the charge solve, the forward-mode pass
+    along dL/dF, the adjoint solve and the forward-mode pass along the
+    adjoint charges, in the given precision policy. Timed on the host clock,
+    since the call synchronises with its stream."""
     import torch
     from paper_1802_07871_gb300 import ctbop
     from paper_1802_07871_gb300 import structures as st
@@ -214,12 +215,15 @@ def run_param_grad(dev, stream, calls=3, warmup=1):
     structs = st.differentiation_batch(1024, seed=5)
     n = sum(s.n for s in structs)
     R = len(structs)
-    sysm = ctbop.System(st.perturbed_params(P0, 55), precision="fp64", device=dev.index or 0)
+    ref = ctbop.System(st.perturbed_params(P0, 55), precision="fp64", device=dev.index or 0)
+    ref.set_stream(stream.cuda_stream)
+    ref.load_replicas(structs)
+    ref.compute()
+    E_ref, F_ref = ref.get("energy"), ref.get("forces")
+    ref.close()
+    sysm = ctbop.System(P0, precision=precision, device=dev.index or 0)
     sysm.set_stream(stream.cuda_stream)
     sysm.load_replicas(structs)
-    sysm.compute()
-    E_ref, F_ref = sysm.get("energy"), sysm.get("forces")
-    sysm.set_params(P0)
     nr = np.array([s.n for s in structs], dtype=np.float64)
     loss = dict(w_E=1.0 / nr ** 2, E_ref=E_ref, w_F=1.0 / (3.0 * nr), F_ref=F_ref)
     for _ in range(warmup):
@@ -236,7 +240,7 @@ def run_param_grad(dev, stream, calls=3, warmup=1):
     return {"workload": "differentiation batch: 1024 configurations of 64-512 atoms (3C-SiC under random "
                         "+-5% diagonal strain, periodic graphene with 1-3 Stone-Wales defects, random Si/C "
                         "clusters at 0.05-0.10 per A^3), force-matching loss on E and F",
-            "n_configs": R, "n_atoms": n, "calls": calls, "warmup": warmup, "precision": "fp64",
+            "n_configs": R, "n_atoms": n, "calls": calls, "warmup": warmup, "precision": precision,
             "ms_per_call": sec * 1e3, "value": n / sec, "unit": "atom-gradients/s",
             "configs_per_s": R / sec, "cg_iters_per_call": (it1 - it0) / calls, "loss": L}
 
@@ -379,7 +383,8 @@ def run_ours(a):
     if world == 1 and not a.no_ensemble:
         line["ensemble"] = run_ensemble(dev, stream)
     if world == 1 and not a.no_grad:
-        line["param_grad"] = run_param_grad(dev, stream)
+        line["param_grad"] = run_param_grad(dev, stream, "mixed")
+        line["param_grad"]["fp64"] = run_param_grad(dev, stream, "fp64")
     if world == 1 and not a.no_cpu:
         line["cpu_baseline"] = cpu_baseline(budget_s=20.0)
     print(json.dumps(line), flush=True)

@@ -145,7 +145,11 @@ int ctbop_destroy(ctbop_system* s);
 /* Message for the last error on s (empty string if none; never null). */
 const char* ctbop_last_error(const ctbop_system* s);
 
-/* Order all later work on `cuda_stream` (a cudaStream_t; null = legacy stream). */
+/* Order all later work on `cuda_stream` (a cudaStream_t; null = the
+ * library's own stream, which synchronises with the legacy stream). Work
+ * already enqueued on the previous stream is waited for first. Every
+ * transfer the library makes, host copies included, is ordered on this
+ * stream, so a non-blocking stream is safe. */
 int ctbop_set_stream(ctbop_system* s, void* cuda_stream);
 
 /* Replica layout: n_replicas >= 1, atom_offsets host int64[n_replicas+1],
@@ -219,8 +223,8 @@ int ctbop_set_thermostat(ctbop_system* s, const double* T0, const double* tau);
 int ctbop_set_params(ctbop_system* s, const ctbop_params* p);
 
 /* Force-matching loss and its gradient with respect to every parameter
- * (the spec differentiation pattern; the paper fits its parameters to
- * energies, forces and charges, Sec. 2, but prints no fitting method).
+ * (the paper fits its parameters to energies, forces and charges, Sec. 2,
+ * but prints no fitting method).
  *   loss = sum_r w_E[r] (E_r - E_ref[r])^2 + sum_r w_F[r] sum_{i in r} |F_i - F_ref_i|^2
  * at the charge minimiser of the current positions. dtheta receives dloss/d
  * of every field of ctbop_params, in that struct's layout (host,
@@ -230,12 +234,12 @@ int ctbop_set_params(ctbop_system* s, const ctbop_params* p);
  * w_E, E_ref: [R] host or NULL (no energy term); w_F: [R] host, F_ref:
  * [N,3] host, or NULL (no force term). The energy part is the analytic
  * partial derivative at fixed charges (exact at the minimiser). The force
- * part adds a directional second derivative along dL/dF (central difference
- * of the analytic gradient, step 1e-4 A over the largest component) and the
- * charge response through one adjoint CG solve. Leaves the system at its
+ * part adds the derivative of that gradient along dL/dF and the charge
+ * response through one adjoint CG solve; both directional derivatives are
+ * exact (forward mode). Arithmetic follows the system's policy: FP64, or FP32
+ * terms with FP64 sums under CTBOP_PREC_MIXED. Leaves the system at its
  * positions with the minimiser charges, energies and forces.
- * FP64 policy only (CTBOP_ERR_INVALID_ARG otherwise); CG_NOT_CONVERGED if the
- * charge or adjoint solve does not converge. */
+ * CG_NOT_CONVERGED if the charge or adjoint solve does not converge. */
 int ctbop_param_grad(ctbop_system* s, const double* w_E, const double* E_ref, const double* w_F,
                      const double* F_ref, double* loss, ctbop_params* dtheta);
 

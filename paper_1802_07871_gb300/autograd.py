@@ -6,7 +6,8 @@ derivative is computed by the library's kernels).
 * ForceMatchingLoss: the force-matching loss of a fixed batch as a function
   of the 144 parameters (field order of ctbop_params); the backward is
   ctbop_param_grad (analytic parameter derivatives, charge response by an
-  adjoint solve). FP64 policy.
+  adjoint solve), in the system's precision policy (FP64, or FP32 terms with
+  FP64 sums).
 """
 import numpy as np
 import torch

@@ -164,6 +164,16 @@ static bool params_valid(const ctbop_params* p, std::string& why) {
 }
 
 // ------------------------------------------------------------- helpers
+// Stream-ordered transfers. The library's kernels run on s->stream, which
+// may be a non-blocking stream (the usual kind from a framework's stream
+// pool); the legacy default stream, where a plain cudaMemcpy or cudaMemset
+// runs, is not ordered with such a stream in either direction.
+static cudaError_t sync_copy(ctbop_system* s, void* dst, const void* src, size_t n, cudaMemcpyKind kind) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, n, kind, s->stream);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(s->stream);
+}
+static cudaError_t zero_async(ctbop_system* s, void* p, size_t n) { return cudaMemsetAsync(p, 0, n, s->stream); }
+
 static void destroy_graphs(ctbop_system* s) {
   if (s->g_eval) cudaGraphExecDestroy(s->g_eval);
   if (s->g_step) cudaGraphExecDestroy(s->g_step);
@@ -211,14 +221,14 @@ static int setup_reps(ctbop_system* s) {
     destroy_graphs(s);
   }
   s->S.ncells = cells;
-  CK(cudaMemcpy(s->S.reps, info.data(), sizeof(RepInfo) * s->R, cudaMemcpyHostToDevice));
+  CK(sync_copy(s, s->S.reps, info.data(), sizeof(RepInfo) * s->R, cudaMemcpyHostToDevice));
   {
     std::vector<int> crep(cells);
     for (int r = 0; r < s->R; ++r) {
       int end = r + 1 < s->R ? info[r + 1].cell_off : cells;
       for (int c = info[r].cell_off; c < end; ++c) crep[c] = r;
     }
-    CK(cudaMemcpy(s->S.cell_rep, crep.data(), sizeof(int) * cells, cudaMemcpyHostToDevice));
+    CK(sync_copy(s, s->S.cell_rep, crep.data(), sizeof(int) * cells, cudaMemcpyHostToDevice));
   }
   // per-replica CG constants
   std::vector<double> cg((size_t)s->R * CG_STRIDE, 0.0);
@@ -226,7 +236,7 @@ static int setup_reps(ctbop_system* s) {
     cg[(size_t)r * CG_STRIDE + CG_Q] = s->Q[r];
     cg[(size_t)r * CG_STRIDE + CG_NAT] = (double)(s->off[r + 1] - s->off[r]);
   }
-  CK(cudaMemcpy(s->S.cg, cg.data(), sizeof(double) * cg.size(), cudaMemcpyHostToDevice));
+  CK(sync_copy(s, s->S.cg, cg.data(), sizeof(double) * cg.size(), cudaMemcpyHostToDevice));
   s->reps_dirty = false;
   return CTBOP_OK;
 }
@@ -269,26 +279,26 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->atom_buf, &S.cqh2, (size_t)N));
   CK(dalloc(s->atom_buf, &S.ncov, (size_t)N));
   CK(dalloc(s->atom_buf, &S.nall, (size_t)N));
-  CK(cudaMemset(S.v, 0, sizeof(double) * 3 * (size_t)N));
-  CK(cudaMemset(S.F, 0, sizeof(double) * 3 * (size_t)N));
-  CK(cudaMemset(S.q, 0, sizeof(double) * (size_t)N));
-  CK(cudaMemset(S.frozen, 0, (size_t)N));
-  CK(cudaMemset(S.cqh1, 0, sizeof(double) * (size_t)N));
-  CK(cudaMemset(S.cqh2, 0, sizeof(double) * (size_t)N));
-  CK(cudaMemset(S.cp, 0, (size_t)N * rs));
-  CK(cudaMemset(S.cs, 0, (size_t)N * rs));
-  CK(cudaMemset(S.qr, 0, (size_t)N * rs));
+  CK(zero_async(s, S.v, sizeof(double) * 3 * (size_t)N));
+  CK(zero_async(s, S.F, sizeof(double) * 3 * (size_t)N));
+  CK(zero_async(s, S.q, sizeof(double) * (size_t)N));
+  CK(zero_async(s, S.frozen, (size_t)N));
+  CK(zero_async(s, S.cqh1, sizeof(double) * (size_t)N));
+  CK(zero_async(s, S.cqh2, sizeof(double) * (size_t)N));
+  CK(zero_async(s, S.cp, (size_t)N * rs));
+  CK(zero_async(s, S.cs, (size_t)N * rs));
+  CK(zero_async(s, S.qr, (size_t)N * rs));
   // replica ids
   std::vector<int> rep(N);
   for (int r = 0; r < s->R; ++r)
     for (int64_t i = s->off[r]; i < s->off[r + 1]; ++i) rep[i] = r;
-  CK(cudaMemcpy(S.rep, rep.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
+  CK(sync_copy(s, S.rep, rep.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
   // per-replica and control
   CK(dalloc(s->rep_buf, &S.reps, (size_t)s->R));
   CK(dalloc(s->rep_buf, &S.rep_acc, (size_t)s->R * RA_STRIDE));
   CK(dalloc(s->rep_buf, &S.cg, (size_t)s->R * CG_STRIDE));
   CK(dalloc(s->rep_buf, &S.nh, (size_t)s->R * NH_STRIDE));
-  CK(cudaMemset(S.nh, 0, sizeof(double) * s->R * NH_STRIDE));
+  CK(zero_async(s, S.nh, sizeof(double) * s->R * NH_STRIDE));
   s->nvt = false;
   CK(dalloc(s->rep_buf, &S.cg_rmax, (size_t)s->R * 6));
   CK(dalloc(s->rep_buf, &S.cg_conv, (size_t)s->R));
@@ -298,21 +308,21 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->rep_buf, &S.rebuild_count, 1));
   CK(dalloc(s->rep_buf, &S.maxcnt, 3));
   CK(dalloc(s->rep_buf, &S.stiff_n, 1));
-  CK(cudaMemset(S.stiff_n, 0, sizeof(int)));
+  CK(zero_async(s, S.stiff_n, sizeof(int)));
   CK(dalloc(s->rep_buf, &S.err, 1));
   CK(dalloc(s->rep_buf, &S.cg_it, 1));
   CK(dalloc(s->rep_buf, &S.cg_blocks, 3));
   CK(dalloc(s->rep_buf, &S.cg_hist, 1));
   CK(dalloc(s->rep_buf, &S.cg_active, 1));
   CK(dalloc(s->rep_buf, &S.cg_total, 1));
-  CK(cudaMemset(S.rep_acc, 0, sizeof(double) * s->R * RA_STRIDE));
-  CK(cudaMemset(S.rebuild_count, 0, sizeof(long long)));
-  CK(cudaMemset(S.err, 0, sizeof(unsigned)));
-  CK(cudaMemset(S.cg_total, 0, sizeof(long long)));
-  CK(cudaMemset(S.cg_blocks, 0, 3 * sizeof(int)));
-  CK(cudaMemset(S.cg_hist, 0, sizeof(int)));
-  CK(cudaMemset(S.maxcnt, 0, 3 * sizeof(int)));
-  CK(cudaMemset(S.cg_it, 0, sizeof(int)));
+  CK(zero_async(s, S.rep_acc, sizeof(double) * s->R * RA_STRIDE));
+  CK(zero_async(s, S.rebuild_count, sizeof(long long)));
+  CK(zero_async(s, S.err, sizeof(unsigned)));
+  CK(zero_async(s, S.cg_total, sizeof(long long)));
+  CK(zero_async(s, S.cg_blocks, 3 * sizeof(int)));
+  CK(zero_async(s, S.cg_hist, sizeof(int)));
+  CK(zero_async(s, S.maxcnt, 3 * sizeof(int)));
+  CK(zero_async(s, S.cg_it, sizeof(int)));
   s->alloc_N = N;
   s->alloc_R = s->R;
   s->reps_dirty = true;
@@ -350,7 +360,7 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   CK(dalloc(s->list_buf, &gs, (size_t)N * cap_cov * 4 * rs));
   // 8 bytes per entry: (j, FP32 coefficient) pairs, or FP64 coefficients
   CK(dalloc(s->list_buf, &M, ncol * 8));
-  CK(cudaMemset(M, 0, ncol * 8));    // defined values for the first tuning run
+  CK(zero_async(s, M, ncol * 8));    // defined values for the first tuning run
   S.bo = bo;
   S.gslot = gs;
   S.M = M;
@@ -460,7 +470,7 @@ static int run_direct(ctbop_system* s, const PotParams<Rr>& P, bool md, double d
 
 static int read_err(ctbop_system* s, unsigned& bits) {
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemcpy(&bits, s->S.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  CK(sync_copy(s, &bits, s->S.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   return CTBOP_OK;
 }
 
@@ -487,7 +497,7 @@ static int ensure_lists(ctbop_system* s) {
     int rc = read_err(s, bits);
     if (rc) return rc;
     int mc[3];
-    CK(cudaMemcpy(mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost));
+    CK(sync_copy(s, mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost));
     if (bits & CT_ERR_NONFINITE) return fail(s, CTBOP_ERR_NONFINITE, "non-finite position");
     bool over = (bits & (CT_ERR_NBR_OVERFLOW | CT_ERR_COV_OVERFLOW)) != 0;
     if (!over && (bits & CT_ERR_REV_MISSING)) return fail(s, CTBOP_ERR_CUDA, "internal: asymmetric covalent list");
@@ -686,7 +696,7 @@ int ctbop_set_thermostat(ctbop_system* s, const double* T0, const double* tau) {
   DevState& S = s->S;
   const int R = s->R;
   std::vector<uint8_t> fr(S.N);
-  if (S.N) CK(cudaMemcpy(fr.data(), S.frozen, S.N, cudaMemcpyDeviceToHost));
+  if (S.N) CK(sync_copy(s, fr.data(), S.frozen, S.N, cudaMemcpyDeviceToHost));
   std::vector<double> h((size_t)R * NH_STRIDE, 0.0);
   bool any = false;
   for (int r = 0; r < R; ++r) {
@@ -708,7 +718,7 @@ int ctbop_set_thermostat(ctbop_system* s, const double* T0, const double* tau) {
     row[NH_QINV] = 1.0 / Qm;
     any = true;
   }
-  CK(cudaMemcpy(S.nh, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
+  CK(sync_copy(s, S.nh, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
   if (any != s->nvt) destroy_graphs(s);   // the step graph holds the end-of-step update or not
   s->nvt = any;
   return CTBOP_OK;
@@ -766,6 +776,8 @@ int ctbop_set_stream(ctbop_system* s, void* stream) {
   if (!s) return CTBOP_ERR_INVALID_ARG;
   // a graph cannot be captured on the legacy default stream: null selects
   // the library's own stream, which synchronises with the legacy stream
+  cudaSetDevice(s->o.device);
+  CK(cudaStreamSynchronize(s->stream));
   s->stream = stream ? (cudaStream_t)stream : s->own_stream;
   return CTBOP_OK;
 }
@@ -967,7 +979,7 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
       *s->h_int = 1;
       cudaMemcpyAsync(S.cg_hist, s->h_int, sizeof(int), cudaMemcpyHostToDevice, s->stream);
       int mc[3];
-      cudaMemcpy(mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost);
+      sync_copy(s, mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost);
       int cc = (std::max(S.cap_cov, mc[0] + mc[0] / 4 + 4) + 3) & ~3;
       int ca = std::max(S.cap_all, cc + mc[1] + mc[1] / 8 + 16);
       result = alloc_lists(s, cc, (ca + 7) & ~7);
@@ -1051,14 +1063,14 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   unsigned bits = 0;
   long long rb = 0, tot = 0;
   int it = 0, mc[3] = {0, 0, 0};
-  CK(cudaMemcpy(&bits, S.err, sizeof(bits), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&rb, S.rebuild_count, sizeof(rb), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&tot, S.cg_total, sizeof(tot), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&it, S.cg_it, sizeof(it), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost));
+  CK(sync_copy(s, &bits, S.err, sizeof(bits), cudaMemcpyDeviceToHost));
+  CK(sync_copy(s, &rb, S.rebuild_count, sizeof(rb), cudaMemcpyDeviceToHost));
+  CK(sync_copy(s, &tot, S.cg_total, sizeof(tot), cudaMemcpyDeviceToHost));
+  CK(sync_copy(s, &it, S.cg_it, sizeof(it), cudaMemcpyDeviceToHost));
+  CK(sync_copy(s, mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost));
   double res = 0, res0 = 0;
-  CK(cudaMemcpy(&res, S.cg + CG_RESMAX, sizeof(double), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&res0, S.cg + CG_RES0, sizeof(double), cudaMemcpyDeviceToHost));
+  CK(sync_copy(s, &res, S.cg + CG_RESMAX, sizeof(double), cudaMemcpyDeviceToHost));
+  CK(sync_copy(s, &res0, S.cg + CG_RES0, sizeof(double), cudaMemcpyDeviceToHost));
   st->cg_residual_start = res0;
   st->cg_mv_batch = S.mv_batch;
   for (int k = 0; k < 3; ++k) st->cg_mv_ms[k] = s->mv_ms[k];
@@ -1071,8 +1083,8 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   st->max_all = mc[2];
   if (S.N > 0 && S.ncov) {
     std::vector<int> a(S.N), b(S.N);
-    CK(cudaMemcpy(a.data(), S.ncov, sizeof(int) * S.N, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(b.data(), S.nall, sizeof(int) * S.N, cudaMemcpyDeviceToHost));
+    CK(sync_copy(s, a.data(), S.ncov, sizeof(int) * S.N, cudaMemcpyDeviceToHost));
+    CK(sync_copy(s, b.data(), S.nall, sizeof(int) * S.N, cudaMemcpyDeviceToHost));
     double sa = 0, sb = 0;
     for (int i = 0; i < S.N; ++i) { sa += a[i]; sb += b[i]; }
     st->mean_cov = sa / S.N;
@@ -1083,29 +1095,30 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   return CTBOP_OK;
 }
 
-// Force-matching gradient (FP64 policy). With g = dL/dF, the force part of
-// dL/dtheta is -T1 + lambda . d(Hq + chi)/dtheta:
+}  // extern "C"
+
+// Force-matching gradient, in the system's precision policy. With g =
+// dL/dF, the force part of dL/dtheta is -T1 + lambda . d(Hq + chi)/dtheta:
 //   T1 = d/de dE/dtheta (x + e g) at the fixed minimiser charges, and
-//   v  = d/de (H q + chi)(x + e g), both exact, from one forward-mode pass of
-//        the parameter-gradient kernels along g;
+//   v  = d/de (H q + chi)(x + e g), both from one forward-mode pass of the
+//        parameter-gradient kernels along g;
 //   lambda solves the projected adjoint system H lambda = v (sum lambda = 0
-//        per replica);
-//   lambda . d(Hq + chi)/dtheta is the derivative of dE/dtheta along q +
-//        s lambda, exact as a central difference because E is quadratic in q.
+//        per replica) with the charge solver;
+//   lambda . d(Hq + chi)/dtheta = d/ds dE/dtheta (q + s lambda), a second
+//        forward-mode pass, along the charges.
+// No step sizes: both passes carry exact directional derivatives.
+template <class Rr>
 static int param_grad_impl(ctbop_system* s, const double* w_E, const double* E_ref, const double* w_F,
                            const double* F_ref, double* loss_out, double* dth) {
   DevState& S = s->S;
   cudaStream_t st = s->stream;
   const int N = S.N, R = s->R;
+  const bool fp32 = sizeof(Rr) == 4;
   int rc = ctbop_compute(s, 0);
   if (rc) return rc;
-  ctbop_stats stt;
-  rc = ctbop_status(s, &stt);
-  if (rc) return rc;
-  std::vector<double> E(R), F((size_t)3 * N), q0(N);
-  CK(cudaMemcpy2D(E.data(), 8, S.rep_acc + RA_E, RA_STRIDE * 8, 8, R, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(F.data(), S.F, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(q0.data(), S.q, sizeof(double) * N, cudaMemcpyDeviceToHost));
+  std::vector<double> E(R), F((size_t)3 * N);
+  CK(cudaMemcpy2DAsync(E.data(), 8, S.rep_acc + RA_E, RA_STRIDE * 8, 8, R, cudaMemcpyDeviceToHost, st));
+  CK(sync_copy(s, F.data(), S.F, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost));
   // loss and its derivatives with respect to E_r and F_i
   double loss = 0.0;
   std::vector<double> a(R, 0.0), g((size_t)3 * N, 0.0), one(R, 1.0);
@@ -1127,113 +1140,103 @@ static int param_grad_impl(ctbop_system* s, const double* w_E, const double* E_r
   }
   *loss_out = loss;
   double *d_w = nullptr, *d_one = nullptr, *d_g = nullptr, *d_dir = nullptr, *d_v = nullptr, *d_cg = nullptr;
-  double *d_h1 = nullptr, *d_h2 = nullptr;
+  double *d_h1 = nullptr, *d_h2 = nullptr, *d_q0 = nullptr, *d_lam = nullptr;
   auto cleanup = [&]() {
-    for (double* p : {d_w, d_one, d_g, d_dir, d_v, d_cg, d_h1, d_h2}) if (p) cudaFree(p);
+    for (double* p : {d_w, d_one, d_g, d_dir, d_v, d_cg, d_h1, d_h2, d_q0, d_lam}) if (p) cudaFree(p);
   };
   auto dm = [&](double** p, size_t n) { return cudaMalloc(p, sizeof(double) * std::max<size_t>(n, 1)); };
   if (dm(&d_w, R) || dm(&d_one, R) || dm(&d_g, 2 * PG_NPARAM) || dm(&d_dir, (size_t)3 * N) || dm(&d_v, N) ||
-      dm(&d_cg, (size_t)R * CG_STRIDE) || dm(&d_h1, N) || dm(&d_h2, N)) {
+      dm(&d_cg, (size_t)R * CG_STRIDE) || dm(&d_h1, N) || dm(&d_h2, N) || dm(&d_q0, N) || dm(&d_lam, N)) {
     cleanup();
     return fail(s, CTBOP_ERR_OOM, "param_grad: temporary buffers");
   }
   const ctbop_params& P = s->p;
-  std::vector<double> G(2 * PG_NPARAM, 0.0), t0(2 * PG_NPARAM), t1(2 * PG_NPARAM);
+  std::vector<double> G(2 * PG_NPARAM, 0.0), L(2 * PG_NPARAM, 0.0);
   CK(cudaMemcpyAsync(d_w, a.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(d_one, one.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
-  // value-only pass at the current charges, weights w
-  auto pgrad = [&](const double* w, std::vector<double>& out) -> int {
-    CK(launch_param_grad(S, P, w, nullptr, nullptr, d_g, nullptr, st));
-    CK(cudaMemcpyAsync(out.data(), d_g, sizeof(double) * 2 * PG_NPARAM, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return CTBOP_OK;
-  };
   if (gmax == 0.0) {
     // energy part only: sum_r a_r dE_r/dtheta at the minimiser
-    rc = pgrad(d_w, G);
+    CK(launch_param_grad(S, P, fp32, d_w, nullptr, nullptr, nullptr, d_g, nullptr, st));
+    CK(cudaMemcpyAsync(G.data(), d_g, sizeof(double) * 2 * PG_NPARAM, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
   } else {
     // energy part, T1 and v in one forward-mode pass along g
     std::vector<double> v(N);
     CK(cudaMemcpyAsync(d_dir, g.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
-    CK(launch_param_grad(S, P, d_w, d_one, d_dir, d_g, d_v, st));
+    CK(launch_param_grad(S, P, fp32, d_w, d_one, d_dir, nullptr, d_g, d_v, st));
     CK(cudaMemcpyAsync(G.data(), d_g, sizeof(double) * 2 * PG_NPARAM, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(v.data(), d_v, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     for (int k = 0; k < PG_NPARAM; ++k) G[k] -= G[PG_NPARAM + k];
     // rhs of the solver's H q + chi = mu 1 form: chi := -v (the matrix at x
     // is the one the charge solve above assembled)
-    for (int i = 0; i < N; ++i) v[i] = -v[i];
+    double vmax = 0.0;
+    for (int i = 0; i < N; ++i) {
+      v[i] = -v[i];
+      vmax = std::max(vmax, std::fabs(v[i]));
+    }
     CK(cudaMemcpyAsync(d_v, v.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st));
-    // keep the solver state of the charges: per-replica scalars, history
+    // keep the charges and the solver state: per-replica scalars, history
+    CK(cudaMemcpyAsync(d_q0, S.q, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(d_cg, S.cg, sizeof(double) * R * CG_STRIDE, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(d_h1, S.cqh1, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(d_h2, S.cqh2, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     int hist_saved = 0;
-    CK(cudaMemcpy(&hist_saved, S.cg_hist, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(sync_copy(s, &hist_saved, S.cg_hist, sizeof(int), cudaMemcpyDeviceToHost));
     // the adjoint: zero total per replica, cold start
     std::vector<double> cgh((size_t)R * CG_STRIDE);
-    CK(cudaMemcpy(cgh.data(), S.cg, sizeof(double) * cgh.size(), cudaMemcpyDeviceToHost));
+    CK(sync_copy(s, cgh.data(), S.cg, sizeof(double) * cgh.size(), cudaMemcpyDeviceToHost));
     for (int r = 0; r < R; ++r) cgh[(size_t)r * CG_STRIDE + CG_Q] = 0.0;
-    CK(cudaMemcpy(S.cg, cgh.data(), sizeof(double) * cgh.size(), cudaMemcpyHostToDevice));
+    CK(sync_copy(s, S.cg, cgh.data(), sizeof(double) * cgh.size(), cudaMemcpyHostToDevice));
     int zero = 0;
-    CK(cudaMemcpy(S.cg_hist, &zero, sizeof(int), cudaMemcpyHostToDevice));
-    SolveCfg cfg{cg_tol(s), s->o.cg_max_iter, 0, 0};
-    launch_cg_begin<double>(S, s->T, st, cfg.tol, d_v);
+    CK(sync_copy(s, S.cg_hist, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    // FP64: the charge solve's absolute tolerance. FP32: the charge solve's
+    // relative reach (its tolerance over the electronegativity scale, about
+    // 2e-6) applied to the size of this right-hand side.
+    double tol = cg_tol(s);
+    if (fp32 && s->o.cg_tol <= 0) tol = std::max(tol, 2e-6 * vmax);
+    SolveCfg cfg{tol, s->o.cg_max_iter, 0, 0};
+    launch_cg_begin<Rr>(S, s->T, st, cfg.tol, d_v);
     for (int it = 0; it < s->o.cg_max_iter + 4; it += 4) {
-      for (int k = 0; k < 4; ++k) launch_cg_iter<double>(S, cfg, st);
+      for (int k = 0; k < 4; ++k) launch_cg_iter<Rr>(S, cfg, st);
       CK(cudaMemcpyAsync(s->h_int, S.cg_active, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       if (*s->h_int == 0) break;
     }
-    launch_cg_end<double>(S, st);
+    launch_cg_end<Rr>(S, st);
     unsigned bits = 0;
     rc = read_err(s, bits);
     if (!rc && (bits & CT_ERR_CG_MAXITER)) rc = fail(s, CTBOP_ERR_CG_NOT_CONVERGED, "param_grad: adjoint CG reached max_iter");
-    std::vector<double> lam(N);
-    if (!rc) CK(cudaMemcpy(lam.data(), S.q, sizeof(double) * N, cudaMemcpyDeviceToHost));
-    // restore the charge solver's state
+    // lambda out, the charges and the solver state back
+    CK(cudaMemcpyAsync(d_lam, S.q, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(S.q, d_q0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    launch_copy_q<Rr>(S, st);
     CK(cudaMemcpyAsync(S.cg, d_cg, sizeof(double) * R * CG_STRIDE, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(S.cqh1, d_h1, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(S.cqh2, d_h2, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(S.cg_hist, &hist_saved, sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
     if (!rc) {
-      // lambda . d(Hq + chi)/dtheta: central difference along q +- s lambda
-      double lmax = 0.0;
-      for (double x : lam) lmax = std::max(lmax, std::fabs(x));
-      if (lmax > 0.0) {
-        double sq = 0.1 / lmax;
-        std::vector<double> qp(N);
-        for (int sg = 0; sg < 2 && !rc; ++sg) {
-          for (int i = 0; i < N; ++i) qp[i] = q0[i] + (sg == 0 ? sq : -sq) * lam[i];
-          CK(cudaMemcpy(S.q, qp.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
-          rc = pgrad(d_one, sg == 0 ? t0 : t1);
-        }
-        if (!rc)
-          for (int k = 0; k < PG_NPARAM; ++k) G[k] += (t0[k] - t1[k]) / (2.0 * sq);
-      }
+      // lambda . d(Hq + chi)/dtheta: forward mode along the charges
+      CK(launch_param_grad(S, P, fp32, d_one, d_one, nullptr, d_lam, d_g, nullptr, st));
+      CK(cudaMemcpyAsync(L.data(), d_g, sizeof(double) * 2 * PG_NPARAM, cudaMemcpyDeviceToHost, st));
     }
-  }
-  // leave the system at x with the minimiser charges and their forces
-  int rc2 = CTBOP_OK;
-  if (gmax > 0.0) {
-    CK(cudaMemcpy(S.q, q0.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
-    launch_copy_q<double>(S, st);
-    rc2 = ctbop_compute(s, CTBOP_FIXED_CHARGES);
+    CK(cudaStreamSynchronize(st));
+    if (!rc)
+      for (int k = 0; k < PG_NPARAM; ++k) G[k] += L[PG_NPARAM + k];
   }
   cleanup();
   if (rc) return rc;
-  if (rc2) return rc2;
   G[PG_MASS] = G[PG_MASS + 1] = 0.0;   // the mass is not in E
   for (int k = 0; k < PG_NPARAM; ++k) dth[k] = G[k];
   return CTBOP_OK;
 }
 
+extern "C" {
+
 int ctbop_param_grad(ctbop_system* s, const double* w_E, const double* E_ref, const double* w_F,
                      const double* F_ref, double* loss, ctbop_params* dtheta) {
   if (!s) return CTBOP_ERR_INVALID_ARG;
   if (!loss || !dtheta) return fail(s, CTBOP_ERR_INVALID_ARG, "null loss or dtheta");
-  if (s->mixed) return fail(s, CTBOP_ERR_INVALID_ARG, "param_grad runs on the FP64 policy");
   if (!s->have_layout || !s->have_pos || !s->have_types)
     return fail(s, CTBOP_ERR_STATE, "set layout, box, types and positions first");
   cudaSetDevice(s->o.device);
@@ -1242,7 +1245,9 @@ int ctbop_param_grad(ctbop_system* s, const double* w_E, const double* E_ref, co
   static_assert(offsetof(ctbop_params, gamma) == PG_GAMMA * sizeof(double), "layout");
   static_assert(offsetof(ctbop_params, E0) == PG_E0 * sizeof(double), "layout");
   static_assert(offsetof(ctbop_params, k_e) == PG_KE * sizeof(double), "layout");
-  return param_grad_impl(s, w_E, E_ref, w_F, F_ref, loss, reinterpret_cast<double*>(dtheta));
+  double* out = reinterpret_cast<double*>(dtheta);
+  return s->mixed ? param_grad_impl<float>(s, w_E, E_ref, w_F, F_ref, loss, out)
+                  : param_grad_impl<double>(s, w_E, E_ref, w_F, F_ref, loss, out);
 }
 
 int ctbop_energy_noalloc(ctbop_system* s, double* energy) {

@@ -33,86 +33,125 @@
 namespace ct {
 
 // ------------------------------------------------------------ dual numbers
-struct Dual {
-  double v, d;
-  Dual() = default;
-  __device__ Dual(double x) : v(x), d(0.0) {}
-  __device__ Dual(double x, double dx) : v(x), d(dx) {}
+// A value and its derivative along one direction, in T = float or double.
+// Operators take the same T on both sides, so no double constant can slip
+// into an FP32 expression.
+template <class T> struct DualT {
+  T v, d;
+  DualT() = default;
+  __device__ DualT(T x) : v(x), d(T(0)) {}
+  __device__ DualT(T x, T dx) : v(x), d(dx) {}
 };
-__device__ inline Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
-__device__ inline Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
-__device__ inline Dual operator-(Dual a) { return {-a.v, -a.d}; }
-__device__ inline Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
-__device__ inline Dual operator/(Dual a, Dual b) {
-  double q = a.v / b.v;
+template <class T> __device__ inline DualT<T> operator+(DualT<T> a, DualT<T> b) { return {a.v + b.v, a.d + b.d}; }
+template <class T> __device__ inline DualT<T> operator-(DualT<T> a, DualT<T> b) { return {a.v - b.v, a.d - b.d}; }
+template <class T> __device__ inline DualT<T> operator-(DualT<T> a) { return {-a.v, -a.d}; }
+template <class T> __device__ inline DualT<T> operator*(DualT<T> a, DualT<T> b) {
+  return {a.v * b.v, a.d * b.v + a.v * b.d};
+}
+template <class T> __device__ inline DualT<T> operator/(DualT<T> a, DualT<T> b) {
+  T q = a.v / b.v;
   return {q, (a.d - q * b.d) / b.v};
 }
-__device__ inline Dual operator+(Dual a, double b) { return {a.v + b, a.d}; }
-__device__ inline Dual operator+(double a, Dual b) { return {a + b.v, b.d}; }
-__device__ inline Dual operator-(Dual a, double b) { return {a.v - b, a.d}; }
-__device__ inline Dual operator-(double a, Dual b) { return {a - b.v, -b.d}; }
-__device__ inline Dual operator*(Dual a, double b) { return {a.v * b, a.d * b}; }
-__device__ inline Dual operator*(double a, Dual b) { return {a * b.v, a * b.d}; }
-__device__ inline Dual operator/(Dual a, double b) { return {a.v / b, a.d / b}; }
-__device__ inline Dual operator/(double a, Dual b) {
-  double q = a / b.v;
+template <class T> __device__ inline DualT<T> operator+(DualT<T> a, T b) { return {a.v + b, a.d}; }
+template <class T> __device__ inline DualT<T> operator+(T a, DualT<T> b) { return {a + b.v, b.d}; }
+template <class T> __device__ inline DualT<T> operator-(DualT<T> a, T b) { return {a.v - b, a.d}; }
+template <class T> __device__ inline DualT<T> operator-(T a, DualT<T> b) { return {a - b.v, -b.d}; }
+template <class T> __device__ inline DualT<T> operator*(DualT<T> a, T b) { return {a.v * b, a.d * b}; }
+template <class T> __device__ inline DualT<T> operator*(T a, DualT<T> b) { return {a * b.v, a * b.d}; }
+template <class T> __device__ inline DualT<T> operator/(DualT<T> a, T b) { return {a.v / b, a.d / b}; }
+template <class T> __device__ inline DualT<T> operator/(T a, DualT<T> b) {
+  T q = a / b.v;
   return {q, -q * b.d / b.v};
 }
-__device__ inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+template <class T> __device__ inline DualT<T>& operator+=(DualT<T>& a, DualT<T> b) { a = a + b; return a; }
 
 __device__ inline double val(double x) { return x; }
-__device__ inline double val(Dual x) { return x.v; }
+__device__ inline float val(float x) { return x; }
+template <class T> __device__ inline T val(DualT<T> x) { return x.v; }
 __device__ inline double tng(double) { return 0.0; }
-__device__ inline double tng(Dual x) { return x.d; }
+__device__ inline float tng(float) { return 0.0f; }
+template <class T> __device__ inline T tng(DualT<T> x) { return x.d; }
 
-__device__ inline double exp_(double x) { return exp(x); }
-__device__ inline Dual exp_(Dual x) { double e = exp(x.v); return {e, e * x.d}; }
-__device__ inline double log_(double x) { return log(x); }
-__device__ inline Dual log_(Dual x) { return {log(x.v), x.d / x.v}; }
-__device__ inline double pow_(double x, double n) { return pow(x, n); }
-__device__ inline Dual pow_(Dual x, double n) {   // x.v > 0
-  double p = pow(x.v, n);
+// elementary functions on T and on DualT<T> (CUDA's own float and double
+// routines for the values; the derivatives from their closed forms)
+__device__ inline double fexp(double x) { return exp(x); }
+__device__ inline float fexp(float x) { return expf(x); }
+__device__ inline double flog(double x) { return log(x); }
+__device__ inline float flog(float x) { return logf(x); }
+__device__ inline double fpow(double x, double n) { return pow(x, n); }
+__device__ inline float fpow(float x, float n) { return powf(x, n); }
+__device__ inline double fcbrt(double x) { return cbrt(x); }
+__device__ inline float fcbrt(float x) { return cbrtf(x); }
+__device__ inline double fcospi(double x) { return cospi(x); }
+__device__ inline float fcospi(float x) { return cospif(x); }
+__device__ inline double fsinpi(double x) { return sinpi(x); }
+__device__ inline float fsinpi(float x) { return sinpif(x); }
+template <class T> __device__ inline DualT<T> fexp(DualT<T> x) { T e = fexp(x.v); return {e, e * x.d}; }
+template <class T> __device__ inline DualT<T> flog(DualT<T> x) { return {flog(x.v), x.d / x.v}; }
+template <class T> __device__ inline DualT<T> fpow(DualT<T> x, T n) {   // x.v > 0
+  T p = fpow(x.v, n);
   return {p, n * p / x.v * x.d};
 }
-__device__ inline double sqrt_(double x) { return sqrt(x); }
-__device__ inline Dual sqrt_(Dual x) { double s = sqrt(x.v); return {s, 0.5 * x.d / s}; }
-__device__ inline double cbrt_(double x) { return cbrt(x); }
-__device__ inline Dual cbrt_(Dual x) { double c = cbrt(x.v); return {c, x.d / (3.0 * c * c)}; }
-__device__ inline double cospi_(double x) { return cospi(x); }
-__device__ inline Dual cospi_(Dual x) { return {cospi(x.v), -M_PI * sinpi(x.v) * x.d}; }
-__device__ inline double sinpi_(double x) { return sinpi(x); }
-__device__ inline Dual sinpi_(Dual x) { return {sinpi(x.v), M_PI * cospi(x.v) * x.d}; }
+template <class T> __device__ inline DualT<T> fcbrt(DualT<T> x) {
+  T c = fcbrt(x.v);
+  return {c, x.d / (T(3) * c * c)};
+}
+template <class T> __device__ inline DualT<T> fcospi(DualT<T> x) {
+  return {fcospi(x.v), -T(M_PI) * fsinpi(x.v) * x.d};
+}
+template <class T> __device__ inline DualT<T> fsinpi(DualT<T> x) {
+  return {fsinpi(x.v), T(M_PI) * fcospi(x.v) * x.d};
+}
+
+// A value with its derivative (kept for DualT, dropped for a plain T).
+template <class S> struct Mk;
+template <> struct Mk<double> { __device__ static double f(double v, double) { return v; } };
+template <> struct Mk<float> { __device__ static float f(float v, float) { return v; } };
+template <class T> struct Mk<DualT<T>> { __device__ static DualT<T> f(T v, T d) { return DualT<T>(v, d); } };
+
+// The parameter struct in the working precision: ctbop_params' fields, in
+// the same order, as R.
+template <class R> struct ParamsT {
+  R A[4], B[4], lambda1[4], lambda2[4], R_[4], S[4], kappa[4];
+  R sigma[4], p[4], g[4][2], n[4][2];
+  R gamma[8][2], c[8][2], d[8][2], h[8][2], alpha[8][2];
+  R E0[2], chi[2], J[2], gamma_c[2], mass[2];
+  R r_coul, k_e;
+};
+static_assert(sizeof(ParamsT<double>) == sizeof(ctbop_params), "ParamsT mirrors ctbop_params");
+static_assert(sizeof(ParamsT<float>) * 2 == sizeof(ctbop_params), "ParamsT mirrors ctbop_params");
 
 // Cutoff fc(r) and its derivatives with respect to R and S.
-template <class S>
-__device__ inline void fc_params(S r, double Rin, double Sc, S& fc, S& dR, S& dS) {
-  dR = dS = S(0.0);
-  if (val(r) < Rin) { fc = S(1.0); return; }
-  if (val(r) >= Sc) { fc = S(0.0); return; }
-  double w = Sc - Rin;
+template <class R, class S>
+__device__ inline void fc_params(S r, R Rin, R Sc, S& fc, S& dR, S& dS) {
+  dR = dS = S(R(0));
+  if (val(r) < Rin) { fc = S(R(1)); return; }
+  if (val(r) >= Sc) { fc = S(R(0)); return; }
+  R w = Sc - Rin;
   S t = (r - Rin) / w;
-  fc = 0.5 * (1.0 + cospi_(t));
-  S dfdt = -0.5 * M_PI * sinpi_(t);
+  fc = R(0.5) * (R(1) + fcospi(t));
+  S dfdt = R(-0.5 * M_PI) * fsinpi(t);
   dR = dfdt * (r - Sc) / (w * w);
   dS = dfdt * (Rin - r) / (w * w);
 }
 
-template <class S>
-__device__ inline S fc_only(S r, double Rin, double Sc) {
-  if (val(r) < Rin) return S(1.0);
-  if (val(r) >= Sc) return S(0.0);
-  return 0.5 * (1.0 + cospi_((r - Rin) / (Sc - Rin)));
+template <class R, class S>
+__device__ inline S fc_only(S r, R Rin, R Sc) {
+  if (val(r) < Rin) return S(R(1));
+  if (val(r) >= Sc) return S(R(0));
+  return R(0.5) * (R(1) + fcospi((r - Rin) / (Sc - Rin)));
 }
 
-// Block accumulator: values weighted by wv, tangents by wt.
+// Block accumulator in FP64: values weighted by wv, tangents by wt.
 struct Acc {
   double* g;    // [PG_NPARAM] values
   double* t;    // [PG_NPARAM] tangents
   double wv, wt;
   __device__ void operator()(int k, double x) const { atomicAdd(&g[k], wv * x); }
-  __device__ void operator()(int k, Dual x) const {
-    atomicAdd(&g[k], wv * x.v);
-    atomicAdd(&t[k], wt * x.d);
+  __device__ void operator()(int k, float x) const { atomicAdd(&g[k], wv * (double)x); }
+  template <class T> __device__ void operator()(int k, DualT<T> x) const {
+    atomicAdd(&g[k], wv * (double)x.v);
+    atomicAdd(&t[k], wt * (double)x.d);
   }
 };
 
@@ -121,72 +160,80 @@ struct Acc {
 
 // One covalent list entry as staged in shared memory: the bond vector and
 // length, and their derivatives along the direction (zero without one).
-struct __align__(16) Ent {
-  double x, y, z, r;
-  double tx, ty, tz, tr;
+template <class R> struct __align__(16) Ent {
+  R x, y, z, r;
+  R tx, ty, tz, tr;
 };
 
-// A value with its derivative (kept for Dual, dropped for double).
-template <class S> __device__ inline S mk(double v, double d);
-template <> __device__ inline double mk<double>(double v, double) { return v; }
-template <> __device__ inline Dual mk<Dual>(double v, double d) { return Dual(v, d); }
+template <class R, class S> __device__ inline void ent_vec(const Ent<R>& a, S& x, S& y, S& z, S& r) {
+  x = Mk<S>::f(a.x, a.tx); y = Mk<S>::f(a.y, a.ty); z = Mk<S>::f(a.z, a.tz); r = Mk<S>::f(a.r, a.tr);
+}
 
-template <class S> __device__ inline void ent_vec(const Ent& a, S& x, S& y, S& z, S& r) {
-  x = mk<S>(a.x, a.tx); y = mk<S>(a.y, a.ty); z = mk<S>(a.z, a.tz); r = mk<S>(a.r, a.tr);
+// Bond vector from atom i to the image of j named by the list code, in the
+// cell-local coordinates the positions are stored in.
+template <class R>
+__device__ inline void bond_vec(const typename Vec4<R>::T& ui, const typename Vec4<R>::T& uj, int code,
+                                const RepInfo& ri, R& rx, R& ry, R& rz) {
+  int dx, dy, dz;
+  unpack_code(code, dx, dy, dz);
+  R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
+  if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
+  rx = (uj.x - ui.x) + (R)dx * hx;
+  ry = (uj.y - ui.y) + (R)dy * hy;
+  rz = (uj.z - ui.z) + (R)dz * hz;
 }
 
 // Covalent terms: one 8-lane group per atom, the atom's covalent entries
 // staged in shared memory; each lane takes bonds e. Block sums in shared
-// memory, then one atomicAdd per parameter and block. With S = Dual the
-// entries carry their derivatives along dir, the tangents of every term go
-// to the second half of grad, and each bond's share of d(Hq + chi)/de goes
-// to vout: the charge-coupling term 1/2 fc kappa (q_i - q_j)^2 b_ij f_A
-// contributes +-kappa fc f_A b_ij (q_i - q_j) to rows i and j.
-template <class S>
+// memory (FP64), then one atomicAdd per parameter and block. R is the
+// working precision, S either R (values only) or DualT<R>: then the entries
+// carry their derivatives along dir and the charges theirs along qdir, the
+// tangents of every term go to the second half of grad, and (with vout) each
+// bond's share of d(Hq + chi)/de goes to vout: the charge-coupling term
+// 1/2 fc kappa (q_i - q_j)^2 b_ij f_A contributes +-kappa fc f_A b_ij
+// (q_i - q_j) to rows i and j.
+template <class R, class S>
 __global__ void __launch_bounds__(PG_APB * PG_GRP)
-    k_pgrad_cov(int N, int cap_cov, int ld, const double4_32a* __restrict__ u, const int* __restrict__ rep,
-                const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
-                const int* __restrict__ ncov, const double* __restrict__ q, const double* __restrict__ wval,
-                const double* __restrict__ wtan, const double* __restrict__ dir, ctbop_params P,
-                double* __restrict__ grad, double* __restrict__ vout) {
+    k_pgrad_cov(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
+                const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
+                const int* __restrict__ ncov, const double* __restrict__ q, const double* __restrict__ qdir,
+                const double* __restrict__ wval, const double* __restrict__ wtan, const double* __restrict__ dir,
+                ParamsT<R> P, double* __restrict__ grad, double* __restrict__ vout) {
+  using R4 = typename Vec4<R>::T;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ double s_g[2 * PG_NPARAM];
   for (int k = threadIdx.x; k < 2 * PG_NPARAM; k += blockDim.x) s_g[k] = 0.0;
   int g = threadIdx.x / PG_GRP, l = threadIdx.x % PG_GRP;
-  Ent* s_e = reinterpret_cast<Ent*>(smem_raw) + (size_t)g * cap_cov;
-  int* s_t = reinterpret_cast<int*>(reinterpret_cast<Ent*>(smem_raw) + (size_t)PG_APB * cap_cov) +
+  Ent<R>* s_e = reinterpret_cast<Ent<R>*>(smem_raw) + (size_t)g * cap_cov;
+  int* s_t = reinterpret_cast<int*>(reinterpret_cast<Ent<R>*>(smem_raw) + (size_t)PG_APB * cap_cov) +
              (size_t)g * cap_cov;
-  int* s_j = reinterpret_cast<int*>(reinterpret_cast<Ent*>(smem_raw) + (size_t)PG_APB * cap_cov) +
+  int* s_j = reinterpret_cast<int*>(reinterpret_cast<Ent<R>*>(smem_raw) + (size_t)PG_APB * cap_cov) +
              (size_t)PG_APB * cap_cov + (size_t)g * cap_cov;
   int i = blockIdx.x * PG_APB + g;
   bool live = i < N;
   int nc = 0, ti = 0;
   Acc acc{s_g, s_g + PG_NPARAM, 0.0, 0.0};
-  double qi = 0.0;
+  S qi = S(R(0));
   if (live) {
-    double4_32a ui = u[i];
+    R4 ui = u[i];
     ti = (int)ui.w;
     nc = min(ncov[i], cap_cov);
     const RepInfo& ri = reps[rep[i]];
     acc.wv = wval[rep[i]];
     acc.wt = wtan ? wtan[rep[i]] : 0.0;
-    qi = q[i];
-    double gix = 0.0, giy = 0.0, giz = 0.0;
-    if (dir) { gix = dir[3 * i]; giy = dir[3 * i + 1]; giz = dir[3 * i + 2]; }
+    qi = Mk<S>::f((R)q[i], qdir ? (R)qdir[i] : R(0));
+    R gix = 0, giy = 0, giz = 0;
+    if (dir) { gix = (R)dir[3 * i]; giy = (R)dir[3 * i + 1]; giz = (R)dir[3 * i + 2]; }
     for (int e = l; e < nc; e += PG_GRP) {
       size_t idx = (size_t)e * ld + i;
       int j = nl[idx].x;
-      double4_32a uj = u[j];
-      int dx, dy, dz;
-      unpack_code(nl[idx].y, dx, dy, dz);
-      Ent w;
-      w.x = (uj.x - ui.x) + dx * ri.hc[0];
-      w.y = (uj.y - ui.y) + dy * ri.hc[1];
-      w.z = (uj.z - ui.z) + dz * ri.hc[2];
+      R4 uj = u[j];
+      Ent<R> w;
+      bond_vec<R>(ui, uj, nl[idx].y, ri, w.x, w.y, w.z);
       w.r = sqrt(w.x * w.x + w.y * w.y + w.z * w.z);
-      w.tx = w.ty = w.tz = w.tr = 0.0;
+      w.tx = w.ty = w.tz = w.tr = R(0);
       if (dir) {
-        w.tx = dir[3 * j] - gix; w.ty = dir[3 * j + 1] - giy; w.tz = dir[3 * j + 2] - giz;
+        w.tx = (R)dir[3 * j] - gix; w.ty = (R)dir[3 * j + 1] - giy; w.tz = (R)dir[3 * j + 2] - giz;
         w.tr = (w.x * w.tx + w.y * w.ty + w.z * w.tz) / w.r;
       }
       s_e[e] = w;
@@ -198,106 +245,107 @@ __global__ void __launch_bounds__(PG_APB * PG_GRP)
   if (live && (acc.wv != 0.0 || acc.wt != 0.0)) {
     for (int e = l; e < nc; e += PG_GRP) {
       S ex, ey, ez, re;
-      ent_vec<S>(s_e[e], ex, ey, ez, re);
+      ent_vec(s_e[e], ex, ey, ez, re);
       int tj = s_t[e], pb = ti * 2 + tj;
       S fc, fcR, fcS;
-      fc_params(re, P.R[pb], P.S[pb], fc, fcR, fcS);
-      if (val(fc) == 0.0) continue;
+      fc_params(re, P.R_[pb], P.S[pb], fc, fcR, fcS);
+      if (val(fc) == R(0)) continue;
       // environment sums of bond e (recomputed)
-      S z[2] = {S(0.0), S(0.0)};
+      S z[2] = {S(R(0)), S(R(0))};
       for (int k = 0; k < nc; ++k) {
         if (k == e) continue;
         S kx, ky, kz, rk;
-        ent_vec<S>(s_e[k], kx, ky, kz, rk);
+        ent_vec(s_e[k], kx, ky, kz, rk);
         int tk = s_t[k], pk = ti * 2 + tk;
-        S fck = fc_only(rk, P.R[pk], P.S[pk]);
-        if (val(fck) == 0.0) continue;
+        S fck = fc_only(rk, P.R_[pk], P.S[pk]);
+        if (val(fck) == R(0)) continue;
         S ct = (ex * kx + ey * ky + ez * kz) / (re * rk);
         int tri = pb * 2 + tk;
         for (int ll = 0; ll < 2; ++ll) {
-          double c2 = P.c[tri][ll] * P.c[tri][ll], d2 = P.d[tri][ll] * P.d[tri][ll];
+          R c2 = P.c[tri][ll] * P.c[tri][ll], d2 = P.d[tri][ll] * P.d[tri][ll];
           S hm = P.h[tri][ll] - ct, den = d2 + hm * hm;
-          S ang = P.gamma[tri][ll] * (1.0 + c2 * hm * hm / (d2 * den));
-          z[ll] += fck * ang * exp_(P.alpha[tri][ll] * (re - rk));
+          S ang = P.gamma[tri][ll] * (R(1) + c2 * hm * hm / (d2 * den));
+          z[ll] += fck * ang * fexp(P.alpha[tri][ll] * (re - rk));
         }
       }
       // bond order (Eq. 7) and its parameter derivatives, via ln b = e (ln S - ln S0)
-      double pp = P.p[pb], sg = P.sigma[pb], ex_ = 1.0 / (2.0 * sg * pp);
+      R pp = P.p[pb], sg = P.sigma[pb], ex_ = R(1) / (R(2) * sg * pp);
       S zn[2], Z[2], t[2], lnz[2];
       for (int ll = 0; ll < 2; ++ll) {
-        bool pos = val(z[ll]) > 0.0;
-        zn[ll] = pos ? pow_(z[ll], P.n[pb][ll]) : S(0.0);
-        lnz[ll] = pos ? log_(z[ll]) : S(0.0);
+        bool pos = val(z[ll]) > R(0);
+        zn[ll] = pos ? fpow(z[ll], P.n[pb][ll]) : S(R(0));
+        lnz[ll] = pos ? flog(z[ll]) : S(R(0));
         Z[ll] = P.g[pb][ll] + zn[ll];
-        t[ll] = pow_(Z[ll], -pp);
+        t[ll] = fpow(Z[ll], -pp);
       }
       S Ssum = t[0] + t[1];
-      double s0a = pow(P.g[pb][0], -pp), s0b = pow(P.g[pb][1], -pp), S0 = s0a + s0b;
-      S lnb = ex_ * (log_(Ssum) - log(S0));
-      S b = exp_(lnb);
-      double dq = qi - q[s_j[e]];
-      double cq = 1.0 - P.kappa[pb] * dq * dq;
-      S e1 = exp_(-P.lambda1[pb] * re), e2 = exp_(-P.lambda2[pb] * re);
+      R s0a = fpow(P.g[pb][0], -pp), s0b = fpow(P.g[pb][1], -pp), S0 = s0a + s0b;
+      S lnb = ex_ * (flog(Ssum) - flog(S0));
+      S b = fexp(lnb);
+      S dq = qi - Mk<S>::f((R)q[s_j[e]], qdir ? (R)qdir[s_j[e]] : R(0));
+      S dq2 = dq * dq;
+      S cq = R(1) - P.kappa[pb] * dq2;
+      S e1 = fexp(-P.lambda1[pb] * re), e2 = fexp(-P.lambda2[pb] * re);
       S fR = P.A[pb] * e1, fA = P.B[pb] * e2;
       S V = fR - cq * b * fA;
-      S Eb = -0.5 * cq * fc * fA;   // dE/db
+      S Eb = R(-0.5) * cq * fc * fA;   // dE/db
       if (vout) {
-        double wq = tng(P.kappa[pb] * (fc * fA * b)) * dq;
+        double wq = (double)tng(P.kappa[pb] * (fc * fA * b)) * (double)val(dq);
         if (wq != 0.0) {
           atomicAdd(vout + i, wq);
           atomicAdd(vout + s_j[e], -wq);
         }
       }
       // pair parameters
-      acc(PG_A + pb, 0.5 * fc * e1);
-      acc(PG_B + pb, (-0.5 * cq) * fc * b * e2);
-      acc(PG_L1 + pb, -0.5 * fc * re * fR);
-      acc(PG_L2 + pb, (0.5 * cq) * fc * b * fA * re);
-      acc(PG_KAPPA + pb, (0.5 * dq * dq) * fc * b * fA);
-      acc(PG_R + pb, 0.5 * fcR * V);
-      acc(PG_S + pb, 0.5 * fcS * V);
+      acc(PG_A + pb, R(0.5) * fc * e1);
+      acc(PG_B + pb, R(-0.5) * cq * fc * b * e2);
+      acc(PG_L1 + pb, R(-0.5) * fc * re * fR);
+      acc(PG_L2 + pb, R(0.5) * cq * fc * b * fA * re);
+      acc(PG_KAPPA + pb, R(0.5) * dq2 * fc * b * fA);
+      acc(PG_R + pb, R(0.5) * fcR * V);
+      acc(PG_S + pb, R(0.5) * fcS * V);
       // bond-order parameters
-      S dlnS_dp = -(t[0] * log_(Z[0]) + t[1] * log_(Z[1])) / Ssum;
-      double dlnS0_dp = -(s0a * log(P.g[pb][0]) + s0b * log(P.g[pb][1])) / S0;
+      S dlnS_dp = -(t[0] * flog(Z[0]) + t[1] * flog(Z[1])) / Ssum;
+      R dlnS0_dp = -(s0a * flog(P.g[pb][0]) + s0b * flog(P.g[pb][1])) / S0;
       S wb = Eb * b;
       acc(PG_SIGMA + pb, wb * (-lnb / sg));
       acc(PG_P + pb, wb * (-lnb / pp + ex_ * (dlnS_dp - dlnS0_dp)));
       for (int ll = 0; ll < 2; ++ll) {
-        S dg = ex_ * (-pp * t[ll] / (Z[ll] * Ssum) + pp * pow(P.g[pb][ll], -pp - 1.0) / S0);
+        S dg = ex_ * (-pp * t[ll] / (Z[ll] * Ssum) + pp * fpow(P.g[pb][ll], -pp - R(1)) / S0);
         acc(PG_G + pb * 2 + ll, wb * dg);
-        S dn = val(z[ll]) > 0.0 ? ex_ * (-pp * t[ll] / (Z[ll] * Ssum)) * zn[ll] * lnz[ll] : S(0.0);
+        S dn = val(z[ll]) > R(0) ? ex_ * (-pp * t[ll] / (Z[ll] * Ssum)) * zn[ll] * lnz[ll] : S(R(0));
         acc(PG_N + pb * 2 + ll, wb * dn);
       }
       // dE/dzeta_l = Eb db/dzeta_l = Eb b (d ln b / d zeta_l)
       S Ez[2];
       for (int ll = 0; ll < 2; ++ll)
-        Ez[ll] = val(z[ll]) > 0.0
+        Ez[ll] = val(z[ll]) > R(0)
                      ? Eb * b * ex_ * (-pp * t[ll] / (Z[ll] * Ssum)) * P.n[pb][ll] * zn[ll] / z[ll]
-                     : S(0.0);
+                     : S(R(0));
       // triplet parameters and the cutoff of the (i, k) pairs inside zeta
       for (int k = 0; k < nc; ++k) {
         if (k == e) continue;
         S kx, ky, kz, rk;
-        ent_vec<S>(s_e[k], kx, ky, kz, rk);
+        ent_vec(s_e[k], kx, ky, kz, rk);
         int tk = s_t[k], pk = ti * 2 + tk;
         S fck, fkR, fkS;
-        fc_params(rk, P.R[pk], P.S[pk], fck, fkR, fkS);
-        if (val(fck) == 0.0) continue;
+        fc_params(rk, P.R_[pk], P.S[pk], fck, fkR, fkS);
+        if (val(fck) == R(0)) continue;
         S ct = (ex * kx + ey * ky + ez * kz) / (re * rk);
         int tri = pb * 2 + tk;
         for (int ll = 0; ll < 2; ++ll) {
-          if (val(Ez[ll]) == 0.0) continue;
-          double cc = P.c[tri][ll], dd = P.d[tri][ll], gm = P.gamma[tri][ll];
-          double c2 = cc * cc, d2 = dd * dd;
+          if (val(Ez[ll]) == R(0)) continue;
+          R cc = P.c[tri][ll], dd = P.d[tri][ll], gm = P.gamma[tri][ll];
+          R c2 = cc * cc, d2 = dd * dd;
           S hm = P.h[tri][ll] - ct, den = d2 + hm * hm;
-          S angg = 1.0 + c2 * hm * hm / (d2 * den);   // ang / gamma
+          S angg = R(1) + c2 * hm * hm / (d2 * den);   // ang / gamma
           S dr = re - rk;
-          S exl = exp_(P.alpha[tri][ll] * dr);
+          S exl = fexp(P.alpha[tri][ll] * dr);
           S wz = Ez[ll] * exl;
           acc(PG_GAMMA + tri * 2 + ll, wz * fck * angg);
-          acc(PG_C + tri * 2 + ll, wz * fck * (gm * 2.0 * cc) * hm * hm / (d2 * den));
-          acc(PG_D + tri * 2 + ll, wz * fck * (2.0 * gm * c2 * dd) * (1.0 / (den * den) - 1.0 / (d2 * d2)));
-          acc(PG_H + tri * 2 + ll, wz * fck * (gm * 2.0 * c2) * hm / (den * den));
+          acc(PG_C + tri * 2 + ll, wz * fck * (gm * R(2) * cc) * hm * hm / (d2 * den));
+          acc(PG_D + tri * 2 + ll, wz * fck * (R(2) * gm * c2 * dd) * (R(1) / (den * den) - R(1) / (d2 * d2)));
+          acc(PG_H + tri * 2 + ll, wz * fck * (gm * R(2) * c2) * hm / (den * den));
           acc(PG_ALPHA + tri * 2 + ll, wz * fck * gm * angg * dr);
           acc(PG_R + pk, wz * fkR * gm * angg);
           acc(PG_S + pk, wz * fkS * gm * angg);
@@ -312,16 +360,18 @@ __global__ void __launch_bounds__(PG_APB * PG_GRP)
 
 // Charge-kernel and self-energy parameters: one thread per atom over all of
 // its entries (each unordered pair appears in both atoms' lists, hence the
-// 1/2 of the energy). Block sums in shared memory. With S = Dual the pair
-// distances carry their derivatives along dir, and vout_i gets the Coulomb
-// share of d(Hq + chi)_i/de, sum_j q_j dK(r_ij)/de.
-template <class S>
+// 1/2 of the energy). Block sums in shared memory (FP64). With S = DualT<R>
+// the distances carry their derivatives along dir and the charges theirs
+// along qdir, and (with vout) vout_i gets the Coulomb share of
+// d(Hq + chi)_i/de, sum_j q_j dK(r_ij)/de.
+template <class R, class S>
 __global__ void __launch_bounds__(256)
-    k_pgrad_coul(int N, int ld, const double4_32a* __restrict__ u, const int* __restrict__ rep,
-                 const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
-                 const int* __restrict__ nall, const double* __restrict__ q, const double* __restrict__ wval,
-                 const double* __restrict__ wtan, const double* __restrict__ dir, ctbop_params P,
+    k_pgrad_coul(int N, int ld, const typename Vec4<R>::T* __restrict__ u, const int* __restrict__ rep,
+                 const RepInfo* __restrict__ reps, const int2* __restrict__ nl, const int* __restrict__ nall,
+                 const double* __restrict__ q, const double* __restrict__ qdir, const double* __restrict__ wval,
+                 const double* __restrict__ wtan, const double* __restrict__ dir, ParamsT<R> P,
                  double* __restrict__ grad, double* __restrict__ vout) {
+  using R4 = typename Vec4<R>::T;
   __shared__ double s_g[2 * PG_NPARAM];
   for (int k = threadIdx.x; k < 2 * PG_NPARAM; k += blockDim.x) s_g[k] = 0.0;
   __syncthreads();
@@ -329,54 +379,54 @@ __global__ void __launch_bounds__(256)
   if (i < N) {
     Acc acc{s_g, s_g + PG_NPARAM, wval[rep[i]], wtan ? wtan[rep[i]] : 0.0};
     if (acc.wv != 0.0 || acc.wt != 0.0) {
-      double4_32a ui = u[i];
+      R4 ui = u[i];
       int ti = (int)ui.w;
-      double qi = q[i];
-      acc(PG_E0 + ti, 1.0);
+      S qi = Mk<S>::f((R)q[i], qdir ? (R)qdir[i] : R(0));
+      acc(PG_E0 + ti, R(1));
       acc(PG_CHI + ti, qi);
       acc(PG_J + ti, qi * qi);
       const RepInfo& ri = reps[rep[i]];
-      double rc = P.r_coul, ke = P.k_e;
-      double gix = 0.0, giy = 0.0, giz = 0.0;
-      if (dir) { gix = dir[3 * i]; giy = dir[3 * i + 1]; giz = dir[3 * i + 2]; }
-      S gke(0.0), grc(0.0), gga[2] = {S(0.0), S(0.0)};
+      R rc = P.r_coul, ke = P.k_e;
+      R gix = 0, giy = 0, giz = 0;
+      if (dir) { gix = (R)dir[3 * i]; giy = (R)dir[3 * i + 1]; giz = (R)dir[3 * i + 2]; }
+      S gke(R(0)), grc(R(0)), gga0(R(0)), gga1(R(0));
       double vi = 0.0;
       int na = nall[i];
       for (int e = 0; e < na; ++e) {
         size_t idx = (size_t)e * ld + i;
         int j = nl[idx].x;
-        double4_32a uj = u[j];
-        int dx, dy, dz;
-        unpack_code(nl[idx].y, dx, dy, dz);
-        double rx = (uj.x - ui.x) + dx * ri.hc[0], ry = (uj.y - ui.y) + dy * ri.hc[1],
-               rz = (uj.z - ui.z) + dz * ri.hc[2];
-        double rv = sqrt(rx * rx + ry * ry + rz * rz);
-        double t = 0.0;
-        if (dir) t = (rx * (dir[3 * j] - gix) + ry * (dir[3 * j + 1] - giy) + rz * (dir[3 * j + 2] - giz)) / rv;
-        S r = mk<S>(rv, t);
+        R4 uj = u[j];
+        R rx, ry, rz;
+        bond_vec<R>(ui, uj, nl[idx].y, ri, rx, ry, rz);
+        R rv = sqrt(rx * rx + ry * ry + rz * rz);
+        R tr = R(0);
+        if (dir) tr = (rx * ((R)dir[3 * j] - gix) + ry * ((R)dir[3 * j + 1] - giy) +
+                       rz * ((R)dir[3 * j + 2] - giz)) / rv;
+        S r = Mk<S>::f(rv, tr);
         S x = r / rc;
-        if (val(x) >= 1.0) continue;
+        if (val(x) >= R(1)) continue;
         int tj = (int)uj.w;
-        double ga = P.gamma_c[ti], gb = P.gamma_c[tj];
-        double gs3 = pow(ga * gb, -1.5);
-        S x2 = x * x, x3 = x2 * x, x4 = x2 * x2, xm = x - 1.0;
-        S T = 1.0 + x4 * (-35.0 + x * (84.0 + x * (-70.0 + 20.0 * x)));
-        S dT = 140.0 * x3 * xm * xm * xm;
-        S D = cbrt_(r * r * r + gs3), iD = 1.0 / D;
+        R ga = P.gamma_c[ti], gb = P.gamma_c[tj];
+        R gs3 = fpow(ga * gb, R(-1.5));
+        S x2 = x * x, x3 = x2 * x, x4 = x2 * x2, xm = x - R(1);
+        S T = R(1) + x4 * (R(-35) + x * (R(84) + x * (R(-70) + R(20) * x)));
+        S dT = R(140) * x3 * xm * xm * xm;
+        S D = fcbrt(r * r * r + gs3), iD = R(1) / D;
         S K = ke * T * iD;
-        double qj = q[j];
-        vi += tng(K) * qj;
-        double w = 0.5 * qi * qj;
+        S qj = Mk<S>::f((R)q[j], qdir ? (R)qdir[j] : R(0));
+        vi += (double)tng(K) * (double)val(qj);
+        S w = R(0.5) * qi * qj;
         gke += w * K / ke;
-        grc += (w * ke / (rc * rc)) * dT * (-r) * iD;
-        S dK_dgs3 = (-ke / 3.0) * T * iD * iD * iD * iD;
-        gga[ti] += (w * (-1.5 * gs3 / ga)) * dK_dgs3;
-        gga[tj] += (w * (-1.5 * gs3 / gb)) * dK_dgs3;
+        grc += (ke / (rc * rc)) * w * dT * (-r) * iD;
+        S dK_dgs3 = (-ke / R(3)) * T * iD * iD * iD * iD;
+        S c0 = w * dK_dgs3 * (R(-1.5) * gs3);
+        if (ti == 0) gga0 += c0 / ga; else gga1 += c0 / ga;
+        if (tj == 0) gga0 += c0 / gb; else gga1 += c0 / gb;
       }
       acc(PG_KE, gke);
       acc(PG_RCOUL, grc);
-      acc(PG_GAMMA_C, gga[0]);
-      acc(PG_GAMMA_C + 1, gga[1]);
+      acc(PG_GAMMA_C, gga0);
+      acc(PG_GAMMA_C + 1, gga1);
       if (vout && vi != 0.0) atomicAdd(vout + i, vi);
     }
   }
@@ -386,27 +436,42 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------- launchers
-template <class S>
-static cudaError_t pgrad_launch(const DevState& S_, const ctbop_params& P, const double* wval, const double* wtan,
-                                const double* dir, double* grad, double* vout, cudaStream_t st) {
-  size_t sm = (size_t)PG_APB * S_.cap_cov * (sizeof(Ent) + 2 * sizeof(int));
-  cudaError_t e = cudaFuncSetAttribute(k_pgrad_cov<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+template <class R, class S>
+static cudaError_t pgrad_launch(const DevState& D, const ParamsT<R>& P, const double* wval, const double* wtan,
+                                const double* dir, const double* qdir, double* grad, double* vout,
+                                cudaStream_t st) {
+  using R4 = typename Vec4<R>::T;
+  size_t sm = (size_t)PG_APB * D.cap_cov * (sizeof(Ent<R>) + 2 * sizeof(int));
+  cudaError_t e = cudaFuncSetAttribute(k_pgrad_cov<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_pgrad_cov<S><<<(S_.N + PG_APB - 1) / PG_APB, PG_APB * PG_GRP, sm, st>>>(
-      S_.N, S_.cap_cov, S_.ld, (const double4_32a*)S_.u, S_.rep, S_.reps, S_.nl, S_.ncov, S_.q, wval, wtan, dir,
-      P, grad, vout);
-  k_pgrad_coul<S><<<(S_.N + 255) / 256, 256, 0, st>>>(S_.N, S_.ld, (const double4_32a*)S_.u, S_.rep, S_.reps,
-                                                      S_.nl, S_.nall, S_.q, wval, wtan, dir, P, grad, vout);
+  k_pgrad_cov<R, S><<<(D.N + PG_APB - 1) / PG_APB, PG_APB * PG_GRP, sm, st>>>(
+      D.N, D.cap_cov, D.ld, (const R4*)D.u, D.rep, D.reps, D.nl, D.ncov, D.q, qdir, wval, wtan, dir, P, grad,
+      vout);
+  k_pgrad_coul<R, S><<<(D.N + 255) / 256, 256, 0, st>>>(D.N, D.ld, (const R4*)D.u, D.rep, D.reps, D.nl, D.nall,
+                                                       D.q, qdir, wval, wtan, dir, P, grad, vout);
   return cudaGetLastError();
 }
 
-cudaError_t launch_param_grad(const DevState& S, const ctbop_params& P, const double* wval, const double* wtan,
-                              const double* dir, double* grad, double* vout, cudaStream_t st) {
+template <class R>
+static cudaError_t pgrad_prec(const DevState& D, const ctbop_params& P, const double* wval, const double* wtan,
+                              const double* dir, const double* qdir, double* grad, double* vout,
+                              cudaStream_t st) {
+  ParamsT<R> Pr;
+  const double* src = reinterpret_cast<const double*>(&P);
+  R* dst = reinterpret_cast<R*>(&Pr);
+  for (int k = 0; k < PG_NPARAM; ++k) dst[k] = (R)src[k];
+  if (dir || qdir) return pgrad_launch<R, DualT<R>>(D, Pr, wval, wtan, dir, qdir, grad, vout, st);
+  return pgrad_launch<R, R>(D, Pr, wval, nullptr, nullptr, nullptr, grad, nullptr, st);
+}
+
+cudaError_t launch_param_grad(const DevState& D, const ctbop_params& P, bool fp32, const double* wval,
+                              const double* wtan, const double* dir, const double* qdir, double* grad,
+                              double* vout, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(double) * 2 * PG_NPARAM, st);
-  if (e == cudaSuccess && vout) e = cudaMemsetAsync(vout, 0, sizeof(double) * std::max(S.N, 1), st);
-  if (e != cudaSuccess || S.N == 0) return e;
-  if (dir) return pgrad_launch<Dual>(S, P, wval, wtan, dir, grad, vout, st);
-  return pgrad_launch<double>(S, P, wval, nullptr, nullptr, grad, nullptr, st);
+  if (e == cudaSuccess && vout) e = cudaMemsetAsync(vout, 0, sizeof(double) * std::max(D.N, 1), st);
+  if (e != cudaSuccess || D.N == 0) return e;
+  if (fp32) return pgrad_prec<float>(D, P, wval, wtan, dir, qdir, grad, vout, st);
+  return pgrad_prec<double>(D, P, wval, wtan, dir, qdir, grad, vout, st);
 }
 
 }  // namespace ct

@@ -149,13 +149,16 @@ template <class R> void launch_copy_q(const DevState& S, cudaStream_t st);
 // launch shape for kernels with one thread per atom: resident blocks only,
 // each block a contiguous chunk of atoms (a multiple of its size)
 int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk);
-// Parameter gradient of the energy, FP64 (csrc/grad.cu). grad[0..143] =
-// sum_r wval_r dE_r/dtheta at the current positions and charges. With a
-// direction dir ([N,3]), grad[144..287] = sum_r wtan_r d/de dE_r/dtheta(x +
-// e dir) at fixed charges and vout ([N]) = d/de (H q + chi)(x + e dir), both
-// exact (forward-mode); without one, those stay zero and vout is unused.
-cudaError_t launch_param_grad(const DevState& S, const ::ctbop_params& P, const double* wval, const double* wtan,
-                              const double* dir, double* grad, double* vout, cudaStream_t st);
+// Parameter gradient of the energy (csrc/grad.cu), in FP32 (fp32) or FP64
+// arithmetic with FP64 sums. grad[0..143] = sum_r wval_r dE_r/dtheta at the
+// current positions and charges. With a direction dir ([N,3], positions)
+// and/or qdir ([N], charges), grad[144..287] = sum_r wtan_r d/de dE_r/dtheta
+// along (x + e dir, q + e qdir), exact (forward mode); with dir, vout ([N])
+// = d/de (H q + chi)(x + e dir) at fixed charges. Without a direction the
+// tangents stay zero and vout is unused.
+cudaError_t launch_param_grad(const DevState& S, const ::ctbop_params& P, bool fp32, const double* wval,
+                              const double* wtan, const double* dir, const double* qdir, double* grad,
+                              double* vout, cudaStream_t st);
 int energy_noalloc(const double* e_atom, const int* rep, int N, int R, int device, cudaStream_t st,
                    double* host_out, std::string& why);
 

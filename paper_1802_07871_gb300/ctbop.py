@@ -290,7 +290,8 @@ class System:
 
     def param_grad(self, w_E=None, E_ref=None, w_F=None, F_ref=None):
         """Force-matching loss and its gradient with respect to every field
-        of the parameter struct (FP64 policy): returns (loss, Params)."""
+        of the parameter struct, in the system's precision policy: returns
+        (loss, Params)."""
         def arr(a, n):
             if a is None:
                 return None, None
