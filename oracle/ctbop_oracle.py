@@ -667,3 +667,47 @@ def loss_grad_fd(structs, params, w_E=None, E_ref=None, w_F=None, F_ref=None, pa
         d1, d2 = central(path, v, step), central(path, v, 0.5 * step)
         out[path] = (4.0 * d2 - d1) / 3.0
     return out
+
+
+# ----------------------------------------------------------------------------
+# Si desorption screening (Sec. 3.3)
+# ----------------------------------------------------------------------------
+def coordination(x, types, box, pbc, params):
+    """Covalent coordination of every atom: neighbours (every periodic image)
+    closer than the cutoff S of the pair, i.e. with f_c > 0."""
+    s = System(x, types, box, pbc, params)
+    return np.bincount(s.bi, minlength=s.N)
+
+
+def removal_energy(x, types, box, pbc, params, i, Q=0.0, E_full=None):
+    """Energy change when atom i is eliminated (Sec. 3.3 screens surface Si
+    atoms by it every 1 ps and removes those below a threshold, 6.5 eV):
+
+        dE_i = E(system without i) + E0_{t_i} - E(system),
+
+    every other atom held in place and both energies at their charge
+    minimiser with total charge Q. Reading (the paper defines the change but
+    not its reference state): the atom leaves as an isolated neutral atom,
+    whose energy is its self-energy constant E0 (U at q = 0), so the rest
+    keeps the total charge. E_full may pass E(system) when already known."""
+    x = np.asarray(x, float)
+    types = np.asarray(types)
+    keep = np.ones(len(x), bool)
+    keep[i] = False
+    P = tables(params) if isinstance(params, dict) else params
+    if E_full is None:
+        E_full = evaluate(x, types, box, pbc, params, Q=Q)["E"]
+    if keep.sum() == 0:
+        E_rest = 0.0
+    else:
+        E_rest = evaluate(x[keep], types[keep], box, pbc, params, Q=Q)["E"]
+    return E_rest + float(P.E0[int(types[i])]) - E_full
+
+
+def desorption_screen(x, types, box, pbc, params, candidates, threshold=6.5, Q=0.0):
+    """Removal energies of the candidate atoms, each taken alone from the
+    same configuration, and the candidates whose energy is below the
+    threshold (the ones the screening removes together)."""
+    E_full = evaluate(x, types, box, pbc, params, Q=Q)["E"]
+    dE = np.array([removal_energy(x, types, box, pbc, params, int(i), Q=Q, E_full=E_full) for i in candidates])
+    return dE, np.asarray(candidates)[dE < threshold]
