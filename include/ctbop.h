@@ -78,6 +78,9 @@ extern "C" {
 #define CTBOP_GET_KINETIC   8   /* double[R]   kinetic energy of the current velocities (eV) */
 #define CTBOP_GET_THERMOSTAT 9  /* double[R*4] Nose-Hoover state per replica: xi (1/fs), eta (fs), thermostat
                                    mass Qm (eV fs^2), g kB T0 (eV); zeros when the replica has none */
+#define CTBOP_GET_COORDINATION 10 /* double[N] covalent coordination: neighbours (every periodic image) closer
+                                   than the cutoff S of the pair, f_c > 0; needs a completed compute or step
+                                   (CTBOP_ERR_STATE otherwise) */
 
 /* ---- parameters --------------------------------------------------------- */
 /* Index conventions: pair tables [ti*2+tj] (symmetric for the pair block),
@@ -242,6 +245,25 @@ int ctbop_set_params(ctbop_system* s, const ctbop_params* p);
  * CG_NOT_CONVERGED if the charge or adjoint solve does not converge. */
 int ctbop_param_grad(ctbop_system* s, const double* w_E, const double* E_ref, const double* w_F,
                      const double* F_ref, double* loss, ctbop_params* dtheta);
+
+/* Removal energies of the Si desorption screening (Sec. 3.3: the stability
+ * of a surface Si atom is the total-energy change when it is eliminated,
+ * taken every 1 ps; atoms below a threshold, 6.5 eV there, are removed).
+ * For every candidate atom i (global index, cand[0..n_cand), host):
+ *   dE[c] = E(replica without i) + E0_{t_i} - E(replica)
+ * with every other atom in place and both energies at their charge
+ * minimiser with the replica's total charge: the atom leaves as an isolated
+ * neutral atom, whose energy is its self-energy constant E0 (a reading: the
+ * paper does not state the reference state). Each candidate is taken alone
+ * from the current state; the screening decides which to remove.
+ * Evaluates the system first if it has not been (compute). The systems
+ * without each candidate run as replicas of one batch, in chunks of at most
+ * max_atoms atoms (0 = 4,194,304), on the system's stream; the batch system
+ * is kept for the next call (its device memory grows with max_atoms).
+ * dE: host, n_cand doubles, caller-owned. Errors: INVALID_ARG (an index
+ * outside [0, N), null arrays), STATE (no layout, box, types or positions),
+ * CG_NOT_CONVERGED (a batch solve), OOM, CUDA. */
+int ctbop_removal_energies(ctbop_system* s, int64_t n_cand, const int64_t* cand, int64_t max_atoms, double* dE);
 
 /* Per-replica total energy (eV) of the last evaluation, written to
  * energy[0..R) (host array, caller-owned): the sum over each replica of the

@@ -68,6 +68,8 @@ struct ctbop_system {
   int* h_int = nullptr;
   // counters
   int64_t steps = 0, solves = 0;
+  // leave-one-out batches of the desorption screening (created on first use)
+  ctbop_system* loo = nullptr;
 };
 
 static int fail(ctbop_system* s, int code, const std::string& msg) {
@@ -749,6 +751,10 @@ int ctbop_set_params(ctbop_system* s, const ctbop_params* p) {
     s->reps_dirty = true;   // cell grids depend on the list radius
   }
   destroy_graphs(s);        // the graphs hold the old parameters
+  if (s->loo) {             // so does the screening's batch system
+    ctbop_destroy(s->loo);
+    s->loo = nullptr;
+  }
   s->need_rebuild = true;
   s->have_forces = false;
   return CTBOP_OK;
@@ -758,6 +764,7 @@ int ctbop_destroy(ctbop_system* s) {
   if (!s) return CTBOP_OK;
   cudaSetDevice(s->o.device);
   cudaStreamSynchronize(s->stream);
+  if (s->loo) ctbop_destroy(s->loo);
   destroy_graphs(s);
   s->atom_buf.release();
   s->list_buf.release();
@@ -1016,6 +1023,20 @@ int ctbop_get(ctbop_system* s, int what, void* dst, int mem) {
   DevState& S = s->S;
   cudaMemcpyKind kind = mem == CTBOP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   size_t N = S.N, R = s->R;
+  if (what == CTBOP_GET_COORDINATION) {
+    // computed from the current lists, which an evaluation leaves valid
+    if (!s->have_forces) return fail(s, CTBOP_ERR_STATE, "coordination: compute or step first");
+    if (N == 0) return CTBOP_OK;
+    double* tmp = nullptr;
+    CK(cudaMallocAsync(&tmp, sizeof(double) * N, s->stream));
+    if (s->mixed) launch_coordination<float>(S, s->Pf, tmp, s->stream);
+    else launch_coordination<double>(S, s->Pd, tmp, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(dst, tmp, sizeof(double) * N, kind, s->stream));
+    CK(cudaFreeAsync(tmp, s->stream));
+    if (mem == CTBOP_HOST) CK(cudaStreamSynchronize(s->stream));
+    return CTBOP_OK;
+  }
   const void* src = nullptr;
   size_t width = 0, pitch = 0, rows = 1;
   switch (what) {
@@ -1259,6 +1280,158 @@ int ctbop_energy_noalloc(ctbop_system* s, double* energy) {
   int rc = energy_noalloc(s->S.e_atom, s->S.rep, s->S.N, s->R, s->o.device, s->stream, energy, why);
   if (rc == -1) return fail(s, CTBOP_ERR_INVALID_ARG, why);
   if (rc) return fail(s, CTBOP_ERR_CUDA, why);
+  return CTBOP_OK;
+}
+
+// Removal energies of the desorption screening (Sec. 3.3). The systems
+// without each candidate are evaluated as replicas of one batch system
+// (s->loo, kept between calls): candidates are grouped by source replica, a
+// chunk holds as many as fit in max_atoms, and a device gather builds each
+// chunk from the current state. The batch's starting charges are the
+// source's (the solver shifts them onto the replica total).
+int ctbop_removal_energies(ctbop_system* s, int64_t n_cand, const int64_t* cand, int64_t max_atoms, double* dE) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (n_cand < 0 || (n_cand > 0 && (!cand || !dE))) return fail(s, CTBOP_ERR_INVALID_ARG, "bad candidate arrays");
+  if (!s->have_layout || !s->have_box || !s->have_types || !s->have_pos)
+    return fail(s, CTBOP_ERR_STATE, "layout, box, types and positions must be set first");
+  cudaSetDevice(s->o.device);
+  DevState& S = s->S;
+  const int64_t N = S.N;
+  for (int64_t c = 0; c < n_cand; ++c)
+    if (cand[c] < 0 || cand[c] >= N) return fail(s, CTBOP_ERR_INVALID_ARG, "candidate index out of range");
+  if (n_cand == 0) return CTBOP_OK;
+  int rc = CTBOP_OK;
+  if (!s->have_forces) {
+    rc = ctbop_compute(s, 0);
+    if (rc) return rc;
+  }
+  const int R = s->R;
+  std::vector<double> E(R);
+  std::vector<int> types(N);
+  CK(cudaMemcpy2DAsync(E.data(), 8, S.rep_acc + RA_E, RA_STRIDE * 8, 8, R, cudaMemcpyDeviceToHost, s->stream));
+  CK(sync_copy(s, types.data(), S.type, sizeof(int) * N, cudaMemcpyDeviceToHost));
+  struct Job { int64_t c; int r; int n; int drop; };
+  std::vector<Job> jobs;
+  for (int64_t c = 0; c < n_cand; ++c) {
+    int r = (int)(std::upper_bound(s->off.begin(), s->off.end(), cand[c]) - s->off.begin()) - 1;
+    int n = (int)(s->off[r + 1] - s->off[r]);
+    if (n == 1) dE[c] = s->T.E0[types[cand[c]]] - E[r];   // nothing remains: E = 0
+    else jobs.push_back({c, r, n, (int)(cand[c] - s->off[r])});
+  }
+  std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& b) { return a.r < b.r; });
+  const int64_t budget = max_atoms > 0 ? max_atoms : ((int64_t)1 << 22);
+  bool one_source = true;
+  for (const Job& j : jobs) one_source = one_source && j.r == jobs[0].r;
+  if (!s->loo && !jobs.empty()) {
+    ctbop_options o2 = s->o;
+    o2.cap_cov = o2.cap_all = 0;
+    rc = ctbop_create(&s->p, &o2, &s->loo);
+    if (rc) return fail(s, rc, "removal energies: batch system");
+  }
+  if (s->loo) {
+    rc = ctbop_set_stream(s->loo, s->stream);
+    if (rc) return fail(s, rc, "removal energies: " + s->loo->err);
+  }
+  ctbop_system* L = s->loo;
+  double *d_x = nullptr, *d_q = nullptr;
+  int* d_t = nullptr;
+  uint8_t* d_f = nullptr;
+  LooItem* d_items = nullptr;
+  size_t cap_atoms = 0, cap_items = 0;
+  auto release = [&]() {
+    if (d_x) cudaFreeAsync(d_x, s->stream);
+    if (d_q) cudaFreeAsync(d_q, s->stream);
+    if (d_t) cudaFreeAsync(d_t, s->stream);
+    if (d_f) cudaFreeAsync(d_f, s->stream);
+    if (d_items) cudaFreeAsync(d_items, s->stream);
+    d_x = d_q = nullptr;
+    d_t = nullptr;
+    d_f = nullptr;
+    d_items = nullptr;
+  };
+  size_t first_chunk = 0;
+  for (size_t j0 = 0; j0 < jobs.size() && !rc;) {
+    // the chunk: jobs [j0, j1), padded (single source) to the first chunk's size
+    size_t j1 = j0;
+    int64_t atoms = 0;
+    while (j1 < jobs.size() && j1 - j0 < 65535 && (j1 == j0 || atoms + jobs[j1].n - 1 <= budget)) {
+      atoms += jobs[j1].n - 1;
+      ++j1;
+    }
+    if (j0 == 0) first_chunk = j1 - j0;
+    std::vector<Job> chunk(jobs.begin() + j0, jobs.begin() + j1);
+    while (one_source && chunk.size() < first_chunk) chunk.push_back(chunk.back());
+    const int C = (int)chunk.size();
+    std::vector<int64_t> off(C + 1, 0);
+    std::vector<LooItem> items(C);
+    std::vector<double> h((size_t)9 * C, 0.0), Q(C);
+    std::vector<uint8_t> pbc((size_t)3 * C);
+    int max_n = 0;
+    for (int k = 0; k < C; ++k) {
+      const Job& jb = chunk[k];
+      off[k + 1] = off[k] + jb.n - 1;
+      items[k] = {s->off[jb.r], jb.n, jb.drop, off[k]};
+      for (int d = 0; d < 3; ++d) {
+        h[9 * k + 4 * d] = s->box[3 * jb.r + d];
+        pbc[3 * k + d] = s->pbc[3 * jb.r + d];
+      }
+      Q[k] = s->Q[jb.r];
+      max_n = std::max(max_n, jb.n);
+    }
+    const size_t na = (size_t)off[C];
+    if (na > cap_atoms || (size_t)C > cap_items) {
+      release();
+      cap_atoms = std::max(na, cap_atoms);
+      cap_items = std::max((size_t)C, cap_items);
+      CK(cudaMallocAsync(&d_x, sizeof(double) * 3 * cap_atoms, s->stream));
+      CK(cudaMallocAsync(&d_q, sizeof(double) * cap_atoms, s->stream));
+      CK(cudaMallocAsync(&d_t, sizeof(int) * cap_atoms, s->stream));
+      CK(cudaMallocAsync(&d_f, cap_atoms, s->stream));
+      CK(cudaMallocAsync(&d_items, sizeof(LooItem) * cap_items, s->stream));
+    }
+    // layout, box and total charge only when they change (a new layout
+    // reallocates the batch system)
+    bool relayout = !L->have_layout || L->R != C || L->off != off;
+    if (relayout) rc = ctbop_set_layout(L, C, off.data());
+    bool rebox = relayout || L->box.size() != (size_t)3 * C;
+    for (int k = 0; !rebox && k < C; ++k)
+      for (int d = 0; d < 3; ++d)
+        rebox = rebox || L->box[3 * k + d] != h[9 * k + 4 * d] || L->pbc[3 * k + d] != pbc[3 * k + d];
+    if (!rc && rebox) rc = ctbop_set_box(L, h.data(), pbc.data());
+    if (!rc && (relayout || L->Q != Q)) rc = ctbop_set_total_charge(L, Q.data());
+    if (!rc) {
+      CK(cudaMemcpyAsync(d_items, items.data(), sizeof(LooItem) * C, cudaMemcpyHostToDevice, s->stream));
+      launch_loo_gather(d_items, C, max_n, S, d_x, d_t, d_f, d_q, s->stream);
+      CK(cudaGetLastError());
+      rc = ctbop_set_types(L, d_t, CTBOP_DEVICE);
+      if (!rc) rc = ctbop_set_frozen(L, d_f, CTBOP_DEVICE);
+      if (!rc) rc = ctbop_set_positions(L, d_x, CTBOP_DEVICE);
+      if (!rc) rc = ctbop_set_charges(L, d_q, CTBOP_DEVICE);
+    }
+    if (!rc) {
+      // start from the given charges, not an extrapolation of another chunk's
+      *L->h_int = 1;
+      CK(cudaMemcpyAsync(L->S.cg_hist, L->h_int, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+      rc = ctbop_compute(L, 0);
+    }
+    if (rc) {
+      std::string why = L->err;
+      release();
+      CK(cudaStreamSynchronize(s->stream));
+      return fail(s, rc, "removal energies: " + why);
+    }
+    std::vector<double> El(C);
+    CK(cudaMemcpy2DAsync(El.data(), 8, L->S.rep_acc + RA_E, RA_STRIDE * 8, 8, C, cudaMemcpyDeviceToHost,
+                         s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (size_t k = 0; k < j1 - j0; ++k) {
+      const Job& jb = chunk[k];
+      dE[jb.c] = El[k] + s->T.E0[types[s->off[jb.r] + jb.drop]] - E[jb.r];
+    }
+    j0 = j1;
+  }
+  release();
+  CK(cudaStreamSynchronize(s->stream));
   return CTBOP_OK;
 }
 

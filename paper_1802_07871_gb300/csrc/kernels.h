@@ -159,6 +159,19 @@ int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk);
 cudaError_t launch_param_grad(const DevState& S, const ::ctbop_params& P, bool fp32, const double* wval,
                               const double* wtan, const double* dir, const double* qdir, double* grad,
                               double* vout, cudaStream_t st);
+// Desorption screening (csrc/screen.cu): covalent coordination per atom
+// (neighbours within S of the pair) and the leave-one-out gather, one item
+// per batch replica: source replica [src_off, src_off + src_n) without its
+// local atom drop, written from dst_off on.
+struct LooItem {
+  long long src_off;
+  int src_n;
+  int drop;
+  long long dst_off;
+};
+template <class R> void launch_coordination(const DevState& S, const PotParams<R>& P, double* out, cudaStream_t st);
+void launch_loo_gather(const LooItem* items, int n_items, int max_n, const DevState& S, double* ox, int* otype,
+                       uint8_t* ofrozen, double* oq, cudaStream_t st);
 int energy_noalloc(const double* e_atom, const int* rep, int N, int R, int device, cudaStream_t st,
                    double* host_out, std::string& why);
 

@@ -25,7 +25,7 @@ HOST, DEVICE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 FIXED_CHARGES = 1
 GET = {"energy": 0, "forces": 1, "charges": 2, "positions": 3, "velocities": 4,
-       "virial": 5, "e_atom": 6, "mu": 7, "kinetic": 8, "thermostat": 9}
+       "virial": 5, "e_atom": 6, "mu": 7, "kinetic": 8, "thermostat": 9, "coordination": 10}
 
 # every symbol include/ctbop.h declares
 EXPORTS = (
@@ -34,6 +34,7 @@ EXPORTS = (
     "ctbop_set_positions", "ctbop_set_velocities", "ctbop_set_charges", "ctbop_set_frozen",
     "ctbop_set_total_charge", "ctbop_compute", "ctbop_step", "ctbop_get", "ctbop_status",
     "ctbop_profile_steps", "ctbop_energy_noalloc", "ctbop_param_grad", "ctbop_set_params", "ctbop_set_thermostat",
+    "ctbop_removal_energies",
 )
 NPHASE = 10
 PHASES = ("kick_drift", "lists", "bond", "assemble", "cg_start", "cg_matvec", "cg_update",
@@ -109,6 +110,7 @@ def lib():
         "ctbop_get": ([vp, C.c_int, vp, C.c_int], C.c_int),
         "ctbop_status": ([vp, C.POINTER(Stats)], C.c_int),
         "ctbop_profile_steps": ([vp, C.c_int64, C.c_double, vp, vp], C.c_int),
+        "ctbop_removal_energies": ([vp, C.c_int64, vp, C.c_int64, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -396,6 +398,17 @@ class System:
         self._check(self._L.ctbop_energy_noalloc(self._h, out.ctypes.data_as(C.c_void_p)), "energy_noalloc")
         return out
 
+    def removal_energies(self, candidates, max_atoms: int = 0) -> np.ndarray:
+        """Energy change (eV) when each candidate atom (global index) is
+        eliminated alone from the current state, the rest in place, charges
+        re-minimised, the atom leaving neutral (E0 of its type): the
+        stability measure of the desorption screening."""
+        c = np.ascontiguousarray(candidates, dtype=np.int64).reshape(-1)
+        out = np.empty(len(c), dtype=np.float64)
+        self._check(self._L.ctbop_removal_energies(self._h, len(c), c.ctypes.data_as(C.c_void_p), int(max_atoms),
+                                                   out.ctypes.data_as(C.c_void_p)), "removal_energies")
+        return out
+
     def status(self) -> dict:
         st = Stats()
         rc = self._L.ctbop_status(self._h, C.byref(st))
@@ -410,7 +423,8 @@ class System:
         sel = GET[what]
         shape = {"energy": (self.R,), "mu": (self.R,), "kinetic": (self.R,), "virial": (self.R, 3, 3),
                  "forces": (self.n, 3), "positions": (self.n, 3), "velocities": (self.n, 3),
-                 "charges": (self.n,), "e_atom": (self.n,), "thermostat": (self.R, 4)}[what]
+                 "charges": (self.n,), "e_atom": (self.n,), "thermostat": (self.R, 4),
+                 "coordination": (self.n,)}[what]
         if out is None:
             out = np.empty(shape, dtype=np.float64)
         ptr, mem = _ptr(out)
