@@ -711,3 +711,64 @@ def desorption_screen(x, types, box, pbc, params, candidates, threshold=6.5, Q=0
     E_full = evaluate(x, types, box, pbc, params, Q=Q)["E"]
     dE = np.array([removal_energy(x, types, box, pbc, params, int(i), Q=Q, E_full=E_full) for i in candidates])
     return dE, np.asarray(candidates)[dE < threshold]
+
+
+# ----------------------------------------------------------------------------
+# Energy minimisation ("relaxed", "energy minimization", Sec. 3)
+# ----------------------------------------------------------------------------
+# FIRE constants as published by Bitzek et al., Phys. Rev. Lett. 97, 170201
+# (2006): N_min, f_inc, f_dec, alpha_start, f_alpha.
+FIRE_NMIN, FIRE_FINC, FIRE_FDEC, FIRE_ALPHA0, FIRE_FALPHA = 5, 1.1, 0.5, 0.1, 0.99
+
+
+def fire_minimize(x, types, box, pbc, params, frozen=None, fmax=1e-3, max_iter=1000, dt0=1.0, dt_max=5.0,
+                  Q=0.0, n_iter=None):
+    """Relax positions to a local minimum of E(x) = min_q E(x, q) (the paper
+    relaxes structures but names no method; reading: FIRE, Bitzek et al.
+    2006, with the semi-implicit Euler step). One iteration, with F the
+    forces at the current positions (charges at their minimiser) and v the
+    velocities (zero at the start), over the mobile atoms:
+      * stop when max_i |F_i| < fmax;
+      * P = F . v. Downhill (P >= 0, so a start from rest counts): n+ += 1;
+        once n+ > N_min, dt = min(f_inc dt, dt_max) and alpha *= f_alpha;
+        then v = (1 - alpha) v + alpha |v| F / |F|. Uphill (P < 0): n+ = 0,
+        dt *= f_dec, alpha = alpha_start, v = 0;
+      * v += dt F / m; x += dt v.
+    Frozen atoms never move. n_iter, if given, stops after that many
+    iterations whatever the forces. Returns (x, iterations taken, the
+    energies at every evaluation, converged)."""
+    P = tables(params)
+    x = np.array(x, float)
+    types = np.asarray(types)
+    frozen = np.zeros(len(x), bool) if frozen is None else np.asarray(frozen, bool)
+    mob = (~frozen)[:, None]
+    inv_m = (ACC / P.mass[types])[:, None]
+    v = np.zeros_like(x)
+    dt, alpha, npos = dt0, FIRE_ALPHA0, 0
+    res = evaluate(x, types, box, pbc, params, Q)
+    energies = [res["E"]]
+    it = 0
+    limit = max_iter if n_iter is None else n_iter
+    while True:
+        F = np.where(mob, res["F"], 0.0)
+        fm = float(np.sqrt(np.max(np.sum(F * F, axis=1)))) if len(F) else 0.0
+        if (n_iter is None and fm < fmax) or it >= limit:
+            return x, it, np.array(energies), fm < fmax
+        Pw = float(np.sum(F * v))
+        if Pw >= 0.0:
+            npos += 1
+            if npos > FIRE_NMIN:
+                dt = min(dt * FIRE_FINC, dt_max)
+                alpha *= FIRE_FALPHA
+            vn, fn = math.sqrt(float(np.sum(v * v))), math.sqrt(float(np.sum(F * F)))
+            v = (1.0 - alpha) * v + (alpha * vn / fn if fn > 0 else 0.0) * F
+        else:
+            npos = 0
+            dt *= FIRE_FDEC
+            alpha = FIRE_ALPHA0
+            v = np.zeros_like(v)
+        v = np.where(mob, v + dt * F * inv_m, 0.0)
+        x = np.where(mob, x + dt * v, x)
+        it += 1
+        res = evaluate(x, types, box, pbc, params, Q)
+        energies.append(res["E"])
