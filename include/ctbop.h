@@ -265,6 +265,28 @@ int ctbop_param_grad(ctbop_system* s, const double* w_E, const double* E_ref, co
  * CG_NOT_CONVERGED (a batch solve), OOM, CUDA. */
 int ctbop_removal_energies(ctbop_system* s, int64_t n_cand, const int64_t* cand, int64_t max_atoms, double* dE);
 
+/* Energy minimisation (the paper relaxes structures and cools them to 0 K,
+ * Sec. 3, naming no method): FIRE (Bitzek et al., Phys. Rev. Lett. 97,
+ * 170201 (2006); N_min 5, f_inc 1.1, f_dec 0.5, alpha_start 0.1, f_alpha
+ * 0.99) with the semi-implicit Euler step, on E(x) = min_q E(x, q): every
+ * force evaluation solves the charges. One FIRE state per replica; over a
+ * replica's mobile atoms, each iteration:
+ *   stop when max_i |F_i| < fmax (eV/A);
+ *   P = F . v; P >= 0: after more than N_min such iterations in a row,
+ *     dt = min(f_inc dt, dt_max) and alpha *= f_alpha; then
+ *     v = (1 - alpha) v + alpha |v| F / |F|;
+ *   P < 0: dt *= f_dec, alpha = alpha_start, v = 0;
+ *   v += dt F / m; x += dt v (dt in fs).
+ * Starts from rest (velocities zeroed) at dt0 and leaves velocities zero;
+ * frozen atoms never move. At most max_iter iterations per replica.
+ * iters ([R] host or NULL): iterations each replica took to converge, -1 if
+ * it reached max_iter first; fmax_out ([R] host or NULL): each replica's
+ * max |F_i| at its last check. Returns CTBOP_OK either way.
+ * Errors: INVALID_ARG (max_iter < 0, fmax <= 0, not 0 < dt0 <= dt_max),
+ * STATE, CG_NOT_CONVERGED, NONFINITE, NEIGH_OVERFLOW, OOM, CUDA. */
+int ctbop_minimize(ctbop_system* s, int64_t max_iter, double fmax, double dt0, double dt_max, int64_t* iters,
+                   double* fmax_out);
+
 /* Per-replica total energy (eV) of the last evaluation, written to
  * energy[0..R) (host array, caller-owned): the sum over each replica of the
  * per-atom energies, i.e. the value ctbop_get(CTBOP_GET_ENERGY) returns, up

@@ -1435,4 +1435,92 @@ int ctbop_removal_energies(ctbop_system* s, int64_t n_cand, const int64_t* cand,
   return CTBOP_OK;
 }
 
+// Grow the lists after an overflow (from the counts the last build
+// measured) and evaluate again at the current positions.
+static int regrow_and_recompute(ctbop_system* s) {
+  DevState& S = s->S;
+  int mc[3];
+  CK(sync_copy(s, mc, S.maxcnt, sizeof(mc), cudaMemcpyDeviceToHost));
+  int cc = (std::max(S.cap_cov, mc[0] + mc[0] / 4 + 4) + 3) & ~3;
+  int ca = std::max(S.cap_all, cc + mc[1] + mc[1] / 8 + 16);
+  int rc = alloc_lists(s, cc, (ca + 7) & ~7);
+  if (rc) return rc;
+  s->need_rebuild = true;
+  rc = ensure_lists(s);
+  if (rc) return rc;
+  CK(zero_async(s, S.err, sizeof(unsigned)));
+  return ctbop_compute(s, 0);
+}
+
+// FIRE minimisation, one state per replica (csrc/relax.cu). Each iteration
+// reads back the number of replicas still moving and the error word.
+int ctbop_minimize(ctbop_system* s, int64_t max_iter, double fmax, double dt0, double dt_max, int64_t* iters,
+                   double* fmax_out) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (max_iter < 0 || !(fmax > 0) || !std::isfinite(fmax) || !(dt0 > 0) || !std::isfinite(dt_max) || dt_max < dt0)
+    return fail(s, CTBOP_ERR_INVALID_ARG, "need max_iter >= 0, fmax > 0, 0 < dt0 <= dt_max");
+  if (!s->have_layout || !s->have_box || !s->have_types || !s->have_pos)
+    return fail(s, CTBOP_ERR_STATE, "layout, box, types and positions must be set first");
+  cudaSetDevice(s->o.device);
+  int rc = CTBOP_OK;
+  DevState& S = s->S;
+  if (!s->have_forces) {
+    rc = ctbop_compute(s, 0);
+    if (rc) return rc;
+  }
+  const int R = s->R;
+  double* fire = nullptr;
+  int* ctl = nullptr;
+  CK(cudaMallocAsync(&fire, sizeof(double) * R * FI_STRIDE, s->stream));
+  CK(cudaMallocAsync(&ctl, 2 * sizeof(int), s->stream));
+  std::vector<double> fh((size_t)R * FI_STRIDE, 0.0);
+  const FireCfg cfg{fmax * fmax, dt_max, 1.1, 0.5, 0.1, 0.99, 5.0, (double)max_iter};
+  for (int r = 0; r < R; ++r) {
+    fh[(size_t)r * FI_STRIDE + FI_DT] = dt0;
+    fh[(size_t)r * FI_STRIDE + FI_ALPHA] = cfg.alpha0;
+  }
+  CK(sync_copy(s, fire, fh.data(), sizeof(double) * fh.size(), cudaMemcpyHostToDevice));
+  CK(zero_async(s, ctl, 2 * sizeof(int)));
+  CK(zero_async(s, S.v, sizeof(double) * 3 * (size_t)S.N));   // from rest
+  const double half_skin2 = 0.25 * s->o.skin * s->o.skin;
+  int redo = 0;
+  for (;;) {
+    launch_fire_reduce(S, fire, cfg, ctl, ctl + 1, s->stream);
+    CK(cudaGetLastError());
+    CK(sync_copy(s, s->h_int, ctl + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (*s->h_int == 0) break;
+    if (s->mixed) launch_fire_move<float>(S, s->T, fire, half_skin2, s->stream);
+    else launch_fire_move<double>(S, s->T, fire, half_skin2, s->stream);
+    CK(cudaGetLastError());
+    CK(zero_async(s, S.err, sizeof(unsigned)));
+    rc = ctbop_compute(s, 0);
+    unsigned bits = 0;
+    if (!rc) rc = read_err(s, bits);
+    while (!rc && (bits & (CT_ERR_NBR_OVERFLOW | CT_ERR_COV_OVERFLOW))) {
+      if (++redo > 3) {
+        rc = fail(s, CTBOP_ERR_NEIGH_OVERFLOW, "neighbour lists kept overflowing");
+        break;
+      }
+      rc = regrow_and_recompute(s);
+      if (!rc) rc = read_err(s, bits);
+    }
+    if (!rc && (bits & CT_ERR_NONFINITE)) rc = fail(s, CTBOP_ERR_NONFINITE, "non-finite energy, force or position");
+    if (!rc && (bits & CT_ERR_CG_MAXITER)) rc = fail(s, CTBOP_ERR_CG_NOT_CONVERGED, "charge CG reached max_iter");
+    if (rc) break;
+  }
+  if (!rc) {
+    CK(sync_copy(s, fh.data(), fire, sizeof(double) * fh.size(), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < R; ++r) {
+      const double* f = fh.data() + (size_t)r * FI_STRIDE;
+      if (iters) iters[r] = f[FI_DONE] == 1.0 ? (int64_t)f[FI_ITERS] : -1;
+      if (fmax_out) fmax_out[r] = std::sqrt(f[FI_LASTF2]);
+    }
+  }
+  CK(zero_async(s, S.v, sizeof(double) * 3 * (size_t)S.N));   // left at rest
+  cudaFreeAsync(fire, s->stream);
+  cudaFreeAsync(ctl, s->stream);
+  CK(cudaStreamSynchronize(s->stream));
+  return rc;
+}
+
 }  // extern "C"

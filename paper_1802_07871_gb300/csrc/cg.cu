@@ -50,19 +50,6 @@ namespace ct {
 
 __device__ inline double ldcg(const double* p) { return __ldcg(p); }
 
-// Grid-wide "am I the last block" after this block's atomics.
-__device__ inline bool last_block(int* counter) {
-  __shared__ bool am_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    int t = atomicAdd(counter, 1);
-    am_last = (t == (int)gridDim.x - 1);
-  }
-  __syncthreads();
-  if (am_last) __threadfence();
-  return am_last;
-}
 
 // Order-preserving map of doubles to unsigned 64-bit ints (max of the map =
 // map of the max), for atomicMax on signed values.

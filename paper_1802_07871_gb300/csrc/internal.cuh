@@ -315,6 +315,20 @@ __device__ inline void lane_flush(RepAcc<NV>& a, double* out, int stride) {
   block_flush<NV>(w, out, stride);
 }
 
+// Grid-wide "am I the last block" after this block's atomics.
+__device__ inline bool last_block(int* counter) {
+  __shared__ bool am_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    int t = atomicAdd(counter, 1);
+    am_last = (t == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
 // atomic max for non-negative floats (bit patterns order like the values)
 __device__ inline void atomic_max_nonneg(float* addr, float v) {
   atomicMax(reinterpret_cast<unsigned*>(addr), __float_as_uint(v));

@@ -159,6 +159,21 @@ int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk);
 cudaError_t launch_param_grad(const DevState& S, const ::ctbop_params& P, bool fp32, const double* wval,
                               const double* wtan, const double* dir, const double* qdir, double* grad,
                               double* vout, cudaStream_t st);
+// Energy minimisation (csrc/relax.cu): one FIRE state per replica,
+// [R][FI_STRIDE] doubles; FI_P..FI_FMAX2 are the per-iteration sums.
+enum FireSlots {
+  FI_P = 0, FI_VV = 1, FI_FF = 2, FI_FMAX2 = 3, FI_DT = 4, FI_ALPHA = 5, FI_NPOS = 6,
+  FI_DONE = 7,     // 0 moving, 1 converged, -1 stopped at the iteration limit
+  FI_CV = 8, FI_CF = 9, FI_ITERS = 10, FI_LASTF2 = 11, FI_STRIDE = 12
+};
+struct FireCfg {
+  double fmax2, dt_max, f_inc, f_dec, alpha0, f_alpha, n_min, max_iter;
+};
+void launch_fire_reduce(const DevState& S, double* fire, const FireCfg& cfg, int* blocks, int* active,
+                        cudaStream_t st);
+template <class R>
+void launch_fire_move(const DevState& S, const TypeParams& T, const double* fire, double half_skin2,
+                      cudaStream_t st);
 // Desorption screening (csrc/screen.cu): covalent coordination per atom
 // (neighbours within S of the pair) and the leave-one-out gather, one item
 // per batch replica: source replica [src_off, src_off + src_n) without its

@@ -34,7 +34,7 @@ EXPORTS = (
     "ctbop_set_positions", "ctbop_set_velocities", "ctbop_set_charges", "ctbop_set_frozen",
     "ctbop_set_total_charge", "ctbop_compute", "ctbop_step", "ctbop_get", "ctbop_status",
     "ctbop_profile_steps", "ctbop_energy_noalloc", "ctbop_param_grad", "ctbop_set_params", "ctbop_set_thermostat",
-    "ctbop_removal_energies",
+    "ctbop_removal_energies", "ctbop_minimize",
 )
 NPHASE = 10
 PHASES = ("kick_drift", "lists", "bond", "assemble", "cg_start", "cg_matvec", "cg_update",
@@ -111,6 +111,7 @@ def lib():
         "ctbop_status": ([vp, C.POINTER(Stats)], C.c_int),
         "ctbop_profile_steps": ([vp, C.c_int64, C.c_double, vp, vp], C.c_int),
         "ctbop_removal_energies": ([vp, C.c_int64, vp, C.c_int64, vp], C.c_int),
+        "ctbop_minimize": ([vp, C.c_int64, C.c_double, C.c_double, C.c_double, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -408,6 +409,17 @@ class System:
         self._check(self._L.ctbop_removal_energies(self._h, len(c), c.ctypes.data_as(C.c_void_p), int(max_atoms),
                                                    out.ctypes.data_as(C.c_void_p)), "removal_energies")
         return out
+
+    def minimize(self, max_iter: int = 1000, fmax: float = 1e-3, dt0: float = 1.0, dt_max: float = 5.0):
+        """FIRE relaxation of every replica (charges re-minimised at every
+        force evaluation). Returns (iterations per replica, -1 where max_iter
+        was reached first; max |F_i| per replica at the end)."""
+        it = np.empty(self.R, dtype=np.int64)
+        fm = np.empty(self.R, dtype=np.float64)
+        self._check(self._L.ctbop_minimize(self._h, int(max_iter), float(fmax), float(dt0), float(dt_max),
+                                           it.ctypes.data_as(C.c_void_p), fm.ctypes.data_as(C.c_void_p)),
+                    "minimize")
+        return it, fm
 
     def status(self) -> dict:
         st = Stats()
