@@ -772,3 +772,96 @@ def fire_minimize(x, types, box, pbc, params, frozen=None, fmax=1e-3, max_iter=1
         it += 1
         res = evaluate(x, types, box, pbc, params, Q)
         energies.append(res["E"])
+
+
+# ----------------------------------------------------------------------------
+# Ring statistics of the C network (Sec. 3.3: counts of 5-, 6- and 7-membered
+# rings over time, and the in-plane orientation of 6-membered rings)
+# ----------------------------------------------------------------------------
+def carbon_bonds(x, types, box, pbc, bond_cut):
+    """C-C bonds (every periodic image) shorter than bond_cut: for each C
+    atom, the list of (neighbour, bond vector)."""
+    x = np.asarray(x, float)
+    types = np.asarray(types)
+    i, j, _, u = pairs(x, np.asarray(box, float), np.asarray(pbc, bool), bond_cut)
+    r = np.sqrt(np.einsum("ij,ij->i", u, u))
+    nb = [[] for _ in range(len(x))]
+    for a, b, v, rr in zip(i, j, u, r):
+        if types[a] == 1 and types[b] == 1 and rr < bond_cut:
+            nb[a].append((int(b), v))
+    return nb
+
+
+def rings(x, types, box, pbc, bond_cut, max_size=8, close_tol=0.1):
+    """Primitive rings of the C bond graph, sizes 3..max_size (a reading of
+    the paper's "n-membered rings"; it gives no ring criterion). A ring is a
+    closed path of distinct atoms whose bond vectors sum to zero (so a path
+    around a periodic box does not count), and is primitive when no two of
+    its atoms are joined in the graph by a path shorter than their distance
+    along the ring (with the same displacement). Each ring once: starting at
+    its lowest atom index, second atom below the last. Returns a list of
+    (size, centre (3,), orientation in degrees or nan): the orientation of a
+    6-ring is the in-plane angle of its three vertex diagonals taken modulo
+    60 degrees (their circular mean in that period), zero when a diagonal
+    points along x."""
+    x = np.asarray(x, float)
+    nb = carbon_bonds(x, types, box, pbc, bond_cut)
+    out = []
+
+    def has_shortcut(a, b, disp, k):
+        # a walk of length < k from a reaching b with displacement disp
+        frontier = [(a, np.zeros(3))]
+        for _ in range(k - 1):
+            nxt = []
+            for v, d in frontier:
+                for w, bv in nb[v]:
+                    dw = d + bv
+                    if w == b and np.linalg.norm(dw - disp) < close_tol:
+                        return True
+                    nxt.append((w, dw))
+            frontier = nxt
+        return False
+
+    def primitive(path, pos):
+        n = len(path)
+        for s in range(n):
+            for t in range(s + 2, n):
+                k = min(t - s, n - (t - s))
+                if k >= 2 and has_shortcut(path[s], path[t], pos[t] - pos[s], k):
+                    return False
+        return True
+
+    def orientation(pos):
+        psi = []
+        for k in range(3):
+            d = pos[k + 3] - pos[k]
+            psi.append(6.0 * math.atan2(d[1], d[0]))
+        m = math.atan2(sum(math.sin(p) for p in psi), sum(math.cos(p) for p in psi)) / 6.0
+        return math.degrees(m) % 60.0
+
+    def dfs(path, pos):
+        v, d = path[-1], pos[-1]
+        for w, bv in nb[v]:
+            dw = d + bv
+            if w == path[0] and len(path) >= 3:
+                if np.linalg.norm(dw) < close_tol and path[1] < path[-1] and primitive(path, pos):
+                    P = np.array(pos)
+                    c = x[path[0]] + P.mean(axis=0)
+                    out.append((len(path), c, orientation(P) if len(path) == 6 else float("nan")))
+                continue
+            if w <= path[0] or w in path or len(path) >= max_size:
+                continue
+            dfs(path + [w], pos + [dw])
+
+    for a in range(len(x)):
+        if nb[a]:
+            dfs([a], [np.zeros(3)])
+    return out
+
+
+def ring_counts(ring_list, max_size=8):
+    """Number of rings of each size 3..max_size."""
+    c = np.zeros(max_size - 2, dtype=np.int64)
+    for n, _, _ in ring_list:
+        c[n - 3] += 1
+    return c
