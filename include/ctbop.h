@@ -287,6 +287,29 @@ int ctbop_removal_energies(ctbop_system* s, int64_t n_cand, const int64_t* cand,
 int ctbop_minimize(ctbop_system* s, int64_t max_iter, double fmax, double dt0, double dt_max, int64_t* iters,
                    double* fmax_out);
 
+/* One ring of the C network (ctbop_rings). */
+typedef struct ctbop_ring {
+    int32_t replica;      /* replica the ring's atoms belong to */
+    int32_t size;         /* number of atoms, 3..8 */
+    double  centre[3];    /* mean of its atoms' positions, unwrapped along the ring (A) */
+    double  orientation;  /* 6-rings: in-plane angle of the vertex diagonals modulo 60 degrees (their
+                             circular mean in that period), 0 when a diagonal points along x; NaN otherwise */
+} ctbop_ring;
+
+/* Ring statistics of the C network (Sec. 3.3 follows the numbers of 5-, 6-
+ * and 7-membered C rings and the in-plane orientation of the 6-membered
+ * ones; it gives no ring criterion). Counts primitive rings: closed paths
+ * of distinct C atoms joined by C-C bonds shorter than bond_cut, whose bond
+ * vectors sum to zero (a path around a periodic box is no ring), with no
+ * shorter path in the bond graph between any two of their atoms (same
+ * displacement) than along the ring; sizes 3..max_size (max_size <= 8).
+ * bond_cut: 0 = the C-C covalent cutoff S; at most that S (the lists hold
+ * every pair within it). Needs a completed compute or step (STATE).
+ * Writes up to cap records to out (host, caller-owned; any order) and the
+ * total number of rings to *n_rings, which may exceed cap (call again with
+ * a larger cap). Errors: INVALID_ARG, STATE, OOM, CUDA. */
+int ctbop_rings(ctbop_system* s, double bond_cut, int32_t max_size, int64_t cap, ctbop_ring* out, int64_t* n_rings);
+
 /* Per-replica total energy (eV) of the last evaluation, written to
  * energy[0..R) (host array, caller-owned): the sum over each replica of the
  * per-atom energies, i.e. the value ctbop_get(CTBOP_GET_ENERGY) returns, up

@@ -1523,4 +1523,33 @@ int ctbop_minimize(ctbop_system* s, int64_t max_iter, double fmax, double dt0, d
   return rc;
 }
 
+int ctbop_rings(ctbop_system* s, double bond_cut, int32_t max_size, int64_t cap, ctbop_ring* out, int64_t* n_rings) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  const double scc = s->p.S[3];   // C-C pair
+  if (!n_rings || cap < 0 || (cap > 0 && !out) || max_size < 3 || max_size > 8 || !(bond_cut >= 0) ||
+      bond_cut > scc)
+    return fail(s, CTBOP_ERR_INVALID_ARG, "rings: need n_rings, cap >= 0 (out if cap > 0), 3 <= max_size <= 8, "
+                                          "0 <= bond_cut <= the C-C cutoff S");
+  if (!s->have_forces) return fail(s, CTBOP_ERR_STATE, "rings: compute or step first");
+  cudaSetDevice(s->o.device);
+  if (bond_cut == 0) bond_cut = scc;
+  ctbop_ring* d_out = nullptr;
+  unsigned long long* d_cnt = nullptr;
+  CK(cudaMallocAsync(&d_out, sizeof(ctbop_ring) * std::max<int64_t>(cap, 1), s->stream));
+  CK(cudaMallocAsync(&d_cnt, sizeof(unsigned long long), s->stream));
+  CK(zero_async(s, d_cnt, sizeof(unsigned long long)));
+  if (s->mixed) launch_rings<float>(s->S, bond_cut, max_size, d_out, cap, d_cnt, s->stream);
+  else launch_rings<double>(s->S, bond_cut, max_size, d_out, cap, d_cnt, s->stream);
+  CK(cudaGetLastError());
+  unsigned long long n = 0;
+  CK(sync_copy(s, &n, d_cnt, sizeof(n), cudaMemcpyDeviceToHost));
+  int64_t m = std::min<int64_t>((int64_t)n, cap);
+  if (m > 0) CK(sync_copy(s, out, d_out, sizeof(ctbop_ring) * m, cudaMemcpyDeviceToHost));
+  *n_rings = (int64_t)n;
+  cudaFreeAsync(d_out, s->stream);
+  cudaFreeAsync(d_cnt, s->stream);
+  CK(cudaStreamSynchronize(s->stream));
+  return CTBOP_OK;
+}
+
 }  // extern "C"

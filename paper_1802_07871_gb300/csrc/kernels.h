@@ -174,6 +174,11 @@ void launch_fire_reduce(const DevState& S, double* fire, const FireCfg& cfg, int
 template <class R>
 void launch_fire_move(const DevState& S, const TypeParams& T, const double* fire, double half_skin2,
                       cudaStream_t st);
+// Primitive C rings (csrc/rings.cu): records appended through *count (the
+// total, which may exceed cap; records past cap are dropped).
+template <class R>
+void launch_rings(const DevState& S, double bond_cut, int max_size, ::ctbop_ring* out, long long cap,
+                  unsigned long long* count, cudaStream_t st);
 // Desorption screening (csrc/screen.cu): covalent coordination per atom
 // (neighbours within S of the pair) and the leave-one-out gather, one item
 // per batch replica: source replica [src_off, src_off + src_n) without its

@@ -34,8 +34,10 @@ EXPORTS = (
     "ctbop_set_positions", "ctbop_set_velocities", "ctbop_set_charges", "ctbop_set_frozen",
     "ctbop_set_total_charge", "ctbop_compute", "ctbop_step", "ctbop_get", "ctbop_status",
     "ctbop_profile_steps", "ctbop_energy_noalloc", "ctbop_param_grad", "ctbop_set_params", "ctbop_set_thermostat",
-    "ctbop_removal_energies", "ctbop_minimize",
+    "ctbop_removal_energies", "ctbop_minimize", "ctbop_rings",
 )
+# one record of ctbop_rings (struct ctbop_ring)
+RING_DTYPE = np.dtype([("replica", "<i4"), ("size", "<i4"), ("centre", "<f8", 3), ("orientation", "<f8")])
 NPHASE = 10
 PHASES = ("kick_drift", "lists", "bond", "assemble", "cg_start", "cg_matvec", "cg_update",
           "cg_charges", "cov_force", "coul_gather_kick")
@@ -112,6 +114,7 @@ def lib():
         "ctbop_profile_steps": ([vp, C.c_int64, C.c_double, vp, vp], C.c_int),
         "ctbop_removal_energies": ([vp, C.c_int64, vp, C.c_int64, vp], C.c_int),
         "ctbop_minimize": ([vp, C.c_int64, C.c_double, C.c_double, C.c_double, vp, vp], C.c_int),
+        "ctbop_rings": ([vp, C.c_double, C.c_int32, C.c_int64, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -420,6 +423,19 @@ class System:
                                            it.ctypes.data_as(C.c_void_p), fm.ctypes.data_as(C.c_void_p)),
                     "minimize")
         return it, fm
+
+    def rings(self, bond_cut: float = 0.0, max_size: int = 8) -> np.ndarray:
+        """Primitive C rings of the current state (records of RING_DTYPE, in
+        no particular order); bond_cut 0 = the C-C covalent cutoff."""
+        cap = max(1024, self.n)
+        while True:
+            out = np.empty(cap, dtype=RING_DTYPE)
+            n = C.c_int64(0)
+            self._check(self._L.ctbop_rings(self._h, float(bond_cut), int(max_size), cap,
+                                            out.ctypes.data_as(C.c_void_p), C.byref(n)), "rings")
+            if n.value <= cap:
+                return out[:n.value].copy()
+            cap = n.value
 
     def status(self) -> dict:
         st = Stats()
