@@ -101,6 +101,13 @@ typedef struct ctbop_params {
     double r_coul, k_e;
 } ctbop_params;
 
+/* Preconditioners of the charge CG (ctbop_options.precond). BLOCK: the
+ * exact inverse of each 32 x 32 diagonal block of H (atoms 32b .. 32b+31 in
+ * the order they were given; atoms listed in spatially coherent order make
+ * the blocks compact and the preconditioner strong). JACOBI: 1 / diag(H). */
+#define CTBOP_PRECOND_BLOCK 0
+#define CTBOP_PRECOND_JACOBI 1
+
 typedef struct ctbop_options {
     int32_t precision;    /* CTBOP_PREC_FP64 or CTBOP_PREC_MIXED */
     int32_t cg_max_iter;  /* charge-solve iteration cap (default 200) */
@@ -111,7 +118,7 @@ typedef struct ctbop_options {
     int32_t cap_cov;      /* covalent entries per atom; 0 = sized from the first configuration */
     int32_t cap_all;      /* all entries (charge cutoff) per atom; 0 = sized automatically */
     int32_t device;       /* CUDA device ordinal */
-    int32_t reserved;
+    int32_t precond;      /* charge-solve preconditioner: CTBOP_PRECOND_BLOCK (default) or CTBOP_PRECOND_JACOBI */
 } ctbop_options;
 
 typedef struct ctbop_stats {

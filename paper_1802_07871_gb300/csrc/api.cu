@@ -277,6 +277,13 @@ static int alloc_atoms(ctbop_system* s) {
       *pp = b;
     }
   }
+  {
+    unsigned char *bi = nullptr, *bs = nullptr;
+    CK(dalloc(s->atom_buf, &bi, (size_t)((N + 31) / 32) * 1024 * rs));
+    CK(dalloc(s->atom_buf, &bs, (size_t)N * rs));
+    S.binv = bi;
+    S.bsum = bs;
+  }
   CK(dalloc(s->atom_buf, &S.cqh1, (size_t)N));
   CK(dalloc(s->atom_buf, &S.cqh2, (size_t)N));
   CK(dalloc(s->atom_buf, &S.ncov, (size_t)N));
@@ -392,6 +399,7 @@ static void enqueue_middle(ctbop_system* s, const PotParams<Rr>& P, cudaStream_t
   DevState& S = s->S;
   launch_bond<Rr>(S, P, st);
   launch_assemble<Rr>(S, P, s->T, st);
+  if (S.precond) launch_block_setup<Rr>(S, st);
   launch_cg_begin<Rr>(S, s->T, st, cg_tol(s));
 }
 
@@ -655,12 +663,14 @@ int ctbop_create(const ctbop_params* p, const ctbop_options* o, ctbop_system** o
   std::string why;
   if (!params_valid(p, why)) return CTBOP_ERR_INVALID_ARG;
   if (o->precision != CTBOP_PREC_FP64 && o->precision != CTBOP_PREC_MIXED) return CTBOP_ERR_INVALID_ARG;
+  if (o->precond != CTBOP_PRECOND_BLOCK && o->precond != CTBOP_PRECOND_JACOBI) return CTBOP_ERR_INVALID_ARG;
   if (!(o->skin >= 0) || o->cg_max_iter < 1) return CTBOP_ERR_INVALID_ARG;
   if (cudaSetDevice(o->device) != cudaSuccess) return CTBOP_ERR_CUDA;
   ctbop_system* s = new ctbop_system();
   s->p = *p;
   s->o = *o;
   s->mixed = o->precision == CTBOP_PREC_MIXED;
+  s->S.precond = o->precond == CTBOP_PRECOND_BLOCK ? 1 : 0;
   pack_params<float>(*p, o->skin, s->Pf);
   pack_params<double>(*p, o->skin, s->Pd);
   for (int t = 0; t < 2; ++t) {

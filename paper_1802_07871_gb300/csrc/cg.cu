@@ -3,9 +3,10 @@
 //
 // E is quadratic in q, so the constrained minimum (sum_r q = Q_r per
 // replica) solves H q + chi = mu 1 on the set sum q = Q. The solve is a
-// projected, Jacobi-preconditioned CG that keeps the iterate feasible:
+// projected, preconditioned CG that keeps the iterate feasible (M^-1 the
+// block-Jacobi inverse below, or D^-1):
 //   r = -(H q + chi)                       (negative gradient)
-//   y = D^-1 r,  z = y - (sum y / sum d) d  with d = D^-1 1 (sum z = 0)
+//   y = M^-1 r,  z = y - (sum y / sum d) d  with d = M^-1 1 (sum z = 0)
 //   w = H z = H y - c H d                   (c = sum y / sum d)
 // so every direction keeps the total charge and q never leaves the
 // constraint. The iteration is the one-reduction (Chronopoulos-Gear) form:
@@ -211,6 +212,114 @@ __global__ void k_cg_prep(int R, double* __restrict__ cg, unsigned long long* __
   }
 }
 
+// Block-Jacobi preconditioner: M^-1 is the exact inverse of each 32 x 32
+// diagonal block of H (atoms 32b .. 32b+31 in storage order; in Jacobi
+// order the blocks hold the strong local couplings, the covalent w terms and
+// the near charge-kernel entries). One warp per block assembles the block
+// from the stored rows (diagonal, self-images, entries whose atom is in the
+// block), symmetrises it, factorises it (Cholesky), inverts the factor and
+// forms M_b^-1 = W^T W with W = L^-1 (exactly symmetric: both triangles are
+// the same sums in the same order). Lanes past N get an identity row. Atoms
+// of different replicas in one block have exactly zero coupling, which the
+// factorisation keeps. A block that is not numerically positive definite
+// falls back to its Jacobi inverse. Also writes d = M^-1 1 (row sums).
+template <class R>
+__global__ void __launch_bounds__(128)
+    k_block_setup(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nall,
+                  const void* __restrict__ M, const R* __restrict__ Dg, R* __restrict__ binv,
+                  R* __restrict__ bsum) {
+  __shared__ R sh[4][32][33];
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int base = (blockIdx.x * 4 + warp) * 32;
+  if (base >= N) return;   // whole warps only
+  R(*A)[33] = sh[warp];
+  for (int j = 0; j < 32; ++j) A[lane][j] = R(0);
+  __syncwarp();
+  int i = base + lane;
+  if (i < N) {
+    MatView<R> mv(nl, M);
+    int na = nall[i];
+    for (int e = 0; e < na; ++e) {
+      int j;
+      R v;
+      mv.get((size_t)e * ld + i, j, v);
+      unsigned dj = (unsigned)(j - base);
+      if (dj < 32u) A[lane][dj] += v;
+    }
+    A[lane][lane] += Dg[i];
+  } else {
+    A[lane][lane] = R(1);
+  }
+  __syncwarp();
+  for (int j = lane + 1; j < 32; ++j) {
+    R m = R(0.5) * (A[lane][j] + A[j][lane]);
+    A[lane][j] = m;
+    A[j][lane] = m;
+  }
+  __syncwarp();
+  R hii = A[lane][lane];
+  bool ok = true;
+  for (int k = 0; k < 32; ++k) {   // Cholesky, lower triangle in place
+    R piv = A[k][k];
+    if (!(piv > R(0))) { ok = false; break; }   // the same value in every lane
+    R lk = sqrt(piv);
+    __syncwarp();
+    if (lane == k) A[k][k] = lk;
+    if (lane > k) A[lane][k] /= lk;
+    __syncwarp();
+    if (lane > k)
+      for (int j = k + 1; j <= lane; ++j) A[lane][j] -= A[lane][k] * A[j][k];
+    __syncwarp();
+  }
+  R* out = binv + (size_t)(base >> 5) * 1024;
+  if (!ok) {
+    __syncwarp();
+    for (int j = 0; j < 32; ++j) out[j * 32 + lane] = j == lane ? R(1) / hii : R(0);
+    if (i < N) bsum[i] = R(1) / hii;
+    return;
+  }
+  // column `lane` of W = L^-1 by forward substitution (registers)
+  R w[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    R t = r == lane ? R(1) : R(0);
+#pragma unroll
+    for (int m = 0; m < r; ++m) t -= A[r][m] * w[m];
+    w[r] = r < lane ? R(0) : t / A[r][r];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 32; ++r) A[r][lane] = w[r];   // A now holds W (A[r][c] = W_rc)
+  __syncwarp();
+  R rs = R(0);
+  for (int j = 0; j < 32; ++j) {
+    R t = R(0);
+    for (int k = max(lane, j); k < 32; ++k) t += A[k][lane] * A[k][j];
+    out[j * 32 + lane] = t;   // element (lane, j), column-major
+    rs += t;
+  }
+  if (i < N) bsum[i] = rs;
+}
+
+template <class R>
+void launch_block_setup(const DevState& S, cudaStream_t st) {
+  if (S.N == 0) return;
+  int nb = (S.N + 31) / 32;
+  k_block_setup<R><<<(nb + 3) / 4, 128, 0, st>>>(S.N, S.ld, S.nl, S.nall, S.M, (const R*)S.Dg, (R*)S.binv,
+                                                 (R*)S.bsum);
+}
+
+// y = M_b^-1 r for the warp's block: every lane of a full warp, i = 32b +
+// lane, r_i of this lane (zero where no atom).
+template <class R>
+__device__ inline R block_apply(const R* __restrict__ binv, int i, R ri) {
+  const R* col = binv + (size_t)(i >> 5) * 1024 + (i & 31);
+  R y = R(0);
+#pragma unroll 8
+  for (int j = 0; j < 32; ++j) y += col[j * 32] * __shfl_sync(CT_FULL, ri, j);
+  return y;
+}
+
 // Starting guess (extrapolated from the stored solutions, zero without
 // history), its working-precision copy for the gathers, d = D^-1 1 and the
 // guess's total per replica; shifts the history (h2 <- h1, h1 <- the last
@@ -381,6 +490,7 @@ template <class R>
 __global__ void __launch_bounds__(256)
     k_cg_init(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nall,
                           const void* __restrict__ M, const R* __restrict__ Dg, const R* __restrict__ dinv,
+                          const R* __restrict__ binv,
                           const int* __restrict__ type, const int* __restrict__ rep, TypeParams T,
                           double* __restrict__ q, const R* __restrict__ qr, const R* __restrict__ d,
                           R* __restrict__ r, R* __restrict__ y, R* __restrict__ v, R* __restrict__ dqv,
@@ -407,16 +517,22 @@ __global__ void __launch_bounds__(256)
     q[i] = qi;
     double chi_i = rhs ? rhs[i] : T.chi[type[i]];   // rhs: a per-atom chi (adjoint solves)
     R ri = (R)(-chi_i - ((double)Di * qi + (double)hq + dq * (double)hm) - s0);
-    R yi = dinv[i] * ri;
     r[i] = ri;
-    y[i] = yi;
     v[i] = Di * di + hd;
     dqv[i] = R(0);
-    part[0] = yi;
     part[1] = ri;
     part[2] = ri * ri;
     pd[0] = di;
     lm.add(rid, ri, rmax + 2 * 2);
+  }
+  {
+    // y = M^-1 r (the block product takes every lane of the warp)
+    R ri = rid >= 0 ? r[i] : R(0);
+    R yi = binv ? block_apply(binv, i, ri) : (rid >= 0 ? dinv[i] * ri : R(0));
+    if (rid >= 0) {
+      y[i] = yi;
+      part[0] = yi;
+    }
   }
   flush_values<R, 3>(rid, part, cg + ub, CG_STRIDE);
   flush_values<R, 1>(rid, pd, cg + CG_SD, CG_STRIDE);
@@ -503,7 +619,8 @@ __global__ void __launch_bounds__(256)
 // the loop issues no FP64 arithmetic per atom.
 template <class R>
 __global__ void __launch_bounds__(256)
-    k_cg_up(int N, const int* __restrict__ rep, const R* __restrict__ dinv, int* __restrict__ conv,
+    k_cg_up(int N, const int* __restrict__ rep, const R* __restrict__ dinv, const R* __restrict__ binv,
+            int* __restrict__ conv,
             int* __restrict__ iters, int* __restrict__ itp, const R* __restrict__ w, const R* __restrict__ d,
             R* __restrict__ dqv, R* __restrict__ r, R* __restrict__ p, R* __restrict__ s,
             R* __restrict__ y, double* __restrict__ cg, unsigned long long* __restrict__ rmax, int Rn,
@@ -534,10 +651,10 @@ __global__ void __launch_bounds__(256)
   R part[3] = {R(0), R(0), R(0)};   // sum y, sum r, sum r^2
   for (int t = blockIdx.x; (long long)t * 256 < N; t += gridDim.x) {
     int i = t * 256 + (int)threadIdx.x;
-    if (i >= N) break;
-    int rid = rep[i];
-    if (conv[rid]) continue;
-    if (rid != crid) {
+    int rid = i < N ? rep[i] : -1;
+    bool act = rid >= 0 && !conv[rid];
+    R ri = R(0);
+    if (act && rid != crid) {
       if (crid >= 0) {   // a replica boundary in this thread's atoms
         double* o = cg + (size_t)crid * CG_STRIDE + ubuf;
         for (int k = 0; k < 3; ++k) atomicAdd(o + k, (double)part[k]);
@@ -550,20 +667,26 @@ __global__ void __launch_bounds__(256)
       mprev = (R)ldcg(cc + CG_M);
       crid = rid;
     }
-    R zi = y[i] - c * d[i];   // the same z as the matrix pass formed
-    R pi = zi + b * p[i];
-    R si = w[i] + b * s[i];
-    R ri = (r[i] - a * si) - mprev;
-    R yi = dinv[i] * ri;
-    p[i] = pi;
-    s[i] = si;
-    dqv[i] += a * pi;
-    r[i] = ri;
-    y[i] = yi;
-    part[0] += yi;
-    part[1] += ri;
-    part[2] += ri * ri;
-    lm.add(rid, ri, rmax + mb * 2);
+    if (act) {
+      R zi = y[i] - c * d[i];   // the same z as the matrix pass formed
+      R pi = zi + b * p[i];
+      R si = w[i] + b * s[i];
+      ri = (r[i] - a * si) - mprev;
+      p[i] = pi;
+      s[i] = si;
+      dqv[i] += a * pi;
+      r[i] = ri;
+    }
+    // y = M^-1 r: the block product takes every lane of the warp (blocks do
+    // not couple replicas, so a converged replica's lanes enter with r = 0)
+    R yi = binv ? block_apply(binv, i, ri) : (act ? dinv[i] * ri : R(0));
+    if (act) {
+      y[i] = yi;
+      part[0] += yi;
+      part[1] += ri;
+      part[2] += ri * ri;
+      lm.add(rid, ri, rmax + mb * 2);
+    }
   }
   flush_values<R, 3>(crid, part, cg + ubuf, CG_STRIDE);
   lm.finish(rmax + mb * 2);
@@ -642,10 +765,12 @@ template <class R>
 void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, double tol, const double* rhs) {
   k_cg_prep<<<1, 256, 0, st>>>(S.R, S.cg, S.cg_rmax, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
   if (S.N == 0) return;
-  k_cg_extrap<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.q, S.cqh1, S.cqh2, (R*)S.qr, (const R*)S.dinv,
+  const R* binv = S.precond ? (const R*)S.binv : nullptr;
+  k_cg_extrap<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.q, S.cqh1, S.cqh2, (R*)S.qr,
+                                                    (const R*)(S.precond ? S.bsum : S.dinv),
                                                     (R*)S.cd, S.rep, S.cg, S.R, S.cg_hist, S.cg_blocks);
   k_cg_init<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nl, S.nall, S.M, (const R*)S.Dg,
-                                     (const R*)S.dinv, S.type, S.rep, T, S.q, (const R*)S.qr, (const R*)S.cd,
+                                     (const R*)S.dinv, binv, S.type, S.rep, T, S.q, (const R*)S.qr, (const R*)S.cd,
                                      (R*)S.cr, (R*)S.cy, (R*)S.cv, (R*)S.cdq, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
                                      S.cg_blocks, S.cg_active, tol, rhs);
 }
@@ -708,7 +833,8 @@ template <class R>
 void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
   if (S.N == 0) return;
   int grid = stride_grid(S.N, S.nsm, (const void*)k_cg_up<R>);
-  k_cg_up<R><<<grid, 256, 0, st>>>(S.N, S.rep, (const R*)S.dinv, S.cg_conv, S.cg_iters, S.cg_it, (const R*)S.cw,
+  k_cg_up<R><<<grid, 256, 0, st>>>(S.N, S.rep, (const R*)S.dinv, S.precond ? (const R*)S.binv : nullptr,
+                                   S.cg_conv, S.cg_iters, S.cg_it, (const R*)S.cw,
                                    (const R*)S.cd, (R*)S.cdq, (R*)S.cr, (R*)S.cp, (R*)S.cs, (R*)S.cy, S.cg, S.cg_rmax,
                                    S.R, S.cg_blocks, S.cg_active, S.err, cfg.tol, cfg.max_iter, cfg.use_cond,
                                    cfg.cond);
@@ -737,6 +863,8 @@ void launch_copy_q(const DevState& S, cudaStream_t st) {
   k_copy_q<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.q, (R*)S.qr);
 }
 
+template void launch_block_setup<float>(const DevState&, cudaStream_t);
+template void launch_block_setup<double>(const DevState&, cudaStream_t);
 template void launch_cg_begin<float>(const DevState&, const TypeParams&, cudaStream_t, double, const double*);
 template void launch_cg_begin<double>(const DevState&, const TypeParams&, cudaStream_t, double, const double*);
 template void launch_cg_mv<float>(const DevState&, cudaStream_t);

@@ -114,6 +114,10 @@ struct DevState {
   // sizes for launches
   int nsm = 152;
   int mv_batch = 16;            // list entries in flight per thread in the CG matrix pass (tuned)
+  // charge-CG preconditioner: block-Jacobi on 32-atom blocks (1) or Jacobi (0)
+  int precond = 1;
+  void* binv = nullptr;         // Real[ceil(N/32)][32][32]: block inverses, column-major per block
+  void* bsum = nullptr;         // Real[N]: row sums of the block inverses (d = M^-1 1)
 };
 
 struct SolveCfg {
@@ -149,6 +153,7 @@ template <class R> void launch_copy_q(const DevState& S, cudaStream_t st);
 // launch shape for kernels with one thread per atom: resident blocks only,
 // each block a contiguous chunk of atoms (a multiple of its size)
 int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk);
+template <class R> void launch_block_setup(const DevState& S, cudaStream_t st);
 // Parameter gradient of the energy (csrc/grad.cu), in FP32 (fp32) or FP64
 // arithmetic with FP64 sums. grad[0..143] = sum_r wval_r dE_r/dtheta at the
 // current positions and charges. With a direction dir ([N,3], positions)

@@ -62,7 +62,7 @@ class Options(C.Structure):
     _fields_ = [
         ("precision", C.c_int32), ("cg_max_iter", C.c_int32), ("cg_tol", C.c_double),
         ("skin", C.c_double), ("cap_cov", C.c_int32), ("cap_all", C.c_int32),
-        ("device", C.c_int32), ("reserved", C.c_int32),
+        ("device", C.c_int32), ("precond", C.c_int32),
     ]
 
 
@@ -229,7 +229,7 @@ class System:
 
     def __init__(self, params: dict, precision: str = "mixed", skin: float = 0.3,
                  cg_tol: float = 0.0, cg_max_iter: int = 200, device: int = 0,
-                 cap_cov: int = 0, cap_all: int = 0):
+                 cap_cov: int = 0, cap_all: int = 0, precond: str = "block"):
         L = lib()
         self._L = L
         o = Options()
@@ -237,6 +237,9 @@ class System:
         o.precision = PREC_MIXED if precision == "mixed" else PREC_FP64
         o.skin, o.cg_tol, o.cg_max_iter, o.device = skin, cg_tol, cg_max_iter, device
         o.cap_cov, o.cap_all = cap_cov, cap_all
+        if precond not in ("block", "jacobi"):
+            raise ValueError("precond: 'block' or 'jacobi'")
+        o.precond = 0 if precond == "block" else 1
         self._p = params_struct(params)
         h = C.c_void_p()
         rc = L.ctbop_create(C.byref(self._p), C.byref(o), C.byref(h))

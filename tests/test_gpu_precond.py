@@ -1,0 +1,54 @@
+"""The charge solve's two preconditioners (block-Jacobi on 32-atom blocks,
+the default, and Jacobi) reach the same minimiser: charges, energies and
+forces agree to the solve's tolerance, on systems whose blocks straddle
+replica boundaries and whose atom count is not a multiple of 32; and on the
+stepped slab the block preconditioner needs fewer iterations."""
+import numpy as np
+import pytest
+
+from oracle import ctbop_oracle as O
+from paper_1802_07871_gb300 import ctbop
+from paper_1802_07871_gb300 import structures as st
+
+pytestmark = pytest.mark.gpu
+P0 = st.load_params("p0")
+
+
+def _eval(structs, prec, pc):
+    sysm = ctbop.System(P0, precision=prec, precond=pc)
+    sysm.load_replicas(structs)
+    sysm.compute()
+    out = {k: sysm.get(k) for k in ("charges", "energy", "forces", "mu")}
+    out["iters"] = sysm.status()["cg_iters_last"]
+    sysm.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_same_minimiser(prec):
+    structs = [st.sic_3c(1, 4.36, 0.1, seed=11), st.stepped_slab_small(6, 3, 4),
+               st.amorphous_carbon_cluster(45, 2.0, 12), st.sic_3c(2, 4.36, 0.08, seed=13)]
+    assert sum(s.n for s in structs) % 32 != 0
+    a, b = _eval(structs, prec, "block"), _eval(structs, prec, "jacobi")
+    qtol = 1e-9 if prec == "fp64" else 1e-5
+    assert np.max(np.abs(a["charges"] - b["charges"])) < qtol
+    np.testing.assert_allclose(a["energy"], b["energy"], rtol=0, atol=(1e-9 if prec == "fp64" else 1e-5) * 600)
+    rms = np.sqrt(np.mean(b["forces"] ** 2))
+    assert np.max(np.abs(a["forces"] - b["forces"])) < (1e-8 if prec == "fp64" else 1e-4) * rms
+    # and both against the oracle, replica by replica
+    off = np.cumsum([0] + [s.n for s in structs])
+    for r, s in enumerate(structs):
+        o = O.evaluate(s.x, s.types, s.box, s.pbc, P0)
+        assert np.max(np.abs(a["charges"][off[r]:off[r + 1]] - o["q"])) < (1e-8 if prec == "fp64" else 3e-5)
+
+
+def test_fewer_iterations_on_the_slab():
+    s = st.stepped_slab_20k()
+    a, b = _eval([s], "mixed", "block"), _eval([s], "mixed", "jacobi")
+    assert a["iters"] < b["iters"], (a["iters"], b["iters"])
+    assert np.max(np.abs(a["charges"] - b["charges"])) < 1e-5
+
+
+def test_bad_option_is_rejected():
+    with pytest.raises(ValueError):
+        ctbop.System(P0, precond="ilu")
