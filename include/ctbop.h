@@ -196,6 +196,20 @@ int ctbop_compute(ctbop_system* s, uint32_t flags);
  * and redoing the affected steps). */
 int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs);
 
+/* Storage order of the atoms (optional; call after ctbop_set_layout and
+ * before any per-atom setter). order[k] (host, N entries) is the caller's
+ * index of the atom the library stores in slot k; it must permute the atoms
+ * within each replica. Every later per-atom input and output (set_types,
+ * set_positions, set_velocities, set_charges, set_frozen, per-atom
+ * ctbop_get selectors, param_grad's F_ref, removal_energies' candidates)
+ * stays in the caller's order; the library permutes on the device. A
+ * spatially coherent storage order (e.g. along a Morton curve) makes the
+ * charge solve's 32-atom preconditioner blocks compact and its gathers
+ * local. NULL or the identity: storage order = caller order. Errors:
+ * INVALID_ARG (not such a permutation), STATE (no layout, or per-atom
+ * arrays already set). */
+int ctbop_set_order(ctbop_system* s, const int64_t* order);
+
 /* Copy a result out (see CTBOP_GET_*). mem = CTBOP_HOST synchronises. */
 int ctbop_get(ctbop_system* s, int what, void* dst, int mem);
 

@@ -70,6 +70,10 @@ struct ctbop_system {
   int64_t steps = 0, solves = 0;
   // leave-one-out batches of the desorption screening (created on first use)
   ctbop_system* loo = nullptr;
+  // storage order (ctbop_set_order): slot k holds the caller's atom order[k]
+  bool ordered = false;
+  std::vector<int64_t> order, slot;
+  int* d_order = nullptr;
 };
 
 static int fail(ctbop_system* s, int code, const std::string& msg) {
@@ -775,6 +779,7 @@ int ctbop_destroy(ctbop_system* s) {
   cudaSetDevice(s->o.device);
   cudaStreamSynchronize(s->stream);
   if (s->loo) ctbop_destroy(s->loo);
+  if (s->d_order) cudaFree(s->d_order);
   destroy_graphs(s);
   s->atom_buf.release();
   s->list_buf.release();
@@ -814,6 +819,9 @@ int ctbop_set_layout(ctbop_system* s, int32_t n_replicas, const int64_t* atom_of
   s->pbc.assign(3 * n_replicas, 0);
   s->have_layout = true;
   s->have_box = s->have_types = s->have_pos = false;
+  s->ordered = false;
+  s->order.clear();
+  s->slot.clear();
   s->need_rebuild = true;
   s->reps_dirty = true;
   s->alloc_N = -1;
@@ -857,6 +865,62 @@ static int copy_in(ctbop_system* s, void* dst, const void* src, size_t bytes, in
   return CTBOP_OK;
 }
 
+// A per-atom input (caller order) into a storage-order device array.
+static int copy_in_atoms(ctbop_system* s, void* dst, const void* src, int elem_bytes, int mem) {
+  size_t bytes = (size_t)elem_bytes * s->S.N;
+  if (!s->ordered) return copy_in(s, dst, src, bytes, mem);
+  if (!src && bytes) return fail(s, CTBOP_ERR_INVALID_ARG, "null input pointer");
+  if (mem != CTBOP_HOST && mem != CTBOP_DEVICE) return fail(s, CTBOP_ERR_INVALID_ARG, "mem must be CTBOP_HOST or CTBOP_DEVICE");
+  cudaSetDevice(s->o.device);
+  void* tmp = nullptr;
+  CK(cudaMallocAsync(&tmp, std::max<size_t>(bytes, 1), s->stream));
+  CK(cudaMemcpyAsync(tmp, src, bytes, mem == CTBOP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                     s->stream));
+  CK(launch_permute(s->S.N, s->d_order, tmp, dst, elem_bytes, true, s->stream));
+  CK(cudaFreeAsync(tmp, s->stream));
+  if (mem == CTBOP_HOST) CK(cudaStreamSynchronize(s->stream));
+  return CTBOP_OK;
+}
+
+int ctbop_set_order(ctbop_system* s, const int64_t* order) {
+  if (!s) return CTBOP_ERR_INVALID_ARG;
+  if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
+  if (s->have_types || s->have_pos) return fail(s, CTBOP_ERR_STATE, "set the order before the per-atom arrays");
+  cudaSetDevice(s->o.device);
+  const int64_t N = s->S.N;
+  if (!order) {
+    s->ordered = false;
+    s->order.clear();
+    s->slot.clear();
+    return CTBOP_OK;
+  }
+  std::vector<int64_t> slot(N, -1);
+  bool ident = true;
+  for (int r = 0; r < s->R; ++r)
+    for (int64_t k = s->off[r]; k < s->off[r + 1]; ++k) {
+      int64_t a = order[k];
+      if (a < s->off[r] || a >= s->off[r + 1] || slot[a] >= 0)
+        return fail(s, CTBOP_ERR_INVALID_ARG, "order must permute the atoms within each replica");
+      slot[a] = k;
+      ident = ident && a == k;
+    }
+  if (ident) {
+    s->ordered = false;
+    s->order.clear();
+    s->slot.clear();
+    return CTBOP_OK;
+  }
+  std::vector<int> o32(order, order + N);
+  if (s->d_order) cudaFree(s->d_order);
+  s->d_order = nullptr;
+  CK(cudaMalloc(&s->d_order, sizeof(int) * std::max<int64_t>(N, 1)));
+  CK(sync_copy(s, s->d_order, o32.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
+  s->order.assign(order, order + N);
+  s->slot = std::move(slot);
+  s->ordered = true;
+  return CTBOP_OK;
+}
+
 int ctbop_set_types(ctbop_system* s, const int32_t* types, int mem) {
   if (!s) return CTBOP_ERR_INVALID_ARG;
   if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
@@ -864,7 +928,7 @@ int ctbop_set_types(ctbop_system* s, const int32_t* types, int mem) {
   if (mem == CTBOP_HOST && types)
     for (size_t i = 0; i < N; ++i)
       if (types[i] != 0 && types[i] != 1) return fail(s, CTBOP_ERR_INVALID_ARG, "types must be 0 (Si) or 1 (C)");
-  int rc = copy_in(s, s->S.type, types, sizeof(int) * N, mem);
+  int rc = copy_in_atoms(s, s->S.type, types, sizeof(int), mem);
   if (rc) return rc;
   s->have_types = true;
   s->need_rebuild = true;
@@ -874,7 +938,7 @@ int ctbop_set_types(ctbop_system* s, const int32_t* types, int mem) {
 int ctbop_set_positions(ctbop_system* s, const double* x, int mem) {
   if (!s) return CTBOP_ERR_INVALID_ARG;
   if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
-  int rc = copy_in(s, s->S.x, x, sizeof(double) * 3 * s->S.N, mem);
+  int rc = copy_in_atoms(s, s->S.x, x, 3 * sizeof(double), mem);
   if (rc) return rc;
   // new positions break the time series the CG start extrapolates: keep
   // only the last solution as the starting guess
@@ -890,13 +954,13 @@ int ctbop_set_positions(ctbop_system* s, const double* x, int mem) {
 int ctbop_set_velocities(ctbop_system* s, const double* v, int mem) {
   if (!s) return CTBOP_ERR_INVALID_ARG;
   if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
-  return copy_in(s, s->S.v, v, sizeof(double) * 3 * s->S.N, mem);
+  return copy_in_atoms(s, s->S.v, v, 3 * sizeof(double), mem);
 }
 
 int ctbop_set_charges(ctbop_system* s, const double* q, int mem) {
   if (!s) return CTBOP_ERR_INVALID_ARG;
   if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
-  int rc = copy_in(s, s->S.q, q, sizeof(double) * s->S.N, mem);
+  int rc = copy_in_atoms(s, s->S.q, q, sizeof(double), mem);
   if (rc) return rc;
   if (s->mixed) launch_copy_q<float>(s->S, s->stream);
   else launch_copy_q<double>(s->S, s->stream);
@@ -907,7 +971,7 @@ int ctbop_set_charges(ctbop_system* s, const double* q, int mem) {
 int ctbop_set_frozen(ctbop_system* s, const uint8_t* frozen, int mem) {
   if (!s) return CTBOP_ERR_INVALID_ARG;
   if (!s->have_layout) return fail(s, CTBOP_ERR_STATE, "set_layout first");
-  return copy_in(s, s->S.frozen, frozen, s->S.N, mem);
+  return copy_in_atoms(s, s->S.frozen, frozen, 1, mem);
 }
 
 int ctbop_set_total_charge(ctbop_system* s, const double* Q) {
@@ -1042,6 +1106,13 @@ int ctbop_get(ctbop_system* s, int what, void* dst, int mem) {
     if (s->mixed) launch_coordination<float>(S, s->Pf, tmp, s->stream);
     else launch_coordination<double>(S, s->Pd, tmp, s->stream);
     CK(cudaGetLastError());
+    if (s->ordered) {
+      double* tmp2 = nullptr;
+      CK(cudaMallocAsync(&tmp2, sizeof(double) * N, s->stream));
+      CK(launch_permute((int)N, s->d_order, tmp, tmp2, 8, false, s->stream));
+      CK(cudaFreeAsync(tmp, s->stream));
+      tmp = tmp2;
+    }
     CK(cudaMemcpyAsync(dst, tmp, sizeof(double) * N, kind, s->stream));
     CK(cudaFreeAsync(tmp, s->stream));
     if (mem == CTBOP_HOST) CK(cudaStreamSynchronize(s->stream));
@@ -1063,7 +1134,18 @@ int ctbop_get(ctbop_system* s, int what, void* dst, int mem) {
     default: return fail(s, CTBOP_ERR_INVALID_ARG, "unknown selector");
   }
   if (width == 0) return CTBOP_OK;
-  CK(cudaMemcpy2DAsync(dst, width, src, pitch, width, rows, kind, s->stream));
+  const bool per_atom = what == CTBOP_GET_FORCES || what == CTBOP_GET_POSITIONS || what == CTBOP_GET_VELOCITIES ||
+                        what == CTBOP_GET_CHARGES || what == CTBOP_GET_E_ATOM;
+  if (per_atom && s->ordered) {
+    // back to the caller's order
+    void* tmp = nullptr;
+    CK(cudaMallocAsync(&tmp, width, s->stream));
+    CK(launch_permute((int)N, s->d_order, src, tmp, (int)(width / N), false, s->stream));
+    CK(cudaMemcpyAsync(dst, tmp, width, kind, s->stream));
+    CK(cudaFreeAsync(tmp, s->stream));
+  } else {
+    CK(cudaMemcpy2DAsync(dst, width, src, pitch, width, rows, kind, s->stream));
+  }
   if (mem == CTBOP_HOST) CK(cudaStreamSynchronize(s->stream));
   return CTBOP_OK;
 }
@@ -1277,6 +1359,13 @@ int ctbop_param_grad(ctbop_system* s, const double* w_E, const double* E_ref, co
   static_assert(offsetof(ctbop_params, E0) == PG_E0 * sizeof(double), "layout");
   static_assert(offsetof(ctbop_params, k_e) == PG_KE * sizeof(double), "layout");
   double* out = reinterpret_cast<double*>(dtheta);
+  std::vector<double> Fs;
+  if (F_ref && s->ordered) {   // the targets in storage order
+    Fs.resize((size_t)3 * s->S.N);
+    for (int64_t k = 0; k < s->S.N; ++k)
+      for (int d = 0; d < 3; ++d) Fs[3 * k + d] = F_ref[3 * s->order[k] + d];
+    F_ref = Fs.data();
+  }
   return s->mixed ? param_grad_impl<float>(s, w_E, E_ref, w_F, F_ref, loss, out)
                   : param_grad_impl<double>(s, w_E, E_ref, w_F, F_ref, loss, out);
 }
@@ -1323,10 +1412,11 @@ int ctbop_removal_energies(ctbop_system* s, int64_t n_cand, const int64_t* cand,
   struct Job { int64_t c; int r; int n; int drop; };
   std::vector<Job> jobs;
   for (int64_t c = 0; c < n_cand; ++c) {
-    int r = (int)(std::upper_bound(s->off.begin(), s->off.end(), cand[c]) - s->off.begin()) - 1;
+    int64_t k = s->ordered ? s->slot[cand[c]] : cand[c];   // storage slot
+    int r = (int)(std::upper_bound(s->off.begin(), s->off.end(), k) - s->off.begin()) - 1;
     int n = (int)(s->off[r + 1] - s->off[r]);
-    if (n == 1) dE[c] = s->T.E0[types[cand[c]]] - E[r];   // nothing remains: E = 0
-    else jobs.push_back({c, r, n, (int)(cand[c] - s->off[r])});
+    if (n == 1) dE[c] = s->T.E0[types[k]] - E[r];   // nothing remains: E = 0
+    else jobs.push_back({c, r, n, (int)(k - s->off[r])});
   }
   std::stable_sort(jobs.begin(), jobs.end(), [](const Job& a, const Job& b) { return a.r < b.r; });
   const int64_t budget = max_atoms > 0 ? max_atoms : ((int64_t)1 << 22);

@@ -184,6 +184,10 @@ void launch_fire_move(const DevState& S, const TypeParams& T, const double* fire
 template <class R>
 void launch_rings(const DevState& S, double bond_cut, int max_size, ::ctbop_ring* out, long long cap,
                   unsigned long long* count, cudaStream_t st);
+// Storage order (csrc/order.cu): dst[k] = src[order[k]] (to_storage) or
+// dst[order[k]] = src[k], elements of 1, 4, 8 or 24 bytes.
+cudaError_t launch_permute(int N, const int* order, const void* src, void* dst, int elem_bytes, bool to_storage,
+                           cudaStream_t st);
 // Desorption screening (csrc/screen.cu): covalent coordination per atom
 // (neighbours within S of the pair) and the leave-one-out gather, one item
 // per batch replica: source replica [src_off, src_off + src_n) without its

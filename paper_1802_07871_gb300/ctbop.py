@@ -34,7 +34,7 @@ EXPORTS = (
     "ctbop_set_positions", "ctbop_set_velocities", "ctbop_set_charges", "ctbop_set_frozen",
     "ctbop_set_total_charge", "ctbop_compute", "ctbop_step", "ctbop_get", "ctbop_status",
     "ctbop_profile_steps", "ctbop_energy_noalloc", "ctbop_param_grad", "ctbop_set_params", "ctbop_set_thermostat",
-    "ctbop_removal_energies", "ctbop_minimize", "ctbop_rings",
+    "ctbop_removal_energies", "ctbop_minimize", "ctbop_rings", "ctbop_set_order",
 )
 # one record of ctbop_rings (struct ctbop_ring)
 RING_DTYPE = np.dtype([("replica", "<i4"), ("size", "<i4"), ("centre", "<f8", 3), ("orientation", "<f8")])
@@ -115,6 +115,7 @@ def lib():
         "ctbop_removal_energies": ([vp, C.c_int64, vp, C.c_int64, vp], C.c_int),
         "ctbop_minimize": ([vp, C.c_int64, C.c_double, C.c_double, C.c_double, vp, vp], C.c_int),
         "ctbop_rings": ([vp, C.c_double, C.c_int32, C.c_int64, vp, vp], C.c_int),
+        "ctbop_set_order": ([vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -159,6 +160,23 @@ def params_struct(d: dict) -> Params:
         P.gamma_c[t], P.mass[t] = co["gamma"][t], d["mass"][t]
     P.r_coul, P.k_e = co["r_coul"], co["k_e"]
     return P
+
+
+def morton_order(x, box, pbc, cell: float = 2.5) -> np.ndarray:
+    """Indices of the atoms along a Morton (Z-order) curve over a grid of
+    `cell` A cells (periodic axes wrapped into the box first): neighbouring
+    indices are then neighbouring atoms. A storage order for
+    System.set_order."""
+    x = np.asarray(x, float).copy()
+    box, pbc = np.asarray(box, float), np.asarray(pbc, bool)
+    x = np.where(pbc, np.mod(x, np.where(pbc, box, 1.0)), x)
+    c = np.floor((x - x.min(axis=0)) / cell).astype(np.int64) if len(x) else np.zeros((0, 3), np.int64)
+    c = np.clip(c, 0, (1 << 20) - 1)
+    key = np.zeros(len(x), dtype=np.int64)
+    for b in range(20):
+        for d in range(3):
+            key |= ((c[:, d] >> b) & 1) << (3 * b + d)
+    return np.argsort(key, kind="stable")
 
 
 def params_vector(P: Params) -> np.ndarray:
@@ -359,10 +377,21 @@ class System:
         Q = np.ascontiguousarray(np.atleast_1d(Q), dtype=np.float64)
         self._check(self._L.ctbop_set_total_charge(self._h, Q.ctypes.data_as(C.c_void_p)), "set_total_charge")
 
-    def load(self, structure, velocities=None, charges=None):
-        """Set layout, box, types, positions and frozen mask of one structure."""
+    def set_order(self, order):
+        """Storage order (after set_layout, before the per-atom arrays):
+        order[k] is the caller's index of the atom stored in slot k. Inputs
+        and outputs stay in the caller's order."""
+        o = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
+        self._check(self._L.ctbop_set_order(self._h, None if o is None else o.ctypes.data_as(C.c_void_p)),
+                    "set_order")
+
+    def load(self, structure, velocities=None, charges=None, order="morton"):
+        """Set layout, box, types, positions and frozen mask of one structure
+        (stored along a Morton curve unless order=None)."""
         s = structure
         self.set_layout([0, s.n])
+        if order == "morton":
+            self.set_order(morton_order(s.x, s.box, s.pbc))
         self.set_box(s.box, s.pbc)
         self.set_types(s.types)
         self.set_positions(s.x)
@@ -372,9 +401,13 @@ class System:
         if charges is not None:
             self.set_charges(charges)
 
-    def load_replicas(self, structures):
+    def load_replicas(self, structures, order="morton"):
+        """Set the layout and every array of a batch of structures (each
+        replica stored along a Morton curve unless order=None)."""
         off = np.concatenate([[0], np.cumsum([s.n for s in structures])])
         self.set_layout(off)
+        if order == "morton":
+            self.set_order(np.concatenate([o + morton_order(s.x, s.box, s.pbc) for o, s in zip(off, structures)]))
         self.set_box(np.array([s.box for s in structures]), np.array([s.pbc for s in structures]))
         self.set_types(np.concatenate([s.types for s in structures]))
         self.set_positions(np.concatenate([s.x for s in structures]))

@@ -129,7 +129,11 @@ def test_device_pointer_path_matches_host():
     torch = pytest.importorskip("torch")
     from paper_1802_07871_gb300 import ctbop
     s = st.sic_3c(2, 4.36, 0.1, seed=3)
-    gh = gpu_eval(s, P0, "mixed")
+    ref = ctbop.System(P0, precision="mixed")
+    ref.load(s, order=None)                # the storage order the device path below uses
+    ref.compute()
+    gh = {"forces": ref.get("forces")}
+    ref.close()
     sysm = ctbop.System(P0, precision="mixed")
     sysm.set_stream(torch.cuda.current_stream().cuda_stream)
     sysm.set_layout([0, s.n])
