@@ -319,6 +319,8 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->rep_buf, &S.scan_tmp, 1040));
   CK(dalloc(s->rep_buf, &S.flag_rebuild, 1));
   CK(dalloc(s->rep_buf, &S.rebuild_count, 1));
+  CK(dalloc(s->rep_buf, &S.precond_epoch, 1));
+  CK(cudaMemsetAsync(S.precond_epoch, 0xff, sizeof(long long), s->stream));   // -1: form at the first solve
   CK(dalloc(s->rep_buf, &S.maxcnt, 3));
   CK(dalloc(s->rep_buf, &S.stiff_n, 1));
   CK(zero_async(s, S.stiff_n, sizeof(int)));
@@ -618,7 +620,10 @@ static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double 
     if (!rc) rc = timed(1, 12, [&] { launch_zero_acc(S, st); launch_rebuild<Rr>(S, P, st); });
     if (!rc) rc = timed(2, 1, [&] { launch_bond<Rr>(S, P, st); });
     if (!rc) rc = timed(3, 1, [&] { launch_assemble<Rr>(S, P, s->T, st); });
-    if (!rc) rc = timed(4, 3, [&] { launch_cg_begin<Rr>(S, s->T, st, cg_tol(s)); });
+    if (!rc) rc = timed(4, S.precond ? 5 : 3, [&] {
+      if (S.precond) launch_block_setup<Rr>(S, st);
+      launch_cg_begin<Rr>(S, s->T, st, cg_tol(s));
+    });
     for (int it = 0; it < s->o.cg_max_iter && !rc; ++it) {
       CK(cudaMemcpyAsync(s->h_int, S.cg_active, sizeof(int), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));

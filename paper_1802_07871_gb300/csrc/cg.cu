@@ -223,11 +223,20 @@ __global__ void k_cg_prep(int R, double* __restrict__ cg, unsigned long long* __
 // of different replicas in one block have exactly zero coupling, which the
 // factorisation keeps. A block that is not numerically positive definite
 // falls back to its Jacobi inverse. Also writes d = M^-1 1 (row sums).
+//
+// The inverses are formed again only after a list rebuild (the rebuild count
+// differs from the one they were formed at; k_precond_mark records it once
+// every block is done): between rebuilds no atom moves more than half the
+// skin, H drifts by a few per cent, and a slightly stale M^-1 is still a
+// fixed symmetric positive definite preconditioner for the whole solve, so
+// only the iteration count can change, never the converged result.
 template <class R>
 __global__ void __launch_bounds__(128)
     k_block_setup(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nall,
                   const void* __restrict__ M, const R* __restrict__ Dg, R* __restrict__ binv,
-                  R* __restrict__ bsum) {
+                  R* __restrict__ bsum, const long long* __restrict__ rebuilds,
+                  const long long* __restrict__ epoch) {
+  if (*rebuilds == *epoch) return;
   __shared__ R sh[4][32][33];
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int base = (blockIdx.x * 4 + warp) * 32;
@@ -239,7 +248,19 @@ __global__ void __launch_bounds__(128)
   if (i < N) {
     MatView<R> mv(nl, M);
     int na = nall[i];
-    for (int e = 0; e < na; ++e) {
+    int e = 0;
+    for (; e + 8 <= na; e += 8) {   // eight entries in flight
+      int jj[8];
+      R vv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) mv.get((size_t)(e + u) * ld + i, jj[u], vv[u]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        unsigned dj = (unsigned)(jj[u] - base);
+        if (dj < 32u) A[lane][dj] += vv[u];
+      }
+    }
+    for (; e < na; ++e) {
       int j;
       R v;
       mv.get((size_t)e * ld + i, j, v);
@@ -301,12 +322,17 @@ __global__ void __launch_bounds__(128)
   if (i < N) bsum[i] = rs;
 }
 
+__global__ void k_precond_mark(const long long* __restrict__ rebuilds, long long* __restrict__ epoch) {
+  *epoch = *rebuilds;
+}
+
 template <class R>
 void launch_block_setup(const DevState& S, cudaStream_t st) {
   if (S.N == 0) return;
   int nb = (S.N + 31) / 32;
   k_block_setup<R><<<(nb + 3) / 4, 128, 0, st>>>(S.N, S.ld, S.nl, S.nall, S.M, (const R*)S.Dg, (R*)S.binv,
-                                                 (R*)S.bsum);
+                                                 (R*)S.bsum, S.rebuild_count, S.precond_epoch);
+  k_precond_mark<<<1, 1, 0, st>>>(S.rebuild_count, S.precond_epoch);
 }
 
 // y = M_b^-1 r for the warp's block: every lane of a full warp, i = 32b +

@@ -118,6 +118,7 @@ struct DevState {
   int precond = 1;
   void* binv = nullptr;         // Real[ceil(N/32)][32][32]: block inverses, column-major per block
   void* bsum = nullptr;         // Real[N]: row sums of the block inverses (d = M^-1 1)
+  long long* precond_epoch = nullptr;   // rebuild count the block inverses were formed at (-1: never)
 };
 
 struct SolveCfg {
