@@ -340,9 +340,12 @@ void launch_block_setup(const DevState& S, cudaStream_t st) {
 template <class R>
 __device__ inline R block_apply(const R* __restrict__ binv, int i, R ri) {
   const R* col = binv + (size_t)(i >> 5) * 1024 + (i & 31);
+  R b[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) b[j] = __ldg(col + j * 32);   // all 32 loads in flight
   R y = R(0);
-#pragma unroll 8
-  for (int j = 0; j < 32; ++j) y += col[j * 32] * __shfl_sync(CT_FULL, ri, j);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) y += b[j] * __shfl_sync(CT_FULL, ri, j);
   return y;
 }
 
