@@ -134,9 +134,10 @@ def peaks():
 # DRAM traffic of one k_cg_mv launch from one `ncu --set full` capture on
 # the 251,366-atom stepped slab (dram__bytes_read.sum + dram__bytes_write.sum)
 # and the list entries of that launch. Traffic grows with the entries
-# (it is 0.98 x the algorithmic bytes there), so a full launch is scaled by
-# its entry count. Reset to None when the kernel changes.
-MV_TRAFFIC_CAPTURE = {"bytes": 461.367040e6 + 3.391232e6, "entries": 251366 * 226.5986569384881}
+# (1.02 x the algorithmic bytes there, atoms stored along a Morton curve), so
+# a full launch is scaled by its entry count. Reset to None when the kernel
+# changes.
+MV_TRAFFIC_CAPTURE = {"bytes": 467.825920e6 + 3.875072e6, "entries": 251366 * 226.5986569384881}
 
 
 def cg_matvec_bytes(n_atoms, entries, rs):
