@@ -137,6 +137,8 @@ typedef struct ctbop_stats {
     int32_t cg_mv_batch;      /* list entries in flight per thread in the CG matrix pass (autotuned) */
     int32_t reserved0;
     double  cg_mv_ms[3];      /* ms per matrix pass of the depths 4, 8, 16 at the last tuning (0: not timed) */
+    double  mean_mat;         /* mean stored charge-matrix entries per atom (the entries a matrix pass
+                                 streams: those inside the charge cutoff under the mixed policy) */
 } ctbop_stats;
 
 typedef struct ctbop_system ctbop_system;

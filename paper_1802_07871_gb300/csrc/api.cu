@@ -62,6 +62,7 @@ struct ctbop_system {
   // matrix-pass autotuning: the lists it was tuned on, and the timings
   int tuned_N = -1, tuned_cap = -1;
   float mv_ms[3] = {0.f, 0.f, 0.f};
+  bool tune_pending = false;
   double g_step_dt = -1.0;
   bool use_graph = true;
   // pinned host scratch
@@ -292,6 +293,12 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->atom_buf, &S.cqh2, (size_t)N));
   CK(dalloc(s->atom_buf, &S.ncov, (size_t)N));
   CK(dalloc(s->atom_buf, &S.nall, (size_t)N));
+  if (s->mixed) {
+    CK(dalloc(s->atom_buf, &S.nmat, (size_t)N));
+    CK(zero_async(s, S.nmat, sizeof(int) * (size_t)N));
+  } else {
+    S.nmat = S.nall;   // FP64 keeps the coefficients aligned with the list
+  }
   CK(zero_async(s, S.v, sizeof(double) * 3 * (size_t)N));
   CK(zero_async(s, S.F, sizeof(double) * 3 * (size_t)N));
   CK(zero_async(s, S.q, sizeof(double) * (size_t)N));
@@ -541,18 +548,14 @@ static int ensure_lists(ctbop_system* s) {
   }
   s->need_rebuild = false;
   CK(cudaMemsetAsync(S.err, 0, sizeof(unsigned), s->stream));
-  // choose the matrix pass's depth for these lists (CTBOP_MV_BATCH = 4, 8
-  // or 16 forces one)
+  // the matrix pass's depth for these lists (CTBOP_MV_BATCH = 4, 8 or 16
+  // forces one): chosen by timing on the first solve's assembled matrix
   if (S.N > 0 && (s->tuned_N != S.N || s->tuned_cap != S.cap_all)) {
     int before = S.mv_batch;
     const char* fb = getenv("CTBOP_MV_BATCH");
     int forced = fb ? atoi(fb) : 0;
-    if (forced == 4 || forced == 8 || forced == 16) {
-      S.mv_batch = forced;
-    } else {
-      cudaError_t e = s->mixed ? tune_cg_mv<float>(S, s->stream, s->mv_ms) : tune_cg_mv<double>(S, s->stream, s->mv_ms);
-      if (e != cudaSuccess) return fail(s, CTBOP_ERR_CUDA, std::string("matrix-pass tuning: ") + cudaGetErrorString(e));
-    }
+    if (forced == 4 || forced == 8 || forced == 16) S.mv_batch = forced;
+    else s->tune_pending = true;
     s->tuned_N = S.N;
     s->tuned_cap = S.cap_all;
     if (S.mv_batch != before) destroy_graphs(s);
@@ -579,6 +582,20 @@ static int prepare(ctbop_system* s) {
 template <class Rr>
 static int eval_t(ctbop_system* s, const PotParams<Rr>& P, uint32_t flags) {
   bool solve = !(flags & CTBOP_FIXED_CHARGES);
+  if (solve && s->tune_pending) {
+    // this evaluation runs directly; its assembled matrix then times the
+    // matrix pass's depths (the solver state is kept across the timing)
+    int rc = run_direct<Rr>(s, P, false, 0.0, true);
+    if (rc) return rc;
+    int before = s->S.mv_batch;
+    cudaError_t e = tune_cg_mv<Rr>(s->S, s->stream, s->mv_ms);
+    if (e != cudaSuccess) return fail(s, CTBOP_ERR_CUDA, std::string("matrix-pass tuning: ") + cudaGetErrorString(e));
+    s->tune_pending = false;
+    if (s->S.mv_batch != before) destroy_graphs(s);
+    s->solves++;
+    s->have_forces = true;
+    return CTBOP_OK;
+  }
   if (s->use_graph && solve) {
     if (!s->g_eval) {
       int rc = capture_graph<Rr>(s, P, false, 0.0, &s->g_eval);
@@ -1200,13 +1217,15 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   st->max_cov = mc[0];
   st->max_all = mc[2];
   if (S.N > 0 && S.ncov) {
-    std::vector<int> a(S.N), b(S.N);
+    std::vector<int> a(S.N), b(S.N), c(S.N);
     CK(sync_copy(s, a.data(), S.ncov, sizeof(int) * S.N, cudaMemcpyDeviceToHost));
     CK(sync_copy(s, b.data(), S.nall, sizeof(int) * S.N, cudaMemcpyDeviceToHost));
-    double sa = 0, sb = 0;
-    for (int i = 0; i < S.N; ++i) { sa += a[i]; sb += b[i]; }
+    CK(sync_copy(s, c.data(), S.nmat, sizeof(int) * S.N, cudaMemcpyDeviceToHost));
+    double sa = 0, sb = 0, sc = 0;
+    for (int i = 0; i < S.N; ++i) { sa += a[i]; sb += b[i]; sc += c[i]; }
     st->mean_cov = sa / S.N;
     st->mean_all = sb / S.N;
+    st->mean_mat = sc / S.N;
   }
   if (bits & CT_ERR_NONFINITE) return fail(s, CTBOP_ERR_NONFINITE, "non-finite energy, force or position");
   if (bits & CT_ERR_CG_MAXITER) return fail(s, CTBOP_ERR_CG_NOT_CONVERGED, "charge CG reached max_iter");

@@ -232,7 +232,7 @@ __global__ void k_cg_prep(int R, double* __restrict__ cg, unsigned long long* __
 // only the iteration count can change, never the converged result.
 template <class R>
 __global__ void __launch_bounds__(128)
-    k_block_setup(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nall,
+    k_block_setup(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nmat,
                   const void* __restrict__ M, const R* __restrict__ Dg, R* __restrict__ binv,
                   R* __restrict__ bsum, const long long* __restrict__ rebuilds,
                   const long long* __restrict__ epoch) {
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(128)
   int i = base + lane;
   if (i < N) {
     MatView<R> mv(nl, M);
-    int na = nall[i];
+    int na = nmat[i];
     int e = 0;
     for (; e + 8 <= na; e += 8) {   // eight entries in flight
       int jj[8];
@@ -330,7 +330,7 @@ template <class R>
 void launch_block_setup(const DevState& S, cudaStream_t st) {
   if (S.N == 0) return;
   int nb = (S.N + 31) / 32;
-  k_block_setup<R><<<(nb + 3) / 4, 128, 0, st>>>(S.N, S.ld, S.nl, S.nall, S.M, (const R*)S.Dg, (R*)S.binv,
+  k_block_setup<R><<<(nb + 3) / 4, 128, 0, st>>>(S.N, S.ld, S.nl, S.nmat, S.M, (const R*)S.Dg, (R*)S.binv,
                                                  (R*)S.bsum, S.rebuild_count, S.precond_epoch);
   k_precond_mark<<<1, 1, 0, st>>>(S.rebuild_count, S.precond_epoch);
 }
@@ -517,7 +517,7 @@ __device__ inline void row_sum_stream3(int i, int na, int ld, const int2* __rest
 // starts the accumulated one, so mu = -(mean of stored r + shift) holds.
 template <class R>
 __global__ void __launch_bounds__(256)
-    k_cg_init(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nall,
+    k_cg_init(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nmat,
                           const void* __restrict__ M, const R* __restrict__ Dg, const R* __restrict__ dinv,
                           const R* __restrict__ binv,
                           const int* __restrict__ type, const int* __restrict__ rep, TypeParams T,
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(256)
     double mp = ldcg(cc + CG_MU);
     double s0 = isfinite(mp) ? -mp : 0.0;
     R hq, hd, hm;
-    row_sum_stream3<R, 8>(i, nall[i], ld, nl, M, qr, d, hq, hd, hm);
+    row_sum_stream3<R, 8>(i, nmat[i], ld, nl, M, qr, d, hq, hd, hm);
     R Di = Dg[i], di = d[i];
     // the guess shifted by dq: H (q0 + dq 1) = D (q0 + dq) + sum M q0_j + dq sum M
     double qi = q[i] + dq;
@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(256)
 // starts near the tolerance then diverge).
 template <class R, int B>
 __global__ void __launch_bounds__(256)
-    k_cg_mv(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nall, const void* __restrict__ M,
+    k_cg_mv(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nmat, const void* __restrict__ M,
             const R* __restrict__ Dg, const int* __restrict__ rep, const int* __restrict__ conv,
             const int* __restrict__ itp, const R* __restrict__ y, const R* __restrict__ d, const R* __restrict__ v,
             const R* __restrict__ r, R* __restrict__ w, double* __restrict__ cg, int Rn,
@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(256)
     const double* cc = cg + (size_t)rid * CG_STRIDE;
     R c = (R)ldcg(cc + CG_C);
     R m = (R)ldcg(cc + CG_M);   // mean of the stored r
-    R hy = row_sum_stream<R, B>(i, nall[i], ld, nl, M, y);
+    R hy = row_sum_stream<R, B>(i, nmat[i], ld, nl, M, y);
     R yi = y[i];
     R zi = yi - c * d[i];
     R wi = Dg[i] * yi + hy - c * v[i];
@@ -798,7 +798,7 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
   k_cg_extrap<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.q, S.cqh1, S.cqh2, (R*)S.qr,
                                                     (const R*)(S.precond ? S.bsum : S.dinv),
                                                     (R*)S.cd, S.rep, S.cg, S.R, S.cg_hist, S.cg_blocks);
-  k_cg_init<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nl, S.nall, S.M, (const R*)S.Dg,
+  k_cg_init<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nl, S.nmat, S.M, (const R*)S.Dg,
                                      (const R*)S.dinv, binv, S.type, S.rep, T, S.q, (const R*)S.qr, (const R*)S.cd,
                                      (R*)S.cr, (R*)S.cy, (R*)S.cv, (R*)S.cdq, S.cg, S.cg_rmax, S.R, S.cg_conv, S.cg_iters,
                                      S.cg_blocks, S.cg_active, tol, rhs);
@@ -806,7 +806,7 @@ void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, do
 
 template <class R, int B>
 static void launch_cg_mv_b(const DevState& S, cudaStream_t st) {
-  k_cg_mv<R, B><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nl, S.nall, S.M, (const R*)S.Dg, S.rep,
+  k_cg_mv<R, B><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.ld, S.nl, S.nmat, S.M, (const R*)S.Dg, S.rep,
                                                    S.cg_conv, S.cg_it, (const R*)S.cy, (const R*)S.cd,
                                                    (const R*)S.cv, (const R*)S.cr, (R*)S.cw, S.cg, S.R,
                                                    S.cg_blocks, S.cg_active);
@@ -838,6 +838,28 @@ cudaError_t tune_cg_mv(DevState& S, cudaStream_t st, float* ms_out) {
   if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
   float best = 1e30f;
   int pick = 16;
+  // the solver state the timing runs overwrite (per-replica scalars and
+  // maxima, convergence flags, counters), kept and put back
+  const size_t ncg = (size_t)S.R * CG_STRIDE * sizeof(double), nrm = (size_t)S.R * 6 * sizeof(unsigned long long);
+  const size_t nri = (size_t)S.R * sizeof(int);
+  char* keep = nullptr;
+  e = cudaMallocAsync(&keep, ncg + nrm + 2 * nri + 5 * sizeof(int), st);
+  auto save = [&](bool back) {
+    char* p = keep;
+    auto mv = [&](void* dev, size_t n) {
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(back ? dev : p, back ? p : dev, n, cudaMemcpyDeviceToDevice, st);
+      p += n;
+    };
+    mv(S.cg, ncg);
+    mv(S.cg_rmax, nrm);
+    mv(S.cg_conv, nri);
+    mv(S.cg_iters, nri);
+    mv(S.cg_it, sizeof(int));
+    mv(S.cg_active, sizeof(int));
+    mv(S.cg_blocks, 3 * sizeof(int));
+  };
+  save(false);
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
     S.mv_batch = depth[k];
     k_cg_prep<<<1, 256, 0, st>>>(S.R, S.cg, S.cg_rmax, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
@@ -852,6 +874,8 @@ cudaError_t tune_cg_mv(DevState& S, cudaStream_t st, float* ms_out) {
     if (ms_out) ms_out[k] = ms;
     if (ms < best) { best = ms; pick = depth[k]; }
   }
+  save(true);
+  if (keep) cudaFreeAsync(keep, st);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   S.mv_batch = pick;

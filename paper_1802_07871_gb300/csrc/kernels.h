@@ -84,6 +84,8 @@ struct DevState {
   // lists
   int2* nl = nullptr;           // [cap_all*ld] (j, code) list entries, column-major
   int *ncov = nullptr, *nall = nullptr, *rev = nullptr;
+  int* nmat = nullptr;          // [N] stored charge-matrix entries per atom: the list entries inside the
+                                // charge cutoff (FP32, compacted), or nall (FP64)
   int2* lst = nullptr;          // [N][cap_all] row-major build scratch (j, code)
   // stiff covalent bonds (FP32 path): a queue of bond ids i * cap_cov + e and,
   // per bond, the FP64-evaluated pair term (dE/dr, energy) as float2

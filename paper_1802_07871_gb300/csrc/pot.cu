@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(256)
                const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
                 const int* __restrict__ ncov, const int* __restrict__ nall,
                const int* __restrict__ rev, const typename Vec4<R>::T* __restrict__ bo, PotParams<R> P,
-               TypeParams T, void* __restrict__ M, R* __restrict__ Dg, R* __restrict__ dinv) {
+               TypeParams T, void* __restrict__ M, R* __restrict__ Dg, R* __restrict__ dinv,
+               int* __restrict__ nmat) {
   using R4 = typename Vec4<R>::T;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -251,7 +252,11 @@ __global__ void __launch_bounds__(256)
     if (j == i) selfm += m;
     mat_store(M, off + i, j, m);
   }
-  // the rest: K only, streamed
+  // the rest: K only, streamed. FP32 stores only the entries inside the
+  // charge cutoff (those beyond it, in the list's skin, have K = 0), packed
+  // after the covalent ones: about 10% fewer bytes for every matrix pass.
+  // FP64 keeps its coefficients aligned with the list (its index stream).
+  int em = nc;
   const R gs_i0 = P.gshield3[ti * 2], gs_i1 = P.gshield3[ti * 2 + 1];
   int jn[PB], cn[PB];
 #pragma unroll
@@ -284,10 +289,16 @@ __global__ void __launch_bounds__(256)
         R r2 = rx * rx + ry * ry + rz * rz;
         R m = coul_K_r2<R>(r2, uj[k].w != R(0) ? gs_i1 : gs_i0, P.inv_rcoul, P.ke);
         if (jc[k] == i) selfm += m;
-        mat_store(M, (size_t)(e + k) * ld + i, jc[k], m);
+        if (sizeof(R) == 8) {
+          mat_store(M, (size_t)(e + k) * ld + i, jc[k], m);
+        } else if (m != R(0)) {
+          mat_store(M, (size_t)em * ld + i, jc[k], m);
+          ++em;
+        }
       }
     }
   }
+  if (sizeof(R) == 4) nmat[i] = em;
   R D = (R)(2.0 * T.J[ti]) + R(2) * wsum;
   Dg[i] = D;
   dinv[i] = R(1) / (D + selfm);
@@ -635,7 +646,7 @@ void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams&
   if (S.N == 0) return;
   k_assemble<R><<<(S.N + 255) / 256, 256, 0, st>>>(
       S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
-      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, S.M, (R*)S.Dg, (R*)S.dinv);
+      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, S.M, (R*)S.Dg, (R*)S.dinv, S.nmat);
 }
 
 template <class R>

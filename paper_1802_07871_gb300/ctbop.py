@@ -73,6 +73,7 @@ class Stats(C.Structure):
         ("cg_residual_last", C.c_double), ("max_all", C.c_int32), ("error_bits", C.c_uint32),
         ("mean_cov", C.c_double), ("mean_all", C.c_double), ("cg_residual_start", C.c_double),
         ("cg_mv_batch", C.c_int32), ("reserved0", C.c_int32), ("cg_mv_ms", C.c_double * 3),
+        ("mean_mat", C.c_double),
     ]
 
     def as_dict(self):
