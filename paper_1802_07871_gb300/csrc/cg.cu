@@ -192,8 +192,8 @@ __device__ inline int check_replicas(int R, double* cg, const unsigned long long
 }
 
 // --------------------------------------------------------------- prepare
-__global__ void k_cg_prep(int R, double* __restrict__ cg, unsigned long long* __restrict__ rmax, int* __restrict__ conv,
-                          int* __restrict__ iters, int* __restrict__ it, int* __restrict__ blocks,
+__global__ void k_cg_prep(int N, int R, double* __restrict__ cg, unsigned long long* __restrict__ rmax,
+                          int* __restrict__ conv, int* __restrict__ iters, int* __restrict__ it, int* __restrict__ blocks,
                           int* __restrict__ active) {
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     double* c = cg + (size_t)r * CG_STRIDE;
@@ -208,7 +208,7 @@ __global__ void k_cg_prep(int R, double* __restrict__ cg, unsigned long long* __
     blocks[0] = 0;
     blocks[1] = 0;
     blocks[2] = 0;
-    *active = 1;
+    *active = N > 0 ? 1 : 0;   // no atoms: nothing to solve, the loop ends at once
   }
 }
 
@@ -792,7 +792,7 @@ __global__ void k_copy_q(int N, const double* __restrict__ q, R* __restrict__ qr
 // --------------------------------------------------------------- launchers
 template <class R>
 void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, double tol, const double* rhs) {
-  k_cg_prep<<<1, 256, 0, st>>>(S.R, S.cg, S.cg_rmax, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
+  k_cg_prep<<<1, 256, 0, st>>>(S.N, S.R, S.cg, S.cg_rmax, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
   if (S.N == 0) return;
   const R* binv = S.precond ? (const R*)S.binv : nullptr;
   k_cg_extrap<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.q, S.cqh1, S.cqh2, (R*)S.qr,
@@ -862,7 +862,7 @@ cudaError_t tune_cg_mv(DevState& S, cudaStream_t st, float* ms_out) {
   save(false);
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
     S.mv_batch = depth[k];
-    k_cg_prep<<<1, 256, 0, st>>>(S.R, S.cg, S.cg_rmax, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
+    k_cg_prep<<<1, 256, 0, st>>>(S.N, S.R, S.cg, S.cg_rmax, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
     launch_cg_mv<R>(S, st);
     cudaEventRecord(e0, st);
     for (int rep = 0; rep < 3; ++rep) launch_cg_mv<R>(S, st);
@@ -884,7 +884,9 @@ cudaError_t tune_cg_mv(DevState& S, cudaStream_t st, float* ms_out) {
 
 template <class R>
 void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
-  if (S.N == 0) return;
+  // launched even without atoms: inside the graph's WHILE node this kernel
+  // is what ends the loop (it finds the loop inactive and clears the
+  // condition)
   int grid = stride_grid(S.N, S.nsm, (const void*)k_cg_up<R>);
   k_cg_up<R><<<grid, 256, 0, st>>>(S.N, S.rep, (const R*)S.dinv, S.precond ? (const R*)S.binv : nullptr,
                                    S.cg_conv, S.cg_iters, S.cg_it, (const R*)S.cw,

@@ -95,3 +95,23 @@ def test_create_rejects_bad_options():
         ctbop.System(P0, cg_max_iter=0)
     with pytest.raises(ctbop.CtbopError):
         ctbop.System(P0, skin=-0.1)
+
+
+def test_empty_system_runs_every_entry_point():
+    """A layout with no atoms at all: every entry point returns cleanly with
+    empty results (zero energy)."""
+    empty = st.Structure("empty", np.zeros((0, 3)), np.zeros(0, np.int32), np.full(3, 20.0), np.array([True] * 3))
+    sysm = ctbop.System(P0, precision="mixed")
+    sysm.load(empty)
+    sysm.compute()
+    assert sysm.get("energy").tolist() == [0.0]
+    assert sysm.get("forces").shape == (0, 3)
+    sysm.step(3, 0.5)
+    it, fm = sysm.minimize(max_iter=5, fmax=1e-3)
+    assert it[0] == 0
+    assert len(sysm.rings()) == 0
+    assert sysm.removal_energies([]).shape == (0,)
+    assert sysm.get("coordination").shape == (0,)
+    L, G = sysm.param_grad(w_E=[1.0], E_ref=[0.0])
+    assert L == 0.0
+    sysm.close()
