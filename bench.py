@@ -53,6 +53,7 @@ def args_():
     ap.add_argument("--no-screen", action="store_true")
     ap.add_argument("--no-relax", action="store_true")
     ap.add_argument("--no-rings", action="store_true")
+    ap.add_argument("--no-drift", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=10)
     return ap.parse_args()
@@ -346,6 +347,36 @@ def run_rings(dev, stream, calls=3, warmup=1):
             "ms_per_call": sec * 1e3, "value": n_c / sec, "unit": "C atoms/s", "precision": "mixed"}
 
 
+def run_nve_drift(dev, stream, steps=1000, every=10):
+    """Energy conservation of the NVE integrator, reported as the drift of
+    E_pot + E_kin in eV/atom/ns (slope of a straight-line fit over the run):
+    the 512-atom 3C-SiC cell (FP64, 300 K) and the 19,488-atom stepped slab
+    (mixed, 2000 K, bottom frozen), dt = 0.5 fs."""
+    from paper_1802_07871_gb300 import ctbop
+    from paper_1802_07871_gb300 import structures as st
+    P0 = st.load_params("p0")
+    out = {}
+    for name, s, T, prec, seed in (("3C-SiC 512 atoms, FP64, 300 K", st.bulk_3c_512(), 300.0, "fp64", 101),
+                                   ("stepped slab 19,488 atoms, mixed, 2000 K", st.stepped_slab_20k(), 2000.0,
+                                    "mixed", 102)):
+        v = st.maxwell_boltzmann(s.types, T, seed=seed, frozen=s.frozen)
+        sysm = ctbop.System(P0, precision=prec, device=dev.index or 0)
+        sysm.set_stream(stream.cuda_stream)
+        sysm.load(s, velocities=v)
+        sysm.compute()
+        t, e = [], []
+        for k in range(0, steps + 1, every):
+            if k:
+                sysm.step(every, DT)
+            t.append(k * DT)
+            e.append(float(sysm.get("energy")[0] + sysm.get("kinetic")[0]))
+        sysm.close()
+        slope = np.polyfit(np.array(t), np.array(e), 1)[0]   # eV/fs
+        out[name] = {"drift_eV_per_atom_per_ns": slope * 1e6 / s.n, "steps": steps,
+                     "max_excursion_eV_per_atom": (max(e) - min(e)) / s.n}
+    return out
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -493,6 +524,8 @@ def run_ours(a):
         line["relax"] = run_relax(dev, stream)
     if world == 1 and not a.no_rings:
         line["rings"] = run_rings(dev, stream)
+    if world == 1 and not a.no_drift:
+        line["nve_drift"] = run_nve_drift(dev, stream)
     if world == 1 and not a.no_cpu:
         line["cpu_baseline"] = cpu_baseline(budget_s=20.0)
     print(json.dumps(line), flush=True)
