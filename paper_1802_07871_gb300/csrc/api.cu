@@ -289,6 +289,11 @@ static int alloc_atoms(ctbop_system* s) {
     S.binv = bi;
     S.bsum = bs;
   }
+  {
+    unsigned char* sg = nullptr;
+    CK(dalloc(s->atom_buf, &sg, (size_t)N * 24));
+    S.stage = sg;
+  }
   CK(dalloc(s->atom_buf, &S.cqh1, (size_t)N));
   CK(dalloc(s->atom_buf, &S.cqh2, (size_t)N));
   CK(dalloc(s->atom_buf, &S.ncov, (size_t)N));
@@ -894,12 +899,10 @@ static int copy_in_atoms(ctbop_system* s, void* dst, const void* src, int elem_b
   if (!src && bytes) return fail(s, CTBOP_ERR_INVALID_ARG, "null input pointer");
   if (mem != CTBOP_HOST && mem != CTBOP_DEVICE) return fail(s, CTBOP_ERR_INVALID_ARG, "mem must be CTBOP_HOST or CTBOP_DEVICE");
   cudaSetDevice(s->o.device);
-  void* tmp = nullptr;
-  CK(cudaMallocAsync(&tmp, std::max<size_t>(bytes, 1), s->stream));
+  void* tmp = s->S.stage;   // N x 24 bytes: the largest element
   CK(cudaMemcpyAsync(tmp, src, bytes, mem == CTBOP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                      s->stream));
   CK(launch_permute(s->S.N, s->d_order, tmp, dst, elem_bytes, true, s->stream));
-  CK(cudaFreeAsync(tmp, s->stream));
   if (mem == CTBOP_HOST) CK(cudaStreamSynchronize(s->stream));
   return CTBOP_OK;
 }
@@ -1159,12 +1162,10 @@ int ctbop_get(ctbop_system* s, int what, void* dst, int mem) {
   const bool per_atom = what == CTBOP_GET_FORCES || what == CTBOP_GET_POSITIONS || what == CTBOP_GET_VELOCITIES ||
                         what == CTBOP_GET_CHARGES || what == CTBOP_GET_E_ATOM;
   if (per_atom && s->ordered) {
-    // back to the caller's order
-    void* tmp = nullptr;
-    CK(cudaMallocAsync(&tmp, width, s->stream));
+    // back to the caller's order, through the staging buffer
+    void* tmp = S.stage;
     CK(launch_permute((int)N, s->d_order, src, tmp, (int)(width / N), false, s->stream));
     CK(cudaMemcpyAsync(dst, tmp, width, kind, s->stream));
-    CK(cudaFreeAsync(tmp, s->stream));
   } else {
     CK(cudaMemcpy2DAsync(dst, width, src, pitch, width, rows, kind, s->stream));
   }

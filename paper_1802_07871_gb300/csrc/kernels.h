@@ -121,6 +121,7 @@ struct DevState {
   void* binv = nullptr;         // Real[ceil(N/32)][32][32]: block inverses, column-major per block
   void* bsum = nullptr;         // Real[N]: row sums of the block inverses (d = M^-1 1)
   long long* precond_epoch = nullptr;   // rebuild count the block inverses were formed at (-1: never)
+  void* stage = nullptr;        // [N * 24 bytes] staging for per-atom inputs and outputs in the caller's order
 };
 
 struct SolveCfg {
