@@ -59,22 +59,20 @@ def args_():
     return ap.parse_args()
 
 
+WORKLOADS = {
+    "1m": "stepped 4H-SiC(0001) slab 96x48 cells x 56 bilayers, 3 steps, + 5% C adatoms",
+    "250k": "stepped 4H-SiC(0001) slab 48x24 cells x 56 bilayers, 3 steps, + 5% C adatoms",
+    "20k": "stepped 4H-SiC(0001) slab 24x14 cells x 15 bilayers, 2 step edges",
+    "512": "3C-SiC 4x4x4 cells",
+}
+
+
 def workload(name):
     from paper_1802_07871_gb300 import structures as st
-    if name == "1m":
-        s = st.stepped_slab_1m()
-        desc = "stepped 4H-SiC(0001) slab 96x48 cells x 56 bilayers, 3 steps, + 5% C adatoms"
-    elif name == "250k":
-        s = st.stepped_slab_250k()
-        desc = "stepped 4H-SiC(0001) slab 48x24 cells x 56 bilayers, 3 steps, + 5% C adatoms"
-    elif name == "20k":
-        s = st.stepped_slab_20k()
-        desc = "stepped 4H-SiC(0001) slab 24x14 cells x 15 bilayers, 2 step edges"
-    else:
-        s = st.bulk_3c_512()
-        desc = "3C-SiC 4x4x4 cells"
+    s = {"1m": st.stepped_slab_1m, "250k": st.stepped_slab_250k, "20k": st.stepped_slab_20k,
+         "512": st.bulk_3c_512}[name]()
     v = st.maxwell_boltzmann(s.types, T_K, seed=103, frozen=s.frozen)
-    return s, v, desc
+    return s, v, WORKLOADS[name]
 
 
 class Clocks:
@@ -589,8 +587,8 @@ def run_reference(a):
     line = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": "bounded sample of the stepped 4H-SiC(0001) slab with C adatoms",
-                       "precision": "fp64", "dt_fs": DT},
+            "config": {"workload": WORKLOADS[a.workload], "precision": "fp64", "dt_fs": DT, "T_K": T_K,
+                       "sample": "each step a bounded sample of this workload (see cpu_baseline.sample)"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
