@@ -54,6 +54,7 @@ def args_():
     ap.add_argument("--no-relax", action="store_true")
     ap.add_argument("--no-rings", action="store_true")
     ap.add_argument("--no-drift", action="store_true")
+    ap.add_argument("--no-nvt", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=0, help="0: as many as --steps")
     return ap.parse_args()
@@ -345,6 +346,31 @@ def run_rings(dev, stream, calls=3, warmup=1):
             "ms_per_call": sec * 1e3, "value": n_c / sec, "unit": "C atoms/s", "precision": "mixed"}
 
 
+def run_nvt(dev, stream, s, v, steps=30, warmup=3):
+    """Secondary measurement: the same slab under the Nose-Hoover thermostat
+    the paper's runs use (NVT at 2500 K, tau = 100 fs), atom-steps/s."""
+    import torch
+    from paper_1802_07871_gb300 import ctbop
+    from paper_1802_07871_gb300 import structures as st
+    sysm = ctbop.System(st.load_params("p0"), precision="mixed", device=dev.index or 0)
+    sysm.set_stream(stream.cuda_stream)
+    sysm.load(s, velocities=v)
+    sysm.set_thermostat(T_K, 100.0)
+    sysm.compute()
+    sysm.step(warmup, DT)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sysm.step(steps, DT)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sysm.close()
+    return {"workload": "the timed slab, Nose-Hoover NVT at 2500 K (tau 100 fs)", "steps": steps,
+            "warmup": warmup, "ms_per_step": ms / steps, "value": s.n * steps / (ms / 1e3), "unit": UNIT}
+
+
 def run_nve_drift(dev, stream, steps=1000, every=10):
     """Energy conservation of the NVE integrator, reported as the drift of
     E_pot + E_kin in eV/atom/ns (slope of a straight-line fit over the run):
@@ -520,6 +546,8 @@ def run_ours(a):
         "clocks": ck,
         "fp64": fp64,
     }
+    if world == 1 and not a.no_nvt:
+        line["nvt"] = run_nvt(dev, stream, s, v)
     if world == 1 and not a.no_ensemble:
         line["ensemble"] = run_ensemble(dev, stream)
     if world == 1 and not a.no_grad:
