@@ -102,7 +102,22 @@ template <class R> __device__ inline R ct_rsqrt(R x);
 template <> __device__ inline float ct_rsqrt<float>(float x) { return rsqrtf(x); }
 template <> __device__ inline double ct_rsqrt<double>(double x) { return 1.0 / sqrt(x); }
 template <class R> __device__ inline R ct_rcbrt(R x);
-template <> __device__ inline float ct_rcbrt<float>(float x) { return rcbrtf(x); }
+// x^(-1/3) in FP32 for positive normal x (the charge kernel's
+// r^3 + gamma^-3, a few to a few hundred): a first guess 2^(-log2(x)/3) from
+// the hardware base-2 logarithm and exponential (relative error near 2^-21),
+// then one Newton step for f(y) = y^-3 - x, written as a small correction,
+// y <- y + y (1 - x y^3) / 3, which squares that error and rounds once at
+// the end; the result is within about one ulp (checked against the library
+// rcbrtf and an FP64 reference by the tests).
+__device__ inline float rcbrt_newton(float x) {
+  float l, y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+  l *= -0.333333343f;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(l));
+  float e = fmaf(-x, y * y * y, 1.0f);
+  return fmaf(y * 0.333333343f, e, y);
+}
+template <> __device__ inline float ct_rcbrt<float>(float x) { return rcbrt_newton(x); }
 template <> __device__ inline double ct_rcbrt<double>(double x) { return 1.0 / cbrt(x); }
 template <class R> __device__ inline R ct_cospi(R x);
 template <> __device__ inline float ct_cospi<float>(float x) { return cospif(x); }
