@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <cstdio>
 #include <cstddef>
@@ -27,6 +28,27 @@ struct DevBuf {
   void release() {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
+  }
+};
+
+// Temporary device buffers of one call, stream-ordered, freed on every
+// return path (error returns included).
+struct Scratch {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  Scratch(const Scratch&) = delete;
+  Scratch& operator=(const Scratch&) = delete;
+  template <class T> cudaError_t alloc(T** out, size_t n) {
+    void* q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(n, 1) * sizeof(T), st);
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(q);
+    *out = static_cast<T*>(q);
+    return cudaSuccess;
+  }
+  ~Scratch() {
+    for (void* q : ptrs) cudaFreeAsync(q, st);
   }
 };
 
@@ -1037,10 +1059,11 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
   // snapshot buffers for redoing a chunk after a list overflow
   double *sx = nullptr, *sv = nullptr, *sF = nullptr, *sq = nullptr;
   size_t N = S.N;
-  CK(cudaMallocAsync(&sx, sizeof(double) * 3 * N + 8, s->stream));
-  CK(cudaMallocAsync(&sv, sizeof(double) * 3 * N + 8, s->stream));
-  CK(cudaMallocAsync(&sF, sizeof(double) * 3 * N + 8, s->stream));
-  CK(cudaMallocAsync(&sq, sizeof(double) * N + 8, s->stream));
+  Scratch scr(s->stream);
+  CK(scr.alloc(&sx, 3 * N + 1));
+  CK(scr.alloc(&sv, 3 * N + 1));
+  CK(scr.alloc(&sF, 3 * N + 1));
+  CK(scr.alloc(&sq, N + 1));
   int result = CTBOP_OK;
   int64_t done = 0;
   int redo = 0;
@@ -1105,10 +1128,6 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
     s->solves += n;
     if (bits & CT_ERR_CG_MAXITER) { result = fail(s, CTBOP_ERR_CG_NOT_CONVERGED, "charge CG reached max_iter"); break; }
   }
-  cudaFreeAsync(sx, s->stream);
-  cudaFreeAsync(sv, s->stream);
-  cudaFreeAsync(sF, s->stream);
-  cudaFreeAsync(sq, s->stream);
   cudaStreamSynchronize(s->stream);
   return result;
 }
@@ -1126,20 +1145,19 @@ int ctbop_get(ctbop_system* s, int what, void* dst, int mem) {
     // computed from the current lists, which an evaluation leaves valid
     if (!s->have_forces) return fail(s, CTBOP_ERR_STATE, "coordination: compute or step first");
     if (N == 0) return CTBOP_OK;
+    Scratch scr(s->stream);
     double* tmp = nullptr;
-    CK(cudaMallocAsync(&tmp, sizeof(double) * N, s->stream));
+    CK(scr.alloc(&tmp, N));
     if (s->mixed) launch_coordination<float>(S, s->Pf, tmp, s->stream);
     else launch_coordination<double>(S, s->Pd, tmp, s->stream);
     CK(cudaGetLastError());
     if (s->ordered) {
       double* tmp2 = nullptr;
-      CK(cudaMallocAsync(&tmp2, sizeof(double) * N, s->stream));
+      CK(scr.alloc(&tmp2, N));
       CK(launch_permute((int)N, s->d_order, tmp, tmp2, 8, false, s->stream));
-      CK(cudaFreeAsync(tmp, s->stream));
       tmp = tmp2;
     }
     CK(cudaMemcpyAsync(dst, tmp, sizeof(double) * N, kind, s->stream));
-    CK(cudaFreeAsync(tmp, s->stream));
     if (mem == CTBOP_HOST) CK(cudaStreamSynchronize(s->stream));
     return CTBOP_OK;
   }
@@ -1279,15 +1297,11 @@ static int param_grad_impl(ctbop_system* s, const double* w_E, const double* E_r
   *loss_out = loss;
   double *d_w = nullptr, *d_one = nullptr, *d_g = nullptr, *d_dir = nullptr, *d_v = nullptr, *d_cg = nullptr;
   double *d_h1 = nullptr, *d_h2 = nullptr, *d_q0 = nullptr, *d_lam = nullptr;
-  auto cleanup = [&]() {
-    for (double* p : {d_w, d_one, d_g, d_dir, d_v, d_cg, d_h1, d_h2, d_q0, d_lam}) if (p) cudaFree(p);
-  };
-  auto dm = [&](double** p, size_t n) { return cudaMalloc(p, sizeof(double) * std::max<size_t>(n, 1)); };
-  if (dm(&d_w, R) || dm(&d_one, R) || dm(&d_g, 2 * PG_NPARAM) || dm(&d_dir, (size_t)3 * N) || dm(&d_v, N) ||
-      dm(&d_cg, (size_t)R * CG_STRIDE) || dm(&d_h1, N) || dm(&d_h2, N) || dm(&d_q0, N) || dm(&d_lam, N)) {
-    cleanup();
+  Scratch scr(st);
+  if (scr.alloc(&d_w, R) || scr.alloc(&d_one, R) || scr.alloc(&d_g, 2 * PG_NPARAM) ||
+      scr.alloc(&d_dir, (size_t)3 * N) || scr.alloc(&d_v, N) || scr.alloc(&d_cg, (size_t)R * CG_STRIDE) ||
+      scr.alloc(&d_h1, N) || scr.alloc(&d_h2, N) || scr.alloc(&d_q0, N) || scr.alloc(&d_lam, N))
     return fail(s, CTBOP_ERR_OOM, "param_grad: temporary buffers");
-  }
   const ctbop_params& P = s->p;
   std::vector<double> G(2 * PG_NPARAM, 0.0), L(2 * PG_NPARAM, 0.0);
   CK(cudaMemcpyAsync(d_w, a.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
@@ -1362,7 +1376,6 @@ static int param_grad_impl(ctbop_system* s, const double* w_E, const double* E_r
     if (!rc)
       for (int k = 0; k < PG_NPARAM; ++k) G[k] += L[PG_NPARAM + k];
   }
-  cleanup();
   if (rc) return rc;
   G[PG_MASS] = G[PG_MASS + 1] = 0.0;   // the mass is not in E
   for (int k = 0; k < PG_NPARAM; ++k) dth[k] = G[k];
@@ -1463,17 +1476,7 @@ int ctbop_removal_energies(ctbop_system* s, int64_t n_cand, const int64_t* cand,
   uint8_t* d_f = nullptr;
   LooItem* d_items = nullptr;
   size_t cap_atoms = 0, cap_items = 0;
-  auto release = [&]() {
-    if (d_x) cudaFreeAsync(d_x, s->stream);
-    if (d_q) cudaFreeAsync(d_q, s->stream);
-    if (d_t) cudaFreeAsync(d_t, s->stream);
-    if (d_f) cudaFreeAsync(d_f, s->stream);
-    if (d_items) cudaFreeAsync(d_items, s->stream);
-    d_x = d_q = nullptr;
-    d_t = nullptr;
-    d_f = nullptr;
-    d_items = nullptr;
-  };
+  std::unique_ptr<Scratch> scr;   // the chunk buffers; replaced when a chunk needs more
   size_t first_chunk = 0;
   for (size_t j0 = 0; j0 < jobs.size() && !rc;) {
     // the chunk: jobs [j0, j1), padded (single source) to the first chunk's size
@@ -1505,14 +1508,14 @@ int ctbop_removal_energies(ctbop_system* s, int64_t n_cand, const int64_t* cand,
     }
     const size_t na = (size_t)off[C];
     if (na > cap_atoms || (size_t)C > cap_items) {
-      release();
       cap_atoms = std::max(na, cap_atoms);
       cap_items = std::max((size_t)C, cap_items);
-      CK(cudaMallocAsync(&d_x, sizeof(double) * 3 * cap_atoms, s->stream));
-      CK(cudaMallocAsync(&d_q, sizeof(double) * cap_atoms, s->stream));
-      CK(cudaMallocAsync(&d_t, sizeof(int) * cap_atoms, s->stream));
-      CK(cudaMallocAsync(&d_f, cap_atoms, s->stream));
-      CK(cudaMallocAsync(&d_items, sizeof(LooItem) * cap_items, s->stream));
+      scr.reset(new Scratch(s->stream));
+      CK(scr->alloc(&d_x, 3 * cap_atoms));
+      CK(scr->alloc(&d_q, cap_atoms));
+      CK(scr->alloc(&d_t, cap_atoms));
+      CK(scr->alloc(&d_f, cap_atoms));
+      CK(scr->alloc(&d_items, cap_items));
     }
     // layout, box and total charge only when they change (a new layout
     // reallocates the batch system)
@@ -1541,7 +1544,6 @@ int ctbop_removal_energies(ctbop_system* s, int64_t n_cand, const int64_t* cand,
     }
     if (rc) {
       std::string why = L->err;
-      release();
       CK(cudaStreamSynchronize(s->stream));
       return fail(s, rc, "removal energies: " + why);
     }
@@ -1555,7 +1557,6 @@ int ctbop_removal_energies(ctbop_system* s, int64_t n_cand, const int64_t* cand,
     }
     j0 = j1;
   }
-  release();
   CK(cudaStreamSynchronize(s->stream));
   return CTBOP_OK;
 }
@@ -1596,8 +1597,9 @@ int ctbop_minimize(ctbop_system* s, int64_t max_iter, double fmax, double dt0, d
   const int R = s->R;
   double* fire = nullptr;
   int* ctl = nullptr;
-  CK(cudaMallocAsync(&fire, sizeof(double) * R * FI_STRIDE, s->stream));
-  CK(cudaMallocAsync(&ctl, 2 * sizeof(int), s->stream));
+  Scratch scr(s->stream);
+  CK(scr.alloc(&fire, (size_t)R * FI_STRIDE));
+  CK(scr.alloc(&ctl, 2));
   std::vector<double> fh((size_t)R * FI_STRIDE, 0.0);
   const FireCfg cfg{fmax * fmax, dt_max, 1.1, 0.5, 0.1, 0.99, 5.0, (double)max_iter};
   for (int r = 0; r < R; ++r) {
@@ -1642,8 +1644,6 @@ int ctbop_minimize(ctbop_system* s, int64_t max_iter, double fmax, double dt0, d
     }
   }
   CK(zero_async(s, S.v, sizeof(double) * 3 * (size_t)S.N));   // left at rest
-  cudaFreeAsync(fire, s->stream);
-  cudaFreeAsync(ctl, s->stream);
   CK(cudaStreamSynchronize(s->stream));
   return rc;
 }
@@ -1660,8 +1660,9 @@ int ctbop_rings(ctbop_system* s, double bond_cut, int32_t max_size, int64_t cap,
   if (bond_cut == 0) bond_cut = scc;
   ctbop_ring* d_out = nullptr;
   unsigned long long* d_cnt = nullptr;
-  CK(cudaMallocAsync(&d_out, sizeof(ctbop_ring) * std::max<int64_t>(cap, 1), s->stream));
-  CK(cudaMallocAsync(&d_cnt, sizeof(unsigned long long), s->stream));
+  Scratch scr(s->stream);
+  CK(scr.alloc(&d_out, (size_t)std::max<int64_t>(cap, 1)));
+  CK(scr.alloc(&d_cnt, 1));
   CK(zero_async(s, d_cnt, sizeof(unsigned long long)));
   if (s->mixed) launch_rings<float>(s->S, bond_cut, max_size, d_out, cap, d_cnt, s->stream);
   else launch_rings<double>(s->S, bond_cut, max_size, d_out, cap, d_cnt, s->stream);
@@ -1671,8 +1672,6 @@ int ctbop_rings(ctbop_system* s, double bond_cut, int32_t max_size, int64_t cap,
   int64_t m = std::min<int64_t>((int64_t)n, cap);
   if (m > 0) CK(sync_copy(s, out, d_out, sizeof(ctbop_ring) * m, cudaMemcpyDeviceToHost));
   *n_rings = (int64_t)n;
-  cudaFreeAsync(d_out, s->stream);
-  cudaFreeAsync(d_cnt, s->stream);
   CK(cudaStreamSynchronize(s->stream));
   return CTBOP_OK;
 }
