@@ -535,7 +535,9 @@ def run_ours(a):
                    "mean_entries_per_atom": st2["mean_all"], "mean_matrix_entries_per_atom": st2["mean_mat"],
                    "mean_covalent_entries": st2["mean_cov"],
                    "cg_matvec_depth_tuned": st2["cg_mv_batch"],
-                   "cg_matvec_ms_by_depth_4_8_16": [round(x, 4) for x in st2["cg_mv_ms"]]},
+                   "cg_matvec_ms_by_depth_4_8_16": [round(x, 4) for x in st2["cg_mv_ms"]],
+                   "assembly_depth_tuned": st2["asm_batch"],
+                   "assembly_ms_by_depth_4_8_16": [round(x, 4) for x in st2["asm_ms"]]},
         "roofline": {"kernel": "k_cg_mv (charge CG matrix pass)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                      "traffic": traffic, "peak_kind": peak_kind,

@@ -135,10 +135,11 @@ typedef struct ctbop_stats {
     double  mean_all;         /* mean total entries at the last rebuild */
     double  cg_residual_start; /* max_i |H q0 + chi - mu|_i of the last solve's starting guess, replica 0 (eV/e) */
     int32_t cg_mv_batch;      /* list entries in flight per thread in the CG matrix pass (autotuned) */
-    int32_t reserved0;
+    int32_t asm_batch;        /* list entries in flight per thread in the matrix assembly (autotuned) */
     double  cg_mv_ms[3];      /* ms per matrix pass of the depths 4, 8, 16 at the last tuning (0: not timed) */
     double  mean_mat;         /* mean stored charge-matrix entries per atom (the entries a matrix pass
                                  streams: those inside the charge cutoff under the mixed policy) */
+    double  asm_ms[3];        /* ms per assembly of the depths 4, 8, 16 at the last tuning (0: not timed) */
 } ctbop_stats;
 
 typedef struct ctbop_system ctbop_system;

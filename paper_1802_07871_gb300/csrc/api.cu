@@ -84,6 +84,7 @@ struct ctbop_system {
   // matrix-pass autotuning: the lists it was tuned on, and the timings
   int tuned_N = -1, tuned_cap = -1;
   float mv_ms[3] = {0.f, 0.f, 0.f};
+  float asm_ms[3] = {0.f, 0.f, 0.f};
   bool tune_pending = false;
   double g_step_dt = -1.0;
   bool use_graph = true;
@@ -614,11 +615,12 @@ static int eval_t(ctbop_system* s, const PotParams<Rr>& P, uint32_t flags) {
     // matrix pass's depths (the solver state is kept across the timing)
     int rc = run_direct<Rr>(s, P, false, 0.0, true);
     if (rc) return rc;
-    int before = s->S.mv_batch;
+    int before = s->S.mv_batch, before_asm = s->S.asm_batch;
     cudaError_t e = tune_cg_mv<Rr>(s->S, s->stream, s->mv_ms);
-    if (e != cudaSuccess) return fail(s, CTBOP_ERR_CUDA, std::string("matrix-pass tuning: ") + cudaGetErrorString(e));
+    if (e == cudaSuccess) e = tune_assemble<Rr>(s->S, P, s->T, s->stream, s->asm_ms);
+    if (e != cudaSuccess) return fail(s, CTBOP_ERR_CUDA, std::string("pass tuning: ") + cudaGetErrorString(e));
     s->tune_pending = false;
-    if (s->S.mv_batch != before) destroy_graphs(s);
+    if (s->S.mv_batch != before || s->S.asm_batch != before_asm) destroy_graphs(s);
     s->solves++;
     s->have_forces = true;
     return CTBOP_OK;
@@ -1228,6 +1230,8 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   st->cg_residual_start = res0;
   st->cg_mv_batch = S.mv_batch;
   for (int k = 0; k < 3; ++k) st->cg_mv_ms[k] = s->mv_ms[k];
+  for (int k = 0; k < 3; ++k) st->asm_ms[k] = s->asm_ms[k];
+  st->asm_batch = S.asm_batch;
   st->error_bits = bits;
   st->rebuilds = rb;
   st->cg_iters_total = tot;

@@ -116,6 +116,7 @@ struct DevState {
   // sizes for launches
   int nsm = 152;
   int mv_batch = 16;            // list entries in flight per thread in the CG matrix pass (tuned)
+  int asm_batch = 8;            // list entries in flight per thread in the assembly (tuned)
   // charge-CG preconditioner: block-Jacobi on 32-atom blocks (1) or Jacobi (0)
   int precond = 1;
   void* binv = nullptr;         // Real[ceil(N/32)][32][32]: block inverses, column-major per block
@@ -158,6 +159,8 @@ template <class R> void launch_copy_q(const DevState& S, cudaStream_t st);
 // each block a contiguous chunk of atoms (a multiple of its size)
 int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk);
 template <class R> void launch_block_setup(const DevState& S, cudaStream_t st);
+template <class R>
+cudaError_t tune_assemble(DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st, float* ms_out);
 // Parameter gradient of the energy (csrc/grad.cu), in FP32 (fp32) or FP64
 // arithmetic with FP64 sums. grad[0..143] = sum_r wval_r dE_r/dtheta at the
 // current positions and charges. With a direction dir ([N,3], positions)

@@ -204,10 +204,12 @@ __global__ void __launch_bounds__(256)
 
 // ---------------------------------------------------------------- assembly
 // Entries past the covalent part are streamed: the list indices and offset
-// codes of the next PB entries are loaded before the current ones are used,
-// so the list (the bound of these passes) always has loads in flight.
+// codes of the next batch of entries are loaded before the current ones are
+// used, so the list (the bound of these passes) always has loads in flight.
+// The batch is AB in the assembly (4, 8 or 16, timed on the first solve of
+// new lists, tune_assemble) and PB in the charge-force gather.
 #define PB 8
-template <class R>
+template <class R, int AB>
 __global__ void __launch_bounds__(256)
     k_assemble(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
                const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
@@ -258,31 +260,31 @@ __global__ void __launch_bounds__(256)
   // FP64 keeps its coefficients aligned with the list (its index stream).
   int em = nc;
   const R gs_i0 = P.gshield3[ti * 2], gs_i1 = P.gshield3[ti * 2 + 1];
-  int jn[PB], cn[PB];
+  int jn[AB], cn[AB];
 #pragma unroll
-  for (int k = 0; k < PB; ++k) {
+  for (int k = 0; k < AB; ++k) {
     bool ok = nc + k < na;
     int2 t = ok ? __ldg(pl + (size_t)(nc + k) * ld) : make_int2(i, pack_code(0, 0, 0));
     jn[k] = t.x;
     cn[k] = t.y;
   }
-  for (int e = nc; e < na; e += PB) {
-    int jc[PB], cc[PB];
+  for (int e = nc; e < na; e += AB) {
+    int jc[AB], cc[AB];
 #pragma unroll
-    for (int k = 0; k < PB; ++k) {
+    for (int k = 0; k < AB; ++k) {
       jc[k] = jn[k];
       cc[k] = cn[k];
-      int en = e + PB + k;
+      int en = e + AB + k;
       bool ok = en < na;
       int2 t = ok ? __ldg(pl + (size_t)en * ld) : make_int2(i, pack_code(0, 0, 0));
       jn[k] = t.x;
       cn[k] = t.y;
     }
-    R4 uj[PB];
+    R4 uj[AB];
 #pragma unroll
-    for (int k = 0; k < PB; ++k) uj[k] = u[jc[k]];
+    for (int k = 0; k < AB; ++k) uj[k] = u[jc[k]];
 #pragma unroll
-    for (int k = 0; k < PB; ++k) {
+    for (int k = 0; k < AB; ++k) {
       if (e + k < na) {
         R rx, ry, rz;
         rel_vec<R>(ui, uj[k], cc[k], hx, hy, hz, rx, ry, rz);
@@ -644,9 +646,14 @@ void launch_bond(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
 template <class R>
 void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st) {
   if (S.N == 0) return;
-  k_assemble<R><<<(S.N + 255) / 256, 256, 0, st>>>(
-      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
-      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.bo, P, T, S.M, (R*)S.Dg, (R*)S.dinv, S.nmat);
+#define ASM_ARGS                                                                                        \
+  S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl, S.ncov, S.nall, S.rev,  \
+      (const typename Vec4<R>::T*)S.bo, P, T, S.M, (R*)S.Dg, (R*)S.dinv, S.nmat
+  const int g = (S.N + 255) / 256;
+  if (S.asm_batch == 4) k_assemble<R, 4><<<g, 256, 0, st>>>(ASM_ARGS);
+  else if (S.asm_batch == 16) k_assemble<R, 16><<<g, 256, 0, st>>>(ASM_ARGS);
+  else k_assemble<R, 8><<<g, 256, 0, st>>>(ASM_ARGS);
+#undef ASM_ARGS
 }
 
 template <class R>
@@ -701,6 +708,51 @@ template cudaError_t setup_pot<double>(int);
 
 template void launch_bond<float>(const DevState&, const PotParams<float>&, cudaStream_t);
 template void launch_bond<double>(const DevState&, const PotParams<double>&, cudaStream_t);
+// Entries in flight per thread in the assembly (4, 8 or 16): each depth
+// assembles the current matrix (the pass is idempotent: the same inputs give
+// the same matrix), one warm-up and two timed launches. Another depth
+// replaces the default 8 only when it is more than 10% faster: back to back
+// on warm caches the depths time within a few per cent of each other, while
+// inside a step (cold caches, moved atoms) depth 4 ran 28% slower than 8 on
+// the 1M-atom slab after winning such a timing by 1%.
+template <class R>
+cudaError_t tune_assemble(DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st,
+                          float* ms_out) {
+  if (S.N == 0) return cudaSuccess;
+  const int depth[3] = {4, 8, 16};
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  float t[3] = {0.f, 0.f, 0.f};
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    S.asm_batch = depth[k];
+    launch_assemble<R>(S, P, T, st);
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 2; ++rep) launch_assemble<R>(S, P, T, st);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 2.0f;
+    if (ms_out) ms_out[k] = ms;
+    t[k] = ms;
+  }
+  int pick = 8;
+  float best = 0.9f * t[1];
+  for (int k = 0; k < 3; k += 2)
+    if (t[k] > 0.f && t[k] < best) { best = t[k]; pick = depth[k]; }
+  S.asm_batch = pick;
+  if (e == cudaSuccess) launch_assemble<R>(S, P, T, st);   // the matrix as the kept depth sums it
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+template cudaError_t tune_assemble<float>(DevState&, const PotParams<float>&, const TypeParams&, cudaStream_t, float*);
+template cudaError_t tune_assemble<double>(DevState&, const PotParams<double>&, const TypeParams&, cudaStream_t,
+                                           float*);
+
 template void launch_assemble<float>(const DevState&, const PotParams<float>&, const TypeParams&, cudaStream_t);
 template void launch_assemble<double>(const DevState&, const PotParams<double>&, const TypeParams&, cudaStream_t);
 template void launch_cov_force<float>(const DevState&, const PotParams<float>&, const TypeParams&, cudaStream_t);

@@ -72,13 +72,14 @@ class Stats(C.Structure):
         ("max_cov", C.c_int32), ("cg_iters_total", C.c_int64), ("solves", C.c_int64),
         ("cg_residual_last", C.c_double), ("max_all", C.c_int32), ("error_bits", C.c_uint32),
         ("mean_cov", C.c_double), ("mean_all", C.c_double), ("cg_residual_start", C.c_double),
-        ("cg_mv_batch", C.c_int32), ("reserved0", C.c_int32), ("cg_mv_ms", C.c_double * 3),
-        ("mean_mat", C.c_double),
+        ("cg_mv_batch", C.c_int32), ("asm_batch", C.c_int32), ("cg_mv_ms", C.c_double * 3),
+        ("mean_mat", C.c_double), ("asm_ms", C.c_double * 3),
     ]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["cg_mv_ms"] = list(self.cg_mv_ms)
+        d["asm_ms"] = list(self.asm_ms)
         return d
 
 

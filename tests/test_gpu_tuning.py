@@ -1,7 +1,8 @@
-"""The CG matrix pass's autotuner: the depth it keeps (list entries in
-flight per thread) is the fastest it timed, and every depth gives the same
-charges and forces to working-precision rounding (only the grouping of the
-row sums differs)."""
+"""The autotuners of the CG matrix pass and of the matrix assembly: the
+depth each keeps (list entries in flight per thread) is the fastest it
+timed, and every matrix-pass depth gives the same charges and forces to
+working-precision rounding (only the grouping of the row sums differs; the
+assembly computes every entry alike at any depth)."""
 import numpy as np
 import pytest
 
@@ -27,6 +28,11 @@ def test_tuner_keeps_the_fastest_depth():
     assert d["cg_mv_batch"] in (4, 8, 16)
     assert all(m > 0 for m in ms)
     assert d["cg_mv_batch"] == (4, 8, 16)[int(np.argmin(ms))]
+    am = d["asm_ms"]
+    assert d["asm_batch"] in (4, 8, 16) and all(m > 0 for m in am)
+    # the assembly keeps its default depth 8 unless another is 10% faster
+    k = int(np.argmin(am))
+    assert d["asm_batch"] == ((4, 8, 16)[k] if am[k] < 0.9 * am[1] else 8)
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
