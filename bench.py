@@ -428,7 +428,7 @@ def run_ours(a):
     sysm.set_stream(stream.cuda_stream)
     sysm.load(s, velocities=v)
     sysm.compute()
-    F_mixed0 = sysm.get("forces")
+    F_mixed0, E_mixed0, q_mixed0 = sysm.get("forces"), sysm.get("energy")[0], sysm.get("charges")
     sysm.step(a.warmup, DT)
     st0 = sysm.status()
 
@@ -505,9 +505,11 @@ def run_ours(a):
         s64.set_stream(stream.cuda_stream)
         s64.load(s, velocities=v)
         s64.compute()
-        F64 = s64.get("forces")
+        F64, E64, q64 = s64.get("forces"), s64.get("energy")[0], s64.get("charges")
         rms = float(np.sqrt(np.mean(F64 ** 2)))
         ferr = float(np.max(np.abs(F_mixed0 - F64)) / rms)
+        eerr = float(abs(E_mixed0 - E64) / n)
+        qerr = float(np.max(np.abs(q_mixed0 - q64)))
         k64 = max(2, min(a.steps, 10))
         s64.step(2, DT)
         barrier()
@@ -519,7 +521,8 @@ def run_ours(a):
         barrier()
         ms64 = f0.elapsed_time(f1)
         fp64 = {"value": n * k64 * world / (ms64 / 1e3), "ms_per_step": ms64 / k64, "steps": k64,
-                "mixed_vs_fp64_force_err": ferr}
+                "mixed_vs_fp64_force_err": ferr, "mixed_vs_fp64_energy_err_eV_per_atom": eerr,
+                "mixed_vs_fp64_charge_err_e": qerr}
         s64.close()
 
     if rank != 0:

@@ -35,6 +35,27 @@ readings are the model card, stated where used):
   relative vector u, per-atom energies.
 * Velocity-Verlet NVE with frozen atoms (the paper runs MD with a fixed
   substrate bottom, Sec. 3.3).
+* NVT by one Nose-Hoover thermostat per system (the paper's MD is NVT,
+  Sec. 3.3, with no thermostat named). Pinned: a heavy thermostat gives the
+  NVE trajectory, the extended energy drifts as dt^2, and a hot bath heats a
+  cold start.
+* Parameter gradients of a force-matching loss on E and F (the paper fits
+  its parameters to energies, forces and charges, Sec. 2, without a method):
+  central differences of the loss, Richardson-extrapolated. Pinned: closed
+  forms for the self-energy parameters, the repulsion prefactor and the
+  Coulomb constant; F does not depend on E0.
+* Si desorption screening (Sec. 3.3): covalent coordination and the energy
+  change on removing one atom with the charges re-solved. Pinned: the SiC
+  dimer and linear Si3 in closed form, a far atom of an all-Si system,
+  equivalent sites of an ideal crystal.
+* FIRE minimisation (Bitzek et al. 2006; the paper relaxes structures
+  without naming a method). Pinned: closed-form minima of the dimer and of
+  linear Si3, an ideal crystal takes no iteration, descent with frozen
+  atoms.
+* Primitive rings of the C network and the 6-ring orientation (Sec. 3.3
+  follows 5-, 6- and 7-rings). Pinned: perfect graphene, a Stone-Wales
+  defect, lone polygons, two squares sharing an edge, rotation, and a path
+  around a periodic box that is no ring.
 """
 from __future__ import annotations
 
