@@ -180,12 +180,10 @@ static bool params_valid(const ctbop_params* p, std::string& why) {
       return false;
     }
   }
-  int a = 0;
   for (int t = 0; t < 2; ++t) {
     if (!(p->mass[t] > 0)) { why = "masses must be positive"; return false; }
     if (!(p->gamma_c[t] > 0)) { why = "charge shielding gamma_c must be positive"; return false; }
     if (!(p->J[t] > 0)) { why = "J must be positive"; return false; }
-    ++a;
   }
   double smax = 0;
   for (int k = 0; k < 4; ++k) smax = std::max(smax, p->S[k]);
@@ -640,13 +638,28 @@ static int eval_t(ctbop_system* s, const PotParams<Rr>& P, uint32_t flags) {
   return CTBOP_OK;
 }
 
+namespace {
+// A pair of timing events, destroyed on every return path.
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreate(&a);
+    return e != cudaSuccess ? e : cudaEventCreate(&b);
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+}  // namespace
+
 template <class Rr>
 static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double dt, double* ms, int64_t* cnt) {
   cudaStream_t st = s->stream;
   DevState& S = s->S;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  EventPair ev;
+  CK(ev.create());
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   auto timed = [&](int ph, int launches, auto&& fn) -> int {
     CK(cudaEventRecord(e0, st));
     fn();
@@ -693,8 +706,6 @@ static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double 
     s->steps++;
     s->solves++;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   return rc;
 }
 
@@ -747,6 +758,8 @@ int ctbop_create(const ctbop_params* p, const ctbop_options* o, ctbop_system** o
   if (cudaStreamCreate(&s->own_stream) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMallocHost(&s->h_int, 64) != cudaSuccess) {
+    if (s->body_stream) cudaStreamDestroy(s->body_stream);
+    if (s->own_stream) cudaStreamDestroy(s->own_stream);
     delete s;
     return CTBOP_ERR_CUDA;
   }
