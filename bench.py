@@ -147,6 +147,24 @@ def cg_matvec_bytes(n_atoms, entries, rs):
     return entries * (4 + rs) + n_atoms * (7 * rs + 8)
 
 
+class nvtx_range:
+    """An NVTX push/pop range around a timed region, so that a profiler can
+    select one leg's launches (e.g. ncu --nvtx --nvtx-include "param_grad_mixed/")."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        import torch
+        torch.cuda.nvtx.range_push(self.name)
+        return self
+
+    def __exit__(self, *exc):
+        import torch
+        torch.cuda.nvtx.range_pop()
+        return False
+
+
 def max_over_ranks(x, device, world):
     """Max of a per-rank float over all ranks (identity at world 1)."""
     if world <= 1:
@@ -235,9 +253,10 @@ def run_param_grad(dev, stream, precision="mixed", calls=3, warmup=1):
     it0 = sysm.status()["cg_iters_total"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(calls):
-        L, _ = sysm.param_grad(**loss)
-    torch.cuda.synchronize()
+    with nvtx_range(f"param_grad_{precision}"):
+        for _ in range(calls):
+            L, _ = sysm.param_grad(**loss)
+        torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / calls
     it1 = sysm.status()["cg_iters_total"]
     sysm.close()
@@ -270,9 +289,10 @@ def run_screen(dev, stream, calls=3, warmup=1):
     it0 = sysm.status()["cg_iters_total"]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(calls):
-        dE = sysm.removal_energies(cand)
-    torch.cuda.synchronize()
+    with nvtx_range("desorption_screen"):
+        for _ in range(calls):
+            dE = sysm.removal_energies(cand)
+        torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / calls
     sysm.close()
     return {"workload": "Si desorption screening of the 19,488-atom stepped 4H-SiC slab: removal energy of every "
@@ -300,8 +320,9 @@ def run_relax(dev, stream, max_iter=500, fmax=0.05):
     st0 = sysm.status()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    it, fm = sysm.minimize(max_iter=max_iter, fmax=fmax, dt0=1.0, dt_max=5.0)
-    torch.cuda.synchronize()
+    with nvtx_range("relax"):
+        it, fm = sysm.minimize(max_iter=max_iter, fmax=fmax, dt0=1.0, dt_max=5.0)
+        torch.cuda.synchronize()
     sec = time.perf_counter() - t0
     st1 = sysm.status()
     E1 = float(sysm.get("energy")[0])
@@ -335,9 +356,10 @@ def run_rings(dev, stream, calls=3, warmup=1):
         sysm.rings()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(calls):
-        rec = sysm.rings()
-    torch.cuda.synchronize()
+    with nvtx_range("rings"):
+        for _ in range(calls):
+            rec = sysm.rings()
+        torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / calls
     sysm.close()
     c = RG.counts(rec, len(structs)).sum(axis=0)
