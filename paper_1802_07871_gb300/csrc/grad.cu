@@ -26,11 +26,16 @@
 // positions carries its exact directional derivative, with no step size.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
+
 #include "internal.cuh"
 #include "kernels.h"
 #include "ctbop.h"
 
 namespace ct {
+
+namespace cg = cooperative_groups;
 
 // ------------------------------------------------------------ dual numbers
 // A value and its derivative along one direction, in T = float or double.
@@ -142,18 +147,54 @@ __device__ inline S fc_only(S r, R Rin, R Sc) {
   return R(0.5) * (R(1) + fcospi((r - Rin) / (Sc - Rin)));
 }
 
-// Block accumulator in FP64: values weighted by wv, tangents by wt.
-struct Acc {
+// Block accumulator in FP64: values weighted by wv, tangents by wt. With
+// Agg, the lanes of a warp that reach one call together and name the same
+// slot first sum their shares with shuffles and one of them adds the sum
+// (the charge-kernel pass, whose lanes all name the same few slots at the
+// end of their rows); without, every lane adds its own share.
+template <bool Agg> struct Acc {
   double* g;    // [PG_NPARAM] values
   double* t;    // [PG_NPARAM] tangents
   double wv, wt;
-  __device__ void operator()(int k, double x) const { atomicAdd(&g[k], wv * x); }
-  __device__ void operator()(int k, float x) const { atomicAdd(&g[k], wv * (double)x); }
+  __device__ void put(int k, double a) const {
+    if (!Agg) {
+      atomicAdd(&g[k], a);
+      return;
+    }
+    cg::coalesced_group grp = cg::labeled_partition(cg::coalesced_threads(), k);
+    double sa = cg::reduce(grp, a, cg::plus<double>());
+    if (grp.thread_rank() == 0) atomicAdd(&g[k], sa);
+  }
+  __device__ void put2(int k, double a, double b) const {
+    if (!Agg) {
+      atomicAdd(&g[k], a);
+      atomicAdd(&t[k], b);
+      return;
+    }
+    cg::coalesced_group grp = cg::labeled_partition(cg::coalesced_threads(), k);
+    double sa = cg::reduce(grp, a, cg::plus<double>());
+    double sb = cg::reduce(grp, b, cg::plus<double>());
+    if (grp.thread_rank() == 0) {
+      atomicAdd(&g[k], sa);
+      atomicAdd(&t[k], sb);
+    }
+  }
+  __device__ void operator()(int k, double x) const { put(k, wv * x); }
+  __device__ void operator()(int k, float x) const { put(k, wv * (double)x); }
   template <class T> __device__ void operator()(int k, DualT<T> x) const {
-    atomicAdd(&g[k], wv * (double)x.v);
-    atomicAdd(&t[k], wt * (double)x.d);
+    put2(k, wv * (double)x.v, wt * (double)x.d);
   }
 };
+
+// FP64 partial sums of working-precision terms (values, or values with
+// their tangents), kept in registers over a short loop.
+template <class S> struct SumT { using type = double; };
+template <class T> struct SumT<DualT<T>> { using type = DualT<double>; };
+__device__ inline double to_sum(double x) { return x; }
+__device__ inline double to_sum(float x) { return (double)x; }
+template <class T> __device__ inline DualT<double> to_sum(DualT<T> x) {
+  return DualT<double>((double)x.v, (double)x.d);
+}
 
 #define PG_GRP 8     // lanes per atom
 #define PG_APB 16    // atoms per block
@@ -212,7 +253,7 @@ __global__ void __launch_bounds__(PG_APB * PG_GRP)
   int i = blockIdx.x * PG_APB + g;
   bool live = i < N;
   int nc = 0, ti = 0;
-  Acc acc{s_g, s_g + PG_NPARAM, 0.0, 0.0};
+  Acc<false> acc{s_g, s_g + PG_NPARAM, 0.0, 0.0};
   S qi = S(R(0));
   if (live) {
     R4 ui = u[i];
@@ -322,34 +363,52 @@ __global__ void __launch_bounds__(PG_APB * PG_GRP)
         Ez[ll] = val(z[ll]) > R(0)
                      ? Eb * b * ex_ * (-pp * t[ll] / (Z[ll] * Ssum)) * P.n[pb][ll] * zn[ll] / z[ll]
                      : S(R(0));
-      // triplet parameters and the cutoff of the (i, k) pairs inside zeta
-      for (int k = 0; k < nc; ++k) {
-        if (k == e) continue;
-        S kx, ky, kz, rk;
-        ent_vec(s_e[k], kx, ky, kz, rk);
-        int tk = s_t[k], pk = ti * 2 + tk;
-        S fck, fkR, fkS;
-        fc_params(rk, P.R_[pk], P.S[pk], fck, fkR, fkS);
-        if (val(fck) == R(0)) continue;
-        S ct = (ex * kx + ey * ky + ez * kz) / (re * rk);
-        int tri = pb * 2 + tk;
-        for (int ll = 0; ll < 2; ++ll) {
-          if (val(Ez[ll]) == R(0)) continue;
-          R cc = P.c[tri][ll], dd = P.d[tri][ll], gm = P.gamma[tri][ll];
-          R c2 = cc * cc, d2 = dd * dd;
-          S hm = P.h[tri][ll] - ct, den = d2 + hm * hm;
-          S angg = R(1) + c2 * hm * hm / (d2 * den);   // ang / gamma
-          S dr = re - rk;
-          S exl = fexp(P.alpha[tri][ll] * dr);
-          S wz = Ez[ll] * exl;
-          acc(PG_GAMMA + tri * 2 + ll, wz * fck * angg);
-          acc(PG_C + tri * 2 + ll, wz * fck * (gm * R(2) * cc) * hm * hm / (d2 * den));
-          acc(PG_D + tri * 2 + ll, wz * fck * (R(2) * gm * c2 * dd) * (R(1) / (den * den) - R(1) / (d2 * d2)));
-          acc(PG_H + tri * 2 + ll, wz * fck * (gm * R(2) * c2) * hm / (den * den));
-          acc(PG_ALPHA + tri * 2 + ll, wz * fck * gm * angg * dr);
-          acc(PG_R + pk, wz * fkR * gm * angg);
-          acc(PG_S + pk, wz * fkS * gm * angg);
+      // triplet parameters and the cutoff of the (i, k) pairs inside zeta:
+      // the terms of the k of one type share their slots, so they are summed
+      // in registers (FP64) and added once per bond and type of k
+      using ST = typename SumT<S>::type;
+      for (int tk = 0; tk < 2; ++tk) {
+        const int tri = pb * 2 + tk, pk = ti * 2 + tk;
+        ST sg_[2], sc_[2], sd_[2], sh_[2], sa_[2], sR(0.0), sS(0.0);
+        for (int ll = 0; ll < 2; ++ll) sg_[ll] = sc_[ll] = sd_[ll] = sh_[ll] = sa_[ll] = ST(0.0);
+        bool any = false;
+        for (int k = 0; k < nc; ++k) {
+          if (k == e || s_t[k] != tk) continue;
+          S kx, ky, kz, rk;
+          ent_vec(s_e[k], kx, ky, kz, rk);
+          S fck, fkR, fkS;
+          fc_params(rk, P.R_[pk], P.S[pk], fck, fkR, fkS);
+          if (val(fck) == R(0)) continue;
+          S ct = (ex * kx + ey * ky + ez * kz) / (re * rk);
+          for (int ll = 0; ll < 2; ++ll) {
+            if (val(Ez[ll]) == R(0)) continue;
+            R cc = P.c[tri][ll], dd = P.d[tri][ll], gm = P.gamma[tri][ll];
+            R c2 = cc * cc, d2 = dd * dd;
+            S hm = P.h[tri][ll] - ct, den = d2 + hm * hm;
+            S angg = R(1) + c2 * hm * hm / (d2 * den);   // ang / gamma
+            S dr = re - rk;
+            S exl = fexp(P.alpha[tri][ll] * dr);
+            S wz = Ez[ll] * exl;
+            sg_[ll] += to_sum(wz * fck * angg);
+            sc_[ll] += to_sum(wz * fck * (gm * R(2) * cc) * hm * hm / (d2 * den));
+            sd_[ll] += to_sum(wz * fck * (R(2) * gm * c2 * dd) * (R(1) / (den * den) - R(1) / (d2 * d2)));
+            sh_[ll] += to_sum(wz * fck * (gm * R(2) * c2) * hm / (den * den));
+            sa_[ll] += to_sum(wz * fck * gm * angg * dr);
+            sR += to_sum(wz * fkR * gm * angg);
+            sS += to_sum(wz * fkS * gm * angg);
+            any = true;
+          }
         }
+        if (!any) continue;
+        for (int ll = 0; ll < 2; ++ll) {
+          acc(PG_GAMMA + tri * 2 + ll, sg_[ll]);
+          acc(PG_C + tri * 2 + ll, sc_[ll]);
+          acc(PG_D + tri * 2 + ll, sd_[ll]);
+          acc(PG_H + tri * 2 + ll, sh_[ll]);
+          acc(PG_ALPHA + tri * 2 + ll, sa_[ll]);
+        }
+        acc(PG_R + pk, sR);
+        acc(PG_S + pk, sS);
       }
     }
   }
@@ -377,7 +436,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
-    Acc acc{s_g, s_g + PG_NPARAM, wval[rep[i]], wtan ? wtan[rep[i]] : 0.0};
+    Acc<true> acc{s_g, s_g + PG_NPARAM, wval[rep[i]], wtan ? wtan[rep[i]] : 0.0};
     if (acc.wv != 0.0 || acc.wt != 0.0) {
       R4 ui = u[i];
       int ti = (int)ui.w;
