@@ -240,6 +240,26 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+def _check_buffer(a, dtype, count: int, what: str):
+    """A caller's buffer (numpy array or torch tensor) that the library will
+    read or write `count` elements of `dtype` from: its element type and its
+    size must match, or the library would read or write past it."""
+    dt = np.dtype(dtype)
+    if isinstance(a, np.ndarray):
+        if a.dtype != dt:
+            raise TypeError(f"{what}: need {dt.name} elements, got {a.dtype}")
+        n = a.size
+    elif hasattr(a, "data_ptr"):
+        tn = str(a.dtype).replace("torch.", "")
+        if not (tn == dt.name or (dt == np.uint8 and tn == "bool")):
+            raise TypeError(f"{what}: need {dt.name} elements, got {tn}")
+        n = a.numel()
+    else:
+        raise TypeError(f"{what}: unsupported array type {type(a)}")
+    if n != count:
+        raise ValueError(f"{what}: need {count} elements, got {n}")
+
+
 class CtbopError(RuntimeError):
     pass
 
@@ -269,6 +289,7 @@ class System:
         self.n = 0
         self.R = 0
         self.precision = precision
+        self.device = device
 
     def _check(self, rc, what):
         if rc != OK:
@@ -350,12 +371,18 @@ class System:
             h[r] = np.diag(lengths[r])
         h = np.ascontiguousarray(h)
         p = np.ascontiguousarray(np.asarray(pbc).reshape(-1, 3), dtype=np.uint8)
+        if self.R > 0 and (len(h) != self.R or len(p) != self.R):
+            raise ValueError(f"set_box: need {self.R} boxes and pbc rows, got {len(h)} and {len(p)}")
         self._check(self._L.ctbop_set_box(self._h, h.ctypes.data_as(C.c_void_p), p.ctypes.data_as(C.c_void_p)),
                     "set_box")
 
-    def _set(self, fn, a, dtype, what):
-        if isinstance(a, np.ndarray):
+    def _set(self, fn, a, dtype, what, per_atom=1):
+        if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
             a = np.ascontiguousarray(a, dtype=dtype)
+        if self.R > 0:   # without a layout the library reports the state error
+            _check_buffer(a, dtype, per_atom * self.n, what)
+        if getattr(a, "is_cuda", False) and a.device.index != self.device:
+            raise ValueError(f"{what}: tensor on cuda:{a.device.index}, system on cuda:{self.device}")
         ptr, mem = _ptr(a)
         self._keep = a
         self._check(fn(self._h, ptr, mem), what)
@@ -364,10 +391,10 @@ class System:
         self._set(self._L.ctbop_set_types, t, np.int32, "set_types")
 
     def set_positions(self, x):
-        self._set(self._L.ctbop_set_positions, x, np.float64, "set_positions")
+        self._set(self._L.ctbop_set_positions, x, np.float64, "set_positions", 3)
 
     def set_velocities(self, v):
-        self._set(self._L.ctbop_set_velocities, v, np.float64, "set_velocities")
+        self._set(self._L.ctbop_set_velocities, v, np.float64, "set_velocities", 3)
 
     def set_charges(self, q):
         self._set(self._L.ctbop_set_charges, q, np.float64, "set_charges")
@@ -376,7 +403,9 @@ class System:
         self._set(self._L.ctbop_set_frozen, f, np.uint8, "set_frozen")
 
     def set_total_charge(self, Q):
-        Q = np.ascontiguousarray(np.atleast_1d(Q), dtype=np.float64)
+        Q = np.atleast_1d(np.asarray(Q, dtype=np.float64))
+        if self.R > 0:
+            Q = np.ascontiguousarray(np.broadcast_to(Q, (self.R,)))
         self._check(self._L.ctbop_set_total_charge(self._h, Q.ctypes.data_as(C.c_void_p)), "set_total_charge")
 
     def set_order(self, order):
@@ -384,6 +413,8 @@ class System:
         order[k] is the caller's index of the atom stored in slot k. Inputs
         and outputs stay in the caller's order."""
         o = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
+        if o is not None and self.R > 0:
+            _check_buffer(o, np.int64, self.n, "set_order")
         self._check(self._L.ctbop_set_order(self._h, None if o is None else o.ctypes.data_as(C.c_void_p)),
                     "set_order")
 
@@ -493,6 +524,9 @@ class System:
                  "coordination": (self.n,)}[what]
         if out is None:
             out = np.empty(shape, dtype=np.float64)
+        _check_buffer(out, np.float64, int(np.prod(shape)), f"get {what}")
+        if getattr(out, "is_cuda", False) and out.device.index != self.device:
+            raise ValueError(f"get {what}: tensor on cuda:{out.device.index}, system on cuda:{self.device}")
         ptr, mem = _ptr(out)
         self._check(self._L.ctbop_get(self._h, sel, ptr, mem), f"get {what}")
         return out

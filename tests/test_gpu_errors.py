@@ -90,6 +90,33 @@ def test_invalid_arguments_are_rejected():
     sysm.close()
 
 
+def test_caller_buffers_are_checked_before_the_library_sees_them():
+    """Buffers shorter than the system, or of a narrower element type, are
+    rejected on the host: the library would read or write past them."""
+    torch = pytest.importorskip("torch")
+    s = st.bulk_3c_512()
+    sysm = ctbop.System(P0, precision="mixed")
+    sysm.load(s)
+    with pytest.raises(ValueError, match="elements"):
+        sysm.set_positions(s.x[:-1])
+    with pytest.raises(ValueError, match="elements"):
+        sysm.set_velocities(torch.zeros((s.n - 1, 3), dtype=torch.float64, device="cuda"))
+    with pytest.raises(TypeError, match="float64"):
+        sysm.set_positions(torch.tensor(s.x, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError, match="boxes"):
+        sysm.set_box(np.ones((2, 3)) * 20.0, np.ones((2, 3), bool))
+    sysm.compute()
+    with pytest.raises(ValueError, match="elements"):
+        sysm.get("forces", torch.empty((s.n, 2), dtype=torch.float64, device="cuda"))
+    with pytest.raises(TypeError, match="float64"):
+        sysm.get("charges", np.empty(s.n, np.float32))
+    F = torch.empty((s.n, 3), dtype=torch.float64, device="cuda")
+    sysm.get("forces", F)
+    torch.cuda.synchronize()
+    assert np.array_equal(F.cpu().numpy(), sysm.get("forces"))
+    sysm.close()
+
+
 def test_create_rejects_bad_options():
     with pytest.raises(ctbop.CtbopError):
         ctbop.System(P0, cg_max_iter=0)

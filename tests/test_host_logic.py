@@ -144,3 +144,27 @@ def test_peak_comes_from_the_measured_file(bench):
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
         hbm = float(json.load(f)["hbm_gbs"])
     assert bench.peaks() == (hbm, "measured")
+
+
+# ---------------------------------------------------------------- caller buffers
+def test_buffer_checks_reject_wrong_type_and_size():
+    """A buffer the library would read or write past (too short, or of a
+    narrower element type) is rejected on the host before any call."""
+    chk = ctbop._check_buffer
+    chk(np.zeros((4, 3)), np.float64, 12, "x")
+    with pytest.raises(ValueError, match="12 elements"):
+        chk(np.zeros((3, 3)), np.float64, 12, "x")
+    with pytest.raises(TypeError, match="float64"):
+        chk(np.zeros((4, 3), np.float32), np.float64, 12, "x")
+    torch = pytest.importorskip("torch")
+    chk(torch.zeros(4, 3, dtype=torch.float64), np.float64, 12, "x")
+    chk(torch.zeros(5, dtype=torch.bool), np.uint8, 5, "frozen")
+    chk(torch.zeros(5, dtype=torch.int32), np.int32, 5, "types")
+    with pytest.raises(TypeError, match="float64"):
+        chk(torch.zeros(4, 3, dtype=torch.float32), np.float64, 12, "x")
+    with pytest.raises(TypeError, match="int32"):
+        chk(torch.zeros(5, dtype=torch.int64), np.int32, 5, "types")
+    with pytest.raises(ValueError, match="5 elements"):
+        chk(torch.zeros(4, dtype=torch.uint8), np.uint8, 5, "frozen")
+    with pytest.raises(TypeError):
+        chk([0.0] * 12, np.float64, 12, "x")
