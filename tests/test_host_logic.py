@@ -141,7 +141,11 @@ def test_matrix_pass_bytes(bench):
 
 
 def test_peak_comes_from_the_measured_file(bench):
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if not os.path.exists(path):      # written per machine; absent: the stated fallback
+        assert bench.peaks() == (6800.0, "fallback")
+        return
+    with open(path) as f:
         hbm = float(json.load(f)["hbm_gbs"])
     assert bench.peaks() == (hbm, "measured")
 
