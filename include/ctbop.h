@@ -213,7 +213,13 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs);
  * arrays already set). */
 int ctbop_set_order(ctbop_system* s, const int64_t* order);
 
-/* Copy a result out (see CTBOP_GET_*). mem = CTBOP_HOST synchronises. */
+/* Copy a result out: dst (caller-owned, host or device as mem says) must
+ * hold the element count the CTBOP_GET_* selector lists, in doubles; the
+ * library cannot check its size. Per-atom selectors come back in the
+ * caller's atom order (ctbop_set_order). mem = CTBOP_HOST synchronises the
+ * system's stream; CTBOP_DEVICE is stream-ordered. Errors: INVALID_ARG
+ * (null dst, unknown selector, bad mem), STATE (no layout; coordination
+ * before an evaluation), CUDA. */
 int ctbop_get(ctbop_system* s, int what, void* dst, int mem);
 
 /* Synchronise and report counters and device error bits. */
