@@ -37,6 +37,27 @@ def test_bulk_512(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_bulk_512_after_100_fp64_steps(prec):
+    """The bars hold at an MD state as well as at the initial one: the
+    512-atom crystal after 100 FP64 GPU steps of 0.5 fs from 300 K
+    velocities, evaluated by each GPU path and by the oracle at those
+    positions."""
+    from paper_1802_07871_gb300 import ctbop
+    s = st.bulk_3c_512()
+    md = ctbop.System(P0, precision="fp64")
+    md.load(s, velocities=st.maxwell_boltzmann(s.types, 300.0, seed=101))
+    md.compute()
+    md.step(100, 0.5)
+    x = md.get("positions")
+    md.close()
+    s100 = st.Structure(s.name, x, s.types, s.box, s.pbc, s.frozen)
+    g = gpu_eval(s100, P0, prec)
+    o = oracle_eval(s100, P0)
+    compare(g, o, s.n, prec)
+    assert g["status"]["rc"] == "OK"
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_stepped_slab_with_adatoms(prec):
     """Open-z 4H-SiC(0001) staircase slab with C adatoms and a frozen bottom."""
     s = st.stepped_slab_small(8, 4, 6)
