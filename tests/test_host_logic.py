@@ -172,3 +172,27 @@ def test_buffer_checks_reject_wrong_type_and_size():
         chk(torch.zeros(4, dtype=torch.uint8), np.uint8, 5, "frozen")
     with pytest.raises(TypeError):
         chk([0.0] * 12, np.float64, 12, "x")
+
+
+def test_reference_arm_line(bench, monkeypatch, capsys):
+    """`bench.py --impl reference` prints one JSON line in the benchmark's
+    format, marked as the reference arm, its value the oracle's rate."""
+    fake = {"value": 1234.5, "unit": bench.UNIT, "cores": 1, "kind": "oracle", "sample": "s"}
+    monkeypatch.setattr(bench, "cpu_baseline", lambda **kw: dict(fake))
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "3", "--warmup", "1"])
+    bench.main()
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] == 1234.5 and line["unit"] == bench.UNIT and line["higher_is_better"] is True
+    assert line["steps"] == 3 and line["warmup"] == 1 and line["n_gpus"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"] == {"value": 1234.5, "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == bench.WORKLOADS["1m"]
+
+
+def test_cpu_baseline_times_the_oracle_on_a_bounded_sample(bench):
+    cb = bench.cpu_baseline(budget_s=2.0, steps=1)
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
+    assert "stepped 4H-SiC slab" in cb["sample"]
