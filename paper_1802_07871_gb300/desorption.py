@@ -11,7 +11,7 @@ Readings (the paper states neither):
 * surface Si = mobile Si atoms with covalent coordination (neighbours within
   the cutoff S of the pair) below 4;
 * the removed atoms of one screening are all those below the threshold,
-  each judged alone from the same state.
+  each evaluated alone from the same state.
 Threshold: the paper uses 6.5 eV, 3.5 eV below its typical terrace Si
 (about 10 eV). The synthetic parameter set puts terrace Si much lower, so
 threshold="relative" takes the median removal energy of the 3-coordinated
