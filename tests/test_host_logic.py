@@ -196,3 +196,9 @@ def test_cpu_baseline_times_the_oracle_on_a_bounded_sample(bench):
     cb = bench.cpu_baseline(budget_s=2.0, steps=1)
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
     assert "stepped 4H-SiC slab" in cb["sample"]
+
+
+def test_cpu_baseline_all_cores_runs_in_a_child_process(bench):
+    cb = bench.cpu_baseline_all_cores(budget_s=2.0, steps=1)
+    assert "unavailable" not in cb, cb
+    assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1) and cb["value"] > 0
