@@ -194,7 +194,7 @@ def run_ensemble(dev, stream, steps=20, warmup=3):
     v = np.concatenate([st.maxwell_boltzmann(s.types, T, seed=500 + r, frozen=s.frozen)
                         for r, (s, T) in enumerate(zip(structs, temps))])
     n = sum(s.n for s in structs)
-    sysm = ctbop.System(st.load_params("p0"), precision="mixed", device=dev.index or 0)
+    sysm = ctbop.System(st.load_params("p1"), precision="mixed", device=dev.index or 0)
     sysm.set_stream(stream.cuda_stream)
     sysm.load_replicas(structs)
     sysm.set_velocities(v)
@@ -233,17 +233,17 @@ def run_param_grad(dev, stream, precision="mixed", calls=3, warmup=1):
     import torch
     from paper_1802_07871_gb300 import ctbop
     from paper_1802_07871_gb300 import structures as st
-    P0 = st.load_params("p0")
+    P1 = st.load_params("p1")
     structs = st.differentiation_batch(1024, seed=5)
     n = sum(s.n for s in structs)
     R = len(structs)
-    ref = ctbop.System(st.perturbed_params(P0, 55), precision="fp64", device=dev.index or 0)
+    ref = ctbop.System(st.perturbed_params(P1, 55), precision="fp64", device=dev.index or 0)
     ref.set_stream(stream.cuda_stream)
     ref.load_replicas(structs)
     ref.compute()
     E_ref, F_ref = ref.get("energy"), ref.get("forces")
     ref.close()
-    sysm = ctbop.System(P0, precision=precision, device=dev.index or 0)
+    sysm = ctbop.System(P1, precision=precision, device=dev.index or 0)
     sysm.set_stream(stream.cuda_stream)
     sysm.load_replicas(structs)
     nr = np.array([s.n for s in structs], dtype=np.float64)
@@ -279,7 +279,7 @@ def run_screen(dev, stream, calls=3, warmup=1):
     from paper_1802_07871_gb300 import desorption as D
     from paper_1802_07871_gb300 import structures as st
     s = st.stepped_slab_20k()
-    sysm = ctbop.System(st.load_params("p0"), precision="mixed", device=dev.index or 0)
+    sysm = ctbop.System(st.load_params("p1"), precision="mixed", device=dev.index or 0)
     sysm.set_stream(stream.cuda_stream)
     sysm.load(s)
     sysm.compute()
@@ -312,7 +312,7 @@ def run_relax(dev, stream, max_iter=500, fmax=0.05):
     from paper_1802_07871_gb300 import ctbop
     from paper_1802_07871_gb300 import structures as st
     s = st.stepped_slab_20k()
-    sysm = ctbop.System(st.load_params("p0"), precision="mixed", device=dev.index or 0)
+    sysm = ctbop.System(st.load_params("p1"), precision="mixed", device=dev.index or 0)
     sysm.set_stream(stream.cuda_stream)
     sysm.load(s)
     sysm.compute()
@@ -348,7 +348,7 @@ def run_rings(dev, stream, calls=3, warmup=1):
     structs, _ = st.annealing_ensemble(256, seed=4)
     n = sum(s.n for s in structs)
     n_c = int(sum(int(np.sum(s.types == 1)) for s in structs))
-    sysm = ctbop.System(st.load_params("p0"), precision="mixed", device=dev.index or 0)
+    sysm = ctbop.System(st.load_params("p1"), precision="mixed", device=dev.index or 0)
     sysm.set_stream(stream.cuda_stream)
     sysm.load_replicas(structs)
     sysm.compute()
@@ -374,7 +374,7 @@ def run_nvt(dev, stream, s, v, steps=30, warmup=3):
     import torch
     from paper_1802_07871_gb300 import ctbop
     from paper_1802_07871_gb300 import structures as st
-    sysm = ctbop.System(st.load_params("p0"), precision="mixed", device=dev.index or 0)
+    sysm = ctbop.System(st.load_params("p1"), precision="mixed", device=dev.index or 0)
     sysm.set_stream(stream.cuda_stream)
     sysm.load(s, velocities=v)
     sysm.set_thermostat(T_K, 100.0)
@@ -400,13 +400,13 @@ def run_nve_drift(dev, stream, steps=1000, every=10):
     (mixed, 2000 K, bottom frozen), dt = 0.5 fs."""
     from paper_1802_07871_gb300 import ctbop
     from paper_1802_07871_gb300 import structures as st
-    P0 = st.load_params("p0")
+    P1 = st.load_params("p1")
     out = {}
     for name, s, T, prec, seed in (("3C-SiC 512 atoms, FP64, 300 K", st.bulk_3c_512(), 300.0, "fp64", 101),
                                    ("stepped slab 19,488 atoms, mixed, 2000 K", st.stepped_slab_20k(), 2000.0,
                                     "mixed", 102)):
         v = st.maxwell_boltzmann(s.types, T, seed=seed, frozen=s.frozen)
-        sysm = ctbop.System(P0, precision=prec, device=dev.index or 0)
+        sysm = ctbop.System(P1, precision=prec, device=dev.index or 0)
         sysm.set_stream(stream.cuda_stream)
         sysm.load(s, velocities=v)
         sysm.compute()
@@ -443,10 +443,10 @@ def run_ours(a):
         torch.cuda.synchronize()
 
     s, v, desc = workload(a.workload)
-    P0 = st.load_params("p0")
+    P1 = st.load_params("p1")
     stream = torch.cuda.Stream(device=dev)
 
-    sysm = ctbop.System(P0, precision="mixed", device=local)
+    sysm = ctbop.System(P1, precision="mixed", device=local)
     sysm.set_stream(stream.cuda_stream)
     sysm.load(s, velocities=v)
     sysm.compute()
@@ -497,7 +497,7 @@ def run_ours(a):
     # (the charge solve's iteration count changes as the slab heats).
     sysm.close()
     e2e_steps = a.e2e_steps if a.e2e_steps > 0 else a.steps
-    sysm = ctbop.System(P0, precision="mixed", device=local)
+    sysm = ctbop.System(P1, precision="mixed", device=local)
     sysm.set_stream(stream.cuda_stream)
     sysm.load(s, velocities=v)
     sysm.compute()
@@ -523,7 +523,7 @@ def run_ours(a):
 
     fp64 = None
     if not a.no_fp64:
-        s64 = ctbop.System(P0, precision="fp64", device=local)
+        s64 = ctbop.System(P1, precision="fp64", device=local)
         s64.set_stream(stream.cuda_stream)
         s64.load(s, velocities=v)
         s64.compute()
@@ -599,10 +599,10 @@ def _sample_structure(budget_per_step):
     one oracle step fits the budget."""
     from paper_1802_07871_gb300 import structures as st
     from oracle import ctbop_oracle as O
-    P0 = st.load_params("p0")
+    P1 = st.load_params("p1")
     probe = st.stepped_slab_small(8, 4, 6)
     t0 = time.perf_counter()
-    O.evaluate(probe.x, probe.types, probe.box, probe.pbc, P0)
+    O.evaluate(probe.x, probe.types, probe.box, probe.pbc, P1)
     t1 = time.perf_counter() - t0
     per_atom = t1 / probe.n
     best = probe
@@ -617,15 +617,15 @@ def cpu_baseline(budget_s=20.0, steps=None, warmup=0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload."""
     from paper_1802_07871_gb300 import structures as st
     from oracle import ctbop_oracle as O
-    P0 = st.load_params("p0")
+    P1 = st.load_params("p1")
     if steps is None:
         steps = 2
     s = _sample_structure(budget_s / (steps + 1 + warmup))
     v = st.maxwell_boltzmann(s.types, T_K, seed=103, frozen=s.frozen)
     if warmup:
-        O.velocity_verlet(s.x, v, s.types, s.box, s.pbc, P0, DT, warmup, s.frozen)
+        O.velocity_verlet(s.x, v, s.types, s.box, s.pbc, P1, DT, warmup, s.frozen)
     t0 = time.perf_counter()
-    O.velocity_verlet(s.x, v, s.types, s.box, s.pbc, P0, DT, steps, s.frozen)
+    O.velocity_verlet(s.x, v, s.types, s.box, s.pbc, P1, DT, steps, s.frozen)
     t = time.perf_counter() - t0
     return {"value": s.n * steps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{s.n}-atom stepped 4H-SiC slab with C adatoms (same shape as the workload), "

@@ -21,16 +21,21 @@
 // CG scalar are unchanged by adding a constant to r, so each update subtracts
 // the previous mean of r and accumulates the shift (mu = -(mean r + shift)).
 //
-// Precision: the iterate q, the recursion vectors r, p, s = H p and every
-// reduction (dots, sums) are FP64 (in FP32 the s = H p recursion loses
-// conjugacy and the iteration stalls); y = D^-1 r, w = H z, d, v, the matrix
+// Precision: the iterate q and every reduction (dots, sums, maxima, the
+// scalars alpha, beta, c, mu) are FP64. The recursion vectors r, p, s = H p,
+// the iteration's change dq = q - q0, y = M^-1 r, w = H z, d, v, the matrix
 // entries and the gathered y_j are in the working precision (FP32 in the
-// mixed policy). Rounding of y and d keeps sum z from being exactly zero, so
-// after the solve q is shifted uniformly onto sum q = Q.
+// mixed policy, FP64 in the FP64 policy). FP32 recursion vectors keep
+// conjugacy only because r.z is formed from the centred residual (below);
+// dq is folded into the FP64 q once per solve. Rounding of y and d keeps
+// sum z from being exactly zero, so after the solve q is shifted uniformly
+// onto sum q = Q.
 //
 // The matrix passes run one thread per atom over its column of the list
 // (entry e of atom i at e * ld + i): a warp load of entry e of 32 consecutive
-// atoms is one 128-byte line, four entries are in flight per thread, and the
+// atoms is one 128-byte line. The number of entries in flight per thread
+// (the batch depth B of k_cg_mv: 4, 8 or 16) is a template parameter, timed
+// on the live matrix after every list allocation and the fastest kept. The
 // FP64 epilogue (issued at a small fraction of the FP32 rate on this GPU) is
 // lane-parallel.
 //

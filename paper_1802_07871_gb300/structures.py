@@ -63,7 +63,7 @@ class Structure:
         return int(self.types.shape[0])
 
 
-def load_params(name: str = "p0") -> dict:
+def load_params(name: str = "p1") -> dict:
     """Load a parameter set (JSON) shipped with the package."""
     path = name if os.path.isfile(name) else os.path.join(_PARAM_DIR, f"{name}.json")
     with open(path) as fh:
@@ -104,6 +104,45 @@ def sic_3c(ncell: int = 4, a: float = 4.36, disp: float = 0.05, seed: int = 1,
     x = np.mod(x, box)
     return Structure(f"3C-SiC {nc[0]}x{nc[1]}x{nc[2]}", x, types, box,
                      np.array([True, True, True]))
+
+
+def sic_3c_110(rep=(1, 1, 1), a: float = 4.36, stretch_x: float = 0.0) -> Structure:
+    """Zincblende SiC in the frame x = [110]/sqrt2, y = [-110]/sqrt2, z = [001]:
+    a periodic tetragonal cell a/sqrt2 x a/sqrt2 x a holding 2 Si and 2 C,
+    replicated rep times. A strain along this x is a shear of the cubic
+    axes, so the cell carries the elastic constant C44. stretch_x scales
+    x (positions and box) by 1 + stretch_x."""
+    ah = a / math.sqrt(2.0)
+    # cubic-frame fractional sites of the 4 atoms, mapped to the rotated cell:
+    # Si at (0,0,0) and (1/2,1/2,0)a; C at (1/4,1/4,1/4) and (3/4,3/4,3/4)a
+    # minus a lattice vector, so that every atom lies inside the cell
+    cub = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.5], [0.25, 0.25, 0.25], [0.75, 0.25, 0.75]]) * a
+    rot = np.array([[1.0, 1.0, 0.0], [-1.0, 1.0, 0.0], [0.0, 0.0, math.sqrt(2.0)]]) / math.sqrt(2.0)
+    box1 = np.array([ah, ah, a])
+    x1 = np.mod(cub @ rot.T, box1)
+    t1 = np.array([SI, SI, C, C], dtype=np.int32)
+    rep = np.broadcast_to(np.asarray(rep, dtype=int), (3,))
+    cells = np.stack(np.meshgrid(*(np.arange(k) for k in rep), indexing="ij"), -1).reshape(-1, 3)
+    x = (cells[:, None, :] * box1 + x1[None, :, :]).reshape(-1, 3)
+    types = np.tile(t1, len(cells))
+    box = box1 * rep
+    f = np.array([1.0 + stretch_x, 1.0, 1.0])
+    return Structure(f"3C-SiC [110] cell {rep[0]}x{rep[1]}x{rep[2]}", x * f, types, box * f,
+                     np.array([True, True, True]))
+
+
+def sic_4h_bulk(nx: int = 1, ny: int = 1, n_periods: int = 1, a: float = 4.36) -> Structure:
+    """Periodic 4H-SiC: the slab geometry of sic_4h_slab (orthorhombic
+    a_h x sqrt(3) a_h in-plane cell, ABCB stacking, bilayer period a/sqrt(3))
+    with 4 n_periods bilayers and the z axis periodic (box c = 4 n_periods
+    a/sqrt(3)): the top Si bonds straight up to the C of the next period's
+    bottom bilayer. 16 nx ny n_periods atoms, ideal positions."""
+    P = a / math.sqrt(3.0)
+    s = sic_4h_slab(nx, ny, 4 * n_periods, a=a, n_frozen_bilayers=0)
+    x = s.x.copy()
+    x[:, 2] -= x[:, 2].min()
+    box = np.array([s.box[0], s.box[1], 4 * n_periods * P])
+    return Structure(f"4H-SiC bulk {nx}x{ny}x{n_periods}", x, s.types, box, np.array([True, True, True]))
 
 
 # --------------------------------------------------------------------------

@@ -44,5 +44,5 @@ def test_params_marshalling_l1_padding():
     from paper_1802_07871_gb300 import ctbop, structures as st
     p = ctbop.params_struct(st.load_params("pt"))
     assert p.g[1][1] == 1e30 and p.gamma[3][1] == 0.0
-    p0 = ctbop.params_struct(st.load_params("p0"))
-    assert p0.g[2][0] != p0.g[1][0]   # ordered pairs kept apart
+    p1 = ctbop.params_struct(st.load_params("p1"))
+    assert p1.g[2][0] != p1.g[1][0]   # ordered pairs kept apart

@@ -13,21 +13,21 @@ from paper_1802_07871_gb300 import desorption as D
 from paper_1802_07871_gb300 import structures as st
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 # removal energies are differences of two total energies, each within 1e-6
 # eV/atom (mixed) or 1e-9 (FP64) of the oracle
 TOL = {"fp64": 1e-7, "mixed": 1e-6}
 
 
 def _system(structs, prec):
-    sysm = ctbop.System(P0, precision=prec)
+    sysm = ctbop.System(P1, precision=prec)
     sysm.load_replicas(structs)
     sysm.compute()
     return sysm
 
 
 def _oracle_candidates(s):
-    c = O.coordination(s.x, s.types, s.box, s.pbc, P0)
+    c = O.coordination(s.x, s.types, s.box, s.pbc, P1)
     return np.nonzero((s.types == 0) & (c < 4) & ~s.frozen)[0], c
 
 
@@ -37,7 +37,7 @@ def test_coordination_matches_oracle(prec):
         sysm = _system([s], prec)
         c = sysm.get("coordination")
         sysm.close()
-        co = O.coordination(s.x, s.types, s.box, s.pbc, P0)
+        co = O.coordination(s.x, s.types, s.box, s.pbc, P1)
         bad = np.count_nonzero(c != co)
         assert bad == 0 if prec == "fp64" else bad <= 1, (bad, np.nonzero(c != co))
 
@@ -46,7 +46,7 @@ def test_coordination_matches_oracle(prec):
 def test_removal_energies_match_oracle(prec):
     s = st.stepped_slab_small(6, 3, 4)
     cand, _ = _oracle_candidates(s)
-    dEo, rmo = O.desorption_screen(s.x, s.types, s.box, s.pbc, P0, cand, threshold=4.3)
+    dEo, rmo = O.desorption_screen(s.x, s.types, s.box, s.pbc, P1, cand, threshold=4.3)
     sysm = _system([s], prec)
     dE = sysm.removal_energies(cand)
     sysm.close()
@@ -83,13 +83,13 @@ def test_several_source_replicas_and_a_single_atom():
     sysm.close()
     for (r, i), d in zip(picks, dE):
         s = structs[r]
-        ref = O.removal_energy(s.x, s.types, s.box, s.pbc, P0, i)
+        ref = O.removal_energy(s.x, s.types, s.box, s.pbc, P1, i)
         assert d == pytest.approx(ref, abs=TOL["fp64"] * s.n), (r, i)
 
 
 def test_arguments_and_state():
     s = st.stepped_slab_small(6, 3, 4)
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.load(s)
     with pytest.raises(ctbop.CtbopError, match="STATE"):
         sysm.get("coordination")                                   # no evaluation yet
@@ -116,10 +116,10 @@ def test_full_size_sampled_against_separate_systems():
         a = int(cand[i])
         keep = np.ones(s.n, bool)
         keep[a] = False
-        sub = ctbop.System(P0, precision="mixed")
+        sub = ctbop.System(P1, precision="mixed")
         sub.load(st.Structure("minus one", s.x[keep], s.types[keep], s.box, s.pbc, s.frozen[keep]))
         sub.compute()
-        ref = sub.get("energy")[0] + P0["self"]["E0"][0] - E
+        ref = sub.get("energy")[0] + P1["self"]["E0"][0] - E
         sub.close()
         assert dE[i] == pytest.approx(ref, abs=2 * TOL["mixed"] * s.n), (a, dE[i], ref)
 
@@ -127,7 +127,7 @@ def test_full_size_sampled_against_separate_systems():
 def test_desorption_run_removes_and_continues():
     s = st.stepped_slab_small(6, 3, 4)
     v = st.maxwell_boltzmann(s.types, 1500.0, seed=4, frozen=s.frozen)
-    run = D.DesorptionRun(s, P0, v, precision="mixed", T0=1500.0, tau=50.0, threshold=100.0)
+    run = D.DesorptionRun(s, P1, v, precision="mixed", T0=1500.0, tau=50.0, threshold=100.0)
     ev = run.run(1, steps_per_interval=20)
     n_cand = ev[0].candidates
     assert len(ev[0].removed) == n_cand > 0                       # every candidate is below 100 eV

@@ -9,11 +9,11 @@ from paper_1802_07871_gb300 import ctbop
 from paper_1802_07871_gb300 import structures as st
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 
 
 def _system(s, **kw):
-    sysm = ctbop.System(P0, **kw)
+    sysm = ctbop.System(P1, **kw)
     sysm.load(s)
     return sysm
 
@@ -59,7 +59,7 @@ def test_nonfinite_position_is_reported():
     s = st.bulk_3c_512()
     x = s.x.copy()
     x[7, 1] = np.nan
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.load(st.Structure("bad", x, s.types, s.box, s.pbc))
     with pytest.raises(ctbop.CtbopError, match="NONFINITE"):
         sysm.compute()
@@ -68,7 +68,7 @@ def test_nonfinite_position_is_reported():
 
 def test_invalid_arguments_are_rejected():
     s = st.bulk_3c_512()
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     with pytest.raises(ctbop.CtbopError, match="STATE"):
         sysm.set_types(s.types)                    # before set_layout
     with pytest.raises(ctbop.CtbopError, match="INVALID_ARG"):
@@ -95,7 +95,7 @@ def test_caller_buffers_are_checked_before_the_library_sees_them():
     rejected on the host: the library would read or write past them."""
     torch = pytest.importorskip("torch")
     s = st.bulk_3c_512()
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.load(s)
     with pytest.raises(ValueError, match="elements"):
         sysm.set_positions(s.x[:-1])
@@ -119,16 +119,16 @@ def test_caller_buffers_are_checked_before_the_library_sees_them():
 
 def test_create_rejects_bad_options():
     with pytest.raises(ctbop.CtbopError):
-        ctbop.System(P0, cg_max_iter=0)
+        ctbop.System(P1, cg_max_iter=0)
     with pytest.raises(ctbop.CtbopError):
-        ctbop.System(P0, skin=-0.1)
+        ctbop.System(P1, skin=-0.1)
 
 
 def test_empty_system_runs_every_entry_point():
     """A layout with no atoms at all: every entry point returns cleanly with
     empty results (zero energy)."""
     empty = st.Structure("empty", np.zeros((0, 3)), np.zeros(0, np.int32), np.full(3, 20.0), np.array([True] * 3))
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.load(empty)
     sysm.compute()
     assert sysm.get("energy").tolist() == [0.0]

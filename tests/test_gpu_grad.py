@@ -10,7 +10,7 @@ from paper_1802_07871_gb300 import ctbop
 from paper_1802_07871_gb300 import structures as st
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 
 
 def _cluster(n, seed, spread=3.2, min_sep=1.45):
@@ -37,10 +37,10 @@ def _leaf(d, path):
 
 
 def _gpu_grad(structs, precision="fp64", **loss):
-    sysm = ctbop.System(P0, precision=precision)
+    sysm = ctbop.System(P1, precision=precision)
     sysm.load_replicas(structs)
     L, G = sysm.param_grad(**loss)
-    out = ctbop.grad_to_dict(G, P0)
+    out = ctbop.grad_to_dict(G, P1)
     F = sysm.get("forces")
     sysm.close()
     return L, out, F
@@ -48,9 +48,9 @@ def _gpu_grad(structs, precision="fp64", **loss):
 
 def _compare(structs, loss, rtol, precision="fp64", ltol=1e-9):
     L, g, _ = _gpu_grad(structs, precision, **loss)
-    Lo = O.force_matching_loss(structs, P0, **loss)
+    Lo = O.force_matching_loss(structs, P1, **loss)
     assert L == pytest.approx(Lo, rel=ltol, abs=1e-12)
-    fd = O.loss_grad_fd(structs, P0, **loss)
+    fd = O.loss_grad_fd(structs, P1, **loss)
     scale = max(abs(v) for v in fd.values())
     worst = sorted(((abs(_leaf(g, p) - v) / (abs(v) + 1e-3 * scale), p, _leaf(g, p), v) for p, v in fd.items()),
                    reverse=True)[:5]
@@ -60,7 +60,7 @@ def _compare(structs, loss, rtol, precision="fp64", ltol=1e-9):
 
 def test_energy_loss_gradient_matches_oracle():
     structs = _batch()
-    E = [O.evaluate(s.x, s.types, s.box, s.pbc, P0)["E"] for s in structs]
+    E = [O.evaluate(s.x, s.types, s.box, s.pbc, P1)["E"] for s in structs]
     _compare(structs, dict(w_E=[0.5, 0.3], E_ref=[E[0] - 1.0, E[1] + 2.0]), rtol=1e-8)
 
 
@@ -69,9 +69,9 @@ def test_force_matching_gradient_matches_oracle():
     loss has energy and force terms, and the force term's gradient carries
     the charge response through the adjoint solve."""
     structs = _batch()
-    Pt = O.with_leaf(P0, ("pair", "SiC", "A"), P0["pair"]["SiC"]["A"] * 1.03)
-    Pt = O.with_leaf(Pt, ("self", "chi", 1), P0["self"]["chi"][1] * 0.97)
-    Pt = O.with_leaf(Pt, ("triplet", "SiCSi", "h", 1), P0["triplet"]["SiCSi"]["h"][1] + 0.05)
+    Pt = O.with_leaf(P1, ("pair", "SiC", "A"), P1["pair"]["SiC"]["A"] * 1.03)
+    Pt = O.with_leaf(Pt, ("self", "chi", 1), P1["self"]["chi"][1] * 0.97)
+    Pt = O.with_leaf(Pt, ("triplet", "SiCSi", "h", 1), P1["triplet"]["SiCSi"]["h"][1] + 0.05)
     ref = [O.evaluate(s.x, s.types, s.box, s.pbc, Pt) for s in structs]
     loss = dict(w_E=[0.2, 0.1], E_ref=[o["E"] for o in ref], w_F=[1.0, 0.5],
                 F_ref=np.concatenate([o["F"] for o in ref]))
@@ -83,7 +83,7 @@ def test_force_matching_gradient_matches_oracle():
 def test_energy_constant_gradient_exact():
     """dE/dE0_t is the count of type-t atoms, from the analytic kernel."""
     structs = _batch()
-    sysm = ctbop.System(P0, precision="fp64")
+    sysm = ctbop.System(P1, precision="fp64")
     sysm.load_replicas(structs)
     sysm.compute()
     E = sysm.get("energy")
@@ -99,7 +99,7 @@ def test_autograd_energy_backward_is_minus_force():
     import torch
     from paper_1802_07871_gb300.autograd import Energy
     structs = _batch()
-    sysm = ctbop.System(P0, precision="fp64")
+    sysm = ctbop.System(P1, precision="fp64")
     sysm.load_replicas(structs)
     x = torch.tensor(np.concatenate([s.x for s in structs]), dtype=torch.float64, requires_grad=True)
     E = Energy.apply(x, sysm)
@@ -127,13 +127,13 @@ def test_autograd_force_matching_step_reduces_loss():
     import torch
     from paper_1802_07871_gb300.autograd import ForceMatchingLoss
     structs = _batch()
-    Pt = O.with_leaf(P0, ("pair", "SiC", "B"), P0["pair"]["SiC"]["B"] * 1.02)
+    Pt = O.with_leaf(P1, ("pair", "SiC", "B"), P1["pair"]["SiC"]["B"] * 1.02)
     ref = [O.evaluate(s.x, s.types, s.box, s.pbc, Pt) for s in structs]
     kw = dict(w_E=[0.1, 0.1], E_ref=[o["E"] for o in ref], w_F=[1.0, 1.0],
               F_ref=np.concatenate([o["F"] for o in ref]))
-    sysm = ctbop.System(P0, precision="fp64")
+    sysm = ctbop.System(P1, precision="fp64")
     sysm.load_replicas(structs)
-    theta = torch.tensor(ctbop.params_vector(ctbop.params_struct(P0)), dtype=torch.float64, requires_grad=True)
+    theta = torch.tensor(ctbop.params_vector(ctbop.params_struct(P1)), dtype=torch.float64, requires_grad=True)
     L0 = ForceMatchingLoss.apply(theta, sysm, *kw.values())
     L0.backward()
     g = theta.grad.clone()
@@ -159,7 +159,7 @@ def _members():
 
 def _member_loss(kind):
     structs = _members()
-    Pt = st.perturbed_params(P0, 55)
+    Pt = st.perturbed_params(P1, 55)
     ref = [O.evaluate(s.x, s.types, s.box, s.pbc, Pt) for s in structs]
     nr = np.array([s.n for s in structs], float)
     loss = dict(w_E=1.0 / nr ** 2, E_ref=[o["E"] for o in ref])
@@ -186,15 +186,15 @@ def test_differentiation_batch_full_size():
     halves (replicas do not interact)."""
     from gpu_helpers import oracle_EF_many
     structs = st.differentiation_batch()
-    Pt = st.perturbed_params(P0, 55)
+    Pt = st.perturbed_params(P1, 55)
     E_ref, F_ref = oracle_EF_many(structs, Pt)
-    E_o, F_o = oracle_EF_many(structs, P0)
+    E_o, F_o = oracle_EF_many(structs, P1)
     nr = np.array([s.n for s in structs], float)
     w_E, w_F = 1.0 / nr ** 2, 1.0 / (3.0 * nr)
     E_ref = np.array(E_ref)
     F_ref = np.concatenate(F_ref)
     loss = dict(w_E=w_E, E_ref=E_ref, w_F=w_F, F_ref=F_ref)
-    sysm = ctbop.System(P0, precision="fp64")
+    sysm = ctbop.System(P1, precision="fp64")
     sysm.load_replicas(structs)
     L, G = sysm.param_grad(**loss)
     E, F = sysm.get("energy"), sysm.get("forces")
@@ -205,7 +205,7 @@ def test_differentiation_batch_full_size():
     rep = np.repeat(np.arange(len(structs)), nr.astype(int))
     Lo = np.sum(w_E * (E_o - E_ref) ** 2) + np.sum(w_F[rep][:, None] * (F_o - F_ref) ** 2)
     assert L == pytest.approx(Lo, rel=1e-8)
-    g = ctbop.grad_to_dict(G, P0)
+    g = ctbop.grad_to_dict(G, P1)
     a = 2.0 * w_E * (E_o - E_ref)
     for t in (0, 1):
         n_t = np.array([np.sum(s.types == t) for s in structs])
@@ -216,7 +216,7 @@ def test_differentiation_batch_full_size():
         sub = structs[sl]
         m = np.zeros(len(structs), bool)
         m[sl] = True
-        part = ctbop.System(P0, precision="fp64")
+        part = ctbop.System(P1, precision="fp64")
         part.load_replicas(sub)
         parts.append(ctbop.params_vector(part.param_grad(w_E=w_E[m], E_ref=E_ref[m], w_F=w_F[m],
                                                           F_ref=F_ref[np.repeat(m, nr.astype(int))])[1]))
@@ -246,15 +246,15 @@ def test_set_params_equals_a_fresh_system(prec):
     gives what a new system with those parameters gives: energies, forces,
     charges, and the force-matching loss and gradient."""
     structs = _members()
-    Pt = st.perturbed_params(P0, 55)
+    Pt = st.perturbed_params(P1, 55)
     a = ctbop.System(Pt, precision=prec)
     a.load_replicas(structs)
     a.compute()
     E_ref, F_ref = a.get("energy"), a.get("forces")
-    a.set_params(P0)
+    a.set_params(P1)
     a.compute()
     Ea, Fa, qa = a.get("energy"), a.get("forces"), a.get("charges")
-    b = ctbop.System(P0, precision=prec)
+    b = ctbop.System(P1, precision=prec)
     b.load_replicas(structs)
     b.compute()
     Eb, Fb, qb = b.get("energy"), b.get("forces"), b.get("charges")
@@ -282,14 +282,14 @@ def test_param_grad_on_a_non_blocking_stream():
     before the evaluation finished would differ."""
     torch = pytest.importorskip("torch")
     structs = st.differentiation_batch()[:96]
-    Pt = st.perturbed_params(P0, 55)
+    Pt = st.perturbed_params(P1, 55)
     ref = [O.evaluate(s.x, s.types, s.box, s.pbc, Pt) for s in structs]
     nr = np.array([s.n for s in structs], float)
     loss = dict(w_E=1.0 / nr ** 2, E_ref=[o["E"] for o in ref], w_F=1.0 / (3.0 * nr),
                 F_ref=np.concatenate([o["F"] for o in ref]))
     L0, g0, F0 = _gpu_grad(structs, **loss)
     stream = torch.cuda.Stream()
-    sysm = ctbop.System(P0, precision="fp64")
+    sysm = ctbop.System(P1, precision="fp64")
     sysm.set_stream(stream.cuda_stream)
     sysm.load_replicas(structs)
     L1, G1 = sysm.param_grad(**loss)
@@ -298,6 +298,6 @@ def test_param_grad_on_a_non_blocking_stream():
     # equal up to the order of FP64 atomic sums (1e-11 eV/A seen)
     assert L1 == pytest.approx(L0, rel=1e-10)
     np.testing.assert_allclose(F1, F0, rtol=0, atol=1e-9)
-    g1 = ctbop.grad_to_dict(G1, P0)
+    g1 = ctbop.grad_to_dict(G1, P1)
     for k in ("A", "lambda1", "R", "S"):
         np.testing.assert_allclose(g1["pair"]["SiC"][k], g0["pair"]["SiC"][k], rtol=1e-8)

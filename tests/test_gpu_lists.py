@@ -14,7 +14,7 @@ from paper_1802_07871_gb300 import ctbop
 from paper_1802_07871_gb300 import structures as st
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 SKIN = 0.3
 TYPES = ["Si", "C"]
 
@@ -28,10 +28,10 @@ def _s_matrix(params):
 
 
 def _oracle_counts(s):
-    rall = P0["coulomb"]["r_coul"] + SKIN
+    rall = P1["coulomb"]["r_coul"] + SKIN
     i, j, n, u = O.pairs(s.x, s.box, s.pbc, rall)
     r = np.sqrt(np.einsum("ij,ij->i", u, u))
-    S = _s_matrix(P0)
+    S = _s_matrix(P1)
     cov = r < S[s.types[i], s.types[j]] + SKIN
     per_all = np.bincount(i, minlength=s.n)
     per_cov = np.bincount(i[cov], minlength=s.n)
@@ -39,7 +39,7 @@ def _oracle_counts(s):
 
 
 def _gpu_counts(structs, prec):
-    sysm = ctbop.System(P0, precision=prec, skin=SKIN)
+    sysm = ctbop.System(P1, precision=prec, skin=SKIN)
     sysm.load_replicas(structs)
     sysm.compute()
     d = sysm.status()

@@ -9,7 +9,7 @@ from paper_1802_07871_gb300 import ctbop
 from paper_1802_07871_gb300 import structures as st
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 
 
 def _wrap(d, box, pbc):
@@ -26,13 +26,13 @@ def test_nvt_matches_oracle_trajectory(prec, case):
         s = st.stepped_slab_small(6, 3, 4)
         v = st.maxwell_boltzmann(s.types, 600.0, seed=93, frozen=s.frozen)
     T0, tau, n = 1800.0, 8.0, 20
-    sysm = ctbop.System(P0, precision=prec)
+    sysm = ctbop.System(P1, precision=prec)
     sysm.load(s, velocities=v)
     sysm.set_thermostat(T0, tau)
     sysm.step(n, 0.5)
     xg, vg, th = sysm.get("positions"), sysm.get("velocities"), sysm.get("thermostat")[0]
     sysm.close()
-    xo, vo, qo, xi, eta, ext = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P0, 0.5, n, T0, tau, s.frozen)
+    xo, vo, qo, xi, eta, ext = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P1, 0.5, n, T0, tau, s.frozen)
     tol = 1e-9 if prec == "fp64" else 1e-5
     assert np.max(np.abs(_wrap(xg - xo, s.box, s.pbc))) < tol
     assert np.max(np.abs(vg - vo)) < tol
@@ -43,7 +43,7 @@ def test_nvt_matches_oracle_trajectory(prec, case):
 
 
 def _gpu_extended(s, v, dt, n, every):
-    sysm = ctbop.System(P0, precision="fp64")
+    sysm = ctbop.System(P1, precision="fp64")
     sysm.load(s, velocities=v)
     sysm.set_thermostat(1200.0, 10.0)
     sysm.compute()
@@ -67,7 +67,7 @@ def test_nvt_extended_energy_follows_oracle_and_drifts_as_dt_squared():
     v = st.maxwell_boltzmann(s.types, 300.0, seed=95)
     g1 = _gpu_extended(s, v, 0.5, 200, 10)
     g2 = _gpu_extended(s, v, 0.25, 400, 20)
-    *_, ext = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P0, 0.5, 200, 1200.0, 10.0)
+    *_, ext = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P1, 0.5, 200, 1200.0, 10.0)
     np.testing.assert_allclose(g1[1:], ext[9::10], rtol=0, atol=1e-6 * s.n)
     d1, d2 = np.max(np.abs(g1 - g1[0])), np.max(np.abs(g2 - g2[0]))
     assert 3.0 < d1 / d2 < 6.0, (d1, d2)
@@ -80,7 +80,7 @@ def test_nvt_and_nve_replicas_in_one_batch():
     b = st.sic_3c(2, 4.36, 0.05, seed=97)
     va = st.maxwell_boltzmann(a.types, 500.0, seed=98)
     vb = st.maxwell_boltzmann(b.types, 500.0, seed=99)
-    sysm = ctbop.System(P0, precision="fp64")
+    sysm = ctbop.System(P1, precision="fp64")
     sysm.load_replicas([a, b])
     sysm.set_velocities(np.concatenate([va, vb]))
     sysm.set_thermostat([2000.0, 0.0], [5.0, 1.0])
@@ -88,7 +88,7 @@ def test_nvt_and_nve_replicas_in_one_batch():
     xb = sysm.get("positions")[a.n:]
     th = sysm.get("thermostat")
     sysm.close()
-    ref = ctbop.System(P0, precision="fp64")
+    ref = ctbop.System(P1, precision="fp64")
     ref.load(b, velocities=vb)
     ref.step(15, 0.5)
     xr = ref.get("positions")

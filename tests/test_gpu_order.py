@@ -10,7 +10,7 @@ from paper_1802_07871_gb300 import ctbop
 from paper_1802_07871_gb300 import structures as st
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 
 
 def _structs():
@@ -18,13 +18,13 @@ def _structs():
 
 
 def _run(structs, order, prec="fp64"):
-    sysm = ctbop.System(P0, precision=prec)
+    sysm = ctbop.System(P1, precision=prec)
     if order == "random":
         off = np.concatenate([[0], np.cumsum([s.n for s in structs])])
         sysm.load_replicas(structs, order=None)
         rng = np.random.default_rng(0)
         perm = np.concatenate([o + rng.permutation(s.n) for o, s in zip(off, structs)])
-        sysm2 = ctbop.System(P0, precision=prec)
+        sysm2 = ctbop.System(P1, precision=prec)
         sysm2.set_layout(off)
         sysm2.set_order(perm)
         sysm2.set_box(np.array([s.box for s in structs]), np.array([s.pbc for s in structs]))
@@ -74,7 +74,7 @@ def test_results_do_not_depend_on_storage_order(order):
 def test_bad_orders_are_refused():
     structs = _structs()
     off = np.concatenate([[0], np.cumsum([s.n for s in structs])])
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.set_layout(off)
     bad = np.arange(off[-1])
     bad[0], bad[-1] = bad[-1], bad[0]          # swaps atoms of two replicas

@@ -9,7 +9,7 @@ from paper_1802_07871_gb300 import structures as st
 from tests.gpu_helpers import TOL, compare, gpu_eval, oracle_eval, sampled_local_check
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 PT = st.load_params("pt")
 PRECS = ["fp64", "mixed"]
 
@@ -30,8 +30,8 @@ def _cluster(n, seed, spread=3.5, min_sep=1.45):
 def test_bulk_512(prec):
     """3C-SiC 4x4x4 cells, 512 atoms, +-0.05 A displacements, periodic."""
     s = st.bulk_3c_512()
-    g = gpu_eval(s, P0, prec)
-    o = oracle_eval(s, P0)
+    g = gpu_eval(s, P1, prec)
+    o = oracle_eval(s, P1)
     compare(g, o, s.n, prec)
     assert g["status"]["rc"] == "OK"
 
@@ -44,15 +44,15 @@ def test_bulk_512_after_100_fp64_steps(prec):
     positions."""
     from paper_1802_07871_gb300 import ctbop
     s = st.bulk_3c_512()
-    md = ctbop.System(P0, precision="fp64")
+    md = ctbop.System(P1, precision="fp64")
     md.load(s, velocities=st.maxwell_boltzmann(s.types, 300.0, seed=101))
     md.compute()
     md.step(100, 0.5)
     x = md.get("positions")
     md.close()
     s100 = st.Structure(s.name, x, s.types, s.box, s.pbc, s.frozen)
-    g = gpu_eval(s100, P0, prec)
-    o = oracle_eval(s100, P0)
+    g = gpu_eval(s100, P1, prec)
+    o = oracle_eval(s100, P1)
     compare(g, o, s.n, prec)
     assert g["status"]["rc"] == "OK"
 
@@ -61,8 +61,8 @@ def test_bulk_512_after_100_fp64_steps(prec):
 def test_stepped_slab_with_adatoms(prec):
     """Open-z 4H-SiC(0001) staircase slab with C adatoms and a frozen bottom."""
     s = st.stepped_slab_small(8, 4, 6)
-    g = gpu_eval(s, P0, prec)
-    o = oracle_eval(s, P0)
+    g = gpu_eval(s, P1, prec)
+    o = oracle_eval(s, P1)
     compare(g, o, s.n, prec)
 
 
@@ -75,8 +75,8 @@ def test_small_periodic_boxes_images(prec, ncell):
     t = s.types.copy()
     t[1] = 1 - t[1]
     s = st.Structure("small", s.x, t, s.box, s.pbc)
-    g = gpu_eval(s, P0, prec)
-    o = oracle_eval(s, P0)
+    g = gpu_eval(s, P1, prec)
+    o = oracle_eval(s, P1)
     compare(g, o, s.n, prec, stress=True)
 
 
@@ -84,8 +84,8 @@ def test_small_periodic_boxes_images(prec, ncell):
 def test_open_cluster(prec):
     """Random Si/C cluster, open boundaries, pairs down to 1.45 A."""
     s = _cluster(41, 3)
-    g = gpu_eval(s, P0, prec)
-    o = oracle_eval(s, P0)
+    g = gpu_eval(s, P1, prec)
+    o = oracle_eval(s, P1)
     compare(g, o, s.n, prec, stress=True)
 
 
@@ -99,21 +99,21 @@ def test_batched_replicas_uneven(prec):
             st.Structure("atom", np.array([[5.0, 5.0, 5.0]]), np.array([1], np.int32), np.full(3, 12.0),
                          np.array([False] * 3)),
             st.sic_4h_slab(3, 2, 4, step="strip")]
-    g = gpu_eval(reps, P0, prec)
+    g = gpu_eval(reps, P1, prec)
     off = np.concatenate([[0], np.cumsum([s.n for s in reps])])
     for r, s in enumerate(reps):
-        o = oracle_eval(s, P0) if s.n else {"F": np.zeros((0, 3)), "E": 0.0, "q": np.zeros(0),
+        o = oracle_eval(s, P1) if s.n else {"F": np.zeros((0, 3)), "E": 0.0, "q": np.zeros(0),
                                               "virial": np.zeros((3, 3)), "e_atom": np.zeros(0), "mu": None}
         compare(g, o, s.n, prec, sl=slice(off[r], off[r + 1]), r=r, stress=True)
     # the lone C atom: no neighbours, q = Q = 0, E = E0(C)
-    assert abs(g["energy"][3] - P0["self"]["E0"][1]) < 1e-12
+    assert abs(g["energy"][3] - P1["self"]["E0"][1]) < 1e-12
 
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_charged_system(prec):
     s = st.sic_4h_slab(3, 2, 4, step="strip")
-    g = gpu_eval(s, P0, prec, Q=[1.5])
-    o = oracle_eval(s, P0, Q=1.5)
+    g = gpu_eval(s, P1, prec, Q=[1.5])
+    o = oracle_eval(s, P1, Q=1.5)
     compare(g, o, s.n, prec)
     assert abs(g["charges"].sum() - 1.5) < 1e-9
 
@@ -122,8 +122,8 @@ def test_charged_system(prec):
 def test_fixed_charges(prec):
     s = st.sic_3c(2, 4.36, 0.1, seed=77)
     q = np.random.default_rng(4).normal(0, 0.3, s.n)
-    g = gpu_eval(s, P0, prec, charges=q, fixed=True)
-    o = oracle_eval(s, P0, q=q)
+    g = gpu_eval(s, P1, prec, charges=q, fixed=True)
+    o = oracle_eval(s, P1, q=q)
     compare(g, o, s.n, prec, check_mu=False)
 
 
@@ -140,8 +140,8 @@ def test_tersoff_reduction_parameters(prec):
 def test_dimer_closed_form_gpu():
     x = np.array([[10.0, 10.0, 10.0], [11.9, 10.0, 10.0]])
     s = st.Structure("dimer", x, np.array([0, 1], np.int32), np.full(3, 30.0), np.array([False] * 3))
-    g = gpu_eval(s, P0, "fp64")
-    o = oracle_eval(s, P0)
+    g = gpu_eval(s, P1, "fp64")
+    o = oracle_eval(s, P1)
     compare(g, o, 2, "fp64")
     assert abs(g["charges"][0] + g["charges"][1]) < 1e-14
 
@@ -153,12 +153,12 @@ def test_device_pointer_path_matches_host(monkeypatch):
     monkeypatch.setenv("CTBOP_MV_BATCH", "8")
     from paper_1802_07871_gb300 import ctbop
     s = st.sic_3c(2, 4.36, 0.1, seed=3)
-    ref = ctbop.System(P0, precision="mixed")
+    ref = ctbop.System(P1, precision="mixed")
     ref.load(s, order=None)                # the storage order the device path below uses
     ref.compute()
     gh = {"forces": ref.get("forces")}
     ref.close()
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.set_stream(torch.cuda.current_stream().cuda_stream)
     sysm.set_layout([0, s.n])
     sysm.set_box(s.box, s.pbc)
@@ -180,13 +180,13 @@ def test_md_matches_oracle_trajectory(prec):
     from paper_1802_07871_gb300 import ctbop
     s = st.bulk_3c_512()
     v = st.maxwell_boltzmann(s.types, 300.0, seed=101)
-    sysm = ctbop.System(P0, precision=prec)
+    sysm = ctbop.System(P1, precision=prec)
     sysm.load(s, velocities=v)
     sysm.step(20, 0.5)
     xg = sysm.get("positions")
     vg = sysm.get("velocities")
     sysm.close()
-    xo, vo, qo, _ = O.velocity_verlet(s.x, v, s.types, s.box, s.pbc, P0, 0.5, 20)
+    xo, vo, qo, _ = O.velocity_verlet(s.x, v, s.types, s.box, s.pbc, P1, 0.5, 20)
     d = xg - xo
     d -= np.round(d / s.box) * s.box
     tol = 1e-9 if prec == "fp64" else 1e-5
@@ -198,10 +198,10 @@ def _nve_trace(prec, dt, nsteps, every):
     from paper_1802_07871_gb300 import ctbop
     s = st.bulk_3c_512()
     v = st.maxwell_boltzmann(s.types, 300.0, seed=101)
-    sysm = ctbop.System(P0, precision=prec)
+    sysm = ctbop.System(P1, precision=prec)
     sysm.load(s, velocities=v)
     sysm.compute()
-    e0 = sysm.get("energy")[0] + O.kinetic_energy(v, s.types, P0)
+    e0 = sysm.get("energy")[0] + O.kinetic_energy(v, s.types, P1)
     et = []
     for _ in range(nsteps // every):
         sysm.step(every, dt)
@@ -235,14 +235,14 @@ def test_full_size_slab_20k_sampled(prec):
     by the oracle on local cuts with the GPU charges held fixed; charge
     stationarity dE/dq_i = mu at the sampled atoms; neutrality."""
     s = st.stepped_slab_20k()
-    g = gpu_eval(s, P0, prec)
+    g = gpu_eval(s, P1, prec)
     rng = np.random.default_rng(20)
     top = np.argsort(s.x[:, 2])[-200:]
     samples = np.concatenate([rng.choice(s.n, 24, replace=False), rng.choice(top, 8, replace=False)])
-    sampled_local_check(s, P0, g, prec, samples)
+    sampled_local_check(s, P1, g, prec, samples)
     assert abs(g["charges"].sum()) < 1e-8
     # total energy per atom against the oracle's full solve (CG path)
-    o = oracle_eval(s, P0)
+    o = oracle_eval(s, P1)
     assert abs(g["energy"][0] - o["E"]) / s.n <= TOL[prec]["energy"]
     assert np.max(np.abs(g["charges"] - o["q"])) <= TOL[prec]["charge"]
     # Newton's third law holds for the whole system (all forces are internal)
@@ -253,11 +253,11 @@ def test_full_size_slab_1m_sampled():
     """The ~1.005M-atom stepped slab with C adatoms, mixed precision, in the
     launch configuration the benchmark times: sampled local oracle checks."""
     s = st.stepped_slab_1m()
-    g = gpu_eval(s, P0, "mixed")
+    g = gpu_eval(s, P1, "mixed")
     rng = np.random.default_rng(1)
     ad = np.nonzero(s.types == 1)[0][-900:]
     samples = np.concatenate([rng.choice(s.n, 24, replace=False), rng.choice(ad, 8, replace=False)])
-    sampled_local_check(s, P0, g, "mixed", samples)
+    sampled_local_check(s, P1, g, "mixed", samples)
     assert abs(g["charges"].sum()) < 1e-6
 
 
@@ -268,9 +268,9 @@ def test_annealing_ensemble_replicas(prec):
     flakes on SiC, uneven sizes; every replica against its own oracle
     evaluation."""
     structs, _ = st.annealing_ensemble(n_replicas=9, seed=7, n_min=150, n_max=500)
-    g = gpu_eval(structs, P0, prec)
+    g = gpu_eval(structs, P1, prec)
     off = 0
     for r, s in enumerate(structs):
-        o = oracle_eval(s, P0)
+        o = oracle_eval(s, P1)
         compare(g, o, s.n, prec, sl=slice(off, off + s.n), r=r, stress=True)
         off += s.n

@@ -11,11 +11,11 @@ from paper_1802_07871_gb300 import ctbop
 from paper_1802_07871_gb300 import structures as st
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 
 
 def _eval(structs, prec, pc):
-    sysm = ctbop.System(P0, precision=prec, precond=pc)
+    sysm = ctbop.System(P1, precision=prec, precond=pc)
     sysm.load_replicas(structs)
     sysm.compute()
     out = {k: sysm.get(k) for k in ("charges", "energy", "forces", "mu")}
@@ -38,7 +38,7 @@ def test_same_minimiser(prec):
     # and both against the oracle, replica by replica
     off = np.cumsum([0] + [s.n for s in structs])
     for r, s in enumerate(structs):
-        o = O.evaluate(s.x, s.types, s.box, s.pbc, P0)
+        o = O.evaluate(s.x, s.types, s.box, s.pbc, P1)
         assert np.max(np.abs(a["charges"][off[r]:off[r + 1]] - o["q"])) < (1e-8 if prec == "fp64" else 3e-5)
 
 
@@ -50,7 +50,7 @@ def test_fewer_iterations_in_md_on_the_slab():
     v = st.maxwell_boltzmann(s.types, 2500.0, seed=103, frozen=s.frozen)
     it, q = {}, {}
     for pc in ("block", "jacobi"):
-        sysm = ctbop.System(P0, precision="mixed", precond=pc)
+        sysm = ctbop.System(P1, precision="mixed", precond=pc)
         sysm.load(s, velocities=v)
         sysm.compute()
         sysm.step(5, 0.5)
@@ -65,4 +65,4 @@ def test_fewer_iterations_in_md_on_the_slab():
 
 def test_bad_option_is_rejected():
     with pytest.raises(ValueError):
-        ctbop.System(P0, precond="ilu")
+        ctbop.System(P1, precond="ilu")

@@ -14,7 +14,7 @@ from paper_1802_07871_gb300 import ctbop
 from paper_1802_07871_gb300 import structures as st
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 OPEN = np.array([False] * 3)
 
 
@@ -41,7 +41,7 @@ CASES = {
 
 
 def _gpu_relax(structs, prec, **kw):
-    sysm = ctbop.System(P0, precision=prec)
+    sysm = ctbop.System(P1, precision=prec)
     sysm.load_replicas(structs)
     it, fm = sysm.minimize(**kw)
     x, v, E, F = sysm.get("positions"), sysm.get("velocities"), sysm.get("energy"), sysm.get("forces")
@@ -55,7 +55,7 @@ def test_trajectory_matches_oracle(case, prec):
     s = CASES[case]()
     n = 25
     it, fm, x, v, E, F = _gpu_relax([s], prec, max_iter=n, fmax=1e-12)
-    xo, ito, Eo, ok = O.fire_minimize(s.x, s.types, s.box, s.pbc, P0, frozen=s.frozen, n_iter=n)
+    xo, ito, Eo, ok = O.fire_minimize(s.x, s.types, s.box, s.pbc, P1, frozen=s.frozen, n_iter=n)
     assert it[0] == -1 and ito == n and not ok
     tol = 1e-9 if prec == "fp64" else 1e-4
     assert np.max(np.abs(_wrap(x - xo, s.box, s.pbc))) < tol
@@ -84,9 +84,9 @@ def test_reaches_oracle_minima(prec, fmax, tol):
     structs = [_dimer(), _si3()]
     it, fm, x, v, E, F = _gpu_relax(structs, prec, max_iter=5000, fmax=fmax)
     assert np.all(it > 0) and np.all(fm < fmax)
-    xd, _, _, okd = O.fire_minimize(structs[0].x, structs[0].types, structs[0].box, OPEN, P0, fmax=1e-7,
+    xd, _, _, okd = O.fire_minimize(structs[0].x, structs[0].types, structs[0].box, OPEN, P1, fmax=1e-7,
                                     max_iter=5000)
-    xs, _, _, oks = O.fire_minimize(structs[1].x, structs[1].types, structs[1].box, OPEN, P0, fmax=1e-7,
+    xs, _, _, oks = O.fire_minimize(structs[1].x, structs[1].types, structs[1].box, OPEN, P1, fmax=1e-7,
                                     max_iter=5000)
     assert okd and oks
     assert np.linalg.norm(x[1] - x[0]) == pytest.approx(np.linalg.norm(xd[1] - xd[0]), abs=tol)
@@ -121,7 +121,7 @@ def test_stationary_crystal_and_arguments():
     s = st.sic_3c(2, 4.36, 0.0, seed=1)
     it, fm, x, v, E, F = _gpu_relax([s], "fp64", max_iter=100, fmax=1e-6)
     assert it[0] == 0 and np.max(np.abs(_wrap(x - s.x, s.box, s.pbc))) == 0.0
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.load(s)
     for kw in (dict(max_iter=-1), dict(fmax=0.0), dict(dt0=2.0, dt_max=1.0)):
         with pytest.raises(ctbop.CtbopError, match="INVALID_ARG"):
@@ -134,7 +134,7 @@ def test_full_size_slab_invariants():
     atoms stay, velocities end at zero, and the forces reported are the
     evaluation at the final positions."""
     s = st.stepped_slab_20k()
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.load(s)
     sysm.compute()
     E0 = sysm.get("energy")[0]

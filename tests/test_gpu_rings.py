@@ -14,8 +14,8 @@ from paper_1802_07871_gb300 import rings as RG
 from paper_1802_07871_gb300 import structures as st
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
-SCC = P0["pair"]["CC"]["S"]
+P1 = st.load_params("p1")
+SCC = P1["pair"]["CC"]["S"]
 OPEN = np.array([False] * 3)
 
 
@@ -28,7 +28,7 @@ def _pdist(a, b, box, pbc):
 def _compare(structs, prec, bond_cut=0.0):
     """Every GPU ring matches one oracle ring of the same size and centre
     (periodic distance), one to one; 6-ring orientations agree."""
-    sysm = ctbop.System(P0, precision=prec)
+    sysm = ctbop.System(P1, precision=prec)
     sysm.load_replicas(structs)
     sysm.compute()
     rec = sysm.rings(bond_cut=bond_cut)
@@ -98,7 +98,7 @@ def test_annealing_ensemble_full_size():
     600 atoms against the oracle one by one (the rest: every record is a
     valid primitive-ring record of its replica's type mix)."""
     structs, _ = st.annealing_ensemble(256, seed=4)
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.load_replicas(structs)
     sysm.compute()
     rec = sysm.rings()
@@ -120,7 +120,7 @@ def test_annealing_ensemble_full_size():
 
 def test_arguments_and_state():
     s = st.graphene_sheet(100, seed=1, n_stone_wales=0, disp=0.0)
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.load(s)
     with pytest.raises(ctbop.CtbopError, match="STATE"):
         sysm.rings()

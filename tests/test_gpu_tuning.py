@@ -10,11 +10,11 @@ from paper_1802_07871_gb300 import ctbop
 from paper_1802_07871_gb300 import structures as st
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 
 
 def _run(s, prec):
-    sysm = ctbop.System(P0, precision=prec)
+    sysm = ctbop.System(P1, precision=prec)
     sysm.load(s)
     sysm.compute()
     out = sysm.get("forces"), sysm.get("charges"), sysm.status()

@@ -56,7 +56,7 @@ def test_morton_order_edge_cases():
 
 # ---------------------------------------------------------------- parameters
 def test_parameter_vector_round_trip():
-    P = ctbop.params_struct(st.load_params("p0"))
+    P = ctbop.params_struct(st.load_params("p1"))
     v = ctbop.params_vector(P)
     assert v.shape == (144,) and np.all(np.isfinite(v))
     assert bytes(ctbop.params_from_vector(v)) == bytes(P)

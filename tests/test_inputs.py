@@ -6,7 +6,7 @@ import pytest
 
 from paper_1802_07871_gb300 import structures as st
 
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 
 
 @pytest.fixture(scope="module")
@@ -57,18 +57,18 @@ def test_clusters_keep_their_separation(batch):
 
 
 def test_perturbed_params_change_only_stated_leaves():
-    Pt = st.perturbed_params(P0, 55, rel=0.02)
-    for name in P0["pair"]:
-        for k, v in P0["pair"][name].items():
+    Pt = st.perturbed_params(P1, 55, rel=0.02)
+    for name in P1["pair"]:
+        for k, v in P1["pair"][name].items():
             if k in ("A", "B", "lambda1", "lambda2"):
                 assert abs(Pt["pair"][name][k] / v - 1.0) <= 0.02 and Pt["pair"][name][k] != v
             else:
                 assert Pt["pair"][name][k] == v
     for k in ("chi", "J"):
-        for a, b in zip(Pt["self"][k], P0["self"][k]):
+        for a, b in zip(Pt["self"][k], P1["self"][k]):
             assert abs(a / b - 1.0) <= 0.02
-    assert Pt["self"]["E0"] == P0["self"]["E0"]
-    assert Pt["triplet"] == P0["triplet"] and Pt["bond"] == P0["bond"] and Pt["coulomb"] == P0["coulomb"]
+    assert Pt["self"]["E0"] == P1["self"]["E0"]
+    assert Pt["triplet"] == P1["triplet"] and Pt["bond"] == P1["bond"] and Pt["coulomb"] == P1["coulomb"]
 
 
 def test_sic_3c_cubic_unchanged_by_shape_argument():

@@ -162,7 +162,7 @@ def test_angular_minima_match_paper():
     """Sec. 3.1: the minimum bond angle of zeta_1 is 180 deg and that of
     zeta_2 is 127 deg. The synthetic parameter set honours both for every
     type triplet."""
-    P = O.tables(st.load_params("p0"))
+    P = O.tables(st.load_params("p1"))
     theta = np.radians(np.linspace(60.0, 180.0, 120001))
     ct = np.cos(theta)
     want = [GOLDEN["angle_min_zeta1_deg"]["value"], GOLDEN["angle_min_zeta2_deg"]["value"]]

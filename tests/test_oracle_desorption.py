@@ -23,12 +23,12 @@ import pytest
 from oracle import ctbop_oracle as O
 from paper_1802_07871_gb300 import structures as st
 
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 OPEN = np.array([False] * 3)
 
 
 def _dimer_energy(r):
-    pr, se, co = P0["pair"]["SiC"], P0["self"], P0["coulomb"]
+    pr, se, co = P1["pair"]["SiC"], P1["self"], P1["coulomb"]
     fA = pr["B"] * math.exp(-pr["lambda2"] * r)
     fR = pr["A"] * math.exp(-pr["lambda1"] * r)
     gam = math.sqrt(co["gamma"][0] * co["gamma"][1])
@@ -44,17 +44,17 @@ def _dimer_energy(r):
 @pytest.mark.parametrize("i", [0, 1])
 def test_dimer(r, i):
     x = np.array([[10.0, 10.0, 10.0], [10.0 + r, 10.0, 10.0]])
-    dE = O.removal_energy(x, np.array([0, 1]), np.full(3, 40.0), OPEN, P0, i)
-    ref = P0["self"]["E0"][0] + P0["self"]["E0"][1] - _dimer_energy(r)
+    dE = O.removal_energy(x, np.array([0, 1]), np.full(3, 40.0), OPEN, P1, i)
+    ref = P1["self"]["E0"][0] + P1["self"]["E0"][1] - _dimer_energy(r)
     assert dE == pytest.approx(ref, rel=1e-12, abs=1e-12)
 
 
 @pytest.mark.parametrize("d", [2.2, 2.35, 2.44])
 def test_linear_si3_end_atom(d):
-    pr, bo, tp = P0["pair"]["SiSi"], P0["bond"]["SiSi"], P0["triplet"]["SiSiSi"]
+    pr, bo, tp = P1["pair"]["SiSi"], P1["bond"]["SiSi"], P1["triplet"]["SiSiSi"]
     x = np.array([[10.0, 10.0, 10.0], [10.0 + d, 10.0, 10.0], [10.0 + 2 * d, 10.0, 10.0]])
     t = np.zeros(3, int)
-    dE = O.removal_energy(x, t, np.full(3, 40.0), OPEN, P0, 2)
+    dE = O.removal_energy(x, t, np.full(3, 40.0), OPEN, P1, 2)
     fR = pr["A"] * math.exp(-pr["lambda1"] * d)
     fA = pr["B"] * math.exp(-pr["lambda2"] * d)
     p, sg = bo["p"], bo["sigma"]
@@ -73,24 +73,24 @@ def test_far_atom_of_an_all_si_system():
     si = s.types == 0
     x = np.concatenate([s.x[si] + 10.0, [[60.0, 60.0, 60.0]]])
     t = np.zeros(len(x), int)
-    o = O.evaluate(x, t, np.full(3, 80.0), OPEN, P0)
+    o = O.evaluate(x, t, np.full(3, 80.0), OPEN, P1)
     assert np.max(np.abs(o["q"])) < 1e-12
-    dE = O.removal_energy(x, t, np.full(3, 80.0), OPEN, P0, len(x) - 1)
+    dE = O.removal_energy(x, t, np.full(3, 80.0), OPEN, P1, len(x) - 1)
     assert abs(dE) < 1e-10
 
 
 def test_equivalent_sites_in_ideal_crystal():
     s = st.sic_3c(2, 4.36, 0.0, seed=1)
     si = np.nonzero(s.types == 0)[0][:4]
-    dE, _ = O.desorption_screen(s.x, s.types, s.box, s.pbc, P0, si)
+    dE, _ = O.desorption_screen(s.x, s.types, s.box, s.pbc, P1, si)
     assert np.ptp(dE) < 1e-9 * abs(dE[0])
 
 
 def test_coordination():
     s = st.sic_3c(2, 4.36, 0.05, seed=3)
-    assert np.all(O.coordination(s.x, s.types, s.box, s.pbc, P0) == 4)
+    assert np.all(O.coordination(s.x, s.types, s.box, s.pbc, P1) == 4)
     slab = st.sic_4h_slab(4, 2, 3)
-    c = O.coordination(slab.x, slab.types, slab.box, slab.pbc, P0)
+    c = O.coordination(slab.x, slab.types, slab.box, slab.pbc, P1)
     top = slab.x[:, 2] > slab.x[:, 2].max() - 0.1
     assert np.all(slab.types[top] == 0) and np.all(c[top] == 3)
     assert np.all(c[~top & (slab.x[:, 2] > slab.x[:, 2].min() + 0.1)] == 4)

@@ -15,7 +15,7 @@ import pytest
 from oracle import ctbop_oracle as O
 from paper_1802_07871_gb300 import structures as st
 
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 
 
 def _cell():
@@ -23,9 +23,9 @@ def _cell():
 
 
 def _energy_grad(s, paths):
-    o = O.evaluate(s.x, s.types, s.box, s.pbc, P0)
+    o = O.evaluate(s.x, s.types, s.box, s.pbc, P1)
     # loss = 1/2 (E - (E - 1))^2 -> dloss/dtheta = dE/dtheta
-    return o, O.loss_grad_fd([s], P0, w_E=[0.5], E_ref=[o["E"] - 1.0], paths=paths)
+    return o, O.loss_grad_fd([s], P1, w_E=[0.5], E_ref=[o["E"] - 1.0], paths=paths)
 
 
 def test_self_energy_parameters_closed_form():
@@ -49,7 +49,7 @@ def test_repulsion_prefactor_closed_form():
     names = {(0, 0): "SiSi", (0, 1): "SiC", (1, 0): "SiC", (1, 1): "CC"}
     ref = {"SiSi": 0.0, "SiC": 0.0, "CC": 0.0}
     for a, b, rr in zip(s.types[i], s.types[j], r):
-        pr = P0["pair"][names[(a, b)]]
+        pr = P1["pair"][names[(a, b)]]
         if rr < pr["R"]:
             fc = 1.0
         elif rr < pr["S"]:
@@ -64,21 +64,21 @@ def test_repulsion_prefactor_closed_form():
 def test_coulomb_constant_closed_form():
     s = _cell()
     o, g = _energy_grad(s, [("coulomb", "k_e")])
-    no_c = O.evaluate(s.x, s.types, s.box, s.pbc, O.with_leaf(P0, ("coulomb", "k_e"), 0.0), q=o["q"])["E"]
-    ke = P0["coulomb"]["k_e"]
+    no_c = O.evaluate(s.x, s.types, s.box, s.pbc, O.with_leaf(P1, ("coulomb", "k_e"), 0.0), q=o["q"])["E"]
+    ke = P1["coulomb"]["k_e"]
     assert g[("coulomb", "k_e")] == pytest.approx((o["E"] - no_c) / ke, rel=1e-6)
 
 
 def test_force_term_does_not_depend_on_self_energy_constant():
     s = _cell()
-    o = O.evaluate(s.x, s.types, s.box, s.pbc, P0)
+    o = O.evaluate(s.x, s.types, s.box, s.pbc, P1)
     F_ref = o["F"] + 0.1
-    g = O.loss_grad_fd([s], P0, w_F=[1.0], F_ref=F_ref, paths=[("self", "E0", 0), ("self", "E0", 1)])
+    g = O.loss_grad_fd([s], P1, w_F=[1.0], F_ref=F_ref, paths=[("self", "E0", 0), ("self", "E0", 1)])
     assert abs(g[("self", "E0", 0)]) < 1e-9 and abs(g[("self", "E0", 1)]) < 1e-9
 
 
 def test_leaves_cover_every_parameter_once():
-    leaves = O.param_leaves(P0)
+    leaves = O.param_leaves(P1)
     paths = [p for p, _ in leaves]
     assert len(paths) == len(set(paths))
     # 3 pairs x 7 + 4 bonds x 6 + 8 triplets x 5 x 2 + 6 self + 2 gamma_c + r_coul + k_e

@@ -6,18 +6,18 @@ import numpy as np
 from oracle import ctbop_oracle as O
 from paper_1802_07871_gb300 import structures as st
 
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 
 
 def _run(dt, nsteps, s, v):
-    x, v2, q, et = O.velocity_verlet(s.x, v, s.types, s.box, s.pbc, P0, dt, nsteps, s.frozen)
+    x, v2, q, et = O.velocity_verlet(s.x, v, s.types, s.box, s.pbc, P1, dt, nsteps, s.frozen)
     return x, v2, et
 
 
 def test_energy_error_scales_as_dt_squared():
     s = st.sic_3c(2, 4.36, 0.05, seed=1)
     v = st.maxwell_boltzmann(s.types, 600.0, seed=101)
-    e0 = O.evaluate(s.x, s.types, s.box, s.pbc, P0)["E"] + O.kinetic_energy(v, s.types, P0)
+    e0 = O.evaluate(s.x, s.types, s.box, s.pbc, P1)["E"] + O.kinetic_energy(v, s.types, P1)
     _, _, e1 = _run(0.5, 40, s, v)
     _, _, e2 = _run(0.25, 80, s, v)
     d1 = np.max(np.abs(e1 - e0))

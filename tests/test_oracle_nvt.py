@@ -10,7 +10,7 @@ import pytest
 from oracle import ctbop_oracle as O
 from paper_1802_07871_gb300 import structures as st
 
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 
 
 def _small():
@@ -21,8 +21,8 @@ def _small():
 
 def test_heavy_thermostat_is_nve():
     s, v = _small()
-    x1, v1, q1, _ = O.velocity_verlet(s.x, v, s.types, s.box, s.pbc, P0, 0.5, 12)
-    x2, v2, q2, xi, eta, _ = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P0, 0.5, 12, T0=300.0, tau=1e12)
+    x1, v1, q1, _ = O.velocity_verlet(s.x, v, s.types, s.box, s.pbc, P1, 0.5, 12)
+    x2, v2, q2, xi, eta, _ = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P1, 0.5, 12, T0=300.0, tau=1e12)
     assert np.max(np.abs(x1 - x2)) < 1e-12 and np.max(np.abs(v1 - v2)) < 1e-12
     assert abs(xi) < 1e-20
 
@@ -31,7 +31,7 @@ def test_extended_energy_drift_scales_as_dt_squared():
     s, v = _small()
     drift = []
     for dt, n in ((0.5, 40), (0.25, 80)):
-        *_, ext = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P0, dt, n, T0=900.0, tau=10.0)
+        *_, ext = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P1, dt, n, T0=900.0, tau=10.0)
         drift.append(np.max(np.abs(ext - ext[0])))
     assert drift[0] < 1e-3 * s.n
     assert 2.5 < drift[0] / drift[1] < 6.0, drift
@@ -39,6 +39,6 @@ def test_extended_energy_drift_scales_as_dt_squared():
 
 def test_hot_bath_heats_a_cold_start():
     s, v = _small()
-    K0 = O.kinetic_energy(v, s.types, P0)
-    _, v1, *_ = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P0, 0.5, 60, T0=3000.0, tau=5.0)
-    assert O.kinetic_energy(v1, s.types, P0) > 2.0 * K0
+    K0 = O.kinetic_energy(v, s.types, P1)
+    _, v1, *_ = O.nose_hoover(s.x, v, s.types, s.box, s.pbc, P1, 0.5, 60, T0=3000.0, tau=5.0)
+    assert O.kinetic_energy(v1, s.types, P1) > 2.0 * K0

@@ -19,12 +19,12 @@ from scipy.optimize import minimize_scalar
 from oracle import ctbop_oracle as O
 from paper_1802_07871_gb300 import structures as st
 
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 OPEN = np.array([False] * 3)
 
 
 def _dimer_energy(r):
-    pr, se, co = P0["pair"]["SiC"], P0["self"], P0["coulomb"]
+    pr, se, co = P1["pair"]["SiC"], P1["self"], P1["coulomb"]
     fA = pr["B"] * math.exp(-pr["lambda2"] * r)
     fR = pr["A"] * math.exp(-pr["lambda1"] * r)
     gam = math.sqrt(co["gamma"][0] * co["gamma"][1])
@@ -37,7 +37,7 @@ def _dimer_energy(r):
 
 
 def _si3_energy(d):
-    pr, bo, tp = P0["pair"]["SiSi"], P0["bond"]["SiSi"], P0["triplet"]["SiSiSi"]
+    pr, bo, tp = P1["pair"]["SiSi"], P1["bond"]["SiSi"], P1["triplet"]["SiSiSi"]
     fR = pr["A"] * math.exp(-pr["lambda1"] * d)
     fA = pr["B"] * math.exp(-pr["lambda2"] * d)
     p, sg = bo["p"], bo["sigma"]
@@ -48,14 +48,14 @@ def _si3_energy(d):
         terms += (bo["g"][l] + zeta ** bo["n"][l]) ** (-p)
         norm += bo["g"][l] ** (-p)
     b_mid = (terms / norm) ** (1.0 / (2.0 * sg * p))
-    return 3 * P0["self"]["E0"][0] + 2 * fR - fA - b_mid * fA
+    return 3 * P1["self"]["E0"][0] + 2 * fR - fA - b_mid * fA
 
 
 def test_dimer_reaches_closed_form_minimum():
     rs = minimize_scalar(_dimer_energy, bounds=(1.0, 2.19), method="bounded", options={"xatol": 1e-12})
     assert 1.1 < rs.x < 2.1
     x = np.array([[10.0, 10.0, 10.0], [12.0, 10.3, 9.8]])
-    xf, it, E, ok = O.fire_minimize(x, np.array([0, 1]), np.full(3, 40.0), OPEN, P0, fmax=1e-7, max_iter=5000)
+    xf, it, E, ok = O.fire_minimize(x, np.array([0, 1]), np.full(3, 40.0), OPEN, P1, fmax=1e-7, max_iter=5000)
     assert ok and it > 0
     r = np.linalg.norm(xf[1] - xf[0])
     assert r == pytest.approx(rs.x, abs=1e-7)
@@ -64,10 +64,10 @@ def test_dimer_reaches_closed_form_minimum():
 
 def test_linear_si3_reaches_closed_form_minimum():
     rs = minimize_scalar(_si3_energy, bounds=(1.9, 2.44), method="bounded", options={"xatol": 1e-12})
-    assert 1.9 < rs.x < 2.44 and 2 * rs.x > P0["pair"]["SiSi"]["S"]
+    assert 1.9 < rs.x < 2.44 and 2 * rs.x > P1["pair"]["SiSi"]["S"]
     d0 = 2.3
     x = np.array([[10.0, 10.0, 10.0], [10.0 + d0, 10.0, 10.0], [10.0 + 2 * d0, 10.0, 10.0]])
-    xf, it, E, ok = O.fire_minimize(x, np.zeros(3, int), np.full(3, 40.0), OPEN, P0, fmax=1e-7, max_iter=5000)
+    xf, it, E, ok = O.fire_minimize(x, np.zeros(3, int), np.full(3, 40.0), OPEN, P1, fmax=1e-7, max_iter=5000)
     assert ok
     d1, d2 = np.linalg.norm(xf[1] - xf[0]), np.linalg.norm(xf[2] - xf[1])
     assert d1 == pytest.approx(rs.x, abs=1e-7) and d2 == pytest.approx(rs.x, abs=1e-7)
@@ -75,13 +75,13 @@ def test_linear_si3_reaches_closed_form_minimum():
 
 def test_ideal_crystal_takes_no_iteration():
     s = st.sic_3c(2, 4.36, 0.0, seed=1)
-    xf, it, E, ok = O.fire_minimize(s.x, s.types, s.box, s.pbc, P0, fmax=1e-6)
+    xf, it, E, ok = O.fire_minimize(s.x, s.types, s.box, s.pbc, P1, fmax=1e-6)
     assert ok and it == 0 and np.array_equal(xf, s.x)
 
 
 def test_descent_and_frozen_atoms():
     s = st.stepped_slab_small(6, 3, 4)
-    xf, it, E, ok = O.fire_minimize(s.x, s.types, s.box, s.pbc, P0, frozen=s.frozen, fmax=1e-9, n_iter=40)
+    xf, it, E, ok = O.fire_minimize(s.x, s.types, s.box, s.pbc, P1, frozen=s.frozen, fmax=1e-9, n_iter=40)
     assert it == 40 and E[-1] < E[0]
     assert np.array_equal(xf[s.frozen], s.x[s.frozen])
     assert np.max(np.abs(xf[~s.frozen] - s.x[~s.frozen])) > 1e-3

@@ -20,8 +20,8 @@ import pytest
 from oracle import ctbop_oracle as O
 from paper_1802_07871_gb300 import structures as st
 
-P0 = st.load_params("p0")
-SCC = P0["pair"]["CC"]["S"]
+P1 = st.load_params("p1")
+SCC = P1["pair"]["CC"]["S"]
 OPEN = np.array([False] * 3)
 
 

@@ -16,8 +16,8 @@ import pytest
 from oracle import ctbop_oracle as O
 from paper_1802_07871_gb300 import structures as st
 
-P0 = st.load_params("p0")
-T0 = O.tables(P0)
+P1 = st.load_params("p1")
+T0 = O.tables(P1)
 
 
 def _cluster(n, seed, box=30.0, min_sep=1.6, spread=4.0):
@@ -61,11 +61,11 @@ def test_dimer_closed_form():
     """Isolated Si-C dimer inside R: no third atom, so zeta = 0 and b = 1
     (Sec. 2). With q_Si = -q_C = q the energy is quadratic in q and the
     minimiser is q = (chi_C - chi_Si) / (2 J_Si + 2 J_C + 8 kappa f_A - 2 K)."""
-    pr = P0["pair"]["SiC"]
-    se, co = P0["self"], P0["coulomb"]
+    pr = P1["pair"]["SiC"]
+    se, co = P1["self"], P1["coulomb"]
     for r in (1.7, 1.9, 2.1):
         x = np.array([[10.0, 10.0, 10.0], [10.0 + r, 10.0, 10.0]])
-        res = O.evaluate(x, np.array([0, 1]), np.full(3, 40.0), np.array([False] * 3), P0)
+        res = O.evaluate(x, np.array([0, 1]), np.full(3, 40.0), np.array([False] * 3), P1)
         fA = pr["B"] * math.exp(-pr["lambda2"] * r)
         fR = pr["A"] * math.exp(-pr["lambda1"] * r)
         gam = math.sqrt(co["gamma"][0] * co["gamma"][1])
@@ -152,7 +152,7 @@ def test_energy_bruteforce_loops(case):
         t = t.copy()
         t[[1, 6]] = 1 - t[[1, 6]]      # mixed-type environment
     q = rng.normal(0, 0.3, len(x))
-    sysm = O.System(x, t, box, pbc, P0)
+    sysm = O.System(x, t, box, pbc, P1)
     E = sysm.energy(q)
     Eb = _energy_bruteforce(x, t, box, pbc, q, T0)
     assert abs(E - Eb) <= 1e-11 * max(1.0, abs(Eb))
@@ -186,9 +186,9 @@ def test_forces_match_finite_differences(case):
         t, box, pbc = s.types, s.box, s.pbc
     else:
         x, t, box, pbc = _cluster(12, 6, spread=3.0, min_sep=1.45)
-    res = O.evaluate(x, t, box, pbc, P0)
+    res = O.evaluate(x, t, box, pbc, P1)
     idx = np.arange(0, len(x), max(1, len(x) // 6))[:6]
-    Ffd = _fd_forces(x, t, box, pbc, P0, idx)
+    Ffd = _fd_forces(x, t, box, pbc, P1, idx)
     Fan = res["F"][idx]
     scale = np.sqrt(np.mean(res["F"] ** 2))
     assert np.max(np.abs(Fan - Ffd)) <= 1e-6 * scale
@@ -198,13 +198,13 @@ def test_virial_matches_strain_derivative():
     """W = -dE/d(eps) under homogeneous strain of box and positions, with the
     charges re-minimised."""
     s = st.sic_3c(2, 4.36, 0.1, seed=12)
-    res = O.evaluate(s.x, s.types, s.box, s.pbc, P0)
+    res = O.evaluate(s.x, s.types, s.box, s.pbc, P1)
     W = res["virial"]
     h = 1e-6
     for a in range(3):
         e = np.zeros(3); e[a] = h
-        Ep = O.evaluate(s.x * (1 + e), s.types, s.box * (1 + e), s.pbc, P0)["E"]
-        Em = O.evaluate(s.x * (1 - e), s.types, s.box * (1 - e), s.pbc, P0)["E"]
+        Ep = O.evaluate(s.x * (1 + e), s.types, s.box * (1 + e), s.pbc, P1)["E"]
+        Em = O.evaluate(s.x * (1 - e), s.types, s.box * (1 - e), s.pbc, P1)["E"]
         dE = (Ep - Em) / (2 * h)
         assert abs(W[a, a] + dE) <= 1e-6 * max(1.0, abs(dE))
     assert np.allclose(W, W.T, atol=1e-8 * np.abs(W).max())
@@ -214,7 +214,7 @@ def test_zero_pressure_3c_sic_at_4p36():
     """The synthetic set is tuned so that ideal 3C-SiC is stress-free at
     a = 4.36 A (the lattice constant of the 3C-SiC workload)."""
     s = st.sic_3c(3, 4.36, 0.0)
-    res = O.evaluate(s.x, s.types, s.box, s.pbc, P0)
+    res = O.evaluate(s.x, s.types, s.box, s.pbc, P1)
     V = np.prod(s.box)
     assert abs(np.trace(res["virial"]) / (3 * V)) < 1e-9
     assert res["q"][s.types == 0].min() > 0.1     # Si donates charge to C
@@ -222,10 +222,10 @@ def test_zero_pressure_3c_sic_at_4p36():
 
 def test_newton_third_law_and_torque():
     s = st.sic_3c(2, 4.36, 0.1, seed=14)
-    res = O.evaluate(s.x, s.types, s.box, s.pbc, P0)
+    res = O.evaluate(s.x, s.types, s.box, s.pbc, P1)
     assert np.abs(res["F"].sum(0)).max() < 1e-10 * np.abs(res["F"]).max() * len(s.x)
     x, t, box, pbc = _cluster(14, 15, spread=3.0, min_sep=1.45)
-    r = O.evaluate(x, t, box, pbc, P0)
+    r = O.evaluate(x, t, box, pbc, P1)
     assert np.abs(r["F"].sum(0)).max() < 1e-11 * len(x)
     torque = np.cross(x - x.mean(0), r["F"]).sum(0)
     assert np.abs(torque).max() < 1e-10 * len(x)
@@ -233,9 +233,9 @@ def test_newton_third_law_and_torque():
 
 def test_invariances():
     x, t, box, pbc = _cluster(12, 17, spread=3.0, min_sep=1.45)
-    r0 = O.evaluate(x, t, box, pbc, P0)
+    r0 = O.evaluate(x, t, box, pbc, P1)
     # translation
-    r1 = O.evaluate(x + np.array([0.37, -1.2, 0.9]), t, box, pbc, P0)
+    r1 = O.evaluate(x + np.array([0.37, -1.2, 0.9]), t, box, pbc, P1)
     assert abs(r1["E"] - r0["E"]) < 1e-12 * abs(r0["E"])
     # rotation about the centre
     th = 0.7
@@ -244,13 +244,13 @@ def test_invariances():
     Kx = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
     Rm = np.eye(3) + math.sin(th) * Kx + (1 - math.cos(th)) * Kx @ Kx
     c = x.mean(0)
-    r2 = O.evaluate((x - c) @ Rm.T + c, t, box, pbc, P0)
+    r2 = O.evaluate((x - c) @ Rm.T + c, t, box, pbc, P1)
     assert abs(r2["E"] - r0["E"]) < 1e-12 * abs(r0["E"])
     assert np.allclose(r2["F"], r0["F"] @ Rm.T, atol=1e-10)
     assert np.allclose(r2["q"], r0["q"], atol=1e-12)
     # permutation
     perm = np.random.default_rng(3).permutation(len(x))
-    r3 = O.evaluate(x[perm], t[perm], box, pbc, P0)
+    r3 = O.evaluate(x[perm], t[perm], box, pbc, P1)
     assert abs(r3["E"] - r0["E"]) < 1e-12 * abs(r0["E"])
     assert np.allclose(r3["F"], r0["F"][perm], atol=1e-11)
 
@@ -266,8 +266,8 @@ def test_periodic_supercell_consistency():
     shifts = np.array([[a, b, c] for a in range(2) for b in range(2) for c in range(2)]) * s.box
     X = np.concatenate([x + sh for sh in shifts])
     Tt = np.tile(t, 8)
-    r1 = O.evaluate(x, t, s.box, s.pbc, P0)
-    r8 = O.evaluate(X, Tt, 2 * s.box, s.pbc, P0)
+    r1 = O.evaluate(x, t, s.box, s.pbc, P1)
+    r8 = O.evaluate(X, Tt, 2 * s.box, s.pbc, P1)
     assert abs(r8["E"] - 8 * r1["E"]) < 1e-10 * abs(r8["E"])
     assert np.allclose(r8["q"], np.tile(r1["q"], 8), atol=1e-12)
     assert np.allclose(r8["F"], np.tile(r1["F"], (8, 1)), atol=1e-9)
@@ -278,7 +278,7 @@ def test_charges_equalise_electronegativity():
     charges minimise E_tot), for Q = 0 and a charged system."""
     s = st.sic_4h_slab(3, 2, 4, step="strip")
     for Q in (0.0, 1.5):
-        sysm = O.System(s.x, s.types, s.box, s.pbc, P0)
+        sysm = O.System(s.x, s.types, s.box, s.pbc, P1)
         q, mu = sysm.solve_charges(Q)
         g = sysm.dE_dq(q)
         assert abs(q.sum() - Q) < 1e-12
@@ -292,14 +292,14 @@ def test_charges_equalise_electronegativity():
 
 def test_cg_matches_dense():
     s = st.sic_4h_slab(3, 2, 5, step="strip")
-    sysm = O.System(s.x, s.types, s.box, s.pbc, P0)
+    sysm = O.System(s.x, s.types, s.box, s.pbc, P1)
     qd, mud = sysm.solve_charges(0.0, method="dense")
     qc, muc = sysm.solve_charges(0.0, method="cg")
     assert np.max(np.abs(qd - qc)) < 1e-10
     assert abs(mud - muc) < 1e-10
 
 
-@pytest.mark.parametrize("pname", ["p0", "pt"])
+@pytest.mark.parametrize("pname", ["p1", "pt"])
 def test_hessian_positive_definite(pname):
     """Sec. 2: the charges minimise E_tot, which has a unique minimum only
     when the charge Hessian is positive definite; every shipped parameter
@@ -321,7 +321,7 @@ def test_energy_continuous_across_cutoffs():
         F = []
         for r in rs:
             x = np.array([[10.0, 10, 10], [10.0 + r, 10, 10]])
-            res = O.evaluate(x, np.array(typ), np.full(3, 40.0), np.array([False] * 3), P0)
+            res = O.evaluate(x, np.array(typ), np.full(3, 40.0), np.array([False] * 3), P1)
             E.append(res["E"]); F.append(res["F"][1, 0])
         E, F = np.array(E), np.array(F)
         dr = rs[1] - rs[0]

@@ -13,7 +13,7 @@ from paper_1802_07871_gb300 import ctbop
 from paper_1802_07871_gb300 import structures as st
 
 pytestmark = pytest.mark.gpu
-P0 = st.load_params("p0")
+P1 = st.load_params("p1")
 
 
 def _dimer(d, box=20.0):
@@ -24,7 +24,7 @@ def _dimer(d, box=20.0):
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_noalloc_energy_matches_get_on_consecutive_calls(prec):
     structs = [st.stepped_slab_small(8, 4, 6), st.bulk_3c_512(), _dimer(1.9)]
-    sysm = ctbop.System(P0, precision=prec)
+    sysm = ctbop.System(P1, precision=prec)
     sysm.load_replicas(structs)
     v = np.concatenate([st.maxwell_boltzmann(s.types, 1500.0, seed=7 + k, frozen=s.frozen)
                         for k, s in enumerate(structs)])
@@ -42,7 +42,7 @@ def test_noalloc_energy_matches_get_on_consecutive_calls(prec):
 
 def test_noalloc_energy_rejects_too_many_replicas():
     structs = [_dimer(1.9 + 0.001 * k) for k in range(65)]
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.load_replicas(structs)
     sysm.compute()
     with pytest.raises(ctbop.CtbopError, match="INVALID_ARG"):
@@ -51,7 +51,7 @@ def test_noalloc_energy_rejects_too_many_replicas():
 
 
 def test_noalloc_energy_needs_an_evaluation():
-    sysm = ctbop.System(P0, precision="mixed")
+    sysm = ctbop.System(P1, precision="mixed")
     sysm.load(_dimer(1.9))
     with pytest.raises(ctbop.CtbopError, match="STATE"):
         sysm.energy_noalloc()
