@@ -140,6 +140,12 @@ typedef struct ctbop_stats {
     double  mean_mat;         /* mean stored charge-matrix entries per atom (the entries a matrix pass
                                  streams: those inside the charge cutoff under the mixed policy) */
     double  asm_ms[3];        /* ms per assembly of the depths 4, 8, 16 at the last tuning (0: not timed) */
+    int32_t gather_batch;     /* list entries in flight per thread in the charge-force gather (autotuned) */
+    int32_t fp64_atoms;       /* MIXED: atoms whose covalent terms the last evaluation redid in FP64 (see
+                                 ctbop_compute) */
+    int32_t fp64_bonds;       /* MIXED: bonds whose pair term the last evaluation took in FP64 */
+    int32_t pad;
+    double  gather_ms[3];     /* ms per charge-force gather of the depths 4, 6, 8 at the last tuning */
 } ctbop_stats;
 
 typedef struct ctbop_system ctbop_system;
@@ -355,13 +361,37 @@ int ctbop_rings(ctbop_system* s, double bond_cut, int32_t max_size, int64_t cap,
  * that loads the library until the process exits), which limits it to
  * systems of at most 64 replicas (more -> CTBOP_ERR_INVALID_ARG, nothing
  * computed); there is no limit on the atom count.
- * The first call on a device looks up the scratch array's address (make that
- * call before any stream capture); later calls only launch one kernel on the
- * system's stream and copy R doubles back, synchronising the stream.
+ * The scratch array's address is looked up when the system is created
+ * (ctbop_create, which also loads the kernel if the runtime loads modules
+ * lazily), so every call, the first included, only launches one kernel on
+ * the system's stream and copies R doubles back, synchronising the stream.
  * Calls must not overlap (on any stream or thread): they share the scratch.
  * Errors: INVALID_ARG (null pointer, too many replicas), STATE (no
  * evaluation yet), CUDA. */
 int ctbop_energy_noalloc(ctbop_system* s, double* energy);
+
+/* Arithmetic-pipe peaks of a GPU (a measurement utility, not part of the
+ * method: the roofline of the kernels bound by arithmetic needs them, and
+ * the FP32, special-function and FP64 rates are not published for every
+ * part). Microkernels run independent dependent chains of one instruction
+ * kind on every SM at full occupancy (FP32 fused multiply-add; the
+ * special-function instructions ex2.approx and rsqrt.approx; FP64 fused
+ * multiply-add), each timed by CUDA events on `cuda_stream` (a
+ * cudaStream_t; null = the legacy stream) around one launch of about 40 ms
+ * after a warm-up launch. Allocates and frees a small device buffer.
+ * Synchronises the stream. Errors: INVALID_ARG (null out), CUDA. */
+typedef struct ctbop_peaks {
+    double fp32_tflops;     /* FP32 FMA rate x 2 flops (TFLOP/s) */
+    double mufu_ex2_tops;   /* ex2.approx.f32 per second (1e12/s) */
+    double mufu_rsq_tops;   /* rsqrt.approx.f32 per second (1e12/s) */
+    double fp64_tflops;     /* FP64 FMA rate x 2 flops (TFLOP/s) */
+    double ms[4];           /* timed launch of each microkernel, in that order (ms) */
+    double sm_mhz;          /* median SM clock of the blocks of the FP32 launch (clock64 over globaltimer) */
+    int32_t sms;            /* multiprocessors */
+    int32_t pad;
+} ctbop_peaks;
+
+int ctbop_measure_peaks(int32_t device, void* cuda_stream, ctbop_peaks* out);
 
 #ifdef __cplusplus
 }

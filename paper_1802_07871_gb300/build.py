@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libctbop.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "nbr.cu", "pot.cu", "cg.cu", "md.cu", "noalloc.cu", "grad.cu", "screen.cu", "relax.cu", "rings.cu", "order.cu"]
+SOURCES = ["api.cu", "nbr.cu", "pot.cu", "cg.cu", "md.cu", "noalloc.cu", "grad.cu", "screen.cu", "relax.cu", "rings.cu", "order.cu", "peaks.cu"]
 
 
 def _nvcc() -> str:

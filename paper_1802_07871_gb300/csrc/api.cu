@@ -60,6 +60,7 @@ struct ctbop_system {
   cudaStream_t stream = nullptr;       // stream all work is ordered on
   cudaStream_t own_stream = nullptr;   // used when the caller gives none
   cudaStream_t body_stream = nullptr;
+  void* noalloc_scratch = nullptr;     // the allocation-free energy's scratch array on this device
   std::string err;
   DevState S;
   PotParams<float> Pf;
@@ -85,6 +86,8 @@ struct ctbop_system {
   int tuned_N = -1, tuned_cap = -1;
   float mv_ms[3] = {0.f, 0.f, 0.f};
   float asm_ms[3] = {0.f, 0.f, 0.f};
+  float gather_ms[3] = {0.f, 0.f, 0.f};
+  bool gather_forced = false;
   bool tune_pending = false;
   double g_step_dt = -1.0;
   bool use_graph = true;
@@ -170,6 +173,7 @@ static void pack_params(const ctbop_params& p, double skin, PotParams<Rr>& P) {
   P.inv_rcoul = (Rr)(1.0 / p.r_coul);
   P.ke = (Rr)p.k_e;
   P.rall_list2 = (Rr)((p.r_coul + skin) * (p.r_coul + skin));
+  P.rcore_list2 = p.r_coul > skin ? (Rr)((p.r_coul - skin) * (p.r_coul - skin)) : (Rr)0;
 }
 
 static bool params_valid(const ctbop_params* p, std::string& why) {
@@ -319,6 +323,7 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->atom_buf, &S.cqh2, (size_t)N));
   CK(dalloc(s->atom_buf, &S.ncov, (size_t)N));
   CK(dalloc(s->atom_buf, &S.nall, (size_t)N));
+  CK(dalloc(s->atom_buf, &S.nfix, (size_t)N));
   if (s->mixed) {
     CK(dalloc(s->atom_buf, &S.nmat, (size_t)N));
     CK(zero_async(s, S.nmat, sizeof(int) * (size_t)N));
@@ -357,6 +362,16 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->rep_buf, &S.maxcnt, 3));
   CK(dalloc(s->rep_buf, &S.stiff_n, 1));
   CK(zero_async(s, S.stiff_n, sizeof(int)));
+  CK(dalloc(s->rep_buf, &S.f2_prev, (size_t)s->R));
+  CK(zero_async(s, S.f2_prev, sizeof(double) * s->R));
+  if (s->mixed) {
+    CK(dalloc(s->rep_buf, &S.flag_n, 1));
+    CK(zero_async(s, S.flag_n, sizeof(int)));
+    CK(dalloc(s->atom_buf, &S.flag_q, (size_t)std::max(N, 1)));
+    unsigned char* u64 = nullptr;
+    CK(dalloc(s->atom_buf, &u64, (size_t)std::max(N, 1) * 32));
+    S.u64 = u64;
+  }
   CK(dalloc(s->rep_buf, &S.err, 1));
   CK(dalloc(s->rep_buf, &S.cg_it, 1));
   CK(dalloc(s->rep_buf, &S.cg_blocks, 3));
@@ -398,8 +413,13 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   CK(dalloc(s->list_buf, &S.lst, (size_t)std::max(N, 1) * cap_all));
   CK(dalloc(s->list_buf, &S.rev, (size_t)N * cap_cov));
   CK(dalloc(s->list_buf, &S.stiff_q, (size_t)std::max(N, 1) * cap_cov));
+  if (s->mixed) {
+    unsigned char* b64 = nullptr;
+    CK(dalloc(s->list_buf, &b64, (size_t)std::max(N, 1) * cap_cov * 32));
+    S.bo64 = b64;
+  }
   {
-    float2* pe = nullptr;
+    double2* pe = nullptr;
     CK(dalloc(s->list_buf, &pe, (size_t)std::max(N, 1) * cap_cov));
     S.stiff_pe = pe;
   }
@@ -416,6 +436,15 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   CK(s->mixed ? setup_pot<float>(cap_cov) : setup_pot<double>(cap_cov));
   s->alloc_cov = cap_cov;
   s->alloc_all = cap_all;
+  return CTBOP_OK;
+}
+
+// The next evaluation of every replica in the accurate mode of the FP32
+// path (see k_bond): no previous RMS force counts for new positions, box,
+// types or parameters.
+static int reset_precision_mode(ctbop_system* s) {
+  if (s->alloc_N < 0 || !s->S.rep_acc) return CTBOP_OK;
+  CK(cudaMemset2DAsync(s->S.rep_acc + RA_F2, RA_STRIDE * sizeof(double), 0, sizeof(double), s->R, s->stream));
   return CTBOP_OK;
 }
 
@@ -582,6 +611,14 @@ static int ensure_lists(ctbop_system* s) {
     int forced = fb ? atoi(fb) : 0;
     if (forced == 4 || forced == 8 || forced == 16) S.mv_batch = forced;
     else s->tune_pending = true;
+    // the gather's depth likewise (CTBOP_GATHER_BATCH = 4, 6 or 8 forces one)
+    const char* gbv = getenv("CTBOP_GATHER_BATCH");
+    int gforced = gbv ? atoi(gbv) : 0;
+    s->gather_forced = gforced == 4 || gforced == 6 || gforced == 8;
+    if (s->gather_forced && S.gather_batch != gforced) {
+      S.gather_batch = gforced;
+      destroy_graphs(s);
+    }
     s->tuned_N = S.N;
     s->tuned_cap = S.cap_all;
     if (S.mv_batch != before) destroy_graphs(s);
@@ -613,12 +650,13 @@ static int eval_t(ctbop_system* s, const PotParams<Rr>& P, uint32_t flags) {
     // matrix pass's depths (the solver state is kept across the timing)
     int rc = run_direct<Rr>(s, P, false, 0.0, true);
     if (rc) return rc;
-    int before = s->S.mv_batch, before_asm = s->S.asm_batch;
+    int before = s->S.mv_batch, before_asm = s->S.asm_batch, before_g = s->S.gather_batch;
     cudaError_t e = tune_cg_mv<Rr>(s->S, s->stream, s->mv_ms);
     if (e == cudaSuccess) e = tune_assemble<Rr>(s->S, P, s->T, s->stream, s->asm_ms);
+    if (e == cudaSuccess && !s->gather_forced) e = tune_gather<Rr>(s->S, P, s->T, s->stream, s->gather_ms);
     if (e != cudaSuccess) return fail(s, CTBOP_ERR_CUDA, std::string("pass tuning: ") + cudaGetErrorString(e));
     s->tune_pending = false;
-    if (s->S.mv_batch != before || s->S.asm_batch != before_asm) destroy_graphs(s);
+    if (s->S.mv_batch != before || s->S.asm_batch != before_asm || s->S.gather_batch != before_g) destroy_graphs(s);
     s->solves++;
     s->have_forces = true;
     return CTBOP_OK;
@@ -677,7 +715,7 @@ static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double 
     CK(cudaMemsetAsync(S.err, 0, sizeof(unsigned), st));
     rc = timed(0, 1, [&] { launch_kick_drift<Rr>(S, s->T, dt, 0.25 * s->o.skin * s->o.skin, st); });
     if (!rc) rc = timed(1, 12, [&] { launch_zero_acc(S, st); launch_rebuild<Rr>(S, P, st); });
-    if (!rc) rc = timed(2, 1, [&] { launch_bond<Rr>(S, P, st); });
+    if (!rc) rc = timed(2, sizeof(Rr) == 4 ? 3 : 1, [&] { launch_bond<Rr>(S, P, st); });
     if (!rc) rc = timed(3, 1, [&] { launch_assemble<Rr>(S, P, s->T, st); });
     if (!rc) rc = timed(4, S.precond ? 5 : 3, [&] {
       if (S.precond) launch_block_setup<Rr>(S, st);
@@ -691,7 +729,7 @@ static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double 
       if (!rc) rc = timed(6, 1, [&] { launch_cg_up<Rr>(S, cfg, st); });
     }
     if (!rc) rc = timed(7, 2, [&] { launch_cg_end<Rr>(S, st); });
-    if (!rc) rc = timed(8, sizeof(Rr) == 4 ? 2 : 1, [&] { launch_cov_force<Rr>(S, P, s->T, st); });
+    if (!rc) rc = timed(8, sizeof(Rr) == 4 ? 3 : 1, [&] { launch_cov_force<Rr>(S, P, s->T, st); });
     if (!rc) rc = timed(9, s->nvt ? 2 : 1, [&] {
       launch_coul_gather<Rr>(S, P, s->T, 1, 0.5 * dt, st);
       if (s->nvt) launch_nh_end(S, dt, st);
@@ -739,6 +777,7 @@ int ctbop_create(const ctbop_params* p, const ctbop_options* o, ctbop_system** o
   s->S.precond = o->precond == CTBOP_PRECOND_BLOCK ? 1 : 0;
   pack_params<float>(*p, o->skin, s->Pf);
   pack_params<double>(*p, o->skin, s->Pd);
+  s->S.Pd = &s->Pd;
   for (int t = 0; t < 2; ++t) {
     s->T.E0[t] = p->E0[t];
     s->T.chi[t] = p->chi[t];
@@ -764,6 +803,16 @@ int ctbop_create(const ctbop_params* p, const ctbop_options* o, ctbop_system** o
     return CTBOP_ERR_CUDA;
   }
   s->stream = s->own_stream;
+  {
+    std::string why;
+    if (noalloc_setup(&s->noalloc_scratch, why)) {
+      cudaFreeHost(s->h_int);
+      cudaStreamDestroy(s->body_stream);
+      cudaStreamDestroy(s->own_stream);
+      delete s;
+      return CTBOP_ERR_CUDA;
+    }
+  }
   *out = s;
   return CTBOP_OK;
 }
@@ -835,7 +884,7 @@ int ctbop_set_params(ctbop_system* s, const ctbop_params* p) {
   }
   s->need_rebuild = true;
   s->have_forces = false;
-  return CTBOP_OK;
+  return reset_precision_mode(s);
 }
 
 int ctbop_destroy(ctbop_system* s) {
@@ -913,7 +962,7 @@ int ctbop_set_box(ctbop_system* s, const double* h, const uint8_t* pbc) {
   s->have_box = true;
   s->reps_dirty = true;
   s->need_rebuild = true;
-  return CTBOP_OK;
+  return reset_precision_mode(s);
 }
 
 static int copy_in(ctbop_system* s, void* dst, const void* src, size_t bytes, int mem) {
@@ -994,7 +1043,7 @@ int ctbop_set_types(ctbop_system* s, const int32_t* types, int mem) {
   if (rc) return rc;
   s->have_types = true;
   s->need_rebuild = true;
-  return CTBOP_OK;
+  return reset_precision_mode(s);
 }
 
 int ctbop_set_positions(ctbop_system* s, const double* x, int mem) {
@@ -1010,7 +1059,7 @@ int ctbop_set_positions(ctbop_system* s, const double* x, int mem) {
   s->have_pos = true;
   s->need_rebuild = true;
   s->have_forces = false;
-  return CTBOP_OK;
+  return reset_precision_mode(s);
 }
 
 int ctbop_set_velocities(ctbop_system* s, const double* v, int mem) {
@@ -1245,6 +1294,10 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   for (int k = 0; k < 3; ++k) st->cg_mv_ms[k] = s->mv_ms[k];
   for (int k = 0; k < 3; ++k) st->asm_ms[k] = s->asm_ms[k];
   st->asm_batch = S.asm_batch;
+  for (int k = 0; k < 3; ++k) st->gather_ms[k] = s->gather_ms[k];
+  st->gather_batch = S.gather_batch;
+  if (S.flag_n) CK(sync_copy(s, &st->fp64_atoms, S.flag_n, sizeof(int), cudaMemcpyDeviceToHost));
+  if (S.stiff_n) CK(sync_copy(s, &st->fp64_bonds, S.stiff_n, sizeof(int), cudaMemcpyDeviceToHost));
   st->error_bits = bits;
   st->rebuilds = rb;
   st->cg_iters_total = tot;
@@ -1431,7 +1484,7 @@ int ctbop_energy_noalloc(ctbop_system* s, double* energy) {
   if (!s->have_forces || s->alloc_N < 0) return fail(s, CTBOP_ERR_STATE, "compute or step first");
   cudaSetDevice(s->o.device);
   std::string why;
-  int rc = energy_noalloc(s->S.e_atom, s->S.rep, s->S.N, s->R, s->o.device, s->stream, energy, why);
+  int rc = energy_noalloc(s->S.e_atom, s->S.rep, s->S.N, s->R, s->noalloc_scratch, s->stream, energy, why);
   if (rc == -1) return fail(s, CTBOP_ERR_INVALID_ARG, why);
   if (rc) return fail(s, CTBOP_ERR_CUDA, why);
   return CTBOP_OK;

@@ -133,9 +133,12 @@ __device__ inline void fc_params(S r, R Rin, R Sc, S& fc, S& dR, S& dS) {
   if (val(r) < Rin) { fc = S(R(1)); return; }
   if (val(r) >= Sc) { fc = S(R(0)); return; }
   R w = Sc - Rin;
-  S t = (r - Rin) / w;
-  fc = R(0.5) * (R(1) + fcospi(t));
-  S dfdt = R(-0.5 * M_PI) * fsinpi(t);
+  // 1/2 [1 + cos(pi t)] as cos^2(pi t / 2), free of the cancellation near
+  // t = 1 (the cutoff function of the force kernels does the same)
+  S h = R(0.5) * ((r - Rin) / w);
+  S c = fcospi(h), sn = fsinpi(h);
+  fc = c * c;
+  S dfdt = R(-M_PI) * sn * c;
   dR = dfdt * (r - Sc) / (w * w);
   dS = dfdt * (Rin - r) / (w * w);
 }
@@ -144,7 +147,8 @@ template <class R, class S>
 __device__ inline S fc_only(S r, R Rin, R Sc) {
   if (val(r) < Rin) return S(R(1));
   if (val(r) >= Sc) return S(R(0));
-  return R(0.5) * (R(1) + fcospi((r - Rin) / (Sc - Rin)));
+  S c = fcospi(R(0.5) * ((r - Rin) / (Sc - Rin)));
+  return c * c;
 }
 
 // Block accumulator in FP64: values weighted by wv, tangents by wt. With

@@ -9,8 +9,9 @@
 //   nl               int2[cap*ld]  one list per atom of (j, code) pairs, column-major: entry e of
 //                                  atom i at e*ld + i (ld = N rounded up to 32), so a warp reading
 //                                  entry e of 32 consecutive atoms touches 256 contiguous bytes. Entries
-//                                  [0, ncov) are the covalent list (r < S + skin), [ncov, nall)
-//                                  the rest inside Rc + skin
+//                                  [0, ncov) are the covalent list (r < S + skin), [ncov, nfix)
+//                                  the core (r < Rc - skin when built, so inside Rc until the next
+//                                  rebuild) and [nfix, nall) the shell, the rest inside Rc + skin
 //   code             packed cell offset (dx,dy,dz) such that r_ij = u_j - u_i + d*h
 //   rev              int32[N*capc] entry of j's list that points back to i (covalent part)
 //   bo               Real4[N*capc] b_ij, db/dzeta_1, db/dzeta_2 per directed bond
@@ -55,6 +56,8 @@ template <class R> struct PotParams {
   R gshield3[4];                   // (gamma_i gamma_j)^(-3/2)
   R rcoul, inv_rcoul, ke;
   R rall_list2;                    // (Rc + skin)^2
+  R rcore_list2;                   // (Rc - skin)^2 (0 if Rc <= skin): entries inside stay inside Rc
+                                   // until the next rebuild
   // the pair block in FP64, for the stiff-bond pair terms of the FP32 path
   double A64[4], B64[4], lam1_64[4], lam2_64[4], Rin64[4], Sout64[4], kappa64[4];
 };
@@ -126,14 +129,21 @@ template <class R> __device__ inline R ct_sinpi(R x);
 template <> __device__ inline float ct_sinpi<float>(float x) { return sinpif(x); }
 template <> __device__ inline double ct_sinpi<double>(double x) { return sinpi(x); }
 
-// Tersoff cutoff and its derivative.
+// Tersoff cutoff and its derivative. In the taper, 1/2 [1 + cos(pi t)] is
+// evaluated as cos^2(pi t / 2) and its derivative from sin(pi t / 2) and
+// cos(pi t / 2): the sum 1 + cos(pi t) cancels near t = 1 (a pair just inside
+// S), where FP32 then lost five digits of f_c (relative error 1e-5 at
+// f_c = 3e-3); through zeta^n with n < 1, whose derivative grows without
+// bound as zeta -> 0, that error reached the forces of atoms with a single
+// neighbour in the taper.
 template <class R>
 __device__ inline void cutoff_fn(R r, R Rin, R Sout, R pi_SR, R& f, R& df) {
   if (r < Rin) { f = R(1); df = R(0); return; }
   if (r >= Sout) { f = R(0); df = R(0); return; }
-  R t = (r - Rin) / (Sout - Rin);
-  f = R(0.5) * (R(1) + ct_cospi<R>(t));
-  df = R(-0.5) * pi_SR * ct_sinpi<R>(t);
+  R h = R(0.5) * (r - Rin) / (Sout - Rin);
+  R c = ct_cospi<R>(h), s = ct_sinpi<R>(h);
+  f = c * c;
+  df = -pi_SR * s * c;
 }
 
 // Shielded, tapered charge kernel K(r) and dK/dr.

@@ -22,7 +22,8 @@ enum ParamOffsets {
 enum RepSlots {
   RA_E = 0,        // potential energy
   RA_KE = 1,       // kinetic energy
-  RA_W = 2,        // virial, 9 components
+  RA_F2 = 2,       // sum of |F_i|^2 (the RMS force that selects the next evaluation's precision mode)
+  RA_W = 3,        // virial, 9 components
   RA_STRIDE = 12
 };
 
@@ -84,14 +85,25 @@ struct DevState {
   // lists
   int2* nl = nullptr;           // [cap_all*ld] (j, code) list entries, column-major
   int *ncov = nullptr, *nall = nullptr, *rev = nullptr;
+  int* nfix = nullptr;          // [N] end of the core part of each list (covalent + core entries)
   int* nmat = nullptr;          // [N] stored charge-matrix entries per atom: the list entries inside the
                                 // charge cutoff (FP32, compacted), or nall (FP64)
   int2* lst = nullptr;          // [N][cap_all] row-major build scratch (j, code)
   // stiff covalent bonds (FP32 path): a queue of bond ids i * cap_cov + e and,
-  // per bond, the FP64-evaluated pair term (dE/dr, energy) as float2
+  // per bond, the FP64-evaluated pair term (dE/dr, energy) as double2
   int* stiff_n = nullptr;
   int* stiff_q = nullptr;       // [N * cap_cov]
-  void* stiff_pe = nullptr;     // float2 [N * cap_cov]
+  // atoms whose covalent terms the FP32 path recomputes in FP64 (accurate
+  // mode, see k_bond): a queue of atom ids, FP64 cell offsets of every atom
+  // and FP64 bond orders of the queued atoms; sum |F|^2 of each replica's
+  // previous evaluation (0: none yet, the accurate mode)
+  int* flag_n = nullptr;
+  int* flag_q = nullptr;        // [N]
+  void* u64 = nullptr;          // double4 [N]
+  void* bo64 = nullptr;         // double4 [N * cap_cov]
+  double* f2_prev = nullptr;    // [R]
+  const PotParams<double>* Pd = nullptr;   // host copy of the FP64 parameters
+  void* stiff_pe = nullptr;     // double2 [N * cap_cov]
   void* bo = nullptr;           // Real4[N*cap_cov]
   void* gslot = nullptr;        // Real4[N*cap_cov]
   void* M = nullptr;            // [cap_all*ld] charge matrix: FP32 (j, coefficient) int2 pairs, or FP64 coefficients
@@ -117,6 +129,7 @@ struct DevState {
   int nsm = 152;
   int mv_batch = 16;            // list entries in flight per thread in the CG matrix pass (tuned)
   int asm_batch = 8;            // list entries in flight per thread in the assembly (tuned)
+  int gather_batch = 8;         // list entries in flight per thread in the charge-force gather (tuned)
   // charge-CG preconditioner: block-Jacobi on 32-atom blocks (1) or Jacobi (0)
   int precond = 1;
   void* binv = nullptr;         // Real[ceil(N/32)][32][32]: block inverses, column-major per block
@@ -161,6 +174,8 @@ int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk);
 template <class R> void launch_block_setup(const DevState& S, cudaStream_t st);
 template <class R>
 cudaError_t tune_assemble(DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st, float* ms_out);
+template <class R>
+cudaError_t tune_gather(DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st, float* ms_out);
 // Parameter gradient of the energy (csrc/grad.cu), in FP32 (fp32) or FP64
 // arithmetic with FP64 sums. grad[0..143] = sum_r wval_r dE_r/dtheta at the
 // current positions and charges. With a direction dir ([N,3], positions)
@@ -208,7 +223,8 @@ struct LooItem {
 template <class R> void launch_coordination(const DevState& S, const PotParams<R>& P, double* out, cudaStream_t st);
 void launch_loo_gather(const LooItem* items, int n_items, int max_n, const DevState& S, double* ox, int* otype,
                        uint8_t* ofrozen, double* oq, cudaStream_t st);
-int energy_noalloc(const double* e_atom, const int* rep, int N, int R, int device, cudaStream_t st,
+int noalloc_setup(void** addr, std::string& why);
+int energy_noalloc(const double* e_atom, const int* rep, int N, int R, void* scratch, cudaStream_t st,
                    double* host_out, std::string& why);
 
 }  // namespace ct

@@ -75,10 +75,18 @@ void launch_nh_end(const DevState& S, double dt, cudaStream_t st) {
   k_nh_end<<<1, 256, 0, st>>>(S.R, dt, S.nh, S.rep_acc);
 }
 
-__global__ void k_zero_acc(int n, double* __restrict__ a, int* __restrict__ stiff_n) {
+__global__ void k_zero_acc(int n, double* __restrict__ a, int* __restrict__ stiff_n, double* __restrict__ f2_prev,
+                           int* __restrict__ flag_n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) a[i] = 0.0;
-  if (i == 0) *stiff_n = 0;   // the stiff-bond queue of this evaluation
+  if (i < n) {
+    // the previous evaluation's sum of |F|^2 selects this one's precision mode
+    if (i % RA_STRIDE == RA_F2) f2_prev[i / RA_STRIDE] = a[i];
+    a[i] = 0.0;
+  }
+  if (i == 0) {   // the queues of this evaluation
+    *stiff_n = 0;
+    if (flag_n) *flag_n = 0;
+  }
 }
 
 template <class R>
@@ -92,7 +100,7 @@ void launch_kick_drift(const DevState& S, const TypeParams& T, double dt, double
 
 void launch_zero_acc(const DevState& S, cudaStream_t st) {
   int n = S.R * RA_STRIDE;
-  k_zero_acc<<<(n + 255) / 256, 256, 0, st>>>(n, S.rep_acc, S.stiff_n);
+  k_zero_acc<<<(n + 255) / 256, 256, 0, st>>>(n, S.rep_acc, S.stiff_n, S.f2_prev, S.flag_n);
 }
 
 template void launch_kick_drift<float>(const DevState&, const TypeParams&, double, double, cudaStream_t);

@@ -4,7 +4,9 @@
 // radius, so a +-2 cell stencil covers the list sphere in large boxes; small
 // periodic boxes get a wider stencil that walks through periodic images,
 // self-images included). One list per atom: the covalent entries
-// (r < S_ij + skin) first, then every other entry inside Rc + skin. An entry
+// (r < S_ij + skin) first, then the core (r < Rc - skin: these stay inside
+// Rc until the next rebuild, since a rebuild comes before any atom moves
+// skin/2), then the shell (every other entry inside Rc + skin). An entry
 // stores the atom index j and the stencil offset d in cells, which is exactly
 // the cell-lattice vector from i's cell to j's image cell, so
 // r_ij = u_j - u_i + d * h with u the offset from the owning cell's origin.
@@ -155,12 +157,12 @@ __device__ inline int wrap_cell(int c, int n) {
 // completed only much later by other warps: with lists far larger than L2
 // the partial lines are evicted and written back piecemeal.
 //
-// One pass writes both parts of a row: covalent entries from slot 0, the
-// others from slot cap_cov. The gap left between them is then closed by
-// moving the last of the other entries into it (their order is free), so
-// entries 0 .. ncov-1 are covalent and ncov .. nall-1 the rest. maxcnt
-// receives the largest covalent count, the largest count of the rest (the
-// list needs cap_cov + that) and the largest total.
+// One pass writes the three parts of a row into the scratch: covalent
+// entries from slot 0, core entries from slot cap_cov up, shell entries
+// from slot cap_all - 1 down. k_list_transpose then lays them out as
+// [covalent | core | shell] without moving anything here. maxcnt receives
+// the largest covalent count, the largest count of the rest (the list needs
+// cap_cov + that) and the largest total.
 #define BC 128   // stencil cells per batch
 #define BW 4     // warps per block
 template <class R>
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(BW * 32)
             const RepInfo* __restrict__ reps, const int* __restrict__ cell_start,
             const int* __restrict__ cell_count, const int* __restrict__ cell_atoms, PotParams<R> P,
             int cap_cov, int cap_all, int2* __restrict__ lst,
-            int* __restrict__ ncov, int* __restrict__ nall, int* __restrict__ maxcnt,
+            int* __restrict__ ncov, int* __restrict__ nfix, int* __restrict__ nall, int* __restrict__ maxcnt,
             unsigned* __restrict__ err, const int* __restrict__ flag) {
   typedef typename Vec4<R>::T R4;
   __shared__ int s_st[BW][BC], s_pre[BW][BC + 1], s_cd[BW][BC];
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(BW * 32)
     const int ns = sx * sy * (2 * ri.m[2] + 1);
     for (int ib = 0; ib < nci; ib += 32) {
       const int ni = min(32, nci - ib);
-      int my_i = -1, cnt_c = 0, cnt_r = 0;
+      int my_i = -1, cnt_c = 0, cnt_k = 0, cnt_s = 0;
       if (lane < ni) {
         my_i = cell_atoms[ci0 + ib + lane];
         s_u[warp][lane] = u[my_i];
@@ -272,38 +274,47 @@ __global__ void __launch_bounds__(BW * 32)
             bool self0 = zero_off && j == i;
             bool in = valid && !self0;
             bool cov = in && r2 < P.rcov_list2[(int)ui.w * 2 + tj];
-            bool rest = in && !cov && r2 < P.rall_list2;
-            unsigned bc = __ballot_sync(CT_FULL, cov), br = __ballot_sync(CT_FULL, rest);
-            int bcc = __shfl_sync(CT_FULL, cnt_c, ii), bcr = __shfl_sync(CT_FULL, cnt_r, ii);
+            bool core = in && !cov && r2 < P.rcore_list2;
+            bool shell = in && !cov && !core && r2 < P.rall_list2;
+            unsigned bc = __ballot_sync(CT_FULL, cov), bk = __ballot_sync(CT_FULL, core);
+            unsigned bs = __ballot_sync(CT_FULL, shell);
+            int bcc = __shfl_sync(CT_FULL, cnt_c, ii), bck = __shfl_sync(CT_FULL, cnt_k, ii);
+            int bcs = __shfl_sync(CT_FULL, cnt_s, ii);
             if (cov) {
               int pos = bcc + __popc(bc & lt);
               if (pos < cap_cov) lst[(size_t)i * cap_all + pos] = make_int2(j, cd);
-            } else if (rest) {
-              int pos = cap_cov + bcr + __popc(br & lt);
+            } else if (core) {
+              int pos = cap_cov + bck + __popc(bk & lt);
               if (pos < cap_all) lst[(size_t)i * cap_all + pos] = make_int2(j, cd);
+            } else if (shell) {
+              // from the end of the row down; an overflow (core and shell
+              // meeting) is flagged below and the lists regrow
+              int pos = cap_all - 1 - (bcs + __popc(bs & lt));
+              if (pos >= cap_cov) lst[(size_t)i * cap_all + pos] = make_int2(j, cd);
             }
             if (lane == ii) {
               cnt_c += __popc(bc);
-              cnt_r += __popc(br);
+              cnt_k += __popc(bk);
+              cnt_s += __popc(bs);
             }
           }
         }
         __syncwarp();
       }
-      // close the gap between the covalent part and the rest
+      // counts of the three parts (k_list_transpose closes the gaps)
       if (lane < ni) {
+        int cnt_r = cnt_k + cnt_s;
         int nc = min(cnt_c, cap_cov);
-        int nr = min(cnt_r, cap_all - cap_cov);
-        int mv = min(cap_cov - nc, nr);
-        int2* row = lst + (size_t)my_i * cap_all;
-        for (int k = 0; k < mv; ++k) row[nc + k] = row[cap_cov + nr - 1 - k];
+        bool over = cap_cov + cnt_r > cap_all;
+        int nk = over ? 0 : cnt_k, ns = over ? 0 : cnt_s;   // an overflowed row is rebuilt after regrowth
         ncov[my_i] = nc;
-        nall[my_i] = nc + nr;
+        nfix[my_i] = nc + nk;
+        nall[my_i] = nc + nk + ns;
         need_cov = max(need_cov, cnt_c);
         need_rest = max(need_rest, cnt_r);
         need_tot = max(need_tot, cnt_c + cnt_r);
         if (cnt_c > cap_cov) atomicOr(err, CT_ERR_COV_OVERFLOW);
-        if (cap_cov + cnt_r > cap_all) atomicOr(err, CT_ERR_NBR_OVERFLOW);
+        if (over) atomicOr(err, CT_ERR_NBR_OVERFLOW);
       }
       __syncwarp();
     }
@@ -333,9 +344,12 @@ __global__ void __launch_bounds__(BW * 32)
 
 // Row-major scratch -> column-major lists (entry e of atom i at e * ld + i),
 // 32 atoms x 32 entries per tile through shared memory; tiles past every
-// row's end are skipped. Grid-strided over the tiles.
+// row's end are skipped. Grid-strided over the tiles. Entry e of atom a
+// comes from scratch slot e (covalent, e < ncov), cap_cov + e - ncov (core,
+// e < nfix) or cap_all - 1 - (e - nfix) (shell).
 __global__ void __launch_bounds__(256)
-    k_list_transpose(int N, int cap_all, int ld, const int2* __restrict__ lst, const int* __restrict__ nall,
+    k_list_transpose(int N, int cap_cov, int cap_all, int ld, const int2* __restrict__ lst,
+                     const int* __restrict__ ncov, const int* __restrict__ nfix, const int* __restrict__ nall,
                      int2* __restrict__ nl, const int* __restrict__ flag) {
   __shared__ int2 tile[32][33];
   if (*flag == 0) return;
@@ -349,7 +363,11 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       int a = a0 + ty + 8 * r, e = e0 + tx;
-      if (a < N && e < nall[a]) tile[ty + 8 * r][tx] = lst[(size_t)a * cap_all + e];
+      if (a < N && e < nall[a]) {
+        int nc = ncov[a], nf = nfix[a];
+        int src = e < nc ? e : (e < nf ? cap_cov + (e - nc) : cap_all - 1 - (e - nf));
+        tile[ty + 8 * r][tx] = lst[(size_t)a * cap_all + src];
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -421,9 +439,10 @@ void launch_rebuild(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   // grid-strided: when no rebuild is due these launches return at once
   int gb = S.nsm * 8;
   k_build<R><<<gb, BW * 32, 0, st>>>(C, (const typename Vec4<R>::T*)S.u, S.cell_rep, S.reps, S.cell_start,
-                                     S.cell_count, S.cell_atoms, P, S.cap_cov, S.cap_all, S.lst, S.ncov, S.nall,
-                                     S.maxcnt, S.err, f);
-  k_list_transpose<<<S.nsm * 8, 256, 0, st>>>(N, S.cap_all, S.ld, S.lst, S.nall, S.nl, f);
+                                     S.cell_count, S.cell_atoms, P, S.cap_cov, S.cap_all, S.lst, S.ncov, S.nfix,
+                                     S.nall, S.maxcnt, S.err, f);
+  k_list_transpose<<<S.nsm * 8, 256, 0, st>>>(N, S.cap_cov, S.cap_all, S.ld, S.lst, S.ncov, S.nfix, S.nall,
+                                              S.nl, f);
   k_rev<<<S.nsm * 4, tb, 0, st>>>(N, S.cap_cov, S.ld, S.nl, S.ncov, S.rev, S.err, f);
   k_finish_rebuild<<<1, 1, 0, st>>>(S.flag_rebuild, S.rebuild_count);
 }

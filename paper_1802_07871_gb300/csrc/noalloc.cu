@@ -20,10 +20,16 @@
 // Limits: at most NA_REPS replicas per system (larger systems are rejected
 // with an error, never truncated); any atom count (the grid strides).
 //
-// The symbol's address is looked up once per device (the first call on a
-// device, with that device current) and passed to the kernel. Concurrent
-// calls share the one scratch array and race; callers must not overlap
-// them, on any stream.
+// The symbol's address is looked up when a system is created
+// (noalloc_setup, called by ctbop_create with the system's device current),
+// kept with that system and passed to the kernel; device code could name the
+// array directly, host code only through this address. The lookup also loads
+// this file's kernels if the runtime loads modules lazily, so that an
+// energy_noalloc call neither loads a module nor looks anything up. A device
+// reset destroys every system of that device, and the next system created
+// looks the address up again, so a kept address never outlives its module.
+// Concurrent calls share the one scratch array and race; callers must not
+// overlap them, on any stream.
 #include <string>
 
 #include "internal.cuh"
@@ -34,7 +40,6 @@ namespace ct {
 #define NA_BLOCKS 304   // 2 blocks per SM on 152 SMs
 #define NA_REPS 64
 #define NA_THREADS 256
-#define NA_MAX_DEVICES 64
 
 struct NoallocScratch {
   double part[NA_BLOCKS][NA_REPS];
@@ -84,32 +89,36 @@ __global__ void __launch_bounds__(NA_THREADS)
   if (threadIdx.x == 0) sc->counter = 0u;
 }
 
-static void* g_scratch_addr[NA_MAX_DEVICES];
-static bool g_scratch_ready[NA_MAX_DEVICES];
+// Address of the scratch array on the current device (a system's set-up).
+// Also loads this file's kernel, so the first energy_noalloc call has nothing
+// left to load. Status 0 or a negative ctbop status with the reason in why.
+int noalloc_setup(void** addr, std::string& why) {
+  *addr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(addr, g_noalloc_scratch);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_energy_noalloc);
+  if (e != cudaSuccess) {
+    *addr = nullptr;
+    why = std::string("energy_noalloc set-up: ") + cudaGetErrorString(e);
+    return -6;
+  }
+  return 0;
+}
 
-// Per-replica sums of e_atom[0..N) into host_out[0..R). Status 0 or a
+// Per-replica sums of e_atom[0..N) into host_out[0..R), with the scratch at
+// `scratch` (noalloc_setup's address for the system's device). Status 0 or a
 // negative ctbop status with the reason in why.
-int energy_noalloc(const double* e_atom, const int* rep, int N, int R, int device, cudaStream_t st,
+int energy_noalloc(const double* e_atom, const int* rep, int N, int R, void* scratch, cudaStream_t st,
                    double* host_out, std::string& why) {
   if (R < 1 || R > NA_REPS) {
     why = "energy_noalloc: at most " + std::to_string(NA_REPS) + " replicas (its scratch is a fixed device array)";
     return -1;
   }
-  if (device < 0 || device >= NA_MAX_DEVICES) {
-    why = "energy_noalloc: device index out of range";
-    return -1;
+  if (!scratch) {
+    why = "energy_noalloc: the scratch array's address was not set up";
+    return -6;
   }
-  if (!g_scratch_ready[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) {
-      why = std::string("energy_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-      return -6;
-    }
-    g_scratch_addr[device] = p;
-    g_scratch_ready[device] = true;
-  }
-  NoallocScratch* sc = static_cast<NoallocScratch*>(g_scratch_addr[device]);
+  NoallocScratch* sc = static_cast<NoallocScratch*>(scratch);
   int grid = (N + NA_THREADS - 1) / NA_THREADS;
   if (grid > NA_BLOCKS) grid = NA_BLOCKS;
   if (grid < 1) grid = 1;

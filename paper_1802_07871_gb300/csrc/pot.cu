@@ -24,9 +24,18 @@ namespace ct {
 #define GRP 8           // lanes per atom in the covalent kernels
 // Bonds whose repulsive radial derivative lambda1 * A e^(-lambda1 r) exceeds
 // this (eV/A) get their pair term in FP64 on the FP32 path (queued by the
-// bond pass, evaluated by k_stiff). Equilibrium Si-C bonds of the synthetic
-// set stay near 11 eV/A; compressed adatom bonds reach 35-65 eV/A.
-#define STIFF_PAIR 20.0f
+// bond pass, evaluated by k_stiff): there the repulsive and attractive
+// derivatives cancel to a few eV/A and the FP32 rounding of both terms and
+// of the bond length would stand out. Equilibrium Si-C bonds of the
+// synthetic set sit at 17.7 eV/A (about twice below the threshold);
+// compressed adatom bonds reach 40-80 eV/A.
+#define STIFF_PAIR 35.0f
+// RMS force (eV/A) below which a replica's next evaluation takes the
+// accurate mode (see k_bond): at the largest FP32 force error measured on
+// ill-conditioned atoms (about 7e-5 eV/A, adatoms in the taper of a Si-C
+// pair or in compressed C-C pairs) a 1e-4 bar relative to the RMS force
+// holds without the FP64 pass from about 0.7 eV/A on.
+#define ACC_RMS 1.0
 #define APB 16          // atoms per block in the covalent kernels
 
 template <class R>
@@ -54,30 +63,56 @@ __device__ inline void rel_vec(const typename Vec4<R>::T& ui, const typename Vec
 }
 
 // ---------------------------------------------------------------- bond pass
+//
+// Precision by need (FP32 path). A replica is in the accurate mode when the
+// RMS force of its previous evaluation is below ACC_RMS (and on its first
+// evaluation after positions or parameters were set, when there is none).
+// Then every bond's pair term is queued for k_stiff (FP64), and every atom
+// with a bond in the cutoff's taper (R < r < S) or a compressed bond (the
+// STIFF_PAIR criterion) is queued as a whole: k_bond<double> and
+// k_cov_force<double, float> recompute its bond orders and force slots in
+// FP64 from the master positions and overwrite the FP32 results. The force
+// of such an atom moves by about 1e-4 eV/A under a position change of the
+// size of FP32 rounding (3e-7 A), above the error a 1e-4 bar relative to a
+// small RMS force allows; with the RMS force above ACC_RMS the FP32 error
+// is far inside the bar and nothing is queued (hot MD pays nothing).
+// qlist/qn: when given, block b takes the queued atoms qlist[b*APB ..], the
+// rest of the grid exits at once.
 template <class R>
 __global__ void __launch_bounds__(APB * GRP)
 k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
        const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
         const int* __restrict__ ncov, PotParams<R> P,
-       typename Vec4<R>::T* __restrict__ bo, int* __restrict__ stiff_n, int* __restrict__ stiff_q) {
+       typename Vec4<R>::T* __restrict__ bo, int* __restrict__ stiff_n, int* __restrict__ stiff_q,
+       const double* __restrict__ f2_prev, int* __restrict__ flag_n, int* __restrict__ flag_q,
+       const int* __restrict__ qlist, const int* __restrict__ qn) {
   using R4 = typename Vec4<R>::T;
   extern __shared__ __align__(32) unsigned char smem_raw[];
-  __shared__ int s_nstiff, s_base;
-  if (threadIdx.x == 0) s_nstiff = 0;
+  __shared__ int s_nstiff, s_base, s_nflag, s_fbase;
+  if (threadIdx.x == 0) { s_nstiff = 0; s_nflag = 0; }
   int g = threadIdx.x / GRP, l = threadIdx.x % GRP;
   R4* s_u = reinterpret_cast<R4*>(smem_raw) + (size_t)g * cap_cov;               // (ux,uy,uz,r)
   R* s_fc = reinterpret_cast<R*>(reinterpret_cast<R4*>(smem_raw) + (size_t)APB * cap_cov) + (size_t)g * cap_cov;
   int* s_t = reinterpret_cast<int*>(reinterpret_cast<R*>(reinterpret_cast<R4*>(smem_raw) + (size_t)APB * cap_cov)
                                     + (size_t)APB * cap_cov) + (size_t)g * cap_cov;
   int i = blockIdx.x * APB + g;
+  if (qlist) {
+    const int nq = *qn;
+    if (blockIdx.x * APB >= nq) return;   // (uniform over the block)
+    i = i < nq ? qlist[i] : N;
+  }
   bool live = i < N;
+  bool acc = false;   // this replica in the accurate mode (FP32 path)
   int nc = 0, ti = 0;
   R4 ui;
   if (live) {
     ui = u[i];
     ti = (int)ui.w;
     nc = min(ncov[i], cap_cov);
-    const RepInfo& ri = reps[rep[i]];
+    const int rid = rep[i];
+    const RepInfo& ri = reps[rid];
+    if (sizeof(R) == 4 && f2_prev)
+      acc = f2_prev[rid] < 3.0 * (double)ri.natoms * (double)(ACC_RMS * ACC_RMS);
     R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
     if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
     for (int e = l; e < nc; e += GRP) {
@@ -98,19 +133,22 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
     }
   }
   __syncthreads();
-  int my_stiff = 0;
+  int my_stiff = 0, my_flag = 0;
   for (int e = l; live && e < nc; e += GRP) {
     R4 ue = s_u[e];
     int tj = s_t[e];
     int pb = ti * 2 + tj;
     R4 out;
     // .w marks a stiff bond (FP32 path): its pair term is evaluated in FP64
-    // by k_stiff, from the queue built below
+    // by k_stiff, from the queue built below (every bond in the accurate mode)
     out.w = R(0);
-    if (sizeof(R) == 4 && ue.w < P.Sout[pb] &&
-        P.lam1[pb] * P.A[pb] * ct_exp<R>(-P.lam1[pb] * ue.w) > R(STIFF_PAIR)) {
-      out.w = R(1);
-      ++my_stiff;
+    if (sizeof(R) == 4 && ue.w < P.Sout[pb]) {
+      bool compressed = P.lam1[pb] * P.A[pb] * ct_exp<R>(-P.lam1[pb] * ue.w) > R(STIFF_PAIR);
+      if (compressed || acc) {
+        out.w = R(1);
+        ++my_stiff;
+      }
+      if (acc && (compressed || ue.w > P.Rin[pb])) my_flag = 1;
     }
     if (ue.w >= P.Sout[pb]) {
       out.x = R(1); out.y = R(0); out.z = R(0);
@@ -146,30 +184,42 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
     out.x = b; out.y = db1; out.z = db2;
     bo[(size_t)i * cap_cov + e] = out;
   }
-  if (sizeof(R) != 4) return;   // (uniform over the block)
-  // append this block's stiff bonds to the queue: one global atomic per block
+  if (sizeof(R) != 4 || qlist) return;   // (uniform over the block)
+  // this atom is queued for the FP64 pass when any lane of its group
+  // flagged it (every lane of the warp takes part in the shuffles)
+#pragma unroll
+  for (int o = GRP / 2; o > 0; o >>= 1) my_flag |= __shfl_xor_sync(CT_FULL, my_flag, o, GRP);
+  // append this block's stiff bonds and flagged atoms to their queues: one
+  // global atomic per block and queue
   int off = my_stiff ? atomicAdd(&s_nstiff, my_stiff) : 0;
+  int foff = (my_flag && l == 0) ? atomicAdd(&s_nflag, 1) : 0;
   __syncthreads();
-  if (threadIdx.x == 0) s_base = s_nstiff ? atomicAdd(stiff_n, s_nstiff) : 0;
+  if (threadIdx.x == 0) {
+    s_base = s_nstiff ? atomicAdd(stiff_n, s_nstiff) : 0;
+    s_fbase = s_nflag ? atomicAdd(flag_n, s_nflag) : 0;
+  }
   __syncthreads();
   if (my_stiff) {
     int pos = s_base + off;
     for (int e = l; e < nc; e += GRP)
       if (bo[(size_t)i * cap_cov + e].w != R(0)) stiff_q[pos++] = i * cap_cov + e;
   }
+  if (my_flag && l == 0) flag_q[s_fbase + foff] = i;
 }
 
 // The pair term of every queued stiff bond in FP64 (fully occupied lanes,
 // unlike a per-bond branch inside the force pass): the bond vector from the
 // master positions (r_ij = x_j - x_i + the periodic shift of the stencil
 // cell), c_ij from the FP64 charges, b_ij from the bond pass. Stores dE/dr
-// and the energy 1/2 fc (A e^{-l1 r} - c b B e^{-l2 r}) as float2.
+// and the energy 1/2 fc (A e^{-l1 r} - c b B e^{-l2 r}) as double2 (the
+// energy stays FP64: the bonds of a crystal round alike, so FP32 energies
+// would add up coherently).
 __global__ void __launch_bounds__(256)
     k_stiff(int cap_cov, int ld, const int* __restrict__ nq, const int* __restrict__ q_ids,
             const int2* __restrict__ nl,  const int* __restrict__ rep,
             const RepInfo* __restrict__ reps, const double* __restrict__ x, const int4* __restrict__ cell4,
             const int* __restrict__ type, const float4* __restrict__ bo, const double* __restrict__ q,
-            PotParams<float> P, float2* __restrict__ pe) {
+            PotParams<float> P, double2* __restrict__ pe) {
   int n = *nq;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     int id = q_ids[t];
@@ -198,7 +248,7 @@ __global__ void __launch_bounds__(256)
     double fR = P.A64[pb] * exp(-P.lam1_64[pb] * r);
     double att = cq * (double)bo[id].x * P.B64[pb] * exp(-P.lam2_64[pb] * r);
     double pd = 0.5 * (dfc * (fR - att) + fc * (-P.lam1_64[pb] * fR + P.lam2_64[pb] * att));
-    pe[id] = make_float2((float)pd, (float)(0.5 * fc * (fR - att)));
+    pe[id] = make_double2(pd, 0.5 * fc * (fR - att));
   }
 }
 
@@ -207,32 +257,41 @@ __global__ void __launch_bounds__(256)
 // codes of the next batch of entries are loaded before the current ones are
 // used, so the list (the bound of these passes) always has loads in flight.
 // The batch is AB in the assembly (4, 8 or 16, timed on the first solve of
-// new lists, tune_assemble) and PB in the charge-force gather.
-#define PB 8
+// new lists, tune_assemble) and PB in the charge-force gather (4, 6 or 8,
+// tune_gather).
+//
+// Matrix layout: entry e of atom i at row e (e * ld + i) for the covalent
+// and core entries, so the assembly walks those rows warp-uniformly and
+// every store of a warp fills one contiguous 256-byte row; the shell entries
+// inside the charge cutoff are packed after the core (FP32 path: those
+// beyond it have K = 0 and are dropped, about 15% of the list), the only
+// stores whose rows differ between lanes. The FP64 path keeps every entry at
+// its list row.
 template <class R, int AB>
 __global__ void __launch_bounds__(256)
     k_assemble(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
                const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
-                const int* __restrict__ ncov, const int* __restrict__ nall,
+               const int* __restrict__ ncov, const int* __restrict__ nfix, const int* __restrict__ nall,
                const int* __restrict__ rev, const typename Vec4<R>::T* __restrict__ bo, PotParams<R> P,
                TypeParams T, void* __restrict__ M, R* __restrict__ Dg, R* __restrict__ dinv,
                int* __restrict__ nmat) {
   using R4 = typename Vec4<R>::T;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned wm = __ballot_sync(CT_FULL, i < N);   // the warp's live lanes
   if (i >= N) return;
   R4 ui = u[i];
   int ti = (int)ui.w;
   const RepInfo& ri = reps[rep[i]];
   R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
   if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
-  int nc = ncov[i], na = nall[i];
+  int nc = ncov[i], nf = nfix[i], na = nall[i];
   R wsum = R(0), selfm = R(0);
   const int2* pl = nl + i;
   // covalent entries: K minus twice the bond-order coupling w
   for (int e = 0; e < nc; ++e) {
     size_t off = (size_t)e * ld;
     int2 jcd = __ldg(pl + off);
-      int j = jcd.x;
+    int j = jcd.x;
     R4 uj = u[j];
     R rx, ry, rz;
     rel_vec<R>(ui, uj, jcd.y, hx, hy, hz, rx, ry, rz);
@@ -254,21 +313,62 @@ __global__ void __launch_bounds__(256)
     if (j == i) selfm += m;
     mat_store(M, off + i, j, m);
   }
-  // the rest: K only, streamed. FP32 stores only the entries inside the
-  // charge cutoff (those beyond it, in the list's skin, have K = 0), packed
-  // after the covalent ones: about 10% fewer bytes for every matrix pass.
-  // FP64 keeps its coefficients aligned with the list (its index stream).
-  int em = nc;
   const R gs_i0 = P.gshield3[ti * 2], gs_i1 = P.gshield3[ti * 2 + 1];
+  // core entries: rows [nc, nf) walked in step by the whole warp (lanes
+  // outside their own range idle), each stored at its own row
+  {
+    const int e_lo = (int)__reduce_min_sync(wm, (unsigned)nc);
+    const int e_hi = (int)__reduce_max_sync(wm, (unsigned)nf);
+    int jn[AB], cn[AB];
+#pragma unroll
+    for (int k = 0; k < AB; ++k) {
+      int en = e_lo + k;
+      bool ok = en >= nc && en < nf;
+      int2 t = ok ? __ldg(pl + (size_t)en * ld) : make_int2(i, pack_code(0, 0, 0));
+      jn[k] = t.x;
+      cn[k] = t.y;
+    }
+    for (int e = e_lo; e < e_hi; e += AB) {
+      int jc[AB], cc[AB];
+#pragma unroll
+      for (int k = 0; k < AB; ++k) {
+        jc[k] = jn[k];
+        cc[k] = cn[k];
+        int en = e + AB + k;
+        bool ok = en >= nc && en < nf;
+        int2 t = ok ? __ldg(pl + (size_t)en * ld) : make_int2(i, pack_code(0, 0, 0));
+        jn[k] = t.x;
+        cn[k] = t.y;
+      }
+      R4 uj[AB];
+#pragma unroll
+      for (int k = 0; k < AB; ++k) uj[k] = u[jc[k]];
+#pragma unroll
+      for (int k = 0; k < AB; ++k) {
+        int row = e + k;
+        if (row >= nc && row < nf) {
+          R rx, ry, rz;
+          rel_vec<R>(ui, uj[k], cc[k], hx, hy, hz, rx, ry, rz);
+          R r2 = rx * rx + ry * ry + rz * rz;
+          R m = coul_K_r2<R>(r2, uj[k].w != R(0) ? gs_i1 : gs_i0, P.inv_rcoul, P.ke);
+          if (jc[k] == i) selfm += m;
+          mat_store(M, (size_t)row * ld + i, jc[k], m);
+        }
+      }
+    }
+  }
+  // shell entries: K only, streamed; the FP32 path stores only those inside
+  // the charge cutoff, packed after the core
+  int em = nf;
   int jn[AB], cn[AB];
 #pragma unroll
   for (int k = 0; k < AB; ++k) {
-    bool ok = nc + k < na;
-    int2 t = ok ? __ldg(pl + (size_t)(nc + k) * ld) : make_int2(i, pack_code(0, 0, 0));
+    bool ok = nf + k < na;
+    int2 t = ok ? __ldg(pl + (size_t)(nf + k) * ld) : make_int2(i, pack_code(0, 0, 0));
     jn[k] = t.x;
     cn[k] = t.y;
   }
-  for (int e = nc; e < na; e += AB) {
+  for (int e = nf; e < na; e += AB) {
     int jc[AB], cc[AB];
 #pragma unroll
     for (int k = 0; k < AB; ++k) {
@@ -307,14 +407,17 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------- covalent forces
-template <class R>
+// O is the type of the stored slots: R, or float for the FP64 pass over the
+// queued atoms of the FP32 path (qlist/qn as in k_bond).
+template <class R, class O>
 __global__ void __launch_bounds__(APB * GRP)
 k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
             const int* __restrict__ rep, const RepInfo* __restrict__ reps,
             const int2* __restrict__ nl,  const int* __restrict__ ncov,
             const typename Vec4<R>::T* __restrict__ bo, const double* __restrict__ q,
-            const R* __restrict__ qr, PotParams<R> P, TypeParams T, typename Vec4<R>::T* __restrict__ gslot,
-            double* __restrict__ e_atom, const void* __restrict__ stiff_pe) {
+            const R* __restrict__ qr, PotParams<R> P, TypeParams T, typename Vec4<O>::T* __restrict__ gslot,
+            double* __restrict__ e_atom, const void* __restrict__ stiff_pe,
+            const int* __restrict__ qlist, const int* __restrict__ qn) {
   using R4 = typename Vec4<R>::T;
   using R2 = typename Vec2<R>::T;
   extern __shared__ __align__(32) unsigned char smem_raw[];
@@ -330,9 +433,15 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
   s_dfc += (size_t)g * cap_cov; s_pd += (size_t)g * cap_cov; s_t += (size_t)g * cap_cov;
 
   int i = blockIdx.x * APB + g;
+  if (qlist) {
+    const int nq = *qn;
+    if (blockIdx.x * APB >= nq) return;   // (uniform over the block)
+    i = i < nq ? qlist[i] : N;
+  }
   bool live = i < N;
   int nc = 0, ti = 0;
   CompSum<R> eacc;
+  double estiff = 0.0;   // FP64 pair energies of the stiff bonds (FP32 path)
   if (live) {
     R4 ui = u[i];
     ti = (int)ui.w;
@@ -364,8 +473,8 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
         R att = cq * bb.x * fA;
         if (sizeof(R) == 4 && bb.w != R(0)) {
           // stiff bond: pair term evaluated in FP64 by k_stiff
-          float2 v = static_cast<const float2*>(stiff_pe)[(size_t)i * cap_cov + e];
-          eacc.add((R)v.y);
+          double2 v = static_cast<const double2*>(stiff_pe)[(size_t)i * cap_cov + e];
+          estiff += v.y;
           pd = (R)v.x;
         } else {
           eacc.add(R(0.5) * fc * (fR - att));
@@ -391,8 +500,8 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
       R4 ux = s_u[e];
       R rx = ux.w;
       R fcx = s_fc[e];
-      R4 out;
-      out.x = R(0); out.y = R(0); out.z = R(0); out.w = R(0);
+      typename Vec4<O>::T out;
+      out.x = O(0); out.y = O(0); out.z = O(0); out.w = O(0);
       if (fcx > R(0)) {
         R irx = R(1) / rx;
         R hx_ = ux.x * irx, hy_ = ux.y * irx, hz_ = ux.z * irx;
@@ -450,9 +559,9 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
           gy += cp * (ky - ct * hy_);
           gz += cp * (kz - ct * hz_);
         }
-        out.x = gx + c_ux * hx_;
-        out.y = gy + c_ux * hy_;
-        out.z = gz + c_ux * hz_;
+        out.x = (O)(gx + c_ux * hx_);
+        out.y = (O)(gy + c_ux * hy_);
+        out.z = (O)(gz + c_ux * hz_);
       }
       gslot[(size_t)i * cap_cov + e] = out;
     }
@@ -463,10 +572,11 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
   for (int o = GRP / 2; o > 0; o >>= 1) {
     es += __shfl_xor_sync(CT_FULL, es, o, GRP);
     ec += __shfl_xor_sync(CT_FULL, ec, o, GRP);
+    estiff += __shfl_xor_sync(CT_FULL, estiff, o, GRP);
   }
   if (live && l == 0) {
     double qd = q[i];
-    e_atom[i] = ((double)es + (double)ec) + T.E0[ti] + T.chi[ti] * qd + T.J[ti] * qd * qd;
+    e_atom[i] = ((double)es + (double)ec) + estiff + T.E0[ti] + T.chi[ti] * qd + T.J[ti] * qd * qd;
   }
 }
 
@@ -476,7 +586,7 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
 // FP64 store, half kick, kinetic energy and per-replica sums. Threads take
 // 256-atom tiles strided over the grid, so the FP64 per-replica reductions
 // are paid once per thread, not once per atom.
-template <class R>
+template <class R, int PB>
 __global__ void __launch_bounds__(256)
     k_coul_gather(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
                   const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
@@ -487,10 +597,10 @@ __global__ void __launch_bounds__(256)
                   double* __restrict__ e_atom, double* __restrict__ rep_acc, unsigned* __restrict__ err,
                   const double* __restrict__ nh) {
   using R4 = typename Vec4<R>::T;
-  RepAcc<2> accE;   // (E, KE)
-  RepAcc<9> accW;   // virial
-  accE.init();
-  accW.init();
+  // per-replica sums in one accumulator (the slot order of rep_acc): E, KE,
+  // sum of |F|^2 (the RMS force that picks the next evaluation's mode), virial
+  RepAcc<RA_STRIDE> acc;
+  acc.init();
   for (int t = blockIdx.x; (long long)t * 256 < N; t += gridDim.x) {
     int i = t * 256 + (int)threadIdx.x;
     if (i >= N) break;
@@ -587,11 +697,11 @@ __global__ void __launch_bounds__(256)
     double ea = e_atom[i] + ec.value();
     e_atom[i] = ea;
     if (!isfinite(ea) || !isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) atomicOr(err, CT_ERR_NONFINITE);
-    accE.to(ri_id, rep_acc, RA_STRIDE);
-    accW.to(ri_id, rep_acc + RA_W, RA_STRIDE);
-    accE.v[0] += ea;
+    acc.to(ri_id, rep_acc, RA_STRIDE);
+    acc.v[RA_E] += ea;
+    acc.v[RA_F2] += Fx * Fx + Fy * Fy + Fz * Fz;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) accW.v[k] += (double)w[k];
+    for (int k = 0; k < 9; ++k) acc.v[RA_W + k] += (double)w[k];
     if (kick && !frozen[i]) {
       double sc = half_dt * T.inv_mass_acc[ti];
       double vx = v[3 * i] + sc * Fx, vy = v[3 * i + 1] + sc * Fy, vz = v[3 * i + 2] + sc * Fz;
@@ -604,11 +714,29 @@ __global__ void __launch_bounds__(256)
     }
     {   // kinetic energy of the current velocities
       double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
-      accE.v[1] += 0.5 * T.mass[ti] * (vx * vx + vy * vy + vz * vz);
+      acc.v[RA_KE] += 0.5 * T.mass[ti] * (vx * vx + vy * vy + vz * vz);
     }
   }
-  lane_flush<2>(accE, rep_acc, RA_STRIDE);
-  lane_flush<9>(accW, rep_acc + RA_W, RA_STRIDE);
+  lane_flush<RA_STRIDE>(acc, rep_acc, RA_STRIDE);
+}
+
+// FP64 offsets of every atom from its cell's origin (the layout of u), for
+// the FP64 pass over queued atoms; nothing to do when the queue is empty.
+__global__ void k_fill_u64(int N, const int* __restrict__ nq, const double* __restrict__ x,
+                           const int4* __restrict__ cell4, const int* __restrict__ type,
+                           const int* __restrict__ rep, const RepInfo* __restrict__ reps,
+                           double4_32a* __restrict__ u64) {
+  if (*nq == 0) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const RepInfo& ri = reps[rep[i]];
+    int4 c = cell4[i];
+    double4_32a w;
+    w.x = x[3 * i] - c.x * ri.hc[0];
+    w.y = x[3 * i + 1] - c.y * ri.hc[1];
+    w.z = x[3 * i + 2] - c.z * ri.hc[2];
+    w.w = (double)type[i];
+    u64[i] = w;
+  }
 }
 
 // ---------------------------------------------------------------- launchers
@@ -638,16 +766,26 @@ template <class R>
 void launch_bond(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   if (S.N == 0) return;
   size_t sm = bond_smem<R>(S.cap_cov);
-  k_bond<R><<<(S.N + APB - 1) / APB, APB * GRP, sm, st>>>(
+  const int gb = (S.N + APB - 1) / APB;
+  k_bond<R><<<gb, APB * GRP, sm, st>>>(
       S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
-      S.ncov, P, (typename Vec4<R>::T*)S.bo, S.stiff_n, S.stiff_q);
+      S.ncov, P, (typename Vec4<R>::T*)S.bo, S.stiff_n, S.stiff_q, S.f2_prev, S.flag_n, S.flag_q,
+      nullptr, nullptr);
+  if constexpr (sizeof(R) == 4) {
+    // the queued atoms in FP64: master-precision offsets, then their bond orders
+    k_fill_u64<<<S.nsm * 4, 256, 0, st>>>(S.N, S.flag_n, S.x, S.cell4, S.type, S.rep, S.reps,
+                                         (double4_32a*)S.u64);
+    k_bond<double><<<gb, APB * GRP, bond_smem<double>(S.cap_cov), st>>>(
+        S.N, S.cap_cov, S.ld, (const double4_32a*)S.u64, S.rep, S.reps, S.nl, S.ncov, *S.Pd,
+        (double4_32a*)S.bo64, nullptr, nullptr, nullptr, nullptr, nullptr, S.flag_q, S.flag_n);
+  }
 }
 
 template <class R>
 void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st) {
   if (S.N == 0) return;
 #define ASM_ARGS                                                                                        \
-  S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl, S.ncov, S.nall, S.rev,  \
+  S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl, S.ncov, S.nfix, S.nall, S.rev, \
       (const typename Vec4<R>::T*)S.bo, P, T, S.M, (R*)S.Dg, (R*)S.dinv, S.nmat
   const int g = (S.N + 255) / 256;
   if (S.asm_batch == 4) k_assemble<R, 4><<<g, 256, 0, st>>>(ASM_ARGS);
@@ -662,28 +800,39 @@ void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams
   if constexpr (sizeof(R) == 4) {
     // the stiff bonds queued by the bond pass, in FP64 (grid-strided over the queue)
     k_stiff<<<S.nsm * 4, 256, 0, st>>>(S.cap_cov, S.ld, S.stiff_n, S.stiff_q, S.nl, S.rep, S.reps, S.x,
-                                       S.cell4, S.type, (const float4*)S.bo, S.q, P, (float2*)S.stiff_pe);
+                                       S.cell4, S.type, (const float4*)S.bo, S.q, P, (double2*)S.stiff_pe);
   }
   size_t sm = force_smem<R>(S.cap_cov);
-  k_cov_force<R><<<(S.N + APB - 1) / APB, APB * GRP, sm, st>>>(
+  const int gb = (S.N + APB - 1) / APB;
+  k_cov_force<R, R><<<gb, APB * GRP, sm, st>>>(
       S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl, S.ncov,
       (const typename Vec4<R>::T*)S.bo, S.q, (const R*)S.qr, P, T, (typename Vec4<R>::T*)S.gslot, S.e_atom,
-      S.stiff_pe);
+      S.stiff_pe, nullptr, nullptr);
+  if constexpr (sizeof(R) == 4) {
+    // the queued atoms' slots and covalent energies again, in FP64
+    k_cov_force<double, float><<<gb, APB * GRP, force_smem<double>(S.cap_cov), st>>>(
+        S.N, S.cap_cov, S.ld, (const double4_32a*)S.u64, S.rep, S.reps, S.nl, S.ncov,
+        (const double4_32a*)S.bo64, S.q, S.q, *S.Pd, T, (float4*)S.gslot, S.e_atom, nullptr, S.flag_q, S.flag_n);
+  }
 }
 
 template <class R>
 void launch_coul_gather(const DevState& S, const PotParams<R>& P, const TypeParams& T, int kick, double half_dt,
                         cudaStream_t st) {
   if (S.N == 0) return;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coul_gather<R>, 256, 0) != cudaSuccess || occ < 1)
-    occ = 1;
-  long long tiles = ((long long)S.N + 255) / 256, slots = (long long)S.nsm * occ;
-  int grid = (int)(tiles < slots ? tiles : slots);
-  k_coul_gather<R><<<grid, 256, 0, st>>>(
-      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
-      S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.gslot, (const R*)S.qr, P, T, kick, half_dt,
-      S.frozen, S.F, S.v, S.e_atom, S.rep_acc, S.err, S.nh);
+  auto go = [&](auto kernel) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+    long long tiles = ((long long)S.N + 255) / 256, slots = (long long)S.nsm * occ;
+    int grid = (int)(tiles < slots ? tiles : slots);
+    kernel<<<grid, 256, 0, st>>>(
+        S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
+        S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.gslot, (const R*)S.qr, P, T, kick, half_dt,
+        S.frozen, S.F, S.v, S.e_atom, S.rep_acc, S.err, S.nh);
+  };
+  if (S.gather_batch == 4) go(k_coul_gather<R, 4>);
+  else if (S.gather_batch == 6) go(k_coul_gather<R, 6>);
+  else go(k_coul_gather<R, 8>);
 }
 
 template <class R>
@@ -700,8 +849,15 @@ cudaError_t setup_pot(int cap_cov) {
   cudaError_t e = cudaFuncSetAttribute(k_bond<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)bond_smem<R>(cap_cov));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_cov_force<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)force_smem<R>(cap_cov));
+  e = cudaFuncSetAttribute(k_cov_force<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)force_smem<R>(cap_cov));
+  if (e != cudaSuccess || sizeof(R) == 8) return e;
+  // the FP32 path's FP64 pass over queued atoms
+  e = cudaFuncSetAttribute(k_bond<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bond_smem<double>(cap_cov));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_cov_force<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)force_smem<double>(cap_cov));
 }
 template cudaError_t setup_pot<float>(int);
 template cudaError_t setup_pot<double>(int);
@@ -752,6 +908,58 @@ cudaError_t tune_assemble(DevState& S, const PotParams<R>& P, const TypeParams& 
 template cudaError_t tune_assemble<float>(DevState&, const PotParams<float>&, const TypeParams&, cudaStream_t, float*);
 template cudaError_t tune_assemble<double>(DevState&, const PotParams<double>&, const TypeParams&, cudaStream_t,
                                            float*);
+
+// Entries in flight per thread in the charge-force gather (4, 6 or 8; the
+// depth sets the registers, 104 to 128, and so the resident blocks): on the
+// state of a completed evaluation without a kick, each depth runs the
+// covalent force pass (untimed: the gather adds to the per-atom energies it
+// writes) and the gather (timed), twice; the fastest is kept and the pair
+// runs once more so the evaluation's results are as the kept depth sums them.
+template <class R>
+cudaError_t tune_gather(DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st, float* ms_out) {
+  if (S.N == 0) return cudaSuccess;
+  const int depth[3] = {4, 6, 8};
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  const size_t acc_bytes = sizeof(double) * (size_t)S.R * RA_STRIDE;
+  float t[3] = {0.f, 0.f, 0.f};
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    S.gather_batch = depth[k];
+    float sum = 0.f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      cudaMemsetAsync(S.rep_acc, 0, acc_bytes, st);
+      launch_cov_force<R>(S, P, T, st);
+      cudaEventRecord(e0, st);
+      launch_coul_gather<R>(S, P, T, 0, 0.0, st);
+      cudaEventRecord(e1, st);
+      e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) sum += ms;   // the first is a warm-up
+    }
+    t[k] = 0.5f * sum;
+    if (ms_out) ms_out[k] = t[k];
+  }
+  int pick = 8;
+  float best = t[2];
+  for (int k = 0; k < 2; ++k)
+    if (t[k] > 0.f && t[k] < best) { best = t[k]; pick = depth[k]; }
+  S.gather_batch = pick;
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(S.rep_acc, 0, acc_bytes, st);
+    launch_cov_force<R>(S, P, T, st);
+    launch_coul_gather<R>(S, P, T, 0, 0.0, st);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+template cudaError_t tune_gather<float>(DevState&, const PotParams<float>&, const TypeParams&, cudaStream_t, float*);
+template cudaError_t tune_gather<double>(DevState&, const PotParams<double>&, const TypeParams&, cudaStream_t,
+                                         float*);
 
 template void launch_assemble<float>(const DevState&, const PotParams<float>&, const TypeParams&, cudaStream_t);
 template void launch_assemble<double>(const DevState&, const PotParams<double>&, const TypeParams&, cudaStream_t);

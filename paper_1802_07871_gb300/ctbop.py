@@ -35,6 +35,7 @@ EXPORTS = (
     "ctbop_set_total_charge", "ctbop_compute", "ctbop_step", "ctbop_get", "ctbop_status",
     "ctbop_profile_steps", "ctbop_energy_noalloc", "ctbop_param_grad", "ctbop_set_params", "ctbop_set_thermostat",
     "ctbop_removal_energies", "ctbop_minimize", "ctbop_rings", "ctbop_set_order",
+    "ctbop_measure_peaks",
 )
 # one record of ctbop_rings (struct ctbop_ring)
 RING_DTYPE = np.dtype([("replica", "<i4"), ("size", "<i4"), ("centre", "<f8", 3), ("orientation", "<f8")])
@@ -74,13 +75,25 @@ class Stats(C.Structure):
         ("mean_cov", C.c_double), ("mean_all", C.c_double), ("cg_residual_start", C.c_double),
         ("cg_mv_batch", C.c_int32), ("asm_batch", C.c_int32), ("cg_mv_ms", C.c_double * 3),
         ("mean_mat", C.c_double), ("asm_ms", C.c_double * 3),
+        ("gather_batch", C.c_int32), ("fp64_atoms", C.c_int32), ("fp64_bonds", C.c_int32), ("pad", C.c_int32),
+        ("gather_ms", C.c_double * 3),
     ]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["cg_mv_ms"] = list(self.cg_mv_ms)
         d["asm_ms"] = list(self.asm_ms)
+        d["gather_ms"] = list(self.gather_ms)
+        d.pop("pad", None)
         return d
+
+
+class Peaks(C.Structure):
+    _fields_ = [
+        ("fp32_tflops", C.c_double), ("mufu_ex2_tops", C.c_double), ("mufu_rsq_tops", C.c_double),
+        ("fp64_tflops", C.c_double), ("ms", C.c_double * 4), ("sm_mhz", C.c_double),
+        ("sms", C.c_int32), ("pad", C.c_int32),
+    ]
 
 
 _lib = None
@@ -118,6 +131,7 @@ def lib():
         "ctbop_minimize": ([vp, C.c_int64, C.c_double, C.c_double, C.c_double, vp, vp], C.c_int),
         "ctbop_rings": ([vp, C.c_double, C.c_int32, C.c_int64, vp, vp], C.c_int),
         "ctbop_set_order": ([vp, vp], C.c_int),
+        "ctbop_measure_peaks": ([C.c_int32, vp, C.POINTER(Peaks)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -125,6 +139,19 @@ def lib():
         f.restype = res
     _lib = L
     return L
+
+
+def measure_peaks(device: int = 0, stream=None) -> dict:
+    """FP32 FMA, special-function (ex2, rsqrt) and FP64 FMA rates of the GPU
+    (ctbop_measure_peaks), with the SM clock they were taken at."""
+    out = Peaks()
+    ptr = None if stream is None else int(stream)
+    rc = lib().ctbop_measure_peaks(int(device), ptr, C.byref(out))
+    if rc != OK:
+        raise CtbopError(f"ctbop_measure_peaks: {ERR.get(rc, rc)}")
+    return {"fp32_tflops": out.fp32_tflops, "mufu_ex2_tops": out.mufu_ex2_tops,
+            "mufu_rsq_tops": out.mufu_rsq_tops, "fp64_tflops": out.fp64_tflops,
+            "ms": list(out.ms), "sm_mhz": out.sm_mhz, "sms": out.sms}
 
 
 def params_struct(d: dict) -> Params:

@@ -6,21 +6,24 @@ from oracle import ctbop_oracle as O
 from paper_1802_07871_gb300 import ctbop
 from paper_1802_07871_gb300 import structures as st
 
-# Tolerances. FP64 path: limited by the CG stopping rule (rms stationarity
-# residual 1e-10 eV/e). Mixed path: the stated targets, force error relative
-# to the RMS force 1e-4, energy 1e-6 eV/atom, charges 1e-5 e.
+# Tolerances, the same for every geometry (periodic boxes smaller than the
+# charge cutoff, clusters with pairs compressed to 1.45 A, batched replicas
+# and the annealing ensemble included).
+# FP64 path: limited by the CG stopping rule (max-norm stationarity residual
+# 1e-11 eV/e).
+# Mixed path: the stated targets, force error 1e-4 of the RMS force, total
+# energy 1e-6 eV/atom; charges and mu 1e-5 (the FP32 storage floor of the
+# stored charge matrix, which sets the solve's tolerance). Per-atom energies
+# are not stationary in q one by one, so their error is first order in the
+# charge error: 1e-5 e times the self-energy slope chi + 2 J |q| of C
+# (about 5 eV/e) gives 5e-5 eV.
 TOL = {
     "fp64": dict(force=1e-8, energy=1e-9, charge=1e-8, virial=1e-8, eatom=1e-8, mu=1e-8),
-    "mixed": dict(force=1e-4, energy=1e-6, charge=1e-5, virial=1e-4, eatom=2e-5, mu=1e-5),
-    # Stress geometries in mixed precision: FP32 cell-local positions carry
-    # ~5e-7 A of rounding, so a term's energy error is about |dE_term/dr| x
-    # 5e-7 A, and each stored FP32 charge-matrix entry is rounded by ~6e-8
-    # relative. In cells smaller than the charge cutoff every periodic image
-    # of a pair rounds alike (~240 correlated terms per atom), and random
-    # clusters hold pairs compressed to 1.45 A with 50 eV repulsive terms;
-    # there the errors no longer average out. Forces keep the 1e-4 bar.
-    "mixed_stress": dict(force=1e-4, energy=5e-6, charge=3e-5, virial=1e-4, eatom=1e-4, mu=3e-5),
+    "mixed": dict(force=1e-4, energy=1e-6, charge=1e-5, virial=1e-4, eatom=5e-5, mu=1e-5),
 }
+# every comparison's measured errors (test, policy, errors), printed at the
+# end of the session by the terminal-summary hook of conftest.py
+MEASURED = []
 
 
 def gpu_eval(structures, params, precision, Q=None, charges=None, fixed=False, **kw):
@@ -43,32 +46,28 @@ def oracle_eval(s, params, Q=0.0, q=None):
     return O.evaluate(s.x, s.types, s.box, s.pbc, params, Q=Q, q=q)
 
 
-def compare(g, o, n, precision, sl=slice(None), r=0, check_charges=True, check_mu=True, stress=False):
-    """Compare replica r of a GPU result (atoms sl) with an oracle result."""
-    t = TOL["mixed_stress" if (stress and precision == "mixed") else precision]
+def compare(g, o, n, precision, sl=slice(None), r=0, check_charges=True, check_mu=True):
+    """Compare replica r of a GPU result (atoms sl) with an oracle result;
+    the measured errors are recorded (MEASURED) before any bar is checked."""
+    import os
+    t = TOL[precision]
     F, Fo = g["forces"][sl], o["F"]
     rms = max(np.sqrt(np.mean(Fo ** 2)), 1e-3)
-    ferr = np.max(np.abs(F - Fo)) / rms if len(Fo) else 0.0
-    eerr = abs(g["energy"][r] - o["E"]) / max(n, 1)
-    res = {"force": ferr, "energy": eerr}
-    assert ferr <= t["force"], (precision, "force", ferr)
-    assert eerr <= t["energy"], (precision, "energy", eerr)
+    res = {"force": np.max(np.abs(F - Fo)) / rms if len(Fo) else 0.0,
+           "energy": abs(g["energy"][r] - o["E"]) / max(n, 1)}
     if check_charges and len(Fo):
-        qerr = np.max(np.abs(g["charges"][sl] - o["q"]))
-        res["charge"] = qerr
-        assert qerr <= t["charge"], (precision, "charge", qerr)
+        res["charge"] = np.max(np.abs(g["charges"][sl] - o["q"]))
     W, Wo = g["virial"][r], o["virial"]
-    werr = np.max(np.abs(W - Wo)) / max(np.max(np.abs(Wo)), 1.0)
-    res["virial"] = werr
-    assert werr <= t["virial"], (precision, "virial", werr)
+    res["virial"] = np.max(np.abs(W - Wo)) / max(np.max(np.abs(Wo)), 1.0)
     if len(Fo):
-        aerr = np.max(np.abs(g["e_atom"][sl] - o["e_atom"]))
-        res["eatom"] = aerr
-        assert aerr <= t["eatom"], (precision, "e_atom", aerr)
+        res["eatom"] = np.max(np.abs(g["e_atom"][sl] - o["e_atom"]))
     if check_mu and o.get("mu") is not None and len(Fo) > 1:
-        merr = abs(g["mu"][r] - o["mu"])
-        res["mu"] = merr
-        assert merr <= t["mu"], (precision, "mu", merr)
+        res["mu"] = abs(g["mu"][r] - o["mu"])
+    res = {k: float(v) for k, v in res.items()}
+    test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0].split("::")[-1]
+    MEASURED.append((f"{test} [{r}]", precision, res))
+    for k, v in res.items():
+        assert v <= t[k], (precision, k, v, t[k])
     return res
 
 
@@ -103,6 +102,9 @@ def sampled_local_check(s, params, g, precision, samples, rcut=9.0):
         worst["force"] = max(worst["force"], np.max(np.abs(g["forces"][i] - Fo)) / rmsF)
         worst["eatom"] = max(worst["eatom"], abs(g["e_atom"][i] - eo))
         worst["stationarity"] = max(worst["stationarity"], abs(dq - g["mu"][0]))
+    import os
+    test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0].split("::")[-1]
+    MEASURED.append((f"{test} [sampled]", precision, {k: float(v) for k, v in worst.items()}))
     assert worst["force"] <= t["force"], worst
     assert worst["eatom"] <= t["eatom"], worst
     assert worst["stationarity"] <= 10 * t["mu"], worst
@@ -136,3 +138,66 @@ def oracle_EF_many(structs, params, workers=None):
             else:
                 os.environ[k] = v
     return [e for e, _ in out], [f for _, f in out]
+
+
+def _block_eval(args):
+    """Oracle forces, per-atom energies and dE/dq of the core atoms of one
+    spatial block, from an open cut (block plus halo) at fixed charges
+    (top-level, so a spawn pool can run it)."""
+    x, types, q, ncore, params = args
+    sysm = O.System(x, types, np.full(3, 1e4), np.array([False] * 3), params)
+    F = sysm.forces(q)[:ncore]
+    e = sysm.energy(q, per_atom=True)[:ncore]
+    dq = sysm.dE_dq(q)[:ncore]
+    return F, e, dq
+
+
+def blocked_oracle_check(s, params, g, nblocks=(8, 8), halo=9.0, workers=None):
+    """Every atom of a slab that is periodic in x and y: the oracle evaluates
+    the force, the per-atom energy and dE/dq_i of each atom at the GPU's
+    charges, block by block. A block's cut holds the atoms within `halo` of
+    the block's x-y rectangle (minimum image), treated as an open cluster;
+    an atom's force, energy and dE/dq depend only on atoms within
+    max(Rc, 2 S_max) of it (< halo), so the core atoms are exact. Returns the
+    oracle's (F, e_atom, dE/dq) for all atoms in the structure's order."""
+    import multiprocessing as mp
+    import os
+    assert s.pbc[0] and s.pbc[1] and not s.pbc[2]
+    q = g["charges"]
+    L = s.box[:2]
+    xy = np.mod(s.x[:, :2], L)
+    width = L / np.asarray(nblocks)
+    cell = np.minimum((xy // width).astype(int), np.asarray(nblocks) - 1)   # each atom's block
+    jobs, cores = [], []
+    for bx in range(nblocks[0]):
+        for by in range(nblocks[1]):
+            c = (np.array([bx, by]) + 0.5) * width
+            d = xy - c
+            d -= np.round(d / L) * L                     # minimum image about the block centre
+            core = (cell[:, 0] == bx) & (cell[:, 1] == by)
+            near = np.all(np.abs(d) < 0.5 * width + halo, axis=1)
+            idx = np.concatenate([np.nonzero(core)[0], np.nonzero(near & ~core)[0]])
+            xc = np.concatenate([c + d[idx], s.x[idx, 2:3]], axis=1)
+            jobs.append((xc, s.types[idx], q[idx], int(core.sum()), params))
+            cores.append(np.nonzero(core)[0])
+    allc = np.concatenate(cores)
+    assert len(allc) == s.n and len(np.unique(allc)) == s.n   # every atom in exactly one core
+    workers = workers or min(16, os.cpu_count() or 1)
+    keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in keep:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            out = pool.map(_block_eval, jobs, chunksize=1)
+    finally:
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    F = np.zeros((s.n, 3))
+    e = np.zeros(s.n)
+    dq = np.zeros(s.n)
+    for ids, (Fb, eb, dqb) in zip(cores, out):
+        F[ids], e[ids], dq[ids] = Fb, eb, dqb
+    return F, e, dq

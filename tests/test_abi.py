@@ -31,13 +31,13 @@ def test_library_builds_and_exports_declared_symbols():
 def test_struct_layouts_match_header(tmp_path):
     from paper_1802_07871_gb300 import ctbop
     c = tmp_path / "sz.c"
-    c.write_text('#include <stdio.h>\n#include "ctbop.h"\nint main(){printf("%zu %zu %zu\\n",'
-                 'sizeof(ctbop_params), sizeof(ctbop_options), sizeof(ctbop_stats));}\n')
+    c.write_text('#include <stdio.h>\n#include "ctbop.h"\nint main(){printf("%zu %zu %zu %zu\\n",'
+                 'sizeof(ctbop_params), sizeof(ctbop_options), sizeof(ctbop_stats), sizeof(ctbop_peaks));}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     assert [int(v) for v in out] == [ctypes.sizeof(ctbop.Params), ctypes.sizeof(ctbop.Options),
-                                     ctypes.sizeof(ctbop.Stats)]
+                                     ctypes.sizeof(ctbop.Stats), ctypes.sizeof(ctbop.Peaks)]
 
 
 def test_params_marshalling_l1_padding():

@@ -142,3 +142,23 @@ def test_empty_system_runs_every_entry_point():
     L, G = sysm.param_grad(w_E=[1.0], E_ref=[0.0])
     assert L == 0.0
     sysm.close()
+
+
+def test_triclinic_cell_is_refused():
+    """Cells are orthorhombic (a reading the library documents): a cell
+    matrix with an off-diagonal entry is refused through the C ABI with
+    INVALID_ARG and a message, and nothing of the box is changed."""
+    import ctypes as C
+    s = st.bulk_3c_512()
+    sysm = ctbop.System(P1, precision="mixed")
+    sysm.load(s)
+    h = np.ascontiguousarray(np.diag(s.box).reshape(1, 3, 3))
+    h[0, 0, 1] = 0.2                              # a shear of the first cell vector
+    p = np.ones((1, 3), dtype=np.uint8)
+    L = ctbop.lib()
+    rc = L.ctbop_set_box(sysm._h, h.ctypes.data_as(C.c_void_p), p.ctypes.data_as(C.c_void_p))
+    assert ctbop.ERR[rc] == "INVALID_ARG"
+    assert b"orthorhombic" in L.ctbop_last_error(sysm._h)
+    sysm.compute()                                # the previous box still holds
+    assert sysm.status()["rc"] == "OK"
+    sysm.close()

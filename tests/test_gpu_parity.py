@@ -77,7 +77,7 @@ def test_small_periodic_boxes_images(prec, ncell):
     s = st.Structure("small", s.x, t, s.box, s.pbc)
     g = gpu_eval(s, P1, prec)
     o = oracle_eval(s, P1)
-    compare(g, o, s.n, prec, stress=True)
+    compare(g, o, s.n, prec)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -86,7 +86,7 @@ def test_open_cluster(prec):
     s = _cluster(41, 3)
     g = gpu_eval(s, P1, prec)
     o = oracle_eval(s, P1)
-    compare(g, o, s.n, prec, stress=True)
+    compare(g, o, s.n, prec)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -104,7 +104,7 @@ def test_batched_replicas_uneven(prec):
     for r, s in enumerate(reps):
         o = oracle_eval(s, P1) if s.n else {"F": np.zeros((0, 3)), "E": 0.0, "q": np.zeros(0),
                                               "virial": np.zeros((3, 3)), "e_atom": np.zeros(0), "mu": None}
-        compare(g, o, s.n, prec, sl=slice(off[r], off[r + 1]), r=r, stress=True)
+        compare(g, o, s.n, prec, sl=slice(off[r], off[r + 1]), r=r)
     # the lone C atom: no neighbours, q = Q = 0, E = E0(C)
     assert abs(g["energy"][3] - P1["self"]["E0"][1]) < 1e-12
 
@@ -249,15 +249,29 @@ def test_full_size_slab_20k_sampled(prec):
     assert np.max(np.abs(g["forces"].sum(0))) < (1e-6 if prec == "fp64" else 5e-2)
 
 
-def test_full_size_slab_1m_sampled():
+def test_full_size_slab_1m_every_atom():
     """The ~1.005M-atom stepped slab with C adatoms, mixed precision, in the
-    launch configuration the benchmark times: sampled local oracle checks."""
+    launch configuration the benchmark times, checked at every atom: the
+    oracle evaluates forces, per-atom energies and dE/dq_i at the GPU's
+    charges, block by block (blocked_oracle_check). The total energy is the
+    sum of the oracle's per-atom energies; the charges are the minimiser to
+    the solve's tolerance when dE/dq_i = mu at every atom (the energy at
+    them then differs from the minimum only in second order)."""
+    from tests.gpu_helpers import MEASURED, blocked_oracle_check
     s = st.stepped_slab_1m()
     g = gpu_eval(s, P1, "mixed")
-    rng = np.random.default_rng(1)
-    ad = np.nonzero(s.types == 1)[0][-900:]
-    samples = np.concatenate([rng.choice(s.n, 24, replace=False), rng.choice(ad, 8, replace=False)])
-    sampled_local_check(s, P1, g, "mixed", samples)
+    F, e, dq = blocked_oracle_check(s, P1, g)
+    rms = np.sqrt(np.mean(F ** 2))
+    res = {"force": float(np.max(np.abs(g["forces"] - F)) / rms),
+           "eatom": float(np.max(np.abs(g["e_atom"] - e))),
+           "energy": float(abs(g["energy"][0] - e.sum()) / s.n),
+           "stationarity": float(np.max(np.abs(dq - g["mu"][0])))}
+    MEASURED.append(("test_full_size_slab_1m_every_atom [all atoms]", "mixed", res))
+    t = TOL["mixed"]
+    assert res["force"] <= t["force"] and res["eatom"] <= t["eatom"] and res["energy"] <= t["energy"], res
+    # the solve stops at 1e-5 eV/e in its own FP32 matrix; the FP64 residual
+    # adds that matrix's rounding
+    assert res["stationarity"] <= 3 * t["mu"], res
     assert abs(g["charges"].sum()) < 1e-6
 
 
@@ -272,5 +286,5 @@ def test_annealing_ensemble_replicas(prec):
     off = 0
     for r, s in enumerate(structs):
         o = oracle_eval(s, P1)
-        compare(g, o, s.n, prec, sl=slice(off, off + s.n), r=r, stress=True)
+        compare(g, o, s.n, prec, sl=slice(off, off + s.n), r=r)
         off += s.n

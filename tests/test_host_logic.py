@@ -193,12 +193,37 @@ def test_reference_arm_line(bench, monkeypatch, capsys):
 
 
 def test_cpu_baseline_times_the_oracle_on_a_bounded_sample(bench):
-    cb = bench.cpu_baseline(budget_s=2.0, steps=1)
+    cb = bench.cpu_baseline(steps=1, configs=False)
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0
     assert "stepped 4H-SiC slab" in cb["sample"]
 
 
-def test_cpu_baseline_all_cores_runs_in_a_child_process(bench):
-    cb = bench.cpu_baseline_all_cores(budget_s=2.0, steps=1)
+def test_cpu_baseline_all_cores_runs_one_process_per_core(bench):
+    cb = bench.cpu_baseline_all_cores(steps=1)
     assert "unavailable" not in cb, cb
     assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1) and cb["value"] > 0
+    lo, hi = cb["per_process_min_max"]
+    assert 0 < lo <= hi and cb["value"] >= cb["cores"] * lo * 0.999
+
+
+def test_roofline_table_accounting(bench):
+    """Per-phase roofline: per-step phases divide by the profiled steps, the
+    CG phases by their launches; the binding bound is the largest fraction;
+    the step fraction is the time-weighted mean over the covered phases."""
+    n = 1000
+    work = bench.phase_work(n, entries_all=230 * n, entries_mat=195 * n, n_cov_entries=5 * n,
+                            bonds=4 * n, triplets=12 * n)
+    assert work["bond"]["flops"] == 4 * n * 31 + 12 * n * 32
+    assert work["cg_matvec"]["per"] == "launch"
+    ph = {"bond": (2.0, 2), "cg_matvec": (3.0, 30), "lists": (1.0, 24)}
+    peaks = {"fp32_tflops": 80.0, "mufu_ex2_tops": 5.0, "mufu_rsq_tops": 4.0}
+    table, step = bench.roofline_table(ph, 2, work, peaks, 6000.0)
+    assert set(table) == {"bond", "cg_matvec"}
+    assert table["bond"]["ms_per_step"] == pytest.approx(1.0)
+    assert table["cg_matvec"]["ms_per_launch"] == pytest.approx(0.1)
+    hbm = work["cg_matvec"]["bytes"] / 1e-4 / 1e9 / 6000.0
+    assert table["cg_matvec"]["bound"] == "hbm" and table["cg_matvec"]["frac"] == pytest.approx(hbm)
+    for row in table.values():
+        assert row["frac"] == pytest.approx(max(row["frac_by_bound"].values()), abs=1e-4)
+    want = (2.0 * table["bond"]["frac"] + 3.0 * table["cg_matvec"]["frac"]) / 5.0
+    assert step["frac"] == pytest.approx(want) and step["covered_share"] == pytest.approx(5.0 / 6.0)

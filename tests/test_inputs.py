@@ -74,3 +74,12 @@ def test_perturbed_params_change_only_stated_leaves():
 def test_sic_3c_cubic_unchanged_by_shape_argument():
     a, b = st.sic_3c(3, 4.36, 0.05, 9), st.sic_3c((3, 3, 3), 4.36, 0.05, 9)
     assert np.array_equal(a.x, b.x) and np.array_equal(a.box, b.box)
+
+
+def test_strain_generator_refuses_shear():
+    """The differentiation batch strains its 3C-SiC cells along the cell axes
+    only (the library's cells are orthorhombic): an off-diagonal strain is
+    refused rather than silently dropped."""
+    import pytest
+    with pytest.raises(ValueError, match="orthorhombic"):
+        st.sic_3c(2, 4.36, 0.0, strain=np.array([[0.01, 0.02, 0.0], [0.02, 0.0, 0.0], [0.0, 0.0, 0.0]]))
