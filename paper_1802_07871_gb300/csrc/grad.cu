@@ -190,15 +190,13 @@ template <bool Agg> struct Acc {
   }
 };
 
-// FP64 partial sums of working-precision terms (values, or values with
-// their tangents), kept in registers over a short loop.
-template <class S> struct SumT { using type = double; };
-template <class T> struct SumT<DualT<T>> { using type = DualT<double>; };
-__device__ inline double to_sum(double x) { return x; }
-__device__ inline double to_sum(float x) { return (double)x; }
-template <class T> __device__ inline DualT<double> to_sum(DualT<T> x) {
-  return DualT<double>((double)x.v, (double)x.d);
-}
+// Partial sums of working-precision terms (values, or values with their
+// tangents) over one bond's few third atoms of one type, kept in registers
+// in the working precision: at most a handful of terms, so FP32 adds lose
+// nothing that matters, and the FP64 pipe (a small fraction of the FP32
+// rate on this GPU) sees only the block sums, once per bond and slot.
+template <class S> struct SumT { using type = S; };
+template <class S> __device__ inline S to_sum(S x) { return x; }
 
 #define PG_GRP 8     // lanes per atom
 #define PG_APB 16    // atoms per block

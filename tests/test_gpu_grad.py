@@ -234,17 +234,19 @@ def test_differentiation_batch_full_size():
 
 @pytest.mark.parametrize("kind", ["energy", "force"])
 def test_mixed_policy_gradient_matches_oracle(kind):
-    """The same gradient with FP32 terms (FP64 sums) on the mixed system.
-    Its loss and g = dL/dF come from the mixed path's own energies and
-    forces, whose errors (1e-6 eV/atom, 1e-4 of the RMS force at most) are
-    divided by the target differences (a 2% parameter change moves forces
-    by a few per cent): that, not the FP32 gradient arithmetic, sets the
-    bar."""
+    """The same gradient with FP32 terms (FP64 block sums) on the mixed
+    system. Its loss and g = dL/dF come from the mixed path's own energies
+    and forces, whose errors are divided by the target differences (a 2%
+    parameter change moves forces by a few per cent): that, not the FP32
+    gradient arithmetic, sets the bar. On geometries like these members
+    (strained crystals, graphene, clusters) the mixed forces carry at most
+    about 2e-5 of the RMS force (the parity tests' recorded errors), so the
+    force-loss gradient is held to 2e-5 / 2% = 1e-3 relative."""
     structs, loss = _member_loss(kind)
     if kind == "energy":
         _compare(structs, loss, rtol=1e-5, precision="mixed", ltol=1e-5)
     else:
-        _compare(structs, loss, rtol=5e-3, precision="mixed", ltol=5e-3)
+        _compare(structs, loss, rtol=1e-3, precision="mixed", ltol=1e-3)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
