@@ -272,6 +272,18 @@ def aggregate_value(n_atoms, steps, world, ms):
     return n_atoms * steps * world / (ms / 1e3)
 
 
+def tuned_shapes(d):
+    """The autotuned shapes of a system's passes and the timings they were
+    picked from (ms per launch, in the order of the candidates listed)."""
+    r = lambda xs: [round(x, 4) for x in xs]
+    return {"cg_matvec_depth": d["cg_mv_batch"], "cg_matvec_ms_by_depth_4_8_16": r(d["cg_mv_ms"]),
+            "assembly_depth": d["asm_batch"], "assembly_ms_by_depth_4_8_16": r(d["asm_ms"]),
+            "gather_depth": d["gather_batch"], "gather_ms_by_depth_4_6_8": r(d["gather_ms"]),
+            "covalent_lanes": d["cov_lanes"], "covalent_ms_by_lanes_4_8_16": r(d["cov_ms"]),
+            "list_build_shape": [d["build_warps"], d["build_batch"]],
+            "list_build_ms_by_shape_2x64_2x128_4x64_4x128_8x64_8x128": r(d["build_ms"])}
+
+
 def run_ensemble(dev, stream, steps=20, warmup=3):
     """Secondary measurement: the 256-replica annealing ensemble (uneven
     200-3000-atom SiC slabs with Si vacancies, amorphous C clusters and
@@ -306,7 +318,7 @@ def run_ensemble(dev, stream, steps=20, warmup=3):
             "n_replicas": len(structs), "n_atoms": n, "steps": steps, "warmup": warmup,
             "value": n * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
             "cg_iters_per_step": (st1["cg_iters_total"] - st0["cg_iters_total"]) / steps,
-            "precision": "mixed"}
+            "precision": "mixed", "tuned": tuned_shapes(st1)}
 
 
 def run_param_grad(dev, stream, precision="mixed", calls=3, warmup=1):
@@ -719,12 +731,7 @@ def run_ours(a):
                    "cg_iters_per_step": cg_per_step, "rebuilds_in_timed_region": rebuilds,
                    "mean_entries_per_atom": st2["mean_all"], "mean_matrix_entries_per_atom": st2["mean_mat"],
                    "mean_covalent_entries": st2["mean_cov"],
-                   "cg_matvec_depth_tuned": st2["cg_mv_batch"],
-                   "cg_matvec_ms_by_depth_4_8_16": [round(x, 4) for x in st2["cg_mv_ms"]],
-                   "assembly_depth_tuned": st2["asm_batch"],
-                   "assembly_ms_by_depth_4_8_16": [round(x, 4) for x in st2["asm_ms"]],
-                   "gather_depth_tuned": st2["gather_batch"],
-                   "gather_ms_by_depth_4_6_8": [round(x, 4) for x in st2["gather_ms"]],
+                   "tuned": tuned_shapes(st2),
                    "fp64_atoms_last_step": st2["fp64_atoms"], "fp64_pair_bonds_last_step": st2["fp64_bonds"]},
         "roofline": {"kernel": "k_cg_mv (charge CG matrix pass)", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,

@@ -146,6 +146,12 @@ typedef struct ctbop_stats {
     int32_t fp64_bonds;       /* MIXED: bonds whose pair term the last evaluation took in FP64 */
     int32_t pad;
     double  gather_ms[3];     /* ms per charge-force gather of the depths 4, 6, 8 at the last tuning */
+    int32_t cov_lanes;        /* lanes per atom in the bond-order and covalent-force passes (autotuned) */
+    int32_t pad2;
+    double  cov_ms[3];        /* ms of bond-order + covalent-force pass at 4, 8, 16 lanes at the last tuning */
+    int32_t build_warps;      /* list build: warps per block (autotuned) */
+    int32_t build_batch;      /* list build: stencil cells per batch (autotuned) */
+    double  build_ms[6];      /* ms per list build of the shapes (2,64) (2,128) (4,64) (4,128) (8,64) (8,128) */
 } ctbop_stats;
 
 typedef struct ctbop_system ctbop_system;

@@ -88,6 +88,11 @@ struct ctbop_system {
   float asm_ms[3] = {0.f, 0.f, 0.f};
   float gather_ms[3] = {0.f, 0.f, 0.f};
   bool gather_forced = false;
+  float cov_ms[3] = {0.f, 0.f, 0.f};
+  bool cov_forced = false;
+  bool cov_retune = false;       // time the lanes again once MD has moved the atoms
+  int64_t cov_tuned_at = 0;      // steps at that tuning
+  float build_ms[BUILD_SHAPES] = {};
   bool tune_pending = false;
   double g_step_dt = -1.0;
   bool use_graph = true;
@@ -356,6 +361,12 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->rep_buf, &S.cg_iters, (size_t)s->R));
   CK(dalloc(s->rep_buf, &S.scan_tmp, 1040));
   CK(dalloc(s->rep_buf, &S.flag_rebuild, 1));
+  CK(dalloc(s->rep_buf, &S.flag_one, 1));
+  {
+    int one = 1;
+    CK(cudaMemcpyAsync(S.flag_one, &one, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  }
   CK(dalloc(s->rep_buf, &S.rebuild_count, 1));
   CK(dalloc(s->rep_buf, &S.precond_epoch, 1));
   CK(cudaMemsetAsync(S.precond_epoch, 0xff, sizeof(long long), s->stream));   // -1: form at the first solve
@@ -433,7 +444,11 @@ static int alloc_lists(ctbop_system* s, int cap_cov, int cap_all) {
   S.gslot = gs;
   S.M = M;
   if (cap_cov > 512) return fail(s, CTBOP_ERR_NEIGH_OVERFLOW, "covalent entries per atom beyond 512");
-  CK(s->mixed ? setup_pot<float>(cap_cov) : setup_pot<double>(cap_cov));
+  CK(s->mixed ? setup_pot<float>(cap_cov, &S.cov_lanes_ok) : setup_pot<double>(cap_cov, &S.cov_lanes_ok));
+  if (!(S.cov_lanes_ok & (S.cov_lanes == 4 ? 1 : S.cov_lanes == 8 ? 2 : 4))) {
+    S.cov_lanes = (S.cov_lanes_ok & 2) ? 8 : 16;
+    destroy_graphs(s);
+  }
   s->alloc_cov = cap_cov;
   s->alloc_all = cap_all;
   return CTBOP_OK;
@@ -546,6 +561,10 @@ static int run_direct(ctbop_system* s, const PotParams<Rr>& P, bool md, double d
   return CTBOP_OK;
 }
 
+// MD steps after the first lane tuning at which the covalent lanes are
+// timed again (at the end of the step chunk that reaches it).
+#define COV_RETUNE_STEPS 50
+
 static int read_err(ctbop_system* s, unsigned& bits) {
   CK(cudaStreamSynchronize(s->stream));
   CK(sync_copy(s, &bits, s->S.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
@@ -619,9 +638,30 @@ static int ensure_lists(ctbop_system* s) {
       S.gather_batch = gforced;
       destroy_graphs(s);
     }
+    // and the covalent passes' lanes per atom (CTBOP_COV_LANES = 4, 8 or 16)
+    const char* clv = getenv("CTBOP_COV_LANES");
+    int cforced = clv ? atoi(clv) : 0;
+    s->cov_forced = (cforced == 4 && (S.cov_lanes_ok & 1)) || (cforced == 8 && (S.cov_lanes_ok & 2)) || cforced == 16;
+    if (s->cov_forced && S.cov_lanes != cforced) {
+      S.cov_lanes = cforced;
+      destroy_graphs(s);
+    }
+    // the list build's shape (CTBOP_BUILD_SHAPE = "warps,batch" forces one),
+    // timed here on the lists just built
+    const char* bsv = getenv("CTBOP_BUILD_SHAPE");
+    int bw = 0, bb = 0, bforced = -1;
+    if (bsv && sscanf(bsv, "%d,%d", &bw, &bb) == 2) bforced = build_shape_index(bw, bb);
+    int before_b = S.build_shape;
+    if (bforced >= 0) {
+      S.build_shape = bforced;
+    } else {
+      cudaError_t e = s->mixed ? tune_build<float>(S, s->Pf, S.flag_one, s->stream, s->build_ms)
+                               : tune_build<double>(S, s->Pd, S.flag_one, s->stream, s->build_ms);
+      if (e != cudaSuccess) return fail(s, CTBOP_ERR_CUDA, std::string("list-build tuning: ") + cudaGetErrorString(e));
+    }
     s->tuned_N = S.N;
     s->tuned_cap = S.cap_all;
-    if (S.mv_batch != before) destroy_graphs(s);
+    if (S.mv_batch != before || S.build_shape != before_b) destroy_graphs(s);
   }
   return CTBOP_OK;
 }
@@ -651,12 +691,20 @@ static int eval_t(ctbop_system* s, const PotParams<Rr>& P, uint32_t flags) {
     int rc = run_direct<Rr>(s, P, false, 0.0, true);
     if (rc) return rc;
     int before = s->S.mv_batch, before_asm = s->S.asm_batch, before_g = s->S.gather_batch;
+    int before_c = s->S.cov_lanes;
     cudaError_t e = tune_cg_mv<Rr>(s->S, s->stream, s->mv_ms);
     if (e == cudaSuccess) e = tune_assemble<Rr>(s->S, P, s->T, s->stream, s->asm_ms);
+    if (e == cudaSuccess && !s->cov_forced) {
+      e = tune_cov<Rr>(s->S, P, s->T, s->stream, s->cov_ms, true);
+      s->cov_retune = true;
+      s->cov_tuned_at = s->steps;
+    }
     if (e == cudaSuccess && !s->gather_forced) e = tune_gather<Rr>(s->S, P, s->T, s->stream, s->gather_ms);
     if (e != cudaSuccess) return fail(s, CTBOP_ERR_CUDA, std::string("pass tuning: ") + cudaGetErrorString(e));
     s->tune_pending = false;
-    if (s->S.mv_batch != before || s->S.asm_batch != before_asm || s->S.gather_batch != before_g) destroy_graphs(s);
+    if (s->S.mv_batch != before || s->S.asm_batch != before_asm || s->S.gather_batch != before_g ||
+        s->S.cov_lanes != before_c)
+      destroy_graphs(s);
     s->solves++;
     s->have_forces = true;
     return CTBOP_OK;
@@ -1191,6 +1239,30 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
     s->steps += n;
     s->solves += n;
     if (bits & CT_ERR_CG_MAXITER) { result = fail(s, CTBOP_ERR_CG_NOT_CONVERGED, "charge CG reached max_iter"); break; }
+    if (s->cov_retune && s->steps >= s->cov_tuned_at + COV_RETUNE_STEPS) {
+      // The covalent lanes were timed on the starting configuration, where
+      // the covalent entries per atom can be uniform (an ideal lattice: four
+      // each, which four lanes per atom cover in one round); once MD has
+      // spread them (thermal motion brings second neighbours inside the
+      // covalent radius plus skin) the lane count is timed again, once,
+      // here, on the current state and in its precision mode (its forces
+      // and sums are restored), and the step graph captured again at once
+      // if the count changed.
+      s->cov_retune = false;
+      int before_c = S.cov_lanes;
+      cudaError_t e = s->mixed ? tune_cov<float>(S, s->Pf, s->T, s->stream, s->cov_ms, false)
+                               : tune_cov<double>(S, s->Pd, s->T, s->stream, s->cov_ms, false);
+      if (e != cudaSuccess) { result = fail(s, CTBOP_ERR_CUDA, std::string("lane tuning: ") + cudaGetErrorString(e)); break; }
+      if (S.cov_lanes != before_c) {
+        destroy_graphs(s);
+        if (s->use_graph) {
+          result = s->mixed ? capture_graph<float>(s, s->Pf, true, dt_fs, &s->g_step)
+                            : capture_graph<double>(s, s->Pd, true, dt_fs, &s->g_step);
+          if (result) break;
+          s->g_step_dt = dt_fs;
+        }
+      }
+    }
   }
   cudaStreamSynchronize(s->stream);
   return result;
@@ -1296,6 +1368,10 @@ int ctbop_status(ctbop_system* s, ctbop_stats* st) {
   st->asm_batch = S.asm_batch;
   for (int k = 0; k < 3; ++k) st->gather_ms[k] = s->gather_ms[k];
   st->gather_batch = S.gather_batch;
+  for (int k = 0; k < 3; ++k) st->cov_ms[k] = s->cov_ms[k];
+  st->cov_lanes = S.cov_lanes;
+  build_shape_of(S.build_shape, &st->build_warps, &st->build_batch);
+  for (int k = 0; k < BUILD_SHAPES; ++k) st->build_ms[k] = s->build_ms[k];
   if (S.flag_n) CK(sync_copy(s, &st->fp64_atoms, S.flag_n, sizeof(int), cudaMemcpyDeviceToHost));
   if (S.stiff_n) CK(sync_copy(s, &st->fp64_bonds, S.stiff_n, sizeof(int), cudaMemcpyDeviceToHost));
   st->error_bits = bits;

@@ -118,6 +118,7 @@ struct DevState {
   int* cg_hist = nullptr;       // solutions held in q, cqh1, cqh2 (0..3)
   // control
   int* flag_rebuild = nullptr;
+  int* flag_one = nullptr;      // a flag that stays 1 (list-build tuning)
   long long* rebuild_count = nullptr;
   int* maxcnt = nullptr;        // [3] at the last rebuild: max ncov, max count of the rest, max nall
   unsigned* err = nullptr;
@@ -130,6 +131,9 @@ struct DevState {
   int mv_batch = 16;            // list entries in flight per thread in the CG matrix pass (tuned)
   int asm_batch = 8;            // list entries in flight per thread in the assembly (tuned)
   int gather_batch = 8;         // list entries in flight per thread in the charge-force gather (tuned)
+  int cov_lanes = 8;            // lanes per atom in the covalent passes (4, 8 or 16; tuned)
+  int cov_lanes_ok = 7;         // lane counts whose blocks fit shared memory (bits: 4, 8, 16)
+  int build_shape = 3;          // list-build shape: index into the (warps, stencil batch) table (tuned)
   // charge-CG preconditioner: block-Jacobi on 32-atom blocks (1) or Jacobi (0)
   int precond = 1;
   void* binv = nullptr;         // Real[ceil(N/32)][32][32]: block inverses, column-major per block
@@ -166,7 +170,7 @@ template <class R> void launch_kick_drift(const DevState& S, const TypeParams& T
                                           cudaStream_t st);
 void launch_zero_acc(const DevState& S, cudaStream_t st);
 void launch_nh_end(const DevState& S, double dt, cudaStream_t st);
-template <class R> cudaError_t setup_pot(int cap_cov);
+template <class R> cudaError_t setup_pot(int cap_cov, int* lanes_ok);
 template <class R> void launch_copy_q(const DevState& S, cudaStream_t st);
 // launch shape for kernels with one thread per atom: resident blocks only,
 // each block a contiguous chunk of atoms (a multiple of its size)
@@ -176,6 +180,15 @@ template <class R>
 cudaError_t tune_assemble(DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st, float* ms_out);
 template <class R>
 cudaError_t tune_gather(DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st, float* ms_out);
+// List-build shapes (csrc/nbr.cu): warps per block x stencil cells per batch
+#define BUILD_SHAPES 6
+int build_shape_index(int warps, int batch);   // -1 if not a shape
+void build_shape_of(int k, int* warps, int* batch);
+template <class R>
+cudaError_t tune_build(DevState& S, const PotParams<R>& P, const int* one, cudaStream_t st, float* ms_out);
+template <class R>
+cudaError_t tune_cov(DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st, float* ms_out,
+                     bool fast);
 // Parameter gradient of the energy (csrc/grad.cu), in FP32 (fp32) or FP64
 // arithmetic with FP64 sums. grad[0..143] = sum_r wval_r dE_r/dtheta at the
 // current positions and charges. With a direction dir ([N,3], positions)

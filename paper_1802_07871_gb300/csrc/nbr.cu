@@ -163,9 +163,11 @@ __device__ inline int wrap_cell(int c, int n) {
 // [covalent | core | shell] without moving anything here. maxcnt receives
 // the largest covalent count, the largest count of the rest (the list needs
 // cap_cov + that) and the largest total.
-#define BC 128   // stencil cells per batch
-#define BW 4     // warps per block
-template <class R>
+//
+// BW (warps per block) and BC (stencil cells per batch) only change how the
+// cells are spread over blocks and how the stencil is chunked; every shape
+// writes the same rows (see tune_build).
+template <class R, int BW, int BC>
 __global__ void __launch_bounds__(BW * 32)
     k_build(int C, const typename Vec4<R>::T* __restrict__ u, const int* __restrict__ cell_rep,
             const RepInfo* __restrict__ reps, const int* __restrict__ cell_start,
@@ -420,6 +422,78 @@ __global__ void k_finish_rebuild(int* __restrict__ flag, long long* __restrict__
 }
 
 // ---------------------------------------------------------------- launcher
+// The list-build shapes (warps per block, stencil cells per batch), indexed
+// by DevState::build_shape.
+static const int kBuildShapes[BUILD_SHAPES][2] = {{2, 64}, {2, 128}, {4, 64}, {4, 128}, {8, 64}, {8, 128}};
+
+template <class R, int BW, int BC>
+static void launch_build_s(const DevState& S, const PotParams<R>& P, const int* f, cudaStream_t st) {
+  // about 32 warps resident per SM at every shape
+  const int gb = S.nsm * (32 / BW);
+  k_build<R, BW, BC><<<gb, BW * 32, 0, st>>>(S.ncells, (const typename Vec4<R>::T*)S.u, S.cell_rep, S.reps,
+                                             S.cell_start, S.cell_count, S.cell_atoms, P, S.cap_cov, S.cap_all,
+                                             S.lst, S.ncov, S.nfix, S.nall, S.maxcnt, S.err, f);
+}
+
+template <class R>
+static void launch_build(const DevState& S, const PotParams<R>& P, int shape, const int* f, cudaStream_t st) {
+  switch (shape) {
+    case 0: launch_build_s<R, 2, 64>(S, P, f, st); break;
+    case 1: launch_build_s<R, 2, 128>(S, P, f, st); break;
+    case 2: launch_build_s<R, 4, 64>(S, P, f, st); break;
+    case 4: launch_build_s<R, 8, 64>(S, P, f, st); break;
+    case 5: launch_build_s<R, 8, 128>(S, P, f, st); break;
+    default: launch_build_s<R, 4, 128>(S, P, f, st); break;
+  }
+}
+
+int build_shape_index(int warps, int batch) {
+  for (int k = 0; k < BUILD_SHAPES; ++k)
+    if (kBuildShapes[k][0] == warps && kBuildShapes[k][1] == batch) return k;
+  return -1;
+}
+
+void build_shape_of(int k, int* warps, int* batch) {
+  if (k < 0 || k >= BUILD_SHAPES) k = 3;
+  *warps = kBuildShapes[k][0];
+  *batch = kBuildShapes[k][1];
+}
+
+// List-build shape, on the lists just built: each shape rebuilds the rows
+// from the same cells and positions (the same rows again, so nothing needs
+// restoring), one warm-up and two timed launches under an always-set flag;
+// the fastest is kept. The rebuild flag itself is untouched.
+template <class R>
+cudaError_t tune_build(DevState& S, const PotParams<R>& P, const int* one, cudaStream_t st, float* ms_out) {
+  if (S.N == 0) return cudaSuccess;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  int pick = S.build_shape;
+  float best = 0.f;
+  for (int k = 0; k < BUILD_SHAPES && e == cudaSuccess; ++k) {
+    launch_build<R>(S, P, k, one, st);
+    cudaEventRecord(e0, st);
+    launch_build<R>(S, P, k, one, st);
+    launch_build<R>(S, P, k, one, st);
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    ms *= 0.5f;
+    if (ms_out) ms_out[k] = ms;
+    if (e == cudaSuccess && (best == 0.f || ms < best)) { best = ms; pick = k; }
+  }
+  S.build_shape = pick;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+template cudaError_t tune_build<float>(DevState&, const PotParams<float>&, const int*, cudaStream_t, float*);
+template cudaError_t tune_build<double>(DevState&, const PotParams<double>&, const int*, cudaStream_t, float*);
+
 template <class R>
 void launch_rebuild(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   int N = S.N;
@@ -437,10 +511,7 @@ void launch_rebuild(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   k_scatter<<<(N + tb - 1) / tb, tb, 0, st>>>(N, S.cell4, S.cell_start, S.cell_fill, S.cell_atoms, f);
   k_sort_cells<<<(C + tb - 1) / tb, tb, 0, st>>>(C, S.cell_start, S.cell_count, S.cell_atoms, f);
   // grid-strided: when no rebuild is due these launches return at once
-  int gb = S.nsm * 8;
-  k_build<R><<<gb, BW * 32, 0, st>>>(C, (const typename Vec4<R>::T*)S.u, S.cell_rep, S.reps, S.cell_start,
-                                     S.cell_count, S.cell_atoms, P, S.cap_cov, S.cap_all, S.lst, S.ncov, S.nfix,
-                                     S.nall, S.maxcnt, S.err, f);
+  launch_build<R>(S, P, S.build_shape, f, st);
   k_list_transpose<<<S.nsm * 8, 256, 0, st>>>(N, S.cap_cov, S.cap_all, S.ld, S.lst, S.ncov, S.nfix, S.nall,
                                               S.nl, f);
   k_rev<<<S.nsm * 4, tb, 0, st>>>(N, S.cap_cov, S.ld, S.nl, S.ncov, S.rev, S.err, f);

@@ -21,7 +21,9 @@
 
 namespace ct {
 
-#define GRP 8           // lanes per atom in the covalent kernels
+// Covalent kernels: blocks of CB threads, G lanes per atom (G = 4, 8 or 16,
+// tuned on the live lists by tune_cov), CB / G atoms per block.
+#define CB 128
 // Bonds whose repulsive radial derivative lambda1 * A e^(-lambda1 r) exceeds
 // this (eV/A) get their pair term in FP64 on the FP32 path (queued by the
 // bond pass, evaluated by k_stiff): there the repulsive and attractive
@@ -31,12 +33,12 @@ namespace ct {
 // compressed adatom bonds reach 40-80 eV/A.
 #define STIFF_PAIR 35.0f
 // RMS force (eV/A) below which a replica's next evaluation takes the
-// accurate mode (see k_bond): at the largest FP32 force error measured on
-// ill-conditioned atoms (about 7e-5 eV/A, adatoms in the taper of a Si-C
-// pair or in compressed C-C pairs) a 1e-4 bar relative to the RMS force
-// holds without the FP64 pass from about 0.7 eV/A on.
+// accurate mode (see k_bond): outside it, with the cutoffs of taper bonds
+// from FP64 positions (cutoff_fp64), the largest FP32 force error measured
+// on hot slabs (2000-2500 K, after 50-400 steps) is 1.4e-5 of the RMS force
+// (about 2.5e-5 eV/A), so a 1e-4 bar relative to the RMS force holds from
+// about 0.25 eV/A on; the threshold keeps a margin of four.
 #define ACC_RMS 1.0
-#define APB 16          // atoms per block in the covalent kernels
 
 template <class R>
 __device__ inline void bond_order7(R z1, R z2, int pb, const PotParams<R>& P, R& b, R& db1, R& db2) {
@@ -62,43 +64,82 @@ __device__ inline void rel_vec(const typename Vec4<R>::T& ui, const typename Vec
   rz = (uj.z - ui.z) + (R)dz * hz;
 }
 
+// FP64 taper limits of the four pair types, for the FP32 path's cutoff of
+// bonds inside the taper (see cutoff_fp64).
+struct Taper64 {
+  double R[4], S[4];
+};
+
+// Cutoff and its derivative of bond (i, j, cell code cd) of the FP32 path
+// from the FP64 master positions: the bond length in FP64 (u64 - u64 +
+// shift, the layout of u), its place in the taper in FP64, the cosine
+// factors in FP32. The tapers are a few tenths of an angstrom wide, so the
+// cutoff's curvature (up to pi^2 / (2 (S - R)^2) per A^2) turns the FP32
+// rounding of a cell-local position (about 2e-7 A) into force errors of
+// 1e-4 to 3e-4 eV/A on atoms with a bond in the taper; from the FP64 place
+// in the taper the cutoff is exact to FP32 rounding of its own value.
+__device__ inline void cutoff_fp64(int i, int j, int cd, int pb, const double* __restrict__ x,
+                                   const int4* __restrict__ cell4, const RepInfo& ri, const Taper64& TP,
+                                   float pi_SR, float& fc, float& dfc) {
+  const int4 ci = cell4[i], cj = cell4[j];
+  int dx, dy, dz;
+  unpack_code(cd, dx, dy, dz);
+  const double rx = ((x[3 * j] - cj.x * ri.hc[0]) - (x[3 * i] - ci.x * ri.hc[0])) + dx * ri.hc[0];
+  const double ry = ((x[3 * j + 1] - cj.y * ri.hc[1]) - (x[3 * i + 1] - ci.y * ri.hc[1])) + dy * ri.hc[1];
+  const double rz = ((x[3 * j + 2] - cj.z * ri.hc[2]) - (x[3 * i + 2] - ci.z * ri.hc[2])) + dz * ri.hc[2];
+  const double r = sqrt(rx * rx + ry * ry + rz * rz);
+  if (r <= TP.R[pb]) { fc = 1.f; dfc = 0.f; return; }
+  if (r >= TP.S[pb]) { fc = 0.f; dfc = 0.f; return; }
+  const float h = (float)(0.5 * (r - TP.R[pb]) / (TP.S[pb] - TP.R[pb]));
+  const float c = ct_cospi<float>(h), sn = ct_sinpi<float>(h);
+  fc = c * c;
+  dfc = -pi_SR * sn * c;
+}
+
+// FP32 path: bonds whose FP32 length lies within this of a taper end take
+// the FP64 cutoff (the FP32 length is off by far less).
+#define TAPER_MARGIN 1e-4f
+
 // ---------------------------------------------------------------- bond pass
 //
-// Precision by need (FP32 path). A replica is in the accurate mode when the
-// RMS force of its previous evaluation is below ACC_RMS (and on its first
-// evaluation after positions or parameters were set, when there is none).
-// Then every bond's pair term is queued for k_stiff (FP64), and every atom
-// with a bond in the cutoff's taper (R < r < S) or a compressed bond (the
-// STIFF_PAIR criterion) is queued as a whole: k_bond<double> and
-// k_cov_force<double, float> recompute its bond orders and force slots in
-// FP64 from the master positions and overwrite the FP32 results. The force
-// of such an atom moves by about 1e-4 eV/A under a position change of the
-// size of FP32 rounding (3e-7 A), above the error a 1e-4 bar relative to a
-// small RMS force allows; with the RMS force above ACC_RMS the FP32 error
-// is far inside the bar and nothing is queued (hot MD pays nothing).
-// qlist/qn: when given, block b takes the queued atoms qlist[b*APB ..], the
+// Precision by need (FP32 path). Every bond in a cutoff's taper takes its
+// cutoff from the FP64 positions (cutoff_fp64): without that, hot MD (RMS
+// force near 1.7 eV/A) put its worst atoms at 2e-4 of the RMS force. A
+// replica is in the accurate mode when the RMS force of its previous
+// evaluation is below ACC_RMS (and on its first evaluation after positions
+// or parameters were set, when there is none). Then every bond's pair term
+// is queued for k_stiff (FP64), and every atom with a bond in the taper
+// (R < r < S) or a compressed bond (the STIFF_PAIR criterion) is queued as
+// a whole: k_bond<double> and k_cov_force<double, float> recompute its
+// bond orders and force slots in FP64 from the master positions and
+// overwrite the FP32 results: the FP32 rounding of such an atom's bonds
+// (3e-7 A) moves its force by more than a 1e-4 bar relative to a small RMS
+// force allows.
+// qlist/qn: when given, block b takes the queued atoms qlist[b*CB/G ..], the
 // rest of the grid exits at once.
-template <class R>
-__global__ void __launch_bounds__(APB * GRP)
+template <class R, int G>
+__global__ void __launch_bounds__(CB)
 k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
        const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
         const int* __restrict__ ncov, PotParams<R> P,
        typename Vec4<R>::T* __restrict__ bo, int* __restrict__ stiff_n, int* __restrict__ stiff_q,
        const double* __restrict__ f2_prev, int* __restrict__ flag_n, int* __restrict__ flag_q,
-       const int* __restrict__ qlist, const int* __restrict__ qn) {
+       const int* __restrict__ qlist, const int* __restrict__ qn,
+       const double* __restrict__ x64, const int4* __restrict__ cell4, Taper64 TP) {
   using R4 = typename Vec4<R>::T;
+  constexpr int APB_ = CB / G;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   __shared__ int s_nstiff, s_base, s_nflag, s_fbase;
   if (threadIdx.x == 0) { s_nstiff = 0; s_nflag = 0; }
-  int g = threadIdx.x / GRP, l = threadIdx.x % GRP;
+  int g = threadIdx.x / G, l = threadIdx.x % G;
   R4* s_u = reinterpret_cast<R4*>(smem_raw) + (size_t)g * cap_cov;               // (ux,uy,uz,r)
-  R* s_fc = reinterpret_cast<R*>(reinterpret_cast<R4*>(smem_raw) + (size_t)APB * cap_cov) + (size_t)g * cap_cov;
-  int* s_t = reinterpret_cast<int*>(reinterpret_cast<R*>(reinterpret_cast<R4*>(smem_raw) + (size_t)APB * cap_cov)
-                                    + (size_t)APB * cap_cov) + (size_t)g * cap_cov;
-  int i = blockIdx.x * APB + g;
+  R* s_fc = reinterpret_cast<R*>(reinterpret_cast<R4*>(smem_raw) + (size_t)APB_ * cap_cov) + (size_t)g * cap_cov;
+  int* s_t = reinterpret_cast<int*>(reinterpret_cast<R*>(reinterpret_cast<R4*>(smem_raw) + (size_t)APB_ * cap_cov)
+                                    + (size_t)APB_ * cap_cov) + (size_t)g * cap_cov;
+  int i = blockIdx.x * APB_ + g;
   if (qlist) {
     const int nq = *qn;
-    if (blockIdx.x * APB >= nq) return;   // (uniform over the block)
+    if (blockIdx.x * APB_ >= nq) return;   // (uniform over the block)
     i = i < nq ? qlist[i] : N;
   }
   bool live = i < N;
@@ -115,16 +156,22 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
       acc = f2_prev[rid] < 3.0 * (double)ri.natoms * (double)(ACC_RMS * ACC_RMS);
     R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
     if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
-    for (int e = l; e < nc; e += GRP) {
-      int j = nl[(size_t)e * ld + i].x;
+    for (int e = l; e < nc; e += G) {
+      const int2 jcd = nl[(size_t)e * ld + i];
+      const int j = jcd.x;
       R4 uj = u[j];
       R rx, ry, rz;
-      rel_vec<R>(ui, uj, nl[(size_t)e * ld + i].y, hx, hy, hz, rx, ry, rz);
+      rel_vec<R>(ui, uj, jcd.y, hx, hy, hz, rx, ry, rz);
       R r = ct_sqrt<R>(rx * rx + ry * ry + rz * rz);
       int tj = (int)uj.w;
       int pb = ti * 2 + tj;
       R fc, dfc;
       cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
+      if (sizeof(R) == 4 && x64 && r > P.Rin[pb] - R(TAPER_MARGIN) && r < P.Sout[pb] + R(TAPER_MARGIN)) {
+        float f, df;
+        cutoff_fp64(i, j, jcd.y, pb, x64, cell4, ri, TP, (float)P.pi_SR[pb], f, df);
+        fc = (R)f;
+      }
       R4 w;
       w.x = rx; w.y = ry; w.z = rz; w.w = r;
       s_u[e] = w;
@@ -134,7 +181,7 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
   }
   __syncthreads();
   int my_stiff = 0, my_flag = 0;
-  for (int e = l; live && e < nc; e += GRP) {
+  for (int e = l; live && e < nc; e += G) {
     R4 ue = s_u[e];
     int tj = s_t[e];
     int pb = ti * 2 + tj;
@@ -188,7 +235,7 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
   // this atom is queued for the FP64 pass when any lane of its group
   // flagged it (every lane of the warp takes part in the shuffles)
 #pragma unroll
-  for (int o = GRP / 2; o > 0; o >>= 1) my_flag |= __shfl_xor_sync(CT_FULL, my_flag, o, GRP);
+  for (int o = G / 2; o > 0; o >>= 1) my_flag |= __shfl_xor_sync(CT_FULL, my_flag, o, G);
   // append this block's stiff bonds and flagged atoms to their queues: one
   // global atomic per block and queue
   int off = my_stiff ? atomicAdd(&s_nstiff, my_stiff) : 0;
@@ -201,7 +248,7 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
   __syncthreads();
   if (my_stiff) {
     int pos = s_base + off;
-    for (int e = l; e < nc; e += GRP)
+    for (int e = l; e < nc; e += G)
       if (bo[(size_t)i * cap_cov + e].w != R(0)) stiff_q[pos++] = i * cap_cov + e;
   }
   if (my_flag && l == 0) flag_q[s_fbase + foff] = i;
@@ -409,33 +456,35 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------- covalent forces
 // O is the type of the stored slots: R, or float for the FP64 pass over the
 // queued atoms of the FP32 path (qlist/qn as in k_bond).
-template <class R, class O>
-__global__ void __launch_bounds__(APB * GRP)
+template <class R, class O, int G>
+__global__ void __launch_bounds__(CB)
 k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
             const int* __restrict__ rep, const RepInfo* __restrict__ reps,
             const int2* __restrict__ nl,  const int* __restrict__ ncov,
             const typename Vec4<R>::T* __restrict__ bo, const double* __restrict__ q,
             const R* __restrict__ qr, PotParams<R> P, TypeParams T, typename Vec4<O>::T* __restrict__ gslot,
             double* __restrict__ e_atom, const void* __restrict__ stiff_pe,
-            const int* __restrict__ qlist, const int* __restrict__ qn) {
+            const int* __restrict__ qlist, const int* __restrict__ qn,
+            const double* __restrict__ x64, const int4* __restrict__ cell4, Taper64 TP) {
   using R4 = typename Vec4<R>::T;
   using R2 = typename Vec2<R>::T;
+  constexpr int APB_ = CB / G;
   extern __shared__ __align__(32) unsigned char smem_raw[];
-  int g = threadIdx.x / GRP, l = threadIdx.x % GRP;
-  // layout: R4 u[APB][cap] | R2 D[APB][cap] | R fc | R dfc | R pair dE/dr | int type
+  int g = threadIdx.x / G, l = threadIdx.x % G;
+  // layout: R4 u[APB_][cap] | R2 D[APB_][cap] | R fc | R dfc | R pair dE/dr | int type
   R4* s_u = reinterpret_cast<R4*>(smem_raw);
-  R2* s_D = reinterpret_cast<R2*>(s_u + (size_t)APB * cap_cov);
-  R* s_fc = reinterpret_cast<R*>(s_D + (size_t)APB * cap_cov);
-  R* s_dfc = s_fc + (size_t)APB * cap_cov;
-  R* s_pd = s_dfc + (size_t)APB * cap_cov;
-  int* s_t = reinterpret_cast<int*>(s_pd + (size_t)APB * cap_cov);
+  R2* s_D = reinterpret_cast<R2*>(s_u + (size_t)APB_ * cap_cov);
+  R* s_fc = reinterpret_cast<R*>(s_D + (size_t)APB_ * cap_cov);
+  R* s_dfc = s_fc + (size_t)APB_ * cap_cov;
+  R* s_pd = s_dfc + (size_t)APB_ * cap_cov;
+  int* s_t = reinterpret_cast<int*>(s_pd + (size_t)APB_ * cap_cov);
   s_u += (size_t)g * cap_cov; s_D += (size_t)g * cap_cov; s_fc += (size_t)g * cap_cov;
   s_dfc += (size_t)g * cap_cov; s_pd += (size_t)g * cap_cov; s_t += (size_t)g * cap_cov;
 
-  int i = blockIdx.x * APB + g;
+  int i = blockIdx.x * APB_ + g;
   if (qlist) {
     const int nq = *qn;
-    if (blockIdx.x * APB >= nq) return;   // (uniform over the block)
+    if (blockIdx.x * APB_ >= nq) return;   // (uniform over the block)
     i = i < nq ? qlist[i] : N;
   }
   bool live = i < N;
@@ -450,7 +499,7 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
     R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
     if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
     R qi = qr[i];
-    for (int e = l; e < nc; e += GRP) {
+    for (int e = l; e < nc; e += G) {
       size_t idx = (size_t)e * ld + i;
       int j = nl[idx].x;
       R4 uj = u[j];
@@ -461,6 +510,12 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
       int pb = ti * 2 + tj;
       R fc, dfc;
       cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
+      if (sizeof(R) == 4 && x64 && r > P.Rin[pb] - R(TAPER_MARGIN) && r < P.Sout[pb] + R(TAPER_MARGIN)) {
+        float f, df;
+        cutoff_fp64(i, j, nl[idx].y, pb, x64, cell4, ri, TP, (float)P.pi_SR[pb], f, df);
+        fc = (R)f;
+        dfc = (R)df;
+      }
       R2 D;
       D.x = R(0); D.y = R(0);
       R pd = R(0);
@@ -496,7 +551,7 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
   }
   __syncwarp();
   if (live) {
-    for (int e = l; e < nc; e += GRP) {
+    for (int e = l; e < nc; e += G) {
       R4 ux = s_u[e];
       R rx = ux.w;
       R fcx = s_fc[e];
@@ -569,10 +624,10 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
   // per-atom energy: covalent part + self energy (all lanes take part)
   R es = eacc.s, ec = eacc.c;
 #pragma unroll
-  for (int o = GRP / 2; o > 0; o >>= 1) {
-    es += __shfl_xor_sync(CT_FULL, es, o, GRP);
-    ec += __shfl_xor_sync(CT_FULL, ec, o, GRP);
-    estiff += __shfl_xor_sync(CT_FULL, estiff, o, GRP);
+  for (int o = G / 2; o > 0; o >>= 1) {
+    es += __shfl_xor_sync(CT_FULL, es, o, G);
+    ec += __shfl_xor_sync(CT_FULL, ec, o, G);
+    estiff += __shfl_xor_sync(CT_FULL, estiff, o, G);
   }
   if (live && l == 0) {
     double qd = q[i];
@@ -755,30 +810,49 @@ int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk) {
   return (int)(((long long)N + ch - 1) / ch);
 }
 
-template <class R> static size_t bond_smem(int cap) {
-  return (size_t)APB * cap * (sizeof(typename Vec4<R>::T) + sizeof(R) + sizeof(int));
+static Taper64 taper64(const DevState& S) {
+  Taper64 t;
+  for (int k = 0; k < 4; ++k) {
+    t.R[k] = S.Pd->Rin[k];
+    t.S[k] = S.Pd->Sout[k];
+  }
+  return t;
 }
-template <class R> static size_t force_smem(int cap) {
-  return (size_t)APB * cap * (sizeof(typename Vec4<R>::T) + sizeof(typename Vec2<R>::T) + 3 * sizeof(R) + sizeof(int));
+
+template <class R> static size_t bond_smem(int cap, int G) {
+  return (size_t)(CB / G) * cap * (sizeof(typename Vec4<R>::T) + sizeof(R) + sizeof(int));
+}
+template <class R> static size_t force_smem(int cap, int G) {
+  return (size_t)(CB / G) * cap *
+         (sizeof(typename Vec4<R>::T) + sizeof(typename Vec2<R>::T) + 3 * sizeof(R) + sizeof(int));
+}
+
+template <class R, int G>
+static void launch_bond_g(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
+  size_t sm = bond_smem<R>(S.cap_cov, G);
+  const int gb = (S.N + CB / G - 1) / (CB / G);
+  const Taper64 tp = taper64(S);
+  k_bond<R, G><<<gb, CB, sm, st>>>(
+      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
+      S.ncov, P, (typename Vec4<R>::T*)S.bo, S.stiff_n, S.stiff_q, S.f2_prev, S.flag_n, S.flag_q,
+      nullptr, nullptr, sizeof(R) == 4 ? S.x : nullptr, S.cell4, tp);
+  if constexpr (sizeof(R) == 4) {
+    // the queued atoms in FP64: master-precision offsets, then their bond orders
+    k_fill_u64<<<S.nsm * 4, 256, 0, st>>>(S.N, S.flag_n, S.x, S.cell4, S.type, S.rep, S.reps,
+                                         (double4_32a*)S.u64);
+    k_bond<double, G><<<gb, CB, bond_smem<double>(S.cap_cov, G), st>>>(
+        S.N, S.cap_cov, S.ld, (const double4_32a*)S.u64, S.rep, S.reps, S.nl, S.ncov, *S.Pd,
+        (double4_32a*)S.bo64, nullptr, nullptr, nullptr, nullptr, nullptr, S.flag_q, S.flag_n, nullptr, nullptr,
+        tp);
+  }
 }
 
 template <class R>
 void launch_bond(const DevState& S, const PotParams<R>& P, cudaStream_t st) {
   if (S.N == 0) return;
-  size_t sm = bond_smem<R>(S.cap_cov);
-  const int gb = (S.N + APB - 1) / APB;
-  k_bond<R><<<gb, APB * GRP, sm, st>>>(
-      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
-      S.ncov, P, (typename Vec4<R>::T*)S.bo, S.stiff_n, S.stiff_q, S.f2_prev, S.flag_n, S.flag_q,
-      nullptr, nullptr);
-  if constexpr (sizeof(R) == 4) {
-    // the queued atoms in FP64: master-precision offsets, then their bond orders
-    k_fill_u64<<<S.nsm * 4, 256, 0, st>>>(S.N, S.flag_n, S.x, S.cell4, S.type, S.rep, S.reps,
-                                         (double4_32a*)S.u64);
-    k_bond<double><<<gb, APB * GRP, bond_smem<double>(S.cap_cov), st>>>(
-        S.N, S.cap_cov, S.ld, (const double4_32a*)S.u64, S.rep, S.reps, S.nl, S.ncov, *S.Pd,
-        (double4_32a*)S.bo64, nullptr, nullptr, nullptr, nullptr, nullptr, S.flag_q, S.flag_n);
-  }
+  if (S.cov_lanes == 4) launch_bond_g<R, 4>(S, P, st);
+  else if (S.cov_lanes == 16) launch_bond_g<R, 16>(S, P, st);
+  else launch_bond_g<R, 8>(S, P, st);
 }
 
 template <class R>
@@ -794,6 +868,24 @@ void launch_assemble(const DevState& S, const PotParams<R>& P, const TypeParams&
 #undef ASM_ARGS
 }
 
+template <class R, int G>
+static void launch_cov_force_g(const DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st) {
+  size_t sm = force_smem<R>(S.cap_cov, G);
+  const int gb = (S.N + CB / G - 1) / (CB / G);
+  const Taper64 tp = taper64(S);
+  k_cov_force<R, R, G><<<gb, CB, sm, st>>>(
+      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl, S.ncov,
+      (const typename Vec4<R>::T*)S.bo, S.q, (const R*)S.qr, P, T, (typename Vec4<R>::T*)S.gslot, S.e_atom,
+      S.stiff_pe, nullptr, nullptr, sizeof(R) == 4 ? S.x : nullptr, S.cell4, tp);
+  if constexpr (sizeof(R) == 4) {
+    // the queued atoms' slots and covalent energies again, in FP64
+    k_cov_force<double, float, G><<<gb, CB, force_smem<double>(S.cap_cov, G), st>>>(
+        S.N, S.cap_cov, S.ld, (const double4_32a*)S.u64, S.rep, S.reps, S.nl, S.ncov,
+        (const double4_32a*)S.bo64, S.q, S.q, *S.Pd, T, (float4*)S.gslot, S.e_atom, nullptr, S.flag_q, S.flag_n,
+        nullptr, nullptr, tp);
+  }
+}
+
 template <class R>
 void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st) {
   if (S.N == 0) return;
@@ -802,18 +894,9 @@ void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams
     k_stiff<<<S.nsm * 4, 256, 0, st>>>(S.cap_cov, S.ld, S.stiff_n, S.stiff_q, S.nl, S.rep, S.reps, S.x,
                                        S.cell4, S.type, (const float4*)S.bo, S.q, P, (double2*)S.stiff_pe);
   }
-  size_t sm = force_smem<R>(S.cap_cov);
-  const int gb = (S.N + APB - 1) / APB;
-  k_cov_force<R, R><<<gb, APB * GRP, sm, st>>>(
-      S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl, S.ncov,
-      (const typename Vec4<R>::T*)S.bo, S.q, (const R*)S.qr, P, T, (typename Vec4<R>::T*)S.gslot, S.e_atom,
-      S.stiff_pe, nullptr, nullptr);
-  if constexpr (sizeof(R) == 4) {
-    // the queued atoms' slots and covalent energies again, in FP64
-    k_cov_force<double, float><<<gb, APB * GRP, force_smem<double>(S.cap_cov), st>>>(
-        S.N, S.cap_cov, S.ld, (const double4_32a*)S.u64, S.rep, S.reps, S.nl, S.ncov,
-        (const double4_32a*)S.bo64, S.q, S.q, *S.Pd, T, (float4*)S.gslot, S.e_atom, nullptr, S.flag_q, S.flag_n);
-  }
+  if (S.cov_lanes == 4) launch_cov_force_g<R, 4>(S, P, T, st);
+  else if (S.cov_lanes == 16) launch_cov_force_g<R, 16>(S, P, T, st);
+  else launch_cov_force_g<R, 8>(S, P, T, st);
 }
 
 template <class R>
@@ -842,25 +925,47 @@ void launch_forces(const DevState& S, const PotParams<R>& P, const TypeParams& T
   launch_coul_gather<R>(S, P, T, kick, half_dt, st);
 }
 
-// Allow the dynamic shared memory the covalent kernels need for cap_cov
-// entries per atom (call before launching or capturing them).
-template <class R>
-cudaError_t setup_pot(int cap_cov) {
-  cudaError_t e = cudaFuncSetAttribute(k_bond<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)bond_smem<R>(cap_cov));
+template <class R, int G>
+static cudaError_t setup_pot_g(int cap_cov) {
+  cudaError_t e = cudaFuncSetAttribute(k_bond<R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)bond_smem<R>(cap_cov, G));
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_cov_force<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)force_smem<R>(cap_cov));
+  e = cudaFuncSetAttribute(k_cov_force<R, R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)force_smem<R>(cap_cov, G));
   if (e != cudaSuccess || sizeof(R) == 8) return e;
   // the FP32 path's FP64 pass over queued atoms
-  e = cudaFuncSetAttribute(k_bond<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)bond_smem<double>(cap_cov));
+  e = cudaFuncSetAttribute(k_bond<double, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bond_smem<double>(cap_cov, G));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_cov_force<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)force_smem<double>(cap_cov));
+  return cudaFuncSetAttribute(k_cov_force<double, float, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)force_smem<double>(cap_cov, G));
 }
-template cudaError_t setup_pot<float>(int);
-template cudaError_t setup_pot<double>(int);
+
+// Allow the dynamic shared memory the covalent kernels need for cap_cov
+// entries per atom (call before launching or capturing them), at each lane
+// count whose blocks fit the per-block limit: fewer lanes per atom stage
+// more atoms per block. *lanes_ok gets a bit per usable count (1: 4 lanes,
+// 2: 8, 4: 16); 16 lanes must fit.
+template <class R>
+cudaError_t setup_pot(int cap_cov, int* lanes_ok) {
+  int dev = 0, lim = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  auto fits = [&](int G) {
+    size_t need = std::max(force_smem<R>(cap_cov, G), bond_smem<R>(cap_cov, G));
+    if (sizeof(R) == 4) need = std::max(need, force_smem<double>(cap_cov, G));
+    return need <= (size_t)lim;
+  };
+  int ok = 0;
+  if (fits(4)) { e = setup_pot_g<R, 4>(cap_cov); ok |= 1; }
+  if (e == cudaSuccess && fits(8)) { e = setup_pot_g<R, 8>(cap_cov); ok |= 2; }
+  if (e == cudaSuccess) { e = setup_pot_g<R, 16>(cap_cov); ok |= 4; }
+  if (lanes_ok) *lanes_ok = ok;
+  return e;
+}
+template cudaError_t setup_pot<float>(int, int*);
+template cudaError_t setup_pot<double>(int, int*);
 
 template void launch_bond<float>(const DevState&, const PotParams<float>&, cudaStream_t);
 template void launch_bond<double>(const DevState&, const PotParams<double>&, cudaStream_t);
@@ -908,6 +1013,106 @@ cudaError_t tune_assemble(DevState& S, const PotParams<R>& P, const TypeParams& 
 template cudaError_t tune_assemble<float>(DevState&, const PotParams<float>&, const TypeParams&, cudaStream_t, float*);
 template cudaError_t tune_assemble<double>(DevState&, const PotParams<double>&, const TypeParams&, cudaStream_t,
                                            float*);
+
+// Streams up to 320 MB (about 2.5 L2 capacities) of the list-build scratch
+// through L2 so that the next timed launch meets the cold cache it meets in
+// a step (the scratch holds nothing between builds: one word per block is
+// stored back into it only so that the loads are kept).
+__global__ void k_l2_evict(const uint4* buf, size_t n, uint4* sink) {
+  unsigned acc = 0;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    uint4 v = __ldcg(buf + k);
+    acc ^= v.x ^ v.y ^ v.z ^ v.w;
+  }
+  acc = __reduce_xor_sync(CT_FULL, acc);
+  if (threadIdx.x == 0 && blockIdx.x < n) sink[blockIdx.x] = make_uint4(acc, 0, 0, 0);
+}
+
+static void evict_l2(const DevState& S, cudaStream_t st) {
+  size_t n = (size_t)std::max(S.N, 1) * S.cap_all * sizeof(int2) / sizeof(uint4);
+  n = std::min(n, (size_t)320 << 20 >> 4);
+  if (n == 0 || S.lst == nullptr) return;
+  k_l2_evict<<<S.nsm * 8, 256, 0, st>>>(reinterpret_cast<const uint4*>(S.lst), n, reinterpret_cast<uint4*>(S.lst));
+}
+
+// Lanes per atom in the covalent passes (4, 8 or 16; CB / G atoms per
+// block): on the state of a completed evaluation, each lane count runs the
+// bond pass (its queues emptied first, so repeated runs do not grow them)
+// and the covalent force pass, three times each, the first a warm-up, each
+// pass timed after an L2 eviction (in a step the matrix passes between them
+// leave no covalent data in L2). The count with the least bond + force
+// time is kept, and both passes, then the charge-force gather (no kick:
+// forces, energies and sums as the evaluation left them), run once more in
+// it. With fast set the timed runs take the FP32 path's fast mode (no
+// previous force sums: the accurate mode of a first evaluation queues every
+// pair term for FP64, a mix that MD steps above the RMS-force threshold
+// never see); otherwise, and in the final run, the mode of the evaluation.
+// Every count computes every bond alike (a lane owns whole bonds), so the
+// results do not depend on the choice.
+template <class R>
+cudaError_t tune_cov(DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st, float* ms_out,
+                     bool fast) {
+  if (S.N == 0) return cudaSuccess;
+  const int lanes[3] = {4, 8, 16};
+  const int start = S.cov_lanes;
+  cudaEvent_t ev[3];
+  cudaError_t e = cudaSuccess;
+  int made = 0;
+  for (; made < 3 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+  if (e != cudaSuccess) {
+    for (int k = 0; k < made - 1; ++k) cudaEventDestroy(ev[k]);
+    return e;
+  }
+  auto clear_queues = [&]() {
+    cudaMemsetAsync(S.stiff_n, 0, sizeof(int), st);
+    if (S.flag_n) cudaMemsetAsync(S.flag_n, 0, sizeof(int), st);
+  };
+  float t[3] = {0.f, 0.f, 0.f};
+  DevState F = S;
+  if (fast) F.f2_prev = nullptr;   // the fast mode
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    if (!(S.cov_lanes_ok & (1 << k))) continue;
+    F.cov_lanes = lanes[k];
+    float sum = 0.f;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      clear_queues();
+      evict_l2(S, st);
+      cudaEventRecord(ev[0], st);
+      launch_bond<R>(F, P, st);
+      cudaEventRecord(ev[1], st);
+      e = cudaEventSynchronize(ev[1]);
+      float a = 0.f, b = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+      evict_l2(S, st);
+      cudaEventRecord(ev[1], st);
+      launch_cov_force<R>(F, P, T, st);
+      cudaEventRecord(ev[2], st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+      if (rep > 0) sum += a + b;
+    }
+    t[k] = 0.5f * sum;
+    if (ms_out) ms_out[k] = t[k];
+  }
+  int pick = start;
+  float best = 0.f;
+  for (int k = 0; k < 3; ++k)
+    if (t[k] > 0.f && (best == 0.f || t[k] < best)) { best = t[k]; pick = lanes[k]; }
+  S.cov_lanes = pick;
+  if (e == cudaSuccess) {
+    clear_queues();
+    launch_bond<R>(S, P, st);
+    launch_cov_force<R>(S, P, T, st);
+    cudaMemsetAsync(S.rep_acc, 0, sizeof(double) * (size_t)S.R * RA_STRIDE, st);
+    launch_coul_gather<R>(S, P, T, 0, 0.0, st);
+  }
+  for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
+  return e == cudaSuccess ? cudaGetLastError() : e;
+}
+template cudaError_t tune_cov<float>(DevState&, const PotParams<float>&, const TypeParams&, cudaStream_t, float*,
+                                     bool);
+template cudaError_t tune_cov<double>(DevState&, const PotParams<double>&, const TypeParams&, cudaStream_t, float*,
+                                      bool);
 
 // Entries in flight per thread in the charge-force gather (4, 6 or 8; the
 // depth sets the registers, 104 to 128, and so the resident blocks): on the

@@ -76,7 +76,8 @@ class Stats(C.Structure):
         ("cg_mv_batch", C.c_int32), ("asm_batch", C.c_int32), ("cg_mv_ms", C.c_double * 3),
         ("mean_mat", C.c_double), ("asm_ms", C.c_double * 3),
         ("gather_batch", C.c_int32), ("fp64_atoms", C.c_int32), ("fp64_bonds", C.c_int32), ("pad", C.c_int32),
-        ("gather_ms", C.c_double * 3),
+        ("gather_ms", C.c_double * 3), ("cov_lanes", C.c_int32), ("pad2", C.c_int32), ("cov_ms", C.c_double * 3),
+        ("build_warps", C.c_int32), ("build_batch", C.c_int32), ("build_ms", C.c_double * 6),
     ]
 
     def as_dict(self):
@@ -84,7 +85,10 @@ class Stats(C.Structure):
         d["cg_mv_ms"] = list(self.cg_mv_ms)
         d["asm_ms"] = list(self.asm_ms)
         d["gather_ms"] = list(self.gather_ms)
+        d["cov_ms"] = list(self.cov_ms)
+        d["build_ms"] = list(self.build_ms)
         d.pop("pad", None)
+        d.pop("pad2", None)
         return d
 
 

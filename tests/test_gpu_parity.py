@@ -221,6 +221,31 @@ def test_md_energy_error_scales_as_dt_squared():
     assert d1 < 1e-3
 
 
+def test_hot_md_state_in_the_fast_mode():
+    """The bars hold on the state hot MD runs in: the stepped slab after 200
+    mixed steps of 0.5 fs from 2000 K velocities, whose RMS force (about
+    1.7 eV/A) keeps the mixed path out of its accurate mode, evaluated in
+    that mode by the MD system itself and by the oracle at its positions."""
+    from paper_1802_07871_gb300 import ctbop
+    s = st.stepped_slab_small(8, 4, 6)
+    md = ctbop.System(P1, precision="mixed")
+    md.load(s, velocities=st.maxwell_boltzmann(s.types, 2000.0, seed=3, frozen=s.frozen))
+    md.compute()
+    md.step(200, 0.5)
+    md.compute()
+    g = {k: md.get(k) for k in ("energy", "forces", "charges", "virial", "e_atom", "mu")}
+    g["status"] = md.status()
+    x = md.get("positions")
+    md.close()
+    # the fast mode: only compressed bonds took the FP64 pair term
+    assert 0 < g["status"]["fp64_bonds"] < 0.1 * g["status"]["mean_cov"] * s.n
+    sh = st.Structure(s.name, x, s.types, s.box, s.pbc, s.frozen)
+    o = oracle_eval(sh, P1)
+    assert np.sqrt(np.mean(o["F"] ** 2)) > 1.2
+    compare(g, o, s.n, "mixed")
+    assert g["status"]["rc"] == "OK"
+
+
 def test_md_mixed_tracks_fp64_energy():
     """The mixed path's energy excursion matches the FP64 path's: its own
     rounding adds far less than the integrator's dt^2 error."""
