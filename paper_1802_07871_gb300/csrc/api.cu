@@ -373,8 +373,8 @@ static int alloc_atoms(ctbop_system* s) {
   CK(dalloc(s->rep_buf, &S.maxcnt, 3));
   CK(dalloc(s->rep_buf, &S.stiff_n, 1));
   CK(zero_async(s, S.stiff_n, sizeof(int)));
-  CK(dalloc(s->rep_buf, &S.f2_prev, (size_t)s->R));
-  CK(zero_async(s, S.f2_prev, sizeof(double) * s->R));
+  CK(dalloc(s->rep_buf, &S.acc_mode, (size_t)s->R));
+  CK(cudaMemsetAsync(S.acc_mode, 0, sizeof(int) * s->R, s->stream));
   if (s->mixed) {
     CK(dalloc(s->rep_buf, &S.flag_n, 1));
     CK(zero_async(s, S.flag_n, sizeof(int)));

@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(256)
     // the guess shifted by dq: H (q0 + dq 1) = D (q0 + dq) + sum M q0_j + dq sum M
     double qi = q[i] + dq;
     q[i] = qi;
-    double chi_i = rhs ? rhs[i] : T.chi[type[i]];   // rhs: a per-atom chi (adjoint solves)
+    double chi_i = rhs ? rhs[i] : by_type(T.chi, type[i]);   // rhs: a per-atom chi (adjoint solves)
     R ri = (R)(-chi_i - ((double)Di * qi + (double)hq + dq * (double)hm) - s0);
     r[i] = ri;
     v[i] = Di * di + hd;

@@ -67,6 +67,13 @@ struct TypeParams {
   double E0[2], chi[2], J[2], inv_mass_acc[2], mass[2];
 };
 
+// Element t (0 or 1) of a two-entry kernel-parameter array: a select, not
+// an indexed load (an indexed parameter array is copied to local memory).
+template <class V>
+__host__ __device__ inline V by_type(const V (&a)[2], int t) {
+  return t ? a[1] : a[0];
+}
+
 // One replica's box and cell grid.
 struct RepInfo {
   double L[3];        // box lengths (binning extent along open axes)

@@ -8,6 +8,14 @@
 
 namespace ct {
 
+// RMS force (eV/A) below which a replica's next evaluation takes the
+// accurate mode (see k_bond): outside it, with the cutoffs of taper bonds
+// from FP64 positions (cutoff_fp64), the largest FP32 force error measured
+// on hot slabs (2000-2500 K, after 50-400 steps) is 1.4e-5 of the RMS force
+// (about 2.5e-5 eV/A), so a 1e-4 bar relative to the RMS force holds from
+// about 0.25 eV/A on; the threshold keeps a margin of four.
+#define ACC_RMS 1.0
+
 // Offsets (in doubles) of the fields of ctbop_params: the layout of a
 // parameter gradient.
 enum ParamOffsets {
@@ -101,7 +109,7 @@ struct DevState {
   int* flag_q = nullptr;        // [N]
   void* u64 = nullptr;          // double4 [N]
   void* bo64 = nullptr;         // double4 [N * cap_cov]
-  double* f2_prev = nullptr;    // [R]
+  int* acc_mode = nullptr;      // [R] 1: the replica's evaluation takes the FP32 path's accurate mode
   const PotParams<double>* Pd = nullptr;   // host copy of the FP64 parameters
   void* stiff_pe = nullptr;     // double2 [N * cap_cov]
   void* bo = nullptr;           // Real4[N*cap_cov]

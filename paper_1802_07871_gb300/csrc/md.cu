@@ -38,7 +38,7 @@ __global__ void k_kick_drift(int N, double dt, double half_skin2, const int* __r
     v[3 * i] *= scale;
     v[3 * i + 1] *= scale;
     v[3 * i + 2] *= scale;
-    double s = 0.5 * dt * T.inv_mass_acc[ti];
+    double s = 0.5 * dt * by_type(T.inv_mass_acc, ti);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       double vv = v[3 * i + d] + s * F[3 * i + d];
@@ -75,12 +75,17 @@ void launch_nh_end(const DevState& S, double dt, cudaStream_t st) {
   k_nh_end<<<1, 256, 0, st>>>(S.R, dt, S.nh, S.rep_acc);
 }
 
-__global__ void k_zero_acc(int n, double* __restrict__ a, int* __restrict__ stiff_n, double* __restrict__ f2_prev,
-                           int* __restrict__ flag_n) {
+__global__ void k_zero_acc(int n, double* __restrict__ a, int* __restrict__ stiff_n, int* __restrict__ acc_mode,
+                           const RepInfo* __restrict__ reps, int* __restrict__ flag_n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
-    // the previous evaluation's sum of |F|^2 selects this one's precision mode
-    if (i % RA_STRIDE == RA_F2) f2_prev[i / RA_STRIDE] = a[i];
+    // the previous evaluation's sum of |F|^2 selects this one's precision
+    // mode (the accurate mode below an RMS force of ACC_RMS, and after a
+    // reset of the sum)
+    if (i % RA_STRIDE == RA_F2) {
+      const int r = i / RA_STRIDE;
+      acc_mode[r] = a[i] < 3.0 * (double)reps[r].natoms * (ACC_RMS * ACC_RMS) ? 1 : 0;
+    }
     a[i] = 0.0;
   }
   if (i == 0) {   // the queues of this evaluation
@@ -100,7 +105,7 @@ void launch_kick_drift(const DevState& S, const TypeParams& T, double dt, double
 
 void launch_zero_acc(const DevState& S, cudaStream_t st) {
   int n = S.R * RA_STRIDE;
-  k_zero_acc<<<(n + 255) / 256, 256, 0, st>>>(n, S.rep_acc, S.stiff_n, S.f2_prev, S.flag_n);
+  k_zero_acc<<<(n + 255) / 256, 256, 0, st>>>(n, S.rep_acc, S.stiff_n, S.acc_mode, S.reps, S.flag_n);
 }
 
 template void launch_kick_drift<float>(const DevState&, const TypeParams&, double, double, cudaStream_t);

@@ -32,13 +32,6 @@ namespace ct {
 // synthetic set sit at 17.7 eV/A (about twice below the threshold);
 // compressed adatom bonds reach 40-80 eV/A.
 #define STIFF_PAIR 35.0f
-// RMS force (eV/A) below which a replica's next evaluation takes the
-// accurate mode (see k_bond): outside it, with the cutoffs of taper bonds
-// from FP64 positions (cutoff_fp64), the largest FP32 force error measured
-// on hot slabs (2000-2500 K, after 50-400 steps) is 1.4e-5 of the RMS force
-// (about 2.5e-5 eV/A), so a 1e-4 bar relative to the RMS force holds from
-// about 0.25 eV/A on; the threshold keeps a margin of four.
-#define ACC_RMS 1.0
 
 template <class R>
 __device__ inline void bond_order7(R z1, R z2, int pb, const PotParams<R>& P, R& b, R& db1, R& db2) {
@@ -64,36 +57,53 @@ __device__ inline void rel_vec(const typename Vec4<R>::T& ui, const typename Vec
   rz = (uj.z - ui.z) + (R)dz * hz;
 }
 
-// FP64 taper limits of the four pair types, for the FP32 path's cutoff of
-// bonds inside the taper (see cutoff_fp64).
+// Squared taper limits of the four pair types in FP64, for the FP32 path's
+// cutoff of bonds inside the taper (see cutoff_fp64).
 struct Taper64 {
-  double R[4], S[4];
+  double R2[4], S2[4];
 };
 
-// Cutoff and its derivative of bond (i, j, cell code cd) of the FP32 path
-// from the FP64 master positions: the bond length in FP64 (u64 - u64 +
-// shift, the layout of u), its place in the taper in FP64, the cosine
-// factors in FP32. The tapers are a few tenths of an angstrom wide, so the
-// cutoff's curvature (up to pi^2 / (2 (S - R)^2) per A^2) turns the FP32
-// rounding of a cell-local position (about 2e-7 A) into force errors of
-// 1e-4 to 3e-4 eV/A on atoms with a bond in the taper; from the FP64 place
-// in the taper the cutoff is exact to FP32 rounding of its own value.
+// Cutoff and its derivative of bond (i, j, cell code cd) of the FP32 path,
+// placed in the taper from the FP64 master positions. The tapers are a few
+// tenths of an angstrom wide, so the cutoff's curvature (up to
+// pi^2 / (2 (S - R)^2) per A^2) turns the FP32 rounding of a cell-local
+// position (about 2e-7 A) into force errors of 1e-4 to 3e-4 eV/A on atoms
+// with a bond in the taper. Here r^2 - R^2 and S^2 - r^2 are formed in
+// FP64 from the bond vector x_j - x_i + shift (no FP64 root or division),
+// and the nearer end's distance follows in FP32 as (r^2 - R^2) / (r + R)
+// or (S^2 - r^2) / (S + r): accurate to FP32 rounding of that small
+// distance, so the cutoff is placed to about 3e-8 A. r32 is the FP32 bond
+// length (it only scales the quotient).
 __device__ inline void cutoff_fp64(int i, int j, int cd, int pb, const double* __restrict__ x,
                                    const int4* __restrict__ cell4, const RepInfo& ri, const Taper64& TP,
-                                   float pi_SR, float& fc, float& dfc) {
+                                   float r32, float Rf, float Sf, float pi_SR, float& fc, float& dfc) {
   const int4 ci = cell4[i], cj = cell4[j];
   int dx, dy, dz;
   unpack_code(cd, dx, dy, dz);
-  const double rx = ((x[3 * j] - cj.x * ri.hc[0]) - (x[3 * i] - ci.x * ri.hc[0])) + dx * ri.hc[0];
-  const double ry = ((x[3 * j + 1] - cj.y * ri.hc[1]) - (x[3 * i + 1] - ci.y * ri.hc[1])) + dy * ri.hc[1];
-  const double rz = ((x[3 * j + 2] - cj.z * ri.hc[2]) - (x[3 * i + 2] - ci.z * ri.hc[2])) + dz * ri.hc[2];
-  const double r = sqrt(rx * rx + ry * ry + rz * rz);
-  if (r <= TP.R[pb]) { fc = 1.f; dfc = 0.f; return; }
-  if (r >= TP.S[pb]) { fc = 0.f; dfc = 0.f; return; }
-  const float h = (float)(0.5 * (r - TP.R[pb]) / (TP.S[pb] - TP.R[pb]));
-  const float c = ct_cospi<float>(h), sn = ct_sinpi<float>(h);
-  fc = c * c;
-  dfc = -pi_SR * sn * c;
+  // u_j - u_i + d hc with u = x - c hc
+  const double rx = (x[3 * j] - x[3 * i]) + (double)(dx + ci.x - cj.x) * ri.hc[0];
+  const double ry = (x[3 * j + 1] - x[3 * i + 1]) + (double)(dy + ci.y - cj.y) * ri.hc[1];
+  const double rz = (x[3 * j + 2] - x[3 * i + 2]) + (double)(dz + ci.z - cj.z) * ri.hc[2];
+  const double r2 = rx * rx + ry * ry + rz * rz;
+  // (selects, not an indexed load: an indexed parameter array is copied to
+  // local memory)
+  const double R2 = pb == 0 ? TP.R2[0] : pb == 1 ? TP.R2[1] : pb == 2 ? TP.R2[2] : TP.R2[3];
+  const double S2 = pb == 0 ? TP.S2[0] : pb == 1 ? TP.S2[1] : pb == 2 ? TP.S2[2] : TP.S2[3];
+  const double aR = r2 - R2, aS = S2 - r2;
+  if (aR <= 0.0) { fc = 1.f; dfc = 0.f; return; }
+  if (aS <= 0.0) { fc = 0.f; dfc = 0.f; return; }
+  const float w = Sf - Rf;
+  if (aR < aS) {   // t = (r - R) / (S - R) <= 1/2: fc = cos^2(pi t / 2)
+    const float h = 0.5f * (float)aR / ((r32 + Rf) * w);
+    const float c = ct_cospi<float>(h), sn = ct_sinpi<float>(h);
+    fc = c * c;
+    dfc = -pi_SR * sn * c;
+  } else {         // u = 1 - t: fc = sin^2(pi u / 2), sin(pi t/2) cos(pi t/2) = cos(pi u/2) sin(pi u/2)
+    const float h = 0.5f * (float)aS / ((Sf + r32) * w);
+    const float c = ct_cospi<float>(h), sn = ct_sinpi<float>(h);
+    fc = sn * sn;
+    dfc = -pi_SR * c * sn;
+  }
 }
 
 // FP32 path: bonds whose FP32 length lies within this of a taper end take
@@ -123,7 +133,7 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
        const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
         const int* __restrict__ ncov, PotParams<R> P,
        typename Vec4<R>::T* __restrict__ bo, int* __restrict__ stiff_n, int* __restrict__ stiff_q,
-       const double* __restrict__ f2_prev, int* __restrict__ flag_n, int* __restrict__ flag_q,
+       const int* __restrict__ acc_mode, int* __restrict__ flag_n, int* __restrict__ flag_q,
        const int* __restrict__ qlist, const int* __restrict__ qn,
        const double* __restrict__ x64, const int4* __restrict__ cell4, Taper64 TP) {
   using R4 = typename Vec4<R>::T;
@@ -152,8 +162,7 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
     nc = min(ncov[i], cap_cov);
     const int rid = rep[i];
     const RepInfo& ri = reps[rid];
-    if (sizeof(R) == 4 && f2_prev)
-      acc = f2_prev[rid] < 3.0 * (double)ri.natoms * (double)(ACC_RMS * ACC_RMS);
+    if (sizeof(R) == 4 && acc_mode) acc = acc_mode[rid] != 0;
     R hx = ri.hcf[0], hy = ri.hcf[1], hz = ri.hcf[2];
     if (sizeof(R) == 8) { hx = (R)ri.hc[0]; hy = (R)ri.hc[1]; hz = (R)ri.hc[2]; }
     for (int e = l; e < nc; e += G) {
@@ -169,7 +178,8 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
       cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
       if (sizeof(R) == 4 && x64 && r > P.Rin[pb] - R(TAPER_MARGIN) && r < P.Sout[pb] + R(TAPER_MARGIN)) {
         float f, df;
-        cutoff_fp64(i, j, jcd.y, pb, x64, cell4, ri, TP, (float)P.pi_SR[pb], f, df);
+        cutoff_fp64(i, j, jcd.y, pb, x64, cell4, ri, TP, (float)r, (float)P.Rin[pb], (float)P.Sout[pb],
+                    (float)P.pi_SR[pb], f, df);
         fc = (R)f;
       }
       R4 w;
@@ -448,7 +458,7 @@ __global__ void __launch_bounds__(256)
     }
   }
   if (sizeof(R) == 4) nmat[i] = em;
-  R D = (R)(2.0 * T.J[ti]) + R(2) * wsum;
+  R D = (R)(2.0 * by_type(T.J, ti)) + R(2) * wsum;
   Dg[i] = D;
   dinv[i] = R(1) / (D + selfm);
 }
@@ -491,6 +501,7 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
   int nc = 0, ti = 0;
   CompSum<R> eacc;
   double estiff = 0.0;   // FP64 pair energies of the stiff bonds (FP32 path)
+  int nstiff = 0;        // how many (the FP64 sum is skipped where a warp has none)
   if (live) {
     R4 ui = u[i];
     ti = (int)ui.w;
@@ -512,7 +523,8 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
       cutoff_fn<R>(r, P.Rin[pb], P.Sout[pb], P.pi_SR[pb], fc, dfc);
       if (sizeof(R) == 4 && x64 && r > P.Rin[pb] - R(TAPER_MARGIN) && r < P.Sout[pb] + R(TAPER_MARGIN)) {
         float f, df;
-        cutoff_fp64(i, j, nl[idx].y, pb, x64, cell4, ri, TP, (float)P.pi_SR[pb], f, df);
+        cutoff_fp64(i, j, nl[idx].y, pb, x64, cell4, ri, TP, (float)r, (float)P.Rin[pb], (float)P.Sout[pb],
+                    (float)P.pi_SR[pb], f, df);
         fc = (R)f;
         dfc = (R)df;
       }
@@ -530,6 +542,7 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
           // stiff bond: pair term evaluated in FP64 by k_stiff
           double2 v = static_cast<const double2*>(stiff_pe)[(size_t)i * cap_cov + e];
           estiff += v.y;
+          ++nstiff;
           pd = (R)v.x;
         } else {
           eacc.add(R(0.5) * fc * (fR - att));
@@ -621,17 +634,25 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
       gslot[(size_t)i * cap_cov + e] = out;
     }
   }
-  // per-atom energy: covalent part + self energy (all lanes take part)
+  // per-atom energy: covalent part + self energy (all lanes take part). An
+  // FP64 warp instruction costs the FP64 pipe as much as dozens of FP32
+  // ones, so the FP64 work here is kept to the few operations the
+  // precision needs: the stiff-bond sum only where the warp has one, the
+  // self energy as two fused multiply-adds.
   R es = eacc.s, ec = eacc.c;
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) {
     es += __shfl_xor_sync(CT_FULL, es, o, G);
     ec += __shfl_xor_sync(CT_FULL, ec, o, G);
-    estiff += __shfl_xor_sync(CT_FULL, estiff, o, G);
+  }
+  if (__any_sync(CT_FULL, nstiff != 0)) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) estiff += __shfl_xor_sync(CT_FULL, estiff, o, G);
   }
   if (live && l == 0) {
-    double qd = q[i];
-    e_atom[i] = ((double)es + (double)ec) + estiff + T.E0[ti] + T.chi[ti] * qd + T.J[ti] * qd * qd;
+    const double qd = q[i];
+    const double self = fma(fma(by_type(T.J, ti), qd, by_type(T.chi, ti)), qd, by_type(T.E0, ti));
+    e_atom[i] = ((double)es + (double)ec) + (self + estiff);
   }
 }
 
@@ -653,9 +674,23 @@ __global__ void __launch_bounds__(256)
                   const double* __restrict__ nh) {
   using R4 = typename Vec4<R>::T;
   // per-replica sums in one accumulator (the slot order of rep_acc): E, KE,
-  // sum of |F|^2 (the RMS force that picks the next evaluation's mode), virial
+  // sum of |F|^2 (the RMS force that picks the next evaluation's mode),
+  // virial. The virial and |F|^2 add up over this thread's atoms in the
+  // working precision first (a dozen atoms at 1M; an FP64 warp instruction
+  // costs the FP64 pipe as much as dozens of FP32 ones) and join the FP64
+  // accumulator at each replica change and at the end.
   RepAcc<RA_STRIDE> acc;
   acc.init();
+  R pw[10];   // virial, |F|^2
+#pragma unroll
+  for (int k = 0; k < 10; ++k) pw[k] = R(0);
+  auto fold = [&]() {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc.v[RA_W + k] += (double)pw[k];
+    acc.v[RA_F2] += (double)pw[9];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) pw[k] = R(0);
+  };
   for (int t = blockIdx.x; (long long)t * 256 < N; t += gridDim.x) {
     int i = t * 256 + (int)threadIdx.x;
     if (i >= N) break;
@@ -751,14 +786,17 @@ __global__ void __launch_bounds__(256)
     F[3 * i] = Fx; F[3 * i + 1] = Fy; F[3 * i + 2] = Fz;
     double ea = e_atom[i] + ec.value();
     e_atom[i] = ea;
-    if (!isfinite(ea) || !isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) atomicOr(err, CT_ERR_NONFINITE);
+    // finiteness from the working-precision sums and the FP64 exponent bits
+    const bool bad_e = (__double_as_longlong(ea) & 0x7ff0000000000000ll) == 0x7ff0000000000000ll;
+    if (bad_e || !isfinite(fx) || !isfinite(fy) || !isfinite(fz)) atomicOr(err, CT_ERR_NONFINITE);
+    if (ri_id != acc.rep) fold();
     acc.to(ri_id, rep_acc, RA_STRIDE);
     acc.v[RA_E] += ea;
-    acc.v[RA_F2] += Fx * Fx + Fy * Fy + Fz * Fz;
+    pw[9] += fx * fx + fy * fy + fz * fz;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) acc.v[RA_W + k] += (double)w[k];
+    for (int k = 0; k < 9; ++k) pw[k] += w[k];
     if (kick && !frozen[i]) {
-      double sc = half_dt * T.inv_mass_acc[ti];
+      double sc = half_dt * by_type(T.inv_mass_acc, ti);
       double vx = v[3 * i] + sc * Fx, vy = v[3 * i + 1] + sc * Fy, vz = v[3 * i + 2] + sc * Fz;
       const double* h = nh + (size_t)ri_id * NH_STRIDE;
       if (h[NH_ON] != 0.0) {   // NVT: the second velocity scaling, exp(-xi' dt/2)
@@ -769,9 +807,10 @@ __global__ void __launch_bounds__(256)
     }
     {   // kinetic energy of the current velocities
       double vx = v[3 * i], vy = v[3 * i + 1], vz = v[3 * i + 2];
-      acc.v[RA_KE] += 0.5 * T.mass[ti] * (vx * vx + vy * vy + vz * vz);
+      acc.v[RA_KE] += 0.5 * by_type(T.mass, ti) * (vx * vx + vy * vy + vz * vz);
     }
   }
+  fold();
   lane_flush<RA_STRIDE>(acc, rep_acc, RA_STRIDE);
 }
 
@@ -813,8 +852,8 @@ int atom_dims(int N, int nsm, const void* kernel, int threads, int& chunk) {
 static Taper64 taper64(const DevState& S) {
   Taper64 t;
   for (int k = 0; k < 4; ++k) {
-    t.R[k] = S.Pd->Rin[k];
-    t.S[k] = S.Pd->Sout[k];
+    t.R2[k] = S.Pd->Rin[k] * S.Pd->Rin[k];
+    t.S2[k] = S.Pd->Sout[k] * S.Pd->Sout[k];
   }
   return t;
 }
@@ -834,7 +873,7 @@ static void launch_bond_g(const DevState& S, const PotParams<R>& P, cudaStream_t
   const Taper64 tp = taper64(S);
   k_bond<R, G><<<gb, CB, sm, st>>>(
       S.N, S.cap_cov, S.ld, (const typename Vec4<R>::T*)S.u, S.rep, S.reps, S.nl,
-      S.ncov, P, (typename Vec4<R>::T*)S.bo, S.stiff_n, S.stiff_q, S.f2_prev, S.flag_n, S.flag_q,
+      S.ncov, P, (typename Vec4<R>::T*)S.bo, S.stiff_n, S.stiff_q, S.acc_mode, S.flag_n, S.flag_q,
       nullptr, nullptr, sizeof(R) == 4 ? S.x : nullptr, S.cell4, tp);
   if constexpr (sizeof(R) == 4) {
     // the queued atoms in FP64: master-precision offsets, then their bond orders
@@ -1069,7 +1108,7 @@ cudaError_t tune_cov(DevState& S, const PotParams<R>& P, const TypeParams& T, cu
   };
   float t[3] = {0.f, 0.f, 0.f};
   DevState F = S;
-  if (fast) F.f2_prev = nullptr;   // the fast mode
+  if (fast) F.acc_mode = nullptr;   // the fast mode
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
     if (!(S.cov_lanes_ok & (1 << k))) continue;
     F.cov_lanes = lanes[k];

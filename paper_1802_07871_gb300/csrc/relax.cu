@@ -102,7 +102,7 @@ __global__ void k_fire_move(int N, double half_skin2, const int* __restrict__ ty
   }
   double cv = f[FI_CV], cf = f[FI_CF], dt = f[FI_DT];
   int ti = type[i];
-  double s = dt * T.inv_mass_acc[ti];
+  double s = dt * by_type(T.inv_mass_acc, ti);
   double xi[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
