@@ -127,6 +127,35 @@ __device__ inline void cutoff_fp64(int i, int j, int cd, int pb, const double* _
 // force allows.
 // qlist/qn: when given, block b takes the queued atoms qlist[b*CB/G ..], the
 // rest of the grid exits at once.
+//
+// Live bonds. Of an atom's covalent entries (r < S + skin) only those with
+// f_c > 0 take part in bond orders and three-body terms; the rest (the skin,
+// about a fifth of the entries in hot MD) get their trivial outputs at once
+// and the bond and three-body loops run over the compacted live list, in
+// list order (the sums add in the same order as over the full list).
+
+// The live bonds of this lane group's atom, in list order, into s_lv; the
+// count is returned to every lane of the group. dead(e) is called by the
+// lane that tested a bond past the cutoff. Every lane of the warp takes
+// part (ballots).
+template <int G, class R, class Dead>
+__device__ inline int compact_live(bool live, int nc, int l, const R* s_fc, int* s_lv, Dead dead) {
+  const int shift = (int)(threadIdx.x & 31) - l;   // the group's first lane in the warp
+  const unsigned gm = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+  const int rounds = (int)__reduce_max_sync(CT_FULL, live ? (unsigned)((nc + G - 1) / G) : 0u);
+  int n = 0;
+  for (int r = 0; r < rounds; ++r) {
+    const int e = r * G + l;
+    const bool inr = live && e < nc;
+    const bool lv = inr && s_fc[e] > R(0);
+    const unsigned m = (__ballot_sync(CT_FULL, lv) >> shift) & gm;
+    if (lv) s_lv[n + __popc(m & ((1u << l) - 1u))] = e;
+    else if (inr) dead(e);
+    n += __popc(m);
+  }
+  return n;
+}
+
 template <class R, int G>
 __global__ void __launch_bounds__(CB)
 k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
@@ -142,10 +171,12 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
   __shared__ int s_nstiff, s_base, s_nflag, s_fbase;
   if (threadIdx.x == 0) { s_nstiff = 0; s_nflag = 0; }
   int g = threadIdx.x / G, l = threadIdx.x % G;
-  R4* s_u = reinterpret_cast<R4*>(smem_raw) + (size_t)g * cap_cov;               // (ux,uy,uz,r)
-  R* s_fc = reinterpret_cast<R*>(reinterpret_cast<R4*>(smem_raw) + (size_t)APB_ * cap_cov) + (size_t)g * cap_cov;
-  int* s_t = reinterpret_cast<int*>(reinterpret_cast<R*>(reinterpret_cast<R4*>(smem_raw) + (size_t)APB_ * cap_cov)
-                                    + (size_t)APB_ * cap_cov) + (size_t)g * cap_cov;
+  // layout: R4 (ux,uy,uz,r)[APB_][cap] | R fc | int type | int live list
+  R4* s_u = reinterpret_cast<R4*>(smem_raw);
+  R* s_fc = reinterpret_cast<R*>(s_u + (size_t)APB_ * cap_cov);
+  int* s_t = reinterpret_cast<int*>(s_fc + (size_t)APB_ * cap_cov);
+  int* s_lv = s_t + (size_t)APB_ * cap_cov;
+  s_u += (size_t)g * cap_cov; s_fc += (size_t)g * cap_cov; s_t += (size_t)g * cap_cov; s_lv += (size_t)g * cap_cov;
   int i = blockIdx.x * APB_ + g;
   if (qlist) {
     const int nq = *qn;
@@ -191,7 +222,14 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
   }
   __syncthreads();
   int my_stiff = 0, my_flag = 0;
-  for (int e = l; live && e < nc; e += G) {
+  const int nlive = compact_live<G, R>(live, nc, l, s_fc, s_lv, [&](int e) {
+    R4 out;
+    out.x = R(1); out.y = R(0); out.z = R(0); out.w = R(0);
+    bo[(size_t)i * cap_cov + e] = out;
+  });
+  __syncwarp();
+  for (int q = l; q < nlive; q += G) {
+    const int e = s_lv[q];
     R4 ue = s_u[e];
     int tj = s_t[e];
     int pb = ti * 2 + tj;
@@ -199,7 +237,7 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
     // .w marks a stiff bond (FP32 path): its pair term is evaluated in FP64
     // by k_stiff, from the queue built below (every bond in the accurate mode)
     out.w = R(0);
-    if (sizeof(R) == 4 && ue.w < P.Sout[pb]) {
+    if (sizeof(R) == 4) {
       bool compressed = P.lam1[pb] * P.A[pb] * ct_exp<R>(-P.lam1[pb] * ue.w) > R(STIFF_PAIR);
       if (compressed || acc) {
         out.w = R(1);
@@ -207,18 +245,13 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
       }
       if (acc && (compressed || ue.w > P.Rin[pb])) my_flag = 1;
     }
-    if (ue.w >= P.Sout[pb]) {
-      out.x = R(1); out.y = R(0); out.z = R(0);
-      bo[(size_t)i * cap_cov + e] = out;
-      continue;
-    }
     R re = ue.w, ire = R(1) / re;
     R z1 = R(0), z2 = R(0);
     int tbase = pb * 2;
-    for (int k = 0; k < nc; ++k) {
+    for (int kk = 0; kk < nlive; ++kk) {
+      const int k = s_lv[kk];
       if (k == e) continue;
       R fck = s_fc[k];
-      if (fck == R(0)) continue;
       R4 uk = s_u[k];
       int tri = tbase + s_t[k];
       R ct = (ue.x * uk.x + ue.y * uk.y + ue.z * uk.z) * ire / uk.w;
@@ -256,10 +289,12 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
     s_fbase = s_nflag ? atomicAdd(flag_n, s_nflag) : 0;
   }
   __syncthreads();
-  if (my_stiff) {
+  if (my_stiff) {   // (the live bonds this lane computed, as above)
     int pos = s_base + off;
-    for (int e = l; e < nc; e += G)
+    for (int q = l; q < nlive; q += G) {
+      const int e = s_lv[q];
       if (bo[(size_t)i * cap_cov + e].w != R(0)) stiff_q[pos++] = i * cap_cov + e;
+    }
   }
   if (my_flag && l == 0) flag_q[s_fbase + foff] = i;
 }
@@ -481,15 +516,17 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
   constexpr int APB_ = CB / G;
   extern __shared__ __align__(32) unsigned char smem_raw[];
   int g = threadIdx.x / G, l = threadIdx.x % G;
-  // layout: R4 u[APB_][cap] | R2 D[APB_][cap] | R fc | R dfc | R pair dE/dr | int type
+  // layout: R4 u[APB_][cap] | R2 D[APB_][cap] | R fc | R dfc | R pair dE/dr | int type | int live list
   R4* s_u = reinterpret_cast<R4*>(smem_raw);
   R2* s_D = reinterpret_cast<R2*>(s_u + (size_t)APB_ * cap_cov);
   R* s_fc = reinterpret_cast<R*>(s_D + (size_t)APB_ * cap_cov);
   R* s_dfc = s_fc + (size_t)APB_ * cap_cov;
   R* s_pd = s_dfc + (size_t)APB_ * cap_cov;
   int* s_t = reinterpret_cast<int*>(s_pd + (size_t)APB_ * cap_cov);
+  int* s_lv = s_t + (size_t)APB_ * cap_cov;
   s_u += (size_t)g * cap_cov; s_D += (size_t)g * cap_cov; s_fc += (size_t)g * cap_cov;
   s_dfc += (size_t)g * cap_cov; s_pd += (size_t)g * cap_cov; s_t += (size_t)g * cap_cov;
+  s_lv += (size_t)g * cap_cov;
 
   int i = blockIdx.x * APB_ + g;
   if (qlist) {
@@ -563,14 +600,21 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
     }
   }
   __syncwarp();
-  if (live) {
-    for (int e = l; e < nc; e += G) {
+  const int nlive = compact_live<G, R>(live, nc, l, s_fc, s_lv, [&](int e) {
+    typename Vec4<O>::T z;
+    z.x = O(0); z.y = O(0); z.z = O(0); z.w = O(0);
+    gslot[(size_t)i * cap_cov + e] = z;
+  });
+  __syncwarp();
+  {
+    for (int q = l; q < nlive; q += G) {
+      const int e = s_lv[q];
       R4 ux = s_u[e];
       R rx = ux.w;
       R fcx = s_fc[e];
       typename Vec4<O>::T out;
       out.x = O(0); out.y = O(0); out.z = O(0); out.w = O(0);
-      if (fcx > R(0)) {
+      {
         R irx = R(1) / rx;
         R hx_ = ux.x * irx, hy_ = ux.y * irx, hz_ = ux.z * irx;
         R2 Dx = s_D[e];
@@ -578,10 +622,10 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
         int tx = s_t[e];
         R c_ux = s_pd[e];
         R gx = R(0), gy = R(0), gz = R(0);
-        for (int k = 0; k < nc; ++k) {
+        for (int kk = 0; kk < nlive; ++kk) {
+          const int k = s_lv[kk];
           if (k == e) continue;
           R fck = s_fc[k];
-          if (fck == R(0)) continue;
           R4 uk = s_u[k];
           R rk = uk.w, irk = R(1) / rk;
           R kx = uk.x * irk, ky = uk.y * irk, kz = uk.z * irk;
@@ -859,11 +903,11 @@ static Taper64 taper64(const DevState& S) {
 }
 
 template <class R> static size_t bond_smem(int cap, int G) {
-  return (size_t)(CB / G) * cap * (sizeof(typename Vec4<R>::T) + sizeof(R) + sizeof(int));
+  return (size_t)(CB / G) * cap * (sizeof(typename Vec4<R>::T) + sizeof(R) + 2 * sizeof(int));
 }
 template <class R> static size_t force_smem(int cap, int G) {
   return (size_t)(CB / G) * cap *
-         (sizeof(typename Vec4<R>::T) + sizeof(typename Vec2<R>::T) + 3 * sizeof(R) + sizeof(int));
+         (sizeof(typename Vec4<R>::T) + sizeof(typename Vec2<R>::T) + 3 * sizeof(R) + 2 * sizeof(int));
 }
 
 template <class R, int G>
