@@ -72,7 +72,10 @@ extern "C" {
 #define CTBOP_GET_CHARGES   2   /* double[N]   charges (e) */
 #define CTBOP_GET_POSITIONS 3   /* double[N*3] positions (A); wrapped into the box along periodic axes at list rebuilds */
 #define CTBOP_GET_VELOCITIES 4  /* double[N*3] velocities (A/fs) */
-#define CTBOP_GET_VIRIAL    5   /* double[R*9] virial W = -sum_u u (x) dE/du, row-major 3x3 (eV) */
+#define CTBOP_GET_VIRIAL    5   /* double[R*9] virial W = -sum_u u (x) dE/du, row-major 3x3 (eV); MD steps
+                                   leave it out of their force pass, so the first read after ctbop_step
+                                   recomputes it from the current state (one covalent-force and charge-force
+                                   pass, no kick) */
 #define CTBOP_GET_E_ATOM    6   /* double[N]   per-atom energies (eV) */
 #define CTBOP_GET_MU        7   /* double[R]   electronegativity (Lagrange multiplier of sum q = Q), eV/e */
 #define CTBOP_GET_KINETIC   8   /* double[R]   kinetic energy of the current velocities (eV) */

@@ -76,6 +76,7 @@ struct ctbop_system {
   std::vector<double> Q;        // R
   bool have_layout = false, have_box = false, have_types = false, have_pos = false;
   bool have_forces = false, need_rebuild = true, reps_dirty = true, caps_known = false;
+  bool virial_stale = false;   // MD steps leave the virial out of the replica sums
   // allocations
   DevBuf atom_buf, list_buf, cell_buf, rep_buf;
   int alloc_N = -1, alloc_R = -1, alloc_cells = -1, alloc_cov = -1, alloc_all = -1;
@@ -491,7 +492,7 @@ static void enqueue_back(ctbop_system* s, const PotParams<Rr>& P, cudaStream_t s
                          bool solve) {
   DevState& S = s->S;
   if (solve) launch_cg_end<Rr>(S, st);
-  launch_forces<Rr>(S, P, s->T, md ? 1 : 0, 0.5 * dt, st);
+  launch_forces<Rr>(S, P, s->T, md ? 1 : 0, 0.5 * dt, st, !md);
   if (md && s->nvt) launch_nh_end(S, dt, st);
 }
 
@@ -707,6 +708,7 @@ static int eval_t(ctbop_system* s, const PotParams<Rr>& P, uint32_t flags) {
       destroy_graphs(s);
     s->solves++;
     s->have_forces = true;
+    s->virial_stale = false;
     return CTBOP_OK;
   }
   if (s->use_graph && solve) {
@@ -721,6 +723,23 @@ static int eval_t(ctbop_system* s, const PotParams<Rr>& P, uint32_t flags) {
   }
   if (solve) s->solves++;
   s->have_forces = true;
+  s->virial_stale = false;
+  return CTBOP_OK;
+}
+
+// The virial of the current state, after MD steps (whose force gather leaves
+// it out: 15% of that pass at 1M atoms): the covalent slots and per-atom
+// energies again, then the gather with the virial and no kick, which
+// recomputes every replica sum from the same positions, charges and
+// velocities.
+template <class Rr>
+static int refresh_virial(ctbop_system* s, const PotParams<Rr>& P) {
+  DevState& S = s->S;
+  launch_cov_force<Rr>(S, P, s->T, s->stream);
+  CK(cudaMemsetAsync(S.rep_acc, 0, sizeof(double) * (size_t)s->R * RA_STRIDE, s->stream));
+  launch_coul_gather<Rr>(S, P, s->T, 0, 0.0, s->stream, true);
+  CK(cudaGetLastError());
+  s->virial_stale = false;
   return CTBOP_OK;
 }
 
@@ -779,7 +798,7 @@ static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double 
     if (!rc) rc = timed(7, 2, [&] { launch_cg_end<Rr>(S, st); });
     if (!rc) rc = timed(8, sizeof(Rr) == 4 ? 3 : 1, [&] { launch_cov_force<Rr>(S, P, s->T, st); });
     if (!rc) rc = timed(9, s->nvt ? 2 : 1, [&] {
-      launch_coul_gather<Rr>(S, P, s->T, 1, 0.5 * dt, st);
+      launch_coul_gather<Rr>(S, P, s->T, 1, 0.5 * dt, st, false);
       if (s->nvt) launch_nh_end(S, dt, st);
     });
     if (!rc) {
@@ -791,6 +810,7 @@ static int profile_t(ctbop_system* s, const PotParams<Rr>& P, int64_t n, double 
     }
     s->steps++;
     s->solves++;
+    s->virial_stale = true;
   }
   return rc;
 }
@@ -1238,6 +1258,7 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
     done += n;
     s->steps += n;
     s->solves += n;
+    if (n > 0) s->virial_stale = true;
     if (bits & CT_ERR_CG_MAXITER) { result = fail(s, CTBOP_ERR_CG_NOT_CONVERGED, "charge CG reached max_iter"); break; }
     if (s->cov_retune && s->steps >= s->cov_tuned_at + COV_RETUNE_STEPS) {
       // The covalent lanes were timed on the starting configuration, where
@@ -1277,6 +1298,10 @@ int ctbop_get(ctbop_system* s, int what, void* dst, int mem) {
   DevState& S = s->S;
   cudaMemcpyKind kind = mem == CTBOP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   size_t N = S.N, R = s->R;
+  if (what == CTBOP_GET_VIRIAL && s->virial_stale && s->have_forces) {
+    int rc = s->mixed ? refresh_virial<float>(s, s->Pf) : refresh_virial<double>(s, s->Pd);
+    if (rc) return rc;
+  }
   if (what == CTBOP_GET_COORDINATION) {
     // computed from the current lists, which an evaluation leaves valid
     if (!s->have_forces) return fail(s, CTBOP_ERR_STATE, "coordination: compute or step first");

@@ -170,10 +170,12 @@ template <class R> cudaError_t tune_cg_mv(DevState& S, cudaStream_t st, float* m
 template <class R> void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st);
 template <class R> void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams& T,
                                          cudaStream_t st);
+// virial: accumulate the virial (an evaluation) or not (an MD step: the
+// library recomputes it when it is read after steps)
 template <class R> void launch_coul_gather(const DevState& S, const PotParams<R>& P, const TypeParams& T,
-                                           int kick, double half_dt, cudaStream_t st);
+                                           int kick, double half_dt, cudaStream_t st, bool virial);
 template <class R> void launch_forces(const DevState& S, const PotParams<R>& P, const TypeParams& T,
-                                      int kick, double half_dt, cudaStream_t st);
+                                      int kick, double half_dt, cudaStream_t st, bool virial);
 template <class R> void launch_kick_drift(const DevState& S, const TypeParams& T, double dt, double half_skin2,
                                           cudaStream_t st);
 void launch_zero_acc(const DevState& S, cudaStream_t st);

@@ -706,7 +706,7 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
 // FP64 store, half kick, kinetic energy and per-replica sums. Threads take
 // 256-atom tiles strided over the grid, so the FP64 per-replica reductions
 // are paid once per thread, not once per atom.
-template <class R, int PB>
+template <class R, int PB, bool VIR>
 __global__ void __launch_bounds__(256)
     k_coul_gather(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
                   const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
@@ -774,9 +774,11 @@ __global__ void __launch_bounds__(256)
       // virial: -1/2 qq K'/r r (x) r for the charge pair, -r (x) slot for the bond
       R hc = R(-0.5) * c;
       R tx = hc * rx - go.x, ty = hc * ry - go.y, tz = hc * rz - go.z;
+      if (VIR) {
       w[0] += rx * tx; w[1] += rx * ty; w[2] += rx * tz;
       w[3] += ry * tx; w[4] += ry * ty; w[5] += ry * tz;
       w[6] += rz * tx; w[7] += rz * ty; w[8] += rz * tz;
+      }
     }
     // remaining entries: charge term only, streamed
     int jn[PB], cn[PB];
@@ -820,9 +822,11 @@ __global__ void __launch_bounds__(256)
           ec.add(R(0.5) * qq * K);
           R hc = R(-0.5) * c;
           R hx_ = hc * rx, hy_ = hc * ry, hz_ = hc * rz;
+          if (VIR) {
           w[0] += rx * hx_; w[1] += rx * hy_; w[2] += rx * hz_;
           w[3] += ry * hx_; w[4] += ry * hy_; w[5] += ry * hz_;
           w[6] += rz * hx_; w[7] += rz * hy_; w[8] += rz * hz_;
+          }
         }
       }
     }
@@ -984,7 +988,7 @@ void launch_cov_force(const DevState& S, const PotParams<R>& P, const TypeParams
 
 template <class R>
 void launch_coul_gather(const DevState& S, const PotParams<R>& P, const TypeParams& T, int kick, double half_dt,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool virial) {
   if (S.N == 0) return;
   auto go = [&](auto kernel) {
     int occ = 0;
@@ -996,16 +1000,22 @@ void launch_coul_gather(const DevState& S, const PotParams<R>& P, const TypePara
         S.ncov, S.nall, S.rev, (const typename Vec4<R>::T*)S.gslot, (const R*)S.qr, P, T, kick, half_dt,
         S.frozen, S.F, S.v, S.e_atom, S.rep_acc, S.err, S.nh);
   };
-  if (S.gather_batch == 4) go(k_coul_gather<R, 4>);
-  else if (S.gather_batch == 6) go(k_coul_gather<R, 6>);
-  else go(k_coul_gather<R, 8>);
+  if (virial) {
+    if (S.gather_batch == 4) go(k_coul_gather<R, 4, true>);
+    else if (S.gather_batch == 6) go(k_coul_gather<R, 6, true>);
+    else go(k_coul_gather<R, 8, true>);
+  } else {
+    if (S.gather_batch == 4) go(k_coul_gather<R, 4, false>);
+    else if (S.gather_batch == 6) go(k_coul_gather<R, 6, false>);
+    else go(k_coul_gather<R, 8, false>);
+  }
 }
 
 template <class R>
 void launch_forces(const DevState& S, const PotParams<R>& P, const TypeParams& T, int kick, double half_dt,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool virial) {
   launch_cov_force<R>(S, P, T, st);
-  launch_coul_gather<R>(S, P, T, kick, half_dt, st);
+  launch_coul_gather<R>(S, P, T, kick, half_dt, st, virial);
 }
 
 template <class R, int G>
@@ -1187,7 +1197,7 @@ cudaError_t tune_cov(DevState& S, const PotParams<R>& P, const TypeParams& T, cu
     launch_bond<R>(S, P, st);
     launch_cov_force<R>(S, P, T, st);
     cudaMemsetAsync(S.rep_acc, 0, sizeof(double) * (size_t)S.R * RA_STRIDE, st);
-    launch_coul_gather<R>(S, P, T, 0, 0.0, st);
+    launch_coul_gather<R>(S, P, T, 0, 0.0, st, true);
   }
   for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
   return e == cudaSuccess ? cudaGetLastError() : e;
@@ -1201,8 +1211,9 @@ template cudaError_t tune_cov<double>(DevState&, const PotParams<double>&, const
 // depth sets the registers, 104 to 128, and so the resident blocks): on the
 // state of a completed evaluation without a kick, each depth runs the
 // covalent force pass (untimed: the gather adds to the per-atom energies it
-// writes) and the gather (timed), twice; the fastest is kept and the pair
-// runs once more so the evaluation's results are as the kept depth sums them.
+// writes) and the gather without the virial (timed: the variant MD steps
+// run), three times; the fastest is kept and the pair runs once more, with
+// the virial, so the evaluation's results are as the kept depth sums them.
 template <class R>
 cudaError_t tune_gather(DevState& S, const PotParams<R>& P, const TypeParams& T, cudaStream_t st, float* ms_out) {
   if (S.N == 0) return cudaSuccess;
@@ -1221,7 +1232,7 @@ cudaError_t tune_gather(DevState& S, const PotParams<R>& P, const TypeParams& T,
       cudaMemsetAsync(S.rep_acc, 0, acc_bytes, st);
       launch_cov_force<R>(S, P, T, st);
       cudaEventRecord(e0, st);
-      launch_coul_gather<R>(S, P, T, 0, 0.0, st);
+      launch_coul_gather<R>(S, P, T, 0, 0.0, st, false);   // the variant MD steps run
       cudaEventRecord(e1, st);
       e = cudaEventSynchronize(e1);
       float ms = 0.0f;
@@ -1239,7 +1250,7 @@ cudaError_t tune_gather(DevState& S, const PotParams<R>& P, const TypeParams& T,
   if (e == cudaSuccess) {
     cudaMemsetAsync(S.rep_acc, 0, acc_bytes, st);
     launch_cov_force<R>(S, P, T, st);
-    launch_coul_gather<R>(S, P, T, 0, 0.0, st);
+    launch_coul_gather<R>(S, P, T, 0, 0.0, st, true);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1254,12 +1265,12 @@ template void launch_assemble<double>(const DevState&, const PotParams<double>&,
 template void launch_cov_force<float>(const DevState&, const PotParams<float>&, const TypeParams&, cudaStream_t);
 template void launch_cov_force<double>(const DevState&, const PotParams<double>&, const TypeParams&, cudaStream_t);
 template void launch_coul_gather<float>(const DevState&, const PotParams<float>&, const TypeParams&, int, double,
-                                        cudaStream_t);
+                                        cudaStream_t, bool);
 template void launch_coul_gather<double>(const DevState&, const PotParams<double>&, const TypeParams&, int, double,
-                                         cudaStream_t);
+                                         cudaStream_t, bool);
 template void launch_forces<float>(const DevState&, const PotParams<float>&, const TypeParams&, int, double,
-                                   cudaStream_t);
+                                   cudaStream_t, bool);
 template void launch_forces<double>(const DevState&, const PotParams<double>&, const TypeParams&, int, double,
-                                    cudaStream_t);
+                                    cudaStream_t, bool);
 
 }  // namespace ct
