@@ -50,6 +50,7 @@
 // replicas, and ends the loop through the CUDA-graph condition (or a device
 // flag the host polls).
 #include "internal.cuh"
+#include <cuda_fp16.h>
 #include "kernels.h"
 
 namespace ct {
@@ -235,10 +236,23 @@ __global__ void k_cg_prep(int N, int R, double* __restrict__ cg, unsigned long l
 // skin, H drifts by a few per cent, and a slightly stale M^-1 is still a
 // fixed symmetric positive definite preconditioner for the whole solve, so
 // only the iteration count can change, never the converged result.
+// Storage of the block inverses: FP16 on the FP32 path (a fixed symmetric
+// preconditioner steers only the iteration count; FP16 halves the largest
+// stream of the update pass, 128 of its 176 bytes per atom), FP64 on the
+// FP64 path. The stored values are exactly symmetric (see k_block_setup), so
+// their FP16 roundings are too, and d = M^-1 1 is summed from the stored
+// values.
+template <class R> struct BlockStore { using T = R; };
+template <> struct BlockStore<float> { using T = __half; };
+__device__ inline __half blk_pack(float v) { return __float2half_rn(v); }
+__device__ inline double blk_pack(double v) { return v; }
+__device__ inline float blk_unpack(__half h) { return __half2float(h); }
+__device__ inline double blk_unpack(double v) { return v; }
+
 template <class R>
 __global__ void __launch_bounds__(128)
     k_block_setup(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nmat,
-                  const void* __restrict__ M, const R* __restrict__ Dg, R* __restrict__ binv,
+                  const void* __restrict__ M, const R* __restrict__ Dg, typename BlockStore<R>::T* __restrict__ binv,
                   R* __restrict__ bsum, const long long* __restrict__ rebuilds,
                   const long long* __restrict__ epoch) {
   if (*rebuilds == *epoch) return;
@@ -297,11 +311,11 @@ __global__ void __launch_bounds__(128)
       for (int j = k + 1; j <= lane; ++j) A[lane][j] -= A[lane][k] * A[j][k];
     __syncwarp();
   }
-  R* out = binv + (size_t)(base >> 5) * 1024;
+  typename BlockStore<R>::T* out = binv + (size_t)(base >> 5) * 1024;
   if (!ok) {
     __syncwarp();
-    for (int j = 0; j < 32; ++j) out[j * 32 + lane] = j == lane ? R(1) / hii : R(0);
-    if (i < N) bsum[i] = R(1) / hii;
+    for (int j = 0; j < 32; ++j) out[j * 32 + lane] = blk_pack(j == lane ? R(1) / hii : R(0));
+    if (i < N) bsum[i] = (R)blk_unpack(blk_pack(R(1) / hii));
     return;
   }
   // column `lane` of W = L^-1 by forward substitution (registers)
@@ -321,8 +335,9 @@ __global__ void __launch_bounds__(128)
   for (int j = 0; j < 32; ++j) {
     R t = R(0);
     for (int k = max(lane, j); k < 32; ++k) t += A[k][lane] * A[k][j];
-    out[j * 32 + lane] = t;   // element (lane, j), column-major
-    rs += t;
+    const auto st = blk_pack(t);   // element (lane, j), column-major
+    out[j * 32 + lane] = st;
+    rs += (R)blk_unpack(st);
   }
   if (i < N) bsum[i] = rs;
 }
@@ -335,7 +350,8 @@ template <class R>
 void launch_block_setup(const DevState& S, cudaStream_t st) {
   if (S.N == 0) return;
   int nb = (S.N + 31) / 32;
-  k_block_setup<R><<<(nb + 3) / 4, 128, 0, st>>>(S.N, S.ld, S.nl, S.nmat, S.M, (const R*)S.Dg, (R*)S.binv,
+  k_block_setup<R><<<(nb + 3) / 4, 128, 0, st>>>(S.N, S.ld, S.nl, S.nmat, S.M, (const R*)S.Dg,
+                                                 (typename BlockStore<R>::T*)S.binv,
                                                  (R*)S.bsum, S.rebuild_count, S.precond_epoch);
   k_precond_mark<<<1, 1, 0, st>>>(S.rebuild_count, S.precond_epoch);
 }
@@ -343,11 +359,11 @@ void launch_block_setup(const DevState& S, cudaStream_t st) {
 // y = M_b^-1 r for the warp's block: every lane of a full warp, i = 32b +
 // lane, r_i of this lane (zero where no atom).
 template <class R>
-__device__ inline R block_apply(const R* __restrict__ binv, int i, R ri) {
-  const R* col = binv + (size_t)(i >> 5) * 1024 + (i & 31);
+__device__ inline R block_apply(const typename BlockStore<R>::T* __restrict__ binv, int i, R ri) {
+  const typename BlockStore<R>::T* col = binv + (size_t)(i >> 5) * 1024 + (i & 31);
   R b[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) b[j] = __ldg(col + j * 32);   // all 32 loads in flight
+  for (int j = 0; j < 32; ++j) b[j] = (R)blk_unpack(__ldg(col + j * 32));   // all 32 loads in flight
   R y = R(0);
 #pragma unroll
   for (int j = 0; j < 32; ++j) y += b[j] * __shfl_sync(CT_FULL, ri, j);
@@ -524,7 +540,7 @@ template <class R>
 __global__ void __launch_bounds__(256)
     k_cg_init(int N, int ld, const int2* __restrict__ nl, const int* __restrict__ nmat,
                           const void* __restrict__ M, const R* __restrict__ Dg, const R* __restrict__ dinv,
-                          const R* __restrict__ binv,
+                          const typename BlockStore<R>::T* __restrict__ binv,
                           const int* __restrict__ type, const int* __restrict__ rep, TypeParams T,
                           double* __restrict__ q, const R* __restrict__ qr, const R* __restrict__ d,
                           R* __restrict__ r, R* __restrict__ y, R* __restrict__ v, R* __restrict__ dqv,
@@ -653,7 +669,8 @@ __global__ void __launch_bounds__(256)
 // the loop issues no FP64 arithmetic per atom.
 template <class R>
 __global__ void __launch_bounds__(256)
-    k_cg_up(int N, const int* __restrict__ rep, const R* __restrict__ dinv, const R* __restrict__ binv,
+    k_cg_up(int N, const int* __restrict__ rep, const R* __restrict__ dinv,
+            const typename BlockStore<R>::T* __restrict__ binv,
             int* __restrict__ conv,
             int* __restrict__ iters, int* __restrict__ itp, const R* __restrict__ w, const R* __restrict__ d,
             R* __restrict__ dqv, R* __restrict__ r, R* __restrict__ p, R* __restrict__ s,
@@ -799,7 +816,7 @@ template <class R>
 void launch_cg_begin(const DevState& S, const TypeParams& T, cudaStream_t st, double tol, const double* rhs) {
   k_cg_prep<<<1, 256, 0, st>>>(S.N, S.R, S.cg, S.cg_rmax, S.cg_conv, S.cg_iters, S.cg_it, S.cg_blocks, S.cg_active);
   if (S.N == 0) return;
-  const R* binv = S.precond ? (const R*)S.binv : nullptr;
+  const auto* binv = S.precond ? (const typename BlockStore<R>::T*)S.binv : nullptr;
   k_cg_extrap<R><<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.q, S.cqh1, S.cqh2, (R*)S.qr,
                                                     (const R*)(S.precond ? S.bsum : S.dinv),
                                                     (R*)S.cd, S.rep, S.cg, S.R, S.cg_hist, S.cg_blocks);
@@ -893,7 +910,8 @@ void launch_cg_up(const DevState& S, const SolveCfg& cfg, cudaStream_t st) {
   // is what ends the loop (it finds the loop inactive and clears the
   // condition)
   int grid = stride_grid(S.N, S.nsm, (const void*)k_cg_up<R>);
-  k_cg_up<R><<<grid, 256, 0, st>>>(S.N, S.rep, (const R*)S.dinv, S.precond ? (const R*)S.binv : nullptr,
+  k_cg_up<R><<<grid, 256, 0, st>>>(S.N, S.rep, (const R*)S.dinv,
+                                   S.precond ? (const typename BlockStore<R>::T*)S.binv : nullptr,
                                    S.cg_conv, S.cg_iters, S.cg_it, (const R*)S.cw,
                                    (const R*)S.cd, (R*)S.cdq, (R*)S.cr, (R*)S.cp, (R*)S.cs, (R*)S.cy, S.cg, S.cg_rmax,
                                    S.R, S.cg_blocks, S.cg_active, S.err, cfg.tol, cfg.max_iter, cfg.use_cond,
