@@ -252,6 +252,7 @@ __global__ void __launch_bounds__(PG_APB * PG_GRP)
              (size_t)g * cap_cov;
   int* s_j = reinterpret_cast<int*>(reinterpret_cast<Ent<R>*>(smem_raw) + (size_t)PG_APB * cap_cov) +
              (size_t)PG_APB * cap_cov + (size_t)g * cap_cov;
+  int* s_lv = s_j + (size_t)PG_APB * cap_cov;   // the live bonds (r < S), in list order
   int i = blockIdx.x * PG_APB + g;
   bool live = i < N;
   int nc = 0, ti = 0;
@@ -285,8 +286,14 @@ __global__ void __launch_bounds__(PG_APB * PG_GRP)
     }
   }
   __syncthreads();
+  // bonds past S have f_c = 0 and no parameter derivative: the loops below
+  // run over the live ones only, in list order
+  const int nlive = compact_live<PG_GRP>(
+      live, nc, l, s_lv, [&](int e) { return s_e[e].r < P.S[ti * 2 + s_t[e]]; }, [](int) {});
+  __syncwarp();
   if (live && (acc.wv != 0.0 || acc.wt != 0.0)) {
-    for (int e = l; e < nc; e += PG_GRP) {
+    for (int b_ = l; b_ < nlive; b_ += PG_GRP) {
+      const int e = s_lv[b_];
       S ex, ey, ez, re;
       ent_vec(s_e[e], ex, ey, ez, re);
       int tj = s_t[e], pb = ti * 2 + tj;
@@ -295,7 +302,8 @@ __global__ void __launch_bounds__(PG_APB * PG_GRP)
       if (val(fc) == R(0)) continue;
       // environment sums of bond e (recomputed)
       S z[2] = {S(R(0)), S(R(0))};
-      for (int k = 0; k < nc; ++k) {
+      for (int kk = 0; kk < nlive; ++kk) {
+        const int k = s_lv[kk];
         if (k == e) continue;
         S kx, ky, kz, rk;
         ent_vec(s_e[k], kx, ky, kz, rk);
@@ -374,7 +382,8 @@ __global__ void __launch_bounds__(PG_APB * PG_GRP)
         ST sg_[2], sc_[2], sd_[2], sh_[2], sa_[2], sR(0.0), sS(0.0);
         for (int ll = 0; ll < 2; ++ll) sg_[ll] = sc_[ll] = sd_[ll] = sh_[ll] = sa_[ll] = ST(0.0);
         bool any = false;
-        for (int k = 0; k < nc; ++k) {
+        for (int kk = 0; kk < nlive; ++kk) {
+          const int k = s_lv[kk];
           if (k == e || s_t[k] != tk) continue;
           S kx, ky, kz, rk;
           ent_vec(s_e[k], kx, ky, kz, rk);
@@ -502,7 +511,7 @@ static cudaError_t pgrad_launch(const DevState& D, const ParamsT<R>& P, const do
                                 const double* dir, const double* qdir, double* grad, double* vout,
                                 cudaStream_t st) {
   using R4 = typename Vec4<R>::T;
-  size_t sm = (size_t)PG_APB * D.cap_cov * (sizeof(Ent<R>) + 2 * sizeof(int));
+  size_t sm = (size_t)PG_APB * D.cap_cov * (sizeof(Ent<R>) + 3 * sizeof(int));
   cudaError_t e = cudaFuncSetAttribute(k_pgrad_cov<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_pgrad_cov<R, S><<<(D.N + PG_APB - 1) / PG_APB, PG_APB * PG_GRP, sm, st>>>(

@@ -347,6 +347,30 @@ __device__ inline void lane_flush(RepAcc<NV>& a, double* out, int stride) {
   block_flush<NV>(w, out, stride);
 }
 
+// The live entries of a lane group's atom (G lanes per atom, G a power of
+// two up to 32), in list order, into s_lv: entry e < nc is live when
+// is_live(e). The count is returned to every lane of the group; dead(e) is
+// called by the lane that tested an entry found not live. Lane l of the
+// group tests e = l, l + G, ... (the entries it staged). Every lane of the
+// warp takes part (ballots).
+template <int G, class Live, class Dead>
+__device__ inline int compact_live(bool live, int nc, int l, int* s_lv, Live is_live, Dead dead) {
+  const int shift = (int)(threadIdx.x & 31) - l;   // the group's first lane in the warp
+  const unsigned gm = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+  const int rounds = (int)__reduce_max_sync(CT_FULL, live ? (unsigned)((nc + G - 1) / G) : 0u);
+  int n = 0;
+  for (int r = 0; r < rounds; ++r) {
+    const int e = r * G + l;
+    const bool inr = live && e < nc;
+    const bool lv = inr && is_live(e);
+    const unsigned m = (__ballot_sync(CT_FULL, lv) >> shift) & gm;
+    if (lv) s_lv[n + __popc(m & ((1u << l) - 1u))] = e;
+    else if (inr) dead(e);
+    n += __popc(m);
+  }
+  return n;
+}
+
 // Grid-wide "am I the last block" after this block's atomics.
 __device__ inline bool last_block(int* counter) {
   __shared__ bool am_last;

@@ -132,30 +132,8 @@ __device__ inline void cutoff_fp64(int i, int j, int cd, int pb, const double* _
 // f_c > 0 take part in bond orders and three-body terms; the rest (the skin,
 // about a fifth of the entries in hot MD) get their trivial outputs at once
 // and the bond and three-body loops run over the compacted live list, in
-// list order (the sums add in the same order as over the full list).
-
-// The live bonds of this lane group's atom, in list order, into s_lv; the
-// count is returned to every lane of the group. dead(e) is called by the
-// lane that tested a bond past the cutoff. Every lane of the warp takes
-// part (ballots).
-template <int G, class R, class Dead>
-__device__ inline int compact_live(bool live, int nc, int l, const R* s_fc, int* s_lv, Dead dead) {
-  const int shift = (int)(threadIdx.x & 31) - l;   // the group's first lane in the warp
-  const unsigned gm = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
-  const int rounds = (int)__reduce_max_sync(CT_FULL, live ? (unsigned)((nc + G - 1) / G) : 0u);
-  int n = 0;
-  for (int r = 0; r < rounds; ++r) {
-    const int e = r * G + l;
-    const bool inr = live && e < nc;
-    const bool lv = inr && s_fc[e] > R(0);
-    const unsigned m = (__ballot_sync(CT_FULL, lv) >> shift) & gm;
-    if (lv) s_lv[n + __popc(m & ((1u << l) - 1u))] = e;
-    else if (inr) dead(e);
-    n += __popc(m);
-  }
-  return n;
-}
-
+// list order (the sums add in the same order as over the full list;
+// compact_live in internal.cuh).
 template <class R, int G>
 __global__ void __launch_bounds__(CB)
 k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
@@ -222,7 +200,7 @@ k_bond(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
   }
   __syncthreads();
   int my_stiff = 0, my_flag = 0;
-  const int nlive = compact_live<G, R>(live, nc, l, s_fc, s_lv, [&](int e) {
+  const int nlive = compact_live<G>(live, nc, l, s_lv, [&](int e) { return s_fc[e] > R(0); }, [&](int e) {
     R4 out;
     out.x = R(1); out.y = R(0); out.z = R(0); out.w = R(0);
     bo[(size_t)i * cap_cov + e] = out;
@@ -600,7 +578,7 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
     }
   }
   __syncwarp();
-  const int nlive = compact_live<G, R>(live, nc, l, s_fc, s_lv, [&](int e) {
+  const int nlive = compact_live<G>(live, nc, l, s_lv, [&](int e) { return s_fc[e] > R(0); }, [&](int e) {
     typename Vec4<O>::T z;
     z.x = O(0); z.y = O(0); z.z = O(0); z.w = O(0);
     gslot[(size_t)i * cap_cov + e] = z;
