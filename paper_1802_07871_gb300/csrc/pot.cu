@@ -24,6 +24,7 @@ namespace ct {
 // Covalent kernels: blocks of CB threads, G lanes per atom (G = 4, 8 or 16,
 // tuned on the live lists by tune_cov), CB / G atoms per block.
 #define CB 128
+#define GATHER_MINB 3
 // Bonds whose repulsive radial derivative lambda1 * A e^(-lambda1 r) exceeds
 // this (eV/A) get their pair term in FP64 on the FP32 path (queued by the
 // bond pass, evaluated by k_stiff): there the repulsive and attractive
@@ -684,8 +685,13 @@ k_cov_force(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ 
 // FP64 store, half kick, kinetic energy and per-replica sums. Threads take
 // 256-atom tiles strided over the grid, so the FP64 per-replica reductions
 // are paid once per thread, not once per atom.
+// Blocks per SM the register allocation must allow: three for the step
+// variant at depth 4 (85 registers, no spills; 37.5% occupancy instead of
+// 25%), one elsewhere (deeper pipelines and the virial spill under a cap).
+template <int PB, bool VIR> constexpr int gather_min_blocks() { return (!VIR && PB <= 4) ? GATHER_MINB : 1; }
+
 template <class R, int PB, bool VIR>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, gather_min_blocks<PB, VIR>())
     k_coul_gather(int N, int cap_cov, int ld, const typename Vec4<R>::T* __restrict__ u,
                   const int* __restrict__ rep, const RepInfo* __restrict__ reps, const int2* __restrict__ nl,
                    const int* __restrict__ ncov, const int* __restrict__ nall,
