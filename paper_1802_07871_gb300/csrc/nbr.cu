@@ -345,40 +345,45 @@ __global__ void __launch_bounds__(BW * 32)
 }
 
 // Row-major scratch -> column-major lists (entry e of atom i at e * ld + i),
-// 32 atoms x 32 entries per tile through shared memory; tiles past every
-// row's end are skipped. Grid-strided over the tiles. Entry e of atom a
-// comes from scratch slot e (covalent, e < ncov), cap_cov + e - ncov (core,
-// e < nfix) or cap_all - 1 - (e - nfix) (shell).
+// 32 atoms x TE entries per tile through shared memory (TE / 4 loads and
+// stores in flight per thread); tiles past every row's end are skipped.
+// Grid-strided over the tiles. Entry e of atom a comes from scratch slot e
+// (covalent, e < ncov), cap_cov + e - ncov (core, e < nfix) or
+// cap_all - 1 - (e - nfix) (shell).
+#define TE 64
 __global__ void __launch_bounds__(256)
     k_list_transpose(int N, int cap_cov, int cap_all, int ld, const int2* __restrict__ lst,
                      const int* __restrict__ ncov, const int* __restrict__ nfix, const int* __restrict__ nall,
                      int2* __restrict__ nl, const int* __restrict__ flag) {
-  __shared__ int2 tile[32][33];
+  __shared__ int2 tile[32][TE + 1];
   if (*flag == 0) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int ta = (N + 31) / 32, te = (cap_all + 31) / 32;
+  const int ta = (N + 31) / 32, te = (cap_all + TE - 1) / TE;
   for (long long t = blockIdx.x; t < (long long)ta * te; t += gridDim.x) {
-    const int a0 = (int)(t % ta) * 32, e0 = (int)(t / ta) * 32;
+    const int a0 = (int)(t % ta) * 32, e0 = (int)(t / ta) * TE;
     int na = a0 + tx < N ? nall[a0 + tx] : 0;
     int nmax = __reduce_max_sync(CT_FULL, (unsigned)na);
     if (e0 >= nmax) continue;   // uniform over the block: every warp reads the same 32 counts
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      int a = a0 + ty + 8 * r, e = e0 + tx;
-      if (a < N && e < nall[a]) {
-        int nc = ncov[a], nf = nfix[a];
-        int src = e < nc ? e : (e < nf ? cap_cov + (e - nc) : cap_all - 1 - (e - nf));
-        tile[ty + 8 * r][tx] = lst[(size_t)a * cap_all + src];
+      const int a = a0 + ty + 8 * r;
+      if (a < N) {
+        const int n = nall[a], nc = ncov[a], nf = nfix[a];
+#pragma unroll
+        for (int h = 0; h < TE / 32; ++h) {
+          const int e = e0 + 32 * h + tx;
+          if (e < n) {
+            const int src = e < nc ? e : (e < nf ? cap_cov + (e - nc) : cap_all - 1 - (e - nf));
+            tile[ty + 8 * r][32 * h + tx] = lst[(size_t)a * cap_all + src];
+          }
+        }
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      int e = e0 + ty + 8 * r, a = a0 + tx;
-      if (e < na) {
-        int2 v = tile[tx][ty + 8 * r];
-        nl[(size_t)e * ld + a] = v;
-      }
+    for (int r = 0; r < TE / 8; ++r) {
+      const int e = e0 + ty + 8 * r, a = a0 + tx;
+      if (e < na) nl[(size_t)e * ld + a] = tile[tx][ty + 8 * r];
     }
     __syncthreads();
   }
