@@ -689,6 +689,8 @@ def run_ours(a):
         ferr = float(np.max(np.abs(F_mixed0 - F64)) / rms)
         eerr = float(abs(E_mixed0 - E64) / n)
         qerr = float(np.max(np.abs(q_mixed0 - q64)))
+        # per-component relative error with a 1e-3 eV/A floor
+        cerr = float(np.max(np.abs(F_mixed0 - F64) / np.maximum(np.abs(F64), 1e-3)))
         k64 = max(2, min(a.steps, 10))
         s64.step(2, DT)
         barrier()
@@ -701,7 +703,7 @@ def run_ours(a):
         ms64 = f0.elapsed_time(f1)
         fp64 = {"value": n * k64 * world / (ms64 / 1e3), "ms_per_step": ms64 / k64, "steps": k64,
                 "mixed_vs_fp64_force_err": ferr, "mixed_vs_fp64_energy_err_eV_per_atom": eerr,
-                "mixed_vs_fp64_charge_err_e": qerr}
+                "mixed_vs_fp64_charge_err_e": qerr, "mixed_vs_fp64_force_component_rel_err_floor_1e-3": cerr}
         s64.close()
         # the same comparison at the hot state the timed MD reached: the
         # mixed forces of its last step against an FP64 evaluation there
@@ -714,6 +716,8 @@ def run_ours(a):
         s64.close()
         rms_h = float(np.sqrt(np.mean(F64h ** 2)))
         fp64["hot_state"] = {"mixed_vs_fp64_force_err": float(np.max(np.abs(F_hot - F64h)) / rms_h),
+                             "mixed_vs_fp64_force_component_rel_err_floor_1e-3":
+                                 float(np.max(np.abs(F_hot - F64h) / np.maximum(np.abs(F64h), 1e-3))),
                              "rms_force_eV_per_A": rms_h,
                              "mixed_vs_fp64_energy_err_eV_per_atom": float(abs(E_hot - E64h) / n),
                              "mixed_fp64_atoms": st_hot["fp64_atoms"], "mixed_fp64_pair_bonds": st_hot["fp64_bonds"],
