@@ -274,6 +274,31 @@ def test_full_size_slab_20k_sampled(prec):
     assert np.max(np.abs(g["forces"].sum(0))) < (1e-6 if prec == "fp64" else 5e-2)
 
 
+@pytest.fixture(scope="module")
+def slab_20k_after_100_steps():
+    from paper_1802_07871_gb300 import ctbop
+    s = st.stepped_slab_20k()
+    md = ctbop.System(P1, precision="fp64")
+    md.load(s, velocities=st.maxwell_boltzmann(s.types, 2000.0, seed=102, frozen=s.frozen))
+    md.compute()
+    md.step(100, 0.5)
+    x = md.get("positions")
+    md.close()
+    s100 = st.Structure(s.name, x, s.types, s.box, s.pbc, s.frozen)
+    return s100, oracle_eval(s100, P1)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_slab_20k_after_100_fp64_steps(prec, slab_20k_after_100_steps):
+    """The bars at an MD state of the 19,488-atom slab, every atom: after 100
+    FP64 GPU steps of 0.5 fs from 2000 K (bottom bilayers frozen), each GPU
+    path evaluated at those positions against the oracle's full solve."""
+    s100, o = slab_20k_after_100_steps
+    g = gpu_eval(s100, P1, prec)
+    compare(g, o, s100.n, prec)
+    assert g["status"]["rc"] == "OK"
+
+
 def test_full_size_slab_1m_every_atom():
     """The ~1.005M-atom stepped slab with C adatoms, mixed precision, in the
     launch configuration the benchmark times, checked at every atom: the
