@@ -90,6 +90,8 @@ struct ctbop_system {
   float gather_ms[3] = {0.f, 0.f, 0.f};
   bool gather_forced = false;
   float cov_ms[3] = {0.f, 0.f, 0.f};
+  // a step chunk's starting state, for redoing it after a list overflow
+  double *snap_x = nullptr, *snap_v = nullptr, *snap_F = nullptr, *snap_q = nullptr;
   bool cov_forced = false;
   bool cov_retune = false;       // time the lanes again once MD has moved the atoms
   int64_t cov_tuned_at = 0;      // steps at that tuning
@@ -325,6 +327,13 @@ static int alloc_atoms(ctbop_system* s) {
     CK(dalloc(s->atom_buf, &sg, (size_t)N * 24));
     S.stage = sg;
   }
+  // kept allocated: a stream-ordered allocation per ctbop_step call returned
+  // its memory to the pool's owner at every synchronisation and cost about
+  // 0.2 ms per call at 1M atoms
+  CK(dalloc(s->atom_buf, &s->snap_x, 3 * (size_t)N + 1));
+  CK(dalloc(s->atom_buf, &s->snap_v, 3 * (size_t)N + 1));
+  CK(dalloc(s->atom_buf, &s->snap_F, 3 * (size_t)N + 1));
+  CK(dalloc(s->atom_buf, &s->snap_q, (size_t)N + 1));
   CK(dalloc(s->atom_buf, &S.cqh1, (size_t)N));
   CK(dalloc(s->atom_buf, &S.cqh2, (size_t)N));
   CK(dalloc(s->atom_buf, &S.ncov, (size_t)N));
@@ -1189,13 +1198,8 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
   DevState& S = s->S;
   const int64_t chunk = 100;
   // snapshot buffers for redoing a chunk after a list overflow
-  double *sx = nullptr, *sv = nullptr, *sF = nullptr, *sq = nullptr;
+  double *sx = s->snap_x, *sv = s->snap_v, *sF = s->snap_F, *sq = s->snap_q;
   size_t N = S.N;
-  Scratch scr(s->stream);
-  CK(scr.alloc(&sx, 3 * N + 1));
-  CK(scr.alloc(&sv, 3 * N + 1));
-  CK(scr.alloc(&sF, 3 * N + 1));
-  CK(scr.alloc(&sq, N + 1));
   int result = CTBOP_OK;
   int64_t done = 0;
   int redo = 0;
@@ -1345,6 +1349,13 @@ int ctbop_get(ctbop_system* s, int what, void* dst, int mem) {
     void* tmp = S.stage;
     CK(launch_permute((int)N, s->d_order, src, tmp, (int)(width / N), false, s->stream));
     CK(cudaMemcpyAsync(dst, tmp, width, kind, s->stream));
+  } else if (rows == 1 || pitch == width) {
+    CK(cudaMemcpyAsync(dst, src, width * rows, kind, s->stream));
+  } else if (mem == CTBOP_HOST && width * rows <= 24 * N) {
+    // strided per-replica sums: packed on the device first (a strided copy
+    // straight to host memory took 0.2 ms for a few bytes), then one copy
+    CK(cudaMemcpy2DAsync(S.stage, width, src, pitch, width, rows, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(dst, S.stage, width * rows, kind, s->stream));
   } else {
     CK(cudaMemcpy2DAsync(dst, width, src, pitch, width, rows, kind, s->stream));
   }
