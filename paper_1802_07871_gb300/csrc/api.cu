@@ -33,15 +33,20 @@ struct DevBuf {
 
 // Temporary device buffers of one call, stream-ordered, freed on every
 // return path (error returns included).
+// From the system's own memory pool (which keeps what it has mapped: a pool
+// that returns its memory at every synchronisation made each call pay about
+// 0.2 ms at 1M atoms to map it again), or the device's default pool.
 struct Scratch {
   cudaStream_t st;
+  cudaMemPool_t pool;
   std::vector<void*> ptrs;
-  explicit Scratch(cudaStream_t s) : st(s) {}
+  explicit Scratch(cudaStream_t s, cudaMemPool_t p = nullptr) : st(s), pool(p) {}
   Scratch(const Scratch&) = delete;
   Scratch& operator=(const Scratch&) = delete;
   template <class T> cudaError_t alloc(T** out, size_t n) {
     void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(n, 1) * sizeof(T), st);
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    cudaError_t e = pool ? cudaMallocFromPoolAsync(&q, bytes, pool, st) : cudaMallocAsync(&q, bytes, st);
     if (e != cudaSuccess) return e;
     ptrs.push_back(q);
     *out = static_cast<T*>(q);
@@ -59,6 +64,7 @@ struct ctbop_system {
   ctbop_options o;
   cudaStream_t stream = nullptr;       // stream all work is ordered on
   cudaStream_t own_stream = nullptr;   // used when the caller gives none
+  cudaMemPool_t pool = nullptr;        // per-call scratch (Scratch)
   cudaStream_t body_stream = nullptr;
   void* noalloc_scratch = nullptr;     // the allocation-free energy's scratch array on this device
   std::string err;
@@ -881,8 +887,22 @@ int ctbop_create(const ctbop_params* p, const ctbop_options* o, ctbop_system** o
   }
   s->stream = s->own_stream;
   {
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = dev;
+    if (cudaMemPoolCreate(&s->pool, &pp) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      s->pool = nullptr;   // the default pool then
+      cudaGetLastError();
+    }
+  }
+  {
     std::string why;
     if (noalloc_setup(&s->noalloc_scratch, why)) {
+      if (s->pool) cudaMemPoolDestroy(s->pool);
       cudaFreeHost(s->h_int);
       cudaStreamDestroy(s->body_stream);
       cudaStreamDestroy(s->own_stream);
@@ -978,6 +998,7 @@ int ctbop_destroy(ctbop_system* s) {
   if (s->body_stream) cudaStreamDestroy(s->body_stream);
   if (s->own_stream) cudaStreamDestroy(s->own_stream);
   if (s->h_int) cudaFreeHost(s->h_int);
+  if (s->pool) cudaMemPoolDestroy(s->pool);
   delete s;
   return CTBOP_OK;
 }
@@ -1310,7 +1331,7 @@ int ctbop_get(ctbop_system* s, int what, void* dst, int mem) {
     // computed from the current lists, which an evaluation leaves valid
     if (!s->have_forces) return fail(s, CTBOP_ERR_STATE, "coordination: compute or step first");
     if (N == 0) return CTBOP_OK;
-    Scratch scr(s->stream);
+    Scratch scr(s->stream, s->pool);
     double* tmp = nullptr;
     CK(scr.alloc(&tmp, N));
     if (s->mixed) launch_coordination<float>(S, s->Pf, tmp, s->stream);
@@ -1479,7 +1500,7 @@ static int param_grad_impl(ctbop_system* s, const double* w_E, const double* E_r
   *loss_out = loss;
   double *d_w = nullptr, *d_one = nullptr, *d_g = nullptr, *d_dir = nullptr, *d_v = nullptr, *d_cg = nullptr;
   double *d_h1 = nullptr, *d_h2 = nullptr, *d_q0 = nullptr, *d_lam = nullptr;
-  Scratch scr(st);
+  Scratch scr(st, s->pool);
   if (scr.alloc(&d_w, R) || scr.alloc(&d_one, R) || scr.alloc(&d_g, 2 * PG_NPARAM) ||
       scr.alloc(&d_dir, (size_t)3 * N) || scr.alloc(&d_v, N) || scr.alloc(&d_cg, (size_t)R * CG_STRIDE) ||
       scr.alloc(&d_h1, N) || scr.alloc(&d_h2, N) || scr.alloc(&d_q0, N) || scr.alloc(&d_lam, N))
@@ -1779,7 +1800,7 @@ int ctbop_minimize(ctbop_system* s, int64_t max_iter, double fmax, double dt0, d
   const int R = s->R;
   double* fire = nullptr;
   int* ctl = nullptr;
-  Scratch scr(s->stream);
+  Scratch scr(s->stream, s->pool);
   CK(scr.alloc(&fire, (size_t)R * FI_STRIDE));
   CK(scr.alloc(&ctl, 2));
   std::vector<double> fh((size_t)R * FI_STRIDE, 0.0);
@@ -1842,7 +1863,7 @@ int ctbop_rings(ctbop_system* s, double bond_cut, int32_t max_size, int64_t cap,
   if (bond_cut == 0) bond_cut = scc;
   ctbop_ring* d_out = nullptr;
   unsigned long long* d_cnt = nullptr;
-  Scratch scr(s->stream);
+  Scratch scr(s->stream, s->pool);
   CK(scr.alloc(&d_out, (size_t)std::max<int64_t>(cap, 1)));
   CK(scr.alloc(&d_cnt, 1));
   CK(zero_async(s, d_cnt, sizeof(unsigned long long)));
