@@ -25,7 +25,8 @@
 // scalars alpha, beta, c, mu) are FP64. The recursion vectors r, p, s = H p,
 // the iteration's change dq = q - q0, y = M^-1 r, w = H z, d, v, the matrix
 // entries and the gathered y_j are in the working precision (FP32 in the
-// mixed policy, FP64 in the FP64 policy). FP32 recursion vectors keep
+// mixed policy, FP64 in the FP64 policy); the mixed policy stores the
+// block-Jacobi inverses in FP16 (see BlockStore). FP32 recursion vectors keep
 // conjugacy only because r.z is formed from the centred residual (below);
 // dq is folded into the FP64 q once per solve. Rounding of y and d keeps
 // sum z from being exactly zero, so after the solve q is shifted uniformly

@@ -1,21 +1,23 @@
 // pot.cu — bond pass, charge-system assembly and forces.
 //
-// bond pass (k_bond): eight lanes per atom i; i's covalent entries are staged
-//   in shared memory; each lane owns bonds e and sums over the third atoms k
+// bond pass (k_bond): G lanes per atom i (4, 8 or 16, tuned); i's covalent
+//   entries are staged in shared memory and its live bonds (f_c > 0)
+//   compacted; each lane owns live bonds e and sums over the live third atoms k
 //   the environment terms zeta_l,ie = sum_k fc(r_ik) ang_l(cos) e^{alpha_l (r_ie - r_ik)}
 //   (Sec. 2, Eq. 2), then b_ie and db/dzeta_l from the L = 2 form (Eq. 7).
 // assembly (k_assemble): one thread per atom over its column of the list;
 //   the off-diagonal charge Hessian entries M_e = K(r_e) - 2 w_e
 //   (w_e = 1/2 kappa fc B e^{-lambda2 r} (b_ij + b_ji) on covalent entries),
 //   diagonal 2 J + 2 sum w and the Jacobi inverse.
-// covalent forces (k_cov_force): eight lanes per atom; for every entry e the
-//   gradient dE_i/du_e of all terms centred on i (pair part, and the
-//   environment-sum chain rule both with e as bond and e as third atom);
-//   written to a per-bond slot, no atomics.
+// covalent forces (k_cov_force): G lanes per atom over its live bonds; for
+//   every entry e the gradient dE_i/du_e of all terms centred on i (pair
+//   part, and the environment-sum chain rule both with e as bond and e as
+//   third atom); written to a per-bond slot (zero for bonds past S), no
+//   atomics.
 // charge forces + gather (k_coul_gather): one thread per atom over all entries;
 //   F_i = sum_j q_i q_j K'(r) u_ij/r + sum_e slot(i,e) - sum_e slot(j_e, rev_e);
-//   per-atom energy, virial, optional velocity-Verlet half kick; FP64
-//   per-replica sums.
+//   per-atom energy, the virial (evaluations; MD steps leave it out),
+//   optional velocity-Verlet half kick; FP64 per-replica sums.
 #include "internal.cuh"
 #include "kernels.h"
 
