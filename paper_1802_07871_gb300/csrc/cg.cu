@@ -249,6 +249,16 @@ __device__ inline __half blk_pack(float v) { return __float2half_rn(v); }
 __device__ inline double blk_pack(double v) { return v; }
 __device__ inline float blk_unpack(__half h) { return __half2float(h); }
 __device__ inline double blk_unpack(double v) { return v; }
+// Row `lane` of a block inverse, 32 values, with 16-byte stores.
+template <class R>
+__device__ inline void store_block_row(typename BlockStore<R>::T* out, int lane,
+                                       const typename BlockStore<R>::T (&row)[32]) {
+  constexpr int NV = 32 * (int)sizeof(typename BlockStore<R>::T) / 16;
+  uint4* dst = reinterpret_cast<uint4*>(out + (size_t)lane * 32);
+  const uint4* src = reinterpret_cast<const uint4*>(row);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) dst[k] = src[k];
+}
 
 template <class R>
 __global__ void __launch_bounds__(128)
@@ -315,7 +325,10 @@ __global__ void __launch_bounds__(128)
   typename BlockStore<R>::T* out = binv + (size_t)(base >> 5) * 1024;
   if (!ok) {
     __syncwarp();
-    for (int j = 0; j < 32; ++j) out[j * 32 + lane] = blk_pack(j == lane ? R(1) / hii : R(0));
+    __align__(16) typename BlockStore<R>::T row[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) row[j] = blk_pack(j == lane ? R(1) / hii : R(0));
+    store_block_row<R>(out, lane, row);
     if (i < N) bsum[i] = (R)blk_unpack(blk_pack(R(1) / hii));
     return;
   }
@@ -333,13 +346,15 @@ __global__ void __launch_bounds__(128)
   for (int r = 0; r < 32; ++r) A[r][lane] = w[r];   // A now holds W (A[r][c] = W_rc)
   __syncwarp();
   R rs = R(0);
+  __align__(16) typename BlockStore<R>::T row[32];   // row `lane` of the block
+#pragma unroll
   for (int j = 0; j < 32; ++j) {
     R t = R(0);
     for (int k = max(lane, j); k < 32; ++k) t += A[k][lane] * A[k][j];
-    const auto st = blk_pack(t);   // element (lane, j), column-major
-    out[j * 32 + lane] = st;
-    rs += (R)blk_unpack(st);
+    row[j] = blk_pack(t);   // element (lane, j)
+    rs += (R)blk_unpack(row[j]);
   }
+  store_block_row<R>(out, lane, row);
   if (i < N) bsum[i] = rs;
 }
 
@@ -359,15 +374,23 @@ void launch_block_setup(const DevState& S, cudaStream_t st) {
 
 // y = M_b^-1 r for the warp's block: every lane of a full warp, i = 32b +
 // lane, r_i of this lane (zero where no atom).
+// The block is stored row by row (row a = element (a, j) for j = 0..31,
+// contiguous), so a lane reads its row with 16-byte loads (4 in FP16, 16 in
+// FP64; the inverse is symmetric, so the row is also the column).
 template <class R>
 __device__ inline R block_apply(const typename BlockStore<R>::T* __restrict__ binv, int i, R ri) {
-  const typename BlockStore<R>::T* col = binv + (size_t)(i >> 5) * 1024 + (i & 31);
-  R b[32];
+  using BT = typename BlockStore<R>::T;
+  constexpr int NV = 32 * (int)sizeof(BT) / 16;
+  const uint4* rp = reinterpret_cast<const uint4*>(binv + (size_t)(i >> 5) * 1024 + (size_t)(i & 31) * 32);
+  union {
+    uint4 v[NV];
+    BT b[32];
+  } row;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) b[j] = (R)blk_unpack(__ldg(col + j * 32));   // all 32 loads in flight
+  for (int k = 0; k < NV; ++k) row.v[k] = __ldg(rp + k);   // all in flight
   R y = R(0);
 #pragma unroll
-  for (int j = 0; j < 32; ++j) y += b[j] * __shfl_sync(CT_FULL, ri, j);
+  for (int j = 0; j < 32; ++j) y += (R)blk_unpack(row.b[j]) * __shfl_sync(CT_FULL, ri, j);
   return y;
 }
 

@@ -144,7 +144,7 @@ struct DevState {
   int build_shape = 3;          // list-build shape: index into the (warps, stencil batch) table (tuned)
   // charge-CG preconditioner: block-Jacobi on 32-atom blocks (1) or Jacobi (0)
   int precond = 1;
-  void* binv = nullptr;         // [ceil(N/32)][32][32] block inverses, column-major per block: FP16 (FP32 path) or FP64
+  void* binv = nullptr;         // [ceil(N/32)][32][32] block inverses, row by row per block: FP16 (FP32 path) or FP64
   void* bsum = nullptr;         // Real[N]: row sums of the block inverses (d = M^-1 1)
   long long* precond_epoch = nullptr;   // rebuild count the block inverses were formed at (-1: never)
   void* stage = nullptr;        // [N * 24 bytes] staging for per-atom inputs and outputs in the caller's order
