@@ -50,9 +50,27 @@ __device__ inline void bond_order7(R z1, R z2, int pb, const PotParams<R>& P, R&
   db2 = z2 > R(0) ? pre * (t2 / Z2) * n2 * (zn2 / z2) : R(0);
 }
 
+// The cell offsets of a packed code as exact FP32 values: a 10-bit field m
+// placed in the mantissa of 2^23 reads as 2^23 + m, so one subtraction
+// gives m - 512 (the same values an integer conversion gives, without one).
+__device__ inline void unpack_code_f(int c, float& dx, float& dy, float& dz) {
+  const float base = 8388608.0f + 512.0f;
+  dx = __int_as_float(0x4B000000 | (c & 1023)) - base;
+  dy = __int_as_float(0x4B000000 | ((c >> 10) & 1023)) - base;
+  dz = __int_as_float(0x4B000000 | ((c >> 20) & 1023)) - base;
+}
+
 template <class R>
 __device__ inline void rel_vec(const typename Vec4<R>::T& ui, const typename Vec4<R>::T& uj, int cd,
                                R hx, R hy, R hz, R& rx, R& ry, R& rz) {
+  if (sizeof(R) == 4) {
+    float dx, dy, dz;
+    unpack_code_f(cd, dx, dy, dz);
+    rx = (uj.x - ui.x) + (R)dx * hx;
+    ry = (uj.y - ui.y) + (R)dy * hy;
+    rz = (uj.z - ui.z) + (R)dz * hz;
+    return;
+  }
   int dx, dy, dz;
   unpack_code(cd, dx, dy, dz);
   rx = (uj.x - ui.x) + (R)dx * hx;
