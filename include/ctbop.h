@@ -124,6 +124,13 @@ typedef struct ctbop_options {
     int32_t precond;      /* charge-solve preconditioner: CTBOP_PRECOND_BLOCK (default) or CTBOP_PRECOND_JACOBI */
 } ctbop_options;
 
+/* Counters, and the shapes the autotuners keep. The tuners time every
+ * candidate on the live lists after each list allocation (the covalent lane
+ * count again once, 50 MD steps later) and keep the fastest; environment
+ * variables force a choice instead: CTBOP_MV_BATCH (4, 8, 16: matrix-pass
+ * depth), CTBOP_GATHER_BATCH (4, 6, 8), CTBOP_COV_LANES (4, 8, 16),
+ * CTBOP_BUILD_SHAPE ("warps,batch"). CTBOP_NO_GRAPH=1 runs steps as direct
+ * launches with a host-polled charge loop instead of CUDA graphs. */
 typedef struct ctbop_stats {
     int64_t steps;            /* MD steps taken */
     int64_t rebuilds;         /* neighbour-list rebuilds */
