@@ -125,8 +125,8 @@ typedef struct ctbop_options {
 } ctbop_options;
 
 /* Counters, and the shapes the autotuners keep. The tuners time every
- * candidate on the live lists after each list allocation (the covalent lane
- * count again once, 50 MD steps later) and keep the fastest; environment
+ * candidate on the live lists after each list allocation and keep the
+ * fastest; environment
  * variables force a choice instead: CTBOP_MV_BATCH (4, 8, 16: matrix-pass
  * depth), CTBOP_GATHER_BATCH (4, 6, 8), CTBOP_COV_LANES (4, 8, 16),
  * CTBOP_BUILD_SHAPE ("warps,batch"). CTBOP_NO_GRAPH=1 runs steps as direct

@@ -99,8 +99,6 @@ struct ctbop_system {
   // a step chunk's starting state, for redoing it after a list overflow
   double *snap_x = nullptr, *snap_v = nullptr, *snap_F = nullptr, *snap_q = nullptr;
   bool cov_forced = false;
-  bool cov_retune = false;       // time the lanes again once MD has moved the atoms
-  int64_t cov_tuned_at = 0;      // steps at that tuning
   float build_ms[BUILD_SHAPES] = {};
   bool tune_pending = false;
   double g_step_dt = -1.0;
@@ -577,10 +575,6 @@ static int run_direct(ctbop_system* s, const PotParams<Rr>& P, bool md, double d
   return CTBOP_OK;
 }
 
-// MD steps after the first lane tuning at which the covalent lanes are
-// timed again (at the end of the step chunk that reaches it).
-#define COV_RETUNE_STEPS 50
-
 static int read_err(ctbop_system* s, unsigned& bits) {
   CK(cudaStreamSynchronize(s->stream));
   CK(sync_copy(s, &bits, s->S.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
@@ -710,11 +704,7 @@ static int eval_t(ctbop_system* s, const PotParams<Rr>& P, uint32_t flags) {
     int before_c = s->S.cov_lanes;
     cudaError_t e = tune_cg_mv<Rr>(s->S, s->stream, s->mv_ms);
     if (e == cudaSuccess) e = tune_assemble<Rr>(s->S, P, s->T, s->stream, s->asm_ms);
-    if (e == cudaSuccess && !s->cov_forced) {
-      e = tune_cov<Rr>(s->S, P, s->T, s->stream, s->cov_ms, true);
-      s->cov_retune = true;
-      s->cov_tuned_at = s->steps;
-    }
+    if (e == cudaSuccess && !s->cov_forced) e = tune_cov<Rr>(s->S, P, s->T, s->stream, s->cov_ms, true);
     if (e == cudaSuccess && !s->gather_forced) e = tune_gather<Rr>(s->S, P, s->T, s->stream, s->gather_ms);
     if (e != cudaSuccess) return fail(s, CTBOP_ERR_CUDA, std::string("pass tuning: ") + cudaGetErrorString(e));
     s->tune_pending = false;
@@ -1285,30 +1275,6 @@ int ctbop_step(ctbop_system* s, int64_t n_steps, double dt_fs) {
     s->solves += n;
     if (n > 0) s->virial_stale = true;
     if (bits & CT_ERR_CG_MAXITER) { result = fail(s, CTBOP_ERR_CG_NOT_CONVERGED, "charge CG reached max_iter"); break; }
-    if (s->cov_retune && s->steps >= s->cov_tuned_at + COV_RETUNE_STEPS) {
-      // The covalent lanes were timed on the starting configuration, where
-      // the covalent entries per atom can be uniform (an ideal lattice: four
-      // each, which four lanes per atom cover in one round); once MD has
-      // spread them (thermal motion brings second neighbours inside the
-      // covalent radius plus skin) the lane count is timed again, once,
-      // here, on the current state and in its precision mode (its forces
-      // and sums are restored), and the step graph captured again at once
-      // if the count changed.
-      s->cov_retune = false;
-      int before_c = S.cov_lanes;
-      cudaError_t e = s->mixed ? tune_cov<float>(S, s->Pf, s->T, s->stream, s->cov_ms, false)
-                               : tune_cov<double>(S, s->Pd, s->T, s->stream, s->cov_ms, false);
-      if (e != cudaSuccess) { result = fail(s, CTBOP_ERR_CUDA, std::string("lane tuning: ") + cudaGetErrorString(e)); break; }
-      if (S.cov_lanes != before_c) {
-        destroy_graphs(s);
-        if (s->use_graph) {
-          result = s->mixed ? capture_graph<float>(s, s->Pf, true, dt_fs, &s->g_step)
-                            : capture_graph<double>(s, s->Pd, true, dt_fs, &s->g_step);
-          if (result) break;
-          s->g_step_dt = dt_fs;
-        }
-      }
-    }
   }
   cudaStreamSynchronize(s->stream);
   return result;

@@ -159,33 +159,3 @@ def test_every_list_build_shape_gives_identical_lists(prec, monkeypatch):
             continue
         assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
         assert out[2:] == ref[2:]
-
-
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_lanes_timed_again_after_md_steps(prec):
-    """The lane count is timed again once after 50 MD steps (on the moved
-    atoms) and the fastest kept; the forces and energy that retiming leaves
-    are the evaluation's own: a fresh evaluation at the same positions
-    agrees to the charge solve's tolerance."""
-    s = st.stepped_slab_small(8, 4, 6)
-    v = st.maxwell_boltzmann(s.types, 2000.0, seed=3, frozen=s.frozen)
-    sysm = ctbop.System(P1, precision=prec)
-    sysm.load(s, velocities=v)
-    sysm.compute()
-    ms0 = list(sysm.status()["cov_ms"])
-    sysm.step(49, 0.5)
-    assert list(sysm.status()["cov_ms"]) == ms0
-    sysm.step(1, 0.5)
-    d = sysm.status()
-    assert d["cov_ms"] != ms0 and all(m > 0 for m in d["cov_ms"])
-    assert d["cov_ms"][(4, 8, 16).index(d["cov_lanes"])] == min(d["cov_ms"])
-    F1, E1, x = sysm.get("forces"), sysm.get("energy")[0], sysm.get("positions")
-    sysm.step(2, 0.5)   # the new count in the step graph
-    sysm.set_positions(x)
-    sysm.compute()
-    F2, E2 = sysm.get("forces"), sysm.get("energy")[0]
-    sysm.close()
-    rms = np.sqrt(np.mean(F2 ** 2))
-    ftol, etol = (1e-7, 1e-9) if prec == "fp64" else (1e-4, 1e-6)
-    assert np.max(np.abs(F1 - F2)) / rms < ftol
-    assert abs(E1 - E2) / s.n < etol
