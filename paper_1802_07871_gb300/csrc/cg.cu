@@ -244,6 +244,8 @@ __global__ void k_cg_prep(int N, int R, double* __restrict__ cg, unsigned long l
 // their FP16 roundings are too, and d = M^-1 1 is summed from the stored
 // values.
 template <class R> struct BlockStore { using T = R; };
+// largest block-inverse entry kept (FP16's largest finite value is 65504)
+constexpr double kBlockMax = 6.0e4;
 template <> struct BlockStore<float> { using T = __half; };
 __device__ inline __half blk_pack(float v) { return __float2half_rn(v); }
 __device__ inline double blk_pack(double v) { return v; }
@@ -323,13 +325,22 @@ __global__ void __launch_bounds__(128)
     __syncwarp();
   }
   typename BlockStore<R>::T* out = binv + (size_t)(base >> 5) * 1024;
-  if (!ok) {
+  // the diagonal (Jacobi) block instead, where the factorisation fails or
+  // the inverse leaves the stored type's range (FP16: a block with an
+  // eigenvalue below 2e-5, never met with physical parameters); the
+  // preconditioner only has to stay fixed and positive definite
+  auto jacobi_block = [&]() {
     __syncwarp();
+    const bool half = sizeof(typename BlockStore<R>::T) == 2;
+    const R di = half ? min(R(1) / hii, (R)kBlockMax) : R(1) / hii;
     __align__(16) typename BlockStore<R>::T row[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) row[j] = blk_pack(j == lane ? R(1) / hii : R(0));
+    for (int j = 0; j < 32; ++j) row[j] = blk_pack(j == lane ? di : R(0));
     store_block_row<R>(out, lane, row);
-    if (i < N) bsum[i] = (R)blk_unpack(blk_pack(R(1) / hii));
+    if (i < N) bsum[i] = (R)blk_unpack(blk_pack(di));
+  };
+  if (!ok) {
+    jacobi_block();
     return;
   }
   // column `lane` of W = L^-1 by forward substitution (registers)
@@ -345,14 +356,19 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
   for (int r = 0; r < 32; ++r) A[r][lane] = w[r];   // A now holds W (A[r][c] = W_rc)
   __syncwarp();
-  R rs = R(0);
+  R rs = R(0), tmax = R(0);
   __align__(16) typename BlockStore<R>::T row[32];   // row `lane` of the block
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     R t = R(0);
     for (int k = max(lane, j); k < 32; ++k) t += A[k][lane] * A[k][j];
+    tmax = max(tmax, fabs(t));
     row[j] = blk_pack(t);   // element (lane, j)
     rs += (R)blk_unpack(row[j]);
+  }
+  if (sizeof(typename BlockStore<R>::T) == 2 && __any_sync(CT_FULL, !(tmax <= (R)kBlockMax))) {
+    jacobi_block();
+    return;
   }
   store_block_row<R>(out, lane, row);
   if (i < N) bsum[i] = rs;
