@@ -149,6 +149,16 @@ __device__ inline int wrap_cell(int c, int n) {
 // flattens the batch into one candidate sequence that the lanes walk 32 at a
 // time (a lane finds its cell by binary search over the prefix sums).
 //
+// A candidate farther than the list radius from the bounding box of the
+// cell's atoms cannot enter any of their rows: about half of the stencil's
+// candidates on the SiC slabs (the stencil is a 5 x 5 x 5 block of
+// half-radius cells). Each candidate is tested once against the box, and the
+// survivors are staged in shared memory in stencil order; the pair tests
+// against the cell's atoms, the costly part, run only on full batches of 32
+// survivors (the last batch of a cell may be partial). The box test has a
+// 1e-4 relative margin, so the rows are the same, entry for entry, as
+// without it.
+//
 // The atoms of a cell have scattered indices, so the pass writes each atom's
 // entries contiguously (row-major scratch `lst`, one int2 (j, code) per
 // entry: a ballot's entries land on one or two lines) and k_list_transpose
@@ -180,10 +190,19 @@ __global__ void __launch_bounds__(BW * 32)
   __shared__ R4 s_u[BW][32];
   __shared__ int s_i[BW][32];
   __shared__ int s_need[BW][3];
+  // candidates that passed the box test, first in first out (up to 63 held)
+  __shared__ R4 s_cu[BW][64];
+  __shared__ int s_cj[BW][64], s_cc[BW][64];
   if (*flag == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   int need_cov = 0, need_rest = 0, need_tot = 0;   // this lane's maxima over the atoms it owned
+  // the largest list radius squared, widened by 1e-4 (relative) so that
+  // rounding never drops a candidate the pair test below would keep
+  R r2max = P.rall_list2;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r2max = max(r2max, P.rcov_list2[k]);
+  r2max *= R(1.0001);
   for (int g = blockIdx.x * BW + warp; g < C; g += gridDim.x * BW) {
     int nci = cell_count[g];
     if (nci == 0) continue;
@@ -197,12 +216,83 @@ __global__ void __launch_bounds__(BW * 32)
     for (int ib = 0; ib < nci; ib += 32) {
       const int ni = min(32, nci - ib);
       int my_i = -1, cnt_c = 0, cnt_k = 0, cnt_s = 0;
+      // bounding box of this group's atoms (offsets from the cell origin)
+      R lox = R(1e30), loy = R(1e30), loz = R(1e30), hix = R(-1e30), hiy = R(-1e30), hiz = R(-1e30);
       if (lane < ni) {
         my_i = cell_atoms[ci0 + ib + lane];
-        s_u[warp][lane] = u[my_i];
+        const R4 ui = u[my_i];
+        s_u[warp][lane] = ui;
         s_i[warp][lane] = my_i;
+        lox = hix = ui.x;
+        loy = hiy = ui.y;
+        loz = hiz = ui.z;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lox = min(lox, __shfl_xor_sync(CT_FULL, lox, o));
+        loy = min(loy, __shfl_xor_sync(CT_FULL, loy, o));
+        loz = min(loz, __shfl_xor_sync(CT_FULL, loz, o));
+        hix = max(hix, __shfl_xor_sync(CT_FULL, hix, o));
+        hiy = max(hiy, __shfl_xor_sync(CT_FULL, hiy, o));
+        hiz = max(hiz, __shfl_xor_sync(CT_FULL, hiz, o));
       }
       __syncwarp();
+      // Pair tests of the first n staged candidates (one per lane) against
+      // every atom of the group, in staging order, which is stencil order:
+      // each row receives its entries in the same order as without staging.
+      auto pair_tests = [&](int n) {
+        const bool valid = lane < n;
+        int j = -1, cd = 0;
+        R4 uj;
+        uj.x = uj.y = uj.z = uj.w = R(0);
+        R ox = R(0), oy = R(0), oz = R(0);
+        if (valid) {
+          uj = s_cu[warp][lane];
+          j = s_cj[warp][lane];
+          cd = s_cc[warp][lane];
+          int dx, dy, dz;
+          unpack_code(cd, dx, dy, dz);
+          ox = (R)dx * hx;
+          oy = (R)dy * hy;
+          oz = (R)dz * hz;
+        }
+        const int tj = (int)uj.w;
+        const bool zero_off = cd == pack_code(0, 0, 0);
+        for (int ii = 0; ii < ni; ++ii) {
+          const R4 ui = s_u[warp][ii];
+          const int i = s_i[warp][ii];
+          R rx = (uj.x - ui.x) + ox, ry = (uj.y - ui.y) + oy, rz = (uj.z - ui.z) + oz;
+          R r2 = rx * rx + ry * ry + rz * rz;
+          bool self0 = zero_off && j == i;
+          bool in = valid && !self0;
+          bool cov = in && r2 < P.rcov_list2[(int)ui.w * 2 + tj];
+          bool core = in && !cov && r2 < P.rcore_list2;
+          bool shell = in && !cov && !core && r2 < P.rall_list2;
+          unsigned bc = __ballot_sync(CT_FULL, cov), bk = __ballot_sync(CT_FULL, core);
+          unsigned bs = __ballot_sync(CT_FULL, shell);
+          int bcc = __shfl_sync(CT_FULL, cnt_c, ii), bck = __shfl_sync(CT_FULL, cnt_k, ii);
+          int bcs = __shfl_sync(CT_FULL, cnt_s, ii);
+          if (cov) {
+            int pos = bcc + __popc(bc & lt);
+            if (pos < cap_cov) lst[(size_t)i * cap_all + pos] = make_int2(j, cd);
+          } else if (core) {
+            int pos = cap_cov + bck + __popc(bk & lt);
+            if (pos < cap_all) lst[(size_t)i * cap_all + pos] = make_int2(j, cd);
+          } else if (shell) {
+            // from the end of the row down; an overflow (core and shell
+            // meeting) is flagged below and the lists regrow
+            int pos = cap_all - 1 - (bcs + __popc(bs & lt));
+            if (pos >= cap_cov) lst[(size_t)i * cap_all + pos] = make_int2(j, cd);
+          }
+          if (lane == ii) {
+            cnt_c += __popc(bc);
+            cnt_k += __popc(bk);
+            cnt_s += __popc(bs);
+          }
+        }
+        __syncwarp();
+      };
+      int nst = 0;   // staged candidates (warp-uniform, < 32 between batches)
       for (int sb = 0; sb < ns; sb += BC) {
         const int nb = min(BC, ns - sb);
         // this batch's cells: start, count (0 outside an open box) and offset code
@@ -246,12 +336,10 @@ __global__ void __launch_bounds__(BW * 32)
         __syncwarp();
         for (int t0 = 0; t0 < T; t0 += 32) {
           const int t = t0 + lane;
-          const bool valid = t < T;
+          bool keep = false;
           int j = -1, cd = 0;
           R4 uj;
-          uj.x = uj.y = uj.z = uj.w = R(0);
-          R ox = R(0), oy = R(0), oz = R(0);
-          if (valid) {
+          if (t < T) {
             int lo = 0, hi = nb;   // largest k with s_pre[k] <= t
             while (hi - lo > 1) {
               int mid = (lo + hi) >> 1;
@@ -262,47 +350,40 @@ __global__ void __launch_bounds__(BW * 32)
             uj = u[j];
             int dx, dy, dz;
             unpack_code(cd, dx, dy, dz);
-            ox = (R)dx * hx;
-            oy = (R)dy * hy;
-            oz = (R)dz * hz;
+            // distance from the candidate's image to the group's box: past
+            // the list radius, no atom of the group can take it
+            const R px = uj.x + (R)dx * hx, py = uj.y + (R)dy * hy, pz = uj.z + (R)dz * hz;
+            const R bx = max(max(lox - px, px - hix), R(0));
+            const R by = max(max(loy - py, py - hiy), R(0));
+            const R bz = max(max(loz - pz, pz - hiz), R(0));
+            keep = bx * bx + by * by + bz * bz <= r2max;
           }
-          const int tj = (int)uj.w;
-          const bool zero_off = cd == pack_code(0, 0, 0);
-          for (int ii = 0; ii < ni; ++ii) {
-            const R4 ui = s_u[warp][ii];
-            const int i = s_i[warp][ii];
-            R rx = (uj.x - ui.x) + ox, ry = (uj.y - ui.y) + oy, rz = (uj.z - ui.z) + oz;
-            R r2 = rx * rx + ry * ry + rz * rz;
-            bool self0 = zero_off && j == i;
-            bool in = valid && !self0;
-            bool cov = in && r2 < P.rcov_list2[(int)ui.w * 2 + tj];
-            bool core = in && !cov && r2 < P.rcore_list2;
-            bool shell = in && !cov && !core && r2 < P.rall_list2;
-            unsigned bc = __ballot_sync(CT_FULL, cov), bk = __ballot_sync(CT_FULL, core);
-            unsigned bs = __ballot_sync(CT_FULL, shell);
-            int bcc = __shfl_sync(CT_FULL, cnt_c, ii), bck = __shfl_sync(CT_FULL, cnt_k, ii);
-            int bcs = __shfl_sync(CT_FULL, cnt_s, ii);
-            if (cov) {
-              int pos = bcc + __popc(bc & lt);
-              if (pos < cap_cov) lst[(size_t)i * cap_all + pos] = make_int2(j, cd);
-            } else if (core) {
-              int pos = cap_cov + bck + __popc(bk & lt);
-              if (pos < cap_all) lst[(size_t)i * cap_all + pos] = make_int2(j, cd);
-            } else if (shell) {
-              // from the end of the row down; an overflow (core and shell
-              // meeting) is flagged below and the lists regrow
-              int pos = cap_all - 1 - (bcs + __popc(bs & lt));
-              if (pos >= cap_cov) lst[(size_t)i * cap_all + pos] = make_int2(j, cd);
+          const unsigned bk = __ballot_sync(CT_FULL, keep);
+          if (keep) {
+            const int pos = nst + __popc(bk & lt);
+            s_cu[warp][pos] = uj;
+            s_cj[warp][pos] = j;
+            s_cc[warp][pos] = cd;
+          }
+          nst += __popc(bk);
+          __syncwarp();
+          if (nst >= 32) {
+            pair_tests(32);
+            // move the rest (fewer than 32) to the front
+            if (lane < nst - 32) {
+              const R4 a = s_cu[warp][32 + lane];
+              const int b = s_cj[warp][32 + lane], c = s_cc[warp][32 + lane];
+              s_cu[warp][lane] = a;
+              s_cj[warp][lane] = b;
+              s_cc[warp][lane] = c;
             }
-            if (lane == ii) {
-              cnt_c += __popc(bc);
-              cnt_k += __popc(bk);
-              cnt_s += __popc(bs);
-            }
+            nst -= 32;
+            __syncwarp();
           }
         }
         __syncwarp();
       }
+      if (nst > 0) pair_tests(nst);
       // counts of the three parts (k_list_transpose closes the gaps)
       if (lane < ni) {
         int cnt_r = cnt_k + cnt_s;
@@ -433,8 +514,15 @@ static const int kBuildShapes[BUILD_SHAPES][2] = {{2, 64}, {2, 128}, {4, 64}, {4
 
 template <class R, int BW, int BC>
 static void launch_build_s(const DevState& S, const PotParams<R>& P, const int* f, cudaStream_t st) {
-  // about 32 warps resident per SM at every shape
-  const int gb = S.nsm * (32 / BW);
+  // as many blocks as are resident at once (the cells are grid-strided, so
+  // a block past that would run as a tail after the others)
+  static int occ = 0;
+  if (occ == 0) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_build<R, BW, BC>, BW * 32, 0) != cudaSuccess || o < 1) o = 1;
+    occ = o;
+  }
+  const int gb = S.nsm * occ;
   k_build<R, BW, BC><<<gb, BW * 32, 0, st>>>(S.ncells, (const typename Vec4<R>::T*)S.u, S.cell_rep, S.reps,
                                              S.cell_start, S.cell_count, S.cell_atoms, P, S.cap_cov, S.cap_all,
                                              S.lst, S.ncov, S.nfix, S.nall, S.maxcnt, S.err, f);
