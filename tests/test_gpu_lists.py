@@ -6,6 +6,8 @@ oracle's enumeration over every periodic image, self-images included. The
 FP64 path compares exactly. The mixed path tests distances in FP32, where a
 pair within ~1e-6 A of a cutoff can fall either way, so it allows a couple
 of entries per ten thousand atoms."""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -91,5 +93,60 @@ def test_list_counts_match_bruteforce(case, prec):
 def test_list_counts_slab_20k_fp64():
     """The 19,488-atom stepped slab: every cell row of a large open-z grid."""
     s = st.stepped_slab_20k()
+    c, a, mc, ma = _oracle_counts(s)
+    assert _gpu_counts([s], "fp64") == (c, a, mc, ma)
+
+
+def _boundary_structure():
+    """Atoms 1e-9 (relative) inside the list radius of one centre atom and
+    1e-9 outside that of another, in all 26 stencil directions, both centres
+    on cell corners (the 90 A open box has 21^3 cells of 30/7 A); and a third
+    centre with neighbours just inside and just outside the covalent list
+    radii of each type pair."""
+    rall = P1["coulomb"]["r_coul"] + SKIN
+    S = _s_matrix(P1)
+    dirs = [np.array(v, float) / np.linalg.norm(v)
+            for v in itertools.product((-1, 0, 1), repeat=3) if any(v)]
+    xs, ts = [], []
+    for c, f, t0 in [((30.0 + 1e-9, 30.0 - 1e-9, 30.0), 1 - 1e-9, 0),
+                     ((60.0, 30.0 + 1e-9, 30.0 - 1e-9), 1 + 1e-9, 1)]:
+        c = np.array(c)
+        xs.append(c)
+        ts.append(t0)
+        for k, d in enumerate(dirs):
+            xs.append(c + d * rall * f)
+            ts.append(k % 2)
+    c1 = np.array([45.3, 60.7, 29.6])
+    xs.append(c1)
+    ts.append(1)
+    for d, tj, inside in [((1, 0, 0), 0, True), ((-1, 0, 0), 0, False), ((0, 1, 0), 1, True),
+                          ((0, -1, 0), 1, False), ((0, 0, 1), 0, False), ((0, 0, -1), 1, True)]:
+        r = (S[1, tj] + SKIN) * ((1 - 1e-9) if inside else (1 + 1e-9))
+        xs.append(c1 + np.array(d, float) * r)
+        ts.append(tj)
+    x = np.array(xs)
+    return st.Structure("list_radius_boundary", x, np.array(ts, np.int32), np.full(3, 90.0),
+                        np.array([False] * 3))
+
+
+def test_boundary_structure_is_well_separated():
+    """The boundary structure keeps its atoms apart (no accidental bonds or
+    coincident atoms) and puts its boundary pairs where intended."""
+    s = _boundary_structure()
+    d = np.linalg.norm(s.x[:, None, :] - s.x[None, :, :], axis=2)
+    np.fill_diagonal(d, np.inf)
+    assert d.min() > 1.5, d.min()
+    rall = P1["coulomb"]["r_coul"] + SKIN
+    r0 = np.linalg.norm(s.x[1:27] - s.x[0], axis=1)
+    r1 = np.linalg.norm(s.x[28:54] - s.x[27], axis=1)
+    assert np.all(r0 < rall) and np.all(rall - r0 < 1e-7)
+    assert np.all(r1 > rall) and np.all(r1 - rall < 1e-7)
+
+
+def test_list_counts_at_the_list_radii_fp64():
+    """Pairs 1e-9 inside the list radius and the covalent radii are listed,
+    pairs 1e-9 outside are not: exact counts against brute force, for the
+    candidate filter against each cell's bounding box as for the pair test."""
+    s = _boundary_structure()
     c, a, mc, ma = _oracle_counts(s)
     assert _gpu_counts([s], "fp64") == (c, a, mc, ma)
