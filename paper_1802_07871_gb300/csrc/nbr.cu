@@ -150,7 +150,8 @@ __device__ inline int wrap_cell(int c, int n) {
 // time (a lane finds its cell by binary search over the prefix sums).
 //
 // A candidate farther than the list radius from the bounding box of the
-// cell's atoms cannot enter any of their rows: about half of the stencil's
+// cell's atoms (of each group of up to 32 of them) cannot enter any of their
+// rows: about half of the stencil's
 // candidates on the SiC slabs (the stencil is a 5 x 5 x 5 block of
 // half-radius cells). Each candidate is tested once against the box, and the
 // survivors are staged in shared memory in stencil order; the pair tests
