@@ -138,7 +138,7 @@ def peaks():
 # (1.05 x the algorithmic bytes there, atoms stored along a Morton curve), so
 # a full launch is scaled by its entry count. Reset to None when the kernel
 # changes.
-MV_TRAFFIC_CAPTURE = {"bytes": 417.045248e6 + 3.708672e6, "entries": 251366 * 193.9266408344804}
+MV_TRAFFIC_CAPTURE = {"bytes": 416.962816e6 + 4.241920e6, "entries": 251366 * 193.9466117135969}
 
 
 def cg_matvec_bytes(n_atoms, entries, rs):
